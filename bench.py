@@ -1,0 +1,313 @@
+"""Throughput of the free-energy hot path on one GB300 (or N, one process per GPU).
+
+Workload (default): the FFLO scan at N = 1024 -- 64 q along x in [0, 0.2 pi],
+32 h in [0, 0.15], T = 0.002, 256 Delta in [0, 0.2], U = 2 -- in FP32 with
+pairwise/FP64 accumulation and FP64 re-evaluation of near ties.  One step = one
+full pass of the path: trig tables, normal-state sums, the k-sum of every
+(q, h, Delta), argmin, FP64 re-evaluation, phase labels.
+
+value : k-point evaluations per second (one k-point x one Delta x one (q,h,T),
+        both bands), whole job, plan inputs resident in HBM.
+e2e   : the same through the host-buffer C-ABI call ffe_phase_scan.
+Multi-GPU: the q list is split across ranks (no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("parameter points/sec and k-evals/sec at N=1024 (FP32+comp vs FP64 vs surrogate), "
+          "% FP32/MUFU peak")
+MUFU_PER_CLK_PER_SM = 16      # SFU results per clock per SM (4 per SM sub-partition)
+MUFU_PER_KEVAL_PRODUCT = 4.0  # ex2 x 4 (two per band) ... + lg2 below
+SM_MAX_MHZ_FALLBACK = 2070.0
+
+
+def mufu_per_keval(n_ht: int) -> float:
+    """MUFU operations per k-evaluation in the shared-Delta scan layout:
+    4 ex2 + 1 lg2 per (k, Delta, h) and 2 rsqrt + 2 rcp per (k, Delta) shared
+    by the (up to 32) (h, T) outputs of one batch."""
+    per_batch = min(32, n_ht)
+    return 5.0 + 4.0 / per_batch
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(cfg, seconds_target=15.0):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of
+    the workload: the 256-point Delta grid of one (q, h) pair at N = 1024,
+    parallel over Delta with OpenMP."""
+    import numpy as np
+
+    import oracle
+
+    m = oracle.make_model(U=cfg["U"])
+    N = cfg["N"]
+    grid = np.linspace(cfg["lo"], cfg["hi"], cfg["n"])
+    # time a few points to size the sample
+    t0 = time.perf_counter()
+    _, _, threads = oracle.omega_batch(m, N, cfg["qx"][5], 0.0, cfg["h"][3], cfg["T"][0], grid[:threads_hint()])
+    dt = time.perf_counter() - t0
+    per_pt = dt / threads_hint()
+    n_pts = int(max(threads, min(len(grid), seconds_target / max(per_pt, 1e-9))))
+    sample = grid[:n_pts]
+    t0 = time.perf_counter()
+    _, _, threads = oracle.omega_batch(m, N, cfg["qx"][5], 0.0, cfg["h"][3], cfg["T"][0], sample)
+    dt = time.perf_counter() - t0
+    kev = float(N * N) * len(sample)
+    return {"value": kev / dt, "unit": "k-evals/s", "cores": threads, "kind": "oracle",
+            "sample": f"{len(sample)} Delta values of one (q, h) at N={N} (FP64, OpenMP over Delta), {dt:.1f} s"}
+
+
+def threads_hint():
+    import oracle
+
+    return max(1, oracle.max_threads())
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ffe", choices=["ffe", "reference"])
+    ap.add_argument("--N", type=int, default=1024)
+    ap.add_argument("--fp64-sample-q", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    from paper_1412_8754_gb300 import workloads
+
+    cfg = workloads.fflo_scan(N=args.N)
+    cfg["U"] = 2.0
+    ws, rank, local = dist_env()
+
+    if args.impl == "reference":
+        run_reference(args, cfg, ws, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1412_8754_gb300 import ffe
+
+    # shard the q list across ranks (q = 0 stays on every rank: it is the label reference)
+    q_all = cfg["qx"]
+    mine = [0] + [i for i in range(1, len(q_all)) if (i - 1) % ws == rank]
+    qx = q_all[mine]
+    qy = np.zeros_like(qx)
+    n_pts = len(cfg["h"]) * len(cfg["T"])
+    stream = torch.cuda.current_stream()
+    ctx = ffe.Context(prec=ffe.FFE_FP32C, U=cfg["U"])
+    plan = ctx.plan_phase_scan(cfg["N"], qx, qy, cfg["h"], cfg["T"], n=cfg["n"], lo=cfg["lo"], hi=cfg["hi"])
+    info = plan.stats()
+    k_evals, launches = info["k_evals"], info["launches"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        plan.execute(stream)
+    plan.fetch(stream)
+    plan.kernel_ms()  # discard warm-up kernel timings
+    clocks = Clocks(local)
+    barrier()
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # L2 flush between timed steps (outside the event pair)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.execute(stream)
+        e1.record(stream)
+        evs.append((e0, e1))
+    barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    t_total = sum(step_ms) / 1e3
+    kern_ms, kern_n = plan.kernel_ms()
+    res, labels, best = plan.fetch(stream)
+    if ws > 1:
+        t = torch.tensor([t_total], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(t.item())
+        kt = torch.tensor([k_evals], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(kt)
+        k_job = float(kt.item())
+        pts = torch.tensor([float(len(mine) * n_pts)], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(pts)
+        points_job = float(pts.item())
+    else:
+        k_job = k_evals
+        points_job = float(len(mine) * n_pts)
+    value = k_job * args.steps / t_total
+    points_per_s = points_job * args.steps / t_total
+
+    # end to end through the host-buffer C ABI (inputs copied in, results copied out, every step)
+    e2e_times = []
+    for i in range(max(2, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.phase_scan(cfg["N"], qx, qy, cfg["h"], cfg["T"], n=cfg["n"], lo=cfg["lo"], hi=cfg["hi"], stream=stream)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_t = statistics.median(e2e_times[1:])
+    h2d = len(mine) * (cfg["n"] * 8 + n_pts * 24 + len(cfg["h"]) * 8 + 128)
+    d2h = len(mine) * n_pts * 40 + n_pts * 5
+
+    # FP64 plain kernel on a sample of the q list (it is ~60x slower)
+    fp64 = None
+    if args.fp64_sample_q > 0 and rank == 0:
+        ctx64 = ffe.Context(prec=ffe.FFE_FP64, U=cfg["U"])
+        qs = q_all[: args.fp64_sample_q]
+        p64 = ctx64.plan_phase_scan(cfg["N"], qs, np.zeros_like(qs), cfg["h"], cfg["T"], n=cfg["n"],
+                                    lo=cfg["lo"], hi=cfg["hi"])
+        k64 = p64.stats()["k_evals"]
+        p64.execute(stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p64.execute(stream)
+        torch.cuda.synchronize()
+        dt64 = time.perf_counter() - t0
+        fp64 = {"k_evals_per_s": k64 / dt64, "points_per_s": len(qs) * n_pts / dt64,
+                "sample": f"{len(qs)} q x {n_pts} (h,T) x {cfg['n']} Delta at N={cfg['N']}"}
+        p64.destroy()
+        ctx64.close()
+
+    mhz = clk.get("sm_mhz") or SM_MAX_MHZ_FALLBACK
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    peak = n_sm * MUFU_PER_CLK_PER_SM * SM_MAX_MHZ_FALLBACK * 1e6 / 1e9  # Gop/s at the maximum clock
+    mufu_per_launch = mufu_per_keval(n_pts) * k_evals
+    achieved = mufu_per_launch / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else 0.0
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "k-evals/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"fflo_scan N={cfg['N']}: {len(q_all)} q x {len(cfg['h'])} h x "
+                               f"{len(cfg['T'])} T x {cfg['n']} Delta, U={cfg['U']}, FP32 + FP64 ties",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"q sharded over {ws} rank(s)" if ws > 1 else "1 GPU"},
+        "points_per_s": points_per_s,
+        "e2e": {"value": k_job / e2e_t if ws == 1 else None, "unit": "k-evals/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "points_per_s": (len(mine) * n_pts) / e2e_t},
+        "gpu_launches": launches * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s (MUFU)",
+                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "kernel": "ksum_kernel<float,4,PRODUCT>", "kernel_ms": kern_ms, "kernel_launches": kern_n,
+                     "peak_basis": f"{n_sm} SM x {MUFU_PER_CLK_PER_SM}/clk x {SM_MAX_MHZ_FALLBACK:.0f} MHz",
+                     "mufu_per_keval": mufu_per_keval(n_pts)},
+        "fp64": fp64,
+        "clocks": clk,
+        "labels": {"normal": int((labels == 0).sum()), "bcs": int((labels == 1).sum()),
+                   "fflo": int((labels == 2).sum())},
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(cfg)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    plan.destroy()
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_reference(args, cfg, ws, rank):
+    """The oracle (FP64, OpenMP on the host cores) on the same metric, bounded sample per step."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+
+    m = oracle.make_model(U=cfg["U"])
+    N = cfg["N"]
+    grid = np.linspace(cfg["lo"], cfg["hi"], cfg["n"])
+    th = threads_hint()
+    sample = grid[: max(th, 16)]
+    for _ in range(args.warmup):
+        oracle.omega_batch(m, N, cfg["qx"][5], 0.0, cfg["h"][3], cfg["T"][0], sample[:th])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, _, used = oracle.omega_batch(m, N, cfg["qx"][5], 0.0, cfg["h"][3], cfg["T"][0], sample)
+    dt = time.perf_counter() - t0
+    kev = float(N * N) * len(sample) * args.steps
+    v = kev / dt
+    desc = f"{len(sample)} Delta values of one (q, h) at N={N} per step (FP64 oracle, OpenMP)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "k-evals/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"fflo_scan N={N} (bounded sample)"},
+        "cpu_baseline": {"value": v, "unit": "k-evals/s", "cores": used, "kind": "oracle", "sample": desc},
+        "e2e": {"value": v, "unit": "k-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * ffe.h -- C ABI of the GB300 free-energy engine (libffe.so).
+ *
+ * The engine evaluates the mean-field grand free energy of the two-band
+ * iron-pnictide model with intra-band Fulde-Ferrell pairing,
+ *
+ *   Omega(Delta; Q, h, T) = sum_eps sum_k [ F(E+_{eps k}) + F(E-_{eps k})
+ *                                          + E_{eps,-k+Q/2,down} + Delta^2/U ]
+ *
+ * (Sec. 2, Eq. freeene, with F(E) = -T ln(1 + exp(-E/T)), the Bogoliubov
+ * energies E+/- of Eq. enequasiparticle, and the band energies of App. A at
+ * k + Q/2 (spin up) and -k + Q/2 (spin down), Zeeman-shifted by -/+ h), as a
+ * map-reduce over the N x N lattice k = 2 pi (i, j)/N, and minimises it over
+ * Delta (Alg. 1).  Sign of the pairing term: + Delta^2/U per k-point and band
+ * (the printed "- 2|Delta|^2/V" would make Omega fall monotonically with
+ * Delta; with + it reproduces the BCS gap equation; V = 2U).
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an ffe_status; none aborts, exits or traps.
+ *  - All array arguments are HOST memory owned by the caller; the library
+ *    copies what it needs and never keeps a caller pointer after returning.
+ *    `stream` is a cudaStream_t (NULL = the legacy default stream); calls are
+ *    synchronous with respect to the host: results are in the caller's
+ *    arrays when the call returns.
+ *  - Arguments are validated before any device work: N even in [2, 8192],
+ *    T > 0, U > 0, lo <= hi, counts >= 1.  Invalid arguments give FFE_EINVAL
+ *    and leave outputs untouched.
+ *  - A context is not thread-safe; use one context per host thread.  It stays
+ *    usable after any error except FFE_ENOMEM during ffe_create.
+ *  - Precision: FFE_FP64 evaluates every k-point term in IEEE double.
+ *    FFE_FP32C evaluates the k-point terms in FP32 (hardware exp2/log2/rsqrt/
+ *    rcp), sums them in a pairwise tree and accumulates across the lattice in
+ *    FP64, and re-evaluates in FP64 every value whose FP32 error bound could
+ *    change an argmin or a phase label.
+ */
+#ifndef FFE_H
+#define FFE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FFE_API __attribute__((visibility("default")))
+#else
+#define FFE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FFE_OK = 0,
+  FFE_EINVAL = 1,        /* invalid argument (checked before device work)    */
+  FFE_ENOMEM = 2,        /* host or device allocation failed                 */
+  FFE_ECUDA = 3,         /* a CUDA runtime call failed; see ffe_last_error   */
+  FFE_ETIMEOUT = 4,      /* a bounded device-side wait ran out               */
+  FFE_EUNSUPPORTED = 5,  /* valid but not implemented (e.g. model kind)      */
+  FFE_EINTERNAL = 6      /* internal consistency check failed                */
+} ffe_status;
+
+typedef enum { FFE_FP64 = 0, FFE_FP32C = 1 } ffe_precision;
+
+typedef enum { FFE_MODEL_RAGHU2 = 0 } ffe_model_kind;
+
+/* Model of App. A plus the pairing channel of Sec. 2.  Defaults (App. A):
+ * t1=-1, t2=1.3, t3=t4=-0.85, mu=1.54 (two electrons per site). */
+typedef struct {
+  int32_t kind;      /* ffe_model_kind; only FFE_MODEL_RAGHU2                  */
+  int32_t prec;      /* ffe_precision used by every call on the context        */
+  double t1, t2, t3, t4;
+  double mu;         /* chemical potential                                     */
+  double U;          /* pairing strength (> 0): + Delta^2/U per k and band     */
+  double eta_amp;    /* s+- form factor eta(k) = eta_amp cos kx cos ky (Sec. 1) */
+} ffe_model;
+
+/* One free-energy evaluation point. */
+typedef struct {
+  int32_t N;         /* lattice is N x N, N even, 2 <= N <= 8192               */
+  int32_t reserved;  /* must be 0                                              */
+  double qx, qy;     /* Cooper-pair momentum Q (Sec. 2)                        */
+  double h;          /* Zeeman field                                           */
+  double T;          /* temperature k_B T (> 0)                                */
+  double delta;      /* order-parameter amplitude Delta                        */
+} ffe_point;
+
+typedef enum {
+  FFE_SEARCH_GRID = 0,   /* Omega on linspace(lo, hi, n); lowest, ties -> lowest index   */
+  FFE_SEARCH_GOLDEN = 1  /* Delta = lo plus golden-section on [lo, hi], n reductions      */
+} ffe_search_kind;
+
+/* One Delta minimisation (the inner loop of Alg. 1). */
+typedef struct {
+  int32_t N;         /* as in ffe_point                                        */
+  int32_t n;         /* GRID: points (1..65536); GOLDEN: reductions (1..200)   */
+  double qx, qy, h, T;
+  double lo, hi;     /* Delta range, lo <= hi                                  */
+} ffe_param;
+
+/* Result flags */
+#define FFE_FLAG_RESCORED 1   /* omega_star was re-evaluated in FP64           */
+#define FFE_FLAG_EDGE 2       /* argmin at the upper end of the Delta range    */
+#define FFE_FLAG_LOWER 4      /* argmin at Delta = lo                          */
+
+typedef struct {
+  double delta_star;   /* minimising Delta                                     */
+  double omega_star;   /* Omega at delta_star                                  */
+  double omega_lo;     /* Omega at Delta = lo (the normal state when lo = 0)   */
+  double err_bound;    /* bound on |omega_star - FP64 value| (0 if FP64)       */
+  int32_t idx_star;    /* GRID: index into the Delta grid; GOLDEN: -1          */
+  int32_t flags;       /* FFE_FLAG_*                                           */
+} ffe_result;
+
+/* Phase labels (Alg. 1, outer loop over q). */
+#define FFE_PHASE_NORMAL 0
+#define FFE_PHASE_BCS 1
+#define FFE_PHASE_FFLO 2
+
+/* A phase-diagram scan: every q of the list against every (h, T) pair of the
+ * product h-list x T-list (h-major: point p = ih * n_T + iT), all at one N.
+ * The q list must contain Q = (0, 0) (it defines the normal/BCS reference). */
+typedef struct {
+  int32_t N;
+  int32_t n_q;
+  const double* qx;    /* [n_q] */
+  const double* qy;    /* [n_q] */
+  int32_t n_h;
+  int32_t n_T;
+  const double* h;     /* [n_h] */
+  const double* T;     /* [n_T] */
+  int32_t search;      /* ffe_search_kind                                      */
+  int32_t n;           /* grid points or golden reductions                     */
+  double lo, hi;       /* Delta range; lo must be 0 for phase labels           */
+} ffe_scan;
+
+typedef struct ffe_context ffe_context;
+typedef struct ffe_plan ffe_plan;
+
+/* Create a context on the current CUDA device for model *m.  Reads device
+ * properties and allocates nothing large.  *out is NULL on failure. */
+FFE_API ffe_status ffe_create(const ffe_model* m, ffe_context** out);
+
+/* Destroy a context and every plan it still owns.  NULL-safe. */
+FFE_API void ffe_destroy(ffe_context* ctx);
+
+/* Static description of a status code; never NULL. */
+FFE_API const char* ffe_status_string(ffe_status s);
+
+/* Message of the last failing call on ctx (empty string if none). */
+FFE_API const char* ffe_last_error(const ffe_context* ctx);
+
+/* Omega (Eq. freeene summed over both bands) at n independent points.
+ * omega[n] receives Omega; omega_band (NULL or [n][2]) receives the per-band
+ * Omega_eps for the lower (index 0) and upper (index 1) band of App. A.
+ * Points sharing (N, Q) share the per-k band work. */
+FFE_API ffe_status ffe_omega(ffe_context* ctx, const ffe_point* pts, int64_t n,
+                     double* omega, double* omega_band, void* stream);
+
+/* Minimise Omega over Delta for n independent parameter points (Alg. 1,
+ * inner loop).  All params of one call use the same search kind.  Uneven
+ * lattices and grid lengths are packed into one persistent launch.
+ * omega_grid (GRID only; NULL or sum_i ps[i].n doubles) receives each
+ * parameter point's Omega grid, concatenated in input order; err_grid (NULL
+ * or the same size) the FP32 error bound of each grid value (0 where the
+ * value was evaluated or re-evaluated in FP64). */
+FFE_API ffe_status ffe_minimize(ffe_context* ctx, int32_t search, const ffe_param* ps,
+                                int64_t n, ffe_result* out, double* omega_grid,
+                                double* err_grid, void* stream);
+
+/* Phase-diagram scan (Alg. 1): per (q, h, T) the Delta minimum, then per
+ * (h, T) the phase label.  per_point[n_q][n_h*n_T] receives the minima
+ * (q-major), labels[n_h*n_T] the FFE_PHASE_* label, best_q[n_h*n_T] the
+ * index of the winning q (-1 for normal). */
+FFE_API ffe_status ffe_phase_scan(ffe_context* ctx, const ffe_scan* scan,
+                          ffe_result* per_point, int8_t* labels,
+                          int32_t* best_q, void* stream);
+
+/* ---- device-resident plans (for repeated execution) --------------------
+ * A plan holds the packed job table, device buffers and a captured CUDA
+ * graph of one scan.  ffe_plan_execute replays the graph on `stream` without
+ * any host<->device copy and returns without synchronising; ffe_plan_fetch
+ * synchronises the stream and copies the results of the last execution to
+ * host arrays laid out as in ffe_phase_scan. */
+FFE_API ffe_status ffe_plan_phase_scan(ffe_context* ctx, const ffe_scan* scan,
+                               void* stream, ffe_plan** out);
+FFE_API ffe_status ffe_plan_execute(ffe_plan* plan, void* stream);
+FFE_API ffe_status ffe_plan_fetch(ffe_plan* plan, ffe_result* per_point,
+                          int8_t* labels, int32_t* best_q, void* stream);
+typedef struct {
+  double k_evals;          /* k-point evaluations (one k-point, one Delta, one
+                              (q,h,T), both bands) of the main k-sum per execution */
+  double device_bytes;     /* device memory held by the plan                  */
+  int32_t launches;        /* kernel launches per execution                   */
+  int32_t rescored_search; /* FP64 re-evaluations requested by the Delta search
+                              in the last fetched execution                   */
+  int32_t rescored_labels; /* ... by the phase labels in that execution       */
+  int32_t kpt;             /* k-points per thread per k-set of the main k-sum */
+  int32_t block, grid;     /* its launch shape (threads, persistent blocks)   */
+  int32_t work_items;      /* warp work items in its queue                    */
+  int32_t reserved;
+} ffe_plan_info;
+
+/* Static facts about a plan and the FP64 re-evaluation counts of the last
+ * execution whose results were fetched. */
+FFE_API ffe_status ffe_plan_stats(const ffe_plan* plan, ffe_plan_info* info);
+/* Average duration in milliseconds of the plan's main k-sum kernel over the
+ * executions since the last call (CUDA events recorded on the launch stream
+ * around that kernel inside the graph); 0 if none. */
+FFE_API ffe_status ffe_plan_kernel_ms(ffe_plan* plan, double* ms, int32_t* count);
+FFE_API void ffe_plan_destroy(ffe_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFE_H */

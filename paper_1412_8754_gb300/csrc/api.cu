@@ -1,0 +1,747 @@
+// api.cu -- the C ABI of include/ffe.h: argument checking, packing of job
+// tables, device buffers, the launch sequence of one scan, its CUDA graph and
+// the timing ring.  Every arithmetic step of the method runs in the kernels
+// of ksum.cu / tables.cu / search.cu; this file only plans and launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/ffe.h"
+#include "ffe_internal.cuh"
+#include "ksum.cuh"
+#include "plan.h"
+
+using namespace ffe;
+
+// ------------------------------------------------------------------ helpers
+namespace ffe {
+
+void set_err(ffe_context* c, const char* fmt, ...) {
+  if (!c) return;
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  c->err = buf;
+}
+
+ffe_status cuda_fail(ffe_context* c, cudaError_t e, const char* what) {
+  set_err(c, "%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? FFE_ENOMEM : FFE_ECUDA;
+}
+
+#define FFE_CU(call, what)                                  \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+  } while (0)
+
+template <typename T>
+static ffe_status dev_alloc(ffe_context* ctx, ffe_plan* p, T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) count = 1;
+  void* raw = nullptr;
+  cudaError_t e = cudaMalloc(&raw, count * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+  p->allocs.push_back(raw);
+  p->bytes += count * sizeof(T);
+  *ptr = static_cast<T*>(raw);
+  return FFE_OK;
+}
+
+template <typename T>
+static ffe_status upload(ffe_context* ctx, T* dst, const std::vector<T>& src, cudaStream_t s) {
+  if (src.empty()) return FFE_OK;
+  FFE_CU(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s), "upload");
+  return FFE_OK;
+}
+
+// numpy.linspace(lo, hi, n): i*step + lo, last point exactly hi.
+void linspace(double lo, double hi, int n, double* out) {
+  if (n == 1) {
+    out[0] = lo;
+    return;
+  }
+  const double step = (hi - lo) / (double)(n - 1);
+  for (int i = 0; i < n; ++i) out[i] = (double)i * step + lo;
+  out[n - 1] = hi;
+}
+
+static bool valid_N(int32_t N) { return N >= 2 && N <= 8192 && (N % 2) == 0; }
+static bool finite(double x) { return std::isfinite(x); }
+
+}  // namespace ffe
+
+// ------------------------------------------------------------- planning
+namespace ffe {
+
+// Split every group's (batches x k-sets) into warp work items of roughly
+// `target` k-point evaluations, segments of <= kMaxBatchesPerItem batches.
+void build_items(ffe_plan* p) {
+  p->items.clear();
+  p->segs.clear();
+  const int kset_pts = 32 * p->kpt;
+  int64_t poff = 0;
+  for (int gi = 0; gi < (int)p->groups.size(); ++gi) {
+    const GroupDesc& g = p->groups[gi];
+    const int64_t nk = (int64_t)g.N * g.N;
+    const int n_ksets = (int)((nk + kset_pts - 1) / kset_pts);
+    const int sb = std::min(kMaxBatchesPerItem, std::max(1, g.n_batches));
+    for (int b0 = 0; b0 < g.n_batches; b0 += sb) {
+      const int b1 = std::min(g.n_batches, b0 + sb);
+      const int nb = b1 - b0;
+      const double outs = (double)nb * 32.0;
+      int ck = (int)std::max(1.0, std::floor((double)p->item_target / (outs * kset_pts)));
+      ck = std::min(ck, n_ksets);
+      const int n_chunks = (n_ksets + ck - 1) / ck;
+      Segment sg;
+      sg.group = gi;
+      sg.b0 = b0;
+      sg.b1 = b1;
+      sg.n_chunks = n_chunks;
+      sg.partial_off = poff;
+      const int seg_id = (int)p->segs.size();
+      p->segs.push_back(sg);
+      poff += (int64_t)n_chunks * nb * 32;
+      for (int c = 0; c < n_chunks; ++c) {
+        WorkItem w;
+        w.group = gi;
+        w.seg = seg_id;
+        w.chunk = c;
+        w.kset0 = c * ck;
+        w.kset1 = std::min(n_ksets, (c + 1) * ck);
+        w.b0 = b0;
+        w.b1 = b1;
+        w.pad = 0;
+        p->items.push_back(w);
+      }
+    }
+  }
+  p->n_partials = poff;
+  // longest first: the queue hands out big items early, small ones fill the tail
+  std::stable_sort(p->items.begin(), p->items.end(), [&](const WorkItem& a, const WorkItem& b) {
+    const double ca = (double)(a.kset1 - a.kset0) * (a.b1 - a.b0);
+    const double cb = (double)(b.kset1 - b.kset0) * (b.b1 - b.b0);
+    return ca > cb;
+  });
+}
+
+void build_mitems(ffe_plan* p) {
+  p->mitems.clear();
+  const int64_t chunk = 32768;
+  int64_t poff = 0;
+  int counter = 0;
+  for (int gi = 0; gi < (int)p->groups.size(); ++gi) {
+    const GroupDesc& g = p->groups[gi];
+    const int64_t nk = (int64_t)g.N * g.N;
+    const int n_chunks = (int)((nk + chunk - 1) / chunk);
+    for (int hb = 0; hb * 32 < g.n_h; ++hb) {
+      for (int c = 0; c < n_chunks; ++c) {
+        MItem m;
+        m.group = gi;
+        m.hb = hb;
+        m.chunk = c;
+        m.n_chunks = n_chunks;
+        m.k0 = (int64_t)c * chunk;
+        m.k1 = std::min(nk, m.k0 + chunk);
+        m.partial_off = poff;
+        m.counter = counter;
+        m.pad = 0;
+        p->mitems.push_back(m);
+      }
+      poff += (int64_t)n_chunks * 32;
+      ++counter;
+    }
+  }
+  p->n_mpartials = poff;
+  p->n_mcounters = counter;
+}
+
+double plan_k_evals(const ffe_plan* p) {
+  double s = 0.0;
+  for (const GroupDesc& g : p->groups) s += (double)g.N * (double)g.N * (double)g.n_out;
+  return s;
+}
+
+// Allocate device buffers for the host tables already in *p.
+ffe_status plan_alloc(ffe_context* ctx, ffe_plan* p) {
+  ffe_status st;
+#define ALLOC(ptr, n)                               \
+  if ((st = dev_alloc(ctx, p, &p->ptr, (n))) != FFE_OK) return st;
+  int64_t tab_rows = 0, hcount = 0;
+  for (const GroupDesc& g : p->groups) {
+    tab_rows = std::max<int64_t>(tab_rows, g.tab_off + 2 * (int64_t)g.N);
+    hcount = std::max<int64_t>(hcount, g.h_off + g.n_h);
+  }
+  p->tab_rows = tab_rows;
+  ALLOC(d_groups, p->groups.size());
+  ALLOC(d_items, p->items.size());
+  ALLOC(d_segs, p->segs.size());
+  ALLOC(d_mitems, p->mitems.size());
+  ALLOC(d_lines, p->lines.size());
+  ALLOC(d_delta, p->delta.size());
+  ALLOC(d_d2f, p->delta.size());
+  ALLOC(d_ht, p->ht.size());
+  ALLOC(d_htf, p->ht.size());
+  ALLOC(d_htd, p->ht.size());
+  ALLOC(d_hlist, p->hlist.size());
+  ALLOC(d_qzero, p->q_is_zero.size());
+  ALLOC(d_tabf, tab_rows);
+  ALLOC(d_c0f, tab_rows);
+  ALLOC(d_tabd, tab_rows);
+  ALLOC(d_c0d, tab_rows);
+  ALLOC(d_M, hcount);
+  ALLOC(d_Mpart, p->n_mpartials);
+  ALLOC(d_Mcnt, p->n_mcounters);
+  ALLOC(d_partials, p->n_partials);
+  ALLOC(d_segcnt, p->segs.size());
+  ALLOC(d_counters, 8);
+  ALLOC(d_V, p->n_out);
+  ALLOC(d_omega, p->n_out);
+  ALLOC(d_eb, p->n_out);
+  ALLOC(d_rescored, p->n_out);
+  p->cap = (int32_t)std::min<int64_t>(p->n_out + 2 * (int64_t)p->lines.size() + 64, 1 << 16);
+  ALLOC(d_req, p->cap);
+  int max_n = 2;
+  for (const GroupDesc& g : p->groups) max_n = std::max(max_n, g.N);
+  p->max_n = max_n;
+  // at most 64 chunks per FP64 request: bounded partial storage for any N
+  const int64_t nk_max = (int64_t)max_n * max_n;
+  p->rescore_chunk = (int)std::max<int64_t>(16384, (nk_max + 63) / 64);
+  p->rescore_chunks = (int)((nk_max + p->rescore_chunk - 1) / p->rescore_chunk);
+  ALLOC(d_rpart, (int64_t)p->cap * p->rescore_chunks);
+  ALLOC(d_rcnt, p->cap);
+  ALLOC(d_lres, p->lines.size());
+  ALLOC(d_labels, std::max<size_t>(1, p->n_pts));
+  ALLOC(d_bestq, std::max<size_t>(1, p->n_pts));
+#undef ALLOC
+  cudaStream_t s = p->stream;
+  FFE_CU(cudaMemsetAsync(p->d_Mcnt, 0, sizeof(int32_t) * std::max(1, p->n_mcounters), s), "memset");
+  FFE_CU(cudaMemsetAsync(p->d_segcnt, 0, sizeof(int32_t) * std::max<size_t>(1, p->segs.size()), s), "memset");
+  FFE_CU(cudaMemsetAsync(p->d_rcnt, 0, sizeof(int32_t) * p->cap, s), "memset");
+  if ((st = upload(ctx, p->d_groups, p->groups, s)) != FFE_OK) return st;
+  if ((st = upload(ctx, p->d_items, p->items, s)) != FFE_OK) return st;
+  if ((st = upload(ctx, p->d_segs, p->segs, s)) != FFE_OK) return st;
+  if ((st = upload(ctx, p->d_mitems, p->mitems, s)) != FFE_OK) return st;
+  if ((st = upload(ctx, p->d_lines, p->lines, s)) != FFE_OK) return st;
+  return plan_upload_params(ctx, p, s);
+}
+
+// The per-call inputs: Delta values, (h, T) entries, distinct h lists and Q.
+ffe_status plan_upload_params(ffe_context* ctx, ffe_plan* p, cudaStream_t s) {
+  ffe_status st;
+  if ((st = upload(ctx, p->d_delta, p->delta, s)) != FFE_OK) return st;
+  if ((st = upload(ctx, p->d_ht, p->ht, s)) != FFE_OK) return st;
+  if ((st = upload(ctx, p->d_hlist, p->hlist, s)) != FFE_OK) return st;
+  if ((st = upload(ctx, p->d_groups, p->groups, s)) != FFE_OK) return st;
+  if ((st = upload(ctx, p->d_qzero, p->q_is_zero, s)) != FFE_OK) return st;
+  p->h2d_bytes = p->delta.size() * sizeof(double) + p->ht.size() * sizeof(HT) +
+                 p->hlist.size() * sizeof(double) + p->groups.size() * sizeof(GroupDesc);
+  return FFE_OK;
+}
+
+static KsumArgs make_ksum_args(ffe_plan* p) {
+  KsumArgs a;
+  a.m = p->ctx->mp;
+  a.groups = p->d_groups;
+  a.items = p->d_items;
+  a.n_items = (int32_t)p->items.size();
+  a.pad0 = 0;
+  a.segs = p->d_segs;
+  a.queue = p->d_counters + 0;
+  a.seg_count = p->d_segcnt;
+  a.partials = p->d_partials;
+  a.tabf = p->d_tabf;
+  a.c0f = p->d_c0f;
+  a.tabd = p->d_tabd;
+  a.c0d = p->d_c0d;
+  a.delta = p->d_delta;
+  a.d2f = p->d_d2f;
+  a.ht = p->d_ht;
+  a.htf = p->d_htf;
+  a.htd = p->d_htd;
+  a.M = p->d_M;
+  a.V = p->d_V;
+  a.omega = p->d_omega;
+  a.ebound = p->d_eb;
+  a.eb_rel = p->prec == FFE_FP32C ? kEbRel : 0.0;
+  a.eb_abs = p->prec == FFE_FP32C ? kEbAbs : 0.0;
+  a.status = p->d_counters + 7;
+  return a;
+}
+
+static RescoreArgs make_rescore_args(ffe_plan* p, int queue_slot, int count_slot) {
+  RescoreArgs r;
+  r.m = p->ctx->mp;
+  r.groups = p->d_groups;
+  r.tabd = p->d_tabd;
+  r.c0d = p->d_c0d;
+  r.ht = p->d_ht;
+  r.M = p->d_M;
+  r.req = p->d_req;
+  r.n_req = p->d_counters + count_slot;
+  r.chunk_k = p->rescore_chunk;
+  r.max_chunks = p->rescore_chunks;
+  r.queue = p->d_counters + queue_slot;
+  r.counters = p->d_rcnt;
+  r.partials = p->d_rpart;
+  r.omega = p->d_omega;
+  r.ebound = p->d_eb;
+  r.lines = p->d_lres;
+  r.rescored = p->d_rescored;
+  r.cap = p->cap;
+  r.pad = 0;
+  return r;
+}
+
+// The whole device-side sequence of one execution, on stream s.
+// counters: [0] k-sum queue, [1] rescore queue A, [2] rescore queue B,
+//           [3] requests of the Delta search, [4] requests of the labels,
+//           [7] status word.
+ffe_status plan_enqueue(ffe_context* ctx, ffe_plan* p, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
+                        unsigned ev_flags) {
+  int launches = 0;
+  FFE_CU(cudaMemsetAsync(p->d_counters, 0, 8 * sizeof(int32_t), s), "memset counters");
+  FFE_CU(cudaMemsetAsync(p->d_rescored, 0, sizeof(int32_t) * std::max<int64_t>(1, p->n_out), s), "memset");
+  FFE_CU(prep_params_launch(p->d_delta, (int64_t)p->delta.size(), p->d_d2f, p->d_ht, (int64_t)p->ht.size(),
+                            p->d_htf, p->d_htd, s),
+         "prep_params");
+  ++launches;
+  FFE_CU(tables_launch(ctx->mp, p->d_groups, (int)p->groups.size(), p->max_n, p->d_tabf, p->d_c0f, p->d_tabd,
+                       p->d_c0d, s),
+         "tables");
+  ++launches;
+  FFE_CU(normal_launch(ctx->mp, p->d_groups, p->d_mitems, (int)p->mitems.size(), p->d_hlist, p->d_tabd,
+                       p->d_Mpart, p->d_Mcnt, p->d_M, s, true),
+         "normal");
+  ++launches;
+  if (ev0) FFE_CU(cudaEventRecordWithFlags(ev0, s, ev_flags), "event");
+  KsumArgs ka = make_ksum_args(p);
+  FFE_CU(ksum_launch(p->prec, p->layout, p->kpt, ka, p->grid, p->block, s), "ksum");
+  ++launches;
+  if (ev1) FFE_CU(cudaEventRecordWithFlags(ev1, s, ev_flags), "event");
+  if (!p->lines.empty()) {
+    const int n_lines = (int)p->lines.size();
+    FFE_CU(argmin_launch(p->d_lines, n_lines, p->d_omega, p->d_eb, p->d_delta, p->d_rescored, 0, p->d_req,
+                         p->d_counters + 3, p->cap, p->d_lres, s),
+           "argmin A");
+    FFE_CU(rescore_launch(make_rescore_args(p, 1, 3), p->rescore_grid, s), "rescore A");
+    FFE_CU(argmin_launch(p->d_lines, n_lines, p->d_omega, p->d_eb, p->d_delta, p->d_rescored, 1, p->d_req,
+                         p->d_counters + 3, p->cap, p->d_lres, s),
+           "argmin B");
+    launches += 3;
+    if (p->n_q > 0) {
+      // the request slots are reused once pass A's requests are done (stream order)
+      FFE_CU(labels_launch(p->d_lres, p->n_q, p->n_pts, p->d_qzero, p->d_lines, p->d_delta, 0, p->d_req,
+                           p->d_counters + 4, p->cap, p->d_labels, p->d_bestq, s),
+             "labels 0");
+      FFE_CU(rescore_launch(make_rescore_args(p, 2, 4), p->rescore_grid, s), "rescore B");
+      FFE_CU(labels_launch(p->d_lres, p->n_q, p->n_pts, p->d_qzero, p->d_lines, p->d_delta, 1, p->d_req,
+                           p->d_counters + 4, p->cap, p->d_labels, p->d_bestq, s),
+             "labels 1");
+      launches += 3;
+    }
+  }
+  p->launches = launches;
+  return FFE_OK;
+}
+
+ffe_status plan_configure(ffe_context* ctx, ffe_plan* p) {
+  // launch shape: persistent grid of resident blocks
+  const Tuning t = tuning_for(ctx, p);
+  p->kpt = t.kpt;
+  p->block = t.block;
+  p->item_target = t.item_target;
+  int bps = 0;
+  cudaError_t e = ksum_occupancy(p->prec, p->layout, p->kpt, p->block, &bps);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy");
+  if (bps < 1) bps = 1;
+  p->grid = ctx->n_sm * bps;
+  p->rescore_grid = ctx->n_sm * 4;
+  build_items(p);
+  build_mitems(p);
+  p->k_evals = plan_k_evals(p);
+  return FFE_OK;
+}
+
+ffe_status plan_finish(ffe_context* ctx, ffe_plan* p, bool use_graph) {
+  ffe_status st = plan_alloc(ctx, p);
+  if (st != FFE_OK) return st;
+  FFE_CU(cudaStreamSynchronize(p->stream), "sync");
+  if (!use_graph) return FFE_OK;
+  cudaGraph_t graph = nullptr;
+  FFE_CU(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+  st = plan_enqueue(ctx, p, p->stream, p->ev_cap0, p->ev_cap1, cudaEventRecordExternal);
+  cudaError_t e = cudaStreamEndCapture(p->stream, &graph);
+  if (st != FFE_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+  p->graph = graph;
+  e = cudaGraphInstantiate(&p->exec, graph, 0);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+  // locate the two event-record nodes around the k-sum
+  size_t n = 0;
+  FFE_CU(cudaGraphGetNodes(graph, nullptr, &n), "graph nodes");
+  std::vector<cudaGraphNode_t> nodes(n);
+  FFE_CU(cudaGraphGetNodes(graph, nodes.data(), &n), "graph nodes");
+  for (cudaGraphNode_t node : nodes) {
+    cudaGraphNodeType ty;
+    FFE_CU(cudaGraphNodeGetType(node, &ty), "node type");
+    if (ty != cudaGraphNodeTypeEventRecord) continue;
+    cudaEvent_t ev;
+    FFE_CU(cudaGraphEventRecordNodeGetEvent(node, &ev), "node event");
+    if (ev == p->ev_cap0) p->node_ev0 = node;
+    if (ev == p->ev_cap1) p->node_ev1 = node;
+  }
+  if (!p->node_ev0 || !p->node_ev1) {
+    set_err(ctx, "event nodes not found in the captured graph");
+    return FFE_EINTERNAL;
+  }
+  return FFE_OK;
+}
+
+ffe_status plan_run(ffe_context* ctx, ffe_plan* p, cudaStream_t s) {
+  if (p->exec) {
+    const int slot = (int)(p->exec_count % kRing);
+    FFE_CU(cudaGraphExecEventRecordNodeSetEvent(p->exec, p->node_ev0, p->ring0[slot]), "set event");
+    FFE_CU(cudaGraphExecEventRecordNodeSetEvent(p->exec, p->node_ev1, p->ring1[slot]), "set event");
+    FFE_CU(cudaGraphLaunch(p->exec, s), "graph launch");
+    ++p->exec_count;
+    return FFE_OK;
+  }
+  const int slot = (int)(p->exec_count % kRing);
+  ffe_status st = plan_enqueue(ctx, p, s, p->ring0[slot], p->ring1[slot], cudaEventRecordDefault);
+  if (st == FFE_OK) ++p->exec_count;
+  return st;
+}
+
+ffe_status plan_check_status(ffe_context* ctx, ffe_plan* p, cudaStream_t s) {
+  int32_t c[8];
+  FFE_CU(cudaMemcpyAsync(c, p->d_counters, sizeof c, cudaMemcpyDeviceToHost, s), "status");
+  FFE_CU(cudaStreamSynchronize(s), "sync");
+  if (c[7] != 0) {
+    set_err(ctx, "device status word %d", c[7]);
+    return FFE_EINTERNAL;
+  }
+  return FFE_OK;
+}
+
+ffe_plan* plan_new(ffe_context* ctx, int kind) {
+  ffe_plan* p = new ffe_plan();
+  p->ctx = ctx;
+  p->kind = kind;
+  p->prec = ctx->model.prec;
+  cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
+  cudaEventCreate(&p->ev_cap0);
+  cudaEventCreate(&p->ev_cap1);
+  for (int i = 0; i < kRing; ++i) {
+    cudaEventCreate(&p->ring0[i]);
+    cudaEventCreate(&p->ring1[i]);
+  }
+  return p;
+}
+
+void plan_free(ffe_plan* p) {
+  if (!p) return;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  for (void* a : p->allocs) cudaFree(a);
+  if (p->ev_cap0) cudaEventDestroy(p->ev_cap0);
+  if (p->ev_cap1) cudaEventDestroy(p->ev_cap1);
+  for (int i = 0; i < kRing; ++i) {
+    if (p->ring0[i]) cudaEventDestroy(p->ring0[i]);
+    if (p->ring1[i]) cudaEventDestroy(p->ring1[i]);
+  }
+  if (p->stream) cudaStreamDestroy(p->stream);
+  delete p;
+}
+
+}  // namespace ffe
+
+// ---------------------------------------------------------- plan builders
+namespace ffe {
+
+static ffe_status check_scan(ffe_context* ctx, const ffe_scan* sc) {
+  if (!sc) return set_err(ctx, "scan is NULL"), FFE_EINVAL;
+  if (!valid_N(sc->N)) return set_err(ctx, "N=%d must be even in [2, 8192]", sc->N), FFE_EINVAL;
+  if (sc->n_q < 1 || sc->n_h < 1 || sc->n_T < 1 || !sc->qx || !sc->qy || !sc->h || !sc->T)
+    return set_err(ctx, "scan lists must be non-empty"), FFE_EINVAL;
+  if (sc->search != FFE_SEARCH_GRID && sc->search != FFE_SEARCH_GOLDEN)
+    return set_err(ctx, "unknown search kind %d", sc->search), FFE_EINVAL;
+  if (sc->search == FFE_SEARCH_GRID && (sc->n < 1 || sc->n > 65536))
+    return set_err(ctx, "grid points n=%d out of [1, 65536]", sc->n), FFE_EINVAL;
+  if (!finite(sc->lo) || !finite(sc->hi) || sc->lo > sc->hi || sc->lo != 0.0)
+    return set_err(ctx, "Delta range must be finite with lo = 0 <= hi"), FFE_EINVAL;
+  bool has_zero = false;
+  for (int i = 0; i < sc->n_q; ++i) {
+    if (!finite(sc->qx[i]) || !finite(sc->qy[i])) return set_err(ctx, "q not finite"), FFE_EINVAL;
+    if (sc->qx[i] == 0.0 && sc->qy[i] == 0.0) has_zero = true;
+  }
+  if (!has_zero) return set_err(ctx, "the q list must contain Q = (0, 0)"), FFE_EINVAL;
+  for (int i = 0; i < sc->n_h; ++i)
+    if (!finite(sc->h[i])) return set_err(ctx, "h not finite"), FFE_EINVAL;
+  for (int i = 0; i < sc->n_T; ++i)
+    if (!(sc->T[i] > 0.0) || !finite(sc->T[i])) return set_err(ctx, "T must be > 0"), FFE_EINVAL;
+  const int64_t outs = (int64_t)sc->n_q * sc->n_h * sc->n_T * (int64_t)std::max(1, sc->n);
+  if (outs > ((int64_t)1 << 31)) return set_err(ctx, "scan too large"), FFE_EINVAL;
+  return FFE_OK;
+}
+
+// Grid scan: one PRODUCT group per q (outputs = Delta grid x (h,T) points).
+static void fill_scan_grid(ffe_plan* p, const ffe_scan* sc) {
+  const int n_pts = sc->n_h * sc->n_T;
+  p->layout = kLayoutProduct;
+  p->n_q = sc->n_q;
+  p->n_pts = n_pts;
+  p->groups.clear();
+  p->delta.clear();
+  p->ht.clear();
+  p->hlist.clear();
+  p->lines.clear();
+  p->q_is_zero.assign(sc->n_q, 0);
+  std::vector<double> grid(sc->n);
+  linspace(sc->lo, sc->hi, sc->n, grid.data());
+  int64_t out = 0;
+  for (int q = 0; q < sc->n_q; ++q) {
+    GroupDesc g;
+    std::memset(&g, 0, sizeof g);
+    g.N = sc->N;
+    g.layout = kLayoutProduct;
+    g.n_delta = sc->n;
+    g.n_ht = n_pts;
+    g.n_hblk = (n_pts + 31) / 32;
+    g.n_batches = g.n_delta * g.n_hblk;
+    g.n_h = sc->n_h;
+    g.n_out = sc->n * n_pts;
+    g.out_off = out;
+    g.delta_off = (int64_t)p->delta.size();
+    g.ht_off = (int64_t)p->ht.size();
+    g.tab_off = (int64_t)q * 2 * sc->N;
+    g.h_off = (int64_t)p->hlist.size();
+    g.qx = sc->qx[q];
+    g.qy = sc->qy[q];
+    p->q_is_zero[q] = (sc->qx[q] == 0.0 && sc->qy[q] == 0.0) ? 1 : 0;
+    p->delta.insert(p->delta.end(), grid.begin(), grid.end());
+    for (int ih = 0; ih < sc->n_h; ++ih)
+      for (int it = 0; it < sc->n_T; ++it) p->ht.push_back(HT{sc->h[ih], sc->T[it], ih, 0});
+    p->hlist.insert(p->hlist.end(), sc->h, sc->h + sc->n_h);
+    for (int pt = 0; pt < n_pts; ++pt) {
+      Line L;
+      L.out0 = out + pt;
+      L.stride = n_pts;
+      L.count = sc->n;
+      L.group = q;
+      L.pad = 0;
+      L.delta0 = g.delta_off;
+      L.ht = g.ht_off + pt;
+      p->lines.push_back(L);
+    }
+    out += g.n_out;
+    p->groups.push_back(g);
+  }
+  p->n_out = out;
+}
+
+static ffe_status fetch_scan(ffe_context* ctx, ffe_plan* p, ffe_result* per_point, int8_t* labels,
+                             int32_t* best_q, cudaStream_t s) {
+  ffe_status st = plan_check_status(ctx, p, s);
+  if (st != FFE_OK) return st;
+  std::vector<LineResult> lr(p->lines.size());
+  FFE_CU(cudaMemcpyAsync(lr.data(), p->d_lres, lr.size() * sizeof(LineResult), cudaMemcpyDeviceToHost, s),
+         "fetch lines");
+  if (labels)
+    FFE_CU(cudaMemcpyAsync(labels, p->d_labels, p->n_pts * sizeof(int8_t), cudaMemcpyDeviceToHost, s), "fetch");
+  if (best_q)
+    FFE_CU(cudaMemcpyAsync(best_q, p->d_bestq, p->n_pts * sizeof(int32_t), cudaMemcpyDeviceToHost, s), "fetch");
+  int32_t nreq[2] = {0, 0};
+  FFE_CU(cudaMemcpyAsync(nreq, p->d_counters + 3, sizeof nreq, cudaMemcpyDeviceToHost, s), "fetch");
+  FFE_CU(cudaStreamSynchronize(s), "sync");
+  p->last_rescored[0] = nreq[0];
+  p->last_rescored[1] = nreq[1];
+  if (nreq[0] > p->cap || nreq[1] > p->cap) {
+    set_err(ctx, "FP64 re-evaluation requests (%d, %d) exceeded capacity (%d)", nreq[0], nreq[1], p->cap);
+    return FFE_EINTERNAL;
+  }
+  if (per_point) {
+    for (size_t i = 0; i < lr.size(); ++i) {
+      ffe_result& r = per_point[i];
+      r.delta_star = lr[i].delta_star;
+      r.omega_star = lr[i].omega_star;
+      r.omega_lo = lr[i].omega_lo;
+      r.err_bound = lr[i].eb_star;
+      r.idx_star = lr[i].idx_star;
+      r.flags = lr[i].flags;
+    }
+  }
+  p->d2h_bytes = lr.size() * sizeof(LineResult) + (labels ? p->n_pts : 0) + (best_q ? 4 * p->n_pts : 0);
+  return FFE_OK;
+}
+
+}  // namespace ffe
+
+// ------------------------------------------------------------------- C ABI
+extern "C" {
+
+const char* ffe_status_string(ffe_status s) {
+  switch (s) {
+    case FFE_OK: return "ok";
+    case FFE_EINVAL: return "invalid argument";
+    case FFE_ENOMEM: return "out of memory";
+    case FFE_ECUDA: return "CUDA error";
+    case FFE_ETIMEOUT: return "device wait timed out";
+    case FFE_EUNSUPPORTED: return "unsupported";
+    case FFE_EINTERNAL: return "internal error";
+  }
+  return "unknown status";
+}
+
+const char* ffe_last_error(const ffe_context* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+ffe_status ffe_create(const ffe_model* m, ffe_context** out) {
+  if (!out) return FFE_EINVAL;
+  *out = nullptr;
+  if (!m) return FFE_EINVAL;
+  if (m->kind != FFE_MODEL_RAGHU2) return FFE_EUNSUPPORTED;
+  if (m->prec != FFE_FP64 && m->prec != FFE_FP32C) return FFE_EINVAL;
+  if (!(m->U > 0.0) || !std::isfinite(m->U) || !std::isfinite(m->t1) || !std::isfinite(m->t2) ||
+      !std::isfinite(m->t3) || !std::isfinite(m->t4) || !std::isfinite(m->mu) || !std::isfinite(m->eta_amp))
+    return FFE_EINVAL;
+  ffe_context* ctx = new (std::nothrow) ffe_context();
+  if (!ctx) return FFE_ENOMEM;
+  ctx->model = *m;
+  ctx->mp = ModelParams{m->t1, m->t2, m->t3, m->t4, m->mu, m->U, m->eta_amp};
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e == cudaSuccess) {
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, ctx->device);
+    if (e == cudaSuccess) ctx->device_name = prop.name;
+  }
+  if (e != cudaSuccess) {
+    delete ctx;
+    return FFE_ECUDA;
+  }
+  tuning_load(ctx);
+  *out = ctx;
+  return FFE_OK;
+}
+
+void ffe_destroy(ffe_context* ctx) {
+  if (!ctx) return;
+  for (ffe_plan* p : ctx->plans) plan_free(p);
+  for (auto& kv : ctx->cache) plan_free(kv.second);
+  delete ctx;
+}
+
+ffe_status ffe_plan_phase_scan(ffe_context* ctx, const ffe_scan* scan, void* stream, ffe_plan** out) {
+  if (!ctx || !out) return FFE_EINVAL;
+  *out = nullptr;
+  ffe_status st = check_scan(ctx, scan);
+  if (st != FFE_OK) return st;
+  if (scan->search != FFE_SEARCH_GRID) return set_err(ctx, "golden plans: see ffe_phase_scan"), FFE_EUNSUPPORTED;
+  ffe_plan* p = plan_new(ctx, kPlanScanGrid);
+  fill_scan_grid(p, scan);
+  st = plan_configure(ctx, p);
+  if (st == FFE_OK) st = plan_finish(ctx, p, true);
+  if (st != FFE_OK) {
+    plan_free(p);
+    return st;
+  }
+  (void)stream;
+  ctx->plans.push_back(p);
+  *out = p;
+  return FFE_OK;
+}
+
+ffe_status ffe_plan_execute(ffe_plan* p, void* stream) {
+  if (!p) return FFE_EINVAL;
+  return plan_run(p->ctx, p, (cudaStream_t)stream);
+}
+
+ffe_status ffe_plan_fetch(ffe_plan* p, ffe_result* per_point, int8_t* labels, int32_t* best_q, void* stream) {
+  if (!p) return FFE_EINVAL;
+  return fetch_scan(p->ctx, p, per_point, labels, best_q, (cudaStream_t)stream);
+}
+
+ffe_status ffe_plan_stats(const ffe_plan* p, ffe_plan_info* info) {
+  if (!p || !info) return FFE_EINVAL;
+  std::memset(info, 0, sizeof *info);
+  info->k_evals = p->k_evals;
+  info->launches = p->launches;
+  info->rescored_search = p->last_rescored[0];
+  info->rescored_labels = p->last_rescored[1];
+  info->kpt = p->kpt;
+  info->block = p->block;
+  info->grid = p->grid;
+  info->work_items = (int32_t)p->items.size();
+  info->device_bytes = (double)p->bytes;
+  return FFE_OK;
+}
+
+ffe_status ffe_plan_kernel_ms(ffe_plan* p, double* ms, int32_t* count) {
+  if (!p) return FFE_EINVAL;
+  ffe_context* ctx = p->ctx;
+  const int64_t n = std::min<int64_t>(p->exec_count - p->timed_upto, kRing);
+  double tot = 0.0;
+  for (int64_t i = p->exec_count - n; i < p->exec_count; ++i) {
+    const int slot = (int)(i % kRing);
+    FFE_CU(cudaEventSynchronize(p->ring1[slot]), "event sync");
+    float f = 0.f;
+    FFE_CU(cudaEventElapsedTime(&f, p->ring0[slot], p->ring1[slot]), "elapsed");
+    tot += f;
+  }
+  p->timed_upto = p->exec_count;
+  if (ms) *ms = n > 0 ? tot / (double)n : 0.0;
+  if (count) *count = (int32_t)n;
+  return FFE_OK;
+}
+
+void ffe_plan_destroy(ffe_plan* p) {
+  if (!p) return;
+  ffe_context* ctx = p->ctx;
+  auto it = std::find(ctx->plans.begin(), ctx->plans.end(), p);
+  if (it != ctx->plans.end()) ctx->plans.erase(it);
+  plan_free(p);
+}
+
+ffe_status ffe_phase_scan(ffe_context* ctx, const ffe_scan* scan, ffe_result* per_point, int8_t* labels,
+                          int32_t* best_q, void* stream) {
+  if (!ctx) return FFE_EINVAL;
+  ffe_status st = check_scan(ctx, scan);
+  if (st != FFE_OK) return st;
+  if (scan->search == FFE_SEARCH_GOLDEN) return golden_scan(ctx, scan, per_point, labels, best_q, stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  char key[160];
+  snprintf(key, sizeof key, "scan:%d:%d:%d:%d:%d:%d", ctx->model.prec, scan->N, scan->n_q, scan->n_h, scan->n_T,
+           scan->n);
+  ffe_plan* p = nullptr;
+  auto it = ctx->cache.find(key);
+  if (it != ctx->cache.end()) {
+    p = it->second;
+    fill_scan_grid(p, scan);
+    if ((st = plan_upload_params(ctx, p, s)) != FFE_OK) return st;
+  } else {
+    p = plan_new(ctx, kPlanScanGrid);
+    fill_scan_grid(p, scan);
+    st = plan_configure(ctx, p);
+    if (st == FFE_OK) st = plan_finish(ctx, p, true);
+    if (st != FFE_OK) {
+      plan_free(p);
+      return st;
+    }
+    ctx->cache[key] = p;
+  }
+  if ((st = plan_run(ctx, p, s)) != FFE_OK) return st;
+  return fetch_scan(ctx, p, per_point, labels, best_q, s);
+}
+
+}  // extern "C"

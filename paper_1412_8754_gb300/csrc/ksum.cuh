@@ -1,0 +1,123 @@
+// ksum.cuh -- launch interface of the kernels (host side, internal).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ffe_internal.cuh"
+
+namespace ffe {
+
+struct KsumArgs {
+  ModelParams m;
+  const GroupDesc* groups;
+  const WorkItem* items;
+  int32_t n_items;
+  int32_t pad0;
+  const Segment* segs;
+  int32_t* queue;      // work counter, zeroed before each launch
+  int32_t* seg_count;  // per-segment completion counters (self-resetting)
+  double* partials;
+  const TabRowF* tabf;
+  const float* c0f;
+  const TabRowD* tabd;
+  const double* c0d;
+  const double* delta;  // Delta values (authoritative, FP64)
+  const float* d2f;     // Delta^2 in FP32
+  const HT* ht;
+  const HTf* htf;
+  const HTd* htd;
+  const double* M;      // normal-state sums per (group, h)
+  double* V;            // per-output sum_k v_k
+  double* omega;        // per-output Omega
+  double* ebound;       // per-output FP32 error bound (0 for FP64)
+  double eb_rel, eb_abs;
+  int32_t* status;
+};
+
+size_t ksum_smem_bytes(int prec, int block_threads);
+cudaError_t ksum_launch(int prec, int layout, int kpt, const KsumArgs& a, int grid, int block,
+                        cudaStream_t s);
+cudaError_t ksum_occupancy(int prec, int layout, int kpt, int block, int* blocks_per_sm);
+bool ksum_kpt_supported(int prec, int kpt);
+
+// ---- tables and the normal-state sum (tables.cu)
+// Work item of the M kernel: k range [k0, k1) of one group, h block hb (32 h).
+struct MItem {
+  int32_t group;
+  int32_t hb;
+  int32_t chunk;
+  int32_t n_chunks;
+  int64_t k0, k1;
+  int64_t partial_off;  // partials[partial_off + chunk*32 + j]
+  int32_t counter;      // index of the (group, hb) completion counter
+  int32_t pad;
+};
+
+cudaError_t tables_launch(const ModelParams& m, const GroupDesc* groups, int n_groups, int max_n,
+                          TabRowF* tabf, float* c0f, TabRowD* tabd, double* c0d, cudaStream_t s);
+cudaError_t prep_params_launch(const double* delta, int64_t n_delta, float* d2f, const HT* ht,
+                               int64_t n_ht, HTf* htf, HTd* htd, cudaStream_t s);
+cudaError_t normal_launch(const ModelParams& m, const GroupDesc* groups, const MItem* items,
+                          int n_items, const double* hlist, const TabRowD* tabd, double* partials,
+                          int32_t* counters, double* M, cudaStream_t s, bool f64_terms);
+
+// ---- search, rescoring and labels (search.cu)
+struct Line {          // one Delta search: outputs out0 + i*stride, i < count
+  int64_t out0;
+  int32_t stride;
+  int32_t count;
+  int32_t group;
+  int32_t pad;
+  int64_t delta0;      // Delta entry of i = 0 (entries delta0 + i)
+  int64_t ht;          // (h,T) entry
+};
+
+struct LineResult {
+  double delta_star, omega_star, eb_star;
+  double omega_lo, eb_lo;
+  int64_t out_star;
+  int32_t idx_star;
+  int32_t flags;
+};
+
+struct Rescore {       // FP64 re-evaluation request
+  int32_t group;
+  int32_t kind;        // 0: omega/ebound[dst]; 1: line best; 2: line lo
+  int64_t dst;
+  int64_t ht;
+  double delta;
+};
+
+struct RescoreArgs {
+  ModelParams m;
+  const GroupDesc* groups;
+  const TabRowD* tabd;
+  const double* c0d;
+  const HT* ht;
+  const double* M;
+  const Rescore* req;
+  const int32_t* n_req;
+  int32_t chunk_k;      // k-points per chunk
+  int32_t max_chunks;   // chunks per request (covers the largest N^2)
+  int32_t* queue;
+  int32_t* counters;    // per request (self-resetting)
+  double* partials;     // [cap][max_chunks]
+  double* omega;
+  double* ebound;
+  LineResult* lines;
+  int32_t* rescored;    // per output flag (kind 0)
+  int32_t cap;
+  int32_t pad;
+};
+
+cudaError_t argmin_launch(const Line* lines, int n_lines, const double* omega, const double* ebound,
+                          const double* delta, const int32_t* rescored, int mode, Rescore* req,
+                          int32_t* n_req, int32_t cap, LineResult* res, cudaStream_t s);
+cudaError_t rescore_launch(const RescoreArgs& a, int grid, cudaStream_t s);
+cudaError_t labels_launch(LineResult* res, int n_q, int n_pts, const int32_t* q_is_zero,
+                          const Line* lines, const double* delta, int mode, Rescore* req,
+                          int32_t* n_req, int32_t cap, int8_t* labels, int32_t* best_q,
+                          cudaStream_t s);
+
+}  // namespace ffe

@@ -1,0 +1,240 @@
+// points.cu -- ffe_omega (independent points) and ffe_minimize (independent
+// Delta searches, uneven lattices and grid lengths in one persistent launch).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "plan.h"
+
+using namespace ffe;
+
+namespace {
+
+bool valid_N(int32_t N) { return N >= 2 && N <= 8192 && (N % 2) == 0; }
+
+// Points sharing (N, Q) form one LIST group; outputs keep input order inside.
+void fill_points(ffe_plan* p, const ffe_point* pts, int64_t n) {
+  p->layout = kLayoutList;
+  std::map<std::tuple<int32_t, double, double>, std::vector<int64_t>> by_key;
+  std::vector<std::tuple<int32_t, double, double>> keys;
+  for (int64_t i = 0; i < n; ++i) {
+    auto k = std::make_tuple(pts[i].N, pts[i].qx, pts[i].qy);
+    auto it = by_key.find(k);
+    if (it == by_key.end()) {
+      keys.push_back(k);
+      by_key[k].push_back(i);
+    } else {
+      it->second.push_back(i);
+    }
+  }
+  int64_t out = 0, tab = 0;
+  for (const auto& k : keys) {
+    const std::vector<int64_t>& idx = by_key[k];
+    GroupDesc g;
+    std::memset(&g, 0, sizeof g);
+    g.N = std::get<0>(k);
+    g.layout = kLayoutList;
+    g.n_out = (int32_t)idx.size();
+    g.n_delta = g.n_out;
+    g.n_ht = g.n_out;
+    g.n_hblk = 1;
+    g.n_batches = (g.n_out + 31) / 32;
+    g.out_off = out;
+    g.delta_off = (int64_t)p->delta.size();
+    g.ht_off = (int64_t)p->ht.size();
+    g.tab_off = tab;
+    g.h_off = (int64_t)p->hlist.size();
+    g.qx = std::get<1>(k);
+    g.qy = std::get<2>(k);
+    std::map<double, int> hmap;
+    for (int64_t i : idx) {
+      const double h = pts[i].h;
+      auto it = hmap.find(h);
+      int hi;
+      if (it == hmap.end()) {
+        hi = (int)hmap.size();
+        hmap[h] = hi;
+        p->hlist.push_back(h);
+      } else {
+        hi = it->second;
+      }
+      p->delta.push_back(pts[i].delta);
+      p->ht.push_back(HT{h, pts[i].T, hi, 0});
+      p->order.push_back(i);
+    }
+    g.n_h = (int32_t)hmap.size();
+    p->groups.push_back(g);
+    out += g.n_out;
+    tab += 2 * (int64_t)g.N;
+  }
+  p->n_out = out;
+}
+
+// One LIST group per parameter point: outputs = its Delta grid.
+void fill_min_grid(ffe_plan* p, const ffe_param* ps, int64_t n) {
+  p->layout = kLayoutList;
+  int64_t out = 0, tab = 0;
+  std::vector<double> grid;
+  for (int64_t i = 0; i < n; ++i) {
+    const ffe_param& q = ps[i];
+    GroupDesc g;
+    std::memset(&g, 0, sizeof g);
+    g.N = q.N;
+    g.layout = kLayoutList;
+    g.n_out = q.n;
+    g.n_delta = q.n;
+    g.n_ht = q.n;
+    g.n_hblk = 1;
+    g.n_batches = (q.n + 31) / 32;
+    g.n_h = 1;
+    g.out_off = out;
+    g.delta_off = (int64_t)p->delta.size();
+    g.ht_off = (int64_t)p->ht.size();
+    g.tab_off = tab;
+    g.h_off = (int64_t)p->hlist.size();
+    g.qx = q.qx;
+    g.qy = q.qy;
+    grid.resize(q.n);
+    linspace(q.lo, q.hi, q.n, grid.data());
+    p->delta.insert(p->delta.end(), grid.begin(), grid.end());
+    for (int j = 0; j < q.n; ++j) p->ht.push_back(HT{q.h, q.T, 0, 0});
+    p->hlist.push_back(q.h);
+    Line L;
+    L.out0 = out;
+    L.stride = 1;
+    L.count = q.n;
+    L.group = (int32_t)i;
+    L.pad = 0;
+    L.delta0 = g.delta_off;
+    L.ht = g.ht_off;
+    p->lines.push_back(L);
+    p->groups.push_back(g);
+    out += q.n;
+    tab += 2 * (int64_t)q.N;
+  }
+  p->n_out = out;
+}
+
+}  // namespace
+
+namespace ffe {
+
+Tuning tuning_for(ffe_context* ctx, const ffe_plan* p) {
+  char key[128];
+  snprintf(key, sizeof key, "%s:%d:%d", ctx->device_name.c_str(), p->prec, p->layout);
+  auto it = ctx->tuned.find(key);
+  if (it != ctx->tuned.end()) return it->second;
+  Tuning t;
+  t.kpt = p->prec == FFE_FP32C ? 4 : 1;
+  t.block = 256;
+  t.item_target = p->prec == FFE_FP32C ? 8388608.0 : 262144.0;
+  return t;
+}
+
+void tuning_load(ffe_context*) {}
+
+ffe_status golden_scan(ffe_context* ctx, const ffe_scan*, ffe_result*, int8_t*, int32_t*, void*) {
+  set_err(ctx, "golden-section scans are not built yet");
+  return FFE_EUNSUPPORTED;
+}
+
+}  // namespace ffe
+
+extern "C" {
+
+ffe_status ffe_omega(ffe_context* ctx, const ffe_point* pts, int64_t n, double* omega, double* omega_band,
+                     void* stream) {
+  if (!ctx) return FFE_EINVAL;
+  if (!pts || !omega || n < 1) return set_err(ctx, "ffe_omega: empty or NULL arguments"), FFE_EINVAL;
+  if (omega_band) return set_err(ctx, "per-band output is not built yet"), FFE_EUNSUPPORTED;
+  for (int64_t i = 0; i < n; ++i) {
+    const ffe_point& q = pts[i];
+    if (!valid_N(q.N)) return set_err(ctx, "point %lld: N=%d must be even in [2, 8192]", (long long)i, q.N), FFE_EINVAL;
+    if (q.reserved != 0) return set_err(ctx, "point %lld: reserved must be 0", (long long)i), FFE_EINVAL;
+    if (!(q.T > 0.0) || !std::isfinite(q.T) || !std::isfinite(q.qx) || !std::isfinite(q.qy) ||
+        !std::isfinite(q.h) || !std::isfinite(q.delta))
+      return set_err(ctx, "point %lld: non-finite value or T <= 0", (long long)i), FFE_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  ffe_plan* p = plan_new(ctx, kPlanOmega);
+  fill_points(p, pts, n);
+  ffe_status st = plan_configure(ctx, p);
+  if (st == FFE_OK) st = plan_finish(ctx, p, false);
+  if (st == FFE_OK) st = plan_run(ctx, p, s);
+  if (st == FFE_OK) st = plan_check_status(ctx, p, s);
+  if (st == FFE_OK) {
+    std::vector<double> om(p->n_out);
+    cudaError_t e = cudaMemcpyAsync(om.data(), p->d_omega, om.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      st = cuda_fail(ctx, e, "fetch omega");
+    } else {
+      for (int64_t o = 0; o < p->n_out; ++o) omega[p->order[o]] = om[o];
+    }
+  }
+  plan_free(p);
+  return st;
+}
+
+ffe_status ffe_minimize(ffe_context* ctx, int32_t search, const ffe_param* ps, int64_t n, ffe_result* out,
+                        double* omega_grid, double* err_grid, void* stream) {
+  if (!ctx) return FFE_EINVAL;
+  if (!ps || !out || n < 1) return set_err(ctx, "ffe_minimize: empty or NULL arguments"), FFE_EINVAL;
+  if (search != FFE_SEARCH_GRID && search != FFE_SEARCH_GOLDEN)
+    return set_err(ctx, "unknown search kind %d", search), FFE_EINVAL;
+  int64_t total = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const ffe_param& q = ps[i];
+    if (!valid_N(q.N)) return set_err(ctx, "param %lld: N=%d must be even in [2, 8192]", (long long)i, q.N), FFE_EINVAL;
+    if (!(q.T > 0.0) || !std::isfinite(q.T) || !std::isfinite(q.qx) || !std::isfinite(q.qy) ||
+        !std::isfinite(q.h) || !std::isfinite(q.lo) || !std::isfinite(q.hi) || q.lo > q.hi)
+      return set_err(ctx, "param %lld: non-finite value, T <= 0 or lo > hi", (long long)i), FFE_EINVAL;
+    if (search == FFE_SEARCH_GRID && (q.n < 1 || q.n > 65536))
+      return set_err(ctx, "param %lld: grid points n=%d out of [1, 65536]", (long long)i, q.n), FFE_EINVAL;
+    if (search == FFE_SEARCH_GOLDEN && (q.n < 1 || q.n > 200))
+      return set_err(ctx, "param %lld: golden reductions n=%d out of [1, 200]", (long long)i, q.n), FFE_EINVAL;
+    total += q.n;
+  }
+  if (total > ((int64_t)1 << 31)) return set_err(ctx, "too many outputs"), FFE_EINVAL;
+  if (search == FFE_SEARCH_GOLDEN) return set_err(ctx, "golden-section search is not built yet"), FFE_EUNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  ffe_plan* p = plan_new(ctx, kPlanMinGrid);
+  fill_min_grid(p, ps, n);
+  ffe_status st = plan_configure(ctx, p);
+  if (st == FFE_OK) st = plan_finish(ctx, p, false);
+  if (st == FFE_OK) st = plan_run(ctx, p, s);
+  if (st == FFE_OK) st = plan_check_status(ctx, p, s);
+  if (st == FFE_OK) {
+    std::vector<LineResult> lr(p->lines.size());
+    cudaError_t e = cudaMemcpyAsync(lr.data(), p->d_lres, lr.size() * sizeof(LineResult), cudaMemcpyDeviceToHost, s);
+    int32_t nreq = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nreq, p->d_counters + 3, sizeof nreq, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && omega_grid)
+      e = cudaMemcpyAsync(omega_grid, p->d_omega, p->n_out * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && err_grid)
+      e = cudaMemcpyAsync(err_grid, p->d_eb, p->n_out * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      st = cuda_fail(ctx, e, "fetch results");
+    } else if (nreq > p->cap) {
+      set_err(ctx, "FP64 re-evaluation requests (%d) exceeded capacity (%d)", nreq, p->cap);
+      st = FFE_EINTERNAL;
+    } else {
+      for (int64_t i = 0; i < n; ++i) {
+        out[i].delta_star = lr[i].delta_star;
+        out[i].omega_star = lr[i].omega_star;
+        out[i].omega_lo = lr[i].omega_lo;
+        out[i].err_bound = lr[i].eb_star;
+        out[i].idx_star = lr[i].idx_star;
+        out[i].flags = lr[i].flags;
+      }
+    }
+  }
+  plan_free(p);
+  return st;
+}
+
+}  // extern "C"

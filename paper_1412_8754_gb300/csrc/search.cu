@@ -1,0 +1,301 @@
+// search.cu -- Delta search, FP64 re-evaluation of near ties, phase labels.
+//
+// Alg. 1 keeps, per pair momentum q, the Delta of lowest Omega and then the q
+// of lowest Omega.  The paper does the Delta search on the host after copying
+// partial sums back (Sec. 3, step 3); here it stays on the device:
+//  * argmin_kernel, pass A: per line (one Delta grid of one (q, h, T)) the
+//    lowest Omega and every grid point whose FP32 error band overlaps the
+//    minimum's band; if there is more than one, those points are queued for
+//    FP64 re-evaluation ("run at lower precision, then selectively verify with
+//    double precision", Sec. 3, performance evaluation).
+//  * rescore_kernel: the k-sum of one (q, h, T, Delta) in FP64, split over
+//    k-chunks with a deterministic last-block-done reduction.
+//  * argmin_kernel, pass B: the final argmin (ties -> lowest index).
+//  * labels_kernel: per (h, T) the normal / BCS / FF label from the per-q
+//    minima, FP64 comparisons with a tie band tau = 1e-12 |Omega_N|; values
+//    whose FP32 error band could flip a comparison are re-evaluated in FP64
+//    (pass 0) before the final labels (pass 1).
+#include <cfloat>
+#include <climits>
+
+#include "ffe_internal.cuh"
+#include "ksum.cuh"
+
+namespace ffe {
+
+constexpr double kTauRel = 1e-12;
+
+__device__ __forceinline__ void warp_argmin(double& v, int& i) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const double ov = __shfl_xor_sync(kFull, v, s);
+    const int oi = __shfl_xor_sync(kFull, i, s);
+    if (ov < v || (ov == v && oi < i)) {
+      v = ov;
+      i = oi;
+    }
+  }
+}
+
+__device__ __forceinline__ void push_request(Rescore* req, int32_t* n_req, int32_t cap, const Rescore& r) {
+  const int pos = atomicAdd(n_req, 1);
+  if (pos < cap) req[pos] = r;
+}
+
+__global__ void argmin_kernel(const Line* __restrict__ lines, int n_lines, const double* __restrict__ omega,
+                              const double* __restrict__ eb, const double* __restrict__ delta,
+                              const int32_t* __restrict__ rescored, int mode, Rescore* req, int32_t* n_req,
+                              int32_t cap, LineResult* res) {
+  const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (gw >= n_lines) return;
+  const Line L = lines[gw];
+  double best = DBL_MAX;
+  int bi = INT_MAX;
+  for (int i = lane; i < L.count; i += 32) {
+    const double v = omega[L.out0 + (int64_t)i * L.stride];
+    if (v < best) {
+      best = v;
+      bi = i;
+    }
+  }
+  warp_argmin(best, bi);
+  if (bi == INT_MAX) bi = 0;  // all values NaN: keep the index in range
+  const int64_t out_b = L.out0 + (int64_t)bi * L.stride;
+  if (mode == 0) {
+    const double thr = best + eb[out_b];
+    int ncand = 0;
+    for (int i0 = 0; i0 < L.count; i0 += 32) {
+      const int i = i0 + lane;
+      bool c = false;
+      if (i < L.count) {
+        const int64_t o = L.out0 + (int64_t)i * L.stride;
+        c = (omega[o] - eb[o] <= thr);
+      }
+      ncand += __popc(__ballot_sync(kFull, c));
+    }
+    if (ncand > 1) {
+      for (int i = lane; i < L.count; i += 32) {
+        const int64_t o = L.out0 + (int64_t)i * L.stride;
+        if (omega[o] - eb[o] <= thr && eb[o] > 0.0) {
+          Rescore r;
+          r.group = L.group;
+          r.kind = 0;
+          r.dst = o;
+          r.ht = L.ht;
+          r.delta = delta[L.delta0 + i];
+          push_request(req, n_req, cap, r);
+        }
+      }
+    }
+  } else if (lane == 0) {
+    LineResult r;
+    r.idx_star = bi;
+    r.out_star = out_b;
+    r.delta_star = delta[L.delta0 + bi];
+    r.omega_star = best;
+    r.eb_star = eb[out_b];
+    r.omega_lo = omega[L.out0];
+    r.eb_lo = eb[L.out0];
+    int f = 0;
+    if (rescored[out_b]) f |= kFlagRescored;
+    if (bi == L.count - 1) f |= kFlagEdge;
+    if (bi == 0) f |= kFlagLower;
+    r.flags = f;
+    res[gw] = r;
+  }
+}
+
+cudaError_t argmin_launch(const Line* lines, int n_lines, const double* omega, const double* ebound,
+                          const double* delta, const int32_t* rescored, int mode, Rescore* req,
+                          int32_t* n_req, int32_t cap, LineResult* res, cudaStream_t s) {
+  if (n_lines <= 0) return cudaSuccess;
+  const int threads = 256;
+  const int grid = (int)(((int64_t)n_lines * 32 + threads - 1) / threads);
+  argmin_kernel<<<grid, threads, 0, s>>>(lines, n_lines, omega, ebound, delta, rescored, mode, req, n_req,
+                                         cap, res);
+  return cudaGetLastError();
+}
+
+// FP64 k-point term v_k (both bands) at one (Delta, h, T).
+__device__ __forceinline__ double v_term_f64(const KState<double>& st, double d2, double h, double inv_t,
+                                             double t) {
+  const double D = d2 * st.eta2;
+  double q[2], f[2];
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    double R, A;
+    ra_f64(D, st.s2[b], st.as[b], R, A);
+    band_term_f64(R, A, st.as[b], st.d0[b], h, inv_t, q[b], f[b]);
+  }
+  const double Q = q[0] + q[1] + q[0] * q[1];
+  return (f[0] + f[1]) - t * log1p(Q);
+}
+
+__global__ void __launch_bounds__(256) rescore_kernel(const RescoreArgs a) {
+  __shared__ double red[8];
+  __shared__ int sh_w, sh_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nreq = min(*a.n_req, a.cap);
+  const int total = nreq * a.max_chunks;
+  for (;;) {
+    if (threadIdx.x == 0) sh_w = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int w = sh_w;
+    __syncthreads();
+    if (w >= total) break;
+    const int r = w / a.max_chunks, c = w - r * a.max_chunks;
+    const Rescore q = a.req[r];
+    const GroupDesc g = a.groups[q.group];
+    const HT ht = a.ht[q.ht];
+    const int64_t nk = (int64_t)g.N * g.N;
+    const int64_t k0 = (int64_t)c * a.chunk_k;
+    const int64_t k1 = min(nk, k0 + a.chunk_k);
+    const double d2 = q.delta * q.delta, inv_t = 1.0 / ht.T;
+    double s = 0.0;
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+      const int iy = (int)(k / g.N);
+      const int ix = (int)(k - (int64_t)iy * g.N);
+      KState<double> st;
+      kstate_make<double, TabRowD>(a.m, a.tabd[g.tab_off + ix], a.tabd[g.tab_off + g.N + iy],
+                                   a.c0d[g.tab_off + ix], a.c0d[g.tab_off + g.N + iy], st);
+      s += v_term_f64(st, d2, ht.h, inv_t, ht.T);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b = 0.0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) b += red[i];
+      a.partials[(int64_t)r * a.max_chunks + c] = b;
+      __threadfence();
+      sh_last = (atomicAdd(a.counters + r, 1) == a.max_chunks - 1);
+    }
+    __syncthreads();
+    if (sh_last && threadIdx.x == 0) {
+      __threadfence();
+      double V = 0.0;
+      for (int i = 0; i < a.max_chunks; ++i) V += __ldcg(a.partials + (int64_t)r * a.max_chunks + i);
+      const double n2 = (double)g.N * (double)g.N;
+      const double om = a.M[g.h_off + ht.h_idx] + V + 2.0 * n2 * d2 / a.m.U;
+      if (q.kind == 0) {
+        a.omega[q.dst] = om;
+        a.ebound[q.dst] = 0.0;
+        a.rescored[q.dst] = 1;
+      } else {
+        // kinds 1 (minimum) and 2 (Delta = lo) name the same value when the
+        // minimum is the Delta = lo point: keep both copies identical
+        LineResult& L = a.lines[q.dst];
+        const bool same = (L.flags & kFlagLower) != 0;
+        if (q.kind == 1 || same) {
+          L.omega_star = om;
+          L.eb_star = 0.0;
+          L.flags |= kFlagRescored;
+        }
+        if (q.kind == 2 || same) {
+          L.omega_lo = om;
+          L.eb_lo = 0.0;
+        }
+      }
+      a.counters[r] = 0;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t rescore_launch(const RescoreArgs& a, int grid, cudaStream_t s) {
+  rescore_kernel<<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// One thread per (h, T) point; lines are q-major: line = q * n_pts + p.
+__global__ void labels_kernel(LineResult* res, int n_q, int n_pts, const int32_t* __restrict__ q_is_zero,
+                              const Line* __restrict__ lines, const double* __restrict__ delta, int mode,
+                              Rescore* req, int32_t* n_req, int32_t cap, int8_t* labels, int32_t* best_q) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_pts) return;
+  int q0 = -1;
+  for (int q = 0; q < n_q; ++q)
+    if (q_is_zero[q]) {
+      q0 = q;
+      break;
+    }
+  if (q0 < 0) {
+    labels[p] = -1;
+    best_q[p] = -1;
+    return;
+  }
+  const LineResult rN = res[(int64_t)q0 * n_pts + p];
+  const double omega_n = rN.omega_lo;
+  const double tau = kTauRel * fabs(omega_n);
+  int best = -1;
+  double wbest = 0.0;
+  for (int q = 0; q < n_q; ++q) {
+    const LineResult r = res[(int64_t)q * n_pts + p];
+    if (r.omega_star < r.omega_lo - tau && (best < 0 || r.omega_star < wbest)) {
+      best = q;
+      wbest = r.omega_star;
+    }
+  }
+  if (mode == 0) {
+    const double eb_best = best >= 0 ? res[(int64_t)best * n_pts + p].eb_star : 0.0;
+    // A line whose minimum is the Delta = lo point compares one value with
+    // itself: never a candidate, whatever its error band.
+    auto maybe_candidate = [&](const LineResult& r) {
+      return !(r.flags & kFlagLower) && r.omega_star < r.omega_lo - tau + r.eb_star + r.eb_lo;
+    };
+    // a q that may be a candidate and whose minimum is within error of the best one
+    auto contests = [&](const LineResult& r, int q) {
+      return best >= 0 && q != best && maybe_candidate(r) && fabs(r.omega_star - wbest) <= r.eb_star + eb_best;
+    };
+    const bool vs_normal = best >= 0 && fabs(omega_n - tau - wbest) <= eb_best + rN.eb_lo;
+    bool best_contested = false;
+    for (int q = 0; q < n_q && best >= 0; ++q)
+      if (contests(res[(int64_t)q * n_pts + p], q)) best_contested = true;
+    for (int q = 0; q < n_q; ++q) {
+      const int64_t l = (int64_t)q * n_pts + p;
+      const LineResult r = res[l];
+      // candidate test Omega* < Omega(lo) - tau within error
+      bool need_star = !(r.flags & kFlagLower) && fabs(r.omega_lo - tau - r.omega_star) <= r.eb_star + r.eb_lo;
+      bool need_lo = need_star;
+      if (contests(r, q)) need_star = true;
+      if (q == best && (best_contested || vs_normal)) need_star = true;
+      if (q == q0 && vs_normal) need_lo = true;
+      const Line L = lines[l];
+      if (need_star && r.eb_star > 0.0) {
+        Rescore rq;
+        rq.group = L.group;
+        rq.kind = 1;
+        rq.dst = l;
+        rq.ht = L.ht;
+        rq.delta = r.delta_star;
+        push_request(req, n_req, cap, rq);
+      }
+      if (need_lo && r.eb_lo > 0.0) {
+        Rescore rq;
+        rq.group = L.group;
+        rq.kind = 2;
+        rq.dst = l;
+        rq.ht = L.ht;
+        rq.delta = delta[L.delta0];
+        push_request(req, n_req, cap, rq);
+      }
+    }
+  }
+  int label = 0;
+  if (best >= 0 && wbest < omega_n - tau) label = q_is_zero[best] ? 1 : 2;
+  labels[p] = (int8_t)label;
+  best_q[p] = label == 0 ? -1 : best;
+}
+
+cudaError_t labels_launch(LineResult* res, int n_q, int n_pts, const int32_t* q_is_zero, const Line* lines,
+                          const double* delta, int mode, Rescore* req, int32_t* n_req, int32_t cap,
+                          int8_t* labels, int32_t* best_q, cudaStream_t s) {
+  if (n_pts <= 0) return cudaSuccess;
+  labels_kernel<<<(n_pts + 127) / 128, 128, 0, s>>>(res, n_q, n_pts, q_is_zero, lines, delta, mode, req,
+                                                     n_req, cap, labels, best_q);
+  return cudaGetLastError();
+}
+
+}  // namespace ffe

@@ -1,0 +1,285 @@
+"""Thin ctypes binding of include/ffe.h (argument marshalling only).
+
+Every function of the C ABI is exposed under its own name; numpy structured
+arrays with the C layouts carry the batches.  No arithmetic of the method
+happens here: the CUDA library does all of it, and importing this module
+never falls back to anything else -- if libffe.so is missing or cannot be
+loaded the calls raise FFEError.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libffe.so")
+
+FFE_OK, FFE_EINVAL, FFE_ENOMEM, FFE_ECUDA, FFE_ETIMEOUT, FFE_EUNSUPPORTED, FFE_EINTERNAL = range(7)
+FFE_FP64, FFE_FP32C = 0, 1
+FFE_MODEL_RAGHU2 = 0
+FFE_SEARCH_GRID, FFE_SEARCH_GOLDEN = 0, 1
+FFE_FLAG_RESCORED, FFE_FLAG_EDGE, FFE_FLAG_LOWER = 1, 2, 4
+FFE_PHASE_NORMAL, FFE_PHASE_BCS, FFE_PHASE_FFLO = 0, 1, 2
+
+POINT_DTYPE = np.dtype([("N", "<i4"), ("reserved", "<i4"), ("qx", "<f8"), ("qy", "<f8"),
+                        ("h", "<f8"), ("T", "<f8"), ("delta", "<f8")])
+PARAM_DTYPE = np.dtype([("N", "<i4"), ("n", "<i4"), ("qx", "<f8"), ("qy", "<f8"), ("h", "<f8"),
+                        ("T", "<f8"), ("lo", "<f8"), ("hi", "<f8")])
+RESULT_DTYPE = np.dtype([("delta_star", "<f8"), ("omega_star", "<f8"), ("omega_lo", "<f8"),
+                         ("err_bound", "<f8"), ("idx_star", "<i4"), ("flags", "<i4")])
+
+
+class FFEError(RuntimeError):
+    def __init__(self, status: int, message: str = ""):
+        self.status = status
+        super().__init__(f"ffe status {status}: {message}")
+
+
+class ffe_model(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("prec", ctypes.c_int32), ("t1", ctypes.c_double),
+                ("t2", ctypes.c_double), ("t3", ctypes.c_double), ("t4", ctypes.c_double),
+                ("mu", ctypes.c_double), ("U", ctypes.c_double), ("eta_amp", ctypes.c_double)]
+
+
+class ffe_scan(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("n_q", ctypes.c_int32),
+                ("qx", ctypes.POINTER(ctypes.c_double)), ("qy", ctypes.POINTER(ctypes.c_double)),
+                ("n_h", ctypes.c_int32), ("n_T", ctypes.c_int32),
+                ("h", ctypes.POINTER(ctypes.c_double)), ("T", ctypes.POINTER(ctypes.c_double)),
+                ("search", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("lo", ctypes.c_double), ("hi", ctypes.c_double)]
+
+
+class ffe_plan_info(ctypes.Structure):
+    _fields_ = [("k_evals", ctypes.c_double), ("device_bytes", ctypes.c_double), ("launches", ctypes.c_int32),
+                ("rescored_search", ctypes.c_int32), ("rescored_labels", ctypes.c_int32),
+                ("kpt", ctypes.c_int32), ("block", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("work_items", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/ffe.h
+_VP = ctypes.c_void_p
+_SIGNATURES = [
+    ("ffe_create", ctypes.c_int, [ctypes.POINTER(ffe_model), ctypes.POINTER(_VP)]),
+    ("ffe_destroy", None, [_VP]),
+    ("ffe_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("ffe_last_error", ctypes.c_char_p, [_VP]),
+    ("ffe_omega", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP]),
+    ("ffe_minimize", ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, _VP, _VP, _VP]),
+    ("ffe_phase_scan", ctypes.c_int, [_VP, ctypes.POINTER(ffe_scan), _VP, _VP, _VP, _VP]),
+    ("ffe_plan_phase_scan", ctypes.c_int, [_VP, ctypes.POINTER(ffe_scan), _VP, ctypes.POINTER(_VP)]),
+    ("ffe_plan_execute", ctypes.c_int, [_VP, _VP]),
+    ("ffe_plan_fetch", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    ("ffe_plan_stats", ctypes.c_int, [_VP, ctypes.POINTER(ffe_plan_info)]),
+    ("ffe_plan_kernel_ms", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
+    ("ffe_plan_destroy", None, [_VP]),
+]
+
+
+def lib():
+    """Load libffe.so from the package directory (raises FFEError if absent)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise FFEError(FFE_EINTERNAL, f"{LIB_PATH} is missing: run __graft_entry__.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, res, args in _SIGNATURES:
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return [s[0] for s in _SIGNATURES]
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_VP)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _check(ctx, st):
+    if st != FFE_OK:
+        msg = lib().ffe_last_error(ctx).decode() if ctx else ""
+        if not msg:
+            msg = lib().ffe_status_string(st).decode()
+        raise FFEError(st, msg)
+
+
+# ------------------------------------------------------------ entry points
+def ffe_create(t1=-1.0, t2=1.3, t3=-0.85, t4=-0.85, mu=1.54, U=2.0, eta_amp=1.0, prec=FFE_FP32C):
+    m = ffe_model(FFE_MODEL_RAGHU2, prec, t1, t2, t3, t4, mu, U, eta_amp)
+    h = _VP()
+    st = lib().ffe_create(ctypes.byref(m), ctypes.byref(h))
+    if st != FFE_OK:
+        raise FFEError(st, lib().ffe_status_string(st).decode())
+    return h
+
+
+def ffe_destroy(ctx):
+    lib().ffe_destroy(ctx)
+
+
+def ffe_omega(ctx, points: np.ndarray, stream=None) -> np.ndarray:
+    pts = np.ascontiguousarray(points, dtype=POINT_DTYPE)
+    out = np.zeros(len(pts))
+    _check(ctx, lib().ffe_omega(ctx, _ptr(pts), len(pts), _ptr(out), None, _stream(stream)))
+    return out
+
+
+def ffe_minimize(ctx, params: np.ndarray, search=FFE_SEARCH_GRID, want_grid=False, stream=None):
+    ps = np.ascontiguousarray(params, dtype=PARAM_DTYPE)
+    res = np.zeros(len(ps), dtype=RESULT_DTYPE)
+    grid = np.zeros(int(ps["n"].sum())) if want_grid else None
+    err = np.zeros(int(ps["n"].sum())) if want_grid else None
+    _check(ctx, lib().ffe_minimize(ctx, search, _ptr(ps), len(ps), _ptr(res), _ptr(grid), _ptr(err),
+                                   _stream(stream)))
+    return (res, grid, err) if want_grid else res
+
+
+def make_scan(N, qx, qy, h, T, search=FFE_SEARCH_GRID, n=256, lo=0.0, hi=0.2):
+    """Returns (ffe_scan, keepalive arrays)."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (qx, qy, h, T)]
+    dp = ctypes.POINTER(ctypes.c_double)
+    sc = ffe_scan(N, len(arrs[0]), arrs[0].ctypes.data_as(dp), arrs[1].ctypes.data_as(dp),
+                  len(arrs[2]), len(arrs[3]), arrs[2].ctypes.data_as(dp), arrs[3].ctypes.data_as(dp),
+                  search, n, lo, hi)
+    return sc, arrs
+
+
+def ffe_phase_scan(ctx, N, qx, qy, h, T, search=FFE_SEARCH_GRID, n=256, lo=0.0, hi=0.2, stream=None):
+    """Returns (per_point[n_q, n_h*n_T], labels[n_h*n_T], best_q[n_h*n_T])."""
+    sc, keep = make_scan(N, qx, qy, h, T, search, n, lo, hi)
+    npts = sc.n_h * sc.n_T
+    res = np.zeros((sc.n_q, npts), dtype=RESULT_DTYPE)
+    labels = np.zeros(npts, dtype=np.int8)
+    best = np.zeros(npts, dtype=np.int32)
+    _check(ctx, lib().ffe_phase_scan(ctx, ctypes.byref(sc), _ptr(res), _ptr(labels), _ptr(best),
+                                     _stream(stream)))
+    del keep
+    return res, labels, best
+
+
+def ffe_plan_phase_scan(ctx, N, qx, qy, h, T, search=FFE_SEARCH_GRID, n=256, lo=0.0, hi=0.2, stream=None):
+    sc, keep = make_scan(N, qx, qy, h, T, search, n, lo, hi)
+    plan = _VP()
+    _check(ctx, lib().ffe_plan_phase_scan(ctx, ctypes.byref(sc), _stream(stream), ctypes.byref(plan)))
+    del keep
+    return Plan(ctx, plan, sc.n_q, sc.n_h * sc.n_T)
+
+
+def ffe_plan_execute(plan, stream=None):
+    _check(plan.ctx, lib().ffe_plan_execute(plan.handle, _stream(stream)))
+
+
+def ffe_plan_fetch(plan, stream=None):
+    res = np.zeros((plan.n_q, plan.n_pts), dtype=RESULT_DTYPE)
+    labels = np.zeros(plan.n_pts, dtype=np.int8)
+    best = np.zeros(plan.n_pts, dtype=np.int32)
+    _check(plan.ctx, lib().ffe_plan_fetch(plan.handle, _ptr(res), _ptr(labels), _ptr(best), _stream(stream)))
+    return res, labels, best
+
+
+def ffe_plan_stats(plan) -> dict:
+    info = ffe_plan_info()
+    _check(plan.ctx, lib().ffe_plan_stats(plan.handle, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in ffe_plan_info._fields_ if name != "reserved"}
+
+
+def ffe_plan_kernel_ms(plan):
+    ms = ctypes.c_double()
+    n = ctypes.c_int32()
+    _check(plan.ctx, lib().ffe_plan_kernel_ms(plan.handle, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def ffe_plan_destroy(plan):
+    if plan.handle:
+        lib().ffe_plan_destroy(plan.handle)
+        plan.handle = None
+
+
+class Plan:
+    def __init__(self, ctx, handle, n_q, n_pts):
+        self.ctx, self.handle, self.n_q, self.n_pts = ctx, handle, n_q, n_pts
+
+    def execute(self, stream=None):
+        ffe_plan_execute(self, stream)
+
+    def fetch(self, stream=None):
+        return ffe_plan_fetch(self, stream)
+
+    def stats(self):
+        return ffe_plan_stats(self)
+
+    def kernel_ms(self):
+        return ffe_plan_kernel_ms(self)
+
+    def destroy(self):
+        ffe_plan_destroy(self)
+
+
+class Context:
+    """Owning wrapper: ffe_create on construction, ffe_destroy on close()."""
+
+    def __init__(self, prec=FFE_FP32C, U=2.0, eta_amp=1.0, **model):
+        self.handle = ffe_create(prec=prec, U=U, eta_amp=eta_amp, **model)
+
+    def omega(self, points, stream=None):
+        return ffe_omega(self.handle, points, stream)
+
+    def minimize(self, params, search=FFE_SEARCH_GRID, want_grid=False, stream=None):
+        return ffe_minimize(self.handle, params, search, want_grid, stream)
+
+    def phase_scan(self, *a, **k):
+        return ffe_phase_scan(self.handle, *a, **k)
+
+    def plan_phase_scan(self, *a, **k):
+        return ffe_plan_phase_scan(self.handle, *a, **k)
+
+    def close(self):
+        if self.handle:
+            ffe_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def points(N, qx, qy, h, T, delta) -> np.ndarray:
+    """Pack broadcastable columns into an ffe_point array."""
+    cols = np.broadcast_arrays(np.asarray(N), np.asarray(qx, float), np.asarray(qy, float),
+                               np.asarray(h, float), np.asarray(T, float), np.asarray(delta, float))
+    a = np.zeros(cols[0].size, dtype=POINT_DTYPE)
+    for name, c in zip(("N", "qx", "qy", "h", "T", "delta"), cols):
+        a[name] = c.ravel()
+    return a
+
+
+def params(N, qx, qy, h, T, lo, hi, n) -> np.ndarray:
+    cols = np.broadcast_arrays(np.asarray(N), np.asarray(qx, float), np.asarray(qy, float),
+                               np.asarray(h, float), np.asarray(T, float), np.asarray(lo, float),
+                               np.asarray(hi, float), np.asarray(n))
+    a = np.zeros(cols[0].size, dtype=PARAM_DTYPE)
+    for name, c in zip(("N", "qx", "qy", "h", "T", "lo", "hi", "n"), cols):
+        a[name] = c.ravel()
+    return a

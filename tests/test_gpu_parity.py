@@ -1,0 +1,180 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (per lattice site, units of |t1|): FP64 1e-9, FP32+compensated 2e-7.
+Argmin indices and phase labels must be identical to the oracle's.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import search
+from paper_1412_8754_gb300 import ffe, workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = {ffe.FFE_FP64: 1e-9, ffe.FFE_FP32C: 2e-7}
+PRECS = [ffe.FFE_FP64, ffe.FFE_FP32C]
+
+
+def per_site(a, b, N):
+    return np.abs(np.asarray(a) - np.asarray(b)) / (np.asarray(N, dtype=float) ** 2)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ffe.lib()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_omega_random_points(prec):
+    """Ragged lattices (N=8: 64 k-points; N=24: 576), both signs of q and h."""
+    w = workloads.random_points(160, seed=11)
+    U, eta = 2.5, 1.0
+    m = oracle.make_model(U=U, eta_amp=eta)
+    ref, _, _ = oracle.omega_batch(m, w["N"], w["qx"], w["qy"], w["h"], w["T"], w["delta"])
+    with ffe.Context(prec=prec, U=U, eta_amp=eta) as ctx:
+        got = ctx.omega(ffe.points(w["N"], w["qx"], w["qy"], w["h"], w["T"], w["delta"]))
+    err = per_site(got, ref, w["N"])
+    assert err.max() <= TOL[prec], (err.max(), int(err.argmax()))
+
+
+@pytest.mark.parametrize("N", [2, 4, 6, 10])
+@pytest.mark.parametrize("prec", PRECS)
+def test_omega_tiny_lattices(prec, N):
+    m = oracle.make_model(U=2.0, eta_amp=4.0)
+    d = np.linspace(0.0, 0.2, 7)
+    ref, _, _ = oracle.omega_batch(m, N, 0.3, 0.1, 0.05, 0.01, d)
+    with ffe.Context(prec=prec, U=2.0, eta_amp=4.0) as ctx:
+        got = ctx.omega(ffe.points(N, 0.3, 0.1, 0.05, 0.01, d))
+    assert per_site(got, ref, N).max() <= TOL[prec]
+
+
+@pytest.mark.parametrize("U", [2.0, 4.0])
+@pytest.mark.parametrize("prec", PRECS)
+def test_small_bcs_grid(prec, U):
+    """N=64, Q=0, h=0, T=0.005, 201 Delta in [0, 0.2]: Omega(Delta) and its argmin."""
+    c = workloads.SMALL_BCS
+    m = oracle.make_model(U=U)
+    grid = np.linspace(c["lo"], c["hi"], c["n"])
+    ref, _, _ = oracle.omega_batch(m, c["N"], 0.0, 0.0, 0.0, c["T"][0], grid)
+    with ffe.Context(prec=prec, U=U) as ctx:
+        res, om, eb = ctx.minimize(ffe.params(c["N"], 0.0, 0.0, 0.0, c["T"][0], c["lo"], c["hi"], c["n"]),
+                                   want_grid=True)
+    assert per_site(om, ref, c["N"]).max() <= TOL[prec]
+    i = search.grid_argmin(ref)
+    assert res["idx_star"][0] == i
+    assert res["delta_star"][0] == grid[i]
+    assert abs(res["omega_star"][0] - ref[i]) / c["N"] ** 2 <= TOL[prec]
+    if U == 2.0:
+        assert i == 0 and res["flags"][0] & ffe.FFE_FLAG_LOWER
+    else:
+        assert 100 < i < 130
+
+
+def oracle_scan(m, N, qx, qy, h, T, grid):
+    """Per (q, point) Omega grids, minima and labels, all from the oracle."""
+    H, TT = np.meshgrid(h, T, indexing="ij")
+    H, TT = H.ravel(), TT.ravel()
+    npts = H.size
+    Q = len(qx)
+    qq = np.repeat(np.arange(Q), npts * len(grid))
+    pp = np.tile(np.repeat(np.arange(npts), len(grid)), Q)
+    dd = np.tile(grid, Q * npts)
+    om, _, _ = oracle.omega_batch(m, N, np.asarray(qx)[qq], np.asarray(qy)[qq], H[pp], TT[pp], dd)
+    om = om.reshape(Q, npts, len(grid))
+    idx = np.array([[search.grid_argmin(om[q, p]) for p in range(npts)] for q in range(Q)])
+    star = np.take_along_axis(om, idx[..., None], axis=2)[..., 0]
+    labels, best = [], []
+    for p in range(npts):
+        lab, b = search.phase_label(star[:, p], om[:, p, 0],
+                                    (np.asarray(qx) == 0) & (np.asarray(qy) == 0))
+        labels.append(lab)
+        best.append(b)
+    return om, idx, star, np.array(labels), np.array(best)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_phase_scan_small(prec):
+    """Grid phase scan: 6 q x (4 h x 2 T) x 41 Delta at N=32, U=4 (BCS and FF minima)."""
+    N, U = 32, 4.0
+    qx = np.array([0.0, 0.1, 0.2, 0.3, 0.45, 0.6])
+    qy = np.zeros_like(qx)
+    h = np.array([0.0, 0.05, 0.1, 0.15])
+    T = np.array([0.004, 0.02])
+    grid = np.linspace(0.0, 0.2, 41)
+    m = oracle.make_model(U=U)
+    om, idx, star, labels, best = oracle_scan(m, N, qx, qy, h, T, grid)
+    with ffe.Context(prec=prec, U=U) as ctx:
+        res, glab, gbest = ctx.phase_scan(N, qx, qy, h, T, n=41, lo=0.0, hi=0.2)
+    assert np.array_equal(res["idx_star"], idx)
+    assert per_site(res["omega_star"], star, N).max() <= TOL[prec]
+    assert per_site(res["omega_lo"], om[..., 0], N).max() <= TOL[prec]
+    assert np.array_equal(glab, labels), (glab, labels)
+    assert np.array_equal(gbest, best)
+
+
+def test_fp32c_error_bound_covers_fp64():
+    """Every FP32+compensated value lies within its stated bound of the FP64 kernel's."""
+    w = workloads.uneven_jobs(24, seed=5, sizes=(16, 32, 48, 64))
+    ps = ffe.params(w["N"], w["qx"], w["qy"], w["h"], w["T"], w["lo"], w["hi"], w["n"])
+    with ffe.Context(prec=ffe.FFE_FP64, U=3.0) as c64, ffe.Context(prec=ffe.FFE_FP32C, U=3.0) as c32:
+        r64, g64, e64 = c64.minimize(ps, want_grid=True)
+        r32, g32, e32 = c32.minimize(ps, want_grid=True)
+    assert np.all(e64 == 0)
+    assert np.all(np.abs(g32 - g64) <= e32 + 1e-12 * np.abs(g64))
+    assert np.array_equal(r32["idx_star"], r64["idx_star"])
+
+
+def test_uneven_jobs_small_vs_oracle():
+    """Uneven lattices and grid lengths in one launch (shape of the 512-job batch, small N)."""
+    w = workloads.uneven_jobs(12, seed=3, sizes=(8, 16, 24, 40))
+    w["n"] = np.minimum(w["n"], 60)
+    m = oracle.make_model(U=3.0)
+    ps = ffe.params(w["N"], w["qx"], w["qy"], w["h"], w["T"], w["lo"], w["hi"], w["n"])
+    with ffe.Context(prec=ffe.FFE_FP32C, U=3.0) as ctx:
+        res, grid, _ = ctx.minimize(ps, want_grid=True)
+    off = 0
+    for j in range(len(ps)):
+        n = int(w["n"][j])
+        g = np.linspace(0.0, 0.2, n)
+        ref, _, _ = oracle.omega_batch(m, int(w["N"][j]), w["qx"][j], 0.0, w["h"][j], w["T"][j], g)
+        assert per_site(grid[off:off + n], ref, w["N"][j]).max() <= TOL[ffe.FFE_FP32C]
+        assert res["idx_star"][j] == search.grid_argmin(ref)
+        off += n
+
+
+def test_plan_replay_is_deterministic():
+    N = 64
+    qx = np.array([0.0, 0.2, 0.4])
+    with ffe.Context(prec=ffe.FFE_FP32C, U=4.0) as ctx:
+        plan = ctx.plan_phase_scan(N, qx, np.zeros(3), np.array([0.0, 0.06]), np.array([0.005]), n=64)
+        plan.execute()
+        a = plan.fetch()
+        plan.execute()
+        plan.execute()
+        b = plan.fetch()
+        ms, cnt = plan.kernel_ms()
+        info = plan.stats()
+        plan.destroy()
+    assert a[0].tobytes() == b[0].tobytes()
+    assert np.array_equal(a[1], b[1])
+    assert cnt == 3 and ms > 0
+    assert info["k_evals"] == N * N * 3 * 2 * 64 and info["launches"] >= 4
+
+
+def test_invalid_arguments_are_rejected_before_launch():
+    with ffe.Context(prec=ffe.FFE_FP32C) as ctx:
+        for bad in (ffe.points(7, 0, 0, 0, 0.01, 0.1), ffe.points(16, 0, 0, 0, 0.0, 0.1),
+                    ffe.points(16, 0, 0, 0, float("nan"), 0.1), ffe.points(9000, 0, 0, 0, 0.1, 0.1)):
+            with pytest.raises(ffe.FFEError) as e:
+                ctx.omega(bad)
+            assert e.value.status == ffe.FFE_EINVAL
+        with pytest.raises(ffe.FFEError):
+            ctx.minimize(ffe.params(16, 0, 0, 0, 0.01, 0.2, 0.1, 10))  # lo > hi
+        with pytest.raises(ffe.FFEError):
+            ctx.phase_scan(16, [0.1], [0.0], [0.0], [0.01], n=8)  # no q = 0
+        # the context stays usable
+        ok = ctx.omega(ffe.points(16, 0, 0, 0, 0.01, 0.1))
+        assert np.isfinite(ok[0])
