@@ -209,6 +209,19 @@ FFE_API ffe_status ffe_plan_stats(const ffe_plan* plan, ffe_plan_info* info);
 FFE_API ffe_status ffe_plan_kernel_ms(ffe_plan* plan, double* ms, int32_t* count);
 FFE_API void ffe_plan_destroy(ffe_plan* plan);
 
+/* ---- device throughput probe (no counterpart in the paper) -------------
+ * Measured issue rates, in operations per second over the whole device, of
+ * the units the k-sum is bound by: the special-function unit for
+ * ex2/lg2/rsqrt/rcp (FP32 approximate), FP32 FMA and FP64 FMA.  Runs short
+ * self-contained kernels (~0.1 s) on the current device. */
+typedef struct {
+  double ex2, lg2, rsqrt, rcp;  /* MUFU results per second            */
+  double fma32, fma64;          /* fused multiply-adds per second      */
+  int32_t n_sm;                 /* multiprocessors                     */
+  int32_t sm_khz_max;           /* maximum SM clock reported (kHz)     */
+} ffe_peaks;
+FFE_API ffe_status ffe_probe_peaks(ffe_peaks* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -163,6 +163,19 @@ void build_mitems(ffe_plan* p) {
   p->n_mcounters = counter;
 }
 
+// True when every 32-entry (h,T) batch of every PRODUCT group has one T.
+bool batches_share_T(const ffe_plan* p) {
+  for (const GroupDesc& g : p->groups) {
+    if (g.layout != kLayoutProduct) return false;
+    for (int j0 = 0; j0 < g.n_ht; j0 += 32) {
+      const int j1 = std::min(g.n_ht, j0 + 32);
+      for (int j = j0 + 1; j < j1; ++j)
+        if (p->ht[g.ht_off + j].T != p->ht[g.ht_off + j0].T) return false;
+    }
+  }
+  return true;
+}
+
 double plan_k_evals(const ffe_plan* p) {
   double s = 0.0;
   for (const GroupDesc& g : p->groups) s += (double)g.N * (double)g.N * (double)g.n_out;
@@ -273,6 +286,8 @@ static KsumArgs make_ksum_args(ffe_plan* p) {
   a.eb_rel = p->prec == FFE_FP32C ? kEbRel : 0.0;
   a.eb_abs = p->prec == FFE_FP32C ? kEbAbs : 0.0;
   a.status = p->d_counters + 7;
+  a.w_scaled = p->prec == FFE_FP32C ? 1 : 0;
+  a.pad1 = 0;
   return a;
 }
 
@@ -323,7 +338,7 @@ ffe_status plan_enqueue(ffe_context* ctx, ffe_plan* p, cudaStream_t s, cudaEvent
   ++launches;
   if (ev0) FFE_CU(cudaEventRecordWithFlags(ev0, s, ev_flags), "event");
   KsumArgs ka = make_ksum_args(p);
-  FFE_CU(ksum_launch(p->prec, p->layout, p->kpt, ka, p->grid, p->block, s), "ksum");
+  FFE_CU(ksum_launch(p->prec, p->variant, p->kpt, ka, p->grid, p->block, s), "ksum");
   ++launches;
   if (ev1) FFE_CU(cudaEventRecordWithFlags(ev1, s, ev_flags), "event");
   if (!p->lines.empty()) {
@@ -358,8 +373,10 @@ ffe_status plan_configure(ffe_context* ctx, ffe_plan* p) {
   p->kpt = t.kpt;
   p->block = t.block;
   p->item_target = t.item_target;
+  p->variant = p->layout;
+  if (p->prec == FFE_FP32C && p->layout == kLayoutProduct && batches_share_T(p)) p->variant = kLayoutProductUT;
   int bps = 0;
-  cudaError_t e = ksum_occupancy(p->prec, p->layout, p->kpt, p->block, &bps);
+  cudaError_t e = ksum_occupancy(p->prec, p->variant, p->kpt, p->block, &bps);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy");
   if (bps < 1) bps = 1;
   p->grid = ctx->n_sm * bps;
@@ -728,8 +745,16 @@ ffe_status ffe_phase_scan(ffe_context* ctx, const ffe_scan* scan, ffe_result* pe
   if (it != ctx->cache.end()) {
     p = it->second;
     fill_scan_grid(p, scan);
-    if ((st = plan_upload_params(ctx, p, s)) != FFE_OK) return st;
-  } else {
+    const bool ut = ctx->model.prec == FFE_FP32C && batches_share_T(p);
+    if (ut != (p->variant == kLayoutProductUT)) {  // the kernel variant no longer fits: rebuild
+      plan_free(p);
+      ctx->cache.erase(it);
+      p = nullptr;
+    } else if ((st = plan_upload_params(ctx, p, s)) != FFE_OK) {
+      return st;
+    }
+  }
+  if (!p) {
     p = plan_new(ctx, kPlanScanGrid);
     fill_scan_grid(p, scan);
     st = plan_configure(ctx, p);

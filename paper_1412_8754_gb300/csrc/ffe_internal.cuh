@@ -26,6 +26,7 @@ constexpr int kWarp = 32;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kLayoutProduct = 0;  // outputs = Delta-list x (h,T)-list, shared R per Delta
 constexpr int kLayoutList = 1;     // outputs = explicit (Delta, h, T) triples
+constexpr int kLayoutProductUT = 2;  // kernel variant of PRODUCT: one T per 32-output batch
 constexpr int kMaxBatchesPerItem = 16;
 constexpr int kFlagRescored = 1;  // values of include/ffe.h FFE_FLAG_*
 constexpr int kFlagEdge = 2;
@@ -167,27 +168,51 @@ __device__ __forceinline__ void ra_f32(float D, float s2, float as, float& R, fl
   R = u * rsqa(u);
   a = D * rcpa(R + as);
 }
+
+// FP32 k-point term in units of T ln 2.  With c = 1/(T ln 2) the term of one
+// band is  -T ln2 [ c min(max(R - |d|, 0), a) + log2((1+e1)(1+e2)) ],
+// e1 = 2^{-c|R-d|}, e2 = 2^{-c|R+d|} (the pair {|R-d|, |R+d|} equals
+// {|R-|d||, R+|d|}), because
+//   min(0, max(|d|-|s|, 0) - a) = -min(max(R - |d|, 0), a)     (R = |s| + a)
+// and R - |d| = min(R - d, R + d).  The factor -T ln2 is constant over k and
+// is applied once per output after the k-sum, so the accumulated quantity
+// W = sum_k [...] is non-negative.  The two bands are evaluated as the two
+// halves of packed FP32x2 operations.
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// Per-k FP32 state with the two bands packed: eta^2, |s|, s^2, d0.
+struct KState32 {
+  float eta2;
+  float2 as, s2, d0;
+};
+
+// One k-point, both bands, one (h, c): adds c min(...) of each band to cp2 and
+// returns log2 of the product of the four (1 + e) factors.
+// Rc = R c and ac = a c per band; nh2 = (-h, -h); c2 = (c, c); nc2 = -c2.
+__device__ __forceinline__ float w_term32(const KState32& st, float2 Rc, float2 ac, float2 nh2, float2 c2,
+                                          float2 nc2, float2& cp2) {
+  const float2 d = __fadd2_rn(st.d0, nh2);  // d = d0 - h
+  const float2 y1 = __ffma2_rn(d, nc2, Rc);  // c (R - d)
+  const float2 y2 = __ffma2_rn(d, c2, Rc);   // c (R + d)
+  const float2 e1 = make_float2(ex2a(-fabsf(y1.x)), ex2a(-fabsf(y1.y)));
+  const float2 e2 = make_float2(ex2a(-fabsf(y2.x)), ex2a(-fabsf(y2.y)));
+  const float2 o1 = __fadd2_rn(e1, make_float2(1.0f, 1.0f));
+  const float2 p = __ffma2_rn(o1, e2, o1);
+  const float2 cp = make_float2(fmaxf(min3f(y1.x, y2.x, ac.x), 0.0f), fmaxf(min3f(y1.y, y2.y, ac.y), 0.0f));
+  cp2 = __fadd2_rn(cp2, cp);
+  return lg2a(p.x * p.y);
+}
 __device__ __forceinline__ void ra_f64(double D, double s2, double as, double& R, double& a) {
   R = sqrt(D + s2);
   a = D / (R + as);
 }
 
-// One band's contribution for one (h,T): p = (1+e1)(1+e2), first = min(0, g - a).
-__device__ __forceinline__ void band_term_f32(float R, float a, float as, float d0, float h,
-                                              float c, float& p, float& first) {
-  float d = d0 - h;
-  float ad = fabsf(d);
-  float x1 = R - ad;
-  float x2 = R + ad;
-  float e1 = ex2a(-fabsf(x1) * c);
-  float e2 = ex2a(-x2 * c);
-  float o1 = 1.0f + e1;
-  p = fmaf(o1, e2, o1);
-  float g = fmaxf(ad - as, 0.0f);
-  first = fminf(g - a, 0.0f);
-}
-
-// FP64: q = p - 1 = e1 + e2 + e1 e2 (kept as p - 1 for log1p).
+// FP64 band term for one (h,T): q = p - 1 = e1 + e2 + e1 e2 (kept as p - 1
+// for log1p) and first = min(0, max(|d|-|s|, 0) - a).
 __device__ __forceinline__ void band_term_f64(double R, double a, double as, double d0, double h,
                                               double inv_t, double& q, double& first) {
   double d = d0 - h;

@@ -119,20 +119,111 @@ __device__ __forceinline__ int stage_batch(const KsumArgs& a, const GroupDesc& g
   return nvalid;
 }
 
-// v_k summed over this lane's KPT k-points for one output (both bands).
+// ------------------------------------------------------------ FP32 path
 template <int KPT>
-__device__ __forceinline__ float v_sum_f32(const KState<float> (&st)[KPT], const float (&R)[KPT][2],
-                                           const float (&A)[KPT][2], const BParF& p) {
-  float s = 0.0f;
+__device__ __forceinline__ void build_states32(const KsumArgs& a, const GroupDesc& g, int ks, int lane,
+                                               KState32 (&st)[KPT]) {
+  KState<float> s[KPT];
+  build_states<float, KPT>(a, g, ks, lane, s);
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
-    float p0, f0, p1, f1;
-    band_term_f32(R[k][0], A[k][0], st[k].as[0], st[k].d0[0], p.h, p.c, p0, f0);
-    band_term_f32(R[k][1], A[k][1], st[k].as[1], st[k].d0[1], p.h, p.c, p1, f1);
-    const float v = fmaf(-p.tl, lg2a(p0 * p1), f0 + f1);
-    s += v;
+    st[k].eta2 = s[k].eta2;
+    st[k].as = make_float2(s[k].as[0], s[k].as[1]);
+    st[k].s2 = make_float2(s[k].s2[0], s[k].s2[1]);
+    st[k].d0 = make_float2(s[k].d0[0], s[k].d0[1]);
   }
-  return s;
+}
+
+// R and a = Delta^2 eta^2 / (R + |s|) of both bands at Delta^2 = d2.
+__device__ __forceinline__ void ra32(const KState32& st, float d2, float2& R, float2& A) {
+  const float D = d2 * st.eta2;
+  const float2 D2 = make_float2(D, D);
+  const float2 u = __fadd2_rn(D2, st.s2);
+  R = __fmul2_rn(u, make_float2(rsqa(u.x), rsqa(u.y)));
+  const float2 den = __fadd2_rn(R, st.as);
+  A = __fmul2_rn(D2, make_float2(rcpa(den.x), rcpa(den.y)));
+}
+
+// W of one output (both bands) summed over this lane's KPT k-points.
+template <int KPT>
+__device__ __forceinline__ float w_out32(const KState32 (&st)[KPT], const float2 (&Rc)[KPT],
+                                         const float2 (&Ac)[KPT], float h, float c) {
+  const float2 nh2 = make_float2(-h, -h), c2 = make_float2(c, c), nc2 = make_float2(-c, -c);
+  float2 cp2 = make_float2(0.0f, 0.0f);
+  float L = 0.0f;
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) L += w_term32(st[k], Rc[k], Ac[k], nh2, c2, nc2, cp2);
+  return (cp2.x + cp2.y) + L;
+}
+
+// One batch of up to 32 outputs.  Output j's per-lane sum goes to row j of
+// the warp's transpose buffer `red` (row stride 36 floats); lane l then adds
+// row l.  The output loop stays rolled (small code); returns in lane l the
+// warp total of output l (0 for l >= nvalid).
+template <int KPT, int VARIANT>
+__device__ __forceinline__ float eval_batch32(const KState32 (&st)[KPT], const BParF* bp, int nvalid,
+                                              float d2_product, int lane, float* red) {
+  if (VARIANT == kLayoutProductUT) {
+    const float c = bp[0].c;
+    float2 Rc[KPT], Ac[KPT];
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      float2 R, A;
+      ra32(st[k], d2_product, R, A);
+      Rc[k] = __fmul2_rn(R, make_float2(c, c));
+      Ac[k] = __fmul2_rn(A, make_float2(c, c));
+    }
+#pragma unroll 4
+    for (int j = 0; j < nvalid; ++j) red[j * 36 + lane] = w_out32<KPT>(st, Rc, Ac, bp[j].h, c);
+  } else if (VARIANT == kLayoutProduct) {
+    float2 R[KPT], A[KPT];
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) ra32(st[k], d2_product, R[k], A[k]);
+#pragma unroll 2
+    for (int j = 0; j < nvalid; ++j) {
+      const BParF p = bp[j];
+      const float2 c2 = make_float2(p.c, p.c);
+      float2 Rc[KPT], Ac[KPT];
+#pragma unroll
+      for (int k = 0; k < KPT; ++k) {
+        Rc[k] = __fmul2_rn(R[k], c2);
+        Ac[k] = __fmul2_rn(A[k], c2);
+      }
+      red[j * 36 + lane] = w_out32<KPT>(st, Rc, Ac, p.h, p.c);
+    }
+  } else {
+#pragma unroll 2
+    for (int j = 0; j < nvalid; ++j) {
+      const BParF p = bp[j];
+      const float2 c2 = make_float2(p.c, p.c);
+      float2 Rc[KPT], Ac[KPT];
+#pragma unroll
+      for (int k = 0; k < KPT; ++k) {
+        float2 R, A;
+        ra32(st[k], p.d2, R, A);
+        Rc[k] = __fmul2_rn(R, c2);
+        Ac[k] = __fmul2_rn(A, c2);
+      }
+      red[j * 36 + lane] = w_out32<KPT>(st, Rc, Ac, p.h, p.c);
+    }
+  }
+  __syncwarp();
+  float tot = 0.0f;
+  if (lane < nvalid) {
+    const float4* row = reinterpret_cast<const float4*>(red + lane * 36);
+    float4 s4 = row[0];
+#pragma unroll
+    for (int i = 1; i < 8; ++i) {
+      const float4 v = row[i];
+      s4.x += v.x;
+      s4.y += v.y;
+      s4.z += v.z;
+      s4.w += v.w;
+    }
+    tot = (s4.x + s4.y) + (s4.z + s4.w);
+  }
+  __syncwarp();
+  return tot;
 }
 
 template <int KPT>
@@ -166,43 +257,31 @@ __device__ __forceinline__ void ra_all(const KState<Real> (&st)[KPT], Real d2, R
   }
 }
 
-// One batch: returns, in lane l, the warp's sum for output l of the batch.
-template <typename Real, int KPT, int LAYOUT>
-__device__ __forceinline__ Real eval_batch(const KsumArgs& a, const KState<Real> (&st)[KPT],
-                                           const BPar<Real>* bp, int nvalid, Real d2_product, int lane) {
-  Real part[32];
-  if (LAYOUT == kLayoutProduct) {
-    Real R[KPT][2], A[KPT][2];
-    ra_all<Real, KPT>(st, d2_product, R, A);
+// FP64 path, one batch: returns, in lane l, the warp's sum of v for output l
+// (butterfly reduce-scatter of the 32 per-lane sums).
+template <int KPT, int VARIANT>
+__device__ __forceinline__ double eval_batch64(const KState<double> (&st)[KPT], const BParD* bp, int nvalid,
+                                               double d2_product, int lane) {
+  double part[32];
+  if (VARIANT != kLayoutList) {
+    double R[KPT][2], A[KPT][2];
+    ra_all<double, KPT>(st, d2_product, R, A);
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      Real s = (Real)0;
-      if (j < nvalid) {
-        const BPar<Real> p = bp[j];
-        if constexpr (std::is_same<Real, float>::value)
-          s = v_sum_f32<KPT>(st, R, A, p);
-        else
-          s = v_sum_f64<KPT>(st, R, A, p);
-      }
-      part[j] = s;
-    }
+    for (int j = 0; j < 32; ++j) part[j] = (j < nvalid) ? v_sum_f64<KPT>(st, R, A, bp[j]) : 0.0;
   } else {
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
-      Real s = (Real)0;
+      double s = 0.0;
       if (j < nvalid) {
-        const BPar<Real> p = bp[j];
-        Real R[KPT][2], A[KPT][2];
-        ra_all<Real, KPT>(st, (Real)p.d2, R, A);
-        if constexpr (std::is_same<Real, float>::value)
-          s = v_sum_f32<KPT>(st, R, A, p);
-        else
-          s = v_sum_f64<KPT>(st, R, A, p);
+        const BParD p = bp[j];
+        double R[KPT][2], A[KPT][2];
+        ra_all<double, KPT>(st, p.d2, R, A);
+        s = v_sum_f64<KPT>(st, R, A, p);
       }
       part[j] = s;
     }
   }
-  return reduce_scatter32<Real>(part, lane);
+  return reduce_scatter32<double>(part, lane);
 }
 
 // Output index (within the group) of lane `lane` in batch b, or -1.
@@ -234,6 +313,7 @@ __device__ void finalize_segment(const KsumArgs& a, const Segment& sg, const Gro
     for (int c = 0; c < sg.n_chunks; ++c) V += __ldcg(src + (int64_t)c * nb * 32);
     const double dl = a.delta[g.delta_off + di];
     const HT ht = a.ht[g.ht_off + hi];
+    if (a.w_scaled) V *= -ht.T * 0.69314718055994530942;  // W -> sum_k v_k
     const double M = a.M[g.h_off + ht.h_idx];
     const int64_t out = g.out_off + o;
     a.V[out] = V;
@@ -249,9 +329,10 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   double* acc = reinterpret_cast<double*>(smem_raw) + (size_t)warp * (kMaxBatchesPerItem * 32);
-  BPar<Real>* bp = reinterpret_cast<BPar<Real>*>(smem_raw + (size_t)nwarps * kMaxBatchesPerItem * 32 *
-                                                               sizeof(double)) +
-                   warp * 32;
+  unsigned char* after_acc = smem_raw + (size_t)nwarps * kMaxBatchesPerItem * 32 * sizeof(double);
+  BPar<Real>* bp = reinterpret_cast<BPar<Real>*>(after_acc) + warp * 32;
+  // FP32 only: per-warp 32 x 36 transpose buffer of the output reduction
+  float* red = reinterpret_cast<float*>(after_acc + (size_t)nwarps * 32 * sizeof(BPar<Real>)) + warp * 32 * 36;
   for (;;) {
     int it = 0;
     if (lane == 0) it = atomicAdd(a.queue, 1);
@@ -260,28 +341,37 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
     const WorkItem w = a.items[it];
     const GroupDesc g = a.groups[w.group];
     const int nb = w.b1 - w.b0;
-    if (nb > kMaxBatchesPerItem || g.layout != LAYOUT) {
+    constexpr int kGroupLayout = (LAYOUT == kLayoutList) ? kLayoutList : kLayoutProduct;
+    if (nb > kMaxBatchesPerItem || g.layout != kGroupLayout) {
       if (lane == 0) atomicOr(a.status, 1);
       continue;
     }
     for (int b = 0; b < nb; ++b) acc[b * 32 + lane] = 0.0;
     for (int ks = w.kset0; ks < w.kset1; ++ks) {
-      KState<Real> st[KPT];
-      build_states<Real, KPT>(a, g, ks, lane, st);
-      for (int b = w.b0; b < w.b1; ++b) {
-        int di;
-        const int nvalid = stage_batch<Real, LAYOUT>(a, g, b, lane, bp, di);
-        Real d2p = (Real)0;
-        if (LAYOUT == kLayoutProduct) {
-          if constexpr (std::is_same<Real, float>::value)
-            d2p = a.d2f[g.delta_off + di];
-          else {
+      if constexpr (std::is_same<Real, float>::value) {
+        KState32 st[KPT];
+        build_states32<KPT>(a, g, ks, lane, st);
+        for (int b = w.b0; b < w.b1; ++b) {
+          int di;
+          const int nvalid = stage_batch<float, kGroupLayout>(a, g, b, lane, bp, di);
+          const float d2p = (kGroupLayout == kLayoutProduct) ? a.d2f[g.delta_off + di] : 0.0f;
+          const float tot = eval_batch32<KPT, LAYOUT>(st, bp, nvalid, d2p, lane, red);
+          acc[(b - w.b0) * 32 + lane] += (double)tot;
+        }
+      } else {
+        KState<double> st[KPT];
+        build_states<double, KPT>(a, g, ks, lane, st);
+        for (int b = w.b0; b < w.b1; ++b) {
+          int di;
+          const int nvalid = stage_batch<double, kGroupLayout>(a, g, b, lane, bp, di);
+          double d2p = 0.0;
+          if (kGroupLayout == kLayoutProduct) {
             const double dd = a.delta[g.delta_off + di];
             d2p = dd * dd;
           }
+          const double tot = eval_batch64<KPT, LAYOUT>(st, bp, nvalid, d2p, lane);
+          acc[(b - w.b0) * 32 + lane] += tot;
         }
-        const Real tot = eval_batch<Real, KPT, LAYOUT>(a, st, bp, nvalid, d2p, lane);
-        acc[(b - w.b0) * 32 + lane] += (double)tot;
       }
     }
     const Segment sg = a.segs[w.seg];
@@ -304,7 +394,8 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
 size_t ksum_smem_bytes(int prec, int block_threads) {
   const int nw = block_threads / 32;
   const size_t par = (prec == 1) ? sizeof(BParF) : sizeof(BParD);
-  return (size_t)nw * (kMaxBatchesPerItem * 32 * sizeof(double) + 32 * par);
+  const size_t red = (prec == 1) ? 32 * 36 * sizeof(float) : 0;
+  return (size_t)nw * (kMaxBatchesPerItem * 32 * sizeof(double) + 32 * par + red);
 }
 
 template <typename Real, int KPT, int LAYOUT>
@@ -332,7 +423,11 @@ static cudaError_t occupancy_one(int block, size_t smem, int* blocks_per_sm) {
 #define FFE_KSUM_DISPATCH(FN, ...)                                                         \
   do {                                                                                     \
     if (prec == 1) {                                                                       \
-      if (layout == kLayoutProduct) {                                                      \
+      if (layout == kLayoutProductUT) {                                                    \
+        if (kpt == 2) return FN<float, 2, kLayoutProductUT>(__VA_ARGS__);                  \
+        if (kpt == 4) return FN<float, 4, kLayoutProductUT>(__VA_ARGS__);                  \
+        if (kpt == 8) return FN<float, 8, kLayoutProductUT>(__VA_ARGS__);                  \
+      } else if (layout == kLayoutProduct) {                                               \
         if (kpt == 2) return FN<float, 2, kLayoutProduct>(__VA_ARGS__);                    \
         if (kpt == 4) return FN<float, 4, kLayoutProduct>(__VA_ARGS__);                    \
         if (kpt == 8) return FN<float, 8, kLayoutProduct>(__VA_ARGS__);                    \
@@ -342,7 +437,7 @@ static cudaError_t occupancy_one(int block, size_t smem, int* blocks_per_sm) {
         if (kpt == 8) return FN<float, 8, kLayoutList>(__VA_ARGS__);                       \
       }                                                                                    \
     } else {                                                                               \
-      if (layout == kLayoutProduct) {                                                      \
+      if (layout != kLayoutList) {                                                         \
         if (kpt == 1) return FN<double, 1, kLayoutProduct>(__VA_ARGS__);                   \
         if (kpt == 2) return FN<double, 2, kLayoutProduct>(__VA_ARGS__);                   \
       } else {                                                                             \

@@ -33,6 +33,8 @@ struct KsumArgs {
   double* ebound;       // per-output FP32 error bound (0 for FP64)
   double eb_rel, eb_abs;
   int32_t* status;
+  int32_t w_scaled;  // 1: partial sums hold W (FP32 path), V = -T ln2 W; 0: they hold V
+  int32_t pad1;
 };
 
 size_t ksum_smem_bytes(int prec, int block_threads);

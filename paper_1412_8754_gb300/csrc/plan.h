@@ -63,6 +63,7 @@ struct ffe_plan {
   int golden_steps = 0;
   // launch configuration
   int kpt = 4, block = 256, grid = 0, rescore_grid = 0;
+  int variant = 0;  // k-sum kernel variant (kLayoutProduct / kLayoutProductUT / kLayoutList)
   double item_target = 8388608.0;
   int rescore_chunk = 16384, rescore_chunks = 1;
   int32_t cap = 0;
@@ -134,6 +135,7 @@ ffe_status plan_check_status(ffe_context* ctx, ffe_plan* p, cudaStream_t s);
 double plan_k_evals(const ffe_plan* p);
 void build_items(ffe_plan* p);
 void build_mitems(ffe_plan* p);
+bool batches_share_T(const ffe_plan* p);
 
 Tuning tuning_for(ffe_context* ctx, const ffe_plan* p);
 void tuning_load(ffe_context* ctx);

@@ -2,6 +2,8 @@
 // Delta searches, uneven lattices and grid lengths in one persistent launch).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <tuple>
@@ -131,6 +133,17 @@ Tuning tuning_for(ffe_context* ctx, const ffe_plan* p) {
   t.kpt = p->prec == FFE_FP32C ? 4 : 1;
   t.block = 256;
   t.item_target = p->prec == FFE_FP32C ? 8388608.0 : 262144.0;
+  // explicit override "kpt:block:item_target" (used by the tuning sweeps)
+  if (const char* env = getenv(p->prec == FFE_FP32C ? "FFE_KSUM_TUNING_FP32" : "FFE_KSUM_TUNING_FP64")) {
+    int kpt = 0, block = 0;
+    double target = 0.0;
+    if (sscanf(env, "%d:%d:%lf", &kpt, &block, &target) == 3 && ksum_kpt_supported(p->prec, kpt) &&
+        (block == 128 || block == 256) && target >= 1024.0) {
+      t.kpt = kpt;
+      t.block = block;
+      t.item_target = target;
+    }
+  }
   return t;
 }
 

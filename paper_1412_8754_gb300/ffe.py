@@ -79,7 +79,22 @@ _SIGNATURES = [
     ("ffe_plan_stats", ctypes.c_int, [_VP, ctypes.POINTER(ffe_plan_info)]),
     ("ffe_plan_kernel_ms", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     ("ffe_plan_destroy", None, [_VP]),
+    ("ffe_probe_peaks", ctypes.c_int, [_VP]),
 ]
+
+
+class ffe_peaks(ctypes.Structure):
+    _fields_ = [("ex2", ctypes.c_double), ("lg2", ctypes.c_double), ("rsqrt", ctypes.c_double),
+                ("rcp", ctypes.c_double), ("fma32", ctypes.c_double), ("fma64", ctypes.c_double),
+                ("n_sm", ctypes.c_int32), ("sm_khz_max", ctypes.c_int32)]
+
+
+def ffe_probe_peaks() -> dict:
+    p = ffe_peaks()
+    st = lib().ffe_probe_peaks(ctypes.byref(p))
+    if st != FFE_OK:
+        raise FFEError(st, lib().ffe_status_string(st).decode())
+    return {name: getattr(p, name) for name, _ in ffe_peaks._fields_}
 
 
 def lib():
