@@ -92,7 +92,8 @@ typedef enum {
 /* One Delta minimisation (the inner loop of Alg. 1). */
 typedef struct {
   int32_t N;         /* as in ffe_point                                        */
-  int32_t n;         /* GRID: points (1..65536); GOLDEN: reductions (1..200)   */
+  int32_t n;         /* GRID: points (1..65536); GOLDEN: reductions (1..200),
+                        the same for every param of one call               */
   double qx, qy, h, T;
   double lo, hi;     /* Delta range, lo <= hi                                  */
 } ffe_param;

@@ -179,7 +179,8 @@ bool batches_share_T(const ffe_plan* p) {
 double plan_k_evals(const ffe_plan* p) {
   double s = 0.0;
   for (const GroupDesc& g : p->groups) s += (double)g.N * (double)g.N * (double)g.n_out;
-  return s;
+  // a golden-section execution evaluates every line 3 + steps times
+  return p->golden_steps > 0 ? s * (3.0 + p->golden_steps) : s;
 }
 
 // Allocate device buffers for the host tables already in *p.
@@ -233,6 +234,7 @@ ffe_status plan_alloc(ffe_context* ctx, ffe_plan* p) {
   ALLOC(d_lres, p->lines.size());
   ALLOC(d_labels, std::max<size_t>(1, p->n_pts));
   ALLOC(d_bestq, std::max<size_t>(1, p->n_pts));
+  ALLOC(d_golden, p->golden0.size());
 #undef ALLOC
   cudaStream_t s = p->stream;
   FFE_CU(cudaMemsetAsync(p->d_Mcnt, 0, sizeof(int32_t) * std::max(1, p->n_mcounters), s), "memset");
@@ -254,8 +256,10 @@ ffe_status plan_upload_params(ffe_context* ctx, ffe_plan* p, cudaStream_t s) {
   if ((st = upload(ctx, p->d_hlist, p->hlist, s)) != FFE_OK) return st;
   if ((st = upload(ctx, p->d_groups, p->groups, s)) != FFE_OK) return st;
   if ((st = upload(ctx, p->d_qzero, p->q_is_zero, s)) != FFE_OK) return st;
+  if ((st = upload(ctx, p->d_golden, p->golden0, s)) != FFE_OK) return st;
   p->h2d_bytes = p->delta.size() * sizeof(double) + p->ht.size() * sizeof(HT) +
-                 p->hlist.size() * sizeof(double) + p->groups.size() * sizeof(GroupDesc);
+                 p->hlist.size() * sizeof(double) + p->groups.size() * sizeof(GroupDesc) +
+                 p->golden0.size() * sizeof(GoldenState);
   return FFE_OK;
 }
 
@@ -310,6 +314,7 @@ static RescoreArgs make_rescore_args(ffe_plan* p, int queue_slot, int count_slot
   r.ebound = p->d_eb;
   r.lines = p->d_lres;
   r.rescored = p->d_rescored;
+  r.golden = p->d_golden;
   r.cap = p->cap;
   r.pad = 0;
   return r;
@@ -318,6 +323,7 @@ static RescoreArgs make_rescore_args(ffe_plan* p, int queue_slot, int count_slot
 // The whole device-side sequence of one execution, on stream s.
 // counters: [0] k-sum queue, [1] rescore queue A, [2] rescore queue B,
 //           [3] requests of the Delta search, [4] requests of the labels,
+//           [5] requests of a golden step, [6] its rescore queue,
 //           [7] status word.
 ffe_status plan_enqueue(ffe_context* ctx, ffe_plan* p, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
                         unsigned ev_flags) {
@@ -333,16 +339,57 @@ ffe_status plan_enqueue(ffe_context* ctx, ffe_plan* p, cudaStream_t s, cudaEvent
          "tables");
   ++launches;
   FFE_CU(normal_launch(ctx->mp, p->d_groups, p->d_mitems, (int)p->mitems.size(), p->d_hlist, p->d_tabd,
-                       p->d_Mpart, p->d_Mcnt, p->d_M, s, true),
+                       p->d_Mpart, p->d_Mcnt, p->d_M, s),
          "normal");
   ++launches;
-  if (ev0) FFE_CU(cudaEventRecordWithFlags(ev0, s, ev_flags), "event");
   KsumArgs ka = make_ksum_args(p);
-  FFE_CU(ksum_launch(p->prec, p->variant, p->kpt, ka, p->grid, p->block, s), "ksum");
-  ++launches;
-  if (ev1) FFE_CU(cudaEventRecordWithFlags(ev1, s, ev_flags), "event");
+  const int n_lines = (int)p->lines.size();
+  if (p->golden_steps > 0) {
+    // lockstep golden-section: one k-sum launch per evaluation of every line
+    auto golden = [&](int mode) -> ffe_status {
+      FFE_CU(golden_launch(mode, p->d_lines, n_lines, p->d_golden, p->d_omega, p->d_eb, p->d_delta, p->d_d2f,
+                           p->d_req, p->d_counters + 5, p->cap, p->d_lres, s),
+             "golden");
+      ++launches;
+      return FFE_OK;
+    };
+    auto ksum = [&]() -> ffe_status {
+      FFE_CU(cudaMemsetAsync(p->d_counters + 0, 0, sizeof(int32_t), s), "memset");
+      FFE_CU(ksum_launch(p->prec, p->variant, p->kpt, ka, p->grid, p->block, s), "ksum");
+      ++launches;
+      return FFE_OK;
+    };
+    ffe_status st;
+    if ((st = golden(kGoldenInit)) != FFE_OK) return st;
+    if (ev0) FFE_CU(cudaEventRecordWithFlags(ev0, s, ev_flags), "event");
+    const int first[3] = {kGoldenLo, kGoldenX1, kGoldenX2};
+    for (int i = 0; i < 3; ++i) {
+      if ((st = ksum()) != FFE_OK) return st;
+      if ((st = golden(first[i])) != FFE_OK) return st;
+    }
+    for (int step = 0; step < p->golden_steps; ++step) {
+      FFE_CU(cudaMemsetAsync(p->d_counters + 5, 0, 2 * sizeof(int32_t), s), "memset");
+      if ((st = golden(kGoldenMark)) != FFE_OK) return st;
+      FFE_CU(rescore_launch(make_rescore_args(p, 6, 5), p->rescore_grid, s), "rescore golden");
+      ++launches;
+      if ((st = golden(kGoldenDecide)) != FFE_OK) return st;
+      if ((st = ksum()) != FFE_OK) return st;
+      if ((st = golden(kGoldenRecord)) != FFE_OK) return st;
+    }
+    if (ev1) FFE_CU(cudaEventRecordWithFlags(ev1, s, ev_flags), "event");
+    FFE_CU(cudaMemsetAsync(p->d_counters + 5, 0, 2 * sizeof(int32_t), s), "memset");
+    if ((st = golden(kGoldenMarkFinal)) != FFE_OK) return st;
+    FFE_CU(rescore_launch(make_rescore_args(p, 6, 5), p->rescore_grid, s), "rescore golden");
+    ++launches;
+    if ((st = golden(kGoldenFinish)) != FFE_OK) return st;
+  } else {
+    if (ev0) FFE_CU(cudaEventRecordWithFlags(ev0, s, ev_flags), "event");
+    FFE_CU(ksum_launch(p->prec, p->variant, p->kpt, ka, p->grid, p->block, s), "ksum");
+    ++launches;
+    if (ev1) FFE_CU(cudaEventRecordWithFlags(ev1, s, ev_flags), "event");
+  }
   if (!p->lines.empty()) {
-    const int n_lines = (int)p->lines.size();
+    if (p->golden_steps == 0) {
     FFE_CU(argmin_launch(p->d_lines, n_lines, p->d_omega, p->d_eb, p->d_delta, p->d_rescored, 0, p->d_req,
                          p->d_counters + 3, p->cap, p->d_lres, s),
            "argmin A");
@@ -351,6 +398,7 @@ ffe_status plan_enqueue(ffe_context* ctx, ffe_plan* p, cudaStream_t s, cudaEvent
                          p->d_counters + 3, p->cap, p->d_lres, s),
            "argmin B");
     launches += 3;
+    }
     if (p->n_q > 0) {
       // the request slots are reused once pass A's requests are done (stream order)
       FFE_CU(labels_launch(p->d_lres, p->n_q, p->n_pts, p->d_qzero, p->d_lines, p->d_delta, 0, p->d_req,
@@ -496,6 +544,8 @@ static ffe_status check_scan(ffe_context* ctx, const ffe_scan* sc) {
     return set_err(ctx, "unknown search kind %d", sc->search), FFE_EINVAL;
   if (sc->search == FFE_SEARCH_GRID && (sc->n < 1 || sc->n > 65536))
     return set_err(ctx, "grid points n=%d out of [1, 65536]", sc->n), FFE_EINVAL;
+  if (sc->search == FFE_SEARCH_GOLDEN && (sc->n < 1 || sc->n > 200))
+    return set_err(ctx, "golden reductions n=%d out of [1, 200]", sc->n), FFE_EINVAL;
   if (!finite(sc->lo) || !finite(sc->hi) || sc->lo > sc->hi || sc->lo != 0.0)
     return set_err(ctx, "Delta range must be finite with lo = 0 <= hi"), FFE_EINVAL;
   bool has_zero = false;
@@ -566,6 +616,74 @@ static void fill_scan_grid(ffe_plan* p, const ffe_scan* sc) {
     p->groups.push_back(g);
   }
   p->n_out = out;
+}
+
+// Golden scan: one LIST group per q whose outputs are the (h, T) points; each
+// output carries its own Delta, rewritten on the device after every step.
+static void fill_scan_golden(ffe_plan* p, const ffe_scan* sc) {
+  const int n_pts = sc->n_h * sc->n_T;
+  p->layout = kLayoutList;
+  p->n_q = sc->n_q;
+  p->n_pts = n_pts;
+  p->golden_steps = sc->n;
+  p->groups.clear();
+  p->delta.clear();
+  p->ht.clear();
+  p->hlist.clear();
+  p->lines.clear();
+  p->golden0.clear();
+  p->q_is_zero.assign(sc->n_q, 0);
+  int64_t out = 0;
+  for (int q = 0; q < sc->n_q; ++q) {
+    GroupDesc g;
+    std::memset(&g, 0, sizeof g);
+    g.N = sc->N;
+    g.layout = kLayoutList;
+    g.n_out = n_pts;
+    g.n_delta = n_pts;
+    g.n_ht = n_pts;
+    g.n_hblk = 1;
+    g.n_batches = (n_pts + 31) / 32;
+    g.n_h = sc->n_h;
+    g.out_off = out;
+    g.delta_off = (int64_t)p->delta.size();
+    g.ht_off = (int64_t)p->ht.size();
+    g.tab_off = (int64_t)q * 2 * sc->N;
+    g.h_off = (int64_t)p->hlist.size();
+    g.qx = sc->qx[q];
+    g.qy = sc->qy[q];
+    p->q_is_zero[q] = (sc->qx[q] == 0.0 && sc->qy[q] == 0.0) ? 1 : 0;
+    for (int ih = 0; ih < sc->n_h; ++ih)
+      for (int it = 0; it < sc->n_T; ++it) p->ht.push_back(HT{sc->h[ih], sc->T[it], ih, 0});
+    p->hlist.insert(p->hlist.end(), sc->h, sc->h + sc->n_h);
+    for (int pt = 0; pt < n_pts; ++pt) {
+      p->delta.push_back(sc->lo);
+      Line L;
+      L.out0 = out + pt;
+      L.stride = 1;
+      L.count = 1;
+      L.group = q;
+      L.pad = 0;
+      L.delta0 = g.delta_off + pt;
+      L.ht = g.ht_off + pt;
+      p->lines.push_back(L);
+      GoldenState gs;
+      std::memset(&gs, 0, sizeof gs);
+      gs.lo = sc->lo;
+      gs.hi = sc->hi;
+      p->golden0.push_back(gs);
+    }
+    out += g.n_out;
+    p->groups.push_back(g);
+  }
+  p->n_out = out;
+}
+
+void fill_scan(ffe_plan* p, const ffe_scan* sc) {
+  if (sc->search == FFE_SEARCH_GOLDEN)
+    fill_scan_golden(p, sc);
+  else
+    fill_scan_grid(p, sc);
 }
 
 static ffe_status fetch_scan(ffe_context* ctx, ffe_plan* p, ffe_result* per_point, int8_t* labels,
@@ -664,9 +782,8 @@ ffe_status ffe_plan_phase_scan(ffe_context* ctx, const ffe_scan* scan, void* str
   *out = nullptr;
   ffe_status st = check_scan(ctx, scan);
   if (st != FFE_OK) return st;
-  if (scan->search != FFE_SEARCH_GRID) return set_err(ctx, "golden plans: see ffe_phase_scan"), FFE_EUNSUPPORTED;
-  ffe_plan* p = plan_new(ctx, kPlanScanGrid);
-  fill_scan_grid(p, scan);
+  ffe_plan* p = plan_new(ctx, scan->search == FFE_SEARCH_GRID ? kPlanScanGrid : kPlanScanGolden);
+  fill_scan(p, scan);
   st = plan_configure(ctx, p);
   if (st == FFE_OK) st = plan_finish(ctx, p, true);
   if (st != FFE_OK) {
@@ -735,17 +852,17 @@ ffe_status ffe_phase_scan(ffe_context* ctx, const ffe_scan* scan, ffe_result* pe
   if (!ctx) return FFE_EINVAL;
   ffe_status st = check_scan(ctx, scan);
   if (st != FFE_OK) return st;
-  if (scan->search == FFE_SEARCH_GOLDEN) return golden_scan(ctx, scan, per_point, labels, best_q, stream);
   cudaStream_t s = (cudaStream_t)stream;
   char key[160];
-  snprintf(key, sizeof key, "scan:%d:%d:%d:%d:%d:%d", ctx->model.prec, scan->N, scan->n_q, scan->n_h, scan->n_T,
-           scan->n);
+  snprintf(key, sizeof key, "scan:%d:%d:%d:%d:%d:%d:%d", ctx->model.prec, scan->search, scan->N, scan->n_q,
+           scan->n_h, scan->n_T, scan->n);
+  const int kind = scan->search == FFE_SEARCH_GRID ? kPlanScanGrid : kPlanScanGolden;
   ffe_plan* p = nullptr;
   auto it = ctx->cache.find(key);
   if (it != ctx->cache.end()) {
     p = it->second;
-    fill_scan_grid(p, scan);
-    const bool ut = ctx->model.prec == FFE_FP32C && batches_share_T(p);
+    fill_scan(p, scan);
+    const bool ut = ctx->model.prec == FFE_FP32C && kind == kPlanScanGrid && batches_share_T(p);
     if (ut != (p->variant == kLayoutProductUT)) {  // the kernel variant no longer fits: rebuild
       plan_free(p);
       ctx->cache.erase(it);
@@ -755,8 +872,8 @@ ffe_status ffe_phase_scan(ffe_context* ctx, const ffe_scan* scan, ffe_result* pe
     }
   }
   if (!p) {
-    p = plan_new(ctx, kPlanScanGrid);
-    fill_scan_grid(p, scan);
+    p = plan_new(ctx, kind);
+    fill_scan(p, scan);
     st = plan_configure(ctx, p);
     if (st == FFE_OK) st = plan_finish(ctx, p, true);
     if (st != FFE_OK) {

@@ -1,0 +1,180 @@
+// golden.cu -- lockstep golden-section search over Delta for every line
+// (one (q, h, T) point each) of a plan, on the device.
+//
+// Alg. 1 scans Delta from 0 to Delta_max; with a smooth Omega(Delta) the
+// minimum can be bracketed instead.  Every line keeps a bracket [a, b] with
+// interior points x1 = a + (1-phi)(b-a), x2 = a + phi(b-a), phi = (sqrt5-1)/2;
+// it keeps [a, x2] when Omega(x1) <= Omega(x2), else [x1, b], and evaluates
+// one new interior point per reduction.  Delta = lo is evaluated too (it is
+// the normal state).  The result is the lowest Omega seen, ties to the
+// smaller Delta.  All lines advance together: one k-sum launch evaluates the
+// pending Delta of every line.  While the bracket is still wide (more than
+// 1e-3 of the range), a decision whose two FP32 values lie within their
+// error bounds is taken on FP64 re-evaluations instead.
+#include "ffe_internal.cuh"
+#include "ksum.cuh"
+
+namespace ffe {
+
+constexpr double kPhi = 0.61803398874989484820;
+constexpr double kWideRel = 1e-3;
+
+__device__ __forceinline__ void golden_take(GoldenState& s, double x, double f, double eb) {
+  if (f < s.fb || (f == s.fb && x < s.xb)) {
+    s.xb = x;
+    s.fb = f;
+    s.ebb = eb;
+  }
+}
+
+__device__ __forceinline__ void set_delta(double* delta, float* d2f, int64_t e, double x) {
+  delta[e] = x;
+  d2f[e] = (float)(x * x);
+}
+
+__global__ void golden_kernel(int mode, const Line* __restrict__ lines, int n_lines, GoldenState* gs,
+                              const double* __restrict__ omega, const double* __restrict__ ebound, double* delta,
+                              float* d2f, Rescore* req, int32_t* n_req, int32_t cap, LineResult* res) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n_lines) return;
+  const Line L = lines[l];
+  const int64_t o = L.out0;
+  const int64_t e = L.delta0;
+  GoldenState s = gs[l];
+  switch (mode) {
+    case kGoldenInit:
+      s.a = s.lo;
+      s.b = s.hi;
+      s.x1 = s.a + (1.0 - kPhi) * (s.b - s.a);
+      s.x2 = s.a + kPhi * (s.b - s.a);
+      s.side = 0;
+      set_delta(delta, d2f, e, s.lo);
+      break;
+    case kGoldenLo:
+      s.flo = omega[o];
+      s.eblo = ebound[o];
+      s.xb = s.lo;
+      s.fb = s.flo;
+      s.ebb = s.eblo;
+      set_delta(delta, d2f, e, s.x1);
+      break;
+    case kGoldenX1:
+      s.f1 = omega[o];
+      s.eb1 = ebound[o];
+      golden_take(s, s.x1, s.f1, s.eb1);
+      set_delta(delta, d2f, e, s.x2);
+      break;
+    case kGoldenX2:
+      s.f2 = omega[o];
+      s.eb2 = ebound[o];
+      golden_take(s, s.x2, s.f2, s.eb2);
+      break;
+    case kGoldenMark:
+      if (fabs(s.f1 - s.f2) <= s.eb1 + s.eb2 && (s.b - s.a) > kWideRel * (s.hi - s.lo)) {
+        Rescore r;
+        r.group = L.group;
+        r.dst = l;
+        r.ht = L.ht;
+        if (s.eb1 > 0.0) {
+          r.kind = 3;
+          r.delta = s.x1;
+          const int pos = atomicAdd(n_req, 1);
+          if (pos < cap) req[pos] = r;
+        }
+        if (s.eb2 > 0.0) {
+          r.kind = 4;
+          r.delta = s.x2;
+          const int pos = atomicAdd(n_req, 1);
+          if (pos < cap) req[pos] = r;
+        }
+      }
+      return;  // state unchanged (the FP64 values are written by the re-evaluation)
+    case kGoldenDecide:
+      if (s.f1 <= s.f2) {  // keep [a, x2]
+        s.b = s.x2;
+        s.x2 = s.x1;
+        s.f2 = s.f1;
+        s.eb2 = s.eb1;
+        s.x1 = s.a + (1.0 - kPhi) * (s.b - s.a);
+        s.side = 0;
+        set_delta(delta, d2f, e, s.x1);
+      } else {  // keep [x1, b]
+        s.a = s.x1;
+        s.x1 = s.x2;
+        s.f1 = s.f2;
+        s.eb1 = s.eb2;
+        s.x2 = s.a + kPhi * (s.b - s.a);
+        s.side = 1;
+        set_delta(delta, d2f, e, s.x2);
+      }
+      break;
+    case kGoldenRecord:
+      if (s.side == 0) {
+        s.f1 = omega[o];
+        s.eb1 = ebound[o];
+        golden_take(s, s.x1, s.f1, s.eb1);
+      } else {
+        s.f2 = omega[o];
+        s.eb2 = ebound[o];
+        golden_take(s, s.x2, s.f2, s.eb2);
+      }
+      break;
+    case kGoldenMarkFinal:
+      // the best point against Delta = lo: the normal state wins exact ties
+      if (s.xb != s.lo && fabs(s.fb - s.flo) <= s.ebb + s.eblo) {
+        Rescore r;
+        r.group = L.group;
+        r.dst = l;
+        r.ht = L.ht;
+        if (s.ebb > 0.0) {
+          r.kind = 5;
+          r.delta = s.xb;
+          const int pos = atomicAdd(n_req, 1);
+          if (pos < cap) req[pos] = r;
+        }
+        if (s.eblo > 0.0) {
+          r.kind = 6;
+          r.delta = s.lo;
+          const int pos = atomicAdd(n_req, 1);
+          if (pos < cap) req[pos] = r;
+        }
+      }
+      return;
+    case kGoldenFinish: {
+      if (s.xb != s.lo && s.flo <= s.fb) {
+        s.xb = s.lo;
+        s.fb = s.flo;
+        s.ebb = s.eblo;
+      }
+      LineResult r;
+      r.delta_star = s.xb;
+      r.omega_star = s.fb;
+      r.eb_star = s.ebb;
+      r.omega_lo = s.flo;
+      r.eb_lo = s.eblo;
+      r.delta_lo = s.lo;
+      r.out_star = o;
+      r.idx_star = -1;
+      int f = 0;
+      if (s.xb == s.lo) f |= kFlagLower;
+      if (s.b == s.hi) f |= kFlagEdge;
+      r.flags = f;
+      res[l] = r;
+      return;
+    }
+    default:
+      return;
+  }
+  gs[l] = s;
+}
+
+cudaError_t golden_launch(int mode, const Line* lines, int n_lines, GoldenState* gs, const double* omega,
+                          const double* ebound, double* delta, float* d2f, Rescore* req, int32_t* n_req,
+                          int32_t cap, LineResult* res, cudaStream_t s) {
+  if (n_lines <= 0) return cudaSuccess;
+  golden_kernel<<<(n_lines + 127) / 128, 128, 0, s>>>(mode, lines, n_lines, gs, omega, ebound, delta, d2f, req,
+                                                       n_req, cap, res);
+  return cudaGetLastError();
+}
+
+}  // namespace ffe

@@ -62,7 +62,7 @@ cudaError_t prep_params_launch(const double* delta, int64_t n_delta, float* d2f,
                                int64_t n_ht, HTf* htf, HTd* htd, cudaStream_t s);
 cudaError_t normal_launch(const ModelParams& m, const GroupDesc* groups, const MItem* items,
                           int n_items, const double* hlist, const TabRowD* tabd, double* partials,
-                          int32_t* counters, double* M, cudaStream_t s, bool f64_terms);
+                          int32_t* counters, double* M, cudaStream_t s);
 
 // ---- search, rescoring and labels (search.cu)
 struct Line {          // one Delta search: outputs out0 + i*stride, i < count
@@ -78,6 +78,7 @@ struct Line {          // one Delta search: outputs out0 + i*stride, i < count
 struct LineResult {
   double delta_star, omega_star, eb_star;
   double omega_lo, eb_lo;
+  double delta_lo;     // the Delta of omega_lo (the lower end of the range)
   int64_t out_star;
   int32_t idx_star;
   int32_t flags;
@@ -89,6 +90,19 @@ struct Rescore {       // FP64 re-evaluation request
   int64_t dst;
   int64_t ht;
   double delta;
+};
+
+// Golden-section search state of one line (one (q, h, T) point).
+struct GoldenState {
+  double a, b;          // current bracket
+  double x1, x2;        // interior points
+  double f1, f2;        // Omega at x1, x2
+  double eb1, eb2;      // their FP32 error bounds (0 once FP64)
+  double xb, fb, ebb;   // lowest Omega seen so far (ties -> smaller Delta)
+  double flo, eblo;     // Omega at Delta = lo
+  double lo, hi;        // the search range
+  int32_t side;         // 0: the pending evaluation is x1, 1: x2
+  int32_t pad;
 };
 
 struct RescoreArgs {
@@ -109,9 +123,16 @@ struct RescoreArgs {
   double* ebound;
   LineResult* lines;
   int32_t* rescored;    // per output flag (kind 0)
+  GoldenState* golden;  // kinds 3 (x1) and 4 (x2)
   int32_t cap;
   int32_t pad;
 };
+
+enum { kGoldenInit = 0, kGoldenLo, kGoldenX1, kGoldenX2, kGoldenMark, kGoldenDecide, kGoldenRecord,
+       kGoldenMarkFinal, kGoldenFinish };
+cudaError_t golden_launch(int mode, const Line* lines, int n_lines, GoldenState* gs, const double* omega,
+                          const double* ebound, double* delta, float* d2f, Rescore* req, int32_t* n_req,
+                          int32_t cap, LineResult* res, cudaStream_t s);
 
 cudaError_t argmin_launch(const Line* lines, int n_lines, const double* omega, const double* ebound,
                           const double* delta, const int32_t* rescored, int mode, Rescore* req,

@@ -105,7 +105,8 @@ struct ffe_plan {
   ffe::LineResult* d_lres = nullptr;
   int8_t* d_labels = nullptr;
   int32_t* d_bestq = nullptr;
-  void* d_golden = nullptr;  // golden-section state (golden.cu)
+  ffe::GoldenState* d_golden = nullptr;   // golden-section state per line (golden.cu)
+  std::vector<ffe::GoldenState> golden0;  // its initial value (search range per line)
   // execution
   cudaStream_t stream = nullptr;
   cudaGraph_t graph = nullptr;
@@ -139,8 +140,5 @@ bool batches_share_T(const ffe_plan* p);
 
 Tuning tuning_for(ffe_context* ctx, const ffe_plan* p);
 void tuning_load(ffe_context* ctx);
-
-ffe_status golden_scan(ffe_context* ctx, const ffe_scan* scan, ffe_result* per_point, int8_t* labels,
-                       int32_t* best_q, void* stream);
 
 }  // namespace ffe

@@ -120,6 +120,79 @@ void fill_min_grid(ffe_plan* p, const ffe_param* ps, int64_t n) {
   p->n_out = out;
 }
 
+// Golden-section searches: parameter points sharing (N, Q) form one LIST
+// group (their (h, T) and pending Delta are the outputs); one line per point,
+// in input order.
+void fill_min_golden(ffe_plan* p, const ffe_param* ps, int64_t n) {
+  p->layout = kLayoutList;
+  int steps = 0;
+  for (int64_t i = 0; i < n; ++i) steps = std::max(steps, ps[i].n);
+  p->golden_steps = steps;
+  std::map<std::tuple<int32_t, double, double>, std::vector<int64_t>> by_key;
+  std::vector<std::tuple<int32_t, double, double>> keys;
+  for (int64_t i = 0; i < n; ++i) {
+    auto k = std::make_tuple(ps[i].N, ps[i].qx, ps[i].qy);
+    if (by_key.find(k) == by_key.end()) keys.push_back(k);
+    by_key[k].push_back(i);
+  }
+  p->lines.resize(n);
+  p->golden0.resize(n);
+  int64_t out = 0, tab = 0;
+  for (size_t gi = 0; gi < keys.size(); ++gi) {
+    const std::vector<int64_t>& idx = by_key[keys[gi]];
+    GroupDesc g;
+    std::memset(&g, 0, sizeof g);
+    g.N = std::get<0>(keys[gi]);
+    g.layout = kLayoutList;
+    g.n_out = (int32_t)idx.size();
+    g.n_delta = g.n_out;
+    g.n_ht = g.n_out;
+    g.n_hblk = 1;
+    g.n_batches = (g.n_out + 31) / 32;
+    g.out_off = out;
+    g.delta_off = (int64_t)p->delta.size();
+    g.ht_off = (int64_t)p->ht.size();
+    g.tab_off = tab;
+    g.h_off = (int64_t)p->hlist.size();
+    g.qx = std::get<1>(keys[gi]);
+    g.qy = std::get<2>(keys[gi]);
+    std::map<double, int> hmap;
+    for (size_t j = 0; j < idx.size(); ++j) {
+      const ffe_param& q = ps[idx[j]];
+      auto it = hmap.find(q.h);
+      int hi;
+      if (it == hmap.end()) {
+        hi = (int)hmap.size();
+        hmap[q.h] = hi;
+        p->hlist.push_back(q.h);
+      } else {
+        hi = it->second;
+      }
+      p->delta.push_back(q.lo);
+      p->ht.push_back(HT{q.h, q.T, hi, 0});
+      Line L;
+      L.out0 = out + (int64_t)j;
+      L.stride = 1;
+      L.count = 1;
+      L.group = (int32_t)gi;
+      L.pad = 0;
+      L.delta0 = g.delta_off + (int64_t)j;
+      L.ht = g.ht_off + (int64_t)j;
+      p->lines[idx[j]] = L;
+      GoldenState gs;
+      std::memset(&gs, 0, sizeof gs);
+      gs.lo = q.lo;
+      gs.hi = q.hi;
+      p->golden0[idx[j]] = gs;
+    }
+    g.n_h = (int32_t)hmap.size();
+    p->groups.push_back(g);
+    out += g.n_out;
+    tab += 2 * (int64_t)g.N;
+  }
+  p->n_out = out;
+}
+
 }  // namespace
 
 namespace ffe {
@@ -148,11 +221,6 @@ Tuning tuning_for(ffe_context* ctx, const ffe_plan* p) {
 }
 
 void tuning_load(ffe_context*) {}
-
-ffe_status golden_scan(ffe_context* ctx, const ffe_scan*, ffe_result*, int8_t*, int32_t*, void*) {
-  set_err(ctx, "golden-section scans are not built yet");
-  return FFE_EUNSUPPORTED;
-}
 
 }  // namespace ffe
 
@@ -209,13 +277,19 @@ ffe_status ffe_minimize(ffe_context* ctx, int32_t search, const ffe_param* ps, i
       return set_err(ctx, "param %lld: grid points n=%d out of [1, 65536]", (long long)i, q.n), FFE_EINVAL;
     if (search == FFE_SEARCH_GOLDEN && (q.n < 1 || q.n > 200))
       return set_err(ctx, "param %lld: golden reductions n=%d out of [1, 200]", (long long)i, q.n), FFE_EINVAL;
+    if (search == FFE_SEARCH_GOLDEN && q.n != ps[0].n)
+      return set_err(ctx, "param %lld: golden searches of one call share n", (long long)i), FFE_EINVAL;
     total += q.n;
   }
   if (total > ((int64_t)1 << 31)) return set_err(ctx, "too many outputs"), FFE_EINVAL;
-  if (search == FFE_SEARCH_GOLDEN) return set_err(ctx, "golden-section search is not built yet"), FFE_EUNSUPPORTED;
+  if (search == FFE_SEARCH_GOLDEN && (omega_grid || err_grid))
+    return set_err(ctx, "omega_grid/err_grid apply to grid searches only"), FFE_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  ffe_plan* p = plan_new(ctx, kPlanMinGrid);
-  fill_min_grid(p, ps, n);
+  ffe_plan* p = plan_new(ctx, search == FFE_SEARCH_GRID ? kPlanMinGrid : kPlanMinGolden);
+  if (search == FFE_SEARCH_GRID)
+    fill_min_grid(p, ps, n);
+  else
+    fill_min_golden(p, ps, n);
   ffe_status st = plan_configure(ctx, p);
   if (st == FFE_OK) st = plan_finish(ctx, p, false);
   if (st == FFE_OK) st = plan_run(ctx, p, s);

@@ -97,6 +97,7 @@ __global__ void argmin_kernel(const Line* __restrict__ lines, int n_lines, const
     r.eb_star = eb[out_b];
     r.omega_lo = omega[L.out0];
     r.eb_lo = eb[L.out0];
+    r.delta_lo = delta[L.delta0];
     int f = 0;
     if (rescored[out_b]) f |= kFlagRescored;
     if (bi == L.count - 1) f |= kFlagEdge;
@@ -183,6 +184,18 @@ __global__ void __launch_bounds__(256) rescore_kernel(const RescoreArgs a) {
         a.omega[q.dst] = om;
         a.ebound[q.dst] = 0.0;
         a.rescored[q.dst] = 1;
+      } else if (q.kind == 3) {
+        a.golden[q.dst].f1 = om;
+        a.golden[q.dst].eb1 = 0.0;
+      } else if (q.kind == 4) {
+        a.golden[q.dst].f2 = om;
+        a.golden[q.dst].eb2 = 0.0;
+      } else if (q.kind == 5) {
+        a.golden[q.dst].fb = om;
+        a.golden[q.dst].ebb = 0.0;
+      } else if (q.kind == 6) {
+        a.golden[q.dst].flo = om;
+        a.golden[q.dst].eblo = 0.0;
       } else {
         // kinds 1 (minimum) and 2 (Delta = lo) name the same value when the
         // minimum is the Delta = lo point: keep both copies identical
@@ -278,7 +291,7 @@ __global__ void labels_kernel(LineResult* res, int n_q, int n_pts, const int32_t
         rq.kind = 2;
         rq.dst = l;
         rq.ht = L.ht;
-        rq.delta = delta[L.delta0];
+        rq.delta = r.delta_lo;
         push_request(req, n_req, cap, rq);
       }
     }

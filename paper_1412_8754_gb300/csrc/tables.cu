@@ -64,9 +64,7 @@ cudaError_t prep_params_launch(const double* delta, int64_t n_delta, float* d2f,
 }
 
 // M(h) = sum_k sum_eps [min(E_eps(k+Q/2) - mu - h, 0) + min(E_eps(-k+Q/2) - mu + h, 0)]
-// for up to 32 h values per item, over the item's k range.  Band energies in
-// FP64; each term in FP64 (F64TERMS) or in FP32 with FP64 accumulation.
-template <bool F64TERMS>
+// for up to 32 h values per item, over the item's k range, in FP64.
 __global__ void __launch_bounds__(256) normal_kernel(const ModelParams m,
                                                      const GroupDesc* __restrict__ groups,
                                                      const MItem* __restrict__ items,
@@ -81,7 +79,11 @@ __global__ void __launch_bounds__(256) normal_kernel(const ModelParams m,
   const int h0 = it.hb * 32;
   const int nh = min(32, g.n_h - h0);
   __shared__ double hv[32];
-  if (threadIdx.x < 32) hv[threadIdx.x] = ((int)threadIdx.x < nh) ? hlist[g.h_off + h0 + threadIdx.x] : 0.0;
+  __shared__ float hvf[32];
+  if (threadIdx.x < 32) {
+    hv[threadIdx.x] = ((int)threadIdx.x < nh) ? hlist[g.h_off + h0 + threadIdx.x] : 0.0;
+    hvf[threadIdx.x] = (float)hv[threadIdx.x];
+  }
   __syncthreads();
   double acc[32];
 #pragma unroll
@@ -98,24 +100,21 @@ __global__ void __launch_bounds__(256) normal_kernel(const ModelParams m,
     uhi -= m.mu;
     dlo -= m.mu;
     dhi -= m.mu;
-    if (F64TERMS) {
+    // min(u - h, 0) + min(d + h, 0) = min(u, h) + min(d, -h): each min selects
+    // one of two FP64 values; the choice is made on FP32 copies (ALU), only
+    // the sum uses the FP64 pipe.  Where the FP32 copies tie, either value is
+    // within one FP32 ulp of the other.
+    const float fulo = (float)ulo, fuhi = (float)uhi, fdlo = (float)dlo, fdhi = (float)dhi;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        if (j < nh) {
-          const double h = hv[j];
-          acc[j] += (fmin(ulo - h, 0.0) + fmin(uhi - h, 0.0)) + (fmin(dlo + h, 0.0) + fmin(dhi + h, 0.0));
-        }
-      }
-    } else {
-      const float fulo = (float)ulo, fuhi = (float)uhi, fdlo = (float)dlo, fdhi = (float)dhi;
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        if (j < nh) {
-          const float h = (float)hv[j];
-          const float t = (fminf(fulo - h, 0.0f) + fminf(fuhi - h, 0.0f)) +
-                          (fminf(fdlo + h, 0.0f) + fminf(fdhi + h, 0.0f));
-          acc[j] += (double)t;
-        }
+    for (int j = 0; j < 32; ++j) {
+      if (j < nh) {
+        const double h = hv[j];
+        const float hf = hvf[j];
+        const double t0 = fulo < hf ? ulo : h;
+        const double t1 = fuhi < hf ? uhi : h;
+        const double t2 = fdlo < -hf ? dlo : -h;
+        const double t3 = fdhi < -hf ? dhi : -h;
+        acc[j] += (t0 + t1) + (t2 + t3);
       }
     }
   }
@@ -145,12 +144,9 @@ __global__ void __launch_bounds__(256) normal_kernel(const ModelParams m,
 
 cudaError_t normal_launch(const ModelParams& m, const GroupDesc* groups, const MItem* items,
                           int n_items, const double* hlist, const TabRowD* tabd, double* partials,
-                          int32_t* counters, double* M, cudaStream_t s, bool f64_terms) {
+                          int32_t* counters, double* M, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
-  if (f64_terms)
-    normal_kernel<true><<<n_items, 256, 0, s>>>(m, groups, items, hlist, tabd, partials, counters, M);
-  else
-    normal_kernel<false><<<n_items, 256, 0, s>>>(m, groups, items, hlist, tabd, partials, counters, M);
+  normal_kernel<<<n_items, 256, 0, s>>>(m, groups, items, hlist, tabd, partials, counters, M);
   return cudaGetLastError();
 }
 

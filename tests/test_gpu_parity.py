@@ -178,3 +178,87 @@ def test_invalid_arguments_are_rejected_before_launch():
         # the context stays usable
         ok = ctx.omega(ffe.points(16, 0, 0, 0, 0.01, 0.1))
         assert np.isfinite(ok[0])
+
+
+def oracle_golden(m, N, qx, qy, h, T, lo, hi, steps):
+    """Lockstep golden-section of the oracle over many points (broadcast arrays)."""
+    qx, qy, h, T = np.broadcast_arrays(np.asarray(qx, float), np.asarray(qy, float),
+                                       np.asarray(h, float), np.asarray(T, float))
+
+    def ev(d):
+        om, _, _ = oracle.omega_batch(m, N, qx.ravel(), qy.ravel(), h.ravel(), T.ravel(), d)
+        return om
+
+    n = qx.size
+    return search.golden_section_batch(ev, np.full(n, lo), np.full(n, hi), steps)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_golden_minimize_vs_oracle(prec):
+    N, U, steps = 32, 4.0, 24
+    rng = np.random.default_rng(17)
+    n = 40
+    qx = rng.uniform(0, 0.5, n)
+    qx[:4] = 0.0
+    h = rng.uniform(0, 0.12, n)
+    T = rng.uniform(0.002, 0.03, n)
+    m = oracle.make_model(U=U)
+    xb, fb, f0 = oracle_golden(m, N, qx, 0.0, h, T, 0.0, 0.2, steps)
+    with ffe.Context(prec=prec, U=U) as ctx:
+        res = ctx.minimize(ffe.params(N, qx, 0.0, h, T, 0.0, 0.2, steps), search=ffe.FFE_SEARCH_GOLDEN)
+    assert per_site(res["omega_lo"], f0, N).max() <= TOL[prec]
+    # the GPU's minimum is a point the oracle agrees with ...
+    at_gpu, _, _ = oracle.omega_batch(m, N, qx, 0.0, h, T, res["delta_star"])
+    assert per_site(res["omega_star"], at_gpu, N).max() <= TOL[prec]
+    # ... and as low as the oracle's own minimum within the comparison noise
+    slack = {ffe.FFE_FP64: 1e-11, ffe.FFE_FP32C: 1e-9}[prec]
+    assert np.all((at_gpu - fb) / N**2 <= slack)
+    bracket = 0.2 * search.PHI ** (steps + 1)
+    close = np.abs(res["delta_star"] - xb) <= 20 * bracket
+    assert close.mean() >= 0.9, np.abs(res["delta_star"] - xb)
+    assert np.array_equal(res["flags"] & ffe.FFE_FLAG_LOWER != 0, xb == 0.0)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_golden_phase_scan_vs_oracle(prec):
+    """Golden phase scan: 5 q x (3 h x 2 T) at N=32, U=4; labels equal to the oracle's."""
+    N, U, steps = 32, 4.0, 20
+    qx = np.array([0.0, 0.15, 0.3, 0.45, 0.6])
+    h = np.array([0.0, 0.07, 0.14])
+    T = np.array([0.003, 0.02])
+    m = oracle.make_model(U=U)
+    H, TT = np.meshgrid(h, T, indexing="ij")
+    Q = np.repeat(qx, H.size)
+    HH = np.tile(H.ravel(), len(qx))
+    TTT = np.tile(TT.ravel(), len(qx))
+    xb, fb, f0 = oracle_golden(m, N, Q, 0.0, HH, TTT, 0.0, 0.2, steps)
+    xb, fb, f0 = (a.reshape(len(qx), H.size) for a in (xb, fb, f0))
+    labels, best = [], []
+    for p in range(H.size):
+        lab, b = search.phase_label(fb[:, p], f0[:, p], qx == 0.0)
+        labels.append(lab)
+        best.append(b)
+    with ffe.Context(prec=prec, U=U) as ctx:
+        res, glab, gbest = ctx.phase_scan(N, qx, np.zeros_like(qx), h, T, search=ffe.FFE_SEARCH_GOLDEN,
+                                          n=steps, lo=0.0, hi=0.2)
+    assert per_site(res["omega_lo"], f0, N).max() <= TOL[prec]
+    assert per_site(res["omega_star"], fb, N).max() <= TOL[prec] + 1e-9
+    assert np.array_equal(glab, np.array(labels)), (glab, labels)
+    assert np.array_equal(gbest, np.array(best))
+    assert np.all(res["idx_star"] == -1)
+
+
+def test_golden_plan_replay():
+    N = 32
+    qx = np.array([0.0, 0.3])
+    with ffe.Context(prec=ffe.FFE_FP32C, U=4.0) as ctx:
+        plan = ctx.plan_phase_scan(N, qx, np.zeros(2), np.array([0.0, 0.1]), np.array([0.004]),
+                                   search=ffe.FFE_SEARCH_GOLDEN, n=12)
+        plan.execute()
+        a = plan.fetch()
+        plan.execute()
+        b = plan.fetch()
+        info = plan.stats()
+        plan.destroy()
+    assert a[0].tobytes() == b[0].tobytes()
+    assert info["k_evals"] == N * N * 2 * 2 * (3 + 12)  # every line evaluated 3 + steps times
