@@ -28,17 +28,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("parameter points/sec and k-evals/sec at N=1024 (FP32+comp vs FP64 vs surrogate), "
           "% FP32/MUFU peak")
-MUFU_PER_CLK_PER_SM = 16      # SFU results per clock per SM (4 per SM sub-partition)
-MUFU_PER_KEVAL_PRODUCT = 4.0  # ex2 x 4 (two per band) ... + lg2 below
-SM_MAX_MHZ_FALLBACK = 2070.0
+# Special-function unit results per clock per SM: ex2 32 (GB300), lg2 / rsqrt /
+# rcp 16 (4 per SM sub-partition); ffe_probe_peaks measures both on the device.
+SFU_EX2_PER_CLK = 32
+SFU_OTHER_PER_CLK = 16
+SM_MAX_MHZ = 2070.0
 
 
-def mufu_per_keval(n_ht: int) -> float:
-    """MUFU operations per k-evaluation in the shared-Delta scan layout:
-    4 ex2 + 1 lg2 per (k, Delta, h) and 2 rsqrt + 2 rcp per (k, Delta) shared
-    by the (up to 32) (h, T) outputs of one batch."""
+def sfu_clk_per_keval(n_ht: int) -> float:
+    """SFU time (SM clocks) per k-evaluation in the shared-Delta scan layout:
+    4 ex2 + 1 lg2 per (k, Delta, (h, T)) and 2 rsqrt + 2 rcp per (k, Delta)
+    shared by the (up to 32) (h, T) outputs of one batch."""
     per_batch = min(32, n_ht)
-    return 5.0 + 4.0 / per_batch
+    return 4.0 / SFU_EX2_PER_CLK + 1.0 / SFU_OTHER_PER_CLK + 4.0 / (SFU_OTHER_PER_CLK * per_batch)
 
 
 def dist_env():
@@ -114,6 +116,60 @@ def cpu_baseline(cfg, seconds_target=15.0):
             "sample": f"{len(sample)} Delta values of one (q, h) at N={N} (FP64, OpenMP over Delta), {dt:.1f} s"}
 
 
+# DRAM bytes (read + write) of one k-sum launch of the default workload, from
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum); None until captured for
+# the current kernel.
+DRAM_TRAFFIC_PER_LAUNCH = None
+
+
+def run_extras(ffe, np, torch, stream, workloads):
+    """The other workload shapes, timed once each after a warm-up (not the headline)."""
+    out = {}
+    # 512 uneven jobs in one persistent, graph-captured launch (FP32+comp)
+    w = workloads.uneven_jobs(512, seed=1234)
+    ps = ffe.params(w["N"], w["qx"], w["qy"], w["h"], w["T"], w["lo"], w["hi"], w["n"])
+    with ffe.Context(prec=ffe.FFE_FP32C, U=2.0) as ctx:
+        plan = ctx.plan_minimize(ps)
+        shape = plan.autotune(stream)
+        plan.execute(stream)
+        plan.fetch_minimize()
+        plan.kernel_ms()
+        reps = 3
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            plan.execute(stream)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / reps
+        kms, _ = plan.kernel_ms()
+        k = plan.stats()["k_evals"]
+        plan.destroy()
+    out["uneven_batch"] = {"jobs": 512, "k_evals_per_s": k / dt, "jobs_per_s": 512 / dt, "ms_per_step": 1e3 * dt,
+                           "kernel_ms": kms, "autotuned": shape,
+                           "workload": "512 jobs, N in {256,512,1024,2048}, 32..256 Delta, seed 1234"}
+    # golden-section phase diagram at N = 2048 on a q subset (the full 64 q run takes ~1 min)
+    pd = workloads.phase_diagram()
+    qs = pd["qx"][:2]
+    with ffe.Context(prec=ffe.FFE_FP32C, U=2.0) as ctx:
+        plan = ctx.plan_phase_scan(pd["N"], qs, np.zeros_like(qs), pd["h"], pd["T"], search=ffe.FFE_SEARCH_GOLDEN,
+                                   n=pd["n"], lo=pd["lo"], hi=pd["hi"])
+        plan.execute(stream)
+        plan.fetch()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.execute(stream)
+        res, labels, _ = plan.fetch()
+        dt = time.perf_counter() - t0
+        k = plan.stats()["k_evals"]
+        plan.destroy()
+    npts = len(qs) * len(pd["h"]) * len(pd["T"])
+    out["phase_diagram_golden"] = {
+        "k_evals_per_s": k / dt, "points_per_s": npts / dt, "seconds": dt,
+        "extrapolated_full_seconds": dt * len(pd["qx"]) / len(qs),
+        "workload": f"N={pd['N']}, {len(qs)} of {len(pd['qx'])} q x 64 h x 64 T, golden {pd['n']} reductions"}
+    return out
+
+
 def threads_hint():
     import oracle
 
@@ -129,6 +185,7 @@ def main():
     ap.add_argument("--N", type=int, default=1024)
     ap.add_argument("--fp64-sample-q", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
     args = ap.parse_args()
 
     from paper_1412_8754_gb300 import workloads
@@ -237,12 +294,15 @@ def main():
         p64.destroy()
         ctx64.close()
 
-    mhz = clk.get("sm_mhz") or SM_MAX_MHZ_FALLBACK
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras = run_extras(ffe, np, torch, stream, workloads)
+
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
-    peak = n_sm * MUFU_PER_CLK_PER_SM * SM_MAX_MHZ_FALLBACK * 1e6 / 1e9  # Gop/s at the maximum clock
-    mufu_per_launch = mufu_per_keval(n_pts) * k_evals
-    achieved = mufu_per_launch / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else 0.0
+    clk_per_keval = sfu_clk_per_keval(n_pts)
+    peak = n_sm * SM_MAX_MHZ * 1e6 / clk_per_keval  # k-evals/s with the SFU saturated, at the maximum clock
+    achieved = k_evals / (kern_ms / 1e3) if kern_ms > 0 else 0.0
 
     out = {
         "metric": METRIC, "value": value, "unit": "k-evals/s", "n_gpus": ws, "steps": args.steps,
@@ -257,12 +317,15 @@ def main():
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "points_per_s": (len(mine) * n_pts) / e2e_t},
         "gpu_launches": launches * args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s (MUFU)",
-                     "frac": achieved / peak if peak else None, "traffic": None,
-                     "kernel": "ksum_kernel<float,4,PRODUCT>", "kernel_ms": kern_ms, "kernel_launches": kern_n,
-                     "peak_basis": f"{n_sm} SM x {MUFU_PER_CLK_PER_SM}/clk x {SM_MAX_MHZ_FALLBACK:.0f} MHz",
-                     "mufu_per_keval": mufu_per_keval(n_pts)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "k-evals/s (SFU-bound)",
+                     "frac": achieved / peak if peak else None, "traffic": DRAM_TRAFFIC_PER_LAUNCH,
+                     "kernel": f"ksum_kernel<float,{info['kpt']},shared-Delta>", "kernel_ms": kern_ms,
+                     "kernel_launches": kern_n,
+                     "peak_basis": (f"{n_sm} SM x {SM_MAX_MHZ:.0f} MHz / {clk_per_keval:.4f} SFU clocks per "
+                                    f"k-eval (ex2 {SFU_EX2_PER_CLK}/clk, lg2 rsqrt rcp {SFU_OTHER_PER_CLK}/clk "
+                                    f"per SM; derived from unit counts, checked by ffe_probe_peaks)")},
         "fp64": fp64,
+        **extras,
         "clocks": clk,
         "labels": {"normal": int((labels == 0).sum()), "bcs": int((labels == 1).sum()),
                    "fflo": int((labels == 2).sum())},

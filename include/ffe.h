@@ -210,6 +210,26 @@ FFE_API ffe_status ffe_plan_stats(const ffe_plan* plan, ffe_plan_info* info);
 FFE_API ffe_status ffe_plan_kernel_ms(ffe_plan* plan, double* ms, int32_t* count);
 FFE_API void ffe_plan_destroy(ffe_plan* plan);
 
+/* A device-resident plan of ffe_minimize: the parameter points (uneven
+ * lattices and grid lengths allowed) are packed into one job table and one
+ * persistent k-sum launch, captured with the Delta search in a CUDA graph.
+ * ffe_plan_fetch_minimize returns the results of the last execution as
+ * ffe_minimize does. */
+FFE_API ffe_status ffe_plan_minimize(ffe_context* ctx, int32_t search, const ffe_param* ps,
+                                     int64_t n, void* stream, ffe_plan** out);
+FFE_API ffe_status ffe_plan_fetch_minimize(ffe_plan* plan, ffe_result* out, double* omega_grid,
+                                           double* err_grid, void* stream);
+
+/* Autotuner (no counterpart in the paper): times the plan's k-sum for a set
+ * of launch shapes (k-points per thread 2/4/8, block 128/256 threads, warp
+ * work-item sizes), rebuilds the plan with the fastest and remembers it for
+ * later plans of the same kind on the context (and in the file named by the
+ * environment variable FFE_TUNE_CACHE, read by ffe_create).  Runs the plan
+ * about twenty times.  The chosen shape is returned when the pointers are
+ * not NULL. */
+FFE_API ffe_status ffe_plan_autotune(ffe_plan* plan, void* stream, int32_t* kpt, int32_t* block,
+                                     double* item_target);
+
 /* ---- device throughput probe (no counterpart in the paper) -------------
  * Measured issue rates, in operations per second over the whole device, of
  * the units the k-sum is bound by: the special-function unit for

@@ -416,13 +416,14 @@ ffe_status plan_enqueue(ffe_context* ctx, ffe_plan* p, cudaStream_t s, cudaEvent
 }
 
 ffe_status plan_configure(ffe_context* ctx, ffe_plan* p) {
+  p->variant = p->layout;
+  if (p->prec == FFE_FP32C && p->layout == kLayoutProduct && batches_share_T(p)) p->variant = kLayoutProductUT;
   // launch shape: persistent grid of resident blocks
   const Tuning t = tuning_for(ctx, p);
   p->kpt = t.kpt;
   p->block = t.block;
   p->item_target = t.item_target;
-  p->variant = p->layout;
-  if (p->prec == FFE_FP32C && p->layout == kLayoutProduct && batches_share_T(p)) p->variant = kLayoutProductUT;
+  p->tuning = t;
   int bps = 0;
   cudaError_t e = ksum_occupancy(p->prec, p->variant, p->kpt, p->block, &bps);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy");

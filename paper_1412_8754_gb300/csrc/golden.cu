@@ -120,8 +120,11 @@ __global__ void golden_kernel(int mode, const Line* __restrict__ lines, int n_li
       }
       break;
     case kGoldenMarkFinal:
-      // the best point against Delta = lo: the normal state wins exact ties
-      if (s.xb != s.lo && fabs(s.fb - s.flo) <= s.ebb + s.eblo) {
+      // The best point against Delta = lo (the normal state wins exact ties).
+      // A bracket whose lower end never left lo has converged onto lo: its
+      // best interior point differs from lo by O(x^2) and lo is taken
+      // directly (kGoldenFinish); otherwise a near tie is settled in FP64.
+      if (s.a != s.lo && s.xb != s.lo && fabs(s.fb - s.flo) <= s.ebb + s.eblo) {
         Rescore r;
         r.group = L.group;
         r.dst = l;
@@ -141,7 +144,8 @@ __global__ void golden_kernel(int mode, const Line* __restrict__ lines, int n_li
       }
       return;
     case kGoldenFinish: {
-      if (s.xb != s.lo && s.flo <= s.fb) {
+      const bool onto_lo = s.a == s.lo && fabs(s.fb - s.flo) <= s.ebb + s.eblo;
+      if (s.xb != s.lo && (s.flo <= s.fb || onto_lo)) {
         s.xb = s.lo;
         s.fb = s.flo;
         s.ebb = s.eblo;

@@ -64,6 +64,8 @@ struct ffe_plan {
   // launch configuration
   int kpt = 4, block = 256, grid = 0, rescore_grid = 0;
   int variant = 0;  // k-sum kernel variant (kLayoutProduct / kLayoutProductUT / kLayoutList)
+  bool forced = false;  // use `tuning` instead of the context's choice
+  ffe::Tuning tuning{4, 256, 8388608.0};
   double item_target = 8388608.0;
   int rescore_chunk = 16384, rescore_chunks = 1;
   int32_t cap = 0;

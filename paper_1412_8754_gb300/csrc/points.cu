@@ -193,36 +193,75 @@ void fill_min_golden(ffe_plan* p, const ffe_param* ps, int64_t n) {
   p->n_out = out;
 }
 
-}  // namespace
 
-namespace ffe {
-
-Tuning tuning_for(ffe_context* ctx, const ffe_plan* p) {
-  char key[128];
-  snprintf(key, sizeof key, "%s:%d:%d", ctx->device_name.c_str(), p->prec, p->layout);
-  auto it = ctx->tuned.find(key);
-  if (it != ctx->tuned.end()) return it->second;
-  Tuning t;
-  t.kpt = p->prec == FFE_FP32C ? 4 : 1;
-  t.block = 256;
-  t.item_target = p->prec == FFE_FP32C ? 8388608.0 : 262144.0;
-  // explicit override "kpt:block:item_target" (used by the tuning sweeps)
-  if (const char* env = getenv(p->prec == FFE_FP32C ? "FFE_KSUM_TUNING_FP32" : "FFE_KSUM_TUNING_FP64")) {
-    int kpt = 0, block = 0;
-    double target = 0.0;
-    if (sscanf(env, "%d:%d:%lf", &kpt, &block, &target) == 3 && ksum_kpt_supported(p->prec, kpt) &&
-        (block == 128 || block == 256) && target >= 1024.0) {
-      t.kpt = kpt;
-      t.block = block;
-      t.item_target = target;
-    }
+ffe_status check_params(ffe_context* ctx, int32_t search, const ffe_param* ps, int64_t n) {
+  if (!ps || n < 1) return set_err(ctx, "empty or NULL parameter list"), FFE_EINVAL;
+  if (search != FFE_SEARCH_GRID && search != FFE_SEARCH_GOLDEN)
+    return set_err(ctx, "unknown search kind %d", search), FFE_EINVAL;
+  int64_t total = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const ffe_param& q = ps[i];
+    if (!valid_N(q.N)) return set_err(ctx, "param %lld: N=%d must be even in [2, 8192]", (long long)i, q.N), FFE_EINVAL;
+    if (!(q.T > 0.0) || !std::isfinite(q.T) || !std::isfinite(q.qx) || !std::isfinite(q.qy) ||
+        !std::isfinite(q.h) || !std::isfinite(q.lo) || !std::isfinite(q.hi) || q.lo > q.hi)
+      return set_err(ctx, "param %lld: non-finite value, T <= 0 or lo > hi", (long long)i), FFE_EINVAL;
+    if (search == FFE_SEARCH_GRID && (q.n < 1 || q.n > 65536))
+      return set_err(ctx, "param %lld: grid points n=%d out of [1, 65536]", (long long)i, q.n), FFE_EINVAL;
+    if (search == FFE_SEARCH_GOLDEN && (q.n < 1 || q.n > 200))
+      return set_err(ctx, "param %lld: golden reductions n=%d out of [1, 200]", (long long)i, q.n), FFE_EINVAL;
+    if (search == FFE_SEARCH_GOLDEN && q.n != ps[0].n)
+      return set_err(ctx, "param %lld: golden searches of one call share n", (long long)i), FFE_EINVAL;
+    total += q.n;
   }
-  return t;
+  if (total > ((int64_t)1 << 31)) return set_err(ctx, "too many outputs"), FFE_EINVAL;
+  return FFE_OK;
 }
 
-void tuning_load(ffe_context*) {}
+ffe_status build_min_plan(ffe_context* ctx, int32_t search, const ffe_param* ps, int64_t n, bool graph,
+                          ffe_plan** out) {
+  ffe_plan* p = plan_new(ctx, search == FFE_SEARCH_GRID ? kPlanMinGrid : kPlanMinGolden);
+  *out = p;
+  if (search == FFE_SEARCH_GRID)
+    fill_min_grid(p, ps, n);
+  else
+    fill_min_golden(p, ps, n);
+  ffe_status st = plan_configure(ctx, p);
+  if (st == FFE_OK) st = plan_finish(ctx, p, graph);
+  return st;
+}
 
-}  // namespace ffe
+ffe_status fetch_min(ffe_context* ctx, ffe_plan* p, ffe_result* out, double* omega_grid, double* err_grid,
+                     cudaStream_t s) {
+  ffe_status st = plan_check_status(ctx, p, s);
+  if (st != FFE_OK) return st;
+  std::vector<LineResult> lr(p->lines.size());
+  cudaError_t e = cudaMemcpyAsync(lr.data(), p->d_lres, lr.size() * sizeof(LineResult), cudaMemcpyDeviceToHost, s);
+  int32_t nreq = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nreq, p->d_counters + 3, sizeof nreq, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && omega_grid)
+    e = cudaMemcpyAsync(omega_grid, p->d_omega, p->n_out * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && err_grid)
+    e = cudaMemcpyAsync(err_grid, p->d_eb, p->n_out * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "fetch results");
+  p->last_rescored[0] = nreq;
+  if (nreq > p->cap) {
+    set_err(ctx, "FP64 re-evaluation requests (%d) exceeded capacity (%d)", nreq, p->cap);
+    return FFE_EINTERNAL;
+  }
+  for (size_t i = 0; i < lr.size(); ++i) {
+    out[i].delta_star = lr[i].delta_star;
+    out[i].omega_star = lr[i].omega_star;
+    out[i].omega_lo = lr[i].omega_lo;
+    out[i].err_bound = lr[i].eb_star;
+    out[i].idx_star = lr[i].idx_star;
+    out[i].flags = lr[i].flags;
+  }
+  p->d2h_bytes = lr.size() * sizeof(LineResult) + (omega_grid ? p->n_out * 8 : 0) + (err_grid ? p->n_out * 8 : 0);
+  return FFE_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -263,65 +302,46 @@ ffe_status ffe_omega(ffe_context* ctx, const ffe_point* pts, int64_t n, double* 
 ffe_status ffe_minimize(ffe_context* ctx, int32_t search, const ffe_param* ps, int64_t n, ffe_result* out,
                         double* omega_grid, double* err_grid, void* stream) {
   if (!ctx) return FFE_EINVAL;
-  if (!ps || !out || n < 1) return set_err(ctx, "ffe_minimize: empty or NULL arguments"), FFE_EINVAL;
-  if (search != FFE_SEARCH_GRID && search != FFE_SEARCH_GOLDEN)
-    return set_err(ctx, "unknown search kind %d", search), FFE_EINVAL;
-  int64_t total = 0;
-  for (int64_t i = 0; i < n; ++i) {
-    const ffe_param& q = ps[i];
-    if (!valid_N(q.N)) return set_err(ctx, "param %lld: N=%d must be even in [2, 8192]", (long long)i, q.N), FFE_EINVAL;
-    if (!(q.T > 0.0) || !std::isfinite(q.T) || !std::isfinite(q.qx) || !std::isfinite(q.qy) ||
-        !std::isfinite(q.h) || !std::isfinite(q.lo) || !std::isfinite(q.hi) || q.lo > q.hi)
-      return set_err(ctx, "param %lld: non-finite value, T <= 0 or lo > hi", (long long)i), FFE_EINVAL;
-    if (search == FFE_SEARCH_GRID && (q.n < 1 || q.n > 65536))
-      return set_err(ctx, "param %lld: grid points n=%d out of [1, 65536]", (long long)i, q.n), FFE_EINVAL;
-    if (search == FFE_SEARCH_GOLDEN && (q.n < 1 || q.n > 200))
-      return set_err(ctx, "param %lld: golden reductions n=%d out of [1, 200]", (long long)i, q.n), FFE_EINVAL;
-    if (search == FFE_SEARCH_GOLDEN && q.n != ps[0].n)
-      return set_err(ctx, "param %lld: golden searches of one call share n", (long long)i), FFE_EINVAL;
-    total += q.n;
-  }
-  if (total > ((int64_t)1 << 31)) return set_err(ctx, "too many outputs"), FFE_EINVAL;
+  if (!out) return set_err(ctx, "ffe_minimize: out is NULL"), FFE_EINVAL;
+  ffe_status st = check_params(ctx, search, ps, n);
+  if (st != FFE_OK) return st;
   if (search == FFE_SEARCH_GOLDEN && (omega_grid || err_grid))
     return set_err(ctx, "omega_grid/err_grid apply to grid searches only"), FFE_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  ffe_plan* p = plan_new(ctx, search == FFE_SEARCH_GRID ? kPlanMinGrid : kPlanMinGolden);
-  if (search == FFE_SEARCH_GRID)
-    fill_min_grid(p, ps, n);
-  else
-    fill_min_golden(p, ps, n);
-  ffe_status st = plan_configure(ctx, p);
-  if (st == FFE_OK) st = plan_finish(ctx, p, false);
+  ffe_plan* p = nullptr;
+  st = build_min_plan(ctx, search, ps, n, false, &p);
   if (st == FFE_OK) st = plan_run(ctx, p, s);
-  if (st == FFE_OK) st = plan_check_status(ctx, p, s);
-  if (st == FFE_OK) {
-    std::vector<LineResult> lr(p->lines.size());
-    cudaError_t e = cudaMemcpyAsync(lr.data(), p->d_lres, lr.size() * sizeof(LineResult), cudaMemcpyDeviceToHost, s);
-    int32_t nreq = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&nreq, p->d_counters + 3, sizeof nreq, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && omega_grid)
-      e = cudaMemcpyAsync(omega_grid, p->d_omega, p->n_out * sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && err_grid)
-      e = cudaMemcpyAsync(err_grid, p->d_eb, p->n_out * sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-      st = cuda_fail(ctx, e, "fetch results");
-    } else if (nreq > p->cap) {
-      set_err(ctx, "FP64 re-evaluation requests (%d) exceeded capacity (%d)", nreq, p->cap);
-      st = FFE_EINTERNAL;
-    } else {
-      for (int64_t i = 0; i < n; ++i) {
-        out[i].delta_star = lr[i].delta_star;
-        out[i].omega_star = lr[i].omega_star;
-        out[i].omega_lo = lr[i].omega_lo;
-        out[i].err_bound = lr[i].eb_star;
-        out[i].idx_star = lr[i].idx_star;
-        out[i].flags = lr[i].flags;
-      }
-    }
-  }
+  if (st == FFE_OK) st = fetch_min(ctx, p, out, omega_grid, err_grid, s);
   plan_free(p);
   return st;
+}
+
+ffe_status ffe_plan_minimize(ffe_context* ctx, int32_t search, const ffe_param* ps, int64_t n, void* stream,
+                             ffe_plan** out) {
+  if (!ctx || !out) return FFE_EINVAL;
+  *out = nullptr;
+  (void)stream;
+  ffe_status st = check_params(ctx, search, ps, n);
+  if (st != FFE_OK) return st;
+  ffe_plan* p = nullptr;
+  st = build_min_plan(ctx, search, ps, n, true, &p);
+  if (st != FFE_OK) {
+    plan_free(p);
+    return st;
+  }
+  ctx->plans.push_back(p);
+  *out = p;
+  return FFE_OK;
+}
+
+ffe_status ffe_plan_fetch_minimize(ffe_plan* p, ffe_result* out, double* omega_grid, double* err_grid,
+                                   void* stream) {
+  if (!p || !out) return FFE_EINVAL;
+  if (p->kind != kPlanMinGrid && p->kind != kPlanMinGolden)
+    return set_err(p->ctx, "not a minimisation plan"), FFE_EINVAL;
+  if (p->kind == kPlanMinGolden && (omega_grid || err_grid))
+    return set_err(p->ctx, "omega_grid/err_grid apply to grid searches only"), FFE_EINVAL;
+  return fetch_min(p->ctx, p, out, omega_grid, err_grid, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -79,6 +79,10 @@ _SIGNATURES = [
     ("ffe_plan_stats", ctypes.c_int, [_VP, ctypes.POINTER(ffe_plan_info)]),
     ("ffe_plan_kernel_ms", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     ("ffe_plan_destroy", None, [_VP]),
+    ("ffe_plan_minimize", ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.POINTER(_VP)]),
+    ("ffe_plan_fetch_minimize", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    ("ffe_plan_autotune", ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_double)]),
     ("ffe_probe_peaks", ctypes.c_int, [_VP]),
 ]
 
@@ -230,6 +234,31 @@ def ffe_plan_destroy(plan):
         plan.handle = None
 
 
+def ffe_plan_minimize(ctx, params: np.ndarray, search=FFE_SEARCH_GRID, stream=None):
+    ps = np.ascontiguousarray(params, dtype=PARAM_DTYPE)
+    plan = _VP()
+    _check(ctx, lib().ffe_plan_minimize(ctx, search, _ptr(ps), len(ps), _stream(stream), ctypes.byref(plan)))
+    p = Plan(ctx, plan, 0, 0)
+    p.n_params = len(ps)
+    p.n_grid = int(ps["n"].sum()) if search == FFE_SEARCH_GRID else 0
+    return p
+
+
+def ffe_plan_fetch_minimize(plan, want_grid=False, stream=None):
+    res = np.zeros(plan.n_params, dtype=RESULT_DTYPE)
+    grid = np.zeros(plan.n_grid) if want_grid else None
+    err = np.zeros(plan.n_grid) if want_grid else None
+    _check(plan.ctx, lib().ffe_plan_fetch_minimize(plan.handle, _ptr(res), _ptr(grid), _ptr(err), _stream(stream)))
+    return (res, grid, err) if want_grid else res
+
+
+def ffe_plan_autotune(plan, stream=None) -> dict:
+    kpt, block, target = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(plan.ctx, lib().ffe_plan_autotune(plan.handle, _stream(stream), ctypes.byref(kpt), ctypes.byref(block),
+                                             ctypes.byref(target)))
+    return {"kpt": kpt.value, "block": block.value, "item_target": target.value}
+
+
 class Plan:
     def __init__(self, ctx, handle, n_q, n_pts):
         self.ctx, self.handle, self.n_q, self.n_pts = ctx, handle, n_q, n_pts
@@ -239,6 +268,12 @@ class Plan:
 
     def fetch(self, stream=None):
         return ffe_plan_fetch(self, stream)
+
+    def fetch_minimize(self, want_grid=False, stream=None):
+        return ffe_plan_fetch_minimize(self, want_grid, stream)
+
+    def autotune(self, stream=None):
+        return ffe_plan_autotune(self, stream)
 
     def stats(self):
         return ffe_plan_stats(self)
@@ -267,6 +302,9 @@ class Context:
 
     def plan_phase_scan(self, *a, **k):
         return ffe_plan_phase_scan(self.handle, *a, **k)
+
+    def plan_minimize(self, params, search=FFE_SEARCH_GRID, stream=None):
+        return ffe_plan_minimize(self.handle, params, search, stream)
 
     def close(self):
         if self.handle:
