@@ -183,6 +183,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ffe", choices=["ffe", "reference"])
     ap.add_argument("--N", type=int, default=1024)
+    ap.add_argument("--n-q", type=int, default=64, help="q values of the scan (64 = the full workload)")
     ap.add_argument("--fp64-sample-q", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
@@ -190,7 +191,7 @@ def main():
 
     from paper_1412_8754_gb300 import workloads
 
-    cfg = workloads.fflo_scan(N=args.N)
+    cfg = workloads.fflo_scan(N=args.N, n_q=args.n_q)
     cfg["U"] = 2.0
     ws, rank, local = dist_env()
 
@@ -206,11 +207,11 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_1412_8754_gb300 import ffe
+    from paper_1412_8754_gb300 import ffe, shard
 
     # shard the q list across ranks (q = 0 stays on every rank: it is the label reference)
     q_all = cfg["qx"]
-    mine = [0] + [i for i in range(1, len(q_all)) if (i - 1) % ws == rank]
+    mine = shard.shard_q(len(q_all), rank, ws)
     qx = q_all[mine]
     qy = np.zeros_like(qx)
     n_pts = len(cfg["h"]) * len(cfg["T"])
@@ -247,7 +248,9 @@ def main():
     t_total = sum(step_ms) / 1e3
     kern_ms, kern_n = plan.kernel_ms()
     res, labels, best = plan.fetch(stream)
-    if ws > 1:
+    if ws > 1:  # labels over the union of the ranks' q lists (outer argmin of Alg. 1)
+        bv, bq, omega_n = shard.local_candidates(res["omega_star"], res["omega_lo"], mine, qx == 0.0)
+        labels, best = shard.gather_labels(bv, bq, omega_n)
         t = torch.tensor([t_total], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         t_total = float(t.item())
