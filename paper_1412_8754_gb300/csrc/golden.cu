@@ -8,16 +8,16 @@
 // one new interior point per reduction.  Delta = lo is evaluated too (it is
 // the normal state).  The result is the lowest Omega seen, ties to the
 // smaller Delta.  All lines advance together: one k-sum launch evaluates the
-// pending Delta of every line.  While the bracket is still wide (more than
-// 1e-3 of the range), a decision whose two FP32 values lie within their
-// error bounds is taken on FP64 re-evaluations instead.
+// pending Delta of every line.  While the two interior points are far apart
+// (more than 1 % of the range), a decision whose two FP32 values lie within
+// their error bounds is taken on FP64 re-evaluations instead.
 #include "ffe_internal.cuh"
 #include "ksum.cuh"
 
 namespace ffe {
 
 constexpr double kPhi = 0.61803398874989484820;
-constexpr double kWideRel = 1e-3;
+constexpr double kWideRel = 1e-2;
 
 __device__ __forceinline__ void golden_take(GoldenState& s, double x, double f, double eb) {
   if (f < s.fb || (f == s.fb && x < s.xb)) {
@@ -70,7 +70,10 @@ __global__ void golden_kernel(int mode, const Line* __restrict__ lines, int n_li
       golden_take(s, s.x2, s.f2, s.eb2);
       break;
     case kGoldenMark:
-      if (fabs(s.f1 - s.f2) <= s.eb1 + s.eb2 && (s.b - s.a) > kWideRel * (s.hi - s.lo)) {
+      // Only a decision between interior points far apart (possibly different
+      // basins) is worth FP64: close points lie in one basin, where either
+      // choice keeps the minimum inside the bracket to within the error band.
+      if (fabs(s.f1 - s.f2) <= s.eb1 + s.eb2 && (s.x2 - s.x1) > kWideRel * (s.hi - s.lo)) {
         Rescore r;
         r.group = L.group;
         r.dst = l;
