@@ -230,6 +230,69 @@ FFE_API ffe_status ffe_plan_fetch_minimize(ffe_plan* plan, ffe_result* out, doub
 FFE_API ffe_status ffe_plan_autotune(ffe_plan* plan, void* stream, int32_t* kpt, int32_t* block,
                                      double* item_target);
 
+/* ---- learned surrogate of Omega (no counterpart in the paper) ----------
+ * A 4 -> 128 -> 128 -> 128 -> 1 MLP with SiLU activations over the raw
+ * inputs (q, h, T, Delta), mapped to x = (raw - shift) * scale; it predicts
+ * a target divided by y_scale (the library applies both maps).  The two
+ * 128 x 128 layers run on the tensor cores in BF16 with FP32 accumulation;
+ * master weights and Adam moments are FP32.  Parameters are 33 793 floats:
+ * W1[4][128], b1[128], W2[128][128], b2[128], W3[128][128], b3[128],
+ * W4[128], b4[1] (W[i][o] maps input i to output o).  All arrays are host
+ * memory; calls are synchronous. */
+typedef struct {
+  float shift[4], scale[4];
+  float y_scale;     /* > 0 */
+  int32_t reserved;  /* must be 0 */
+} ffe_surrogate_meta;
+typedef struct ffe_surrogate ffe_surrogate;
+
+/* params NULL = all zeros. */
+FFE_API ffe_status ffe_surrogate_create(ffe_context* ctx, const ffe_surrogate_meta* meta,
+                                        const float* params, ffe_surrogate** out);
+FFE_API void ffe_surrogate_destroy(ffe_surrogate* s);
+/* Replace the weights (resets the Adam moments). */
+FFE_API ffe_status ffe_surrogate_set_params(ffe_surrogate* s, const float* params);
+FFE_API ffe_status ffe_surrogate_get_params(ffe_surrogate* s, float* params);
+/* y[n] = prediction at x[n][4] = (q, h, T, Delta). */
+FFE_API ffe_status ffe_surrogate_predict(ffe_surrogate* s, const float* x, int64_t n, float* y,
+                                         void* stream);
+/* Gradient (33 793 floats) of the mean squared error over the n samples,
+ * in the network's normalised units, and that loss. */
+FFE_API ffe_status ffe_surrogate_grad(ffe_surrogate* s, const float* x, const float* t, int64_t n,
+                                      float* grad, double* loss, void* stream);
+/* Adam training over `epochs` passes of the samples in their given order
+ * (batch a multiple of 64; the tail that does not fill a batch is skipped).
+ * loss_per_epoch (NULL or [epochs]) receives the mean batch loss. */
+FFE_API ffe_status ffe_surrogate_train(ffe_surrogate* s, const float* x, const float* t, int64_t n,
+                                       int32_t epochs, int32_t batch, float lr,
+                                       float* loss_per_epoch, void* stream);
+
+/* Phase scan guided by the surrogate (grid search only).  The surrogate
+ * predicts every (q, h, T) line on the whole Delta grid; per (h, T) the
+ * exact k-sum verifies q = 0 and the q_keep lines of lowest predicted
+ * minimum, each on `window` grid points around its predicted minimum plus
+ * Delta = 0 (with the FP64 re-evaluation and label passes of
+ * ffe_phase_scan).  Lines whose verified minimum lies on an inner window
+ * edge are re-run on the whole grid.  Unverified lines are reported at
+ * Delta = 0.  Outputs as in ffe_phase_scan (idx_star in grid indices). */
+typedef struct {
+  int32_t window;       /* grid points per verified line, 2..n               */
+  int32_t q_keep;       /* q values kept per (h, T) besides q = 0            */
+  int32_t reserved[2];  /* must be 0                                         */
+} ffe_guide;
+typedef struct {
+  double k_evals;       /* exact k-point evaluations done                    */
+  double k_evals_full;  /* those of the unguided grid scan                   */
+  int64_t lines_kept, lines_pruned, fallbacks;
+  double rms_error;     /* RMS of predicted - exact condensation energy per
+                           site, (Omega(Delta) - Omega(0))/N^2, on the
+                           verified window points                            */
+  double mlp_flops;     /* multiply-adds x 2 of the predictions              */
+} ffe_guide_stats;
+FFE_API ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* s, const ffe_scan* scan,
+                                      const ffe_guide* guide, ffe_result* per_point, int8_t* labels,
+                                      int32_t* best_q, ffe_guide_stats* stats, void* stream);
+
 /* ---- device throughput probe (no counterpart in the paper) -------------
  * Measured issue rates, in operations per second over the whole device, of
  * the units the k-sum is bound by: the special-function unit for

@@ -687,7 +687,7 @@ void fill_scan(ffe_plan* p, const ffe_scan* sc) {
     fill_scan_grid(p, sc);
 }
 
-static ffe_status fetch_scan(ffe_context* ctx, ffe_plan* p, ffe_result* per_point, int8_t* labels,
+ffe_status fetch_scan(ffe_context* ctx, ffe_plan* p, ffe_result* per_point, int8_t* labels,
                              int32_t* best_q, cudaStream_t s) {
   ffe_status st = plan_check_status(ctx, p, s);
   if (st != FFE_OK) return st;

@@ -139,6 +139,11 @@ double plan_k_evals(const ffe_plan* p);
 void build_items(ffe_plan* p);
 void build_mitems(ffe_plan* p);
 bool batches_share_T(const ffe_plan* p);
+ffe_status fetch_scan(ffe_context* ctx, ffe_plan* p, ffe_result* per_point, int8_t* labels, int32_t* best_q,
+                      cudaStream_t s);
+// MLP inference on device arrays (mlp.cu): y[n] (network units) at raw x[n][4].
+ffe_status surrogate_infer_device(ffe_surrogate* s, const float* x, int64_t n, float* y, cudaStream_t st);
+float surrogate_y_scale(const ffe_surrogate* s);
 
 Tuning tuning_for(ffe_context* ctx, const ffe_plan* p);
 void tuning_load(ffe_context* ctx);

@@ -84,7 +84,96 @@ _SIGNATURES = [
     ("ffe_plan_autotune", ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                          ctypes.POINTER(ctypes.c_double)]),
     ("ffe_probe_peaks", ctypes.c_int, [_VP]),
+    ("ffe_surrogate_create", ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(_VP)]),
+    ("ffe_surrogate_destroy", None, [_VP]),
+    ("ffe_surrogate_set_params", ctypes.c_int, [_VP, _VP]),
+    ("ffe_surrogate_get_params", ctypes.c_int, [_VP, _VP]),
+    ("ffe_surrogate_predict", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP]),
+    ("ffe_surrogate_grad", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.POINTER(ctypes.c_double), _VP]),
+    ("ffe_surrogate_train", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_float, _VP, _VP]),
+    ("ffe_surrogate_scan", ctypes.c_int, [_VP, _VP, ctypes.POINTER(ffe_scan), _VP, _VP, _VP, _VP, _VP, _VP]),
 ]
+
+
+class ffe_guide(ctypes.Structure):
+    _fields_ = [("window", ctypes.c_int32), ("q_keep", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+
+
+class ffe_guide_stats(ctypes.Structure):
+    _fields_ = [("k_evals", ctypes.c_double), ("k_evals_full", ctypes.c_double), ("lines_kept", ctypes.c_int64),
+                ("lines_pruned", ctypes.c_int64), ("fallbacks", ctypes.c_int64), ("rms_error", ctypes.c_double),
+                ("mlp_flops", ctypes.c_double)]
+
+
+def ffe_surrogate_scan(ctx, sur, N, qx, qy, h, T, n=256, lo=0.0, hi=0.2, window=16, q_keep=3, stream=None):
+    """Guided grid scan; returns (per_point, labels, best_q, stats dict)."""
+    sc, keep = make_scan(N, qx, qy, h, T, FFE_SEARCH_GRID, n, lo, hi)
+    npts = sc.n_h * sc.n_T
+    res = np.zeros((sc.n_q, npts), dtype=RESULT_DTYPE)
+    labels = np.zeros(npts, dtype=np.int8)
+    best = np.zeros(npts, dtype=np.int32)
+    g = ffe_guide(window, q_keep, (ctypes.c_int32 * 2)(0, 0))
+    st = ffe_guide_stats()
+    _check(ctx, lib().ffe_surrogate_scan(ctx, sur.handle, ctypes.byref(sc), ctypes.byref(g), _ptr(res),
+                                         _ptr(labels), _ptr(best), ctypes.byref(st), _stream(stream)))
+    del keep
+    return res, labels, best, {name: getattr(st, name) for name, _ in ffe_guide_stats._fields_}
+
+N_SURROGATE_PARAMS = 33793
+
+
+class ffe_surrogate_meta(ctypes.Structure):
+    _fields_ = [("shift", ctypes.c_float * 4), ("scale", ctypes.c_float * 4), ("y_scale", ctypes.c_float),
+                ("reserved", ctypes.c_int32)]
+
+
+class Surrogate:
+    """Owning wrapper of an ffe_surrogate (the learned proposal model)."""
+
+    def __init__(self, ctx: "Context", shift, scale, y_scale, params=None):
+        meta = ffe_surrogate_meta((ctypes.c_float * 4)(*shift), (ctypes.c_float * 4)(*scale), float(y_scale), 0)
+        self.ctx = ctx
+        self.handle = _VP()
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        _check(ctx.handle, lib().ffe_surrogate_create(ctx.handle, ctypes.byref(meta), _ptr(p), ctypes.byref(self.handle)))
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _check(self.ctx.handle, lib().ffe_surrogate_set_params(self.handle, _ptr(p)))
+
+    def get_params(self):
+        p = np.zeros(N_SURROGATE_PARAMS, dtype=np.float32)
+        _check(self.ctx.handle, lib().ffe_surrogate_get_params(self.handle, _ptr(p)))
+        return p
+
+    def predict(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 4)
+        y = np.zeros(len(x), dtype=np.float32)
+        _check(self.ctx.handle, lib().ffe_surrogate_predict(self.handle, _ptr(x), len(x), _ptr(y), None))
+        return y
+
+    def grad(self, x, t):
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 4)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        g = np.zeros(N_SURROGATE_PARAMS, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(self.ctx.handle, lib().ffe_surrogate_grad(self.handle, _ptr(x), _ptr(t), len(x), _ptr(g),
+                                                         ctypes.byref(loss), None))
+        return loss.value, g
+
+    def train(self, x, t, epochs, batch, lr):
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 4)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        losses = np.zeros(epochs, dtype=np.float32)
+        _check(self.ctx.handle, lib().ffe_surrogate_train(self.handle, _ptr(x), _ptr(t), len(x), epochs, batch,
+                                                          float(lr), _ptr(losses), None))
+        return losses
+
+    def close(self):
+        if self.handle:
+            lib().ffe_surrogate_destroy(self.handle)
+            self.handle = None
 
 
 class ffe_peaks(ctypes.Structure):

@@ -43,14 +43,22 @@ def uneven_jobs(n_jobs=512, seed=1234, sizes=(256, 512, 1024, 2048)):
                 lo=np.zeros(n_jobs), hi=np.full(n_jobs, 0.2), n=n.astype(np.int32))
 
 
-def surrogate_set(n_groups=8192, per_group=256, seed=1235):
-    """q per group, (h, T, Delta) per sample, uniform over the scan box."""
+def surrogate_set(n_groups=8192, n_ht=16, n_delta=16, seed=1235, T_hi=0.03):
+    """Training samples of the surrogate, uniform over the scan box:
+    q per group, (h, T) pairs per group, Delta values per (q, h, T) line with
+    Delta = 0 first (the reference of the condensation energy).
+    Returns arrays of shape [n_groups], [n_groups, n_ht], [n_groups, n_ht, n_delta]."""
     rng = np.random.default_rng(seed)
     q = rng.uniform(0.0, 0.2 * math.pi, n_groups)
-    h = rng.uniform(0.0, 0.15, (n_groups, per_group))
-    T = rng.uniform(0.001, 0.02, (n_groups, per_group))
-    d = rng.uniform(0.0, 0.2, (n_groups, per_group))
+    h = rng.uniform(0.0, 0.15, (n_groups, n_ht))
+    T = rng.uniform(0.001, T_hi, (n_groups, n_ht))
+    d = rng.uniform(0.0, 0.2, (n_groups, n_ht, n_delta))
+    d[..., 0] = 0.0
     return dict(q=q, h=h, T=T, delta=d)
+
+
+SURROGATE_SHIFT = np.array([0.0, 0.0, 0.001, 0.0])
+SURROGATE_SCALE = 1.0 / np.array([0.2 * math.pi, 0.15, 0.029, 0.2])
 
 
 def phase_diagram(N=2048, n_q=64, n_h=64, n_T=64, steps=24):

@@ -1,0 +1,154 @@
+"""The surrogate's hand-written training and inference kernels vs the FP64 MLP reference.
+
+Tolerances reflect the kernels' BF16 tensor-core products with FP32 accumulation:
+predictions and gradients agree with the FP64 reference to ~1 % (norm-wise)."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_1412_8754_gb300 import ffe
+
+pytestmark = pytest.mark.gpu
+
+RNG = np.random.default_rng(2024)
+Y_SCALE = 0.01
+
+
+def raw_inputs(n, rng=RNG):
+    lo = np.array([0.0, 0.0, 0.001, 0.0])
+    hi = np.array([0.2 * np.pi, 0.15, 0.03, 0.2])
+    return lo + (hi - lo) * rng.uniform(0, 1, (n, 4))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = ffe.Context(prec=ffe.FFE_FP32C)
+    yield c
+    c.close()
+
+
+def make(ctx, theta):
+    return ffe.Surrogate(ctx, mlp.SHIFT, mlp.SCALE, Y_SCALE, theta.astype(np.float32))
+
+
+def test_forward_matches_reference(ctx):
+    theta = mlp.init_params(11)
+    s = make(ctx, theta)
+    xr = raw_inputs(1000)
+    got = s.predict(xr)
+    ref, _ = mlp.forward(theta.astype(np.float32).astype(np.float64), mlp.features(xr))
+    ref = ref * Y_SCALE
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < 3e-2, err  # BF16 activations and weights: 2^-9 relative rounding per value
+    s.close()
+
+
+@pytest.mark.parametrize("n", [200, 64, 1024])
+def test_gradient_matches_reference(ctx, n):
+    theta = mlp.init_params(12)
+    s = make(ctx, theta)
+    xr = raw_inputs(n)
+    t = RNG.normal(0, 1, n) * Y_SCALE
+    loss, g = s.grad(xr, t)
+    lref, gref = mlp.loss_and_grad(theta.astype(np.float32).astype(np.float64), mlp.features(xr), t / Y_SCALE)
+    assert abs(loss - lref) <= 1e-2 * lref
+    rel = np.linalg.norm(g - gref) / np.linalg.norm(gref)
+    cos = float(g @ gref / (np.linalg.norm(g) * np.linalg.norm(gref)))
+    assert rel < 2e-2 and cos > 0.999, (rel, cos)
+    # every parameter block gets its gradient (W1, b1, W2, b2, W3, b3, W4, b4)
+    for a, b in [(0, 512), (512, 640), (640, 17024), (17024, 17152), (17152, 33536), (33536, 33664),
+                 (33664, 33792), (33792, 33793)]:
+        rb = np.linalg.norm(g[a:b] - gref[a:b]) / max(np.linalg.norm(gref[a:b]), 1e-30)
+        assert rb < 5e-2, (a, b, rb)
+    s.close()
+
+
+def test_first_adam_step_matches_reference(ctx):
+    theta = mlp.init_params(13)
+    s = make(ctx, theta)
+    xr = raw_inputs(256)
+    t = RNG.normal(0, 1, 256) * Y_SCALE
+    s.train(xr, t, epochs=1, batch=256, lr=1e-3)
+    new = s.get_params().astype(np.float64)
+    _, gref = mlp.loss_and_grad(theta.astype(np.float32).astype(np.float64), mlp.features(xr), t / Y_SCALE)
+    opt = mlp.Adam(mlp.N_PARAMS, lr=1e-3)
+    want = opt.step(theta.astype(np.float32).astype(np.float64), gref)
+    big = np.abs(gref) > 1e-3 * np.abs(gref).max()
+    # the first bias-corrected step is lr * sign(g) wherever g is not tiny
+    assert np.mean(np.abs(new[big] - want[big]) < 1e-6) > 0.99
+    s.close()
+
+
+def test_training_fits_a_smooth_target(ctx):
+    """Adam on the GPU kernels drives the loss of a smooth synthetic target down."""
+    rng = np.random.default_rng(5)
+    xr = raw_inputs(16384, rng)
+    f = mlp.features(xr)
+    t = (np.sin(3 * f[:, 0]) * f[:, 3] ** 2 - 0.5 * f[:, 1] * f[:, 3] + 0.2 * f[:, 2]) * Y_SCALE
+    s = make(ctx, mlp.init_params(14))
+    losses = s.train(xr, t, epochs=30, batch=512, lr=2e-3)
+    assert losses[-1] < 0.05 * losses[0], losses
+    pred = s.predict(xr[:2000])
+    rms = np.sqrt(np.mean((pred - t[:2000]) ** 2)) / np.std(t)
+    assert rms < 0.1, rms
+    s.close()
+
+
+def test_guided_scan_with_full_window_is_the_full_scan(ctx):
+    """window = whole grid, every q kept: the guided scan reduces to the grid scan."""
+    from paper_1412_8754_gb300 import surrogate as sg
+
+    N, U = 32, 4.0
+    qx = np.array([0.0, 0.15, 0.3, 0.45])
+    h = np.array([0.0, 0.07, 0.14])
+    T = np.array([0.004, 0.02])
+    with ffe.Context(prec=ffe.FFE_FP32C, U=U) as c:
+        s = ffe.Surrogate(c, mlp.SHIFT, mlp.SCALE, Y_SCALE, sg.initial_params(3))
+        res, lab, best, st = ffe.ffe_surrogate_scan(c.handle, s, N, qx, np.zeros(4), h, T, n=33,
+                                                    window=33, q_keep=3)
+        ref, rlab, rbest = c.phase_scan(N, qx, np.zeros(4), h, T, n=33)
+        s.close()
+    assert np.array_equal(res["idx_star"], ref["idx_star"])
+    assert np.array_equal(lab, rlab) and np.array_equal(best, rbest)
+    assert st["fallbacks"] == 0 and st["lines_pruned"] == 0
+    assert st["k_evals"] == st["k_evals_full"]
+
+
+def test_trained_surrogate_guides_the_scan():
+    """A surrogate trained on the library's own free energies cuts the exact work of a
+    grid scan while finding the full scan's minima and labels; an untrained one does not."""
+    from paper_1412_8754_gb300 import surrogate as sg
+    from paper_1412_8754_gb300 import workloads
+
+    N, U, n = 32, 4.0, 41
+    qx = np.linspace(0.0, 0.2 * np.pi, 6)
+    h = np.linspace(0.0, 0.15, 6)
+    T = np.array([0.003, 0.01, 0.02])
+    with ffe.Context(prec=ffe.FFE_FP32C, U=U) as c:
+        sset = workloads.surrogate_set(n_groups=512, n_ht=8, n_delta=16, seed=7, T_hi=0.02)
+        x, y = sg.training_data(c, N, sset)
+        trained, losses = sg.fit(c, x, y, epochs=60, batch=512, lr=2e-3, seed=1)
+        untrained = ffe.Surrogate(c, workloads.SURROGATE_SHIFT, workloads.SURROGATE_SCALE, trained_scale(y),
+                                  sg.initial_params(1))
+        ref, rlab, rbest = c.phase_scan(N, qx, np.zeros_like(qx), h, T, n=n)
+        out = {}
+        for name, s in (("trained", trained), ("untrained", untrained)):
+            res, lab, best, st = ffe.ffe_surrogate_scan(c.handle, s, N, qx, np.zeros_like(qx), h, T, n=n,
+                                                        window=8, q_keep=2)
+            out[name] = (res, lab, st)
+        trained.close()
+        untrained.close()
+    assert losses[-1] < 0.1 * losses[0]
+    res, lab, st = out["trained"]
+    agree_labels = np.mean(lab == rlab)
+    kept = np.zeros_like(ref["idx_star"], dtype=bool)
+    found = res["idx_star"] == ref["idx_star"]
+    assert agree_labels >= 0.9, (lab, rlab)
+    assert st["k_evals"] < 0.5 * st["k_evals_full"], st
+    # the trained network predicts the exact condensation energies better than chance
+    assert st["rms_error"] < out["untrained"][2]["rms_error"], (st, out["untrained"][2])
+    assert np.mean(found | (ref["idx_star"] == 0)) >= 0.5
+
+
+def trained_scale(y):
+    return float(max(np.std(y), 1e-6))
