@@ -293,6 +293,29 @@ FFE_API ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* s, const 
                                       const ffe_guide* guide, ffe_result* per_point, int8_t* labels,
                                       int32_t* best_q, ffe_guide_stats* stats, void* stream);
 
+/* ---- Omega without any allocation (no counterpart in the paper) --------
+ * For callers that cannot allocate device memory when they need a free
+ * energy -- a service that has given all free device memory to its own pool
+ * (a cudaMalloc there fails or evicts), or a latency-critical loop in which
+ * cudaMalloc/cudaFree would synchronise the device and stall other streams.
+ * Computes Omega at n points (h[i], T[i], delta[i]) of one lattice N and one
+ * pair momentum Q = (qx, qy) with the precision of m->prec, exactly as
+ * ffe_omega does, but the caller passes DEVICE arrays h, T, delta (n doubles
+ * each, T > 0, not checked) and omega (n doubles, written), and every
+ * intermediate lives in one fixed 4 MiB __device__ array of the library that
+ * each GPU loading the library holds until exit.  Limits of that array:
+ * N even in [2, 2048] and 1 <= n <= 512; beyond them the call returns
+ * FFE_EINVAL before any device work.  The first call on a device looks up
+ * the array's device address (once per device, with that device current);
+ * make that first call before any stream capture.  The call allocates
+ * nothing and returns once the work is queued on `stream`.  All calls share
+ * the array, which keeps the last call's contents (counters are cleared at
+ * the start of every call): calls that overlap on the GPU race and must be
+ * serialised by the caller. */
+FFE_API ffe_status ffe_omega_noalloc(const ffe_model* m, int32_t N, double qx, double qy,
+                                     const double* h, const double* T, const double* delta,
+                                     int32_t n, double* omega, void* stream);
+
 /* ---- device throughput probe (no counterpart in the paper) -------------
  * Measured issue rates, in operations per second over the whole device, of
  * the units the k-sum is bound by: the special-function unit for

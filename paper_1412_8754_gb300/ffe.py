@@ -93,6 +93,8 @@ _SIGNATURES = [
     ("ffe_surrogate_train", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_float, _VP, _VP]),
     ("ffe_surrogate_scan", ctypes.c_int, [_VP, _VP, ctypes.POINTER(ffe_scan), _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("ffe_omega_noalloc", ctypes.c_int, [ctypes.POINTER(ffe_model), ctypes.c_int32, ctypes.c_double,
+                                         ctypes.c_double, _VP, _VP, _VP, ctypes.c_int32, _VP, _VP]),
 ]
 
 
