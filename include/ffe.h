@@ -102,6 +102,7 @@ typedef struct {
 #define FFE_FLAG_RESCORED 1   /* omega_star was re-evaluated in FP64           */
 #define FFE_FLAG_EDGE 2       /* argmin at the upper end of the Delta range    */
 #define FFE_FLAG_LOWER 4      /* argmin at Delta = lo                          */
+#define FFE_FLAG_PRUNED 8     /* guided scan: line not evaluated               */
 
 typedef struct {
   double delta_star;   /* minimising Delta                                     */
@@ -273,8 +274,13 @@ FFE_API ffe_status ffe_surrogate_train(ffe_surrogate* s, const float* x, const f
  * minimum, each on `window` grid points around its predicted minimum plus
  * Delta = 0 (with the FP64 re-evaluation and label passes of
  * ffe_phase_scan).  Lines whose verified minimum lies on an inner window
- * edge are re-run on the whole grid.  Unverified lines are reported at
- * Delta = 0.  Outputs as in ffe_phase_scan (idx_star in grid indices). */
+ * edge are re-run on the whole grid.  Unverified (pruned) lines are not
+ * evaluated: they are reported with idx_star 0, flags FFE_FLAG_LOWER |
+ * FFE_FLAG_PRUNED and the Delta = 0 value of the q = 0 line at the same
+ * (h, T); a line whose minimum is its Delta = 0 point never decides a label,
+ * so pruning changes a label only where the exact minimum of a pruned q
+ * would have beaten the kept ones.  Outputs as in ffe_phase_scan (idx_star
+ * in grid indices). */
 typedef struct {
   int32_t window;       /* grid points per verified line, 2..n               */
   int32_t q_keep;       /* q values kept per (h, T) besides q = 0            */

@@ -62,18 +62,24 @@ namespace {
 
 struct LineSpec {
   std::vector<int> grid_idx;  // grid index of each output, grid_idx[0] == 0 (Delta = 0)
+  bool alias = false;         // not evaluated: reads the q = 0 line's Delta = 0 output
 };
 
 // A scan-shaped plan whose lines carry explicit grid-index lists: one LIST
-// group per q, lines q-major (the label passes expect that order).
-void fill_explicit(ffe_plan* p, const ffe_scan* sc, const std::vector<double>& grid,
+// group per q, lines q-major (the label passes expect that order).  A group's
+// h list holds only the h values of its evaluated lines.  An alias line is a
+// one-point line on the q = 0 line's Delta = 0 output: its minimum is its
+// lower end, so it never competes for a label and costs no k-sum work.
+void fill_explicit(ffe_plan* p, const ffe_scan* sc, int q0, const std::vector<double>& grid,
                    const std::vector<LineSpec>& spec) {
   const int n_pts = sc->n_h * sc->n_T;
   p->layout = kLayoutList;
   p->n_q = sc->n_q;
   p->n_pts = n_pts;
   p->q_is_zero.assign(sc->n_q, 0);
+  p->lines.assign((size_t)sc->n_q * n_pts, Line{});
   int64_t out = 0;
+  std::vector<int> h_local(sc->n_h);
   for (int q = 0; q < sc->n_q; ++q) {
     GroupDesc g;
     std::memset(&g, 0, sizeof g);
@@ -84,16 +90,27 @@ void fill_explicit(ffe_plan* p, const ffe_scan* sc, const std::vector<double>& g
     g.ht_off = (int64_t)p->ht.size();
     g.tab_off = (int64_t)q * 2 * sc->N;
     g.h_off = (int64_t)p->hlist.size();
-    g.n_h = sc->n_h;
     g.qx = sc->qx[q];
     g.qy = sc->qy[q];
     p->q_is_zero[q] = (sc->qx[q] == 0.0 && sc->qy[q] == 0.0) ? 1 : 0;
-    p->hlist.insert(p->hlist.end(), sc->h, sc->h + sc->n_h);
+    std::fill(h_local.begin(), h_local.end(), -1);
+    int n_hq = 0;
+    for (int pt = 0; pt < n_pts; ++pt) {
+      const int ih = pt / sc->n_T;
+      if (!spec[(size_t)q * n_pts + pt].alias && h_local[ih] < 0) h_local[ih] = 0;
+    }
+    for (int ih = 0; ih < sc->n_h; ++ih)
+      if (h_local[ih] == 0) {
+        h_local[ih] = n_hq++;
+        p->hlist.push_back(sc->h[ih]);
+      }
+    g.n_h = n_hq;
     int n_out = 0;
     for (int pt = 0; pt < n_pts; ++pt) {
       const LineSpec& ls = spec[(size_t)q * n_pts + pt];
+      if (ls.alias) continue;
       const int ih = pt / sc->n_T, it = pt % sc->n_T;
-      Line L;
+      Line& L = p->lines[(size_t)q * n_pts + pt];
       L.out0 = out + n_out;
       L.stride = 1;
       L.count = (int32_t)ls.grid_idx.size();
@@ -101,10 +118,9 @@ void fill_explicit(ffe_plan* p, const ffe_scan* sc, const std::vector<double>& g
       L.pad = 0;
       L.delta0 = g.delta_off + n_out;
       L.ht = g.ht_off + n_out;
-      p->lines.push_back(L);
       for (int gi : ls.grid_idx) {
         p->delta.push_back(grid[gi]);
-        p->ht.push_back(HT{sc->h[ih], sc->T[it], ih, 0});
+        p->ht.push_back(HT{sc->h[ih], sc->T[it], h_local[ih], 0});
       }
       n_out += L.count;
     }
@@ -116,15 +132,22 @@ void fill_explicit(ffe_plan* p, const ffe_scan* sc, const std::vector<double>& g
     p->groups.push_back(g);
     out += n_out;
   }
+  for (int q = 0; q < sc->n_q; ++q)
+    for (int pt = 0; pt < n_pts; ++pt)
+      if (spec[(size_t)q * n_pts + pt].alias) {
+        Line L = p->lines[(size_t)q0 * n_pts + pt];
+        L.count = 1;
+        p->lines[(size_t)q * n_pts + pt] = L;
+      }
   p->n_out = out;
 }
 
-ffe_status run_explicit(ffe_context* ctx, const ffe_scan* sc, const std::vector<double>& grid,
+ffe_status run_explicit(ffe_context* ctx, const ffe_scan* sc, int q0, const std::vector<double>& grid,
                         const std::vector<LineSpec>& spec, cudaStream_t s, std::vector<ffe_result>& res,
                         std::vector<int8_t>& labels, std::vector<int32_t>& best, std::vector<double>* omega,
                         double* k_evals) {
   ffe_plan* p = plan_new(ctx, kPlanScanGrid);
-  fill_explicit(p, sc, grid, spec);
+  fill_explicit(p, sc, q0, grid, spec);
   ffe_status st = plan_configure(ctx, p);
   if (st == FFE_OK) st = plan_finish(ctx, p, false);
   if (st == FFE_OK) st = plan_run(ctx, p, s);
@@ -230,6 +253,7 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
   for (int l = 0; l < n_lines; ++l) {
     if (!kept[l]) {
       spec[l].grid_idx = {0};
+      spec[l].alias = true;
       continue;
     }
     const int i0 = std::max(0, std::min(n - w, idx[l] - w / 2));
@@ -244,7 +268,7 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
   std::vector<int8_t> labels;
   std::vector<int32_t> best;
   std::vector<double> omega;
-  st = run_explicit(ctx, sc, grid, spec, s, res, labels, best, &omega, &k_evals);
+  st = run_explicit(ctx, sc, q0, grid, spec, s, res, labels, best, &omega, &k_evals);
   if (st != FFE_OK) return st;
 
   // 4. surrogate error on the verified points; lines to re-run on the whole grid
@@ -253,7 +277,7 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
   double se = 0.0;
   int64_t n_se = 0, fallbacks = 0, n_kept = 0;
   std::vector<int64_t> off(n_lines + 1, 0);
-  for (int l = 0; l < n_lines; ++l) off[l + 1] = off[l] + (int64_t)spec[l].grid_idx.size();
+  for (int l = 0; l < n_lines; ++l) off[l + 1] = off[l] + (spec[l].alias ? 0 : (int64_t)spec[l].grid_idx.size());
   std::vector<char> redo(n_lines, 0);
   for (int l = 0; l < n_lines; ++l) {
     if (!kept[l]) continue;
@@ -288,12 +312,13 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
         std::iota(spec2[l].grid_idx.begin(), spec2[l].grid_idx.end(), 0);
       } else {
         spec2[l].grid_idx = {0};
+        spec2[l].alias = !kept[l];
         const int i = res[l].idx_star;
         if (kept[l] && i > 0) spec2[l].grid_idx.push_back(spec[l].grid_idx[i]);
       }
     }
     spec = spec2;
-    st = run_explicit(ctx, sc, grid, spec, s, res, labels, best, nullptr, &k_evals);
+    st = run_explicit(ctx, sc, q0, grid, spec, s, res, labels, best, nullptr, &k_evals);
     if (st != FFE_OK) return st;
   }
 
@@ -305,6 +330,7 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
     r.flags &= ~(FFE_FLAG_EDGE | FFE_FLAG_LOWER);
     if (r.idx_star == 0) r.flags |= FFE_FLAG_LOWER;
     if (r.idx_star == n - 1) r.flags |= FFE_FLAG_EDGE;
+    if (!kept[l]) r.flags |= FFE_FLAG_PRUNED;
     if (per_point) per_point[l] = r;
   }
   if (labels_out) std::memcpy(labels_out, labels.data(), n_pts);

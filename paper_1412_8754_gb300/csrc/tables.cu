@@ -65,6 +65,17 @@ cudaError_t prep_params_launch(const double* delta, int64_t n_delta, float* d2f,
 
 // M(h) = sum_k sum_eps [min(E_eps(k+Q/2) - mu - h, 0) + min(E_eps(-k+Q/2) - mu + h, 0)]
 // for up to 32 h values per item, over the item's k range, in FP64.
+//
+// With u = E(k+Q/2) - mu and d = E(-k+Q/2) - mu the summand is
+// min(u, h) + min(d, -h) - 0, so each band value contributes either itself or
+// +-h.  Lane j of a warp owns h_j.  A value below every h of the item (u) or
+// below every -h (d) adds itself to every h: it goes to a per-lane total S.
+// A value above all of them adds +h_j (u) or -h_j (d) to every h: it goes to
+// a per-lane integer count C, so that S + C h_j is its contribution to h_j.
+// Only the few values inside [h_min, h_max) (or its mirror) need a choice per
+// h: they are broadcast to the warp and lane j adds min(value, +-h_j).  Every
+// choice is made on FP32 copies; where the copies tie, the two candidates
+// differ by at most one FP32 ulp of h.
 __global__ void __launch_bounds__(256) normal_kernel(const ModelParams m,
                                                      const GroupDesc* __restrict__ groups,
                                                      const MItem* __restrict__ items,
@@ -78,48 +89,68 @@ __global__ void __launch_bounds__(256) normal_kernel(const ModelParams m,
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int h0 = it.hb * 32;
   const int nh = min(32, g.n_h - h0);
-  __shared__ double hv[32];
-  __shared__ float hvf[32];
-  if (threadIdx.x < 32) {
-    hv[threadIdx.x] = ((int)threadIdx.x < nh) ? hlist[g.h_off + h0 + threadIdx.x] : 0.0;
-    hvf[threadIdx.x] = (float)hv[threadIdx.x];
+  const double hj = hlist[g.h_off + h0 + min(lane, nh - 1)];
+  const float hjf = (float)hj;
+  float hminf = hjf, hmaxf = hjf;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    hminf = fminf(hminf, __shfl_xor_sync(kFull, hminf, s));
+    hmaxf = fmaxf(hmaxf, __shfl_xor_sync(kFull, hmaxf, s));
   }
-  __syncthreads();
-  double acc[32];
+  double S = 0.0, acc = 0.0;
+  int C = 0;
+  // warp-uniform trip count: every lane takes part in the ballots
+  for (int64_t kb = it.k0 + (threadIdx.x & ~31); kb < it.k1; kb += blockDim.x) {
+    const int64_t k = kb + lane;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    unsigned rare = 0;
+    if (k < it.k1) {
+      const int iy = (int)(k / g.N);
+      const int ix = (int)(k - (int64_t)iy * g.N);
+      const TabRowD rx = tabd[g.tab_off + ix];
+      const TabRowD ry = tabd[g.tab_off + g.N + iy];
+      band_pair<double>(m, rx.cp, ry.cp, rx.sp, ry.sp, v[0], v[1]);
+      band_pair<double>(m, rx.cm, ry.cm, rx.sm, ry.sm, v[2], v[3]);
 #pragma unroll
-  for (int j = 0; j < 32; ++j) acc[j] = 0.0;
-  for (int64_t k = it.k0 + threadIdx.x; k < it.k1; k += blockDim.x) {
-    const int iy = (int)(k / g.N);
-    const int ix = (int)(k - (int64_t)iy * g.N);
-    const TabRowD rx = tabd[g.tab_off + ix];
-    const TabRowD ry = tabd[g.tab_off + g.N + iy];
-    double ulo, uhi, dlo, dhi;
-    band_pair<double>(m, rx.cp, ry.cp, rx.sp, ry.sp, ulo, uhi);
-    band_pair<double>(m, rx.cm, ry.cm, rx.sm, ry.sm, dlo, dhi);
-    ulo -= m.mu;
-    uhi -= m.mu;
-    dlo -= m.mu;
-    dhi -= m.mu;
-    // min(u - h, 0) + min(d + h, 0) = min(u, h) + min(d, -h): each min selects
-    // one of two FP64 values; the choice is made on FP32 copies (ALU), only
-    // the sum uses the FP64 pipe.  Where the FP32 copies tie, either value is
-    // within one FP32 ulp of the other.
-    const float fulo = (float)ulo, fuhi = (float)uhi, fdlo = (float)dlo, fdhi = (float)dhi;
+      for (int i = 0; i < 4; ++i) v[i] -= m.mu;
+      double below = 0.0;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (j < nh) {
-        const double h = hv[j];
-        const float hf = hvf[j];
-        const double t0 = fulo < hf ? ulo : h;
-        const double t1 = fuhi < hf ? uhi : h;
-        const double t2 = fdlo < -hf ? dlo : -h;
-        const double t3 = fdhi < -hf ? dhi : -h;
-        acc[j] += (t0 + t1) + (t2 + t3);
+      for (int i = 0; i < 4; ++i) {
+        const float f = (float)v[i];
+        // u (i < 2) against h; d (i >= 2) against -h
+        const float lo = i < 2 ? hminf : -hmaxf, hi = i < 2 ? hmaxf : -hminf;
+        if (f < lo) {
+          below += v[i];
+        } else if (f >= hi) {
+          C += i < 2 ? 1 : -1;
+        } else {
+          rare |= 1u << i;
+        }
+      }
+      S += below;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      unsigned mask = __ballot_sync(kFull, (rare >> i) & 1u);
+      while (mask) {
+        const int src = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const double x = __shfl_sync(kFull, v[i], src);
+        const float xf = (float)x;
+        if (i < 2)
+          acc += xf < hjf ? x : hj;
+        else
+          acc += xf < -hjf ? x : -hj;
       }
     }
   }
-  const double wsum = reduce_scatter32<double>(acc, lane);
-  red[warp][lane] = wsum;
+  // warp totals of S and C, then this lane's M contribution for h_j
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    S += __shfl_xor_sync(kFull, S, s);
+    C += __shfl_xor_sync(kFull, C, s);
+  }
+  red[warp][lane] = (S + (double)C * hj) + acc;
   __syncthreads();
   if (warp == 0) {
     double s = 0.0;

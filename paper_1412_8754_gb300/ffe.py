@@ -21,7 +21,7 @@ FFE_OK, FFE_EINVAL, FFE_ENOMEM, FFE_ECUDA, FFE_ETIMEOUT, FFE_EUNSUPPORTED, FFE_E
 FFE_FP64, FFE_FP32C = 0, 1
 FFE_MODEL_RAGHU2 = 0
 FFE_SEARCH_GRID, FFE_SEARCH_GOLDEN = 0, 1
-FFE_FLAG_RESCORED, FFE_FLAG_EDGE, FFE_FLAG_LOWER = 1, 2, 4
+FFE_FLAG_RESCORED, FFE_FLAG_EDGE, FFE_FLAG_LOWER, FFE_FLAG_PRUNED = 1, 2, 4, 8
 FFE_PHASE_NORMAL, FFE_PHASE_BCS, FFE_PHASE_FFLO = 0, 1, 2
 
 POINT_DTYPE = np.dtype([("N", "<i4"), ("reserved", "<i4"), ("qx", "<f8"), ("qy", "<f8"),

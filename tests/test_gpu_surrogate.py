@@ -145,6 +145,9 @@ def test_trained_surrogate_guides_the_scan():
     found = res["idx_star"] == ref["idx_star"]
     assert agree_labels >= 0.9, (lab, rlab)
     assert st["k_evals"] < 0.5 * st["k_evals_full"], st
+    pruned = (res["flags"] & ffe.FFE_FLAG_PRUNED) != 0
+    assert pruned.sum() == st["lines_pruned"] > 0
+    assert np.all(res["idx_star"][pruned] == 0)
     # the trained network predicts the exact condensation energies better than chance
     assert st["rms_error"] < out["untrained"][2]["rms_error"], (st, out["untrained"][2])
     assert np.mean(found | (ref["idx_star"] == 0)) >= 0.5
