@@ -87,6 +87,15 @@ void build_items(ffe_plan* p) {
   p->items.clear();
   p->segs.clear();
   const int kset_pts = 32 * p->kpt;
+  // A small plan gets smaller items, so that the persistent grid's warps all
+  // find work: at least about four items per resident warp.
+  double work = 0.0;
+  for (const GroupDesc& g : p->groups) {
+    const int64_t nk = (int64_t)g.N * g.N;
+    work += (double)g.n_batches * 32.0 * (double)((nk + kset_pts - 1) / kset_pts) * kset_pts;
+  }
+  const double n_warps = std::max(1.0, (double)p->grid * (double)(p->block / 32));
+  const double target = std::max((double)kset_pts * 32.0, std::min(p->item_target, work / (4.0 * n_warps)));
   int64_t poff = 0;
   for (int gi = 0; gi < (int)p->groups.size(); ++gi) {
     const GroupDesc& g = p->groups[gi];
@@ -97,7 +106,7 @@ void build_items(ffe_plan* p) {
       const int b1 = std::min(g.n_batches, b0 + sb);
       const int nb = b1 - b0;
       const double outs = (double)nb * 32.0;
-      int ck = (int)std::max(1.0, std::floor((double)p->item_target / (outs * kset_pts)));
+      int ck = (int)std::max(1.0, std::floor(target / (outs * kset_pts)));
       ck = std::min(ck, n_ksets);
       const int n_chunks = (n_ksets + ck - 1) / ck;
       Segment sg;
