@@ -170,6 +170,55 @@ def run_extras(ffe, np, torch, stream, workloads):
     return out
 
 
+def run_surrogate(ffe, np, torch, workloads, cfg, ref, full_s, fp64_rate, epochs=20):
+    """The learned surrogate: ~2M samples at N=512, training, and the guided
+    scan of the headline workload against its full FP32 scan."""
+    from paper_1412_8754_gb300 import surrogate as sg
+
+    ref_res, ref_labels, ref_best = ref
+    with ffe.Context(prec=ffe.FFE_FP32C, U=cfg["U"]) as ctx:
+        sset = workloads.surrogate_set(n_groups=8192, n_ht=16, n_delta=16, seed=1235, T_hi=0.03)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, y = sg.training_data(ctx, 512, sset)
+        torch.cuda.synchronize()
+        t_data = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        sur, losses = sg.fit(ctx, x, y, epochs=epochs, batch=4096, lr=2e-3, seed=1)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        args = (ctx.handle, sur, cfg["N"], cfg["qx"], np.zeros_like(cfg["qx"]), cfg["h"], cfg["T"])
+        kw = dict(n=cfg["n"], lo=cfg["lo"], hi=cfg["hi"], window=16, q_keep=3)
+        ffe.ffe_surrogate_scan(*args, **kw)
+        times = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res, labels, best, st = ffe.ffe_surrogate_scan(*args, **kw)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        sur.close()
+    dt = statistics.median(times)
+    kept = (res["flags"] & ffe.FFE_FLAG_PRUNED) == 0
+    full64_s = st["k_evals_full"] / fp64_rate if fp64_rate else None
+    n_pts = len(labels)
+    return {
+        "workload": (f"train: {len(x)} samples (q,h,T,Delta) at N=512 from the FP32+comp k-sum, {epochs} epochs, "
+                     f"batch 4096; guide: fflo_scan N={cfg['N']}, window 16 + Delta=0, q=0 and 3 q kept per h"),
+        "datagen_s": t_data, "train_s": t_train, "train_loss_first_last": [float(losses[0]), float(losses[-1])],
+        "guided_s": dt, "points_per_s": len(cfg["qx"]) * n_pts / dt,
+        "full_fp32_s": full_s, "speedup_vs_full_fp32": full_s / dt,
+        "full_fp64_s_extrapolated": full64_s, "speedup_vs_full_fp64": full64_s / dt if full64_s else None,
+        "k_evals": st["k_evals"], "k_evals_full": st["k_evals_full"], "mlp_flops": st["mlp_flops"],
+        "rms_error_per_site": st["rms_error"], "rms_unit": "|t1| per lattice site (condensation energy)",
+        "lines_kept": st["lines_kept"], "lines_pruned": st["lines_pruned"], "fallbacks": st["fallbacks"],
+        "fallback_rate": st["fallbacks"] / max(1, st["lines_kept"]),
+        "label_agreement": float(np.mean(labels == ref_labels)),
+        "best_q_agreement": float(np.mean(best == ref_best)),
+        "idx_agreement_kept_lines": float(np.mean(res["idx_star"][kept] == ref_res["idx_star"][kept])),
+    }
+
+
 def threads_hint():
     import oracle
 
@@ -271,7 +320,8 @@ def main():
     for i in range(max(2, min(args.steps, 5))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.phase_scan(cfg["N"], qx, qy, cfg["h"], cfg["T"], n=cfg["n"], lo=cfg["lo"], hi=cfg["hi"], stream=stream)
+        full = ctx.phase_scan(cfg["N"], qx, qy, cfg["h"], cfg["T"], n=cfg["n"], lo=cfg["lo"], hi=cfg["hi"],
+                              stream=stream)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
     e2e_t = statistics.median(e2e_times[1:])
@@ -300,6 +350,9 @@ def main():
     extras = {}
     if rank == 0 and not args.no_extras:
         extras = run_extras(ffe, np, torch, stream, workloads)
+        if ws == 1:
+            extras["surrogate"] = run_surrogate(ffe, np, torch, workloads, cfg, full, e2e_t,
+                                                fp64["k_evals_per_s"] if fp64 else None)
 
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
