@@ -147,32 +147,13 @@ def run_extras(ffe, np, torch, stream, workloads):
     out["uneven_batch"] = {"jobs": 512, "k_evals_per_s": k / dt, "jobs_per_s": 512 / dt, "ms_per_step": 1e3 * dt,
                            "kernel_ms": kms, "autotuned": shape,
                            "workload": "512 jobs, N in {256,512,1024,2048}, 32..256 Delta, seed 1234"}
-    # golden-section phase diagram at N = 2048 on a q subset (the full 64 q run takes ~1 min)
-    pd = workloads.phase_diagram()
-    qs = pd["qx"][:2]
-    with ffe.Context(prec=ffe.FFE_FP32C, U=2.0) as ctx:
-        plan = ctx.plan_phase_scan(pd["N"], qs, np.zeros_like(qs), pd["h"], pd["T"], search=ffe.FFE_SEARCH_GOLDEN,
-                                   n=pd["n"], lo=pd["lo"], hi=pd["hi"])
-        plan.execute(stream)
-        plan.fetch()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        plan.execute(stream)
-        res, labels, _ = plan.fetch()
-        dt = time.perf_counter() - t0
-        k = plan.stats()["k_evals"]
-        plan.destroy()
-    npts = len(qs) * len(pd["h"]) * len(pd["T"])
-    out["phase_diagram_golden"] = {
-        "k_evals_per_s": k / dt, "points_per_s": npts / dt, "seconds": dt,
-        "extrapolated_full_seconds": dt * len(pd["qx"]) / len(qs),
-        "workload": f"N={pd['N']}, {len(qs)} of {len(pd['qx'])} q x 64 h x 64 T, golden {pd['n']} reductions"}
     return out
 
 
-def run_surrogate(ffe, np, torch, workloads, cfg, ref, full_s, fp64_rate, epochs=20):
-    """The learned surrogate: ~2M samples at N=512, training, and the guided
-    scan of the headline workload against its full FP32 scan."""
+def run_surrogate(ffe, np, torch, workloads, cfg, ref, full_s, fp64_rate, epochs=20, diagram=True):
+    """The learned surrogate: ~2M samples at N=512, training, the guided scan of
+    the headline workload against its full FP32 scan, and the N=2048 phase
+    diagram (golden-section) in its full FP32, guided and sampled FP64 forms."""
     from paper_1412_8754_gb300 import surrogate as sg
 
     ref_res, ref_labels, ref_best = ref
@@ -197,15 +178,18 @@ def run_surrogate(ffe, np, torch, workloads, cfg, ref, full_s, fp64_rate, epochs
             res, labels, best, st = ffe.ffe_surrogate_scan(*args, **kw)
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
+        rms_train = sg.rms_error(sur, x, y)
+        pd_out = run_phase_diagram(ffe, np, torch, workloads, ctx, sur, 3.0 * rms_train, fp64_rate) if diagram else None
         sur.close()
     dt = statistics.median(times)
     kept = (res["flags"] & ffe.FFE_FLAG_PRUNED) == 0
     full64_s = st["k_evals_full"] / fp64_rate if fp64_rate else None
     n_pts = len(labels)
-    return {
+    return pd_out, {
         "workload": (f"train: {len(x)} samples (q,h,T,Delta) at N=512 from the FP32+comp k-sum, {epochs} epochs, "
                      f"batch 4096; guide: fflo_scan N={cfg['N']}, window 16 + Delta=0, q=0 and 3 q kept per h"),
         "datagen_s": t_data, "train_s": t_train, "train_loss_first_last": [float(losses[0]), float(losses[-1])],
+        "rms_train_per_site": rms_train,
         "guided_s": dt, "points_per_s": len(cfg["qx"]) * n_pts / dt,
         "full_fp32_s": full_s, "speedup_vs_full_fp32": full_s / dt,
         "full_fp64_s_extrapolated": full64_s, "speedup_vs_full_fp64": full64_s / dt if full64_s else None,
@@ -216,6 +200,55 @@ def run_surrogate(ffe, np, torch, workloads, cfg, ref, full_s, fp64_rate, epochs
         "label_agreement": float(np.mean(labels == ref_labels)),
         "best_q_agreement": float(np.mean(best == ref_best)),
         "idx_agreement_kept_lines": float(np.mean(res["idx_star"][kept] == ref_res["idx_star"][kept])),
+    }
+
+
+def run_phase_diagram(ffe, np, torch, workloads, ctx, sur, margin, fp64_rate):
+    """N=2048, 64 q x 64 h x 64 T, golden-section (24 reductions): the full FP32+comp scan, the
+    surrogate-guided scan, and the FP64 kernel on a sub-grid, with their labels compared."""
+    pd = workloads.phase_diagram()
+    a = (pd["N"], pd["qx"], pd["qy"], pd["h"], pd["T"])
+    kw = dict(search=ffe.FFE_SEARCH_GOLDEN, n=pd["n"], lo=pd["lo"], hi=pd["hi"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    full, flab, fbest = ctx.phase_scan(*a, **kw)
+    torch.cuda.synchronize()
+    t_full = time.perf_counter() - t0
+    n_pts = len(pd["h"]) * len(pd["T"])
+    k_full = float(pd["N"]) ** 2 * len(pd["qx"]) * n_pts * (3 + pd["n"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gres, glab, gbest, gst = ffe.ffe_surrogate_scan(ctx.handle, sur, *a, window=16, q_keep=3, margin=margin, **kw)
+    torch.cuda.synchronize()
+    t_guided = time.perf_counter() - t0
+    # FP64 on a 2 h x 4 T sub-grid with every q (labels need all q of a point)
+    hs, ts = pd["h"][:2], pd["T"][:4]
+    with ffe.Context(prec=ffe.FFE_FP64, U=2.0) as c64:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, lab64, best64 = c64.phase_scan(pd["N"], pd["qx"], pd["qy"], hs, ts, **kw)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+    sub = (np.arange(2)[:, None] * len(pd["T"]) + np.arange(4)[None, :]).ravel()
+    k64 = float(pd["N"]) ** 2 * len(pd["qx"]) * len(sub) * (3 + pd["n"])
+    return {
+        "workload": (f"N={pd['N']}, {len(pd['qx'])} q x {len(pd['h'])} h x {len(pd['T'])} T, golden "
+                     f"{pd['n']} reductions on [0, 0.2], U=2"),
+        "fp32c_full": {"seconds": t_full, "points_per_s": len(pd["qx"]) * n_pts / t_full,
+                       "k_evals_per_s": k_full / t_full,
+                       "labels": [int((flab == i).sum()) for i in range(3)]},
+        "guided": {"seconds": t_guided, "speedup_vs_fp32c_full": t_full / t_guided,
+                   "speedup_vs_fp64_full_extrapolated": (k_full / fp64_rate) / t_guided if fp64_rate else None,
+                   "label_agreement_vs_fp32c_full": float(np.mean(glab == flab)),
+                   "best_q_agreement": float(np.mean(gbest == fbest)),
+                   "k_evals": gst["k_evals"], "k_evals_full": gst["k_evals_full"],
+                   "lines_kept": gst["lines_kept"], "fallbacks": gst["fallbacks"],
+                   "rms_error_per_site": gst["rms_error"], "margin": margin,
+                   "window": 16, "q_keep": 3},
+        "fp64_subgrid": {"points": len(sub), "seconds": t64, "k_evals_per_s": k64 / t64,
+                         "label_agreement_vs_fp32c": float(np.mean(lab64 == flab[sub])),
+                         "best_q_agreement_vs_fp32c": float(np.mean(best64 == fbest[sub])),
+                         "full_seconds_extrapolated": k_full / (k64 / t64)},
     }
 
 
@@ -236,6 +269,7 @@ def main():
     ap.add_argument("--fp64-sample-q", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-diagram", action="store_true", help="skip the N=2048 phase diagram (~70 s)")
     args = ap.parse_args()
 
     from paper_1412_8754_gb300 import workloads
@@ -351,8 +385,11 @@ def main():
     if rank == 0 and not args.no_extras:
         extras = run_extras(ffe, np, torch, stream, workloads)
         if ws == 1:
-            extras["surrogate"] = run_surrogate(ffe, np, torch, workloads, cfg, full, e2e_t,
-                                                fp64["k_evals_per_s"] if fp64 else None)
+            pd_out, extras["surrogate"] = run_surrogate(ffe, np, torch, workloads, cfg, full, e2e_t,
+                                                        fp64["k_evals_per_s"] if fp64 else None,
+                                                        diagram=not args.no_diagram)
+            if pd_out:
+                extras["phase_diagram"] = pd_out
 
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count

@@ -268,28 +268,39 @@ FFE_API ffe_status ffe_surrogate_train(ffe_surrogate* s, const float* x, const f
                                        int32_t epochs, int32_t batch, float lr,
                                        float* loss_per_epoch, void* stream);
 
-/* Phase scan guided by the surrogate (grid search only).  The surrogate
- * predicts every (q, h, T) line on the whole Delta grid; per (h, T) the
- * exact k-sum verifies q = 0 and the q_keep lines of lowest predicted
- * minimum, each on `window` grid points around its predicted minimum plus
- * Delta = 0 (with the FP64 re-evaluation and label passes of
- * ffe_phase_scan).  Lines whose verified minimum lies on an inner window
- * edge are re-run on the whole grid.  Unverified (pruned) lines are not
- * evaluated: they are reported with idx_star 0, flags FFE_FLAG_LOWER |
- * FFE_FLAG_PRUNED and the Delta = 0 value of the q = 0 line at the same
- * (h, T); a line whose minimum is its Delta = 0 point never decides a label,
- * so pruning changes a label only where the exact minimum of a pruned q
- * would have beaten the kept ones.  Outputs as in ffe_phase_scan (idx_star
- * in grid indices). */
+/* Phase scan guided by the surrogate, grid or golden-section search.  The
+ * surrogate predicts every (q, h, T) line on a Delta grid (the search grid;
+ * 256 points on [lo, hi] for golden); per (h, T) the exact k-sum verifies
+ * q = 0 and the q_keep lines of lowest predicted minimum, each on a window
+ * of `window` grid points around its predicted minimum, with Delta = 0 as
+ * the reference (with the FP64 re-evaluation and label passes of
+ * ffe_phase_scan).  Grid: the window's grid points.  Golden: the window is
+ * the initial bracket and takes as many fewer reductions as reach the full
+ * search's final bracket width.  An (h, T) point with a line whose verified
+ * minimum lies on an inner window edge (or that `margin` flags) is scanned
+ * again with that line over the whole range.  Unverified (pruned) lines are
+ * not evaluated: they are reported with idx_star 0 (grid) or -1 (golden),
+ * flags FFE_FLAG_LOWER | FFE_FLAG_PRUNED and the Delta = 0 value of the
+ * q = 0 line at the same (h, T); a line whose minimum is its Delta = 0 point
+ * never decides a label, so pruning changes a label only where the exact
+ * minimum of a pruned q would have beaten the kept ones.  Outputs as in
+ * ffe_phase_scan. */
 typedef struct {
   int32_t window;       /* grid points per verified line, 2..n               */
   int32_t q_keep;       /* q values kept per (h, T) besides q = 0            */
-  int32_t reserved[2];  /* must be 0                                         */
+  double margin;        /* >= 0, |t1| per site: a kept line whose predicted
+                           minimum is in the window at Delta = lo but which has
+                           a second predicted basin outside it with
+                           condensation energy below +margin (the basins may
+                           swap within the surrogate's error, as at a
+                           first-order transition) is searched over the
+                           whole range instead; 0: never               */
 } ffe_guide;
 typedef struct {
   double k_evals;       /* exact k-point evaluations done                    */
   double k_evals_full;  /* those of the unguided grid scan                   */
-  int64_t lines_kept, lines_pruned, fallbacks;
+  int64_t lines_kept, lines_pruned;
+  int64_t fallbacks;    /* kept lines searched over the whole range          */
   double rms_error;     /* RMS of predicted - exact condensation energy per
                            site, (Omega(Delta) - Omega(0))/N^2, on the
                            verified window points                            */

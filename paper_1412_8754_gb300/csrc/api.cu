@@ -681,6 +681,7 @@ static void fill_scan_golden(ffe_plan* p, const ffe_scan* sc) {
       std::memset(&gs, 0, sizeof gs);
       gs.lo = sc->lo;
       gs.hi = sc->hi;
+      gs.x0 = sc->lo;
       p->golden0.push_back(gs);
     }
     out += g.n_out;

@@ -31,6 +31,8 @@ constexpr int kMaxBatchesPerItem = 16;
 constexpr int kFlagRescored = 1;  // values of include/ffe.h FFE_FLAG_*
 constexpr int kFlagEdge = 2;
 constexpr int kFlagLower = 4;
+constexpr int kFlagBracketLo = 16;  // golden, window bracket: lower end never moved (internal)
+constexpr int kLineAlias = 1;       // Line::pad bit: line without outputs of its own
 constexpr float kLn2f = 0.693147180559945309f;
 
 struct ModelParams {

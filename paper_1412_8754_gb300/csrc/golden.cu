@@ -5,9 +5,10 @@
 // minimum can be bracketed instead.  Every line keeps a bracket [a, b] with
 // interior points x1 = a + (1-phi)(b-a), x2 = a + phi(b-a), phi = (sqrt5-1)/2;
 // it keeps [a, x2] when Omega(x1) <= Omega(x2), else [x1, b], and evaluates
-// one new interior point per reduction.  Delta = lo is evaluated too (it is
-// the normal state).  The result is the lowest Omega seen, ties to the
-// smaller Delta.  All lines advance together: one k-sum launch evaluates the
+// one new interior point per reduction.  A reference point x0 is evaluated
+// first: the normal state Delta = lo, or Delta = 0 when the bracket is a
+// window [lo, hi] inside the range.  The result is the lowest Omega seen,
+// ties to the smaller Delta.  All lines advance together: one k-sum launch evaluates the
 // pending Delta of every line.  While the two interior points are far apart
 // (more than 1 % of the range), a decision whose two FP32 values lie within
 // their error bounds is taken on FP64 re-evaluations instead.
@@ -38,6 +39,22 @@ __global__ void golden_kernel(int mode, const Line* __restrict__ lines, int n_li
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= n_lines) return;
   const Line L = lines[l];
+  if (L.pad & kLineAlias) {  // no outputs of its own: never a candidate
+    if (mode == kGoldenFinish) {
+      LineResult r;
+      r.delta_star = 0.0;
+      r.omega_star = NAN;
+      r.eb_star = 0.0;
+      r.omega_lo = NAN;
+      r.eb_lo = 0.0;
+      r.delta_lo = 0.0;
+      r.out_star = L.out0;
+      r.idx_star = -1;
+      r.flags = kFlagLower;
+      res[l] = r;
+    }
+    return;
+  }
   const int64_t o = L.out0;
   const int64_t e = L.delta0;
   GoldenState s = gs[l];
@@ -45,15 +62,16 @@ __global__ void golden_kernel(int mode, const Line* __restrict__ lines, int n_li
     case kGoldenInit:
       s.a = s.lo;
       s.b = s.hi;
+      if (!(s.wide > 0.0)) s.wide = kWideRel * (s.hi - s.lo);
       s.x1 = s.a + (1.0 - kPhi) * (s.b - s.a);
       s.x2 = s.a + kPhi * (s.b - s.a);
       s.side = 0;
-      set_delta(delta, d2f, e, s.lo);
+      set_delta(delta, d2f, e, s.x0);
       break;
     case kGoldenLo:
       s.flo = omega[o];
       s.eblo = ebound[o];
-      s.xb = s.lo;
+      s.xb = s.x0;
       s.fb = s.flo;
       s.ebb = s.eblo;
       set_delta(delta, d2f, e, s.x1);
@@ -73,7 +91,7 @@ __global__ void golden_kernel(int mode, const Line* __restrict__ lines, int n_li
       // Only a decision between interior points far apart (possibly different
       // basins) is worth FP64: close points lie in one basin, where either
       // choice keeps the minimum inside the bracket to within the error band.
-      if (fabs(s.f1 - s.f2) <= s.eb1 + s.eb2 && (s.x2 - s.x1) > kWideRel * (s.hi - s.lo)) {
+      if (fabs(s.f1 - s.f2) <= s.eb1 + s.eb2 && (s.x2 - s.x1) > s.wide) {
         Rescore r;
         r.group = L.group;
         r.dst = l;
@@ -123,11 +141,11 @@ __global__ void golden_kernel(int mode, const Line* __restrict__ lines, int n_li
       }
       break;
     case kGoldenMarkFinal:
-      // The best point against Delta = lo (the normal state wins exact ties).
-      // A bracket whose lower end never left lo has converged onto lo: its
-      // best interior point differs from lo by O(x^2) and lo is taken
-      // directly (kGoldenFinish); otherwise a near tie is settled in FP64.
-      if (s.a != s.lo && s.xb != s.lo && fabs(s.fb - s.flo) <= s.ebb + s.eblo) {
+      // The best point against the reference x0 (the normal state wins exact
+      // ties).  A bracket whose lower end never left lo = x0 has converged
+      // onto x0: its best interior point differs from x0 by O(x^2) and x0 is
+      // taken directly (kGoldenFinish); otherwise a near tie is settled in FP64.
+      if (!(s.a == s.lo && s.lo == s.x0) && s.xb != s.x0 && fabs(s.fb - s.flo) <= s.ebb + s.eblo) {
         Rescore r;
         r.group = L.group;
         r.dst = l;
@@ -140,16 +158,16 @@ __global__ void golden_kernel(int mode, const Line* __restrict__ lines, int n_li
         }
         if (s.eblo > 0.0) {
           r.kind = 6;
-          r.delta = s.lo;
+          r.delta = s.x0;
           const int pos = atomicAdd(n_req, 1);
           if (pos < cap) req[pos] = r;
         }
       }
       return;
     case kGoldenFinish: {
-      const bool onto_lo = s.a == s.lo && fabs(s.fb - s.flo) <= s.ebb + s.eblo;
-      if (s.xb != s.lo && (s.flo <= s.fb || onto_lo)) {
-        s.xb = s.lo;
+      const bool onto_lo = s.a == s.lo && s.lo == s.x0 && fabs(s.fb - s.flo) <= s.ebb + s.eblo;
+      if (s.xb != s.x0 && (s.flo <= s.fb || onto_lo)) {
+        s.xb = s.x0;
         s.fb = s.flo;
         s.ebb = s.eblo;
       }
@@ -159,12 +177,13 @@ __global__ void golden_kernel(int mode, const Line* __restrict__ lines, int n_li
       r.eb_star = s.ebb;
       r.omega_lo = s.flo;
       r.eb_lo = s.eblo;
-      r.delta_lo = s.lo;
+      r.delta_lo = s.x0;
       r.out_star = o;
       r.idx_star = -1;
       int f = 0;
-      if (s.xb == s.lo) f |= kFlagLower;
+      if (s.xb == s.x0) f |= kFlagLower;
       if (s.b == s.hi) f |= kFlagEdge;
+      if (s.a == s.lo && s.lo != s.x0) f |= kFlagBracketLo;
       r.flags = f;
       res[l] = r;
       return;

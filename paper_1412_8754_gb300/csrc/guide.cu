@@ -1,14 +1,16 @@
 // guide.cu -- phase scan guided by the learned surrogate.
 //
-// A grid scan (Alg. 1) evaluates every (q, h, T) line on the whole Delta
-// grid.  Guided, the surrogate first predicts the condensation energy of
-// every line on the whole grid (tensor-core inference); per (h, T) only
-// q = 0 and the q_keep lines with the lowest predicted minimum are verified,
-// each on a window of `window` grid points around its predicted minimum plus
-// Delta = 0, by the exact k-sum (same kernels, same FP64 re-evaluation of
-// near ties, same label passes as the full scan).  A line whose verified
-// minimum sits on an inner edge of its window is re-run on the whole grid.
-// The exact values on the window points also measure the surrogate's error.
+// A full scan (Alg. 1) searches every (q, h, T) line over the whole Delta
+// range.  Guided, the surrogate first predicts the condensation energy of
+// every line on a Delta grid (tensor-core inference); per (h, T) only q = 0
+// and the q_keep lines with the lowest predicted minimum are verified by the
+// exact k-sum, each on a window of `window` grid points around its predicted
+// minimum, with Delta = 0 as the reference (same kernels, same FP64
+// re-evaluation of near ties, same label passes as the full scan).  A grid
+// scan evaluates the window's grid points; a golden-section scan brackets
+// the window and needs fewer reductions for the same final bracket width.
+// Where a verified minimum sits on an inner edge of its window, the (h, T)
+// point is scanned again with that line over the whole range.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -58,26 +60,44 @@ __global__ void guide_argmin_kernel(const float* __restrict__ y, int n_lines, in
   }
 }
 
+// Copies the prediction rows of the listed lines next to each other.
+__global__ void guide_gather_kernel(const float* __restrict__ y, const int32_t* __restrict__ rows, int n_rows, int n,
+                                    float* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n_rows * n) return;
+  const int r = (int)(i / n), j = (int)(i - (int64_t)r * n);
+  out[i] = y[(int64_t)rows[r] * n + j];
+}
+
 namespace {
 
+constexpr int kGuideGrid = 256;  // prediction grid of a golden-section scan
+constexpr double kGuidePhi = 0.61803398874989484820;
+
 struct LineSpec {
-  std::vector<int> grid_idx;  // grid index of each output, grid_idx[0] == 0 (Delta = 0)
-  bool alias = false;         // not evaluated: reads the q = 0 line's Delta = 0 output
+  std::vector<int> grid_idx;    // grid search: grid index of each output, grid_idx[0] == 0
+  double wlo = 0.0, whi = 0.0;  // golden search: bracket
+  bool alias = false;           // not evaluated: reads the q = 0 line's reference output
 };
 
-// A scan-shaped plan whose lines carry explicit grid-index lists: one LIST
-// group per q, lines q-major (the label passes expect that order).  A group's
-// h list holds only the h values of its evaluated lines.  An alias line is a
-// one-point line on the q = 0 line's Delta = 0 output: its minimum is its
-// lower end, so it never competes for a label and costs no k-sum work.
-void fill_explicit(ffe_plan* p, const ffe_scan* sc, int q0, const std::vector<double>& grid,
-                   const std::vector<LineSpec>& spec) {
-  const int n_pts = sc->n_h * sc->n_T;
+// A scan-shaped plan over the points `pts` (indices ih * n_T + it of the
+// scan) whose lines carry explicit Delta lists (grid) or brackets (golden):
+// one LIST group per q, lines q-major (the label passes expect that order),
+// spec[q * pts.size() + j].  A group's h list holds only the h values of its
+// evaluated lines.  An alias line points at the q = 0 line's first output
+// (grid: Delta = 0): its minimum is its lower end, so it never competes for
+// a label and costs no k-sum work.
+void fill_explicit(ffe_plan* p, const ffe_scan* sc, int q0, const std::vector<int>& pts, int golden_steps,
+                   const std::vector<double>& grid, const std::vector<LineSpec>& spec) {
+  const int n_sub = (int)pts.size();
+  const bool golden = golden_steps > 0;
   p->layout = kLayoutList;
   p->n_q = sc->n_q;
-  p->n_pts = n_pts;
+  p->n_pts = n_sub;
+  p->golden_steps = golden_steps;
   p->q_is_zero.assign(sc->n_q, 0);
-  p->lines.assign((size_t)sc->n_q * n_pts, Line{});
+  p->lines.assign((size_t)sc->n_q * n_sub, Line{});
+  if (golden) p->golden0.assign((size_t)sc->n_q * n_sub, GoldenState{});
   int64_t out = 0;
   std::vector<int> h_local(sc->n_h);
   for (int q = 0; q < sc->n_q; ++q) {
@@ -95,10 +115,8 @@ void fill_explicit(ffe_plan* p, const ffe_scan* sc, int q0, const std::vector<do
     p->q_is_zero[q] = (sc->qx[q] == 0.0 && sc->qy[q] == 0.0) ? 1 : 0;
     std::fill(h_local.begin(), h_local.end(), -1);
     int n_hq = 0;
-    for (int pt = 0; pt < n_pts; ++pt) {
-      const int ih = pt / sc->n_T;
-      if (!spec[(size_t)q * n_pts + pt].alias && h_local[ih] < 0) h_local[ih] = 0;
-    }
+    for (int j = 0; j < n_sub; ++j)
+      if (!spec[(size_t)q * n_sub + j].alias) h_local[pts[j] / sc->n_T] = 0;
     for (int ih = 0; ih < sc->n_h; ++ih)
       if (h_local[ih] == 0) {
         h_local[ih] = n_hq++;
@@ -106,21 +124,32 @@ void fill_explicit(ffe_plan* p, const ffe_scan* sc, int q0, const std::vector<do
       }
     g.n_h = n_hq;
     int n_out = 0;
-    for (int pt = 0; pt < n_pts; ++pt) {
-      const LineSpec& ls = spec[(size_t)q * n_pts + pt];
+    for (int j = 0; j < n_sub; ++j) {
+      const size_t l = (size_t)q * n_sub + j;
+      const LineSpec& ls = spec[l];
       if (ls.alias) continue;
-      const int ih = pt / sc->n_T, it = pt % sc->n_T;
-      Line& L = p->lines[(size_t)q * n_pts + pt];
+      const int ih = pts[j] / sc->n_T, it = pts[j] % sc->n_T;
+      Line& L = p->lines[l];
       L.out0 = out + n_out;
       L.stride = 1;
-      L.count = (int32_t)ls.grid_idx.size();
+      L.count = golden ? 1 : (int32_t)ls.grid_idx.size();
       L.group = q;
       L.pad = 0;
       L.delta0 = g.delta_off + n_out;
       L.ht = g.ht_off + n_out;
-      for (int gi : ls.grid_idx) {
-        p->delta.push_back(grid[gi]);
+      if (golden) {
+        p->delta.push_back(sc->lo);
         p->ht.push_back(HT{sc->h[ih], sc->T[it], h_local[ih], 0});
+        GoldenState& gs = p->golden0[l];
+        gs.lo = ls.wlo;
+        gs.hi = ls.whi;
+        gs.x0 = sc->lo;
+        gs.wide = 1e-2 * (sc->hi - sc->lo);  // basins judged on the whole range, as in the full scan
+      } else {
+        for (int gi : ls.grid_idx) {
+          p->delta.push_back(grid[gi]);
+          p->ht.push_back(HT{sc->h[ih], sc->T[it], h_local[ih], 0});
+        }
       }
       n_out += L.count;
     }
@@ -133,32 +162,39 @@ void fill_explicit(ffe_plan* p, const ffe_scan* sc, int q0, const std::vector<do
     out += n_out;
   }
   for (int q = 0; q < sc->n_q; ++q)
-    for (int pt = 0; pt < n_pts; ++pt)
-      if (spec[(size_t)q * n_pts + pt].alias) {
-        Line L = p->lines[(size_t)q0 * n_pts + pt];
+    for (int j = 0; j < n_sub; ++j)
+      if (spec[(size_t)q * n_sub + j].alias) {
+        Line L = p->lines[(size_t)q0 * n_sub + j];
         L.count = 1;
-        p->lines[(size_t)q * n_pts + pt] = L;
+        L.pad = kLineAlias;
+        p->lines[(size_t)q * n_sub + j] = L;
       }
   p->n_out = out;
 }
 
-ffe_status run_explicit(ffe_context* ctx, const ffe_scan* sc, int q0, const std::vector<double>& grid,
-                        const std::vector<LineSpec>& spec, cudaStream_t s, std::vector<ffe_result>& res,
-                        std::vector<int8_t>& labels, std::vector<int32_t>& best, std::vector<double>* omega,
-                        double* k_evals) {
-  ffe_plan* p = plan_new(ctx, kPlanScanGrid);
-  fill_explicit(p, sc, q0, grid, spec);
+struct PassResult {
+  std::vector<ffe_result> res;  // [n_q][pts.size()]
+  std::vector<int8_t> labels;
+  std::vector<int32_t> best;
+  std::vector<double> omega;    // grid search: every output
+};
+
+ffe_status run_explicit(ffe_context* ctx, const ffe_scan* sc, int q0, const std::vector<int>& pts, int golden_steps,
+                        const std::vector<double>& grid, const std::vector<LineSpec>& spec, cudaStream_t s,
+                        PassResult& out, double* k_evals) {
+  ffe_plan* p = plan_new(ctx, golden_steps > 0 ? kPlanScanGolden : kPlanScanGrid);
+  fill_explicit(p, sc, q0, pts, golden_steps, grid, spec);
   ffe_status st = plan_configure(ctx, p);
   if (st == FFE_OK) st = plan_finish(ctx, p, false);
   if (st == FFE_OK) st = plan_run(ctx, p, s);
-  const int n_pts = sc->n_h * sc->n_T;
-  res.assign((size_t)sc->n_q * n_pts, ffe_result{});
-  labels.assign(n_pts, 0);
-  best.assign(n_pts, -1);
-  if (st == FFE_OK) st = fetch_scan(ctx, p, res.data(), labels.data(), best.data(), s);
-  if (st == FFE_OK && omega) {
-    omega->resize(p->n_out);
-    cudaError_t e = cudaMemcpyAsync(omega->data(), p->d_omega, p->n_out * sizeof(double), cudaMemcpyDeviceToHost, s);
+  const int n_sub = (int)pts.size();
+  out.res.assign((size_t)sc->n_q * n_sub, ffe_result{});
+  out.labels.assign(n_sub, 0);
+  out.best.assign(n_sub, -1);
+  if (st == FFE_OK) st = fetch_scan(ctx, p, out.res.data(), out.labels.data(), out.best.data(), s);
+  if (st == FFE_OK && golden_steps == 0) {
+    out.omega.resize(p->n_out);
+    cudaError_t e = cudaMemcpyAsync(out.omega.data(), p->d_omega, p->n_out * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) st = cuda_fail(ctx, e, "fetch omega");
   }
@@ -176,12 +212,15 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
                                          const ffe_guide* guide, ffe_result* per_point, int8_t* labels_out,
                                          int32_t* best_q_out, ffe_guide_stats* stats, void* stream) {
   if (!ctx || !sur || !sc || !guide) return FFE_EINVAL;
-  if (sc->search != FFE_SEARCH_GRID) return set_err(ctx, "guided scans use the grid search"), FFE_EINVAL;
-  if (sc->N < 2 || sc->N > 8192 || sc->N % 2 || sc->n_q < 1 || sc->n_h < 1 || sc->n_T < 1 || sc->n < 2 ||
-      sc->n > 65536 || !(sc->lo == 0.0) || !(sc->hi > sc->lo))
+  const bool golden = sc->search == FFE_SEARCH_GOLDEN;
+  if (sc->search != FFE_SEARCH_GRID && !golden) return set_err(ctx, "unknown search kind"), FFE_EINVAL;
+  if (sc->N < 2 || sc->N > 8192 || sc->N % 2 || sc->n_q < 1 || sc->n_h < 1 || sc->n_T < 1 || !(sc->lo == 0.0) ||
+      !(sc->hi > sc->lo) || (!golden && (sc->n < 2 || sc->n > 65536)) || (golden && (sc->n < 1 || sc->n > 200)))
     return set_err(ctx, "guided scan: invalid scan"), FFE_EINVAL;
-  if (guide->window < 2 || guide->window > sc->n || guide->q_keep < 0)
-    return set_err(ctx, "guided scan: window in [2, n], q_keep >= 0"), FFE_EINVAL;
+  // G: points of the prediction grid (the search grid itself for a grid scan)
+  const int G = golden ? kGuideGrid : sc->n;
+  if (guide->window < 2 || guide->window > G || guide->q_keep < 0)
+    return set_err(ctx, "guided scan: window in [2, grid points], q_keep >= 0"), FFE_EINVAL;
   int q0 = -1;
   for (int q = 0; q < sc->n_q; ++q) {
     if (!std::isfinite(sc->qx[q]) || !std::isfinite(sc->qy[q])) return set_err(ctx, "q not finite"), FFE_EINVAL;
@@ -191,11 +230,11 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
   for (int i = 0; i < sc->n_T; ++i)
     if (!(sc->T[i] > 0.0)) return set_err(ctx, "T must be > 0"), FFE_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  const int n = sc->n, n_pts = sc->n_h * sc->n_T, n_lines = sc->n_q * n_pts;
-  std::vector<double> grid(n);
-  linspace(sc->lo, sc->hi, n, grid.data());
+  const int n_pts = sc->n_h * sc->n_T, n_lines = sc->n_q * n_pts;
+  std::vector<double> grid(G);
+  linspace(sc->lo, sc->hi, G, grid.data());
 
-  // 1. predictions of every line on the whole grid, and their argmin
+  // 1. predictions of every line on the grid, and their argmin
   std::vector<float4> qht(n_lines);
   for (int q = 0; q < sc->n_q; ++q)
     for (int pt = 0; pt < n_pts; ++pt)
@@ -205,143 +244,261 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
   float4 *d_qht = nullptr, *d_x = nullptr;
   float *d_grid = nullptr, *d_y = nullptr, *d_ymin = nullptr;
   int32_t* d_idx = nullptr;
-  const int64_t n_pred = (int64_t)n_lines * n;
+  const int64_t n_pred = (int64_t)n_lines * G;
   cudaError_t e = cudaMalloc(&d_qht, n_lines * sizeof(float4));
-  if (e == cudaSuccess) e = cudaMalloc(&d_grid, n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&d_grid, G * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&d_x, n_pred * sizeof(float4));
   if (e == cudaSuccess) e = cudaMalloc(&d_y, n_pred * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&d_ymin, n_lines * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&d_idx, n_lines * sizeof(int32_t));
   std::vector<int32_t> idx(n_lines);
-  std::vector<float> ymin(n_lines), ypred(n_pred);
+  std::vector<float> ymin(n_lines);
   ffe_status st = FFE_OK;
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_qht, qht.data(), n_lines * sizeof(float4), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_grid, gridf.data(), n * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_grid, gridf.data(), G * sizeof(float), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
-    guide_inputs_kernel<<<(int)((n_pred + 255) / 256), 256, 0, s>>>(d_qht, d_grid, n_lines, n, d_x);
+    guide_inputs_kernel<<<(int)((n_pred + 255) / 256), 256, 0, s>>>(d_qht, d_grid, n_lines, G, d_x);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) st = surrogate_infer_device(sur, reinterpret_cast<const float*>(d_x), n_pred, d_y, s);
   if (e == cudaSuccess && st == FFE_OK) {
-    guide_argmin_kernel<<<(int)(((int64_t)n_lines * 32 + 255) / 256), 256, 0, s>>>(d_y, n_lines, n, d_idx, d_ymin);
+    guide_argmin_kernel<<<(int)(((int64_t)n_lines * 32 + 255) / 256), 256, 0, s>>>(d_y, n_lines, G, d_idx, d_ymin);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && st == FFE_OK) e = cudaMemcpyAsync(idx.data(), d_idx, n_lines * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && st == FFE_OK) e = cudaMemcpyAsync(ymin.data(), d_ymin, n_lines * 4, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && st == FFE_OK) e = cudaMemcpyAsync(ypred.data(), d_y, n_pred * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && st == FFE_OK) e = cudaStreamSynchronize(s);
-  for (void* ptr : {(void*)d_qht, (void*)d_grid, (void*)d_x, (void*)d_y, (void*)d_ymin, (void*)d_idx})
-    if (ptr) cudaFree(ptr);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "surrogate predictions");
-  if (st != FFE_OK) return st;
 
   // 2. which lines to verify, and on which window
   const int w = guide->window;
   std::vector<char> kept(n_lines, 0);
   std::vector<int> wstart(n_lines, 0);
-  for (int pt = 0; pt < n_pts; ++pt) {
+  std::vector<int32_t> kept_rows;
+  std::vector<int64_t> row_of(n_lines, -1);
+  std::vector<float> ypred;  // prediction rows of the kept lines
+  if (e == cudaSuccess && st == FFE_OK) {
     std::vector<int> order;
-    for (int q = 0; q < sc->n_q; ++q)
-      if (q != q0) order.push_back(q);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-      return ymin[(size_t)a * n_pts + pt] < ymin[(size_t)b * n_pts + pt];
-    });
-    kept[(size_t)q0 * n_pts + pt] = 1;
-    for (int k = 0; k < (int)order.size() && k < guide->q_keep; ++k) kept[(size_t)order[k] * n_pts + pt] = 1;
+    for (int pt = 0; pt < n_pts; ++pt) {
+      order.clear();
+      for (int q = 0; q < sc->n_q; ++q)
+        if (q != q0) order.push_back(q);
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return ymin[(size_t)a * n_pts + pt] < ymin[(size_t)b * n_pts + pt];
+      });
+      kept[(size_t)q0 * n_pts + pt] = 1;
+      for (int k = 0; k < (int)order.size() && k < guide->q_keep; ++k) kept[(size_t)order[k] * n_pts + pt] = 1;
+    }
+    for (int l = 0; l < n_lines; ++l)
+      if (kept[l]) {
+        row_of[l] = (int64_t)kept_rows.size();
+        kept_rows.push_back(l);
+      }
+    // the kept lines' prediction rows, gathered on the device into d_x's storage
+    const int n_rows = (int)kept_rows.size();
+    int32_t* d_rows = reinterpret_cast<int32_t*>(d_qht);  // n_rows <= n_lines
+    float* d_rowsy = reinterpret_cast<float*>(d_x);       // n_rows * G <= n_pred
+    ypred.resize((size_t)n_rows * G);
+    e = cudaMemcpyAsync(d_rows, kept_rows.data(), n_rows * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+      guide_gather_kernel<<<(int)(((int64_t)n_rows * G + 255) / 256), 256, 0, s>>>(d_y, d_rows, n_rows, G, d_rowsy);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ypred.data(), d_rowsy, ypred.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  for (void* ptr : {(void*)d_qht, (void*)d_grid, (void*)d_x, (void*)d_y, (void*)d_ymin, (void*)d_idx})
+    if (ptr) cudaFree(ptr);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "surrogate predictions");
+  if (st != FFE_OK) return st;
+
+  // golden: a window of w grid points spans (w - 1)/(G - 1) of the range;
+  // that many fewer reductions reach the full scan's final bracket width
+  int steps_w = 0;
+  if (golden) {
+    const double ratio = (double)(G - 1) / (double)(w - 1);
+    steps_w = std::max(1, (int)std::ceil(sc->n - std::log(ratio) / std::log(1.0 / kGuidePhi) - 1e-9));
   }
   std::vector<LineSpec> spec(n_lines);
+  std::vector<char> redo(n_lines, 0);  // searched over the whole range
+  const double n2 = (double)sc->N * (double)sc->N;
+  const float ys = surrogate_y_scale(sur);
   for (int l = 0; l < n_lines; ++l) {
     if (!kept[l]) {
       spec[l].grid_idx = {0};
       spec[l].alias = true;
       continue;
     }
-    const int i0 = std::max(0, std::min(n - w, idx[l] - w / 2));
+    const int i0 = std::max(0, std::min(G - w, idx[l] - w / 2));
     wstart[l] = i0;
-    if (i0 > 0) spec[l].grid_idx.push_back(0);
-    for (int i = i0; i < i0 + w; ++i) spec[l].grid_idx.push_back(i);
+    if (golden) {
+      spec[l].wlo = grid[i0];
+      spec[l].whi = grid[i0 + w - 1];
+    } else {
+      if (i0 > 0) spec[l].grid_idx.push_back(0);
+      for (int i = i0; i < i0 + w; ++i) spec[l].grid_idx.push_back(i);
+    }
+    // a predicted normal state with a second predicted basin close to it
+    if (i0 == 0 && guide->margin > 0.0) {
+      const float* yrow = ypred.data() + (size_t)row_of[l] * G;
+      float y2 = INFINITY;
+      for (int j = w; j < G; ++j) y2 = std::min(y2, yrow[j]);
+      if ((double)y2 * ys < guide->margin) redo[l] = 1;
+    }
   }
+  int64_t ambiguous = 0;
+  for (int l = 0; l < n_lines; ++l) ambiguous += redo[l];
+
+  // points with a line searched over the whole range go to the second pass
+  std::vector<int> pos_in(n_pts, -1), pts1, again;
+  auto point_has_redo = [&](int pt) {
+    for (int q = 0; q < sc->n_q; ++q)
+      if (redo[(size_t)q * n_pts + pt]) return true;
+    return false;
+  };
+  for (int pt = 0; pt < n_pts; ++pt)
+    if (!point_has_redo(pt)) {
+      pos_in[pt] = (int)pts1.size();
+      pts1.push_back(pt);
+    }
+  const int n1 = (int)pts1.size();
+  auto sub_spec = [&](const std::vector<int>& pts, bool whole_for_redo) {
+    std::vector<LineSpec> out((size_t)sc->n_q * pts.size());
+    for (int q = 0; q < sc->n_q; ++q)
+      for (size_t j = 0; j < pts.size(); ++j) {
+        const size_t l = (size_t)q * n_pts + pts[j];
+        LineSpec ls = spec[l];
+        if (whole_for_redo && redo[l]) {
+          if (golden) {
+            ls.wlo = sc->lo;
+            ls.whi = sc->hi;
+          } else {
+            ls.grid_idx.resize(G);
+            std::iota(ls.grid_idx.begin(), ls.grid_idx.end(), 0);
+          }
+        }
+        out[(size_t)q * pts.size() + j] = ls;
+      }
+    return out;
+  };
 
   // 3. exact verification of the windows
   double k_evals = 0.0;
-  std::vector<ffe_result> res;
-  std::vector<int8_t> labels;
-  std::vector<int32_t> best;
-  std::vector<double> omega;
-  st = run_explicit(ctx, sc, q0, grid, spec, s, res, labels, best, &omega, &k_evals);
-  if (st != FFE_OK) return st;
-
-  // 4. surrogate error on the verified points; lines to re-run on the whole grid
-  const double n2 = (double)sc->N * (double)sc->N;
-  const float ys = surrogate_y_scale(sur);
-  double se = 0.0;
-  int64_t n_se = 0, fallbacks = 0, n_kept = 0;
-  std::vector<int64_t> off(n_lines + 1, 0);
-  for (int l = 0; l < n_lines; ++l) off[l + 1] = off[l] + (spec[l].alias ? 0 : (int64_t)spec[l].grid_idx.size());
-  std::vector<char> redo(n_lines, 0);
-  for (int l = 0; l < n_lines; ++l) {
-    if (!kept[l]) continue;
-    ++n_kept;
-    const std::vector<int>& gi = spec[l].grid_idx;
-    const double om0 = omega[off[l]];
-    int wbest = -1;  // position of the lowest value among the window points
-    for (size_t j = (wstart[l] > 0 ? 1 : 0); j < gi.size(); ++j) {
-      const double om = omega[off[l] + j];
-      const double exact = (om - om0) / n2;
-      const double pred = (double)ypred[(size_t)l * n + gi[j]] * ys;
-      se += (exact - pred) * (exact - pred);
-      ++n_se;
-      if (wbest < 0 || om < omega[off[l] + wbest]) wbest = (int)j;
-    }
-    const int lo_pos = wstart[l] > 0 ? 1 : 0;
-    const int hi_pos = (int)gi.size() - 1;
-    const bool lower_edge = wbest == lo_pos && gi[lo_pos] > 0;
-    const bool upper_edge = wbest == hi_pos && gi[hi_pos] < n - 1;
-    if (lower_edge || upper_edge) {
-      redo[l] = 1;
-      ++fallbacks;
-    }
-  }
-
-  // 5. the whole grid for those lines (the others keep Delta = 0 and their minimum)
-  if (fallbacks > 0) {
-    std::vector<LineSpec> spec2(n_lines);
-    for (int l = 0; l < n_lines; ++l) {
-      if (redo[l]) {
-        spec2[l].grid_idx.resize(n);
-        std::iota(spec2[l].grid_idx.begin(), spec2[l].grid_idx.end(), 0);
-      } else {
-        spec2[l].grid_idx = {0};
-        spec2[l].alias = !kept[l];
-        const int i = res[l].idx_star;
-        if (kept[l] && i > 0) spec2[l].grid_idx.push_back(spec[l].grid_idx[i]);
-      }
-    }
-    spec = spec2;
-    st = run_explicit(ctx, sc, q0, grid, spec, s, res, labels, best, nullptr, &k_evals);
+  PassResult r1;
+  std::vector<LineSpec> spec1;
+  if (n1 > 0) {
+    spec1 = sub_spec(pts1, false);
+    st = run_explicit(ctx, sc, q0, pts1, steps_w, grid, spec1, s, r1, &k_evals);
     if (st != FFE_OK) return st;
   }
 
-  // 6. results in grid indices
+  // 4. surrogate error at the verified points; lines whose minimum sits on an inner window edge
+  double se = 0.0;
+  int64_t n_se = 0, fallbacks = 0, n_kept = 0;
+  std::vector<int64_t> off((size_t)sc->n_q * n1 + 1, 0);
+  for (size_t m = 0; m < (size_t)sc->n_q * n1; ++m)
+    off[m + 1] = off[m] + (spec1[m].alias || golden ? 0 : (int64_t)spec1[m].grid_idx.size());
+  for (int l = 0; l < n_lines; ++l) n_kept += kept[l];
+  for (int q = 0; q < sc->n_q; ++q)
+    for (int j = 0; j < n1; ++j) {
+      const size_t l = (size_t)q * n_pts + pts1[j], m = (size_t)q * n1 + j;
+      if (!kept[l]) continue;
+      const float* yrow = ypred.data() + (size_t)row_of[l] * G;
+      bool lower_edge = false, upper_edge = false;
+      if (golden) {
+        // prediction at Delta*: linear interpolation on the prediction grid
+        const ffe_result& r = r1.res[m];
+        const double u = (r.delta_star - sc->lo) / (sc->hi - sc->lo) * (G - 1);
+        const int i = std::max(0, std::min(G - 2, (int)std::floor(u)));
+        const double t = std::min(1.0, std::max(0.0, u - i));
+        const double pred = ((1.0 - t) * yrow[i] + t * yrow[i + 1]) * ys;
+        const double exact = (r.omega_star - r.omega_lo) / n2;
+        se += (exact - pred) * (exact - pred);
+        ++n_se;
+        lower_edge = (r.flags & kFlagBracketLo) != 0;
+        upper_edge = (r.flags & FFE_FLAG_EDGE) && spec[l].whi < sc->hi;
+      } else {
+        const std::vector<int>& gi = spec[l].grid_idx;
+        const double om0 = r1.omega[off[m]];
+        int wbest = -1;  // position of the lowest value among the window points
+        for (size_t k = (wstart[l] > 0 ? 1 : 0); k < gi.size(); ++k) {
+          const double om = r1.omega[off[m] + k];
+          const double exact = (om - om0) / n2;
+          const double pred = (double)yrow[gi[k]] * ys;
+          se += (exact - pred) * (exact - pred);
+          ++n_se;
+          if (wbest < 0 || om < r1.omega[off[m] + wbest]) wbest = (int)k;
+        }
+        const int lo_pos = wstart[l] > 0 ? 1 : 0;
+        const int hi_pos = (int)gi.size() - 1;
+        lower_edge = wbest == lo_pos && gi[lo_pos] > 0;
+        upper_edge = wbest == hi_pos && gi[hi_pos] < G - 1;
+      }
+      if (lower_edge || upper_edge) {
+        redo[l] = 1;
+        ++fallbacks;
+      }
+    }
+
+  // 5. the second pass: every point with a line to search over the whole range
+  std::vector<int> pos_in2(n_pts, -1);
+  for (int pt = 0; pt < n_pts; ++pt)
+    if (point_has_redo(pt)) {
+      pos_in2[pt] = (int)again.size();
+      again.push_back(pt);
+    }
+  const int n2p = (int)again.size();
+  PassResult r2;
+  std::vector<LineSpec> spec2;
+  if (n2p > 0) {
+    spec2 = sub_spec(again, true);
+    st = run_explicit(ctx, sc, q0, again, golden ? sc->n : 0, grid, spec2, s, r2, &k_evals);
+    if (st != FFE_OK) return st;
+  }
+
+  // 6. results: per line from the pass that scanned its point last; grid indices
   for (int l = 0; l < n_lines; ++l) {
-    ffe_result r = res[l];
-    const int loc = r.idx_star;
-    r.idx_star = (loc >= 0 && loc < (int)spec[l].grid_idx.size()) ? spec[l].grid_idx[loc] : -1;
-    r.flags &= ~(FFE_FLAG_EDGE | FFE_FLAG_LOWER);
-    if (r.idx_star == 0) r.flags |= FFE_FLAG_LOWER;
-    if (r.idx_star == n - 1) r.flags |= FFE_FLAG_EDGE;
-    if (!kept[l]) r.flags |= FFE_FLAG_PRUNED;
+    const int q = l / n_pts, pt = l % n_pts;
+    const bool second = pos_in2[pt] >= 0;
+    const int j = second ? pos_in2[pt] : pos_in[pt];
+    const int nsub = second ? n2p : n1;
+    const size_t m = (size_t)q * nsub + j;
+    const LineSpec& ls = second ? spec2[m] : spec1[m];
+    const PassResult& pr = second ? r2 : r1;
+    ffe_result r = pr.res[m];
+    if (!kept[l]) {  // the q = 0 line's reference value
+      const ffe_result& rn = pr.res[(size_t)q0 * nsub + j];
+      r.delta_star = sc->lo;
+      r.omega_star = rn.omega_lo;
+      r.omega_lo = rn.omega_lo;
+      r.err_bound = 0.0;
+      r.idx_star = golden ? -1 : 0;
+      r.flags = FFE_FLAG_LOWER | FFE_FLAG_PRUNED;
+    } else if (golden) {
+      const bool at_hi = (r.flags & FFE_FLAG_EDGE) && ls.whi == sc->hi;
+      r.flags &= ~(FFE_FLAG_EDGE | kFlagBracketLo);
+      if (at_hi) r.flags |= FFE_FLAG_EDGE;
+    } else {
+      const int loc = r.idx_star;
+      r.idx_star = (loc >= 0 && loc < (int)ls.grid_idx.size()) ? ls.grid_idx[loc] : -1;
+      r.flags &= ~(FFE_FLAG_EDGE | FFE_FLAG_LOWER);
+      if (r.idx_star == 0) r.flags |= FFE_FLAG_LOWER;
+      if (r.idx_star == G - 1) r.flags |= FFE_FLAG_EDGE;
+    }
     if (per_point) per_point[l] = r;
   }
-  if (labels_out) std::memcpy(labels_out, labels.data(), n_pts);
-  if (best_q_out) std::memcpy(best_q_out, best.data(), n_pts * sizeof(int32_t));
+  for (int pt = 0; pt < n_pts; ++pt) {
+    const bool second = pos_in2[pt] >= 0;
+    if (labels_out) labels_out[pt] = second ? r2.labels[pos_in2[pt]] : r1.labels[pos_in[pt]];
+    if (best_q_out) best_q_out[pt] = second ? r2.best[pos_in2[pt]] : r1.best[pos_in[pt]];
+  }
   if (stats) {
     std::memset(stats, 0, sizeof *stats);
     stats->k_evals = k_evals;
-    stats->k_evals_full = n2 * (double)n_lines * (double)n;
+    stats->k_evals_full = n2 * (double)n_lines * (golden ? 3.0 + sc->n : (double)sc->n);
     stats->lines_kept = n_kept;
     stats->lines_pruned = n_lines - n_kept;
-    stats->fallbacks = fallbacks;
+    stats->fallbacks = fallbacks + ambiguous;
     stats->rms_error = n_se > 0 ? std::sqrt(se / (double)n_se) : 0.0;
     stats->mlp_flops = 2.0 * (double)n_pred * (4.0 * 128 + 2 * 128.0 * 128 + 128.0);
   }

@@ -99,8 +99,12 @@ struct GoldenState {
   double f1, f2;        // Omega at x1, x2
   double eb1, eb2;      // their FP32 error bounds (0 once FP64)
   double xb, fb, ebb;   // lowest Omega seen so far (ties -> smaller Delta)
-  double flo, eblo;     // Omega at Delta = lo
-  double lo, hi;        // the search range
+  double flo, eblo;     // Omega at the reference point x0
+  double lo, hi;        // the search range (bracket at the start)
+  double x0;            // reference point, evaluated first: the normal state
+                        // Delta = 0; equal to lo except for a window bracket
+  double wide;          // interior points farther apart than this may lie in
+                        // different basins (0: 1 % of hi - lo)
   int32_t side;         // 0: the pending evaluation is x1, 1: x2
   int32_t pad;
 };

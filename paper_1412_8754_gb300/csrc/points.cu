@@ -183,6 +183,7 @@ void fill_min_golden(ffe_plan* p, const ffe_param* ps, int64_t n) {
       std::memset(&gs, 0, sizeof gs);
       gs.lo = q.lo;
       gs.hi = q.hi;
+      gs.x0 = q.lo;
       p->golden0[idx[j]] = gs;
     }
     g.n_h = (int32_t)hmap.size();

@@ -99,7 +99,7 @@ _SIGNATURES = [
 
 
 class ffe_guide(ctypes.Structure):
-    _fields_ = [("window", ctypes.c_int32), ("q_keep", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+    _fields_ = [("window", ctypes.c_int32), ("q_keep", ctypes.c_int32), ("margin", ctypes.c_double)]
 
 
 class ffe_guide_stats(ctypes.Structure):
@@ -108,14 +108,15 @@ class ffe_guide_stats(ctypes.Structure):
                 ("mlp_flops", ctypes.c_double)]
 
 
-def ffe_surrogate_scan(ctx, sur, N, qx, qy, h, T, n=256, lo=0.0, hi=0.2, window=16, q_keep=3, stream=None):
-    """Guided grid scan; returns (per_point, labels, best_q, stats dict)."""
-    sc, keep = make_scan(N, qx, qy, h, T, FFE_SEARCH_GRID, n, lo, hi)
+def ffe_surrogate_scan(ctx, sur, N, qx, qy, h, T, n=256, lo=0.0, hi=0.2, window=16, q_keep=3, stream=None,
+                       search=FFE_SEARCH_GRID, margin=0.0):
+    """Guided scan (grid: n points; golden: n reductions); returns (per_point, labels, best_q, stats dict)."""
+    sc, keep = make_scan(N, qx, qy, h, T, search, n, lo, hi)
     npts = sc.n_h * sc.n_T
     res = np.zeros((sc.n_q, npts), dtype=RESULT_DTYPE)
     labels = np.zeros(npts, dtype=np.int8)
     best = np.zeros(npts, dtype=np.int32)
-    g = ffe_guide(window, q_keep, (ctypes.c_int32 * 2)(0, 0))
+    g = ffe_guide(window, q_keep, float(margin))
     st = ffe_guide_stats()
     _check(ctx, lib().ffe_surrogate_scan(ctx, sur.handle, ctypes.byref(sc), ctypes.byref(g), _ptr(res),
                                          _ptr(labels), _ptr(best), ctypes.byref(st), _stream(stream)))

@@ -49,3 +49,10 @@ def fit(ctx: ffe.Context, x, y, epochs=30, batch=4096, lr=2e-3, seed=0, y_scale=
     s = ffe.Surrogate(ctx, workloads.SURROGATE_SHIFT, workloads.SURROGATE_SCALE, ys, initial_params(seed))
     losses = s.train(x[perm], y[perm], epochs=epochs, batch=batch, lr=lr)
     return s, losses
+
+
+def rms_error(s: "ffe.Surrogate", x, y, n=65536, seed=0) -> float:
+    """RMS of prediction - target over a seeded subset of (x, y), in the target's units."""
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(len(x), size=min(n, len(x)), replace=False)
+    return float(np.sqrt(np.mean((s.predict(x[pick]).astype(np.float64) - y[pick]) ** 2)))

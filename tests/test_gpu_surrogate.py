@@ -114,6 +114,28 @@ def test_guided_scan_with_full_window_is_the_full_scan(ctx):
     assert st["k_evals"] == st["k_evals_full"]
 
 
+def test_guided_golden_with_whole_range_window_is_the_golden_scan(ctx):
+    """window = the whole prediction grid, every q kept: each line's bracket is [lo, hi] with the
+    full number of reductions, so the guided golden scan is the golden scan."""
+    from paper_1412_8754_gb300 import surrogate as sg
+
+    N, U, steps = 32, 4.0, 12
+    qx = np.array([0.0, 0.2, 0.4])
+    h = np.array([0.0, 0.05, 0.1])
+    T = np.array([0.004, 0.015])
+    with ffe.Context(prec=ffe.FFE_FP32C, U=U) as c:
+        s = ffe.Surrogate(c, mlp.SHIFT, mlp.SCALE, Y_SCALE, sg.initial_params(4))
+        res, lab, best, st = ffe.ffe_surrogate_scan(c.handle, s, N, qx, np.zeros(3), h, T, n=steps, window=256,
+                                                    q_keep=2, search=ffe.FFE_SEARCH_GOLDEN)
+        ref, rlab, rbest = c.phase_scan(N, qx, np.zeros(3), h, T, search=ffe.FFE_SEARCH_GOLDEN, n=steps)
+        s.close()
+    assert np.array_equal(lab, rlab) and np.array_equal(best, rbest)
+    np.testing.assert_array_equal(res["delta_star"], ref["delta_star"])
+    np.testing.assert_allclose(res["omega_star"], ref["omega_star"], rtol=0, atol=1e-9 * N * N)
+    assert st["fallbacks"] == 0 and st["lines_pruned"] == 0
+    assert st["k_evals"] == st["k_evals_full"]
+
+
 def test_trained_surrogate_guides_the_scan():
     """A surrogate trained on the library's own free energies cuts the exact work of a
     grid scan while finding the full scan's minima and labels; an untrained one does not."""
@@ -136,6 +158,10 @@ def test_trained_surrogate_guides_the_scan():
             res, lab, best, st = ffe.ffe_surrogate_scan(c.handle, s, N, qx, np.zeros_like(qx), h, T, n=n,
                                                         window=8, q_keep=2)
             out[name] = (res, lab, st)
+        # golden-section form: windows bracketed, fewer reductions, labels of the full golden scan
+        gref, glab_ref, _ = c.phase_scan(N, qx, np.zeros_like(qx), h, T, search=ffe.FFE_SEARCH_GOLDEN, n=20)
+        gres, glab, _, gst = ffe.ffe_surrogate_scan(c.handle, trained, N, qx, np.zeros_like(qx), h, T, n=20,
+                                                    window=16, q_keep=2, search=ffe.FFE_SEARCH_GOLDEN)
         trained.close()
         untrained.close()
     assert losses[-1] < 0.1 * losses[0]
@@ -151,6 +177,14 @@ def test_trained_surrogate_guides_the_scan():
     # the trained network predicts the exact condensation energies better than chance
     assert st["rms_error"] < out["untrained"][2]["rms_error"], (st, out["untrained"][2])
     assert np.mean(found | (ref["idx_star"] == 0)) >= 0.5
+    assert np.mean(glab == glab_ref) >= 0.9, (glab, glab_ref)
+    assert gst["k_evals"] < 0.5 * gst["k_evals_full"], gst
+    gpruned = (gres["flags"] & ffe.FFE_FLAG_PRUNED) != 0
+    assert gpruned.sum() == gst["lines_pruned"] > 0
+    # a kept line whose minimum lies inside its window finds the full search's minimum
+    both = ~gpruned & ((gref["flags"] & ffe.FFE_FLAG_LOWER) == 0) & ((gres["flags"] & ffe.FFE_FLAG_LOWER) == 0)
+    assert both.sum() > 0
+    np.testing.assert_allclose(gres["delta_star"][both], gref["delta_star"][both], atol=2e-3)
 
 
 def trained_scale(y):
