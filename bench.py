@@ -179,7 +179,8 @@ def run_surrogate(ffe, np, torch, workloads, cfg, ref, full_s, fp64_rate, epochs
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
         rms_train = sg.rms_error(sur, x, y)
-        pd_out = run_phase_diagram(ffe, np, torch, workloads, ctx, sur, 3.0 * rms_train, fp64_rate) if diagram else None
+        pd_out = run_phase_diagram(ffe, np, torch, workloads, ctx, sur, 3.0 * rms_train, fp64_rate,
+                                   cfg["U"]) if diagram else None
         sur.close()
     dt = statistics.median(times)
     kept = (res["flags"] & ffe.FFE_FLAG_PRUNED) == 0
@@ -203,7 +204,7 @@ def run_surrogate(ffe, np, torch, workloads, cfg, ref, full_s, fp64_rate, epochs
     }
 
 
-def run_phase_diagram(ffe, np, torch, workloads, ctx, sur, margin, fp64_rate):
+def run_phase_diagram(ffe, np, torch, workloads, ctx, sur, margin, fp64_rate, U):
     """N=2048, 64 q x 64 h x 64 T, golden-section (24 reductions): the full FP32+comp scan, the
     surrogate-guided scan, and the FP64 kernel on a sub-grid, with their labels compared."""
     pd = workloads.phase_diagram()
@@ -223,7 +224,7 @@ def run_phase_diagram(ffe, np, torch, workloads, ctx, sur, margin, fp64_rate):
     t_guided = time.perf_counter() - t0
     # FP64 on a 2 h x 4 T sub-grid with every q (labels need all q of a point)
     hs, ts = pd["h"][:2], pd["T"][:4]
-    with ffe.Context(prec=ffe.FFE_FP64, U=2.0) as c64:
+    with ffe.Context(prec=ffe.FFE_FP64, U=U) as c64:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, lab64, best64 = c64.phase_scan(pd["N"], pd["qx"], pd["qy"], hs, ts, **kw)
@@ -233,7 +234,7 @@ def run_phase_diagram(ffe, np, torch, workloads, ctx, sur, margin, fp64_rate):
     k64 = float(pd["N"]) ** 2 * len(pd["qx"]) * len(sub) * (3 + pd["n"])
     return {
         "workload": (f"N={pd['N']}, {len(pd['qx'])} q x {len(pd['h'])} h x {len(pd['T'])} T, golden "
-                     f"{pd['n']} reductions on [0, 0.2], U=2"),
+                     f"{pd['n']} reductions on [0, 0.2], U={U}"),
         "fp32c_full": {"seconds": t_full, "points_per_s": len(pd["qx"]) * n_pts / t_full,
                        "k_evals_per_s": k_full / t_full,
                        "labels": [int((flab == i).sum()) for i in range(3)]},
@@ -270,12 +271,13 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-diagram", action="store_true", help="skip the N=2048 phase diagram (~70 s)")
+    ap.add_argument("--U", type=float, default=2.0, help="pairing U of every workload (2 = the stated one)")
     args = ap.parse_args()
 
     from paper_1412_8754_gb300 import workloads
 
     cfg = workloads.fflo_scan(N=args.N, n_q=args.n_q)
-    cfg["U"] = 2.0
+    cfg["U"] = args.U
     ws, rank, local = dist_env()
 
     if args.impl == "reference":
