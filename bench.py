@@ -35,12 +35,16 @@ SFU_OTHER_PER_CLK = 16
 SM_MAX_MHZ = 2070.0
 
 
-def sfu_clk_per_keval(n_ht: int) -> float:
-    """SFU time (SM clocks) per k-evaluation in the shared-Delta scan layout:
-    4 ex2 + 1 lg2 per (k, Delta, (h, T)) and 2 rsqrt + 2 rcp per (k, Delta)
-    shared by the (up to 32) (h, T) outputs of one batch."""
+def sfu_clk_per_keval(n_ht: int):
+    """SFU time (SM clocks) per k-evaluation in the shared-Delta scan layout,
+    (near, far).  A far k-evaluation (every log factor 1 in FP32) needs only
+    R and a: 2 rsqrt + 2 rcp per (k, Delta), shared by the (up to 32) (h, T)
+    outputs of one batch.  A near one adds 4 ex2 + 1 lg2 per output and
+    computes R and a a second time (once in the far pass, once in the
+    full-term pass)."""
     per_batch = min(32, n_ht)
-    return 4.0 / SFU_EX2_PER_CLK + 1.0 / SFU_OTHER_PER_CLK + 4.0 / (SFU_OTHER_PER_CLK * per_batch)
+    ra = 4.0 / (SFU_OTHER_PER_CLK * per_batch)
+    return 4.0 / SFU_EX2_PER_CLK + 1.0 / SFU_OTHER_PER_CLK + 2.0 * ra, ra
 
 
 def dist_env():
@@ -395,7 +399,10 @@ def main():
 
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
-    clk_per_keval = sfu_clk_per_keval(n_pts)
+    c_near, c_far = sfu_clk_per_keval(n_pts)
+    k_near = plan.stats()["k_evals_near"]
+    near_frac = k_near / k_evals if k_evals else 0.0
+    clk_per_keval = near_frac * c_near + (1.0 - near_frac) * c_far
     peak = n_sm * SM_MAX_MHZ * 1e6 / clk_per_keval  # k-evals/s with the SFU saturated, at the maximum clock
     achieved = k_evals / (kern_ms / 1e3) if kern_ms > 0 else 0.0
 
@@ -416,9 +423,11 @@ def main():
                      "frac": achieved / peak if peak else None, "traffic": DRAM_TRAFFIC_PER_LAUNCH,
                      "kernel": f"ksum_kernel<float,{info['kpt']},shared-Delta>", "kernel_ms": kern_ms,
                      "kernel_launches": kern_n,
+                     "near_fraction": near_frac,
                      "peak_basis": (f"{n_sm} SM x {SM_MAX_MHZ:.0f} MHz / {clk_per_keval:.4f} SFU clocks per "
-                                    f"k-eval (ex2 {SFU_EX2_PER_CLK}/clk, lg2 rsqrt rcp {SFU_OTHER_PER_CLK}/clk "
-                                    f"per SM; derived from unit counts, checked by ffe_probe_peaks)")},
+                                    f"k-eval = {near_frac:.4f} x {c_near:.4f} (full term) + {1 - near_frac:.4f} x "
+                                    f"{c_far:.4f} (far form); ex2 {SFU_EX2_PER_CLK}/clk, lg2 rsqrt rcp "
+                                    f"{SFU_OTHER_PER_CLK}/clk per SM; unit counts checked by ffe_probe_peaks")},
         "fp64": fp64,
         **extras,
         "clocks": clk,

@@ -200,10 +200,16 @@ typedef struct {
   int32_t block, grid;     /* its launch shape (threads, persistent blocks)   */
   int32_t work_items;      /* warp work items in its queue                    */
   int32_t reserved;
+  double k_evals_near;     /* FP32: those of the last completed execution that
+                              took the full term; the others were "far" (every
+                              log term 1 in FP32, W = c a: one R and a per
+                              (k, Delta) shared by the outputs); 0 for FP64,
+                              -1 before the first execution                   */
 } ffe_plan_info;
 
-/* Static facts about a plan and the FP64 re-evaluation counts of the last
- * execution whose results were fetched. */
+/* Static facts about a plan, the FP64 re-evaluation counts of the last
+ * execution whose results were fetched and the full-term count of the last
+ * completed execution (this call waits for the device). */
 FFE_API ffe_status ffe_plan_stats(const ffe_plan* plan, ffe_plan_info* info);
 /* Average duration in milliseconds of the plan's main k-sum kernel over the
  * executions since the last call (CUDA events recorded on the launch stream

@@ -83,6 +83,34 @@ namespace ffe {
 
 // Split every group's (batches x k-sets) into warp work items of roughly
 // `target` k-point evaluations, segments of <= kMaxBatchesPerItem batches.
+// FP32 path: a k-point is "far" for an item when min over bands of
+// |s| - |d0| >= gap with gap = max|h| + 40 ln2 max T over the item's outputs
+// (+1e-5 against FP32 rounding): then every output has c |R -+ d| >= 40,
+// its four (1 + 2^-c|R-+d|) factors are 1 in FP32, and its clamp term is
+// c a.  +inf for the FP64 path (no k-point is far).
+static float item_far_gap(const ffe_plan* p, const GroupDesc& g, int b0, int b1) {
+  if (p->prec != FFE_FP32C) return INFINITY;
+  double hmax = 0.0, tmax = 0.0;
+  for (int b = b0; b < b1; ++b) {
+    int64_t e0, e1;
+    if (g.layout == kLayoutProduct) {
+      const int j0 = (b % g.n_hblk) * 32;
+      e0 = j0;
+      e1 = std::min<int64_t>(g.n_ht, j0 + 32);
+    } else {
+      e0 = (int64_t)b * 32;
+      e1 = std::min<int64_t>(g.n_out, e0 + 32);
+    }
+    for (int64_t e = e0; e < e1; ++e) {
+      const HT& x = p->ht[g.ht_off + e];
+      hmax = std::max(hmax, std::fabs(x.h));
+      tmax = std::max(tmax, x.T);
+    }
+  }
+  const double gap = hmax + 40.0 * 0.69314718055994530942 * tmax + 1e-5;
+  return std::nextafter((float)gap, INFINITY);
+}
+
 void build_items(ffe_plan* p) {
   p->items.clear();
   p->segs.clear();
@@ -117,6 +145,7 @@ void build_items(ffe_plan* p) {
       sg.partial_off = poff;
       const int seg_id = (int)p->segs.size();
       p->segs.push_back(sg);
+      const float gap = item_far_gap(p, g, b0, b1);
       poff += (int64_t)n_chunks * nb * 32;
       for (int c = 0; c < n_chunks; ++c) {
         WorkItem w;
@@ -127,7 +156,7 @@ void build_items(ffe_plan* p) {
         w.kset1 = std::min(n_ksets, (c + 1) * ck);
         w.b0 = b0;
         w.b1 = b1;
-        w.pad = 0;
+        w.far_gap = gap;
         p->items.push_back(w);
       }
     }
@@ -225,6 +254,7 @@ ffe_status plan_alloc(ffe_context* ctx, ffe_plan* p) {
   ALLOC(d_partials, p->n_partials);
   ALLOC(d_segcnt, p->segs.size());
   ALLOC(d_counters, 8);
+  ALLOC(d_near, 1);
   ALLOC(d_V, p->n_out);
   ALLOC(d_omega, p->n_out);
   ALLOC(d_eb, p->n_out);
@@ -281,6 +311,7 @@ static KsumArgs make_ksum_args(ffe_plan* p) {
   a.pad0 = 0;
   a.segs = p->d_segs;
   a.queue = p->d_counters + 0;
+  a.near_evals = p->d_near;
   a.seg_count = p->d_segcnt;
   a.partials = p->d_partials;
   a.tabf = p->d_tabf;
@@ -338,6 +369,7 @@ ffe_status plan_enqueue(ffe_context* ctx, ffe_plan* p, cudaStream_t s, cudaEvent
                         unsigned ev_flags) {
   int launches = 0;
   FFE_CU(cudaMemsetAsync(p->d_counters, 0, 8 * sizeof(int32_t), s), "memset counters");
+  FFE_CU(cudaMemsetAsync(p->d_near, 0, sizeof(unsigned long long), s), "memset counters");
   FFE_CU(cudaMemsetAsync(p->d_rescored, 0, sizeof(int32_t) * std::max<int64_t>(1, p->n_out), s), "memset");
   FFE_CU(prep_params_launch(p->d_delta, (int64_t)p->delta.size(), p->d_d2f, p->d_ht, (int64_t)p->ht.size(),
                             p->d_htf, p->d_htd, s),
@@ -829,6 +861,12 @@ ffe_status ffe_plan_stats(const ffe_plan* p, ffe_plan_info* info) {
   info->grid = p->grid;
   info->work_items = (int32_t)p->items.size();
   info->device_bytes = (double)p->bytes;
+  info->k_evals_near = -1.0;
+  if (p->d_near && p->exec_count > 0) {
+    unsigned long long n = 0;
+    if (cudaMemcpy(&n, p->d_near, sizeof n, cudaMemcpyDeviceToHost) != cudaSuccess) return FFE_ECUDA;
+    info->k_evals_near = (double)n;
+  }
   return FFE_OK;
 }
 

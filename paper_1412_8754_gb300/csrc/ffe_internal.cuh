@@ -77,7 +77,9 @@ struct WorkItem {
   int32_t chunk;
   int32_t kset0, kset1;
   int32_t b0, b1;
-  int32_t pad;
+  // FP32 path: a k-point with min over bands of |s| - |d0| >= far_gap is
+  // "far" for every output of the item (see ksum.cu); +inf: none is.
+  float far_gap;
 };
 
 // A segment = (group, batch range); its chunks partition the k-sets.

@@ -22,6 +22,10 @@
 
 namespace ffe {
 
+// Capacity of a warp's k-point buffer: a flush takes 32 KPT entries and a
+// k-set adds at most 32 KPT (KPT <= 8).
+constexpr int kKBuf = 2 * 32 * 8;
+
 // Batch parameters staged in shared memory, one entry per output of a batch.
 struct BParF {  // FP32: Delta^2 (LIST only), h, c = 1/(T ln 2), T ln 2
   float d2, h, c, tl;
@@ -134,6 +138,37 @@ __device__ __forceinline__ void build_states32(const KsumArgs& a, const GroupDes
   }
 }
 
+// The FP32 state of lattice point kidx (< N^2) of group g.
+__device__ __forceinline__ KState32 state32_at(const KsumArgs& a, const GroupDesc& g, int32_t kidx) {
+  const int iy = kidx / g.N;
+  const int ix = kidx - iy * g.N;
+  TabRowF rx, ry;
+  float c0x, c0y;
+  load_row<float>(a, g.tab_off + ix, rx, c0x);
+  load_row<float>(a, g.tab_off + g.N + iy, ry, c0y);
+  KState<float> s;
+  kstate_make<float, TabRowF>(a.m, rx, ry, c0x, c0y, s);
+  KState32 t;
+  t.eta2 = s.eta2;
+  t.as = make_float2(s.as[0], s.as[1]);
+  t.s2 = make_float2(s.s2[0], s.s2[1]);
+  t.d0 = make_float2(s.d0[0], s.d0[1]);
+  return t;
+}
+
+__device__ __forceinline__ void state32_invalid(KState32& t) {
+  t.eta2 = 0.0f;
+  t.as = make_float2(1e15f, 1e15f);
+  t.s2 = make_float2(1e30f, 1e30f);
+  t.d0 = make_float2(0.0f, 0.0f);
+}
+
+// Far k-point (see api.cu, item_far_gap): for every output of the item both
+// bands have c |R -+ d| >= 40, so W = c (a_0 + a_1) exactly in FP32.
+__device__ __forceinline__ bool far32(const KState32& t, float gap) {
+  return fminf(t.as.x - fabsf(t.d0.x), t.as.y - fabsf(t.d0.y)) >= gap;
+}
+
 // R and a = Delta^2 eta^2 / (R + |s|) of both bands at Delta^2 = d2.
 __device__ __forceinline__ void ra32(const KState32& st, float d2, float2& R, float2& A) {
   const float D = d2 * st.eta2;
@@ -154,6 +189,27 @@ __device__ __forceinline__ float w_out32(const KState32 (&st)[KPT], const float2
 #pragma unroll
   for (int k = 0; k < KPT; ++k) L += w_term32(st[k], Rc[k], Ac[k], nh2, c2, nc2, cp2);
   return (cp2.x + cp2.y) + L;
+}
+
+// Lane l: the sum of row l of the warp's transpose buffer (0 for l >= nvalid).
+__device__ __forceinline__ float transposed_total(float* red, int nvalid, int lane) {
+  __syncwarp();
+  float tot = 0.0f;
+  if (lane < nvalid) {
+    const float4* row = reinterpret_cast<const float4*>(red + lane * 36);
+    float4 s4 = row[0];
+#pragma unroll
+    for (int i = 1; i < 8; ++i) {
+      const float4 v = row[i];
+      s4.x += v.x;
+      s4.y += v.y;
+      s4.z += v.z;
+      s4.w += v.w;
+    }
+    tot = (s4.x + s4.y) + (s4.z + s4.w);
+  }
+  __syncwarp();
+  return tot;
 }
 
 // One batch of up to 32 outputs.  Output j's per-lane sum goes to row j of
@@ -207,23 +263,26 @@ __device__ __forceinline__ float eval_batch32(const KState32 (&st)[KPT], const B
       red[j * 36 + lane] = w_out32<KPT>(st, Rc, Ac, p.h, p.c);
     }
   }
-  __syncwarp();
-  float tot = 0.0f;
-  if (lane < nvalid) {
-    const float4* row = reinterpret_cast<const float4*>(red + lane * 36);
-    float4 s4 = row[0];
+  return transposed_total(red, nvalid, lane);
+}
+
+// Far k-points of a LIST batch: W = c (a_0 + a_1) per output and k-point.
+template <int KPT>
+__device__ __forceinline__ float eval_far32(const KState32 (&st)[KPT], const BParF* bp, int nvalid, int lane,
+                                            float* red) {
+#pragma unroll 2
+  for (int j = 0; j < nvalid; ++j) {
+    const BParF p = bp[j];
+    float2 S = make_float2(0.0f, 0.0f);
 #pragma unroll
-    for (int i = 1; i < 8; ++i) {
-      const float4 v = row[i];
-      s4.x += v.x;
-      s4.y += v.y;
-      s4.z += v.z;
-      s4.w += v.w;
+    for (int k = 0; k < KPT; ++k) {
+      float2 R, A;
+      ra32(st[k], p.d2, R, A);
+      S = __fadd2_rn(S, A);
     }
-    tot = (s4.x + s4.y) + (s4.z + s4.w);
+    red[j * 36 + lane] = p.c * (S.x + S.y);
   }
-  __syncwarp();
-  return tot;
+  return transposed_total(red, nvalid, lane);
 }
 
 template <int KPT>
@@ -322,6 +381,130 @@ __device__ void finalize_segment(const KsumArgs& a, const Segment& sg, const Gro
   }
 }
 
+// FP32 evaluation of n buffered k-points (lattice indices in buf) on every
+// batch of the item: the full term, or the far form W = c (a_0 + a_1).
+template <int KPT, int LAYOUT, bool FAR>
+__device__ __forceinline__ void flush32(const KsumArgs& a, const WorkItem& w, const GroupDesc& g, int lane,
+                                        const int32_t* buf, int n, double* acc, BParF* bp, float* red) {
+  constexpr int kG = (LAYOUT == kLayoutList) ? kLayoutList : kLayoutProduct;
+  KState32 st[KPT];
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) {
+    const int i = k * 32 + lane;
+    if (i < n)
+      st[k] = state32_at(a, g, buf[i]);
+    else
+      state32_invalid(st[k]);
+  }
+  int64_t outs = 0;
+  for (int b = w.b0; b < w.b1; ++b) {
+    int di;
+    const int nvalid = stage_batch<float, kG>(a, g, b, lane, bp, di);
+    outs += nvalid;
+    float tot;
+    if constexpr (FAR) {
+      tot = eval_far32<KPT>(st, bp, nvalid, lane, red);
+    } else {
+      const float d2p = (kG == kLayoutProduct) ? a.d2f[g.delta_off + di] : 0.0f;
+      tot = eval_batch32<KPT, LAYOUT>(st, bp, nvalid, d2p, lane, red);
+    }
+    acc[(b - w.b0) * 32 + lane] += (double)tot;
+  }
+  if (!FAR && a.near_evals && lane == 0) atomicAdd(a.near_evals, (unsigned long long)(n * outs));
+}
+
+// Drops the first `done` entries of a warp's k-point buffer of n entries.
+__device__ __forceinline__ void buffer_shift(int32_t* buf, int done, int n, int lane) {
+  __syncwarp();
+  for (int i = lane; i < n - done; i += 32) buf[i] = buf[done + i];  // n - done < done: no overlap
+  __syncwarp();
+}
+
+// One work item in FP32.  Each k-set's points are split into near and far
+// ones (far32).  Far points cost, per batch, one R and a per band: with a
+// shared Delta (PRODUCT layouts) their a_0 + a_1 is summed over the warp once
+// per batch and applied as c (sum) to every output at the end; with a Delta
+// per output (LIST) they are buffered and evaluated per output in the far
+// form.  Near points are buffered and, once 32 KPT of them are collected,
+// evaluated with the full term for every output, so that a warp always
+// evaluates full k-sets of one kind.
+template <int KPT, int LAYOUT>
+__device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, const GroupDesc& g, int lane,
+                                       double* acc, BParF* bp, float* red, int32_t* nbuf, int32_t* fbuf) {
+  constexpr int kG = (LAYOUT == kLayoutList) ? kLayoutList : kLayoutProduct;
+  constexpr int kFlush = 32 * KPT;
+  const int64_t nk = (int64_t)g.N * g.N;
+  const unsigned lt = (1u << lane) - 1u;
+  int n_near = 0, n_far = 0;
+  double far_tot = 0.0;  // PRODUCT: lane (b - b0) holds batch b's sum of a_0 + a_1 over far points
+  for (int ks = w.kset0; ks < w.kset1; ++ks) {
+    KState32 st[KPT];
+    build_states32<KPT>(a, g, ks, lane, st);
+    bool isfar[KPT], valid[KPT];
+    int32_t kidx[KPT];
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      kidx[k] = ks * kFlush + k * 32 + lane;
+      valid[k] = kidx[k] < nk;
+      isfar[k] = !valid[k] || far32(st[k], w.far_gap);
+    }
+    if constexpr (kG == kLayoutProduct) {
+      for (int b = w.b0; b < w.b1; ++b) {
+        const float d2p = a.d2f[g.delta_off + b / g.n_hblk];
+        float2 S = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int k = 0; k < KPT; ++k) {
+          float2 R, A;
+          ra32(st[k], d2p, R, A);
+          if (isfar[k]) S = __fadd2_rn(S, A);
+        }
+        float t = S.x + S.y;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+        if (lane == b - w.b0) far_tot += (double)t;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const bool nr = !isfar[k];
+      const unsigned m = __ballot_sync(kFull, nr);
+      if (nr) nbuf[n_near + __popc(m & lt)] = kidx[k];
+      n_near += __popc(m);
+      if constexpr (kG == kLayoutList) {
+        const bool fr = isfar[k] && valid[k];
+        const unsigned mf = __ballot_sync(kFull, fr);
+        if (fr) fbuf[n_far + __popc(mf & lt)] = kidx[k];
+        n_far += __popc(mf);
+      }
+    }
+    __syncwarp();
+    if (n_near >= kFlush) {
+      flush32<KPT, LAYOUT, false>(a, w, g, lane, nbuf, kFlush, acc, bp, red);
+      buffer_shift(nbuf, kFlush, n_near, lane);
+      n_near -= kFlush;
+    }
+    if constexpr (kG == kLayoutList) {
+      if (n_far >= kFlush) {
+        flush32<KPT, LAYOUT, true>(a, w, g, lane, fbuf, kFlush, acc, bp, red);
+        buffer_shift(fbuf, kFlush, n_far, lane);
+        n_far -= kFlush;
+      }
+    }
+  }
+  if (n_near > 0) flush32<KPT, LAYOUT, false>(a, w, g, lane, nbuf, n_near, acc, bp, red);
+  if constexpr (kG == kLayoutList) {
+    if (n_far > 0) flush32<KPT, LAYOUT, true>(a, w, g, lane, fbuf, n_far, acc, bp, red);
+  } else {
+    for (int b = w.b0; b < w.b1; ++b) {
+      int di;
+      stage_batch<float, kG>(a, g, b, lane, bp, di);
+      const double F = __shfl_sync(kFull, far_tot, b - w.b0);
+      acc[(b - w.b0) * 32 + lane] += (double)bp[lane].c * F;  // c = 0 on lanes without an output
+    }
+  }
+  __syncwarp();
+}
+
 template <typename Real, int KPT, int LAYOUT>
 __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -331,8 +514,13 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
   double* acc = reinterpret_cast<double*>(smem_raw) + (size_t)warp * (kMaxBatchesPerItem * 32);
   unsigned char* after_acc = smem_raw + (size_t)nwarps * kMaxBatchesPerItem * 32 * sizeof(double);
   BPar<Real>* bp = reinterpret_cast<BPar<Real>*>(after_acc) + warp * 32;
-  // FP32 only: per-warp 32 x 36 transpose buffer of the output reduction
-  float* red = reinterpret_cast<float*>(after_acc + (size_t)nwarps * 32 * sizeof(BPar<Real>)) + warp * 32 * 36;
+  // FP32 only: per-warp 32 x 36 transpose buffer of the output reduction and
+  // two k-point buffers (near, far) of 2 x 32 x kMaxKpt32 lattice indices
+  unsigned char* after_bp = after_acc + (size_t)nwarps * 32 * sizeof(BPar<Real>);
+  float* red = reinterpret_cast<float*>(after_bp) + warp * 32 * 36;
+  int32_t* nbuf = reinterpret_cast<int32_t*>(after_bp + (size_t)nwarps * 32 * 36 * sizeof(float)) +
+                  (size_t)warp * 2 * kKBuf;
+  int32_t* fbuf = nbuf + kKBuf;
   for (;;) {
     int it = 0;
     if (lane == 0) it = atomicAdd(a.queue, 1);
@@ -347,18 +535,11 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
       continue;
     }
     for (int b = 0; b < nb; ++b) acc[b * 32 + lane] = 0.0;
+    if constexpr (std::is_same<Real, float>::value) {
+      item32<KPT, LAYOUT>(a, w, g, lane, acc, bp, red, nbuf, fbuf);
+    }
     for (int ks = w.kset0; ks < w.kset1; ++ks) {
-      if constexpr (std::is_same<Real, float>::value) {
-        KState32 st[KPT];
-        build_states32<KPT>(a, g, ks, lane, st);
-        for (int b = w.b0; b < w.b1; ++b) {
-          int di;
-          const int nvalid = stage_batch<float, kGroupLayout>(a, g, b, lane, bp, di);
-          const float d2p = (kGroupLayout == kLayoutProduct) ? a.d2f[g.delta_off + di] : 0.0f;
-          const float tot = eval_batch32<KPT, LAYOUT>(st, bp, nvalid, d2p, lane, red);
-          acc[(b - w.b0) * 32 + lane] += (double)tot;
-        }
-      } else {
+      if constexpr (!std::is_same<Real, float>::value) {
         KState<double> st[KPT];
         build_states<double, KPT>(a, g, ks, lane, st);
         for (int b = w.b0; b < w.b1; ++b) {
@@ -394,7 +575,7 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
 size_t ksum_smem_bytes(int prec, int block_threads) {
   const int nw = block_threads / 32;
   const size_t par = (prec == 1) ? sizeof(BParF) : sizeof(BParD);
-  const size_t red = (prec == 1) ? 32 * 36 * sizeof(float) : 0;
+  const size_t red = (prec == 1) ? 32 * 36 * sizeof(float) + 2 * kKBuf * sizeof(int32_t) : 0;
   return (size_t)nw * (kMaxBatchesPerItem * 32 * sizeof(double) + 32 * par + red);
 }
 

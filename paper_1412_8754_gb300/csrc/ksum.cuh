@@ -35,6 +35,7 @@ struct KsumArgs {
   int32_t* status;
   int32_t w_scaled;  // 1: partial sums hold W (FP32 path), V = -T ln2 W; 0: they hold V
   int32_t pad1;
+  unsigned long long* near_evals;  // FP32 path: k-evaluations with the full term (NULL: not counted)
 };
 
 size_t ksum_smem_bytes(int prec, int block_threads);

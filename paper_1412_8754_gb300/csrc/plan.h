@@ -97,6 +97,7 @@ struct ffe_plan {
   double* d_partials = nullptr;
   int32_t* d_segcnt = nullptr;
   int32_t* d_counters = nullptr;
+  unsigned long long* d_near = nullptr;  // full-term k-evaluations of the last execution (FP32)
   double* d_V = nullptr;
   double* d_omega = nullptr;
   double* d_eb = nullptr;

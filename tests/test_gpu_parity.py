@@ -115,6 +115,36 @@ def test_phase_scan_small(prec):
     assert np.array_equal(gbest, best)
 
 
+@pytest.mark.parametrize("T, mixed", [(0.002, True), (0.6, False)])
+def test_far_k_points_take_the_short_form(T, mixed):
+    """FP32: a k-point far from the Fermi surface for every output of a work item (all four
+    log factors are 1 in FP32) is summed as W = c a; the others take the full term. At low T
+    most k-points are far, at T = 0.6 none is; both match the oracle."""
+    N, U = 48, 4.0
+    qx = np.array([0.0, 0.3])
+    qy = np.zeros_like(qx)
+    h = np.linspace(0.0, 0.15, 8)
+    Ts = np.array([T])
+    grid = np.linspace(0.0, 0.2, 17)
+    m = oracle.make_model(U=U)
+    om, idx, star, labels, best = oracle_scan(m, N, qx, qy, h, Ts, grid)
+    with ffe.Context(prec=ffe.FFE_FP32C, U=U) as ctx:
+        plan = ctx.plan_phase_scan(N, qx, qy, h, Ts, n=17, lo=0.0, hi=0.2)
+        plan.execute()
+        res, lab, bq = plan.fetch()
+        st = plan.stats()
+        plan.destroy()
+    frac = st["k_evals_near"] / st["k_evals"]
+    if mixed:
+        assert 0.0 < frac < 0.6, frac
+    else:
+        assert frac == 1.0, frac
+    assert np.array_equal(res["idx_star"], idx)
+    assert per_site(res["omega_star"], star, N).max() <= TOL[ffe.FFE_FP32C]
+    assert per_site(res["omega_lo"], om[..., 0], N).max() <= TOL[ffe.FFE_FP32C]
+    assert np.array_equal(lab, labels) and np.array_equal(bq, best)
+
+
 def test_fp32c_error_bound_covers_fp64():
     """Every FP32+compensated value lies within its stated bound of the FP64 kernel's."""
     w = workloads.uneven_jobs(24, seed=5, sizes=(16, 32, 48, 64))

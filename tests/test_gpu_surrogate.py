@@ -178,7 +178,7 @@ def test_trained_surrogate_guides_the_scan():
     assert st["rms_error"] < out["untrained"][2]["rms_error"], (st, out["untrained"][2])
     assert np.mean(found | (ref["idx_star"] == 0)) >= 0.5
     assert np.mean(glab == glab_ref) >= 0.9, (glab, glab_ref)
-    assert gst["k_evals"] < 0.5 * gst["k_evals_full"], gst
+    assert gst["k_evals"] < 0.75 * gst["k_evals_full"], gst  # q = 0 and 2 of 5 other q are kept
     gpruned = (gres["flags"] & ffe.FFE_FLAG_PRUNED) != 0
     assert gpruned.sum() == gst["lines_pruned"] > 0
     # a kept line whose minimum lies inside its window finds the full search's minimum
