@@ -83,14 +83,18 @@ namespace ffe {
 
 // Split every group's (batches x k-sets) into warp work items of roughly
 // `target` k-point evaluations, segments of <= kMaxBatchesPerItem batches.
-// FP32 path: a k-point is "far" for an item when min over bands of
-// |s| - |d0| >= gap with gap = max|h| + 40 ln2 max T over the item's outputs
-// (+1e-5 against FP32 rounding): then every output has c |R -+ d| >= 40,
-// its four (1 + 2^-c|R-+d|) factors are 1 in FP32, and its clamp term is
-// c a.  +inf for the FP64 path (no k-point is far).
-static float item_far_gap(const ffe_plan* p, const GroupDesc& g, int b0, int b1) {
-  if (p->prec != FFE_FP32C) return INFINITY;
-  double hmax = 0.0, tmax = 0.0;
+// FP32 path: a k-point is "far" for an item when, with h in [hlo, hhi] and
+// T <= Tmax over the item's outputs, min over bands of
+// |s| - max(|d0 - hlo|, |d0 - hhi|) >= tgap = 40 ln2 Tmax (+1e-5 against FP32
+// rounding): then every output has c |R -+ d| >= 40, its four
+// (1 + 2^-c|R-+d|) factors are 1 in FP32, and its clamp term is c a.
+// tgap = +inf for the FP64 path (no k-point is far).
+static void item_far_window(const ffe_plan* p, const GroupDesc& g, int b0, int b1, WorkItem& w) {
+  w.far_hlo = 0.0f;
+  w.far_hhi = 0.0f;
+  w.far_tgap = INFINITY;
+  if (p->prec != FFE_FP32C) return;
+  double hlo = INFINITY, hhi = -INFINITY, tmax = 0.0;
   for (int b = b0; b < b1; ++b) {
     int64_t e0, e1;
     if (g.layout == kLayoutProduct) {
@@ -103,12 +107,16 @@ static float item_far_gap(const ffe_plan* p, const GroupDesc& g, int b0, int b1)
     }
     for (int64_t e = e0; e < e1; ++e) {
       const HT& x = p->ht[g.ht_off + e];
-      hmax = std::max(hmax, std::fabs(x.h));
+      hlo = std::min(hlo, x.h);
+      hhi = std::max(hhi, x.h);
       tmax = std::max(tmax, x.T);
     }
   }
-  const double gap = hmax + 40.0 * 0.69314718055994530942 * tmax + 1e-5;
-  return std::nextafter((float)gap, INFINITY);
+  if (!(hlo <= hhi)) return;
+  // float bounds that contain the FP64 ones
+  w.far_hlo = std::nextafter((float)hlo, -INFINITY);
+  w.far_hhi = std::nextafter((float)hhi, INFINITY);
+  w.far_tgap = std::nextafter((float)(40.0 * 0.69314718055994530942 * tmax + 1e-5), INFINITY);
 }
 
 void build_items(ffe_plan* p) {
@@ -145,7 +153,9 @@ void build_items(ffe_plan* p) {
       sg.partial_off = poff;
       const int seg_id = (int)p->segs.size();
       p->segs.push_back(sg);
-      const float gap = item_far_gap(p, g, b0, b1);
+      WorkItem proto;
+      std::memset(&proto, 0, sizeof proto);
+      item_far_window(p, g, b0, b1, proto);
       poff += (int64_t)n_chunks * nb * 32;
       for (int c = 0; c < n_chunks; ++c) {
         WorkItem w;
@@ -156,7 +166,10 @@ void build_items(ffe_plan* p) {
         w.kset1 = std::min(n_ksets, (c + 1) * ck);
         w.b0 = b0;
         w.b1 = b1;
-        w.far_gap = gap;
+        w.far_hlo = proto.far_hlo;
+        w.far_hhi = proto.far_hhi;
+        w.far_tgap = proto.far_tgap;
+        w.pad[0] = w.pad[1] = w.pad[2] = 0;
         p->items.push_back(w);
       }
     }
@@ -640,18 +653,21 @@ static void fill_scan_grid(ffe_plan* p, const ffe_scan* sc) {
     g.qy = sc->qy[q];
     p->q_is_zero[q] = (sc->qx[q] == 0.0 && sc->qy[q] == 0.0) ? 1 : 0;
     p->delta.insert(p->delta.end(), grid.begin(), grid.end());
-    for (int ih = 0; ih < sc->n_h; ++ih)
-      for (int it = 0; it < sc->n_T; ++it) p->ht.push_back(HT{sc->h[ih], sc->T[it], ih, 0});
+    // (h, T) entries T-major, so that a batch of 32 shares one T where it can
+    // (point pt = ih n_T + it is entry it n_h + ih); lines stay in point order
+    for (int it = 0; it < sc->n_T; ++it)
+      for (int ih = 0; ih < sc->n_h; ++ih) p->ht.push_back(HT{sc->h[ih], sc->T[it], ih, 0});
     p->hlist.insert(p->hlist.end(), sc->h, sc->h + sc->n_h);
     for (int pt = 0; pt < n_pts; ++pt) {
+      const int e = (pt % sc->n_T) * sc->n_h + pt / sc->n_T;
       Line L;
-      L.out0 = out + pt;
+      L.out0 = out + e;
       L.stride = n_pts;
       L.count = sc->n;
       L.group = q;
       L.pad = 0;
       L.delta0 = g.delta_off;
-      L.ht = g.ht_off + pt;
+      L.ht = g.ht_off + e;
       p->lines.push_back(L);
     }
     out += g.n_out;
@@ -695,19 +711,24 @@ static void fill_scan_golden(ffe_plan* p, const ffe_scan* sc) {
     g.qx = sc->qx[q];
     g.qy = sc->qy[q];
     p->q_is_zero[q] = (sc->qx[q] == 0.0 && sc->qy[q] == 0.0) ? 1 : 0;
-    for (int ih = 0; ih < sc->n_h; ++ih)
-      for (int it = 0; it < sc->n_T; ++it) p->ht.push_back(HT{sc->h[ih], sc->T[it], ih, 0});
+    // outputs T-major, so that a batch of 32 shares one T where it can
+    // (point pt = ih n_T + it is output it n_h + ih); lines stay in point order
+    for (int it = 0; it < sc->n_T; ++it)
+      for (int ih = 0; ih < sc->n_h; ++ih) {
+        p->ht.push_back(HT{sc->h[ih], sc->T[it], ih, 0});
+        p->delta.push_back(sc->lo);
+      }
     p->hlist.insert(p->hlist.end(), sc->h, sc->h + sc->n_h);
     for (int pt = 0; pt < n_pts; ++pt) {
-      p->delta.push_back(sc->lo);
+      const int e = (pt % sc->n_T) * sc->n_h + pt / sc->n_T;
       Line L;
-      L.out0 = out + pt;
+      L.out0 = out + e;
       L.stride = 1;
       L.count = 1;
       L.group = q;
       L.pad = 0;
-      L.delta0 = g.delta_off + pt;
-      L.ht = g.ht_off + pt;
+      L.delta0 = g.delta_off + e;
+      L.ht = g.ht_off + e;
       p->lines.push_back(L);
       GoldenState gs;
       std::memset(&gs, 0, sizeof gs);

@@ -77,9 +77,12 @@ struct WorkItem {
   int32_t chunk;
   int32_t kset0, kset1;
   int32_t b0, b1;
-  // FP32 path: a k-point with min over bands of |s| - |d0| >= far_gap is
-  // "far" for every output of the item (see ksum.cu); +inf: none is.
-  float far_gap;
+  // FP32 path: every output of the item has h in [far_hlo, far_hhi]; a
+  // k-point with min over bands of |s| - max(|d0 - far_hlo|, |d0 - far_hhi|)
+  // >= far_tgap is "far" for all of them (see ksum.cu); far_tgap = +inf:
+  // no k-point is.
+  float far_hlo, far_hhi, far_tgap;
+  int32_t pad[3];
 };
 
 // A segment = (group, batch range); its chunks partition the k-sets.

@@ -163,10 +163,12 @@ __device__ __forceinline__ void state32_invalid(KState32& t) {
   t.d0 = make_float2(0.0f, 0.0f);
 }
 
-// Far k-point (see api.cu, item_far_gap): for every output of the item both
-// bands have c |R -+ d| >= 40, so W = c (a_0 + a_1) exactly in FP32.
-__device__ __forceinline__ bool far32(const KState32& t, float gap) {
-  return fminf(t.as.x - fabsf(t.d0.x), t.as.y - fabsf(t.d0.y)) >= gap;
+// Far k-point (see api.cu, item_far_window): for every output of the item
+// both bands have c |R -+ d| >= 40, so W = c (a_0 + a_1) exactly in FP32.
+__device__ __forceinline__ bool far32(const KState32& t, const WorkItem& w) {
+  const float dx = fmaxf(fabsf(t.d0.x - w.far_hlo), fabsf(t.d0.x - w.far_hhi));
+  const float dy = fmaxf(fabsf(t.d0.y - w.far_hlo), fabsf(t.d0.y - w.far_hhi));
+  return fminf(t.as.x - dx, t.as.y - dy) >= w.far_tgap;
 }
 
 // R and a = Delta^2 eta^2 / (R + |s|) of both bands at Delta^2 = d2.
@@ -446,7 +448,7 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
     for (int k = 0; k < KPT; ++k) {
       kidx[k] = ks * kFlush + k * 32 + lane;
       valid[k] = kidx[k] < nk;
-      isfar[k] = !valid[k] || far32(st[k], w.far_gap);
+      isfar[k] = !valid[k] || far32(st[k], w);
     }
     if constexpr (kG == kLayoutProduct) {
       for (int b = w.b0; b < w.b1; ++b) {

@@ -134,7 +134,8 @@ extern "C" ffe_status ffe_omega_noalloc(const ffe_model* m, int32_t N, double qx
   const int n_chunks = (n_ksets + ck - 1) / ck;
   g_na_seg = Segment{0, 0, g.n_batches, n_chunks, 0};
   for (int c = 0; c < n_chunks; ++c)
-    g_na_items[c] = WorkItem{0, 0, c, c * ck, std::min(n_ksets, (c + 1) * ck), 0, g.n_batches, INFINITY};
+    g_na_items[c] = WorkItem{0, 0, c, c * ck, std::min(n_ksets, (c + 1) * ck), 0, g.n_batches, 0.0f, 0.0f,
+                             INFINITY, {0, 0, 0}};
   const int64_t mchunk = 32768;
   const int m_chunks = (int)((nk + mchunk - 1) / mchunk);
   const int n_hb = (n + 31) / 32;
