@@ -260,6 +260,7 @@ ffe_status plan_alloc(ffe_context* ctx, ffe_plan* p) {
   ALLOC(d_tabf, tab_rows);
   ALLOC(d_c0f, tab_rows);
   ALLOC(d_tabd, tab_rows);
+  ALLOC(d_tabdf, tab_rows);
   ALLOC(d_c0d, tab_rows);
   ALLOC(d_M, hcount);
   ALLOC(d_Mpart, p->n_mpartials);
@@ -389,11 +390,11 @@ ffe_status plan_enqueue(ffe_context* ctx, ffe_plan* p, cudaStream_t s, cudaEvent
          "prep_params");
   ++launches;
   FFE_CU(tables_launch(ctx->mp, p->d_groups, (int)p->groups.size(), p->max_n, p->d_tabf, p->d_c0f, p->d_tabd,
-                       p->d_c0d, s),
+                       p->d_c0d, p->d_tabdf, s),
          "tables");
   ++launches;
   FFE_CU(normal_launch(ctx->mp, p->d_groups, p->d_mitems, (int)p->mitems.size(), p->d_hlist, p->d_tabd,
-                       p->d_Mpart, p->d_Mcnt, p->d_M, s),
+                       p->prec == FFE_FP32C ? p->d_tabdf : nullptr, p->d_Mpart, p->d_Mcnt, p->d_M, s),
          "normal");
   ++launches;
   KsumArgs ka = make_ksum_args(p);

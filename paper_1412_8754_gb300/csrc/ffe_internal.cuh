@@ -96,6 +96,8 @@ struct Segment {
 // Table row: cos/sin of k + q/2 and k - q/2 on one axis, and cos k.
 struct TabRowF { float cp, sp, cm, sm; };
 struct TabRowD { double cp, sp, cm, sm; };
+// The FP64 row as unevaluated sums hi + lo of two floats (double-float).
+struct TabRowDF { float2 cp, sp, cm, sm; };
 
 // ---------------------------------------------------------------- FP32 MUFU
 __device__ __forceinline__ float ex2a(float x) {

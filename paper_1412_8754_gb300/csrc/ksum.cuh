@@ -58,12 +58,15 @@ struct MItem {
 };
 
 cudaError_t tables_launch(const ModelParams& m, const GroupDesc* groups, int n_groups, int max_n,
-                          TabRowF* tabf, float* c0f, TabRowD* tabd, double* c0d, cudaStream_t s);
+                          TabRowF* tabf, float* c0f, TabRowD* tabd, double* c0d, TabRowDF* tabdf,
+                          cudaStream_t s);
 cudaError_t prep_params_launch(const double* delta, int64_t n_delta, float* d2f, const HT* ht,
                                int64_t n_ht, HTf* htf, HTd* htd, cudaStream_t s);
+// tabdf non-NULL: band energies in double-float arithmetic from tabdf (FP32
+// plans); NULL: in FP64 from tabd.
 cudaError_t normal_launch(const ModelParams& m, const GroupDesc* groups, const MItem* items,
-                          int n_items, const double* hlist, const TabRowD* tabd, double* partials,
-                          int32_t* counters, double* M, cudaStream_t s);
+                          int n_items, const double* hlist, const TabRowD* tabd, const TabRowDF* tabdf,
+                          double* partials, int32_t* counters, double* M, cudaStream_t s);
 
 // ---- search, rescoring and labels (search.cu)
 struct Line {          // one Delta search: outputs out0 + i*stride, i < count

@@ -41,7 +41,8 @@ constexpr size_t kOffTabF = 0;
 constexpr size_t kOffC0F = align256(kOffTabF + 2 * kNAMaxN * sizeof(TabRowF));
 constexpr size_t kOffTabD = align256(kOffC0F + 2 * kNAMaxN * sizeof(float));
 constexpr size_t kOffC0D = align256(kOffTabD + 2 * kNAMaxN * sizeof(TabRowD));
-constexpr size_t kOffGroup = align256(kOffC0D + 2 * kNAMaxN * sizeof(double));
+constexpr size_t kOffTabDF = align256(kOffC0D + 2 * kNAMaxN * sizeof(double));
+constexpr size_t kOffGroup = align256(kOffTabDF + 2 * kNAMaxN * sizeof(TabRowDF));
 constexpr size_t kOffSeg = align256(kOffGroup + sizeof(GroupDesc));
 constexpr size_t kOffItems = align256(kOffSeg + sizeof(Segment));
 constexpr size_t kOffMItems = align256(kOffItems + kNAMaxItems * sizeof(WorkItem));
@@ -170,10 +171,12 @@ extern "C" ffe_status ffe_omega_noalloc(const ffe_model* m, int32_t N, double qx
   if (e == cudaSuccess)
     e = tables_launch(mp, d_group, 1, N, reinterpret_cast<TabRowF*>(base + kOffTabF),
                       reinterpret_cast<float*>(base + kOffC0F), reinterpret_cast<TabRowD*>(base + kOffTabD),
-                      reinterpret_cast<double*>(base + kOffC0D), s);
+                      reinterpret_cast<double*>(base + kOffC0D), reinterpret_cast<TabRowDF*>(base + kOffTabDF), s);
   if (e == cudaSuccess)
     e = normal_launch(mp, d_group, reinterpret_cast<const MItem*>(base + kOffMItems), n_mitems, d_hlist,
-                      reinterpret_cast<const TabRowD*>(base + kOffTabD), reinterpret_cast<double*>(base + kOffMPart),
+                      reinterpret_cast<const TabRowD*>(base + kOffTabD),
+                      prec == FFE_FP32C ? reinterpret_cast<const TabRowDF*>(base + kOffTabDF) : nullptr,
+                      reinterpret_cast<double*>(base + kOffMPart),
                       reinterpret_cast<int32_t*>(base + kOffMCnt), reinterpret_cast<double*>(base + kOffM), s);
   if (e != cudaSuccess) return FFE_ECUDA;
   KsumArgs a;

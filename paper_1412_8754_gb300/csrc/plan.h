@@ -90,6 +90,7 @@ struct ffe_plan {
   ffe::TabRowF* d_tabf = nullptr;
   float* d_c0f = nullptr;
   ffe::TabRowD* d_tabd = nullptr;
+  ffe::TabRowDF* d_tabdf = nullptr;  // double-float copy (normal-state sums of FP32 plans)
   double* d_c0d = nullptr;
   double* d_M = nullptr;
   double* d_Mpart = nullptr;

@@ -9,8 +9,13 @@ namespace ffe {
 // Row t of a group: axis = t / N (0: x, 1: y), i = t % N.  Stores
 // cos/sin(2 pi i/N + q/2), cos/sin(2 pi i/N - q/2) and cos(2 pi i/N), computed
 // in FP64 and rounded once to FP32 for the FP32 path.
+__device__ __forceinline__ float2 split_df(double x) {
+  const float hi = (float)x;
+  return make_float2(hi, (float)(x - (double)hi));
+}
+
 __global__ void tables_kernel(const GroupDesc* __restrict__ groups, TabRowF* tabf, float* c0f,
-                              TabRowD* tabd, double* c0d) {
+                              TabRowD* tabd, double* c0d, TabRowDF* tabdf) {
   const GroupDesc g = groups[blockIdx.y];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * g.N) return;
@@ -27,13 +32,15 @@ __global__ void tables_kernel(const GroupDesc* __restrict__ groups, TabRowF* tab
   c0d[row] = c0;
   tabf[row] = TabRowF{(float)cp, (float)sp, (float)cm, (float)sm};
   c0f[row] = (float)c0;
+  if (tabdf) tabdf[row] = TabRowDF{split_df(cp), split_df(sp), split_df(cm), split_df(sm)};
 }
 
 cudaError_t tables_launch(const ModelParams&, const GroupDesc* groups, int n_groups, int max_n,
-                          TabRowF* tabf, float* c0f, TabRowD* tabd, double* c0d, cudaStream_t s) {
+                          TabRowF* tabf, float* c0f, TabRowD* tabd, double* c0d, TabRowDF* tabdf,
+                          cudaStream_t s) {
   if (n_groups <= 0) return cudaSuccess;
   dim3 grid((2 * max_n + 255) / 256, n_groups);
-  tables_kernel<<<grid, 256, 0, s>>>(groups, tabf, c0f, tabd, c0d);
+  tables_kernel<<<grid, 256, 0, s>>>(groups, tabf, c0f, tabd, c0d, tabdf);
   return cudaGetLastError();
 }
 
@@ -63,6 +70,66 @@ cudaError_t prep_params_launch(const double* delta, int64_t n_delta, float* d2f,
   return cudaGetLastError();
 }
 
+// ---- double-float arithmetic: a value is the unevaluated sum hi + lo of two
+// floats with |lo| <= ulp(hi)/2 (Dekker 1971; Knuth's two-sum; the fused
+// multiply-add two-product of Ogita, Rump and Oishi 2005).  About 44 bits of
+// precision at FP32-pipe throughput, which on this GPU is ~77x the FP64 pipe's.
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_quick_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return DF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+  DF s = df_two_sum(x.hi, y.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+  return df_quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ DF df_neg(DF x) { return DF{-x.hi, -x.lo}; }
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return df_quick_two_sum(p, e);
+}
+// sqrt by one Newton step from the FP32 root r: r + (x - r^2) / (2 r)
+__device__ __forceinline__ DF df_sqrt(DF x) {
+  if (!(x.hi > 0.0f)) return DF{0.0f, 0.0f};
+  const float r = sqrtf(x.hi);
+  const float p = __fmul_rn(r, r);
+  const float pe = fmaf(r, r, -p);
+  const float d = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p), pe), x.lo);
+  return df_quick_two_sum(r, __fdiv_rn(d, __fmul_rn(2.0f, r)));
+}
+__device__ __forceinline__ DF df_from(double x) {
+  const float hi = (float)x;
+  return DF{hi, (float)(x - (double)hi)};
+}
+
+struct ModelDF {
+  DF a_sum, a_diff, a_c, a_s, mu;  // -(t1+t2), -(t1-t2), -4 t3, -4 t4, mu
+};
+
+// App. A eigenvalues at one momentum in double-float (as band_pair).
+__device__ __forceinline__ void band_pair_df(const ModelDF& m, DF cx, DF cy, DF sx, DF sy, DF& lo, DF& hi) {
+  const DF mean = df_add(df_mul(m.a_sum, df_add(cx, cy)), df_mul(m.a_c, df_mul(cx, cy)));
+  const DF half = df_mul(m.a_diff, df_add(cx, df_neg(cy)));
+  const DF t12 = df_mul(m.a_s, df_mul(sx, sy));
+  const DF root = df_sqrt(df_add(df_mul(half, half), df_mul(t12, t12)));
+  lo = df_add(mean, df_neg(root));
+  hi = df_add(mean, root);
+}
+
+__device__ __forceinline__ double df_to_double(DF x) { return (double)x.hi + (double)x.lo; }
+
 // M(h) = sum_k sum_eps [min(E_eps(k+Q/2) - mu - h, 0) + min(E_eps(-k+Q/2) - mu + h, 0)]
 // for up to 32 h values per item, over the item's k range, in FP64.
 //
@@ -76,12 +143,74 @@ cudaError_t prep_params_launch(const double* delta, int64_t n_delta, float* d2f,
 // h: they are broadcast to the warp and lane j adds min(value, +-h_j).  Every
 // choice is made on FP32 copies; where the copies tie, the two candidates
 // differ by at most one FP32 ulp of h.
+// Values of the M sum: FP64, or double-float for FP32 plans.
+template <bool DFM>
+struct MVal;
+template <>
+struct MVal<false> {
+  using T = double;
+  static __device__ __forceinline__ double zero() { return 0.0; }
+  static __device__ __forceinline__ double add(double a, double b) { return a + b; }
+  static __device__ __forceinline__ double neg(double a) { return -a; }
+  static __device__ __forceinline__ float f32(double a) { return (float)a; }
+  static __device__ __forceinline__ double to_double(double a) { return a; }
+  static __device__ __forceinline__ double shfl(double a, int src) { return __shfl_sync(kFull, a, src); }
+};
+template <>
+struct MVal<true> {
+  using T = DF;
+  static __device__ __forceinline__ DF zero() { return DF{0.0f, 0.0f}; }
+  static __device__ __forceinline__ DF add(DF a, DF b) { return df_add(a, b); }
+  static __device__ __forceinline__ DF neg(DF a) { return df_neg(a); }
+  static __device__ __forceinline__ float f32(DF a) { return a.hi; }
+  static __device__ __forceinline__ double to_double(DF a) { return df_to_double(a); }
+  static __device__ __forceinline__ DF shfl(DF a, int src) {
+    return DF{__shfl_sync(kFull, a.hi, src), __shfl_sync(kFull, a.lo, src)};
+  }
+};
+
+// The four band values u_lo, u_hi (k+Q/2) and d_lo, d_hi (-k+Q/2), minus mu.
+__device__ __forceinline__ void band_values(const ModelParams& m, const ModelDF&, const TabRowD& rx,
+                                            const TabRowD& ry, const TabRowDF&, const TabRowDF&, double (&v)[4]) {
+  band_pair<double>(m, rx.cp, ry.cp, rx.sp, ry.sp, v[0], v[1]);
+  band_pair<double>(m, rx.cm, ry.cm, rx.sm, ry.sm, v[2], v[3]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] -= m.mu;
+}
+__device__ __forceinline__ void band_values(const ModelParams&, const ModelDF& md, const TabRowD&, const TabRowD&,
+                                            const TabRowDF& rx, const TabRowDF& ry, DF (&v)[4]) {
+  auto f = [](float2 a) { return DF{a.x, a.y}; };
+  band_pair_df(md, f(rx.cp), f(ry.cp), f(rx.sp), f(ry.sp), v[0], v[1]);
+  band_pair_df(md, f(rx.cm), f(ry.cm), f(rx.sm), f(ry.sm), v[2], v[3]);
+  const DF nmu = df_neg(md.mu);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = df_add(v[i], nmu);
+}
+
+// M(h) for up to 32 h values per item, over the item's k range.
+//
+// With u = E(k+Q/2) - mu and d = E(-k+Q/2) - mu the summand is
+// min(u, h) + min(d, -h), so each band value contributes either itself or
+// +-h.  Lane j of a warp owns h_j.  A value below every h of the item (u) or
+// below every -h (d) adds itself to every h: it goes to a per-lane total S.
+// A value above all of them adds +h_j (u) or -h_j (d) to every h: it goes to
+// a per-lane integer count C, so that S + C h_j is its contribution to h_j.
+// Only the few values inside [h_min, h_max) (or its mirror) need a choice per
+// h: they are broadcast to the warp and lane j adds min(value, +-h_j).  Every
+// choice is made on FP32 copies; where the copies tie, the two candidates
+// differ by at most one FP32 ulp of h.  FP64 plans compute the band values and
+// sums in FP64; FP32 plans in double-float (~44 bits), far below their error
+// bound, at FP32-pipe speed.
+template <bool DFM>
 __global__ void __launch_bounds__(256) normal_kernel(const ModelParams m,
                                                      const GroupDesc* __restrict__ groups,
                                                      const MItem* __restrict__ items,
                                                      const double* __restrict__ hlist,
                                                      const TabRowD* __restrict__ tabd,
+                                                     const TabRowDF* __restrict__ tabdf,
                                                      double* partials, int32_t* counters, double* M) {
+  using V = MVal<DFM>;
+  using T = typename V::T;
   __shared__ double red[8][32];
   __shared__ int last_flag;
   const MItem it = items[blockIdx.x];
@@ -91,43 +220,61 @@ __global__ void __launch_bounds__(256) normal_kernel(const ModelParams m,
   const int nh = min(32, g.n_h - h0);
   const double hj = hlist[g.h_off + h0 + min(lane, nh - 1)];
   const float hjf = (float)hj;
+  T hjv, nhjv;
+  if constexpr (DFM) {
+    hjv = df_from(hj);
+  } else {
+    hjv = hj;
+  }
+  nhjv = V::neg(hjv);
+  ModelDF md;
+  if constexpr (DFM) {
+    md.a_sum = df_from(-(m.t1 + m.t2));
+    md.a_diff = df_from(-(m.t1 - m.t2));
+    md.a_c = df_from(-4.0 * m.t3);
+    md.a_s = df_from(-4.0 * m.t4);
+    md.mu = df_from(m.mu);
+  }
   float hminf = hjf, hmaxf = hjf;
 #pragma unroll
   for (int s = 16; s >= 1; s >>= 1) {
     hminf = fminf(hminf, __shfl_xor_sync(kFull, hminf, s));
     hmaxf = fmaxf(hmaxf, __shfl_xor_sync(kFull, hmaxf, s));
   }
-  double S = 0.0, acc = 0.0;
+  T S = V::zero(), acc = V::zero();
   int C = 0;
+  const int k1 = (int)it.k1;
   // warp-uniform trip count: every lane takes part in the ballots
-  for (int64_t kb = it.k0 + (threadIdx.x & ~31); kb < it.k1; kb += blockDim.x) {
-    const int64_t k = kb + lane;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int kb = (int)it.k0 + (threadIdx.x & ~31); kb < k1; kb += blockDim.x) {
+    const int k = kb + lane;
+    T v[4] = {V::zero(), V::zero(), V::zero(), V::zero()};
     unsigned rare = 0;
-    if (k < it.k1) {
-      const int iy = (int)(k / g.N);
-      const int ix = (int)(k - (int64_t)iy * g.N);
-      const TabRowD rx = tabd[g.tab_off + ix];
-      const TabRowD ry = tabd[g.tab_off + g.N + iy];
-      band_pair<double>(m, rx.cp, ry.cp, rx.sp, ry.sp, v[0], v[1]);
-      band_pair<double>(m, rx.cm, ry.cm, rx.sm, ry.sm, v[2], v[3]);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) v[i] -= m.mu;
-      double below = 0.0;
+    if (k < k1) {
+      const int iy = k / g.N;
+      const int ix = k - iy * g.N;
+      TabRowD rx, ry;
+      TabRowDF fx, fy;
+      if constexpr (DFM) {
+        fx = tabdf[g.tab_off + ix];
+        fy = tabdf[g.tab_off + g.N + iy];
+      } else {
+        rx = tabd[g.tab_off + ix];
+        ry = tabd[g.tab_off + g.N + iy];
+      }
+      band_values(m, md, rx, ry, fx, fy, v);
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const float f = (float)v[i];
+        const float f = V::f32(v[i]);
         // u (i < 2) against h; d (i >= 2) against -h
         const float lo = i < 2 ? hminf : -hmaxf, hi = i < 2 ? hmaxf : -hminf;
         if (f < lo) {
-          below += v[i];
+          S = V::add(S, v[i]);
         } else if (f >= hi) {
           C += i < 2 ? 1 : -1;
         } else {
           rare |= 1u << i;
         }
       }
-      S += below;
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -135,22 +282,23 @@ __global__ void __launch_bounds__(256) normal_kernel(const ModelParams m,
       while (mask) {
         const int src = __ffs(mask) - 1;
         mask &= mask - 1;
-        const double x = __shfl_sync(kFull, v[i], src);
-        const float xf = (float)x;
+        const T x = V::shfl(v[i], src);
+        const float xf = V::f32(x);
         if (i < 2)
-          acc += xf < hjf ? x : hj;
+          acc = V::add(acc, xf < hjf ? x : hjv);
         else
-          acc += xf < -hjf ? x : -hj;
+          acc = V::add(acc, xf < -hjf ? x : nhjv);
       }
     }
   }
   // warp totals of S and C, then this lane's M contribution for h_j
+  double Sd = V::to_double(S);
 #pragma unroll
   for (int s = 16; s >= 1; s >>= 1) {
-    S += __shfl_xor_sync(kFull, S, s);
+    Sd += __shfl_xor_sync(kFull, Sd, s);
     C += __shfl_xor_sync(kFull, C, s);
   }
-  red[warp][lane] = (S + (double)C * hj) + acc;
+  red[warp][lane] = (Sd + (double)C * hj) + V::to_double(acc);
   __syncthreads();
   if (warp == 0) {
     double s = 0.0;
@@ -174,10 +322,13 @@ __global__ void __launch_bounds__(256) normal_kernel(const ModelParams m,
 }
 
 cudaError_t normal_launch(const ModelParams& m, const GroupDesc* groups, const MItem* items,
-                          int n_items, const double* hlist, const TabRowD* tabd, double* partials,
-                          int32_t* counters, double* M, cudaStream_t s) {
+                          int n_items, const double* hlist, const TabRowD* tabd, const TabRowDF* tabdf,
+                          double* partials, int32_t* counters, double* M, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
-  normal_kernel<<<n_items, 256, 0, s>>>(m, groups, items, hlist, tabd, partials, counters, M);
+  if (tabdf)
+    normal_kernel<true><<<n_items, 256, 0, s>>>(m, groups, items, hlist, tabd, tabdf, partials, counters, M);
+  else
+    normal_kernel<false><<<n_items, 256, 0, s>>>(m, groups, items, hlist, tabd, tabdf, partials, counters, M);
   return cudaGetLastError();
 }
 
