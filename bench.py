@@ -410,10 +410,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "k-evals/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"fflo_scan N={cfg['N']}: {len(q_all)} q x {len(cfg['h'])} h x "
-                               f"{len(cfg['T'])} T x {cfg['n']} Delta, U={cfg['U']}, FP32 + FP64 ties",
-                   "l2": "flushed between timed steps (256 MiB write)",
-                   "parallelism": f"q sharded over {ws} rank(s)" if ws > 1 else "1 GPU"},
+        "config": arm_config(cfg, ws),
         "points_per_s": points_per_s,
         "e2e": {"value": k_job / e2e_t if ws == 1 else None, "unit": "k-evals/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -444,6 +441,14 @@ def main():
         torch.distributed.destroy_process_group()
 
 
+def arm_config(cfg, ws):
+    """The workload named in both arms' JSON lines."""
+    return {"workload": f"fflo_scan N={cfg['N']}: {len(cfg['qx'])} q x {len(cfg['h'])} h x "
+                        f"{len(cfg['T'])} T x {cfg['n']} Delta, U={cfg['U']}, FP32 + FP64 ties",
+            "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": f"q sharded over {ws} rank(s)" if ws > 1 else "1 GPU"}
+
+
 def run_reference(args, cfg, ws, rank):
     """The oracle (FP64, OpenMP on the host cores) on the same metric, bounded sample per step."""
     if rank != 0:
@@ -470,7 +475,7 @@ def run_reference(args, cfg, ws, rank):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "k-evals/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"fflo_scan N={N} (bounded sample)"},
+        "config": arm_config(cfg, ws),
         "cpu_baseline": {"value": v, "unit": "k-evals/s", "cores": used, "kind": "oracle", "sample": desc},
         "e2e": {"value": v, "unit": "k-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
