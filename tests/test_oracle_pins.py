@@ -168,6 +168,48 @@ def test_delta_zero_is_free_fermions(qx, qy, h, T):
     assert abs(got - ref) <= 1e-12 * abs(ref)
 
 
+@pytest.mark.parametrize("qx,h,T", [(0.0, 0.0, 0.005), (0.37, 0.08, 0.002)])
+def test_per_band_delta_zero_is_free_fermions(qx, h, T):
+    """Per band eps at Delta = 0: Omega_eps = -T sum_{k,sigma} ln(1 + exp(-E_{eps sigma}/T)),
+    with the bands ordered lower (0), upper (1) as the eigenvalues of the App. A matrix."""
+    m = oracle.make_model()
+    N = 24
+    ks = TWO_PI * np.arange(N) / N
+    terms = [[], []]
+    for ky in ks:
+        for kx in ks:
+            e = bands_eigvalsh(oracle.RAGHU2, kx + qx / 2, ky)
+            for b in range(2):
+                for sigma in (+1, -1):
+                    x = e[b] - oracle.RAGHU2["mu"] - sigma * h
+                    terms[b].append(-T * np.logaddexp(0.0, -x / T))
+    _, ob = oracle.omega(m, N, qx, 0.0, h, T, 0.0, bands=True)
+    for b in range(2):
+        ref = math.fsum(terms[b])
+        assert abs(ob[b] - ref) <= 1e-12 * abs(ref), (b, ob[b], ref)
+
+
+def test_per_band_zero_temperature_limit():
+    """T -> 0 per band: each pair of band eps contributes its lowest many-body level plus
+    Delta^2 / U."""
+    m = oracle.make_model(U=2.0)
+    N, qx, h, delta, T = 8, 0.4, 0.05, 0.1, 1e-9
+    ks = TWO_PI * np.arange(N) / N
+    terms = [[], []]
+    for ky in ks:
+        for kx in ks:
+            e_kq = bands_eigvalsh(oracle.RAGHU2, kx + qx / 2, ky)
+            e_mkq = bands_eigvalsh(oracle.RAGHU2, -kx + qx / 2, -ky)
+            gap = delta * math.cos(kx) * math.cos(ky)
+            for b in range(2):
+                eu, ed = e_kq[b] - 1.54 - h, e_mkq[b] - 1.54 + h
+                levels = [0.0, eu, ed, 0.5 * (eu + ed) - math.hypot(0.5 * (eu + ed), gap)]
+                terms[b].append(min(levels) + delta * delta / 2.0)
+    _, ob = oracle.omega(m, N, qx, 0.0, h, T, delta, bands=True)
+    for b in range(2):
+        assert abs(ob[b] - math.fsum(terms[b])) < 1e-9, b
+
+
 def test_zero_temperature_limit_is_ground_state():
     """T -> 0: each pair contributes its lowest many-body level."""
     m = oracle.make_model(U=2.0)
