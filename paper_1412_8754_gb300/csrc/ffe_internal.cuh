@@ -55,6 +55,8 @@ struct GroupDesc {
   int64_t tab_off;    // first table row: x rows [tab_off, tab_off+N), y rows after
   int64_t h_off;      // first entry of the distinct-h list and of the M sums
   double qx, qy;
+  int32_t band_only;  // 0: both bands; 1: the lower band only; 2: the upper band only
+  int32_t pad;
 };
 
 // (h, T) entry with the index of its h in the group's distinct-h list.
@@ -169,6 +171,17 @@ __device__ __forceinline__ void kstate_make(const ModelParams& m, const Row& rx,
   st.as[1] = fabs(s1);
   st.s2[0] = fmax(s0 * s0, (Real)1e-30);
   st.s2[1] = fmax(s1 * s1, (Real)1e-30);
+}
+
+// A group restricted to one band: the other band's state is made inert
+// (|s| = 1e15: no log term, a = Delta^2 eta^2 / 2e15 <= 2e-17 per k-point).
+template <typename Real>
+__device__ __forceinline__ void kstate_band_only(KState<Real>& st, int band_only) {
+  if (band_only == 0) return;
+  const int off = band_only == 1 ? 1 : 0;
+  st.as[off] = (Real)1e15;
+  st.s2[off] = (Real)1e30;
+  st.d0[off] = (Real)0;
 }
 
 // Delta-dependent, (h,T)-independent part for one band: R and a = R - |s|.

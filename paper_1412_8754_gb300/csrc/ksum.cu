@@ -64,6 +64,7 @@ __device__ __forceinline__ void build_states(const KsumArgs& a, const GroupDesc&
       load_row<Real>(a, g.tab_off + ix, rx, c0x);
       load_row<Real>(a, g.tab_off + g.N + iy, ry, c0y);
       kstate_make<Real, Row>(a.m, rx, ry, c0x, c0y, st[j]);
+      kstate_band_only<Real>(st[j], g.band_only);
     } else {
       kstate_invalid<Real>(st[j]);
     }
@@ -148,6 +149,7 @@ __device__ __forceinline__ KState32 state32_at(const KsumArgs& a, const GroupDes
   load_row<float>(a, g.tab_off + g.N + iy, ry, c0y);
   KState<float> s;
   kstate_make<float, TabRowF>(a.m, rx, ry, c0x, c0y, s);
+  kstate_band_only<float>(s, g.band_only);
   KState32 t;
   t.eta2 = s.eta2;
   t.as = make_float2(s.as[0], s.as[1]);
@@ -378,7 +380,7 @@ __device__ void finalize_segment(const KsumArgs& a, const Segment& sg, const Gro
     const double M = a.M[g.h_off + ht.h_idx];
     const int64_t out = g.out_off + o;
     a.V[out] = V;
-    a.omega[out] = M + V + 2.0 * n2 * dl * dl / a.m.U;
+    a.omega[out] = M + V + (g.band_only ? 1.0 : 2.0) * n2 * dl * dl / a.m.U;
     a.ebound[out] = a.eb_rel * fabs(V) + a.eb_abs * n2 * ht.T;
   }
 }

@@ -18,7 +18,9 @@ namespace {
 bool valid_N(int32_t N) { return N >= 2 && N <= 8192 && (N % 2) == 0; }
 
 // Points sharing (N, Q) form one LIST group; outputs keep input order inside.
-void fill_points(ffe_plan* p, const ffe_point* pts, int64_t n) {
+// per_band: every group twice, restricted to the lower then the upper band
+// (outputs [0, n) lower, [n, 2n) upper, in the same order).
+void fill_points(ffe_plan* p, const ffe_point* pts, int64_t n, bool per_band = false) {
   p->layout = kLayoutList;
   std::map<std::tuple<int32_t, double, double>, std::vector<int64_t>> by_key;
   std::vector<std::tuple<int32_t, double, double>> keys;
@@ -33,10 +35,12 @@ void fill_points(ffe_plan* p, const ffe_point* pts, int64_t n) {
     }
   }
   int64_t out = 0, tab = 0;
+  for (int pass = 0; pass < (per_band ? 2 : 1); ++pass)
   for (const auto& k : keys) {
     const std::vector<int64_t>& idx = by_key[k];
     GroupDesc g;
     std::memset(&g, 0, sizeof g);
+    g.band_only = per_band ? pass + 1 : 0;
     g.N = std::get<0>(k);
     g.layout = kLayoutList;
     g.n_out = (int32_t)idx.size();
@@ -270,7 +274,6 @@ ffe_status ffe_omega(ffe_context* ctx, const ffe_point* pts, int64_t n, double* 
                      void* stream) {
   if (!ctx) return FFE_EINVAL;
   if (!pts || !omega || n < 1) return set_err(ctx, "ffe_omega: empty or NULL arguments"), FFE_EINVAL;
-  if (omega_band) return set_err(ctx, "per-band output is not built yet"), FFE_EUNSUPPORTED;
   for (int64_t i = 0; i < n; ++i) {
     const ffe_point& q = pts[i];
     if (!valid_N(q.N)) return set_err(ctx, "point %lld: N=%d must be even in [2, 8192]", (long long)i, q.N), FFE_EINVAL;
@@ -281,7 +284,7 @@ ffe_status ffe_omega(ffe_context* ctx, const ffe_point* pts, int64_t n, double* 
   }
   cudaStream_t s = (cudaStream_t)stream;
   ffe_plan* p = plan_new(ctx, kPlanOmega);
-  fill_points(p, pts, n);
+  fill_points(p, pts, n, omega_band != nullptr);
   ffe_status st = plan_configure(ctx, p);
   if (st == FFE_OK) st = plan_finish(ctx, p, false);
   if (st == FFE_OK) st = plan_run(ctx, p, s);
@@ -293,7 +296,16 @@ ffe_status ffe_omega(ffe_context* ctx, const ffe_point* pts, int64_t n, double* 
     if (e != cudaSuccess) {
       st = cuda_fail(ctx, e, "fetch omega");
     } else {
-      for (int64_t o = 0; o < p->n_out; ++o) omega[p->order[o]] = om[o];
+      if (omega_band) {  // outputs [0, n): lower band, [n, 2n): upper band, same order
+        for (int64_t o = 0; o < n; ++o) {
+          const int64_t i = p->order[o];
+          omega_band[2 * i] = om[o];
+          omega_band[2 * i + 1] = om[n + o];
+          omega[i] = om[o] + om[n + o];
+        }
+      } else {
+        for (int64_t o = 0; o < p->n_out; ++o) omega[p->order[o]] = om[o];
+      }
     }
   }
   plan_free(p);

@@ -160,6 +160,7 @@ __global__ void __launch_bounds__(256) rescore_kernel(const RescoreArgs a) {
       KState<double> st;
       kstate_make<double, TabRowD>(a.m, a.tabd[g.tab_off + ix], a.tabd[g.tab_off + g.N + iy],
                                    a.c0d[g.tab_off + ix], a.c0d[g.tab_off + g.N + iy], st);
+      kstate_band_only<double>(st, g.band_only);
       s += v_term_f64(st, d2, ht.h, inv_t, ht.T);
     }
 #pragma unroll
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(256) rescore_kernel(const RescoreArgs a) {
       double V = 0.0;
       for (int i = 0; i < a.max_chunks; ++i) V += __ldcg(a.partials + (int64_t)r * a.max_chunks + i);
       const double n2 = (double)g.N * (double)g.N;
-      const double om = a.M[g.h_off + ht.h_idx] + V + 2.0 * n2 * d2 / a.m.U;
+      const double om = a.M[g.h_off + ht.h_idx] + V + (g.band_only ? 1.0 : 2.0) * n2 * d2 / a.m.U;
       if (q.kind == 0) {
         a.omega[q.dst] = om;
         a.ebound[q.dst] = 0.0;

@@ -262,6 +262,16 @@ __global__ void __launch_bounds__(256) normal_kernel(const ModelParams m,
         ry = tabd[g.tab_off + g.N + iy];
       }
       band_values(m, md, rx, ry, fx, fy, v);
+      if (g.band_only) {  // the other band: u, d far above every +-h, min(u, h) + min(d, -h) = 0
+        const int off = g.band_only == 1 ? 1 : 0;
+        if constexpr (DFM) {
+          v[off] = DF{1e30f, 0.0f};
+          v[off + 2] = DF{1e30f, 0.0f};
+        } else {
+          v[off] = 1e30;
+          v[off + 2] = 1e30;
+        }
+      }
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const float f = V::f32(v[i]);

@@ -247,11 +247,13 @@ def ffe_destroy(ctx):
     lib().ffe_destroy(ctx)
 
 
-def ffe_omega(ctx, points: np.ndarray, stream=None) -> np.ndarray:
+def ffe_omega(ctx, points: np.ndarray, stream=None, bands=False):
+    """Omega at the points; with bands=True returns (omega[n], omega_band[n, 2])."""
     pts = np.ascontiguousarray(points, dtype=POINT_DTYPE)
     out = np.zeros(len(pts))
-    _check(ctx, lib().ffe_omega(ctx, _ptr(pts), len(pts), _ptr(out), None, _stream(stream)))
-    return out
+    ob = np.zeros((len(pts), 2)) if bands else None
+    _check(ctx, lib().ffe_omega(ctx, _ptr(pts), len(pts), _ptr(out), _ptr(ob), _stream(stream)))
+    return (out, ob) if bands else out
 
 
 def ffe_minimize(ctx, params: np.ndarray, search=FFE_SEARCH_GRID, want_grid=False, stream=None):
@@ -383,8 +385,8 @@ class Context:
     def __init__(self, prec=FFE_FP32C, U=2.0, eta_amp=1.0, **model):
         self.handle = ffe_create(prec=prec, U=U, eta_amp=eta_amp, **model)
 
-    def omega(self, points, stream=None):
-        return ffe_omega(self.handle, points, stream)
+    def omega(self, points, stream=None, bands=False):
+        return ffe_omega(self.handle, points, stream, bands)
 
     def minimize(self, params, search=FFE_SEARCH_GRID, want_grid=False, stream=None):
         return ffe_minimize(self.handle, params, search, want_grid, stream)

@@ -40,6 +40,24 @@ def test_omega_random_points(prec):
     assert err.max() <= TOL[prec], (err.max(), int(err.argmax()))
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_omega_per_band(prec):
+    """Omega_eps of the lower and upper band (each with its own Delta^2/U term) and their sum,
+    ragged lattices, both signs of q and h."""
+    w = workloads.random_points(120, seed=12)
+    U = 3.0
+    m = oracle.make_model(U=U)
+    ref, ref_b, _ = oracle.omega_batch(m, w["N"], w["qx"], w["qy"], w["h"], w["T"], w["delta"], bands=True)
+    pts = ffe.points(w["N"], w["qx"], w["qy"], w["h"], w["T"], w["delta"])
+    with ffe.Context(prec=prec, U=U) as ctx:
+        got, got_b = ctx.omega(pts, bands=True)
+        plain = ctx.omega(pts)
+    for b in range(2):
+        assert per_site(got_b[:, b], ref_b[:, b], w["N"]).max() <= TOL[prec], b
+    assert per_site(got, ref, w["N"]).max() <= TOL[prec]
+    assert per_site(got, plain, w["N"]).max() <= 2 * TOL[prec]
+
+
 @pytest.mark.parametrize("N", [2, 4, 6, 10])
 @pytest.mark.parametrize("prec", PRECS)
 def test_omega_tiny_lattices(prec, N):
