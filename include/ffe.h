@@ -169,6 +169,17 @@ FFE_API ffe_status ffe_minimize(ffe_context* ctx, int32_t search, const ffe_para
                                 int64_t n, ffe_result* out, double* omega_grid,
                                 double* err_grid, void* stream);
 
+/* Per-band independent minimisation (Sec. 2: the paper minimises Omega_eps
+ * of every band separately).  Omega = Omega_lower(Delta_lower) +
+ * Omega_upper(Delta_upper) when each band has its own gap, so the joint
+ * minimum is the two one-dimensional minima.  Each band's search runs on its
+ * own Omega_eps (its Delta^2/U term included) with the point's search
+ * settings; out[n][2] receives the lower (index 0) and upper (index 1)
+ * band's result, fields as in ffe_minimize (omega_star and omega_lo are
+ * Omega_eps). */
+FFE_API ffe_status ffe_minimize_bands(ffe_context* ctx, int32_t search, const ffe_param* ps, int64_t n,
+                                      ffe_result* out, void* stream);
+
 /* Phase-diagram scan (Alg. 1): per (q, h, T) the Delta minimum, then per
  * (h, T) the phase label.  per_point[n_q][n_h*n_T] receives the minima
  * (q-major), labels[n_h*n_T] the FFE_PHASE_* label, best_q[n_h*n_T] the

@@ -79,15 +79,19 @@ void fill_points(ffe_plan* p, const ffe_point* pts, int64_t n, bool per_band = f
   p->n_out = out;
 }
 
-// One LIST group per parameter point: outputs = its Delta grid.
-void fill_min_grid(ffe_plan* p, const ffe_param* ps, int64_t n) {
+// One LIST group per parameter point: outputs = its Delta grid.  per_band:
+// every point twice, restricted to the lower then the upper band (lines
+// [0, n) and [n, 2n)).
+void fill_min_grid(ffe_plan* p, const ffe_param* ps, int64_t n, bool per_band = false) {
   p->layout = kLayoutList;
   int64_t out = 0, tab = 0;
   std::vector<double> grid;
-  for (int64_t i = 0; i < n; ++i) {
+  for (int64_t li = 0; li < (per_band ? 2 * n : n); ++li) {
+    const int64_t i = li % n;
     const ffe_param& q = ps[i];
     GroupDesc g;
     std::memset(&g, 0, sizeof g);
+    g.band_only = per_band ? (int32_t)(li / n) + 1 : 0;
     g.N = q.N;
     g.layout = kLayoutList;
     g.n_out = q.n;
@@ -112,7 +116,7 @@ void fill_min_grid(ffe_plan* p, const ffe_param* ps, int64_t n) {
     L.out0 = out;
     L.stride = 1;
     L.count = q.n;
-    L.group = (int32_t)i;
+    L.group = (int32_t)li;
     L.pad = 0;
     L.delta0 = g.delta_off;
     L.ht = g.ht_off;
@@ -126,8 +130,9 @@ void fill_min_grid(ffe_plan* p, const ffe_param* ps, int64_t n) {
 
 // Golden-section searches: parameter points sharing (N, Q) form one LIST
 // group (their (h, T) and pending Delta are the outputs); one line per point,
-// in input order.
-void fill_min_golden(ffe_plan* p, const ffe_param* ps, int64_t n) {
+// in input order.  per_band: every group twice, restricted to the lower then
+// the upper band (lines [0, n) and [n, 2n)).
+void fill_min_golden(ffe_plan* p, const ffe_param* ps, int64_t n, bool per_band = false) {
   p->layout = kLayoutList;
   int steps = 0;
   for (int64_t i = 0; i < n; ++i) steps = std::max(steps, ps[i].n);
@@ -139,13 +144,17 @@ void fill_min_golden(ffe_plan* p, const ffe_param* ps, int64_t n) {
     if (by_key.find(k) == by_key.end()) keys.push_back(k);
     by_key[k].push_back(i);
   }
-  p->lines.resize(n);
-  p->golden0.resize(n);
+  const int passes = per_band ? 2 : 1;
+  p->lines.resize(n * passes);
+  p->golden0.resize(n * passes);
   int64_t out = 0, tab = 0;
-  for (size_t gi = 0; gi < keys.size(); ++gi) {
+  for (size_t gp = 0; gp < keys.size() * passes; ++gp) {
+    const size_t gi = gp % keys.size();
+    const int pass = (int)(gp / keys.size());
     const std::vector<int64_t>& idx = by_key[keys[gi]];
     GroupDesc g;
     std::memset(&g, 0, sizeof g);
+    g.band_only = per_band ? pass + 1 : 0;
     g.N = std::get<0>(keys[gi]);
     g.layout = kLayoutList;
     g.n_out = (int32_t)idx.size();
@@ -178,17 +187,17 @@ void fill_min_golden(ffe_plan* p, const ffe_param* ps, int64_t n) {
       L.out0 = out + (int64_t)j;
       L.stride = 1;
       L.count = 1;
-      L.group = (int32_t)gi;
+      L.group = (int32_t)gp;
       L.pad = 0;
       L.delta0 = g.delta_off + (int64_t)j;
       L.ht = g.ht_off + (int64_t)j;
-      p->lines[idx[j]] = L;
+      p->lines[pass * n + idx[j]] = L;
       GoldenState gs;
       std::memset(&gs, 0, sizeof gs);
       gs.lo = q.lo;
       gs.hi = q.hi;
       gs.x0 = q.lo;
-      p->golden0[idx[j]] = gs;
+      p->golden0[pass * n + idx[j]] = gs;
     }
     g.n_h = (int32_t)hmap.size();
     p->groups.push_back(g);
@@ -223,13 +232,13 @@ ffe_status check_params(ffe_context* ctx, int32_t search, const ffe_param* ps, i
 }
 
 ffe_status build_min_plan(ffe_context* ctx, int32_t search, const ffe_param* ps, int64_t n, bool graph,
-                          ffe_plan** out) {
+                          ffe_plan** out, bool per_band = false) {
   ffe_plan* p = plan_new(ctx, search == FFE_SEARCH_GRID ? kPlanMinGrid : kPlanMinGolden);
   *out = p;
   if (search == FFE_SEARCH_GRID)
-    fill_min_grid(p, ps, n);
+    fill_min_grid(p, ps, n, per_band);
   else
-    fill_min_golden(p, ps, n);
+    fill_min_golden(p, ps, n, per_band);
   ffe_status st = plan_configure(ctx, p);
   if (st == FFE_OK) st = plan_finish(ctx, p, graph);
   return st;
@@ -308,6 +317,28 @@ ffe_status ffe_omega(ffe_context* ctx, const ffe_point* pts, int64_t n, double* 
       }
     }
   }
+  plan_free(p);
+  return st;
+}
+
+ffe_status ffe_minimize_bands(ffe_context* ctx, int32_t search, const ffe_param* ps, int64_t n, ffe_result* out,
+                              void* stream) {
+  if (!ctx) return FFE_EINVAL;
+  if (!out) return set_err(ctx, "ffe_minimize_bands: out is NULL"), FFE_EINVAL;
+  ffe_status st = check_params(ctx, search, ps, n);
+  if (st != FFE_OK) return st;
+  if (n > ((int64_t)1 << 30)) return set_err(ctx, "too many parameter points"), FFE_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  ffe_plan* p = nullptr;
+  st = build_min_plan(ctx, search, ps, n, false, &p, true);
+  std::vector<ffe_result> lines(2 * n);
+  if (st == FFE_OK) st = plan_run(ctx, p, s);
+  if (st == FFE_OK) st = fetch_min(ctx, p, lines.data(), nullptr, nullptr, s);
+  if (st == FFE_OK)
+    for (int64_t i = 0; i < n; ++i) {
+      out[2 * i] = lines[i];
+      out[2 * i + 1] = lines[n + i];
+    }
   plan_free(p);
   return st;
 }

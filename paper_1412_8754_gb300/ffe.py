@@ -72,6 +72,7 @@ _SIGNATURES = [
     ("ffe_last_error", ctypes.c_char_p, [_VP]),
     ("ffe_omega", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP]),
     ("ffe_minimize", ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, _VP, _VP, _VP]),
+    ("ffe_minimize_bands", ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, _VP]),
     ("ffe_phase_scan", ctypes.c_int, [_VP, ctypes.POINTER(ffe_scan), _VP, _VP, _VP, _VP]),
     ("ffe_plan_phase_scan", ctypes.c_int, [_VP, ctypes.POINTER(ffe_scan), _VP, ctypes.POINTER(_VP)]),
     ("ffe_plan_execute", ctypes.c_int, [_VP, _VP]),
@@ -256,6 +257,14 @@ def ffe_omega(ctx, points: np.ndarray, stream=None, bands=False):
     return (out, ob) if bands else out
 
 
+def ffe_minimize_bands(ctx, params: np.ndarray, search=FFE_SEARCH_GRID, stream=None):
+    """Per-band independent searches; returns results[n, 2] (lower, upper band)."""
+    ps = np.ascontiguousarray(params, dtype=PARAM_DTYPE)
+    res = np.zeros((len(ps), 2), dtype=RESULT_DTYPE)
+    _check(ctx, lib().ffe_minimize_bands(ctx, search, _ptr(ps), len(ps), _ptr(res), _stream(stream)))
+    return res
+
+
 def ffe_minimize(ctx, params: np.ndarray, search=FFE_SEARCH_GRID, want_grid=False, stream=None):
     ps = np.ascontiguousarray(params, dtype=PARAM_DTYPE)
     res = np.zeros(len(ps), dtype=RESULT_DTYPE)
@@ -390,6 +399,9 @@ class Context:
 
     def minimize(self, params, search=FFE_SEARCH_GRID, want_grid=False, stream=None):
         return ffe_minimize(self.handle, params, search, want_grid, stream)
+
+    def minimize_bands(self, params, search=FFE_SEARCH_GRID, stream=None):
+        return ffe_minimize_bands(self.handle, params, search, stream)
 
     def phase_scan(self, *a, **k):
         return ffe_phase_scan(self.handle, *a, **k)

@@ -242,6 +242,61 @@ def oracle_golden(m, N, qx, qy, h, T, lo, hi, steps):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_minimize_bands_grid_vs_oracle(prec):
+    """Per-band independent minimisation on a grid: each band's argmin of its own Omega_eps is
+    the oracle's, index for index."""
+    U, n = 4.0, 41
+    rng = np.random.default_rng(23)
+    k = 16
+    N = rng.choice(np.array([16, 24, 32]), size=k).astype(np.int32)
+    qx = rng.uniform(0, 0.5, k)
+    qx[:3] = 0.0
+    h = rng.uniform(0, 0.12, k)
+    T = rng.uniform(0.002, 0.03, k)
+    m = oracle.make_model(U=U)
+    grid = np.linspace(0.0, 0.2, n)
+    with ffe.Context(prec=prec, U=U) as ctx:
+        res = ctx.minimize_bands(ffe.params(N, qx, 0.0, h, T, 0.0, 0.2, n))
+    assert res.shape == (k, 2)
+    interior = 0
+    for i in range(k):
+        _, ob, _ = oracle.omega_batch(m, int(N[i]), qx[i], 0.0, h[i], T[i], grid, bands=True)
+        for b in range(2):
+            idx = search.grid_argmin(ob[:, b])
+            interior += 0 < idx < n - 1
+            assert res[i, b]["idx_star"] == idx, (i, b, res[i, b]["idx_star"], idx)
+            assert per_site(res[i, b]["omega_star"], ob[idx, b], N[i]) <= TOL[prec]
+            assert per_site(res[i, b]["omega_lo"], ob[0, b], N[i]) <= TOL[prec]
+    assert interior > 0  # some band has a gap of its own
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_minimize_bands_golden_vs_oracle(prec):
+    """Per-band golden-section searches against the oracle's on each band's Omega_eps."""
+    N, U, steps = 24, 4.0, 20
+    rng = np.random.default_rng(29)
+    k = 12
+    qx = rng.uniform(0, 0.4, k)
+    h = rng.uniform(0, 0.1, k)
+    T = rng.uniform(0.002, 0.02, k)
+    m = oracle.make_model(U=U)
+    with ffe.Context(prec=prec, U=U) as ctx:
+        res = ctx.minimize_bands(ffe.params(N, qx, 0.0, h, T, 0.0, 0.2, steps), search=ffe.FFE_SEARCH_GOLDEN)
+    for b in range(2):
+        def ev(d, b=b):
+            _, ob, _ = oracle.omega_batch(m, N, qx, 0.0, h, T, d, bands=True)
+            return ob[:, b]
+
+        xb, fb, f0 = search.golden_section_batch(ev, np.zeros(k), np.full(k, 0.2), steps)
+        assert per_site(res[:, b]["omega_lo"], f0, N).max() <= TOL[prec]
+        at_gpu = ev(res[:, b]["delta_star"])
+        assert per_site(res[:, b]["omega_star"], at_gpu, N).max() <= TOL[prec]
+        slack = {ffe.FFE_FP64: 1e-11, ffe.FFE_FP32C: 1e-9}[prec]
+        assert np.all((at_gpu - fb) / N**2 <= slack)
+        assert np.array_equal(res[:, b]["flags"] & ffe.FFE_FLAG_LOWER != 0, xb == 0.0)
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_golden_minimize_vs_oracle(prec):
     N, U, steps = 32, 4.0, 24
     rng = np.random.default_rng(17)
