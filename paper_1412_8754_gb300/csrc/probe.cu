@@ -13,7 +13,7 @@ enum { kOpEx2 = 0, kOpLg2, kOpRsq, kOpRcp, kOpFma32, kOpFma64 };
 
 template <int OP>
 __global__ void __launch_bounds__(256) probe_kernel(float* sink, int iters) {
-  if (OP == kOpFma64) {
+  if constexpr (OP == kOpFma64) {
     double x[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) x[j] = 1.0 + threadIdx.x * 1e-7 + j * 1e-3;
@@ -25,25 +25,25 @@ __global__ void __launch_bounds__(256) probe_kernel(float* sink, int iters) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) s += x[j];
     if (s == 12345.0) sink[0] = (float)s;
-    return;
-  }
-  float x[8];
+  } else {
+    float x[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) x[j] = 1.0f + threadIdx.x * 1e-6f + j * 1e-3f;
-  for (int i = 0; i < iters; ++i) {
+    for (int j = 0; j < 8; ++j) x[j] = 1.0f + threadIdx.x * 1e-6f + j * 1e-3f;
+    for (int i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      if (OP == kOpEx2) x[j] = ex2a(-x[j]);
-      if (OP == kOpLg2) x[j] = lg2a(x[j] + 2.0f);
-      if (OP == kOpRsq) x[j] = rsqa(x[j]);
-      if (OP == kOpRcp) x[j] = rcpa(x[j]);
-      if (OP == kOpFma32) x[j] = fmaf(x[j], 0.999999f, 1e-6f);
+      for (int j = 0; j < 8; ++j) {
+        if (OP == kOpEx2) x[j] = ex2a(-x[j]);
+        if (OP == kOpLg2) x[j] = lg2a(x[j] + 2.0f);
+        if (OP == kOpRsq) x[j] = rsqa(x[j]);
+        if (OP == kOpRcp) x[j] = rcpa(x[j]);
+        if (OP == kOpFma32) x[j] = fmaf(x[j], 0.999999f, 1e-6f);
+      }
     }
-  }
-  float s = 0.0f;
+    float s = 0.0f;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) s += x[j];
-  if (s == 12345.0f) sink[0] = s;
+    for (int j = 0; j < 8; ++j) s += x[j];
+    if (s == 12345.0f) sink[0] = s;
+  }
 }
 
 template <int OP>
