@@ -210,6 +210,27 @@ def test_per_band_zero_temperature_limit():
         assert abs(ob[b] - math.fsum(terms[b])) < 1e-9, b
 
 
+def test_q_point_group_and_half_period():
+    """The full-FBZ q scan rests on these: the model is symmetric under k_x <-> k_y and
+    k_x -> -k_x (App. A: T11 <-> T22, T12 -> -T12 leave the bands unchanged), so
+    Omega(qx, qy) = Omega(qy, qx) = Omega(-qx, qy); on an even lattice Q -> Q + 2 pi e_x shifts
+    both spins by the lattice vector pi e_x and eta^2 is unchanged."""
+    m = oracle.make_model(U=2.0)
+    N = 20
+    for qx, qy, h, T, d in [(0.7, 0.25, 0.05, 0.004, 0.11), (2.1, -1.3, 0.1, 0.02, 0.05)]:
+        ref = oracle.omega(m, N, qx, qy, h, T, d)
+        tol = 1e-12 * abs(ref)
+        assert abs(oracle.omega(m, N, qy, qx, h, T, d) - ref) <= tol
+        assert abs(oracle.omega(m, N, -qx, qy, h, T, d) - ref) <= tol
+        assert abs(oracle.omega(m, N, qx, -qy, h, T, d) - ref) <= tol
+        assert abs(oracle.omega(m, N, qx + 2 * math.pi, qy, h, T, d) - ref) <= tol
+        assert abs(oracle.omega(m, N, qx, qy - 2 * math.pi, h, T, d) - ref) <= tol
+    # an odd lattice has no pi shift: the half period does not hold there
+    a = oracle.omega(m, 9, 0.7, 0.25, 0.05, 0.004, 0.11)
+    b = oracle.omega(m, 9, 0.7 + 2 * math.pi, 0.25, 0.05, 0.004, 0.11)
+    assert abs(a - b) > 1e-9 * abs(a)
+
+
 def test_zero_temperature_limit_is_ground_state():
     """T -> 0: each pair contributes its lowest many-body level."""
     m = oracle.make_model(U=2.0)
