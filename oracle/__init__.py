@@ -10,6 +10,7 @@ arithmetic.
 Layout:
   ffe_oracle.c   Eq. freeene / Eq. enequasiparticle / App. A in plain C (FP64)
   search.py      grid argmin, golden-section search and phase labels (Alg. 1)
+  threeband.py   the three-band model of App. B (eigvalsh of its 3x3 matrix + the C k-sum)
   mlp.py         FP64 reference of the surrogate MLP (forward, backward, Adam)
 
 Parity status of each function is listed in the module docstrings; every
@@ -86,6 +87,11 @@ def lib():
             L.ffeo_omega_batch.restype = ctypes.c_int
             L.ffeo_band_grid.argtypes = [mp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
             L.ffeo_band_grid.restype = None
+            L.ffeo_omega_given.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp] + [ctypes.c_double] * 6 + [dp, dp]
+            L.ffeo_omega_given.restype = None
+            L.ffeo_omega_given_batch.argtypes = ([ctypes.c_int, ctypes.c_int, dp, dp] + [ctypes.c_double] * 3
+                                                 + [ctypes.c_int64] + [dp] * 5 + [ctypes.c_int])
+            L.ffeo_omega_given_batch.restype = ctypes.c_int
             L.ffeo_max_threads.argtypes = []
             L.ffeo_max_threads.restype = ctypes.c_int
             _lib = L

@@ -129,6 +129,66 @@ void ffeo_omega(const ffeo_model* m, int N, double qx, double qy, double h,
   }
 }
 
+/* Eq. freeene for a model of nb bands whose band energies are given:
+ * e_up[(j*N + i)*nb + b] = E_b(k + Q/2), e_dn[...] = E_b(-k + Q/2) for
+ * k = 2 pi (i, j)/N (the three-band model of App. B, whose 3x3 hopping matrix
+ * the caller diagonalises).  omega_band (may be NULL) receives Omega_b. */
+void ffeo_omega_given(int nb, int N, const double* e_up, const double* e_dn,
+                      double eta_amp, double mu, double U, double h, double T,
+                      double delta, double* omega, double* omega_band) {
+  nsum tot = {0.0, 0.0};
+  nsum band[8];
+  for (int b = 0; b < nb; ++b) band[b].s = band[b].c = 0.0;
+  const double two_pi = 2.0 * M_PI;
+  for (int j = 0; j < N; ++j) {
+    double ky = two_pi * (double)j / (double)N;
+    for (int i = 0; i < N; ++i) {
+      double kx = two_pi * (double)i / (double)N;
+      double eta = eta_amp * cos(kx) * cos(ky);
+      const int64_t base = ((int64_t)j * N + i) * nb;
+      for (int b = 0; b < nb; ++b) {
+        double e_u = e_up[base + b] - mu - h;
+        double e_d = e_dn[base + b] - mu + h;
+        double ep, em;
+        ffeo_quasiparticle(e_u, e_d, delta * eta, &ep, &em);
+        double term = ffeo_F(ep, T) + ffeo_F(em, T) + e_d + delta * delta / U;
+        nsum_add(&tot, term);
+        nsum_add(&band[b], term);
+      }
+    }
+  }
+  *omega = nsum_value(&tot);
+  if (omega_band)
+    for (int b = 0; b < nb; ++b) omega_band[b] = nsum_value(&band[b]);
+}
+
+/* Many (h, T, Delta) points on one set of given band energies, OpenMP over
+ * points; omega_band (may be NULL) is [n][nb].  Returns the threads used. */
+int ffeo_omega_given_batch(int nb, int N, const double* e_up, const double* e_dn,
+                           double eta_amp, double mu, double U, int64_t n,
+                           const double* h, const double* T, const double* delta,
+                           double* omega, double* omega_band, int nthreads) {
+  int used = 1;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+  {
+#pragma omp single
+    used = omp_get_num_threads();
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t p = 0; p < n; ++p)
+      ffeo_omega_given(nb, N, e_up, e_dn, eta_amp, mu, U, h[p], T[p], delta[p],
+                       &omega[p], omega_band ? &omega_band[nb * p] : NULL);
+  }
+#else
+  (void)nthreads;
+  for (int64_t p = 0; p < n; ++p)
+    ffeo_omega_given(nb, N, e_up, e_dn, eta_amp, mu, U, h[p], T[p], delta[p],
+                     &omega[p], omega_band ? &omega_band[nb * p] : NULL);
+#endif
+  return used;
+}
+
 /* A batch of independent points, parallel over points with OpenMP.
  * nthreads <= 0 uses the OpenMP default.  Returns the thread count used. */
 int ffeo_omega_batch(const ffeo_model* m, int64_t n, const int32_t* N,
