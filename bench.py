@@ -148,6 +148,29 @@ def run_extras(ffe, np, torch, stream, workloads):
         kms, _ = plan.kernel_ms()
         k = plan.stats()["k_evals"]
         plan.destroy()
+    # the three-band model of App. B (band tables by FP64 Jacobi, two band pairs per k-point)
+    w3 = workloads.threeband_scan()
+    with ffe.Context(prec=ffe.FFE_FP32C, U=w3["U"], model="daghofer3") as ctx3:
+        plan3 = ctx3.plan_phase_scan(w3["N"], w3["qx"], w3["qy"], w3["h"], w3["T"], n=w3["n"], lo=w3["lo"],
+                                     hi=w3["hi"])
+        plan3.execute(stream)
+        plan3.fetch()
+        plan3.kernel_ms()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            plan3.execute(stream)
+        _, lab3, _ = plan3.fetch()
+        dt3 = (time.perf_counter() - t0) / 3
+        kms3, _ = plan3.kernel_ms()
+        st3 = plan3.stats()
+        plan3.destroy()
+    out["threeband_scan"] = {
+        "k_evals_per_s": st3["k_evals"] / dt3, "ms_per_step": 1e3 * dt3, "kernel_ms": kms3,
+        "kernel_k_evals_per_s": st3["k_evals"] / (kms3 / 1e3) if kms3 else None,
+        "labels": [int((lab3 == i).sum()) for i in range(3)],
+        "workload": (f"three-band model (App. B, eV), N={w3['N']}: {len(w3['qx'])} q x {len(w3['h'])} h x "
+                     f"{w3['n']} Delta, T={w3['T'][0]}, U={w3['U']}, FP32+comp")}
     out["uneven_batch"] = {"jobs": 512, "k_evals_per_s": k / dt, "jobs_per_s": 512 / dt, "ms_per_step": 1e3 * dt,
                            "kernel_ms": kms, "autotuned": shape,
                            "workload": "512 jobs, N in {256,512,1024,2048}, 32..256 Delta, seed 1234"}

@@ -61,17 +61,26 @@ typedef enum {
 
 typedef enum { FFE_FP64 = 0, FFE_FP32C = 1 } ffe_precision;
 
-typedef enum { FFE_MODEL_RAGHU2 = 0 } ffe_model_kind;
+typedef enum { FFE_MODEL_RAGHU2 = 0, FFE_MODEL_DAGHOFER3 = 1 } ffe_model_kind;
 
-/* Model of App. A plus the pairing channel of Sec. 2.  Defaults (App. A):
- * t1=-1, t2=1.3, t3=t4=-0.85, mu=1.54 (two electrons per site). */
+/* Model plus the pairing channel of Sec. 2.
+ * FFE_MODEL_RAGHU2: the two-band model of App. A, hoppings t1..t4 (defaults
+ *   t1=-1, t2=1.3, t3=t4=-0.85, mu=1.54: two electrons per site; t5..eps0
+ *   unused).
+ * FFE_MODEL_DAGHOFER3: the three-band model of App. B, hoppings t1..t12 and
+ *   the d_xy level eps0 (printed values in eV: t1=-0.08, t2=0.1825,
+ *   t3=0.08375, t4=-0.03, t5=0.15, t6=0.15, t7=-0.12, t8=0.06, t9=0,
+ *   t10=-0.024, t11=-0.01, t12=0.0275, eps0=0.75; n = 4 at mu=0.4748).  Its
+ *   three bands are the eigenvalues of the 3x3 hopping matrix, ascending;
+ *   every band pairs intra-band as in the two-band model. */
 typedef struct {
-  int32_t kind;      /* ffe_model_kind; only FFE_MODEL_RAGHU2                  */
+  int32_t kind;      /* ffe_model_kind                                         */
   int32_t prec;      /* ffe_precision used by every call on the context        */
   double t1, t2, t3, t4;
   double mu;         /* chemical potential                                     */
   double U;          /* pairing strength (> 0): + Delta^2/U per k and band     */
   double eta_amp;    /* s+- form factor eta(k) = eta_amp cos kx cos ky (Sec. 1) */
+  double t5, t6, t7, t8, t9, t10, t11, t12, eps0;  /* FFE_MODEL_DAGHOFER3 only  */
 } ffe_model;
 
 /* One free-energy evaluation point. */
@@ -152,8 +161,9 @@ FFE_API const char* ffe_status_string(ffe_status s);
 FFE_API const char* ffe_last_error(const ffe_context* ctx);
 
 /* Omega (Eq. freeene summed over both bands) at n independent points.
- * omega[n] receives Omega; omega_band (NULL or [n][2]) receives the per-band
- * Omega_eps for the lower (index 0) and upper (index 1) band of App. A.
+ * omega[n] receives Omega; omega_band (NULL or [n][nb], nb = 2 for the
+ * two-band and 3 for the three-band model) receives the per-band Omega_eps,
+ * bands in ascending order of energy.
  * Points sharing (N, Q) share the per-k band work. */
 FFE_API ffe_status ffe_omega(ffe_context* ctx, const ffe_point* pts, int64_t n,
                      double* omega, double* omega_band, void* stream);
@@ -174,9 +184,9 @@ FFE_API ffe_status ffe_minimize(ffe_context* ctx, int32_t search, const ffe_para
  * Omega_upper(Delta_upper) when each band has its own gap, so the joint
  * minimum is the two one-dimensional minima.  Each band's search runs on its
  * own Omega_eps (its Delta^2/U term included) with the point's search
- * settings; out[n][2] receives the lower (index 0) and upper (index 1)
- * band's result, fields as in ffe_minimize (omega_star and omega_lo are
- * Omega_eps). */
+ * settings; out[n][nb] (nb = 2 or 3 bands of the model) receives each band's
+ * result in ascending order of band energy, fields as in ffe_minimize
+ * (omega_star and omega_lo are Omega_eps). */
 FFE_API ffe_status ffe_minimize_bands(ffe_context* ctx, int32_t search, const ffe_param* ps, int64_t n,
                                       ffe_result* out, void* stream);
 

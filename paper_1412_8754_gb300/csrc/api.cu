@@ -288,6 +288,14 @@ ffe_status plan_alloc(ffe_context* ctx, ffe_plan* p) {
   ALLOC(d_labels, std::max<size_t>(1, p->n_pts));
   ALLOC(d_bestq, std::max<size_t>(1, p->n_pts));
   ALLOC(d_golden, p->golden0.size());
+  // three-band model: band tables, two momenta x N^2 rows per group
+  int64_t e3_rows = 0;
+  for (GroupDesc& g : p->groups) {
+    g.e3_off = e3_rows;
+    if (ctx->mp.nbands == 3) e3_rows += 2 * (int64_t)g.N * g.N;
+  }
+  ALLOC(d_e3d, e3_rows);
+  ALLOC(d_e3f, e3_rows);
 #undef ALLOC
   cudaStream_t s = p->stream;
   FFE_CU(cudaMemsetAsync(p->d_Mcnt, 0, sizeof(int32_t) * std::max(1, p->n_mcounters), s), "memset");
@@ -326,6 +334,8 @@ static KsumArgs make_ksum_args(ffe_plan* p) {
   a.segs = p->d_segs;
   a.queue = p->d_counters + 0;
   a.near_evals = p->d_near;
+  a.e3f = p->d_e3f;
+  a.e3d = p->d_e3d;
   a.seg_count = p->d_segcnt;
   a.partials = p->d_partials;
   a.tabf = p->d_tabf;
@@ -354,6 +364,7 @@ static RescoreArgs make_rescore_args(ffe_plan* p, int queue_slot, int count_slot
   r.m = p->ctx->mp;
   r.groups = p->d_groups;
   r.tabd = p->d_tabd;
+  r.e3d = p->d_e3d;
   r.c0d = p->d_c0d;
   r.ht = p->d_ht;
   r.M = p->d_M;
@@ -393,8 +404,13 @@ ffe_status plan_enqueue(ffe_context* ctx, ffe_plan* p, cudaStream_t s, cudaEvent
                        p->d_c0d, p->d_tabdf, s),
          "tables");
   ++launches;
+  if (ctx->mp.nbands == 3) {
+    FFE_CU(bands3_launch(ctx->mp, p->d_groups, (int)p->groups.size(), p->max_n, p->d_tabd, p->d_e3d, p->d_e3f, s),
+           "bands3");
+    ++launches;
+  }
   FFE_CU(normal_launch(ctx->mp, p->d_groups, p->d_mitems, (int)p->mitems.size(), p->d_hlist, p->d_tabd,
-                       p->prec == FFE_FP32C ? p->d_tabdf : nullptr, p->d_Mpart, p->d_Mcnt, p->d_M, s),
+                       p->prec == FFE_FP32C ? p->d_tabdf : nullptr, p->d_e3d, p->d_Mpart, p->d_Mcnt, p->d_M, s),
          "normal");
   ++launches;
   KsumArgs ka = make_ksum_args(p);
@@ -810,15 +826,41 @@ ffe_status ffe_create(const ffe_model* m, ffe_context** out) {
   if (!out) return FFE_EINVAL;
   *out = nullptr;
   if (!m) return FFE_EINVAL;
-  if (m->kind != FFE_MODEL_RAGHU2) return FFE_EUNSUPPORTED;
+  if (m->kind != FFE_MODEL_RAGHU2 && m->kind != FFE_MODEL_DAGHOFER3) return FFE_EUNSUPPORTED;
   if (m->prec != FFE_FP64 && m->prec != FFE_FP32C) return FFE_EINVAL;
   if (!(m->U > 0.0) || !std::isfinite(m->U) || !std::isfinite(m->t1) || !std::isfinite(m->t2) ||
       !std::isfinite(m->t3) || !std::isfinite(m->t4) || !std::isfinite(m->mu) || !std::isfinite(m->eta_amp))
     return FFE_EINVAL;
+  if (m->kind == FFE_MODEL_DAGHOFER3) {
+    for (double x : {m->t5, m->t6, m->t7, m->t8, m->t9, m->t10, m->t11, m->t12, m->eps0})
+      if (!std::isfinite(x)) return FFE_EINVAL;
+  }
   ffe_context* ctx = new (std::nothrow) ffe_context();
   if (!ctx) return FFE_ENOMEM;
   ctx->model = *m;
-  ctx->mp = ModelParams{m->t1, m->t2, m->t3, m->t4, m->mu, m->U, m->eta_amp};
+  ModelParams mp;
+  std::memset(&mp, 0, sizeof mp);
+  mp.t1 = m->t1;
+  mp.t2 = m->t2;
+  mp.t3 = m->t3;
+  mp.t4 = m->t4;
+  mp.mu = m->mu;
+  mp.U = m->U;
+  mp.eta_amp = m->eta_amp;
+  mp.kind = m->kind;
+  mp.nbands = m->kind == FFE_MODEL_DAGHOFER3 ? 3 : 2;
+  if (m->kind == FFE_MODEL_DAGHOFER3) {
+    mp.t5 = m->t5;
+    mp.t6 = m->t6;
+    mp.t7 = m->t7;
+    mp.t8 = m->t8;
+    mp.t9 = m->t9;
+    mp.t10 = m->t10;
+    mp.t11 = m->t11;
+    mp.t12 = m->t12;
+    mp.eps0 = m->eps0;
+  }
+  ctx->mp = mp;
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
   if (e == cudaSuccess) {

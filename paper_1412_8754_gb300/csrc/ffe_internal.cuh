@@ -37,6 +37,9 @@ constexpr float kLn2f = 0.693147180559945309f;
 
 struct ModelParams {
   double t1, t2, t3, t4, mu, U, eta_amp;
+  int32_t kind;    // FFE_MODEL_RAGHU2 (0) or FFE_MODEL_DAGHOFER3 (1)
+  int32_t nbands;  // 2 or 3
+  double t5, t6, t7, t8, t9, t10, t11, t12, eps0;  // three-band model only
 };
 
 // One group of outputs sharing (N, Q): the unit that shares per-k band work.
@@ -55,9 +58,20 @@ struct GroupDesc {
   int64_t tab_off;    // first table row: x rows [tab_off, tab_off+N), y rows after
   int64_t h_off;      // first entry of the distinct-h list and of the M sums
   double qx, qy;
-  int32_t band_only;  // 0: both bands; 1: the lower band only; 2: the upper band only
+  int32_t band_only;  // 0: every band; b + 1: band b only (bands in ascending order of energy)
   int32_t pad;
+  int64_t e3_off;     // three-band model: first entry of the group's band tables
+                      // (k + Q/2 at e3_off + k, -k + Q/2 at e3_off + N^2 + k)
 };
+
+// Bands are evaluated two at a time, as the two halves of packed operations:
+// the two-band model in one pair, the three-band model in two, (0, 1) and
+// (2, inert).  Slot s of pair p holds band 2p + s.
+__device__ __forceinline__ int band_pairs(int nbands) { return (nbands + 1) / 2; }
+__device__ __forceinline__ bool slot_active(int nbands, int band_only, int pair, int slot) {
+  const int b = 2 * pair + slot;
+  return b < nbands && (band_only == 0 || band_only - 1 == b);
+}
 
 // (h, T) entry with the index of its h in the group's distinct-h list.
 struct HT {
@@ -98,6 +112,11 @@ struct Segment {
 // Table row: cos/sin of k + q/2 and k - q/2 on one axis, and cos k.
 struct TabRowF { float cp, sp, cm, sm; };
 struct TabRowD { double cp, sp, cm, sm; };
+// The three bands of the three-band model at one momentum, ascending (FP64; the
+// FP32 copy is a float4 with the same layout).
+struct __align__(16) E3D {
+  double x, y, z, pad;
+};
 // The FP64 row as unevaluated sums hi + lo of two floats (double-float).
 struct TabRowDF { float2 cp, sp, cm, sm; };
 
@@ -155,33 +174,55 @@ __device__ __forceinline__ void kstate_invalid(KState<Real>& st) {
   }
 }
 
-template <typename Real, typename Row>
-__device__ __forceinline__ void kstate_make(const ModelParams& m, const Row& rx, const Row& ry,
-                                            Real c0x, Real c0y, KState<Real>& st) {
-  Real eta = (Real)m.eta_amp * c0x * c0y;
+// Per-k state of two bands from their energies at k + Q/2 (u0, u1) and
+// -k + Q/2 (d0, d1).
+template <typename Real>
+__device__ __forceinline__ void kstate_from_bands(const ModelParams& m, Real eta, Real u0, Real u1, Real d0,
+                                                  Real d1, KState<Real>& st) {
   st.eta2 = eta * eta;
-  Real ulo, uhi, dlo, dhi;
-  band_pair<Real>(m, (Real)rx.cp, (Real)ry.cp, (Real)rx.sp, (Real)ry.sp, ulo, uhi);  // k + Q/2
-  band_pair<Real>(m, (Real)rx.cm, (Real)ry.cm, (Real)rx.sm, (Real)ry.sm, dlo, dhi);  // -k + Q/2
   const Real mu = (Real)m.mu;
-  Real s0 = (Real)0.5 * (ulo + dlo) - mu, s1 = (Real)0.5 * (uhi + dhi) - mu;
-  st.d0[0] = (Real)0.5 * (ulo - dlo);
-  st.d0[1] = (Real)0.5 * (uhi - dhi);
+  Real s0 = (Real)0.5 * (u0 + d0) - mu, s1 = (Real)0.5 * (u1 + d1) - mu;
+  st.d0[0] = (Real)0.5 * (u0 - d0);
+  st.d0[1] = (Real)0.5 * (u1 - d1);
   st.as[0] = fabs(s0);
   st.as[1] = fabs(s1);
   st.s2[0] = fmax(s0 * s0, (Real)1e-30);
   st.s2[1] = fmax(s1 * s1, (Real)1e-30);
 }
 
-// A group restricted to one band: the other band's state is made inert
-// (|s| = 1e15: no log term, a = Delta^2 eta^2 / 2e15 <= 2e-17 per k-point).
+template <typename Real, typename Row>
+__device__ __forceinline__ void kstate_make(const ModelParams& m, const Row& rx, const Row& ry,
+                                            Real c0x, Real c0y, KState<Real>& st) {
+  Real eta = (Real)m.eta_amp * c0x * c0y;
+  Real ulo, uhi, dlo, dhi;
+  band_pair<Real>(m, (Real)rx.cp, (Real)ry.cp, (Real)rx.sp, (Real)ry.sp, ulo, uhi);  // k + Q/2
+  band_pair<Real>(m, (Real)rx.cm, (Real)ry.cm, (Real)rx.sm, (Real)ry.sm, dlo, dhi);  // -k + Q/2
+  kstate_from_bands<Real>(m, eta, ulo, uhi, dlo, dhi, st);
+}
+
+// A slot without an active band (one band of a pair selected, or the empty
+// second slot of the three-band model's pair (2, -)) is made inert:
+// |s| = 1e15, so no log term and a = Delta^2 eta^2 / 2e15 <= 2e-17 per k-point.
 template <typename Real>
-__device__ __forceinline__ void kstate_band_only(KState<Real>& st, int band_only) {
-  if (band_only == 0) return;
-  const int off = band_only == 1 ? 1 : 0;
-  st.as[off] = (Real)1e15;
-  st.s2[off] = (Real)1e30;
-  st.d0[off] = (Real)0;
+__device__ __forceinline__ void kstate_mask(KState<Real>& st, int nbands, int band_only, int pair) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+    if (!slot_active(nbands, band_only, pair, s)) {
+      st.as[s] = (Real)1e15;
+      st.s2[s] = (Real)1e30;
+      st.d0[s] = (Real)0;
+    }
+}
+
+// Band energies of the three-band model at one k: slots of pair p from the
+// tables (float4 / double4 rows holding the three bands in ascending order).
+template <typename Real, typename Row4>
+__device__ __forceinline__ void kstate_from_table3(const ModelParams& m, Real eta, const Row4& eu, const Row4& ed,
+                                                   int pair, KState<Real>& st) {
+  if (pair == 0)
+    kstate_from_bands<Real>(m, eta, (Real)eu.x, (Real)eu.y, (Real)ed.x, (Real)ed.y, st);
+  else
+    kstate_from_bands<Real>(m, eta, (Real)eu.z, (Real)eu.z, (Real)ed.z, (Real)ed.z, st);
 }
 
 // Delta-dependent, (h,T)-independent part for one band: R and a = R - |s|.

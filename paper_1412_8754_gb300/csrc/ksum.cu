@@ -23,8 +23,11 @@
 namespace ffe {
 
 // Capacity of a warp's k-point buffer: a flush takes 32 KPT entries and a
-// k-set adds at most 32 KPT (KPT <= 8).
+// k-set adds at most 32 KPT (KPT <= 8).  An entry is a lattice index
+// (< 8192^2 < 2^30) with the band pair in bit 30.
 constexpr int kKBuf = 2 * 32 * 8;
+constexpr int kPairShift = 30;
+constexpr int32_t kKidxMask = (1 << kPairShift) - 1;
 
 // Batch parameters staged in shared memory, one entry per output of a batch.
 struct BParF {  // FP32: Delta^2 (LIST only), h, c = 1/(T ln 2), T ln 2
@@ -48,26 +51,41 @@ __device__ __forceinline__ void load_row(const KsumArgs& a, int64_t row, TabRowD
   c0 = a.c0d[row];
 }
 
-template <typename Real, int KPT>
-__device__ __forceinline__ void build_states(const KsumArgs& a, const GroupDesc& g, int ks, int lane,
-                                             KState<Real> (&st)[KPT]) {
+// The state of lattice point kidx (< N^2) of group g for band pair `pair`.
+template <typename Real>
+__device__ __forceinline__ void state_at(const KsumArgs& a, const GroupDesc& g, int64_t kidx, int pair,
+                                         KState<Real>& st) {
   using Row = typename std::conditional<std::is_same<Real, float>::value, TabRowF, TabRowD>::type;
+  const int iy = (int)(kidx / g.N);
+  const int ix = (int)(kidx - (int64_t)iy * g.N);
+  Row rx, ry;
+  Real c0x, c0y;
+  load_row<Real>(a, g.tab_off + ix, rx, c0x);
+  load_row<Real>(a, g.tab_off + g.N + iy, ry, c0y);
+  if (a.m.nbands == 3) {
+    const Real eta = (Real)a.m.eta_amp * c0x * c0y;
+    const int64_t nk = (int64_t)g.N * g.N;
+    if constexpr (std::is_same<Real, float>::value)
+      kstate_from_table3<float, float4>(a.m, eta, a.e3f[g.e3_off + kidx], a.e3f[g.e3_off + nk + kidx], pair, st);
+    else
+      kstate_from_table3<double, E3D>(a.m, eta, a.e3d[g.e3_off + kidx], a.e3d[g.e3_off + nk + kidx], pair, st);
+  } else {
+    kstate_make<Real, Row>(a.m, rx, ry, c0x, c0y, st);
+  }
+  kstate_mask<Real>(st, a.m.nbands, g.band_only, pair);
+}
+
+template <typename Real, int KPT>
+__device__ __forceinline__ void build_states(const KsumArgs& a, const GroupDesc& g, int ks, int lane, int pair,
+                                             KState<Real> (&st)[KPT]) {
   const int64_t nk = (int64_t)g.N * g.N;
 #pragma unroll
   for (int j = 0; j < KPT; ++j) {
     const int64_t kidx = (int64_t)ks * (32 * KPT) + j * 32 + lane;
-    if (kidx < nk) {
-      const int iy = (int)(kidx / g.N);
-      const int ix = (int)(kidx - (int64_t)iy * g.N);
-      Row rx, ry;
-      Real c0x, c0y;
-      load_row<Real>(a, g.tab_off + ix, rx, c0x);
-      load_row<Real>(a, g.tab_off + g.N + iy, ry, c0y);
-      kstate_make<Real, Row>(a.m, rx, ry, c0x, c0y, st[j]);
-      kstate_band_only<Real>(st[j], g.band_only);
-    } else {
+    if (kidx < nk)
+      state_at<Real>(a, g, kidx, pair, st[j]);
+    else
       kstate_invalid<Real>(st[j]);
-    }
   }
 }
 
@@ -126,10 +144,10 @@ __device__ __forceinline__ int stage_batch(const KsumArgs& a, const GroupDesc& g
 
 // ------------------------------------------------------------ FP32 path
 template <int KPT>
-__device__ __forceinline__ void build_states32(const KsumArgs& a, const GroupDesc& g, int ks, int lane,
+__device__ __forceinline__ void build_states32(const KsumArgs& a, const GroupDesc& g, int ks, int lane, int pair,
                                                KState32 (&st)[KPT]) {
   KState<float> s[KPT];
-  build_states<float, KPT>(a, g, ks, lane, s);
+  build_states<float, KPT>(a, g, ks, lane, pair, s);
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
     st[k].eta2 = s[k].eta2;
@@ -139,17 +157,10 @@ __device__ __forceinline__ void build_states32(const KsumArgs& a, const GroupDes
   }
 }
 
-// The FP32 state of lattice point kidx (< N^2) of group g.
-__device__ __forceinline__ KState32 state32_at(const KsumArgs& a, const GroupDesc& g, int32_t kidx) {
-  const int iy = kidx / g.N;
-  const int ix = kidx - iy * g.N;
-  TabRowF rx, ry;
-  float c0x, c0y;
-  load_row<float>(a, g.tab_off + ix, rx, c0x);
-  load_row<float>(a, g.tab_off + g.N + iy, ry, c0y);
+// The FP32 state of lattice point kidx (< N^2) of group g, band pair `pair`.
+__device__ __forceinline__ KState32 state32_at(const KsumArgs& a, const GroupDesc& g, int32_t kidx, int pair) {
   KState<float> s;
-  kstate_make<float, TabRowF>(a.m, rx, ry, c0x, c0y, s);
-  kstate_band_only<float>(s, g.band_only);
+  state_at<float>(a, g, kidx, pair, s);
   KState32 t;
   t.eta2 = s.eta2;
   t.as = make_float2(s.as[0], s.as[1]);
@@ -380,7 +391,7 @@ __device__ void finalize_segment(const KsumArgs& a, const Segment& sg, const Gro
     const double M = a.M[g.h_off + ht.h_idx];
     const int64_t out = g.out_off + o;
     a.V[out] = V;
-    a.omega[out] = M + V + (g.band_only ? 1.0 : 2.0) * n2 * dl * dl / a.m.U;
+    a.omega[out] = M + V + (g.band_only ? 1.0 : (double)a.m.nbands) * n2 * dl * dl / a.m.U;
     a.ebound[out] = a.eb_rel * fabs(V) + a.eb_abs * n2 * ht.T;
   }
 }
@@ -396,7 +407,7 @@ __device__ __forceinline__ void flush32(const KsumArgs& a, const WorkItem& w, co
   for (int k = 0; k < KPT; ++k) {
     const int i = k * 32 + lane;
     if (i < n)
-      st[k] = state32_at(a, g, buf[i]);
+      st[k] = state32_at(a, g, buf[i] & kKidxMask, buf[i] >> kPairShift);
     else
       state32_invalid(st[k]);
   }
@@ -441,9 +452,12 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
   const unsigned lt = (1u << lane) - 1u;
   int n_near = 0, n_far = 0;
   double far_tot = 0.0;  // PRODUCT: lane (b - b0) holds batch b's sum of a_0 + a_1 over far points
-  for (int ks = w.kset0; ks < w.kset1; ++ks) {
+  const int npairs = band_pairs(a.m.nbands);
+  // buffered entries: lattice index | band pair << kPairShift
+  for (int ks = w.kset0; ks < w.kset1; ++ks)
+  for (int pair = 0; pair < npairs; ++pair) {
     KState32 st[KPT];
-    build_states32<KPT>(a, g, ks, lane, st);
+    build_states32<KPT>(a, g, ks, lane, pair, st);
     bool isfar[KPT], valid[KPT];
     int32_t kidx[KPT];
 #pragma unroll
@@ -451,6 +465,7 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
       kidx[k] = ks * kFlush + k * 32 + lane;
       valid[k] = kidx[k] < nk;
       isfar[k] = !valid[k] || far32(st[k], w);
+      kidx[k] |= pair << kPairShift;
     }
     if constexpr (kG == kLayoutProduct) {
       for (int b = w.b0; b < w.b1; ++b) {
@@ -542,10 +557,11 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
     if constexpr (std::is_same<Real, float>::value) {
       item32<KPT, LAYOUT>(a, w, g, lane, acc, bp, red, nbuf, fbuf);
     }
-    for (int ks = w.kset0; ks < w.kset1; ++ks) {
+    for (int ks = w.kset0; ks < w.kset1; ++ks)
+    for (int pair = 0; pair < band_pairs(a.m.nbands); ++pair) {
       if constexpr (!std::is_same<Real, float>::value) {
         KState<double> st[KPT];
-        build_states<double, KPT>(a, g, ks, lane, st);
+        build_states<double, KPT>(a, g, ks, lane, pair, st);
         for (int b = w.b0; b < w.b1; ++b) {
           int di;
           const int nvalid = stage_batch<double, kGroupLayout>(a, g, b, lane, bp, di);

@@ -36,6 +36,8 @@ struct KsumArgs {
   int32_t w_scaled;  // 1: partial sums hold W (FP32 path), V = -T ln2 W; 0: they hold V
   int32_t pad1;
   unsigned long long* near_evals;  // FP32 path: k-evaluations with the full term (NULL: not counted)
+  const float4* e3f;               // three-band model: band tables (GroupDesc::e3_off), FP32
+  const E3D* e3d;                  // and FP64
 };
 
 size_t ksum_smem_bytes(int prec, int block_threads);
@@ -66,7 +68,10 @@ cudaError_t prep_params_launch(const double* delta, int64_t n_delta, float* d2f,
 // plans); NULL: in FP64 from tabd.
 cudaError_t normal_launch(const ModelParams& m, const GroupDesc* groups, const MItem* items,
                           int n_items, const double* hlist, const TabRowD* tabd, const TabRowDF* tabdf,
-                          double* partials, int32_t* counters, double* M, cudaStream_t s);
+                          const E3D* e3d, double* partials, int32_t* counters, double* M, cudaStream_t s);
+// Three-band model: its band tables (GroupDesc::e3_off) from the FP64 trig tables.
+cudaError_t bands3_launch(const ModelParams& m, const GroupDesc* groups, int n_groups, int max_n,
+                          const TabRowD* tabd, E3D* e3d, float4* e3f, cudaStream_t s);
 
 // ---- search, rescoring and labels (search.cu)
 struct Line {          // one Delta search: outputs out0 + i*stride, i < count
@@ -134,6 +139,7 @@ struct RescoreArgs {
   GoldenState* golden;  // kinds 3 (x1) and 4 (x2)
   int32_t cap;
   int32_t pad;
+  const E3D* e3d;       // three-band model: FP64 band tables (GroupDesc::e3_off)
 };
 
 enum { kGoldenInit = 0, kGoldenLo, kGoldenX1, kGoldenX2, kGoldenMark, kGoldenDecide, kGoldenRecord,

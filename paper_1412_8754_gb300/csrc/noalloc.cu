@@ -159,7 +159,7 @@ extern "C" ffe_status ffe_omega_noalloc(const ffe_model* m, int32_t N, double qx
     e = cudaMemcpyAsync(base + kOffMItems, g_na_mitems, n_mitems * sizeof(MItem), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return FFE_ECUDA;
 
-  const ModelParams mp{m->t1, m->t2, m->t3, m->t4, m->mu, m->U, m->eta_amp};
+  const ModelParams mp{m->t1, m->t2, m->t3, m->t4, m->mu, m->U, m->eta_amp, FFE_MODEL_RAGHU2, 2};
   const GroupDesc* d_group = reinterpret_cast<const GroupDesc*>(base + kOffGroup);
   HT* d_ht = reinterpret_cast<HT*>(base + kOffHT);
   double* d_hlist = reinterpret_cast<double*>(base + kOffHList);
@@ -176,7 +176,7 @@ extern "C" ffe_status ffe_omega_noalloc(const ffe_model* m, int32_t N, double qx
     e = normal_launch(mp, d_group, reinterpret_cast<const MItem*>(base + kOffMItems), n_mitems, d_hlist,
                       reinterpret_cast<const TabRowD*>(base + kOffTabD),
                       prec == FFE_FP32C ? reinterpret_cast<const TabRowDF*>(base + kOffTabDF) : nullptr,
-                      reinterpret_cast<double*>(base + kOffMPart),
+                      nullptr, reinterpret_cast<double*>(base + kOffMPart),
                       reinterpret_cast<int32_t*>(base + kOffMCnt), reinterpret_cast<double*>(base + kOffM), s);
   if (e != cudaSuccess) return FFE_ECUDA;
   KsumArgs a;

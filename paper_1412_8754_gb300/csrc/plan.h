@@ -91,6 +91,8 @@ struct ffe_plan {
   float* d_c0f = nullptr;
   ffe::TabRowD* d_tabd = nullptr;
   ffe::TabRowDF* d_tabdf = nullptr;  // double-float copy (normal-state sums of FP32 plans)
+  ffe::E3D* d_e3d = nullptr;          // three-band model: band tables, FP64
+  float4* d_e3f = nullptr;            // and FP32
   double* d_c0d = nullptr;
   double* d_M = nullptr;
   double* d_Mpart = nullptr;

@@ -18,9 +18,9 @@ namespace {
 bool valid_N(int32_t N) { return N >= 2 && N <= 8192 && (N % 2) == 0; }
 
 // Points sharing (N, Q) form one LIST group; outputs keep input order inside.
-// per_band: every group twice, restricted to the lower then the upper band
-// (outputs [0, n) lower, [n, 2n) upper, in the same order).
-void fill_points(ffe_plan* p, const ffe_point* pts, int64_t n, bool per_band = false) {
+// bands > 0: every group once per band, restricted to it (outputs
+// [b n, (b + 1) n) for band b, in the same order).
+void fill_points(ffe_plan* p, const ffe_point* pts, int64_t n, int bands = 0) {
   p->layout = kLayoutList;
   std::map<std::tuple<int32_t, double, double>, std::vector<int64_t>> by_key;
   std::vector<std::tuple<int32_t, double, double>> keys;
@@ -35,12 +35,12 @@ void fill_points(ffe_plan* p, const ffe_point* pts, int64_t n, bool per_band = f
     }
   }
   int64_t out = 0, tab = 0;
-  for (int pass = 0; pass < (per_band ? 2 : 1); ++pass)
+  for (int pass = 0; pass < std::max(1, bands); ++pass)
   for (const auto& k : keys) {
     const std::vector<int64_t>& idx = by_key[k];
     GroupDesc g;
     std::memset(&g, 0, sizeof g);
-    g.band_only = per_band ? pass + 1 : 0;
+    g.band_only = bands > 0 ? pass + 1 : 0;
     g.N = std::get<0>(k);
     g.layout = kLayoutList;
     g.n_out = (int32_t)idx.size();
@@ -79,19 +79,18 @@ void fill_points(ffe_plan* p, const ffe_point* pts, int64_t n, bool per_band = f
   p->n_out = out;
 }
 
-// One LIST group per parameter point: outputs = its Delta grid.  per_band:
-// every point twice, restricted to the lower then the upper band (lines
-// [0, n) and [n, 2n)).
-void fill_min_grid(ffe_plan* p, const ffe_param* ps, int64_t n, bool per_band = false) {
+// One LIST group per parameter point: outputs = its Delta grid.  bands > 0:
+// every point once per band, restricted to it (lines [b n, (b + 1) n)).
+void fill_min_grid(ffe_plan* p, const ffe_param* ps, int64_t n, int bands = 0) {
   p->layout = kLayoutList;
   int64_t out = 0, tab = 0;
   std::vector<double> grid;
-  for (int64_t li = 0; li < (per_band ? 2 * n : n); ++li) {
+  for (int64_t li = 0; li < std::max(1, bands) * n; ++li) {
     const int64_t i = li % n;
     const ffe_param& q = ps[i];
     GroupDesc g;
     std::memset(&g, 0, sizeof g);
-    g.band_only = per_band ? (int32_t)(li / n) + 1 : 0;
+    g.band_only = bands > 0 ? (int32_t)(li / n) + 1 : 0;
     g.N = q.N;
     g.layout = kLayoutList;
     g.n_out = q.n;
@@ -130,9 +129,9 @@ void fill_min_grid(ffe_plan* p, const ffe_param* ps, int64_t n, bool per_band = 
 
 // Golden-section searches: parameter points sharing (N, Q) form one LIST
 // group (their (h, T) and pending Delta are the outputs); one line per point,
-// in input order.  per_band: every group twice, restricted to the lower then
-// the upper band (lines [0, n) and [n, 2n)).
-void fill_min_golden(ffe_plan* p, const ffe_param* ps, int64_t n, bool per_band = false) {
+// in input order.  bands > 0: every group once per band, restricted to it
+// (lines [b n, (b + 1) n)).
+void fill_min_golden(ffe_plan* p, const ffe_param* ps, int64_t n, int bands = 0) {
   p->layout = kLayoutList;
   int steps = 0;
   for (int64_t i = 0; i < n; ++i) steps = std::max(steps, ps[i].n);
@@ -144,7 +143,7 @@ void fill_min_golden(ffe_plan* p, const ffe_param* ps, int64_t n, bool per_band 
     if (by_key.find(k) == by_key.end()) keys.push_back(k);
     by_key[k].push_back(i);
   }
-  const int passes = per_band ? 2 : 1;
+  const int passes = std::max(1, bands);
   p->lines.resize(n * passes);
   p->golden0.resize(n * passes);
   int64_t out = 0, tab = 0;
@@ -154,7 +153,7 @@ void fill_min_golden(ffe_plan* p, const ffe_param* ps, int64_t n, bool per_band 
     const std::vector<int64_t>& idx = by_key[keys[gi]];
     GroupDesc g;
     std::memset(&g, 0, sizeof g);
-    g.band_only = per_band ? pass + 1 : 0;
+    g.band_only = bands > 0 ? pass + 1 : 0;
     g.N = std::get<0>(keys[gi]);
     g.layout = kLayoutList;
     g.n_out = (int32_t)idx.size();
@@ -232,13 +231,13 @@ ffe_status check_params(ffe_context* ctx, int32_t search, const ffe_param* ps, i
 }
 
 ffe_status build_min_plan(ffe_context* ctx, int32_t search, const ffe_param* ps, int64_t n, bool graph,
-                          ffe_plan** out, bool per_band = false) {
+                          ffe_plan** out, int bands = 0) {
   ffe_plan* p = plan_new(ctx, search == FFE_SEARCH_GRID ? kPlanMinGrid : kPlanMinGolden);
   *out = p;
   if (search == FFE_SEARCH_GRID)
-    fill_min_grid(p, ps, n, per_band);
+    fill_min_grid(p, ps, n, bands);
   else
-    fill_min_golden(p, ps, n, per_band);
+    fill_min_golden(p, ps, n, bands);
   ffe_status st = plan_configure(ctx, p);
   if (st == FFE_OK) st = plan_finish(ctx, p, graph);
   return st;
@@ -293,7 +292,8 @@ ffe_status ffe_omega(ffe_context* ctx, const ffe_point* pts, int64_t n, double* 
   }
   cudaStream_t s = (cudaStream_t)stream;
   ffe_plan* p = plan_new(ctx, kPlanOmega);
-  fill_points(p, pts, n, omega_band != nullptr);
+  const int nb = ctx->mp.nbands;
+  fill_points(p, pts, n, omega_band ? nb : 0);
   ffe_status st = plan_configure(ctx, p);
   if (st == FFE_OK) st = plan_finish(ctx, p, false);
   if (st == FFE_OK) st = plan_run(ctx, p, s);
@@ -305,12 +305,15 @@ ffe_status ffe_omega(ffe_context* ctx, const ffe_point* pts, int64_t n, double* 
     if (e != cudaSuccess) {
       st = cuda_fail(ctx, e, "fetch omega");
     } else {
-      if (omega_band) {  // outputs [0, n): lower band, [n, 2n): upper band, same order
+      if (omega_band) {  // outputs [b n, (b + 1) n): band b, same order
         for (int64_t o = 0; o < n; ++o) {
           const int64_t i = p->order[o];
-          omega_band[2 * i] = om[o];
-          omega_band[2 * i + 1] = om[n + o];
-          omega[i] = om[o] + om[n + o];
+          double tot = 0.0;
+          for (int b = 0; b < nb; ++b) {
+            omega_band[nb * i + b] = om[b * n + o];
+            tot += om[b * n + o];
+          }
+          omega[i] = tot;
         }
       } else {
         for (int64_t o = 0; o < p->n_out; ++o) omega[p->order[o]] = om[o];
@@ -330,15 +333,14 @@ ffe_status ffe_minimize_bands(ffe_context* ctx, int32_t search, const ffe_param*
   if (n > ((int64_t)1 << 30)) return set_err(ctx, "too many parameter points"), FFE_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   ffe_plan* p = nullptr;
-  st = build_min_plan(ctx, search, ps, n, false, &p, true);
-  std::vector<ffe_result> lines(2 * n);
+  const int nb = ctx->mp.nbands;
+  st = build_min_plan(ctx, search, ps, n, false, &p, nb);
+  std::vector<ffe_result> lines(nb * n);
   if (st == FFE_OK) st = plan_run(ctx, p, s);
   if (st == FFE_OK) st = fetch_min(ctx, p, lines.data(), nullptr, nullptr, s);
   if (st == FFE_OK)
-    for (int64_t i = 0; i < n; ++i) {
-      out[2 * i] = lines[i];
-      out[2 * i + 1] = lines[n + i];
-    }
+    for (int64_t i = 0; i < n; ++i)
+      for (int b = 0; b < nb; ++b) out[nb * i + b] = lines[b * n + i];
   plan_free(p);
   return st;
 }

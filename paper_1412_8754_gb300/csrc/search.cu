@@ -157,11 +157,18 @@ __global__ void __launch_bounds__(256) rescore_kernel(const RescoreArgs a) {
     for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
       const int iy = (int)(k / g.N);
       const int ix = (int)(k - (int64_t)iy * g.N);
-      KState<double> st;
-      kstate_make<double, TabRowD>(a.m, a.tabd[g.tab_off + ix], a.tabd[g.tab_off + g.N + iy],
-                                   a.c0d[g.tab_off + ix], a.c0d[g.tab_off + g.N + iy], st);
-      kstate_band_only<double>(st, g.band_only);
-      s += v_term_f64(st, d2, ht.h, inv_t, ht.T);
+      for (int pair = 0; pair < band_pairs(a.m.nbands); ++pair) {
+        KState<double> st;
+        if (a.m.nbands == 3) {
+          const double eta = a.m.eta_amp * a.c0d[g.tab_off + ix] * a.c0d[g.tab_off + g.N + iy];
+          kstate_from_table3<double, E3D>(a.m, eta, a.e3d[g.e3_off + k], a.e3d[g.e3_off + nk + k], pair, st);
+        } else {
+          kstate_make<double, TabRowD>(a.m, a.tabd[g.tab_off + ix], a.tabd[g.tab_off + g.N + iy],
+                                       a.c0d[g.tab_off + ix], a.c0d[g.tab_off + g.N + iy], st);
+        }
+        kstate_mask<double>(st, a.m.nbands, g.band_only, pair);
+        s += v_term_f64(st, d2, ht.h, inv_t, ht.T);
+      }
     }
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
@@ -180,7 +187,7 @@ __global__ void __launch_bounds__(256) rescore_kernel(const RescoreArgs a) {
       double V = 0.0;
       for (int i = 0; i < a.max_chunks; ++i) V += __ldcg(a.partials + (int64_t)r * a.max_chunks + i);
       const double n2 = (double)g.N * (double)g.N;
-      const double om = a.M[g.h_off + ht.h_idx] + V + (g.band_only ? 1.0 : 2.0) * n2 * d2 / a.m.U;
+      const double om = a.M[g.h_off + ht.h_idx] + V + (g.band_only ? 1.0 : (double)a.m.nbands) * n2 * d2 / a.m.U;
       if (q.kind == 0) {
         a.omega[q.dst] = om;
         a.ebound[q.dst] = 0.0;

@@ -44,6 +44,93 @@ cudaError_t tables_launch(const ModelParams&, const GroupDesc* groups, int n_gro
   return cudaGetLastError();
 }
 
+// ---- three-band model (App. B): band tables ----------------------------
+// Its 3x3 hopping matrix has real T11, T22, T33, T12 and purely imaginary
+// T13 = i x, T23 = i y; conjugating with diag(1, 1, i) turns it into the real
+// symmetric matrix with off-diagonals T12, -x, -y and the same eigenvalues,
+// which cyclic Jacobi rotations (Jacobi 1846; the rotation of Rutishauser's
+// formulation) diagonalise in FP64.
+
+// One Jacobi rotation zeroing a_pq of a symmetric 3x3 matrix; r is the third index.
+__device__ __forceinline__ void jacobi_rotate(double& app, double& aqq, double& apq, double& arp, double& arq) {
+  if (apq == 0.0) return;
+  const double theta = (aqq - app) / (2.0 * apq);
+  double t;
+  if (fabs(theta) > 1e150)
+    t = 0.5 / theta;
+  else
+    t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+  const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+  app -= t * apq;
+  aqq += t * apq;
+  apq = 0.0;
+  const double rp = c * arp - s * arq, rq = s * arp + c * arq;
+  arp = rp;
+  arq = rq;
+}
+
+// Eigenvalues, ascending, of the three-band matrix at momentum (cos, sin) of
+// each axis.
+__device__ __forceinline__ void bands3_at(const ModelParams& m, double cx, double sx, double cy, double sy,
+                                          double& e0, double& e1, double& e2) {
+  const double c2x = 2.0 * cx * cx - 1.0, c2y = 2.0 * cy * cy - 1.0;
+  double a00 = 2.0 * m.t2 * cx + 2.0 * m.t1 * cy + 4.0 * m.t3 * cx * cy + 2.0 * m.t11 * (c2x - c2y) +
+               4.0 * m.t12 * c2x * c2y;
+  double a11 = 2.0 * m.t1 * cx + 2.0 * m.t2 * cy + 4.0 * m.t3 * cx * cy - 2.0 * m.t11 * (c2x - c2y) +
+               4.0 * m.t12 * c2x * c2y;
+  double a22 = m.eps0 + 2.0 * m.t5 * (cx + cy) + 4.0 * m.t6 * cx * cy + 2.0 * m.t9 * (c2x + c2y) +
+               4.0 * m.t10 * (c2x * cy + cx * c2y);
+  double a01 = 4.0 * m.t4 * sx * sy;
+  double a02 = -(2.0 * m.t7 * sx + 4.0 * m.t8 * sx * cy);
+  double a12 = -(2.0 * m.t7 * sy + 4.0 * m.t8 * sy * cx);
+  // until the off-diagonal is 1e-14 of the diagonal (eigenvalue error below 1e-14 of the
+  // band width even at a degeneracy); quadratic convergence takes 3 to 4 sweeps
+  for (int sweep = 0; sweep < 8; ++sweep) {
+    const double off = fabs(a01) + fabs(a02) + fabs(a12);
+    if (off <= 1e-14 * (fabs(a00) + fabs(a11) + fabs(a22) + 1e-300)) break;
+    jacobi_rotate(a00, a11, a01, a02, a12);  // (p, q) = (0, 1), r = 2
+    jacobi_rotate(a00, a22, a02, a01, a12);  // (0, 2), r = 1
+    jacobi_rotate(a11, a22, a12, a01, a02);  // (1, 2), r = 0
+  }
+  // sort the diagonal
+  double lo = fmin(a00, fmin(a11, a22)), hi = fmax(a00, fmax(a11, a22));
+  e0 = lo;
+  e2 = hi;
+  e1 = a00 + a11 + a22 - lo - hi;
+}
+
+// Row (group g, momentum m, lattice point k): m = 0 is k + Q/2 (spin up),
+// m = 1 is -k + Q/2 (spin down; the sines' common sign does not change the
+// eigenvalues, so the k - Q/2 rows serve).
+__global__ void bands3_kernel(const ModelParams m, const GroupDesc* __restrict__ groups,
+                              const TabRowD* __restrict__ tabd, E3D* e3d, float4* e3f) {
+  const GroupDesc g = groups[blockIdx.z];
+  const int64_t nk = (int64_t)g.N * g.N;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nk) return;
+  const int mom = blockIdx.y;
+  const int iy = (int)(k / g.N);
+  const int ix = (int)(k - (int64_t)iy * g.N);
+  const TabRowD rx = tabd[g.tab_off + ix], ry = tabd[g.tab_off + g.N + iy];
+  double e0, e1, e2;
+  if (mom == 0)
+    bands3_at(m, rx.cp, rx.sp, ry.cp, ry.sp, e0, e1, e2);
+  else
+    bands3_at(m, rx.cm, rx.sm, ry.cm, ry.sm, e0, e1, e2);
+  const int64_t row = g.e3_off + mom * nk + k;
+  e3d[row] = E3D{e0, e1, e2, 0.0};
+  e3f[row] = make_float4((float)e0, (float)e1, (float)e2, 0.0f);
+}
+
+cudaError_t bands3_launch(const ModelParams& m, const GroupDesc* groups, int n_groups, int max_n,
+                          const TabRowD* tabd, E3D* e3d, float4* e3f, cudaStream_t s) {
+  if (n_groups <= 0 || m.nbands != 3) return cudaSuccess;
+  const int64_t nk = (int64_t)max_n * max_n;
+  dim3 grid((unsigned)((nk + 255) / 256), 2, n_groups);
+  bands3_kernel<<<grid, 256, 0, s>>>(m, groups, tabd, e3d, e3f);
+  return cudaGetLastError();
+}
+
 // FP32 / FP64 parameter forms derived from the authoritative FP64 inputs.
 __global__ void prep_params_kernel(const double* __restrict__ delta, int64_t n_delta, float* d2f,
                                    const HT* __restrict__ ht, int64_t n_ht, HTf* htf, HTd* htd) {
@@ -201,14 +288,18 @@ __device__ __forceinline__ void band_values(const ModelParams&, const ModelDF& m
 // differ by at most one FP32 ulp of h.  FP64 plans compute the band values and
 // sums in FP64; FP32 plans in double-float (~44 bits), far below their error
 // bound, at FP32-pipe speed.
-template <bool DFM>
+template <bool DFM, bool NB3>
 __global__ void __launch_bounds__(256) normal_kernel(const ModelParams m,
                                                      const GroupDesc* __restrict__ groups,
                                                      const MItem* __restrict__ items,
                                                      const double* __restrict__ hlist,
                                                      const TabRowD* __restrict__ tabd,
                                                      const TabRowDF* __restrict__ tabdf,
+                                                     const E3D* __restrict__ e3d,
                                                      double* partials, int32_t* counters, double* M) {
+  // NU band values at k + Q/2 (u) and NU at -k + Q/2 (d)
+  constexpr int NU = NB3 ? 3 : 2;
+  constexpr int NV = 2 * NU;
   using V = MVal<DFM>;
   using T = typename V::T;
   __shared__ double red[8][32];
@@ -247,54 +338,69 @@ __global__ void __launch_bounds__(256) normal_kernel(const ModelParams m,
   // warp-uniform trip count: every lane takes part in the ballots
   for (int kb = (int)it.k0 + (threadIdx.x & ~31); kb < k1; kb += blockDim.x) {
     const int k = kb + lane;
-    T v[4] = {V::zero(), V::zero(), V::zero(), V::zero()};
+    T v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = V::zero();
     unsigned rare = 0;
     if (k < k1) {
-      const int iy = k / g.N;
-      const int ix = k - iy * g.N;
-      TabRowD rx, ry;
-      TabRowDF fx, fy;
-      if constexpr (DFM) {
-        fx = tabdf[g.tab_off + ix];
-        fy = tabdf[g.tab_off + g.N + iy];
+      if constexpr (NB3) {
+        const E3D eu = e3d[g.e3_off + k], ed = e3d[g.e3_off + (int64_t)g.N * g.N + k];
+        v[0] = eu.x - m.mu;
+        v[1] = eu.y - m.mu;
+        v[2] = eu.z - m.mu;
+        v[3] = ed.x - m.mu;
+        v[4] = ed.y - m.mu;
+        v[5] = ed.z - m.mu;
       } else {
-        rx = tabd[g.tab_off + ix];
-        ry = tabd[g.tab_off + g.N + iy];
-      }
-      band_values(m, md, rx, ry, fx, fy, v);
-      if (g.band_only) {  // the other band: u, d far above every +-h, min(u, h) + min(d, -h) = 0
-        const int off = g.band_only == 1 ? 1 : 0;
+        const int iy = k / g.N;
+        const int ix = k - iy * g.N;
+        TabRowD rx, ry;
+        TabRowDF fx, fy;
         if constexpr (DFM) {
-          v[off] = DF{1e30f, 0.0f};
-          v[off + 2] = DF{1e30f, 0.0f};
+          fx = tabdf[g.tab_off + ix];
+          fy = tabdf[g.tab_off + g.N + iy];
         } else {
-          v[off] = 1e30;
-          v[off + 2] = 1e30;
+          rx = tabd[g.tab_off + ix];
+          ry = tabd[g.tab_off + g.N + iy];
         }
+        band_values(m, md, rx, ry, fx, fy, v);
+      }
+      if (g.band_only) {  // other bands: u, d far above every +-h, min(u, h) + min(d, -h) = 0
+#pragma unroll
+        for (int b = 0; b < NU; ++b)
+          if (b != g.band_only - 1) {
+            if constexpr (DFM) {
+              v[b] = DF{1e30f, 0.0f};
+              v[b + NU] = DF{1e30f, 0.0f};
+            } else {
+              v[b] = 1e30;
+              v[b + NU] = 1e30;
+            }
+          }
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < NV; ++i) {
         const float f = V::f32(v[i]);
-        // u (i < 2) against h; d (i >= 2) against -h
-        const float lo = i < 2 ? hminf : -hmaxf, hi = i < 2 ? hmaxf : -hminf;
+        // u (i < NU) against h; d (i >= NU) against -h
+        const float lo = i < NU ? hminf : -hmaxf, hi = i < NU ? hmaxf : -hminf;
         if (f < lo) {
           S = V::add(S, v[i]);
         } else if (f >= hi) {
-          C += i < 2 ? 1 : -1;
+          C += i < NU ? 1 : -1;
         } else {
           rare |= 1u << i;
         }
       }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < NV; ++i) {
       unsigned mask = __ballot_sync(kFull, (rare >> i) & 1u);
       while (mask) {
         const int src = __ffs(mask) - 1;
         mask &= mask - 1;
         const T x = V::shfl(v[i], src);
         const float xf = V::f32(x);
-        if (i < 2)
+        if (i < NU)
           acc = V::add(acc, xf < hjf ? x : hjv);
         else
           acc = V::add(acc, xf < -hjf ? x : nhjv);
@@ -333,12 +439,17 @@ __global__ void __launch_bounds__(256) normal_kernel(const ModelParams m,
 
 cudaError_t normal_launch(const ModelParams& m, const GroupDesc* groups, const MItem* items,
                           int n_items, const double* hlist, const TabRowD* tabd, const TabRowDF* tabdf,
-                          double* partials, int32_t* counters, double* M, cudaStream_t s) {
+                          const E3D* e3d, double* partials, int32_t* counters, double* M, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
-  if (tabdf)
-    normal_kernel<true><<<n_items, 256, 0, s>>>(m, groups, items, hlist, tabd, tabdf, partials, counters, M);
+  if (m.nbands == 3)  // FP64 band tables, either precision
+    normal_kernel<false, true><<<n_items, 256, 0, s>>>(m, groups, items, hlist, tabd, tabdf, e3d, partials,
+                                                       counters, M);
+  else if (tabdf)
+    normal_kernel<true, false><<<n_items, 256, 0, s>>>(m, groups, items, hlist, tabd, tabdf, e3d, partials,
+                                                       counters, M);
   else
-    normal_kernel<false><<<n_items, 256, 0, s>>>(m, groups, items, hlist, tabd, tabdf, partials, counters, M);
+    normal_kernel<false, false><<<n_items, 256, 0, s>>>(m, groups, items, hlist, tabd, tabdf, e3d, partials,
+                                                        counters, M);
   return cudaGetLastError();
 }
 

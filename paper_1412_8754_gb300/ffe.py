@@ -19,7 +19,14 @@ LIB_PATH = os.path.join(HERE, "libffe.so")
 
 FFE_OK, FFE_EINVAL, FFE_ENOMEM, FFE_ECUDA, FFE_ETIMEOUT, FFE_EUNSUPPORTED, FFE_EINTERNAL = range(7)
 FFE_FP64, FFE_FP32C = 0, 1
-FFE_MODEL_RAGHU2 = 0
+FFE_MODEL_RAGHU2, FFE_MODEL_DAGHOFER3 = 0, 1
+
+# Printed model parameters: App. A (two-band, units of |t1|) and App. B
+# (three-band, eV; n = 4 at mu = 0.4748).
+RAGHU2_PARAMS = dict(t1=-1.0, t2=1.3, t3=-0.85, t4=-0.85, mu=1.54)
+DAGHOFER3_PARAMS = dict(t1=-0.08, t2=0.1825, t3=0.08375, t4=-0.03, t5=0.15, t6=0.15, t7=-0.12, t8=0.06,
+                        t9=0.0, t10=-0.024, t11=-0.01, t12=0.0275, eps0=0.75, mu=0.4748)
+MODELS = {"raghu2": (FFE_MODEL_RAGHU2, 2, RAGHU2_PARAMS), "daghofer3": (FFE_MODEL_DAGHOFER3, 3, DAGHOFER3_PARAMS)}
 FFE_SEARCH_GRID, FFE_SEARCH_GOLDEN = 0, 1
 FFE_FLAG_RESCORED, FFE_FLAG_EDGE, FFE_FLAG_LOWER, FFE_FLAG_PRUNED = 1, 2, 4, 8
 FFE_PHASE_NORMAL, FFE_PHASE_BCS, FFE_PHASE_FFLO = 0, 1, 2
@@ -41,7 +48,8 @@ class FFEError(RuntimeError):
 class ffe_model(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("prec", ctypes.c_int32), ("t1", ctypes.c_double),
                 ("t2", ctypes.c_double), ("t3", ctypes.c_double), ("t4", ctypes.c_double),
-                ("mu", ctypes.c_double), ("U", ctypes.c_double), ("eta_amp", ctypes.c_double)]
+                ("mu", ctypes.c_double), ("U", ctypes.c_double), ("eta_amp", ctypes.c_double)] + [
+                    (f"t{i}", ctypes.c_double) for i in range(5, 13)] + [("eps0", ctypes.c_double)]
 
 
 class ffe_scan(ctypes.Structure):
@@ -235,8 +243,13 @@ def _check(ctx, st):
 
 
 # ------------------------------------------------------------ entry points
-def ffe_create(t1=-1.0, t2=1.3, t3=-0.85, t4=-0.85, mu=1.54, U=2.0, eta_amp=1.0, prec=FFE_FP32C):
-    m = ffe_model(FFE_MODEL_RAGHU2, prec, t1, t2, t3, t4, mu, U, eta_amp)
+def ffe_create(U=2.0, eta_amp=1.0, prec=FFE_FP32C, model="raghu2", **params):
+    """A context for `model` ("raghu2": App. A, "daghofer3": App. B) with its printed
+    parameters, any of which `params` overrides."""
+    kind, _, defaults = MODELS[model]
+    p = dict(defaults)
+    p.update(params)
+    m = ffe_model(kind=kind, prec=prec, U=U, eta_amp=eta_amp, **p)
     h = _VP()
     st = lib().ffe_create(ctypes.byref(m), ctypes.byref(h))
     if st != FFE_OK:
@@ -248,19 +261,20 @@ def ffe_destroy(ctx):
     lib().ffe_destroy(ctx)
 
 
-def ffe_omega(ctx, points: np.ndarray, stream=None, bands=False):
-    """Omega at the points; with bands=True returns (omega[n], omega_band[n, 2])."""
+def ffe_omega(ctx, points: np.ndarray, stream=None, bands=0):
+    """Omega at the points; with bands = nb (the model's band count) returns
+    (omega[n], omega_band[n, nb])."""
     pts = np.ascontiguousarray(points, dtype=POINT_DTYPE)
     out = np.zeros(len(pts))
-    ob = np.zeros((len(pts), 2)) if bands else None
+    ob = np.zeros((len(pts), int(bands))) if bands else None
     _check(ctx, lib().ffe_omega(ctx, _ptr(pts), len(pts), _ptr(out), _ptr(ob), _stream(stream)))
     return (out, ob) if bands else out
 
 
-def ffe_minimize_bands(ctx, params: np.ndarray, search=FFE_SEARCH_GRID, stream=None):
-    """Per-band independent searches; returns results[n, 2] (lower, upper band)."""
+def ffe_minimize_bands(ctx, params: np.ndarray, search=FFE_SEARCH_GRID, stream=None, nb=2):
+    """Per-band independent searches; returns results[n, nb] (bands ascending)."""
     ps = np.ascontiguousarray(params, dtype=PARAM_DTYPE)
-    res = np.zeros((len(ps), 2), dtype=RESULT_DTYPE)
+    res = np.zeros((len(ps), nb), dtype=RESULT_DTYPE)
     _check(ctx, lib().ffe_minimize_bands(ctx, search, _ptr(ps), len(ps), _ptr(res), _stream(stream)))
     return res
 
@@ -391,17 +405,18 @@ class Plan:
 class Context:
     """Owning wrapper: ffe_create on construction, ffe_destroy on close()."""
 
-    def __init__(self, prec=FFE_FP32C, U=2.0, eta_amp=1.0, **model):
-        self.handle = ffe_create(prec=prec, U=U, eta_amp=eta_amp, **model)
+    def __init__(self, prec=FFE_FP32C, U=2.0, eta_amp=1.0, model="raghu2", **params):
+        self.nbands = MODELS[model][1]
+        self.handle = ffe_create(prec=prec, U=U, eta_amp=eta_amp, model=model, **params)
 
     def omega(self, points, stream=None, bands=False):
-        return ffe_omega(self.handle, points, stream, bands)
+        return ffe_omega(self.handle, points, stream, self.nbands if bands else 0)
 
     def minimize(self, params, search=FFE_SEARCH_GRID, want_grid=False, stream=None):
         return ffe_minimize(self.handle, params, search, want_grid, stream)
 
     def minimize_bands(self, params, search=FFE_SEARCH_GRID, stream=None):
-        return ffe_minimize_bands(self.handle, params, search, stream)
+        return ffe_minimize_bands(self.handle, params, search, stream, self.nbands)
 
     def phase_scan(self, *a, **k):
         return ffe_phase_scan(self.handle, *a, **k)

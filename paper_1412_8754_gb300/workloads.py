@@ -32,6 +32,14 @@ def fflo_scan(N=1024, n_q=64, n_h=32, n_delta=256, T=0.002):
                 h=np.linspace(0.0, 0.15, n_h), T=np.array([T]), lo=0.0, hi=0.2, n=n_delta)
 
 
+def threeband_scan(N=1024, n_q=16, n_h=16, n_delta=64, T=0.001):
+    """Phase scan of the three-band model (App. B, eV): q along x in [0, 0.1 pi], h in
+    [0, 0.03], Delta in [0, 0.05]; with U = 1.2 eV the gap is ~0.02 eV at h = 0 and the
+    Pauli limit near h = 0.014 eV."""
+    return dict(N=N, qx=np.linspace(0.0, 0.1 * math.pi, n_q), qy=np.zeros(n_q),
+                h=np.linspace(0.0, 0.03, n_h), T=np.array([T]), lo=0.0, hi=0.05, n=n_delta, U=1.2)
+
+
 def uneven_jobs(n_jobs=512, seed=1234, sizes=(256, 512, 1024, 2048)):
     rng = np.random.default_rng(seed)
     N = rng.choice(np.array(sizes), size=n_jobs)
