@@ -11,6 +11,7 @@ Layout:
   ffe_oracle.c   Eq. freeene / Eq. enequasiparticle / App. A in plain C (FP64)
   search.py      grid argmin, golden-section search and phase labels (Alg. 1)
   threeband.py   the three-band model of App. B (eigvalsh of its 3x3 matrix + the C k-sum)
+  chi.py         the static Cooper pair susceptibility of App. C
   mlp.py         FP64 reference of the surrogate MLP (forward, backward, Adam)
 
 Parity status of each function is listed in the module docstrings; every
@@ -92,6 +93,8 @@ def lib():
             L.ffeo_omega_given_batch.argtypes = ([ctypes.c_int, ctypes.c_int, dp, dp] + [ctypes.c_double] * 3
                                                  + [ctypes.c_int64] + [dp] * 5 + [ctypes.c_int])
             L.ffeo_omega_given_batch.restype = ctypes.c_int
+            L.ffeo_chi_given.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp] + [ctypes.c_double] * 3 + [dp]
+            L.ffeo_chi_given.restype = None
             L.ffeo_max_threads.argtypes = []
             L.ffeo_max_threads.restype = ctypes.c_int
             _lib = L

@@ -189,6 +189,42 @@ int ffeo_omega_given_batch(int nb, int N, const double* e_up, const double* e_dn
   return used;
 }
 
+/* Fermi function f(E) = 1 / (1 + exp(E/T)), without overflow. */
+static double fermi(double E, double T) {
+  if (E >= 0.0) {
+    double x = exp(-E / T);
+    return x / (1.0 + x);
+  }
+  return 1.0 / (1.0 + exp(E / T));
+}
+
+/* Static Cooper pair susceptibility (App. C) from given band energies,
+ * e_up[k*nb + e] = E_e at the spin-up momentum of k, e_dn[k*nb + e'] = E_e' at
+ * the spin-down momentum, eta2[k] the squared structure factor:
+ *   chi_{e e'} = -(1/N^2) sum_k eta2 G,  G = [f(-E_up) - f(E_dn)] / (0 - E_up - E_dn)
+ * with E_up = e_up - mu - h, E_dn = e_dn - mu + h.  Where E_up + E_dn is below
+ * 1e-7 T the quotient takes its limit, -f'(-E_up) = f(-E_up) f(E_up) / T.
+ * chi[e*nb + e'] (Neumaier sums). */
+void ffeo_chi_given(int nb, int N, const double* e_up, const double* e_dn,
+                    const double* eta2, double mu, double h, double T, double* chi) {
+  nsum acc[64];
+  for (int i = 0; i < nb * nb; ++i) acc[i].s = acc[i].c = 0.0;
+  const int64_t nk = (int64_t)N * N;
+  for (int64_t k = 0; k < nk; ++k)
+    for (int e = 0; e < nb; ++e)
+      for (int f = 0; f < nb; ++f) {
+        double Eu = e_up[k * nb + e] - mu - h;
+        double Ed = e_dn[k * nb + f] - mu + h;
+        double sum = Eu + Ed, q;
+        if (fabs(sum) > 1e-7 * T)
+          q = (fermi(-Eu, T) - fermi(Ed, T)) / sum; /* = -G */
+        else
+          q = fermi(-Eu, T) * fermi(Eu, T) / T;
+        nsum_add(&acc[e * nb + f], eta2[k] * q);
+      }
+  for (int i = 0; i < nb * nb; ++i) chi[i] = nsum_value(&acc[i]) / (double)nk;
+}
+
 /* A batch of independent points, parallel over points with OpenMP.
  * nthreads <= 0 uses the OpenMP default.  Returns the thread count used. */
 int ffeo_omega_batch(const ffeo_model* m, int64_t n, const int32_t* N,
