@@ -337,6 +337,19 @@ FFE_API ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* s, const 
                                       const ffe_guide* guide, ffe_result* per_point, int8_t* labels,
                                       int32_t* best_q, ffe_guide_stats* stats, void* stream);
 
+/* ---- static Cooper pair susceptibility (App. C) ------------------------
+ * chi[n_q][nb][nb] (nb = 2 or 3 bands of the model, ascending) at pair
+ * momenta q = (qx[i], qy[i]):
+ *   chi_{e e'}(q) = (1/N^2) sum_k eta(-k-q)^2 [1 - f(E_{e,k,up}) - f(E_{e',-k-q,down})]
+ *                                            / (E_{e,k,up} + E_{e',-k-q,down}),
+ * E_{e,k,up} = E_e(k) - mu - h, E_{e',-k-q,down} = E_e'(-k-q) - mu + h, f the
+ * Fermi function at T > 0, eta = eta_amp cos kx cos ky of the context (App. C
+ * uses eta_amp = 4), k over the N x N lattice; the quotient takes its limit
+ * where the denominator vanishes.  FP64.  Host arrays; synchronous on
+ * `stream`.  A peak of chi_{ee}(q) at q != 0 indicates the FF phase. */
+FFE_API ffe_status ffe_pair_susceptibility(ffe_context* ctx, int32_t N, int32_t n_q, const double* qx,
+                                           const double* qy, double h, double T, double* chi, void* stream);
+
 /* ---- Omega without any allocation (no counterpart in the paper) --------
  * For callers that cannot allocate device memory when they need a free
  * energy -- a service that has given all free device memory to its own pool

@@ -155,6 +155,60 @@ __device__ __forceinline__ void band_pair(const ModelParams& m, Real cx, Real cy
   hi = mean + root;
 }
 
+// ---- three-band model (App. B): eigenvalues of its hopping matrix -------
+// Its 3x3 hopping matrix has real T11, T22, T33, T12 and purely imaginary
+// T13 = i x, T23 = i y; conjugating with diag(1, 1, i) turns it into the real
+// symmetric matrix with off-diagonals T12, -x, -y and the same eigenvalues,
+// which cyclic Jacobi rotations (Jacobi 1846; the rotation of Rutishauser's
+// formulation) diagonalise in FP64.
+// One Jacobi rotation zeroing a_pq of a symmetric 3x3 matrix; r is the third index.
+__device__ __forceinline__ void jacobi_rotate(double& app, double& aqq, double& apq, double& arp, double& arq) {
+  if (apq == 0.0) return;
+  const double theta = (aqq - app) / (2.0 * apq);
+  double t;
+  if (fabs(theta) > 1e150)
+    t = 0.5 / theta;
+  else
+    t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+  const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+  app -= t * apq;
+  aqq += t * apq;
+  apq = 0.0;
+  const double rp = c * arp - s * arq, rq = s * arp + c * arq;
+  arp = rp;
+  arq = rq;
+}
+
+// Eigenvalues, ascending, of the three-band matrix at momentum (cos, sin) of
+// each axis.
+__device__ __forceinline__ void bands3_at(const ModelParams& m, double cx, double sx, double cy, double sy,
+                                          double& e0, double& e1, double& e2) {
+  const double c2x = 2.0 * cx * cx - 1.0, c2y = 2.0 * cy * cy - 1.0;
+  double a00 = 2.0 * m.t2 * cx + 2.0 * m.t1 * cy + 4.0 * m.t3 * cx * cy + 2.0 * m.t11 * (c2x - c2y) +
+               4.0 * m.t12 * c2x * c2y;
+  double a11 = 2.0 * m.t1 * cx + 2.0 * m.t2 * cy + 4.0 * m.t3 * cx * cy - 2.0 * m.t11 * (c2x - c2y) +
+               4.0 * m.t12 * c2x * c2y;
+  double a22 = m.eps0 + 2.0 * m.t5 * (cx + cy) + 4.0 * m.t6 * cx * cy + 2.0 * m.t9 * (c2x + c2y) +
+               4.0 * m.t10 * (c2x * cy + cx * c2y);
+  double a01 = 4.0 * m.t4 * sx * sy;
+  double a02 = -(2.0 * m.t7 * sx + 4.0 * m.t8 * sx * cy);
+  double a12 = -(2.0 * m.t7 * sy + 4.0 * m.t8 * sy * cx);
+  // until the off-diagonal is 1e-14 of the diagonal (eigenvalue error below 1e-14 of the
+  // band width even at a degeneracy); quadratic convergence takes 3 to 4 sweeps
+  for (int sweep = 0; sweep < 8; ++sweep) {
+    const double off = fabs(a01) + fabs(a02) + fabs(a12);
+    if (off <= 1e-14 * (fabs(a00) + fabs(a11) + fabs(a22) + 1e-300)) break;
+    jacobi_rotate(a00, a11, a01, a02, a12);  // (p, q) = (0, 1), r = 2
+    jacobi_rotate(a00, a22, a02, a01, a12);  // (0, 2), r = 1
+    jacobi_rotate(a11, a22, a12, a01, a02);  // (1, 2), r = 0
+  }
+  // sort the diagonal
+  double lo = fmin(a00, fmin(a11, a22)), hi = fmax(a00, fmax(a11, a22));
+  e0 = lo;
+  e2 = hi;
+  e1 = a00 + a11 + a22 - lo - hi;
+}
+
 // Per-k state: eta^2 and, per band, |s|, s^2 (floored at 1e-30 so that
 // rsqrt stays finite), d0 = (E(k+Q/2) - E(k-Q/2))/2.
 template <typename Real>

@@ -81,6 +81,8 @@ _SIGNATURES = [
     ("ffe_omega", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP]),
     ("ffe_minimize", ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, _VP, _VP, _VP]),
     ("ffe_minimize_bands", ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, _VP]),
+    ("ffe_pair_susceptibility", ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, ctypes.c_double,
+                                               ctypes.c_double, _VP, _VP]),
     ("ffe_phase_scan", ctypes.c_int, [_VP, ctypes.POINTER(ffe_scan), _VP, _VP, _VP, _VP]),
     ("ffe_plan_phase_scan", ctypes.c_int, [_VP, ctypes.POINTER(ffe_scan), _VP, ctypes.POINTER(_VP)]),
     ("ffe_plan_execute", ctypes.c_int, [_VP, _VP]),
@@ -279,6 +281,16 @@ def ffe_minimize_bands(ctx, params: np.ndarray, search=FFE_SEARCH_GRID, stream=N
     return res
 
 
+def ffe_pair_susceptibility(ctx, N, qx, qy, h, T, nb=2, stream=None):
+    """chi[n_q, nb, nb] of App. C at the pair momenta (qx[i], qy[i])."""
+    qx = np.ascontiguousarray(np.atleast_1d(qx), dtype=np.float64)
+    qy = np.ascontiguousarray(np.broadcast_to(np.asarray(qy, dtype=np.float64), qx.shape))
+    out = np.zeros((len(qx), nb, nb))
+    _check(ctx, lib().ffe_pair_susceptibility(ctx, int(N), len(qx), _ptr(qx), _ptr(qy), float(h), float(T),
+                                              _ptr(out), _stream(stream)))
+    return out
+
+
 def ffe_minimize(ctx, params: np.ndarray, search=FFE_SEARCH_GRID, want_grid=False, stream=None):
     ps = np.ascontiguousarray(params, dtype=PARAM_DTYPE)
     res = np.zeros(len(ps), dtype=RESULT_DTYPE)
@@ -414,6 +426,9 @@ class Context:
 
     def minimize(self, params, search=FFE_SEARCH_GRID, want_grid=False, stream=None):
         return ffe_minimize(self.handle, params, search, want_grid, stream)
+
+    def pair_susceptibility(self, N, qx, qy, h, T, stream=None):
+        return ffe_pair_susceptibility(self.handle, N, qx, qy, h, T, self.nbands, stream)
 
     def minimize_bands(self, params, search=FFE_SEARCH_GRID, stream=None):
         return ffe_minimize_bands(self.handle, params, search, stream, self.nbands)
