@@ -42,16 +42,21 @@ ffe_status cuda_fail(ffe_context* c, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
   } while (0)
 
+// A plan's buffers are carved from one device allocation: plan_alloc runs its
+// list of requests twice, first to add up the sizes (arena == nullptr), then
+// to hand out 256-byte aligned pieces of the arena.
+struct Arena {
+  unsigned char* base = nullptr;
+  size_t off = 0;
+};
+
 template <typename T>
-static ffe_status dev_alloc(ffe_context* ctx, ffe_plan* p, T** ptr, size_t count) {
-  *ptr = nullptr;
+static ffe_status dev_alloc(ffe_context*, ffe_plan* p, Arena& a, T** ptr, size_t count) {
   if (count == 0) count = 1;
-  void* raw = nullptr;
-  cudaError_t e = cudaMalloc(&raw, count * sizeof(T));
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
-  p->allocs.push_back(raw);
-  p->bytes += count * sizeof(T);
-  *ptr = static_cast<T*>(raw);
+  const size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+  *ptr = a.base ? reinterpret_cast<T*>(a.base + a.off) : nullptr;
+  a.off += bytes;
+  if (a.base) p->bytes += count * sizeof(T);
   return FFE_OK;
 }
 
@@ -234,11 +239,11 @@ double plan_k_evals(const ffe_plan* p) {
   return p->golden_steps > 0 ? s * (3.0 + p->golden_steps) : s;
 }
 
-// Allocate device buffers for the host tables already in *p.
-ffe_status plan_alloc(ffe_context* ctx, ffe_plan* p) {
+// The buffers of a plan (sizes from the host tables already in *p).
+static ffe_status plan_alloc_requests(ffe_context* ctx, ffe_plan* p, Arena& arena) {
   ffe_status st;
 #define ALLOC(ptr, n)                               \
-  if ((st = dev_alloc(ctx, p, &p->ptr, (n))) != FFE_OK) return st;
+  if ((st = dev_alloc(ctx, p, arena, &p->ptr, (n))) != FFE_OK) return st;
   int64_t tab_rows = 0, hcount = 0;
   for (const GroupDesc& g : p->groups) {
     tab_rows = std::max<int64_t>(tab_rows, g.tab_off + 2 * (int64_t)g.N);
@@ -297,6 +302,12 @@ ffe_status plan_alloc(ffe_context* ctx, ffe_plan* p) {
   ALLOC(d_e3d, e3_rows);
   ALLOC(d_e3f, e3_rows);
 #undef ALLOC
+  return FFE_OK;
+}
+
+// Clears counters and uploads the host tables into the plan's buffers.
+static ffe_status plan_upload_tables(ffe_context* ctx, ffe_plan* p) {
+  ffe_status st;
   cudaStream_t s = p->stream;
   FFE_CU(cudaMemsetAsync(p->d_Mcnt, 0, sizeof(int32_t) * std::max(1, p->n_mcounters), s), "memset");
   FFE_CU(cudaMemsetAsync(p->d_segcnt, 0, sizeof(int32_t) * std::max<size_t>(1, p->segs.size()), s), "memset");
@@ -308,6 +319,25 @@ ffe_status plan_alloc(ffe_context* ctx, ffe_plan* p) {
   if ((st = upload(ctx, p->d_lines, p->lines, s)) != FFE_OK) return st;
   return plan_upload_params(ctx, p, s);
 }
+
+// Allocate device buffers for the host tables already in *p and upload them.
+ffe_status plan_alloc(ffe_context* ctx, ffe_plan* p) {
+  ffe_status st = FFE_OK;
+  Arena arena;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) {  // one allocation for every buffer of the plan
+      void* raw = nullptr;
+      cudaError_t e = cudaMalloc(&raw, std::max<size_t>(arena.off, 256));
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+      p->allocs.push_back(raw);
+      arena.base = static_cast<unsigned char*>(raw);
+      arena.off = 0;
+    }
+    if ((st = plan_alloc_requests(ctx, p, arena)) != FFE_OK) return st;
+  }
+  return plan_upload_tables(ctx, p);
+}
+
 
 // The per-call inputs: Delta values, (h, T) entries, distinct h lists and Q.
 ffe_status plan_upload_params(ffe_context* ctx, ffe_plan* p, cudaStream_t s) {
@@ -546,6 +576,11 @@ ffe_status plan_finish(ffe_context* ctx, ffe_plan* p, bool use_graph) {
 }
 
 ffe_status plan_run(ffe_context* ctx, ffe_plan* p, cudaStream_t s) {
+  {
+    const int slot = (int)(p->exec_count % kRing);
+    if (!p->ring0[slot]) FFE_CU(cudaEventCreate(&p->ring0[slot]), "event");
+    if (!p->ring1[slot]) FFE_CU(cudaEventCreate(&p->ring1[slot]), "event");
+  }
   if (p->exec) {
     const int slot = (int)(p->exec_count % kRing);
     FFE_CU(cudaGraphExecEventRecordNodeSetEvent(p->exec, p->node_ev0, p->ring0[slot]), "set event");
@@ -578,11 +613,7 @@ ffe_plan* plan_new(ffe_context* ctx, int kind) {
   p->prec = ctx->model.prec;
   cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
   cudaEventCreate(&p->ev_cap0);
-  cudaEventCreate(&p->ev_cap1);
-  for (int i = 0; i < kRing; ++i) {
-    cudaEventCreate(&p->ring0[i]);
-    cudaEventCreate(&p->ring1[i]);
-  }
+  cudaEventCreate(&p->ev_cap1);  // the timing ring's events are made on first use (plan_run)
   return p;
 }
 
