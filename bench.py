@@ -35,16 +35,16 @@ SFU_OTHER_PER_CLK = 16
 SM_MAX_MHZ = 2070.0
 
 
-def sfu_clk_per_keval(n_ht: int):
-    """SFU time (SM clocks) per k-evaluation in the shared-Delta scan layout,
-    (near, far).  A far k-evaluation (every log factor 1 in FP32) needs only
-    R and a: 2 rsqrt + 2 rcp per (k, Delta), shared by the (up to 32) (h, T)
-    outputs of one batch.  A near one adds 4 ex2 + 1 lg2 per output and
-    computes R and a a second time (once in the far pass, once in the
-    full-term pass)."""
+def sfu_clk_per_band_eval(n_ht: int):
+    """SFU time (SM clocks) per band evaluation (one k-point, one band, one output) in the
+    shared-Delta scan layout, (near, far).  A far band (its log factors 1 in FP32) needs only
+    R and a: 1 rsqrt + 1 rcp per (k, Delta, band), shared by the (up to 32) (h, T) outputs of
+    one batch.  A near band is evaluated in full, packed with another near band in a float2
+    slot: per output 2 ex2 and half of one lg2, and its R and a a second time (once in the
+    far pass, once in the full-term pass)."""
     per_batch = min(32, n_ht)
-    ra = 4.0 / (SFU_OTHER_PER_CLK * per_batch)
-    return 4.0 / SFU_EX2_PER_CLK + 1.0 / SFU_OTHER_PER_CLK + 2.0 * ra, ra
+    ra = 2.0 / (SFU_OTHER_PER_CLK * per_batch)
+    return 2.0 / SFU_EX2_PER_CLK + 0.5 / SFU_OTHER_PER_CLK + 2.0 * ra, ra
 
 
 def dist_env():
@@ -121,9 +121,9 @@ def cpu_baseline(cfg, seconds_target=15.0):
 
 
 # DRAM bytes (read + write) of one k-sum launch of the default workload, from
-# ncu (dram__bytes_read.sum 17.44 MB + dram__bytes_write.sum 229.48 MB, one
-# pass on the full-size launch); set back to None when the kernel changes.
-DRAM_TRAFFIC_PER_LAUNCH = 246.92e6
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum, one pass on the full-size
+# launch); None until captured for the current kernel.
+DRAM_TRAFFIC_PER_LAUNCH = None
 
 
 def run_extras(ffe, np, torch, stream, workloads):
@@ -422,10 +422,11 @@ def main():
 
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
-    c_near, c_far = sfu_clk_per_keval(n_pts)
-    k_near = plan.stats()["k_evals_near"]
-    near_frac = k_near / k_evals if k_evals else 0.0
-    clk_per_keval = near_frac * c_near + (1.0 - near_frac) * c_far
+    c_near, c_far = sfu_clk_per_band_eval(n_pts)
+    band_evals = 2.0 * k_evals  # two bands per k-evaluation
+    b_near = plan.stats()["k_evals_near"]  # full-term band evaluations
+    near_frac = b_near / band_evals if band_evals else 0.0
+    clk_per_keval = 2.0 * (near_frac * c_near + (1.0 - near_frac) * c_far)
     peak = n_sm * SM_MAX_MHZ * 1e6 / clk_per_keval  # k-evals/s with the SFU saturated, at the maximum clock
     achieved = k_evals / (kern_ms / 1e3) if kern_ms > 0 else 0.0
 
@@ -443,11 +444,12 @@ def main():
                      "frac": achieved / peak if peak else None, "traffic": DRAM_TRAFFIC_PER_LAUNCH,
                      "kernel": f"ksum_kernel<float,{info['kpt']},shared-Delta>", "kernel_ms": kern_ms,
                      "kernel_launches": kern_n,
-                     "near_fraction": near_frac,
+                     "near_band_fraction": near_frac,
                      "peak_basis": (f"{n_sm} SM x {SM_MAX_MHZ:.0f} MHz / {clk_per_keval:.4f} SFU clocks per "
-                                    f"k-eval = {near_frac:.4f} x {c_near:.4f} (full term) + {1 - near_frac:.4f} x "
-                                    f"{c_far:.4f} (far form); ex2 {SFU_EX2_PER_CLK}/clk, lg2 rsqrt rcp "
-                                    f"{SFU_OTHER_PER_CLK}/clk per SM; unit counts checked by ffe_probe_peaks")},
+                                    f"k-eval = 2 bands x ({near_frac:.4f} x {c_near:.4f} (full term, two bands "
+                                    f"per float2) + {1 - near_frac:.4f} x {c_far:.4f} (far form)); ex2 "
+                                    f"{SFU_EX2_PER_CLK}/clk, lg2 rsqrt rcp {SFU_OTHER_PER_CLK}/clk per SM; unit "
+                                    f"counts checked by ffe_probe_peaks")},
         "fp64": fp64,
         **extras,
         "clocks": clk,

@@ -221,11 +221,13 @@ typedef struct {
   int32_t block, grid;     /* its launch shape (threads, persistent blocks)   */
   int32_t work_items;      /* warp work items in its queue                    */
   int32_t reserved;
-  double k_evals_near;     /* FP32: those of the last completed execution that
-                              took the full term; the others were "far" (every
-                              log term 1 in FP32, W = c a: one R and a per
-                              (k, Delta) shared by the outputs); 0 for FP64,
-                              -1 before the first execution                   */
+  double k_evals_near;     /* FP32: band evaluations (one k, one band, one
+                              output) of the last completed execution that took
+                              the full term; the others were "far" (log terms 1
+                              in FP32, W = c a: one R and a per (k, Delta, band)
+                              shared by the outputs).  A k-evaluation covers
+                              every band.  0 for FP64, -1 before the first
+                              execution                                       */
 } ffe_plan_info;
 
 /* Static facts about a plan, the FP64 re-evaluation counts of the last

@@ -301,9 +301,11 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
   return r;
 }
 
-// Per-k FP32 state with the two bands packed: eta^2, |s|, s^2, d0.
+// FP32 state of two (k-point, band) entries packed as the halves of float2
+// operations: eta^2, |s|, s^2, d0.  Either the two bands of one k-point, or
+// the near bands of two k-points.
 struct KState32 {
-  float eta2;
+  float2 eta2;
   float2 as, s2, d0;
 };
 

@@ -22,12 +22,9 @@
 
 namespace ffe {
 
-// Capacity of a warp's k-point buffer: a flush takes 32 KPT entries and a
-// k-set adds at most 32 KPT (KPT <= 8).  An entry is a lattice index
-// (< 8192^2 < 2^30) with the band pair in bit 30.
-constexpr int kKBuf = 2 * 32 * 8;
-constexpr int kPairShift = 30;
-constexpr int32_t kKidxMask = (1 << kPairShift) - 1;
+// A warp's (k-point, band) entry buffers: a flush takes 64 KPT entries (two
+// per float2 slot) and a k-set adds at most 64 KPT, so 128 KPT entries each.
+__host__ __device__ constexpr int kbuf_entries(int kpt) { return 128 * kpt; }
 
 // Batch parameters staged in shared memory, one entry per output of a batch.
 struct BParF {  // FP32: Delta^2 (LIST only), h, c = 1/(T ln 2), T ln 2
@@ -150,44 +147,50 @@ __device__ __forceinline__ void build_states32(const KsumArgs& a, const GroupDes
   build_states<float, KPT>(a, g, ks, lane, pair, s);
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
-    st[k].eta2 = s[k].eta2;
+    st[k].eta2 = make_float2(s[k].eta2, s[k].eta2);
     st[k].as = make_float2(s[k].as[0], s[k].as[1]);
     st[k].s2 = make_float2(s[k].s2[0], s[k].s2[1]);
     st[k].d0 = make_float2(s[k].d0[0], s[k].d0[1]);
   }
 }
 
-// The FP32 state of lattice point kidx (< N^2) of group g, band pair `pair`.
-__device__ __forceinline__ KState32 state32_at(const KsumArgs& a, const GroupDesc& g, int32_t kidx, int pair) {
+// A buffered (k-point, band) entry: lattice index | band pair << kPairBit |
+// band slot << kSlotBit (lattice index < 8192^2 = 2^26).
+constexpr int kPairBit = 27, kSlotBit = 28;
+constexpr int32_t kKidxMask = (1 << 26) - 1;
+
+// One band of one entry: eta^2, |s|, s^2, d0; an inert band past the end.
+struct Band32 {
+  float eta2, as, s2, d0;
+};
+
+__device__ __forceinline__ Band32 band32_at(const KsumArgs& a, const GroupDesc& g, int32_t e) {
   KState<float> s;
-  state_at<float>(a, g, kidx, pair, s);
+  state_at<float>(a, g, e & kKidxMask, (e >> kPairBit) & 1, s);
+  const int b = (e >> kSlotBit) & 1;
+  return Band32{s.eta2, s.as[b], s.s2[b], s.d0[b]};
+}
+
+__device__ __forceinline__ Band32 band32_inert() { return Band32{0.0f, 1e15f, 1e30f, 0.0f}; }
+
+__device__ __forceinline__ KState32 pack32(const Band32& x, const Band32& y) {
   KState32 t;
-  t.eta2 = s.eta2;
-  t.as = make_float2(s.as[0], s.as[1]);
-  t.s2 = make_float2(s.s2[0], s.s2[1]);
-  t.d0 = make_float2(s.d0[0], s.d0[1]);
+  t.eta2 = make_float2(x.eta2, y.eta2);
+  t.as = make_float2(x.as, y.as);
+  t.s2 = make_float2(x.s2, y.s2);
+  t.d0 = make_float2(x.d0, y.d0);
   return t;
 }
 
-__device__ __forceinline__ void state32_invalid(KState32& t) {
-  t.eta2 = 0.0f;
-  t.as = make_float2(1e15f, 1e15f);
-  t.s2 = make_float2(1e30f, 1e30f);
-  t.d0 = make_float2(0.0f, 0.0f);
+// Far band (see api.cu, item_far_window): for every output of the item the
+// band has c |R -+ d| >= 40, so its W is c a exactly in FP32.
+__device__ __forceinline__ bool far_band32(float as, float d0, const WorkItem& w) {
+  return as - fmaxf(fabsf(d0 - w.far_hlo), fabsf(d0 - w.far_hhi)) >= w.far_tgap;
 }
 
-// Far k-point (see api.cu, item_far_window): for every output of the item
-// both bands have c |R -+ d| >= 40, so W = c (a_0 + a_1) exactly in FP32.
-__device__ __forceinline__ bool far32(const KState32& t, const WorkItem& w) {
-  const float dx = fmaxf(fabsf(t.d0.x - w.far_hlo), fabsf(t.d0.x - w.far_hhi));
-  const float dy = fmaxf(fabsf(t.d0.y - w.far_hlo), fabsf(t.d0.y - w.far_hhi));
-  return fminf(t.as.x - dx, t.as.y - dy) >= w.far_tgap;
-}
-
-// R and a = Delta^2 eta^2 / (R + |s|) of both bands at Delta^2 = d2.
+// R and a = Delta^2 eta^2 / (R + |s|) of both halves at Delta^2 = d2.
 __device__ __forceinline__ void ra32(const KState32& st, float d2, float2& R, float2& A) {
-  const float D = d2 * st.eta2;
-  const float2 D2 = make_float2(D, D);
+  const float2 D2 = __fmul2_rn(make_float2(d2, d2), st.eta2);
   const float2 u = __fadd2_rn(D2, st.s2);
   R = __fmul2_rn(u, make_float2(rsqa(u.x), rsqa(u.y)));
   const float2 den = __fadd2_rn(R, st.as);
@@ -396,8 +399,8 @@ __device__ void finalize_segment(const KsumArgs& a, const Segment& sg, const Gro
   }
 }
 
-// FP32 evaluation of n buffered k-points (lattice indices in buf) on every
-// batch of the item: the full term, or the far form W = c (a_0 + a_1).
+// FP32 evaluation of n buffered (k-point, band) entries on every batch of the
+// item, two entries per float2 slot: the full term, or the far form W = c a.
 template <int KPT, int LAYOUT, bool FAR>
 __device__ __forceinline__ void flush32(const KsumArgs& a, const WorkItem& w, const GroupDesc& g, int lane,
                                         const int32_t* buf, int n, double* acc, BParF* bp, float* red) {
@@ -405,11 +408,10 @@ __device__ __forceinline__ void flush32(const KsumArgs& a, const WorkItem& w, co
   KState32 st[KPT];
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
-    const int i = k * 32 + lane;
-    if (i < n)
-      st[k] = state32_at(a, g, buf[i] & kKidxMask, buf[i] >> kPairShift);
-    else
-      state32_invalid(st[k]);
+    const int i0 = 2 * k * 32 + lane, i1 = i0 + 32;
+    const Band32 x = i0 < n ? band32_at(a, g, buf[i0]) : band32_inert();
+    const Band32 y = i1 < n ? band32_at(a, g, buf[i1]) : band32_inert();
+    st[k] = pack32(x, y);
   }
   int64_t outs = 0;
   for (int b = w.b0; b < w.b1; ++b) {
@@ -428,44 +430,47 @@ __device__ __forceinline__ void flush32(const KsumArgs& a, const WorkItem& w, co
   if (!FAR && a.near_evals && lane == 0) atomicAdd(a.near_evals, (unsigned long long)(n * outs));
 }
 
-// Drops the first `done` entries of a warp's k-point buffer of n entries.
+// Drops the first `done` entries of a warp's buffer of n entries.
 __device__ __forceinline__ void buffer_shift(int32_t* buf, int done, int n, int lane) {
   __syncwarp();
   for (int i = lane; i < n - done; i += 32) buf[i] = buf[done + i];  // n - done < done: no overlap
   __syncwarp();
 }
 
-// One work item in FP32.  Each k-set's points are split into near and far
-// ones (far32).  Far points cost, per batch, one R and a per band: with a
-// shared Delta (PRODUCT layouts) their a_0 + a_1 is summed over the warp once
-// per batch and applied as c (sum) to every output at the end; with a Delta
-// per output (LIST) they are buffered and evaluated per output in the far
-// form.  Near points are buffered and, once 32 KPT of them are collected,
-// evaluated with the full term for every output, so that a warp always
-// evaluates full k-sets of one kind.
+// One work item in FP32.  Every band of every k-point of a k-set is "far"
+// (far_band32: for all outputs of the item its log terms are 1 in FP32 and
+// W = c a) or "near".  Far bands cost, per batch, their R and a: with a
+// shared Delta (PRODUCT layouts) their a is summed over the warp once per
+// batch and applied as c (sum) to every output at the end; with a Delta per
+// output (LIST) they are buffered and evaluated per output in the far form.
+// Near bands are buffered as (k-point, band) entries and, once 64 KPT of
+// them are collected, evaluated with the full term for every output, two
+// entries per float2 slot -- at a near k-point usually one band is near, so
+// this halves the full-term work against evaluating whole k-points.
 template <int KPT, int LAYOUT>
 __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, const GroupDesc& g, int lane,
                                        double* acc, BParF* bp, float* red, int32_t* nbuf, int32_t* fbuf) {
   constexpr int kG = (LAYOUT == kLayoutList) ? kLayoutList : kLayoutProduct;
-  constexpr int kFlush = 32 * KPT;
+  constexpr int kFlush = 64 * KPT;
   const int64_t nk = (int64_t)g.N * g.N;
   const unsigned lt = (1u << lane) - 1u;
   int n_near = 0, n_far = 0;
-  double far_tot = 0.0;  // PRODUCT: lane (b - b0) holds batch b's sum of a_0 + a_1 over far points
+  double far_tot = 0.0;  // PRODUCT: lane (b - b0) holds batch b's sum of a over far bands
   const int npairs = band_pairs(a.m.nbands);
-  // buffered entries: lattice index | band pair << kPairShift
   for (int ks = w.kset0; ks < w.kset1; ++ks)
   for (int pair = 0; pair < npairs; ++pair) {
     KState32 st[KPT];
     build_states32<KPT>(a, g, ks, lane, pair, st);
-    bool isfar[KPT], valid[KPT];
+    const bool act0 = slot_active(a.m.nbands, g.band_only, pair, 0);
+    const bool act1 = slot_active(a.m.nbands, g.band_only, pair, 1);
+    bool far0[KPT], far1[KPT], valid[KPT];
     int32_t kidx[KPT];
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
-      kidx[k] = ks * kFlush + k * 32 + lane;
+      kidx[k] = ks * (32 * KPT) + k * 32 + lane;
       valid[k] = kidx[k] < nk;
-      isfar[k] = !valid[k] || far32(st[k], w);
-      kidx[k] |= pair << kPairShift;
+      far0[k] = !act0 || !valid[k] || far_band32(st[k].as.x, st[k].d0.x, w);
+      far1[k] = !act1 || !valid[k] || far_band32(st[k].as.y, st[k].d0.y, w);
     }
     if constexpr (kG == kLayoutProduct) {
       for (int b = w.b0; b < w.b1; ++b) {
@@ -475,7 +480,10 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
         for (int k = 0; k < KPT; ++k) {
           float2 R, A;
           ra32(st[k], d2p, R, A);
-          if (isfar[k]) S = __fadd2_rn(S, A);
+          // active, valid, far bands only
+          A.x = (far0[k] && act0 && valid[k]) ? A.x : 0.0f;
+          A.y = (far1[k] && act1 && valid[k]) ? A.y : 0.0f;
+          S = __fadd2_rn(S, A);
         }
         float t = S.x + S.y;
 #pragma unroll
@@ -485,15 +493,21 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
     }
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
-      const bool nr = !isfar[k];
-      const unsigned m = __ballot_sync(kFull, nr);
-      if (nr) nbuf[n_near + __popc(m & lt)] = kidx[k];
-      n_near += __popc(m);
-      if constexpr (kG == kLayoutList) {
-        const bool fr = isfar[k] && valid[k];
-        const unsigned mf = __ballot_sync(kFull, fr);
-        if (fr) fbuf[n_far + __popc(mf & lt)] = kidx[k];
-        n_far += __popc(mf);
+#pragma unroll
+      for (int sl = 0; sl < 2; ++sl) {
+        const bool fr = sl == 0 ? far0[k] : far1[k];
+        const bool act = sl == 0 ? act0 : act1;
+        const int32_t e = kidx[k] | (pair << kPairBit) | (sl << kSlotBit);
+        const bool nr = !fr;  // near implies active and valid
+        const unsigned m = __ballot_sync(kFull, nr);
+        if (nr) nbuf[n_near + __popc(m & lt)] = e;
+        n_near += __popc(m);
+        if constexpr (kG == kLayoutList) {
+          const bool fe = fr && act && valid[k];
+          const unsigned mf = __ballot_sync(kFull, fe);
+          if (fe) fbuf[n_far + __popc(mf & lt)] = e;
+          n_far += __popc(mf);
+        }
       }
     }
     __syncwarp();
@@ -534,12 +548,13 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
   unsigned char* after_acc = smem_raw + (size_t)nwarps * kMaxBatchesPerItem * 32 * sizeof(double);
   BPar<Real>* bp = reinterpret_cast<BPar<Real>*>(after_acc) + warp * 32;
   // FP32 only: per-warp 32 x 36 transpose buffer of the output reduction and
-  // two k-point buffers (near, far) of 2 x 32 x kMaxKpt32 lattice indices
+  // the entry buffers (near; far for LIST), kbuf_entries(KPT) each
   unsigned char* after_bp = after_acc + (size_t)nwarps * 32 * sizeof(BPar<Real>);
   float* red = reinterpret_cast<float*>(after_bp) + warp * 32 * 36;
+  constexpr int kBufs = (LAYOUT == kLayoutList) ? 2 : 1;
   int32_t* nbuf = reinterpret_cast<int32_t*>(after_bp + (size_t)nwarps * 32 * 36 * sizeof(float)) +
-                  (size_t)warp * 2 * kKBuf;
-  int32_t* fbuf = nbuf + kKBuf;
+                  (size_t)warp * kBufs * kbuf_entries(KPT);
+  int32_t* fbuf = nbuf + (kBufs - 1) * kbuf_entries(KPT);
   for (;;) {
     int it = 0;
     if (lane == 0) it = atomicAdd(a.queue, 1);
@@ -592,10 +607,11 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
   }
 }
 
-size_t ksum_smem_bytes(int prec, int block_threads) {
+size_t ksum_smem_bytes(int prec, int layout, int kpt, int block_threads) {
   const int nw = block_threads / 32;
   const size_t par = (prec == 1) ? sizeof(BParF) : sizeof(BParD);
-  const size_t red = (prec == 1) ? 32 * 36 * sizeof(float) + 2 * kKBuf * sizeof(int32_t) : 0;
+  const int bufs = layout == kLayoutList ? 2 : 1;
+  const size_t red = (prec == 1) ? 32 * 36 * sizeof(float) + (size_t)bufs * kbuf_entries(kpt) * sizeof(int32_t) : 0;
   return (size_t)nw * (kMaxBatchesPerItem * 32 * sizeof(double) + 32 * par + red);
 }
 
@@ -651,12 +667,12 @@ static cudaError_t occupancy_one(int block, size_t smem, int* blocks_per_sm) {
 
 cudaError_t ksum_launch(int prec, int layout, int kpt, const KsumArgs& a, int grid, int block,
                         cudaStream_t s) {
-  const size_t smem = ksum_smem_bytes(prec, block);
+  const size_t smem = ksum_smem_bytes(prec, layout, kpt, block);
   FFE_KSUM_DISPATCH(launch_one, a, grid, block, smem, s);
 }
 
 cudaError_t ksum_occupancy(int prec, int layout, int kpt, int block, int* blocks_per_sm) {
-  const size_t smem = ksum_smem_bytes(prec, block);
+  const size_t smem = ksum_smem_bytes(prec, layout, kpt, block);
   FFE_KSUM_DISPATCH(occupancy_one, block, smem, blocks_per_sm);
 }
 

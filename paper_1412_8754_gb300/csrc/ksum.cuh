@@ -40,7 +40,7 @@ struct KsumArgs {
   const E3D* e3d;                  // and FP64
 };
 
-size_t ksum_smem_bytes(int prec, int block_threads);
+size_t ksum_smem_bytes(int prec, int layout, int kpt, int block_threads);
 cudaError_t ksum_launch(int prec, int layout, int kpt, const KsumArgs& a, int grid, int block,
                         cudaStream_t s);
 cudaError_t ksum_occupancy(int prec, int layout, int kpt, int block, int* blocks_per_sm);
