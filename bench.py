@@ -40,11 +40,11 @@ def sfu_clk_per_band_eval(n_ht: int):
     shared-Delta scan layout, (near, far).  A far band (its log factors 1 in FP32) needs only
     R and a: 1 rsqrt + 1 rcp per (k, Delta, band), shared by the (up to 32) (h, T) outputs of
     one batch.  A near band is evaluated in full, packed with another near band in a float2
-    slot: per output 2 ex2 and half of one lg2, and its R and a a second time (once in the
-    far pass, once in the full-term pass)."""
+    slot: per output 2 ex2 and an eighth of one lg2 (one lg2 per output over a lane's four
+    slots), and its R and a a second time (once in the far pass, once in the full-term pass)."""
     per_batch = min(32, n_ht)
     ra = 2.0 / (SFU_OTHER_PER_CLK * per_batch)
-    return 2.0 / SFU_EX2_PER_CLK + 0.5 / SFU_OTHER_PER_CLK + 2.0 * ra, ra
+    return 2.0 / SFU_EX2_PER_CLK + 0.125 / SFU_OTHER_PER_CLK + 2.0 * ra, ra
 
 
 def dist_env():
@@ -121,9 +121,9 @@ def cpu_baseline(cfg, seconds_target=15.0):
 
 
 # DRAM bytes (read + write) of one k-sum launch of the default workload, from
-# ncu (dram__bytes_read.sum 16.44 MB + dram__bytes_write.sum 230.17 MB, one
-# pass on the full-size launch); set back to None when the kernel changes.
-DRAM_TRAFFIC_PER_LAUNCH = 246.61e6
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum, one pass on the full-size
+# launch); None until captured for the current kernel.
+DRAM_TRAFFIC_PER_LAUNCH = None
 
 
 def run_extras(ffe, np, torch, stream, workloads):

@@ -309,9 +309,10 @@ struct KState32 {
   float2 as, s2, d0;
 };
 
-// One k-point, both bands, one (h, c): adds c min(...) of each band to cp2 and
-// returns log2 of the product of the four (1 + e) factors.
-// Rc = R c and ac = a c per band; nh2 = (-h, -h); c2 = (c, c); nc2 = -c2.
+// One float2 slot (two entries), one (h, c): adds c min(...) of each entry to
+// cp2 and returns the product of the four (1 + e) factors, in [1, 16] (the
+// caller takes one lg2 of the product over its slots).
+// Rc = R c and ac = a c per entry; nh2 = (-h, -h); c2 = (c, c); nc2 = -c2.
 __device__ __forceinline__ float w_term32(const KState32& st, float2 Rc, float2 ac, float2 nh2, float2 c2,
                                           float2 nc2, float2& cp2) {
   const float2 d = __fadd2_rn(st.d0, nh2);  // d = d0 - h
@@ -323,7 +324,7 @@ __device__ __forceinline__ float w_term32(const KState32& st, float2 Rc, float2 
   const float2 p = __ffma2_rn(o1, e2, o1);
   const float2 cp = make_float2(fmaxf(min3f(y1.x, y2.x, ac.x), 0.0f), fmaxf(min3f(y1.y, y2.y, ac.y), 0.0f));
   cp2 = __fadd2_rn(cp2, cp);
-  return lg2a(p.x * p.y);
+  return p.x * p.y;
 }
 __device__ __forceinline__ void ra_f64(double D, double s2, double as, double& R, double& a) {
   R = sqrt(D + s2);

@@ -197,16 +197,17 @@ __device__ __forceinline__ void ra32(const KState32& st, float d2, float2& R, fl
   A = __fmul2_rn(D2, make_float2(rcpa(den.x), rcpa(den.y)));
 }
 
-// W of one output (both bands) summed over this lane's KPT k-points.
+// W of one output summed over this lane's KPT slots: the clamp terms plus
+// one lg2 of the product of all (1 + e) factors (at most 16^KPT <= 2^32).
 template <int KPT>
 __device__ __forceinline__ float w_out32(const KState32 (&st)[KPT], const float2 (&Rc)[KPT],
                                          const float2 (&Ac)[KPT], float h, float c) {
   const float2 nh2 = make_float2(-h, -h), c2 = make_float2(c, c), nc2 = make_float2(-c, -c);
   float2 cp2 = make_float2(0.0f, 0.0f);
-  float L = 0.0f;
+  float P = 1.0f;
 #pragma unroll
-  for (int k = 0; k < KPT; ++k) L += w_term32(st[k], Rc[k], Ac[k], nh2, c2, nc2, cp2);
-  return (cp2.x + cp2.y) + L;
+  for (int k = 0; k < KPT; ++k) P *= w_term32(st[k], Rc[k], Ac[k], nh2, c2, nc2, cp2);
+  return (cp2.x + cp2.y) + lg2a(P);
 }
 
 // Lane l: the sum of row l of the warp's transpose buffer (0 for l >= nvalid).

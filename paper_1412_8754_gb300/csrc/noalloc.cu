@@ -44,7 +44,8 @@ constexpr size_t kOffC0D = align256(kOffTabD + 2 * kNAMaxN * sizeof(TabRowD));
 constexpr size_t kOffTabDF = align256(kOffC0D + 2 * kNAMaxN * sizeof(double));
 constexpr size_t kOffGroup = align256(kOffTabDF + 2 * kNAMaxN * sizeof(TabRowDF));
 constexpr size_t kOffSeg = align256(kOffGroup + sizeof(GroupDesc));
-constexpr size_t kOffItems = align256(kOffSeg + sizeof(Segment));
+constexpr int kNAMaxSegs = (kNAMaxOut / 32 + kMaxBatchesPerItem - 1) / kMaxBatchesPerItem;
+constexpr size_t kOffItems = align256(kOffSeg + kNAMaxSegs * sizeof(Segment));
 constexpr size_t kOffMItems = align256(kOffItems + kNAMaxItems * sizeof(WorkItem));
 constexpr size_t kOffD2F = align256(kOffMItems + kNAMaxMItems * sizeof(MItem));
 constexpr size_t kOffHT = align256(kOffD2F + kNAMaxOut * sizeof(float));
@@ -55,11 +56,12 @@ constexpr size_t kOffM = align256(kOffHList + kNAMaxOut * sizeof(double));
 constexpr size_t kOffMPart = align256(kOffM + kNAMaxOut * sizeof(double));
 constexpr size_t kOffMCnt = align256(kOffMPart + size_t(kNAMaxMItems) * 32 * sizeof(double));
 constexpr size_t kOffPart = align256(kOffMCnt + 64 * sizeof(int32_t));
+// partials: every k-chunk of every batch: <= kNAMaxItems items of <= kMaxBatchesPerItem batches
 constexpr size_t kOffV = align256(kOffPart + size_t(kNAMaxItems) * kMaxBatchesPerItem * 32 * sizeof(double));
 constexpr size_t kOffEB = align256(kOffV + kNAMaxOut * sizeof(double));
 constexpr size_t kOffCnt = align256(kOffEB + kNAMaxOut * sizeof(double));
 constexpr size_t kOffSegCnt = align256(kOffCnt + 8 * sizeof(int32_t));
-constexpr size_t kNAUsed = align256(kOffSegCnt + sizeof(int32_t));
+constexpr size_t kNAUsed = align256(kOffSegCnt + kNAMaxSegs * sizeof(int32_t));
 static_assert(kNAUsed <= kNAScratchBytes, "scratch regions exceed the static array");
 
 // Device address of g_na_scratch per device, obtained once with that device current.
@@ -69,7 +71,7 @@ std::mutex g_na_mutex;
 
 // Host staging of the job table (static storage: no heap use per call).
 GroupDesc g_na_group;
-Segment g_na_seg;
+Segment g_na_segs[kNAMaxSegs];
 WorkItem g_na_items[kNAMaxItems];
 MItem g_na_mitems[kNAMaxMItems];
 
@@ -128,15 +130,25 @@ extern "C" ffe_status ffe_omega_noalloc(const ffe_model* m, int32_t N, double qx
   const int64_t nk = (int64_t)N * N;
   const int kset_pts = 32 * kpt;
   const int n_ksets = (int)((nk + kset_pts - 1) / kset_pts);
+  // segments of <= kMaxBatchesPerItem batches, each split into the same k-chunks
+  const int n_segs = (g.n_batches + kMaxBatchesPerItem - 1) / kMaxBatchesPerItem;
+  const int seg_b = std::min(g.n_batches, kMaxBatchesPerItem);
   const double target = prec == FFE_FP32C ? 8388608.0 : 262144.0;
-  int ck = (int)(target / ((double)g.n_batches * 32.0 * kset_pts));
-  ck = std::max(ck, (n_ksets + kNAMaxItems - 1) / kNAMaxItems);
+  int ck = (int)(target / ((double)seg_b * 32.0 * kset_pts));
+  ck = std::max(ck, (n_ksets * n_segs + kNAMaxItems - 1) / kNAMaxItems);
   ck = std::max(1, std::min(ck, n_ksets));
+  while ((int64_t)((n_ksets + ck - 1) / ck) * n_segs > kNAMaxItems) ++ck;
   const int n_chunks = (n_ksets + ck - 1) / ck;
-  g_na_seg = Segment{0, 0, g.n_batches, n_chunks, 0};
-  for (int c = 0; c < n_chunks; ++c)
-    g_na_items[c] = WorkItem{0, 0, c, c * ck, std::min(n_ksets, (c + 1) * ck), 0, g.n_batches, 0.0f, 0.0f,
-                             INFINITY, {0, 0, 0}};
+  int n_items = 0;
+  int64_t poff = 0;
+  for (int sg = 0; sg < n_segs; ++sg) {
+    const int b0 = sg * kMaxBatchesPerItem, b1 = std::min(g.n_batches, b0 + kMaxBatchesPerItem);
+    g_na_segs[sg] = Segment{0, b0, b1, n_chunks, poff};
+    poff += (int64_t)n_chunks * (b1 - b0) * 32;
+    for (int c = 0; c < n_chunks; ++c)
+      g_na_items[n_items++] = WorkItem{0, sg, c, c * ck, std::min(n_ksets, (c + 1) * ck), b0, b1, 0.0f, 0.0f,
+                                       INFINITY, {0, 0, 0}};
+  }
   const int64_t mchunk = 32768;
   const int m_chunks = (int)((nk + mchunk - 1) / mchunk);
   const int n_hb = (n + 31) / 32;
@@ -149,12 +161,13 @@ extern "C" ffe_status ffe_omega_noalloc(const ffe_model* m, int32_t N, double qx
 
   // clear what must start at zero; stage the job table
   cudaError_t e = cudaMemsetAsync(base + kOffCnt, 0, 8 * sizeof(int32_t), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffSegCnt, 0, sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffSegCnt, 0, n_segs * sizeof(int32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffMCnt, 0, 64 * sizeof(int32_t), s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(base + kOffGroup, &g, sizeof g, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(base + kOffSeg, &g_na_seg, sizeof g_na_seg, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(base + kOffItems, g_na_items, n_chunks * sizeof(WorkItem), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(base + kOffSeg, g_na_segs, n_segs * sizeof(Segment), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(base + kOffItems, g_na_items, n_items * sizeof(WorkItem), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(base + kOffMItems, g_na_mitems, n_mitems * sizeof(MItem), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return FFE_ECUDA;
@@ -184,7 +197,7 @@ extern "C" ffe_status ffe_omega_noalloc(const ffe_model* m, int32_t N, double qx
   a.m = mp;
   a.groups = d_group;
   a.items = reinterpret_cast<const WorkItem*>(base + kOffItems);
-  a.n_items = n_chunks;
+  a.n_items = n_items;
   a.segs = reinterpret_cast<const Segment*>(base + kOffSeg);
   a.queue = reinterpret_cast<int32_t*>(base + kOffCnt);
   a.seg_count = reinterpret_cast<int32_t*>(base + kOffSegCnt);
