@@ -48,13 +48,11 @@ __device__ __forceinline__ void load_row(const KsumArgs& a, int64_t row, TabRowD
   c0 = a.c0d[row];
 }
 
-// The state of lattice point kidx (< N^2) of group g for band pair `pair`.
+// The state of lattice point kidx = iy N + ix (< N^2 <= 2^26) of group g for band pair `pair`.
 template <typename Real>
-__device__ __forceinline__ void state_at(const KsumArgs& a, const GroupDesc& g, int64_t kidx, int pair,
-                                         KState<Real>& st) {
+__device__ __forceinline__ void state_at_xy(const KsumArgs& a, const GroupDesc& g, int ix, int iy, int kidx,
+                                            int pair, KState<Real>& st) {
   using Row = typename std::conditional<std::is_same<Real, float>::value, TabRowF, TabRowD>::type;
-  const int iy = (int)(kidx / g.N);
-  const int ix = (int)(kidx - (int64_t)iy * g.N);
   Row rx, ry;
   Real c0x, c0y;
   load_row<Real>(a, g.tab_off + ix, rx, c0x);
@@ -72,17 +70,33 @@ __device__ __forceinline__ void state_at(const KsumArgs& a, const GroupDesc& g, 
   kstate_mask<Real>(st, a.m.nbands, g.band_only, pair);
 }
 
+template <typename Real>
+__device__ __forceinline__ void state_at(const KsumArgs& a, const GroupDesc& g, int kidx, int pair,
+                                         KState<Real>& st) {
+  const int iy = kidx / g.N;
+  state_at_xy<Real>(a, g, kidx - iy * g.N, iy, kidx, pair, st);
+}
+
+// The lane's KPT states of k-set ks: points ks 32 KPT + 32 j + lane; one
+// division, then the lattice coordinates advance by 32.
 template <typename Real, int KPT>
 __device__ __forceinline__ void build_states(const KsumArgs& a, const GroupDesc& g, int ks, int lane, int pair,
                                              KState<Real> (&st)[KPT]) {
-  const int64_t nk = (int64_t)g.N * g.N;
+  const int nk = g.N * g.N;
+  const int k0 = ks * (32 * KPT) + lane;
+  int iy = k0 / g.N, ix = k0 - iy * g.N;
 #pragma unroll
   for (int j = 0; j < KPT; ++j) {
-    const int64_t kidx = (int64_t)ks * (32 * KPT) + j * 32 + lane;
+    const int kidx = k0 + j * 32;
     if (kidx < nk)
-      state_at<Real>(a, g, kidx, pair, st[j]);
+      state_at_xy<Real>(a, g, ix, iy, kidx, pair, st[j]);
     else
       kstate_invalid<Real>(st[j]);
+    ix += 32;
+    while (ix >= g.N) {
+      ix -= g.N;
+      ++iy;
+    }
   }
 }
 
@@ -474,8 +488,13 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
       far1[k] = !act1 || !valid[k] || far_band32(st[k].as.y, st[k].d0.y, w);
     }
     if constexpr (kG == kLayoutProduct) {
+      int di = w.b0 / g.n_hblk, hb = w.b0 - di * g.n_hblk;  // batch b = di n_hblk + hb
       for (int b = w.b0; b < w.b1; ++b) {
-        const float d2p = a.d2f[g.delta_off + b / g.n_hblk];
+        const float d2p = a.d2f[g.delta_off + di];
+        if (++hb == g.n_hblk) {
+          hb = 0;
+          ++di;
+        }
         float2 S = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int k = 0; k < KPT; ++k) {
