@@ -121,9 +121,9 @@ def cpu_baseline(cfg, seconds_target=15.0):
 
 
 # DRAM bytes (read + write) of one k-sum launch of the default workload, from
-# ncu (dram__bytes_read.sum 14.64 MB + dram__bytes_write.sum 229.88 MB, one
-# pass on the full-size launch); set back to None when the kernel changes.
-DRAM_TRAFFIC_PER_LAUNCH = 244.52e6
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum, one pass on the full-size
+# launch); None until captured for the current kernel.
+DRAM_TRAFFIC_PER_LAUNCH = None
 
 
 def run_extras(ffe, np, torch, stream, workloads):

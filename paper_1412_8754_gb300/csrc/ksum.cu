@@ -489,6 +489,7 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
     }
     if constexpr (kG == kLayoutProduct) {
       int di = w.b0 / g.n_hblk, hb = w.b0 - di * g.n_hblk;  // batch b = di n_hblk + hb
+      float mine = 0.0f;  // the warp total of batch b0 + lane
       for (int b = w.b0; b < w.b1; ++b) {
         const float d2p = a.d2f[g.delta_off + di];
         if (++hb == g.n_hblk) {
@@ -508,8 +509,9 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
         float t = S.x + S.y;
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
-        if (lane == b - w.b0) far_tot += (double)t;
+        mine = (lane == b - w.b0) ? t : mine;
       }
+      far_tot += (double)mine;  // one FP64 add per lane and k-set
     }
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
