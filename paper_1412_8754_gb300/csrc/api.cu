@@ -94,11 +94,24 @@ namespace ffe {
 // rounding): then every output has c |R -+ d| >= 40, its four
 // (1 + 2^-c|R-+d|) factors are 1 in FP32, and its clamp term is c a.
 // tgap = +inf for the FP64 path (no k-point is far).
-static void item_far_window(const ffe_plan* p, const GroupDesc& g, int b0, int b1, WorkItem& w) {
+static void item_far_window(const ffe_plan* p, const GroupDesc& g, int b0, int b1, double golden_d2, WorkItem& w) {
   w.far_hlo = 0.0f;
   w.far_hhi = 0.0f;
   w.far_tgap = INFINITY;
+  w.far_d2max = INFINITY;
   if (p->prec != FFE_FP32C) return;
+  if (g.layout == kLayoutList) {  // the largest Delta^2 of the item's outputs
+    double d2 = 0.0;
+    if (p->golden_steps > 0) {  // golden brackets stay inside each line's [lo, hi]
+      d2 = golden_d2;
+    } else {
+      for (int64_t o = (int64_t)b0 * 32; o < std::min<int64_t>(g.n_out, (int64_t)b1 * 32); ++o) {
+        const double d = p->delta[g.delta_off + o];
+        d2 = std::max(d2, d * d);
+      }
+    }
+    w.far_d2max = std::nextafter((float)d2, INFINITY);
+  }
   double hlo = INFINITY, hhi = -INFINITY, tmax = 0.0;
   for (int b = b0; b < b1; ++b) {
     int64_t e0, e1;
@@ -128,6 +141,9 @@ void build_items(ffe_plan* p) {
   p->items.clear();
   p->segs.clear();
   const int kset_pts = 32 * p->kpt;
+  double golden_d2 = 0.0;  // golden plans: the largest Delta^2 any bracket can reach
+  for (const GoldenState& gs : p->golden0)  // brackets stay in [lo, hi]; x0 may lie outside
+    golden_d2 = std::max({golden_d2, gs.lo * gs.lo, gs.hi * gs.hi, gs.x0 * gs.x0});
   // A small plan gets smaller items, so that the persistent grid's warps all
   // find work: at least about four items per resident warp.
   double work = 0.0;
@@ -160,7 +176,7 @@ void build_items(ffe_plan* p) {
       p->segs.push_back(sg);
       WorkItem proto;
       std::memset(&proto, 0, sizeof proto);
-      item_far_window(p, g, b0, b1, proto);
+      item_far_window(p, g, b0, b1, golden_d2, proto);
       poff += (int64_t)n_chunks * nb * 32;
       for (int c = 0; c < n_chunks; ++c) {
         WorkItem w;
@@ -174,7 +190,8 @@ void build_items(ffe_plan* p) {
         w.far_hlo = proto.far_hlo;
         w.far_hhi = proto.far_hhi;
         w.far_tgap = proto.far_tgap;
-        w.pad[0] = w.pad[1] = w.pad[2] = 0;
+        w.far_d2max = proto.far_d2max;
+        w.pad[0] = w.pad[1] = 0;
         p->items.push_back(w);
       }
     }

@@ -98,7 +98,9 @@ struct WorkItem {
   // >= far_tgap is "far" for all of them (see ksum.cu); far_tgap = +inf:
   // no k-point is.
   float far_hlo, far_hhi, far_tgap;
-  int32_t pad[3];
+  // LIST items: Delta^2 <= far_d2max for every output (bounds the far series)
+  float far_d2max;
+  int32_t pad[2];
 };
 
 // A segment = (group, batch range); its chunks partition the k-sets.
