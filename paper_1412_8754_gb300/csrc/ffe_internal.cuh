@@ -311,22 +311,18 @@ struct KState32 {
   float2 as, s2, d0;
 };
 
-// One float2 slot (two entries), one (h, c): adds c min(...) of each entry to
-// cp2 and returns the product of the four (1 + e) factors, in [1, 16] (the
-// caller takes one lg2 of the product over its slots).
-// Rc = R c and ac = a c per entry; nh2 = (-h, -h); c2 = (c, c); nc2 = -c2.
-__device__ __forceinline__ float w_term32(const KState32& st, float2 Rc, float2 ac, float2 nh2, float2 c2,
-                                          float2 nc2, float2& cp2) {
-  const float2 d = __fadd2_rn(st.d0, nh2);  // d = d0 - h
-  const float2 y1 = __ffma2_rn(d, nc2, Rc);  // c (R - d)
-  const float2 y2 = __ffma2_rn(d, c2, Rc);   // c (R + d)
+// One float2 slot (two entries), one output, given y1 = c (R - d) and
+// y2 = c (R + d) of each entry: adds c min(max(R - |d|, 0), a) of each entry
+// to cp2 (R - |d| = min(R - d, R + d)) and multiplies each half of P2 by its
+// entry's (1 + 2^-|y1|)(1 + 2^-|y2|), a factor in [1, 4] (the caller takes
+// one lg2 of the product over its slots).  ac = a c per entry.
+__device__ __forceinline__ void w_term32(float2 y1, float2 y2, float2 ac, float2& P2, float2& cp2) {
   const float2 e1 = make_float2(ex2a(-fabsf(y1.x)), ex2a(-fabsf(y1.y)));
   const float2 e2 = make_float2(ex2a(-fabsf(y2.x)), ex2a(-fabsf(y2.y)));
-  const float2 o1 = __fadd2_rn(e1, make_float2(1.0f, 1.0f));
-  const float2 p = __ffma2_rn(o1, e2, o1);
+  P2 = __ffma2_rn(P2, e1, P2);
+  P2 = __ffma2_rn(P2, e2, P2);
   const float2 cp = make_float2(fmaxf(min3f(y1.x, y2.x, ac.x), 0.0f), fmaxf(min3f(y1.y, y2.y, ac.y), 0.0f));
   cp2 = __fadd2_rn(cp2, cp);
-  return p.x * p.y;
 }
 __device__ __forceinline__ void ra_f64(double D, double s2, double as, double& R, double& a) {
   R = sqrt(D + s2);

@@ -212,16 +212,32 @@ __device__ __forceinline__ void ra32(const KState32& st, float d2, float2& R, fl
 }
 
 // W of one output summed over this lane's KPT slots: the clamp terms plus
-// one lg2 of the product of all (1 + e) factors (at most 16^KPT <= 2^32).
+// one lg2 of the product of all (1 + e) factors (each half of P2 at most
+// 4^KPT, the product at most 16^KPT <= 2^32).  Rc = R c, Ac = a c per slot;
+// y1 = c (R - d), y2 = c (R + d) with d = d0 - h.
 template <int KPT>
 __device__ __forceinline__ float w_out32(const KState32 (&st)[KPT], const float2 (&Rc)[KPT],
                                          const float2 (&Ac)[KPT], float h, float c) {
   const float2 nh2 = make_float2(-h, -h), c2 = make_float2(c, c), nc2 = make_float2(-c, -c);
-  float2 cp2 = make_float2(0.0f, 0.0f);
-  float P = 1.0f;
+  float2 cp2 = make_float2(0.0f, 0.0f), P2 = make_float2(1.0f, 1.0f);
 #pragma unroll
-  for (int k = 0; k < KPT; ++k) P *= w_term32(st[k], Rc[k], Ac[k], nh2, c2, nc2, cp2);
-  return (cp2.x + cp2.y) + lg2a(P);
+  for (int k = 0; k < KPT; ++k) {
+    const float2 d = __fadd2_rn(st[k].d0, nh2);
+    w_term32(__ffma2_rn(d, nc2, Rc[k]), __ffma2_rn(d, c2, Rc[k]), Ac[k], P2, cp2);
+  }
+  return (cp2.x + cp2.y) + lg2a(P2.x * P2.y);
+}
+
+// The same for one c shared by the batch, from A1 = c (R - d0) and
+// A2 = c (R + d0) per slot: y1 = A1 + c h, y2 = A2 - c h.
+template <int KPT>
+__device__ __forceinline__ float w_out32_ut(const float2 (&A1)[KPT], const float2 (&A2)[KPT],
+                                            const float2 (&Ac)[KPT], float ch) {
+  const float2 ch2 = make_float2(ch, ch), nch2 = make_float2(-ch, -ch);
+  float2 cp2 = make_float2(0.0f, 0.0f), P2 = make_float2(1.0f, 1.0f);
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) w_term32(__fadd2_rn(A1[k], ch2), __fadd2_rn(A2[k], nch2), Ac[k], P2, cp2);
+  return (cp2.x + cp2.y) + lg2a(P2.x * P2.y);
 }
 
 // Lane l: the sum of row l of the warp's transpose buffer (0 for l >= nvalid).
@@ -283,16 +299,19 @@ __device__ __forceinline__ float eval_batch32(const KState32 (&st)[KPT], const B
                                               float d2_product, int lane, float* red) {
   if (VARIANT == kLayoutProductUT) {
     const float c = bp[0].c;
-    float2 Rc[KPT], Ac[KPT];
+    const float2 c2 = make_float2(c, c), nc2 = make_float2(-c, -c);
+    float2 A1[KPT], A2[KPT], Ac[KPT];
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
       float2 R, A;
       ra32(st[k], d2_product, R, A);
-      Rc[k] = __fmul2_rn(R, make_float2(c, c));
-      Ac[k] = __fmul2_rn(A, make_float2(c, c));
+      const float2 Rc = __fmul2_rn(R, c2);
+      A1[k] = __ffma2_rn(st[k].d0, nc2, Rc);
+      A2[k] = __ffma2_rn(st[k].d0, c2, Rc);
+      Ac[k] = __fmul2_rn(A, c2);
     }
 #pragma unroll 4
-    for (int j = 0; j < nvalid; ++j) red[j * 36 + lane] = w_out32<KPT>(st, Rc, Ac, bp[j].h, c);
+    for (int j = 0; j < nvalid; ++j) red[j * 36 + lane] = w_out32_ut<KPT>(A1, A2, Ac, c * bp[j].h);
   } else if (VARIANT == kLayoutProduct) {
     float2 R[KPT], A[KPT];
 #pragma unroll
