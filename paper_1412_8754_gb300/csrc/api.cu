@@ -256,6 +256,21 @@ double plan_k_evals(const ffe_plan* p) {
   return p->golden_steps > 0 ? s * (3.0 + p->golden_steps) : s;
 }
 
+// Each group's first row in the three-band band tables and in the k-state
+// table (set again whenever the groups are refilled); the row totals.
+static void table_offsets(const ffe_context* ctx, ffe_plan* p, int64_t& e3_rows, int64_t& kst_rows) {
+  e3_rows = 0;
+  kst_rows = 0;
+  const int64_t npairs = (ctx->mp.nbands + 1) / 2;
+  for (GroupDesc& g : p->groups) {
+    const int64_t nk = (int64_t)g.N * g.N;
+    g.e3_off = e3_rows;
+    if (ctx->mp.nbands == 3) e3_rows += 2 * nk;
+    g.kst_off = kst_rows;
+    kst_rows += npairs * nk;
+  }
+}
+
 // The buffers of a plan (sizes from the host tables already in *p).
 static ffe_status plan_alloc_requests(ffe_context* ctx, ffe_plan* p, Arena& arena) {
   ffe_status st;
@@ -310,14 +325,19 @@ static ffe_status plan_alloc_requests(ffe_context* ctx, ffe_plan* p, Arena& aren
   ALLOC(d_labels, std::max<size_t>(1, p->n_pts));
   ALLOC(d_bestq, std::max<size_t>(1, p->n_pts));
   ALLOC(d_golden, p->golden0.size());
-  // three-band model: band tables, two momenta x N^2 rows per group
-  int64_t e3_rows = 0;
-  for (GroupDesc& g : p->groups) {
-    g.e3_off = e3_rows;
-    if (ctx->mp.nbands == 3) e3_rows += 2 * (int64_t)g.N * g.N;
-  }
+  // three-band model: band tables, two momenta x N^2 rows per group; FP32
+  // plans: the k-state table, built once per execution and read by each of
+  // its k-sum launches (a golden search has 3 + steps of them)
+  int64_t e3_rows, kst_rows;
+  table_offsets(ctx, p, e3_rows, kst_rows);
+  p->e3_rows = e3_rows;
   ALLOC(d_e3d, e3_rows);
   ALLOC(d_e3f, e3_rows);
+  if (p->prec != FFE_FP32C || kst_rows * (int64_t)(sizeof(float4) + sizeof(float)) > kKstateTableMaxBytes)
+    kst_rows = 0;
+  p->kst_rows = kst_rows;
+  ALLOC(d_kst4, kst_rows);
+  ALLOC(d_kste, kst_rows);
 #undef ALLOC
   return FFE_OK;
 }
@@ -359,6 +379,10 @@ ffe_status plan_alloc(ffe_context* ctx, ffe_plan* p) {
 // The per-call inputs: Delta values, (h, T) entries, distinct h lists and Q.
 ffe_status plan_upload_params(ffe_context* ctx, ffe_plan* p, cudaStream_t s) {
   ffe_status st;
+  int64_t e3_rows, kst_rows;
+  table_offsets(ctx, p, e3_rows, kst_rows);  // refilled groups: offsets again
+  if (e3_rows > p->e3_rows || (p->kst_rows > 0 && kst_rows > p->kst_rows))
+    return set_err(ctx, "plan groups outgrew their table buffers"), FFE_EINTERNAL;
   if ((st = upload(ctx, p->d_delta, p->delta, s)) != FFE_OK) return st;
   if ((st = upload(ctx, p->d_ht, p->ht, s)) != FFE_OK) return st;
   if ((st = upload(ctx, p->d_hlist, p->hlist, s)) != FFE_OK) return st;
@@ -383,6 +407,8 @@ static KsumArgs make_ksum_args(ffe_plan* p) {
   a.near_evals = p->d_near;
   a.e3f = p->d_e3f;
   a.e3d = p->d_e3d;
+  a.kst4 = p->kst_rows > 0 ? p->d_kst4 : nullptr;
+  a.kste = p->kst_rows > 0 ? p->d_kste : nullptr;
   a.seg_count = p->d_segcnt;
   a.partials = p->d_partials;
   a.tabf = p->d_tabf;
@@ -461,6 +487,10 @@ ffe_status plan_enqueue(ffe_context* ctx, ffe_plan* p, cudaStream_t s, cudaEvent
          "normal");
   ++launches;
   KsumArgs ka = make_ksum_args(p);
+  if (ka.kst4) {
+    FFE_CU(kstate_table_launch(ka, (int)p->groups.size(), p->max_n, s), "k-state table");
+    ++launches;
+  }
   const int n_lines = (int)p->lines.size();
   if (p->golden_steps > 0) {
     // lockstep golden-section: one k-sum launch per evaluation of every line

@@ -62,6 +62,7 @@ struct GroupDesc {
   int32_t pad;
   int64_t e3_off;     // three-band model: first entry of the group's band tables
                       // (k + Q/2 at e3_off + k, -k + Q/2 at e3_off + N^2 + k)
+  int64_t kst_off;    // FP32 k-state table: entry of (pair, k) at kst_off + pair N^2 + k
 };
 
 // Bands are evaluated two at a time, as the two halves of packed operations:

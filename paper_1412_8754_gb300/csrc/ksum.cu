@@ -157,6 +157,29 @@ __device__ __forceinline__ int stage_batch(const KsumArgs& a, const GroupDesc& g
 template <int KPT>
 __device__ __forceinline__ void build_states32(const KsumArgs& a, const GroupDesc& g, int ks, int lane, int pair,
                                                KState32 (&st)[KPT]) {
+  if (a.kst4) {  // from the k-state table (s^2 = |s|^2 exactly, as built)
+    const int nk = g.N * g.N;
+    const int k0 = ks * (32 * KPT) + lane;
+    const int64_t base = g.kst_off + (int64_t)pair * nk;
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+      const int kidx = k0 + j * 32;
+      if (kidx < nk) {
+        const float4 v = a.kst4[base + kidx];
+        const float e = a.kste[base + kidx];
+        st[j].eta2 = make_float2(e, e);
+        st[j].as = make_float2(v.x, v.y);
+        st[j].s2 = make_float2(fmaxf(v.x * v.x, 1e-30f), fmaxf(v.y * v.y, 1e-30f));
+        st[j].d0 = make_float2(v.z, v.w);
+      } else {
+        st[j].eta2 = make_float2(0.0f, 0.0f);
+        st[j].as = make_float2(1e15f, 1e15f);
+        st[j].s2 = make_float2(1e30f, 1e30f);
+        st[j].d0 = make_float2(0.0f, 0.0f);
+      }
+    }
+    return;
+  }
   KState<float> s[KPT];
   build_states<float, KPT>(a, g, ks, lane, pair, s);
 #pragma unroll
@@ -179,9 +202,15 @@ struct Band32 {
 };
 
 __device__ __forceinline__ Band32 band32_at(const KsumArgs& a, const GroupDesc& g, int32_t e) {
+  const int b = (e >> kSlotBit) & 1;
+  if (a.kst4) {  // from the k-state table
+    const int64_t o = g.kst_off + (int64_t)((e >> kPairBit) & 1) * g.N * g.N + (e & kKidxMask);
+    const float4 v = a.kst4[o];
+    const float as = b ? v.y : v.x;
+    return Band32{a.kste[o], as, fmaxf(as * as, 1e-30f), b ? v.w : v.z};
+  }
   KState<float> s;
   state_at<float>(a, g, e & kKidxMask, (e >> kPairBit) & 1, s);
-  const int b = (e >> kSlotBit) & 1;
   return Band32{s.eta2, s.as[b], s.s2[b], s.d0[b]};
 }
 
@@ -695,6 +724,30 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
       if (lane == 0) a.seg_count[w.seg] = 0;  // ready for the next launch
     }
   }
+}
+
+// The FP32 state of every (group, band pair, lattice point) -- the values
+// the k-sum would otherwise rebuild in each of its segments -- as |s| and d0
+// of both slots (float4) and eta^2.  Grid: (k blocks, group, pair).
+__global__ void __launch_bounds__(256) kstate_table_kernel(const KsumArgs a) {
+  const GroupDesc g = a.groups[blockIdx.y];
+  const int pair = blockIdx.z;
+  const int nk = g.N * g.N;
+  const int64_t base = g.kst_off + (int64_t)pair * nk;
+  for (int k = blockIdx.x * 256 + threadIdx.x; k < nk; k += gridDim.x * 256) {
+    KState<float> st;
+    state_at<float>(a, g, k, pair, st);
+    a.kst4[base + k] = make_float4(st.as[0], st.as[1], st.d0[0], st.d0[1]);
+    a.kste[base + k] = st.eta2;
+  }
+}
+
+cudaError_t kstate_table_launch(const KsumArgs& a, int n_groups, int max_n, cudaStream_t s) {
+  if (n_groups < 1 || n_groups > 65535) return cudaErrorInvalidValue;
+  const int64_t nk = (int64_t)max_n * max_n;
+  const int bx = (int)std::min<int64_t>((nk + 255) / 256, 1024);
+  kstate_table_kernel<<<dim3(bx, n_groups, (a.m.nbands + 1) / 2), 256, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 size_t ksum_smem_bytes(int prec, int layout, int kpt, int block_threads) {

@@ -38,9 +38,14 @@ struct KsumArgs {
   unsigned long long* near_evals;  // FP32 path: k-evaluations with the full term (NULL: not counted)
   const float4* e3f;               // three-band model: band tables (GroupDesc::e3_off), FP32
   const E3D* e3d;                  // and FP64
+  // FP32 k-state table (NULL: states are built from the trig tables): per
+  // (group, band pair, lattice point) |s| and d0 of both slots, and eta^2
+  float4* kst4;
+  float* kste;
 };
 
 size_t ksum_smem_bytes(int prec, int layout, int kpt, int block_threads);
+cudaError_t kstate_table_launch(const KsumArgs& a, int n_groups, int max_n, cudaStream_t s);
 cudaError_t ksum_launch(int prec, int layout, int kpt, const KsumArgs& a, int grid, int block,
                         cudaStream_t s);
 cudaError_t ksum_occupancy(int prec, int layout, int kpt, int block, int* blocks_per_sm);

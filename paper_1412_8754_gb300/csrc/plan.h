@@ -13,6 +13,10 @@ namespace ffe {
 constexpr int kRing = 256;                          // timing event pairs per plan
 constexpr double kEbRel = 7.62939453125e-06;        // 2^-17: FP32 bound, relative to |sum_k v_k|
 constexpr double kEbAbs = 1.6527e-07;               // 2^-22 ln 2: log2 error per k-point, times T
+// The FP32 k-state table of a plan (20 bytes per group, band pair and lattice
+// point) is kept when it fits in this many bytes; larger plans build the
+// states inside the k-sum instead.
+constexpr int64_t kKstateTableMaxBytes = int64_t(32) << 30;
 
 enum { kPlanScanGrid = 1, kPlanMinGrid = 2, kPlanOmega = 3, kPlanScanGolden = 4, kPlanMinGolden = 5 };
 
@@ -93,6 +97,10 @@ struct ffe_plan {
   ffe::TabRowDF* d_tabdf = nullptr;  // double-float copy (normal-state sums of FP32 plans)
   ffe::E3D* d_e3d = nullptr;          // three-band model: band tables, FP64
   float4* d_e3f = nullptr;            // and FP32
+  float4* d_kst4 = nullptr;           // FP32 k-state table (|s|, d0 of both slots) and eta^2;
+  float* d_kste = nullptr;            // none when kst_rows == 0
+  int64_t kst_rows = 0;
+  int64_t e3_rows = 0;                // rows of the three-band band tables
   double* d_c0d = nullptr;
   double* d_M = nullptr;
   double* d_Mpart = nullptr;

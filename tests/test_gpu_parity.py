@@ -113,6 +113,13 @@ def oracle_scan(m, N, qx, qy, h, T, grid):
     return om, idx, star, np.array(labels), np.array(best)
 
 
+def assert_same_scan(a, b):
+    """Two executions of one scan agree bit for bit (the k-sum's order of addition is fixed)."""
+    for name in a[0].dtype.names:
+        assert np.array_equal(a[0][name], b[0][name], equal_nan=True), name
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_phase_scan_small(prec):
     """Grid phase scan: 6 q x (4 h x 2 T) x 41 Delta at N=32, U=4 (BCS and FF minima)."""
@@ -126,6 +133,8 @@ def test_phase_scan_small(prec):
     om, idx, star, labels, best = oracle_scan(m, N, qx, qy, h, T, grid)
     with ffe.Context(prec=prec, U=U) as ctx:
         res, glab, gbest = ctx.phase_scan(N, qx, qy, h, T, n=41, lo=0.0, hi=0.2)
+        again = ctx.phase_scan(N, qx, qy, h, T, n=41, lo=0.0, hi=0.2)  # the cached plan, refilled
+    assert_same_scan((res, glab, gbest), again)
     assert np.array_equal(res["idx_star"], idx)
     assert per_site(res["omega_star"], star, N).max() <= TOL[prec]
     assert per_site(res["omega_lo"], om[..., 0], N).max() <= TOL[prec]

@@ -72,6 +72,10 @@ def test_phase_scan_labels_vs_oracle(prec):
     grid = np.linspace(0.0, 0.05, n)
     with ctx3(prec) as c:
         res, lab, best = c.phase_scan(N, qx, np.zeros(3), h, T, n=n, lo=0.0, hi=0.05)
+        res2, lab2, best2 = c.phase_scan(N, qx, np.zeros(3), h, T, n=n, lo=0.0, hi=0.05)  # cached plan
+    for name in res.dtype.names:  # one scan, executed twice: the same bits
+        assert np.array_equal(res[name], res2[name], equal_nan=True), name
+    assert np.array_equal(lab, lab2) and np.array_equal(best, best2)
     star = np.zeros((3, len(h) * len(T)))
     zero = np.zeros_like(star)
     for q in range(3):
