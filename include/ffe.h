@@ -228,6 +228,11 @@ typedef struct {
                               shared by the outputs).  A k-evaluation covers
                               every band.  0 for FP64, -1 before the first
                               execution                                       */
+  double k_evals_single;   /* FP32: those of k_evals_near whose band has
+                              c (R + |d|) >= 27 for every output of its work
+                              item and that were evaluated with one exponential
+                              (the other factor is exactly 1 in FP32); same
+                              conventions                                     */
 } ffe_plan_info;
 
 /* Static facts about a plan, the FP64 re-evaluation counts of the last

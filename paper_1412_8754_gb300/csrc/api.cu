@@ -99,7 +99,24 @@ static void item_far_window(const ffe_plan* p, const GroupDesc& g, int b0, int b
   w.far_hhi = 0.0f;
   w.far_tgap = INFINITY;
   w.far_d2max = INFINITY;
+  w.sgl_d2min = 0.0f;
+  w.sgl_r = INFINITY;
   if (p->prec != FFE_FP32C) return;
+  if (p->golden_steps == 0) {  // the smallest Delta^2 of the item's outputs (golden: 0)
+    double d2 = INFINITY;
+    for (int b = b0; b < b1; ++b) {
+      if (g.layout == kLayoutProduct) {
+        const double d = p->delta[g.delta_off + b / g.n_hblk];
+        d2 = std::min(d2, d * d);
+      } else {
+        for (int64_t o = (int64_t)b * 32; o < std::min<int64_t>(g.n_out, (int64_t)b * 32 + 32); ++o) {
+          const double d = p->delta[g.delta_off + o];
+          d2 = std::min(d2, d * d);
+        }
+      }
+    }
+    if (d2 < INFINITY) w.sgl_d2min = std::nextafter((float)d2, 0.0f);
+  }
   if (g.layout == kLayoutList) {  // the largest Delta^2 of the item's outputs
     double d2 = 0.0;
     if (p->golden_steps > 0) {  // golden brackets stay inside each line's [lo, hi]
@@ -135,6 +152,7 @@ static void item_far_window(const ffe_plan* p, const GroupDesc& g, int b0, int b
   w.far_hlo = std::nextafter((float)hlo, -INFINITY);
   w.far_hhi = std::nextafter((float)hhi, INFINITY);
   w.far_tgap = std::nextafter((float)(40.0 * 0.69314718055994530942 * tmax + 1e-5), INFINITY);
+  w.sgl_r = std::nextafter((float)(27.0 * 0.69314718055994530942 * tmax + 1e-5), INFINITY);
 }
 
 void build_items(ffe_plan* p) {
@@ -191,7 +209,8 @@ void build_items(ffe_plan* p) {
         w.far_hhi = proto.far_hhi;
         w.far_tgap = proto.far_tgap;
         w.far_d2max = proto.far_d2max;
-        w.pad[0] = w.pad[1] = 0;
+        w.sgl_d2min = proto.sgl_d2min;
+        w.sgl_r = proto.sgl_r;
         p->items.push_back(w);
       }
     }
@@ -305,7 +324,7 @@ static ffe_status plan_alloc_requests(ffe_context* ctx, ffe_plan* p, Arena& aren
   ALLOC(d_partials, p->n_partials);
   ALLOC(d_segcnt, p->segs.size());
   ALLOC(d_counters, 8);
-  ALLOC(d_near, 1);
+  ALLOC(d_near, 2);
   ALLOC(d_V, p->n_out);
   ALLOC(d_omega, p->n_out);
   ALLOC(d_eb, p->n_out);
@@ -467,7 +486,7 @@ ffe_status plan_enqueue(ffe_context* ctx, ffe_plan* p, cudaStream_t s, cudaEvent
                         unsigned ev_flags) {
   int launches = 0;
   FFE_CU(cudaMemsetAsync(p->d_counters, 0, 8 * sizeof(int32_t), s), "memset counters");
-  FFE_CU(cudaMemsetAsync(p->d_near, 0, sizeof(unsigned long long), s), "memset counters");
+  FFE_CU(cudaMemsetAsync(p->d_near, 0, 2 * sizeof(unsigned long long), s), "memset counters");
   FFE_CU(cudaMemsetAsync(p->d_rescored, 0, sizeof(int32_t) * std::max<int64_t>(1, p->n_out), s), "memset");
   FFE_CU(prep_params_launch(p->d_delta, (int64_t)p->delta.size(), p->d_d2f, p->d_ht, (int64_t)p->ht.size(),
                             p->d_htf, p->d_htd, s),
@@ -1004,10 +1023,12 @@ ffe_status ffe_plan_stats(const ffe_plan* p, ffe_plan_info* info) {
   info->work_items = (int32_t)p->items.size();
   info->device_bytes = (double)p->bytes;
   info->k_evals_near = -1.0;
+  info->k_evals_single = -1.0;
   if (p->d_near && p->exec_count > 0) {
-    unsigned long long n = 0;
-    if (cudaMemcpy(&n, p->d_near, sizeof n, cudaMemcpyDeviceToHost) != cudaSuccess) return FFE_ECUDA;
-    info->k_evals_near = (double)n;
+    unsigned long long n[2] = {0, 0};
+    if (cudaMemcpy(n, p->d_near, sizeof n, cudaMemcpyDeviceToHost) != cudaSuccess) return FFE_ECUDA;
+    info->k_evals_near = (double)n[0];
+    info->k_evals_single = (double)n[1];
   }
   return FFE_OK;
 }

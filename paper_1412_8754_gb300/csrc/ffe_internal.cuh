@@ -101,7 +101,11 @@ struct WorkItem {
   float far_hlo, far_hhi, far_tgap;
   // LIST items: Delta^2 <= far_d2max for every output (bounds the far series)
   float far_d2max;
-  int32_t pad[2];
+  // Delta^2 >= sgl_d2min for every output; sgl_r = 27 ln2 Tmax (+ rounding
+  // margin): a near band with R + |d| >= sgl_r for every output has
+  // c (R + |d|) >= 27, so its factor (1 + 2^-c(R+|d|)) is exactly 1 in FP32
+  // (see ksum.cu); sgl_r = +inf: no band is tested
+  float sgl_d2min, sgl_r;
 };
 
 // A segment = (group, batch range); its chunks partition the k-sets.
@@ -317,11 +321,20 @@ struct KState32 {
 // to cp2 (R - |d| = min(R - d, R + d)) and multiplies each half of P2 by its
 // entry's (1 + 2^-|y1|)(1 + 2^-|y2|), a factor in [1, 4] (the caller takes
 // one lg2 of the product over its slots).  ac = a c per entry.
+// SINGLE: both entries have c (R + |d|) >= 27, whose factor would leave the
+// product unchanged (P + P e with P e below half an ulp of P), so only the
+// factor of min(|y1|, |y2|) = c |R - |d|| is formed -- the same bits.
+template <bool SINGLE>
 __device__ __forceinline__ void w_term32(float2 y1, float2 y2, float2 ac, float2& P2, float2& cp2) {
-  const float2 e1 = make_float2(ex2a(-fabsf(y1.x)), ex2a(-fabsf(y1.y)));
-  const float2 e2 = make_float2(ex2a(-fabsf(y2.x)), ex2a(-fabsf(y2.y)));
-  P2 = __ffma2_rn(P2, e1, P2);
-  P2 = __ffma2_rn(P2, e2, P2);
+  if constexpr (SINGLE) {
+    const float2 e = make_float2(ex2a(fmaxf(-fabsf(y1.x), -fabsf(y2.x))), ex2a(fmaxf(-fabsf(y1.y), -fabsf(y2.y))));
+    P2 = __ffma2_rn(P2, e, P2);
+  } else {
+    const float2 e1 = make_float2(ex2a(-fabsf(y1.x)), ex2a(-fabsf(y1.y)));
+    const float2 e2 = make_float2(ex2a(-fabsf(y2.x)), ex2a(-fabsf(y2.y)));
+    P2 = __ffma2_rn(P2, e1, P2);
+    P2 = __ffma2_rn(P2, e2, P2);
+  }
   const float2 cp = make_float2(fmaxf(min3f(y1.x, y2.x, ac.x), 0.0f), fmaxf(min3f(y1.y, y2.y, ac.y), 0.0f));
   cp2 = __fadd2_rn(cp2, cp);
 }

@@ -192,8 +192,9 @@ __device__ __forceinline__ void build_states32(const KsumArgs& a, const GroupDes
 }
 
 // A buffered (k-point, band) entry: lattice index | band pair << kPairBit |
-// band slot << kSlotBit (lattice index < 8192^2 = 2^26).
-constexpr int kPairBit = 27, kSlotBit = 28;
+// band slot << kSlotBit | single << kSingleBit (lattice index < 8192^2 = 2^26;
+// single: c (R + |d|) >= 27 for every output of the item).
+constexpr int kPairBit = 27, kSlotBit = 28, kSingleBit = 29;
 constexpr int32_t kKidxMask = (1 << 26) - 1;
 
 // One band of one entry: eta^2, |s|, s^2, d0; an inert band past the end.
@@ -244,7 +245,7 @@ __device__ __forceinline__ void ra32(const KState32& st, float d2, float2& R, fl
 // one lg2 of the product of all (1 + e) factors (each half of P2 at most
 // 4^KPT, the product at most 16^KPT <= 2^32).  Rc = R c, Ac = a c per slot;
 // y1 = c (R - d), y2 = c (R + d) with d = d0 - h.
-template <int KPT>
+template <int KPT, bool SINGLE>
 __device__ __forceinline__ float w_out32(const KState32 (&st)[KPT], const float2 (&Rc)[KPT],
                                          const float2 (&Ac)[KPT], float h, float c) {
   const float2 nh2 = make_float2(-h, -h), c2 = make_float2(c, c), nc2 = make_float2(-c, -c);
@@ -252,20 +253,20 @@ __device__ __forceinline__ float w_out32(const KState32 (&st)[KPT], const float2
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
     const float2 d = __fadd2_rn(st[k].d0, nh2);
-    w_term32(__ffma2_rn(d, nc2, Rc[k]), __ffma2_rn(d, c2, Rc[k]), Ac[k], P2, cp2);
+    w_term32<SINGLE>(__ffma2_rn(d, nc2, Rc[k]), __ffma2_rn(d, c2, Rc[k]), Ac[k], P2, cp2);
   }
   return (cp2.x + cp2.y) + lg2a(P2.x * P2.y);
 }
 
 // The same for one c shared by the batch, from A1 = c (R - d0) and
 // A2 = c (R + d0) per slot: y1 = A1 + c h, y2 = A2 - c h.
-template <int KPT>
+template <int KPT, bool SINGLE>
 __device__ __forceinline__ float w_out32_ut(const float2 (&A1)[KPT], const float2 (&A2)[KPT],
                                             const float2 (&Ac)[KPT], float ch) {
   const float2 ch2 = make_float2(ch, ch), nch2 = make_float2(-ch, -ch);
   float2 cp2 = make_float2(0.0f, 0.0f), P2 = make_float2(1.0f, 1.0f);
 #pragma unroll
-  for (int k = 0; k < KPT; ++k) w_term32(__fadd2_rn(A1[k], ch2), __fadd2_rn(A2[k], nch2), Ac[k], P2, cp2);
+  for (int k = 0; k < KPT; ++k) w_term32<SINGLE>(__fadd2_rn(A1[k], ch2), __fadd2_rn(A2[k], nch2), Ac[k], P2, cp2);
   return (cp2.x + cp2.y) + lg2a(P2.x * P2.y);
 }
 
@@ -323,7 +324,7 @@ __device__ __forceinline__ float eval_far32_series(const KState32 (&st)[KPT], co
 // the warp's transpose buffer `red` (row stride 36 floats); lane l then adds
 // row l.  The output loop stays rolled (small code); returns in lane l the
 // warp total of output l (0 for l >= nvalid).
-template <int KPT, int VARIANT>
+template <int KPT, int VARIANT, bool SINGLE>
 __device__ __forceinline__ float eval_batch32(const KState32 (&st)[KPT], const BParF* bp, int nvalid,
                                               float d2_product, int lane, float* red) {
   if (VARIANT == kLayoutProductUT) {
@@ -340,7 +341,7 @@ __device__ __forceinline__ float eval_batch32(const KState32 (&st)[KPT], const B
       Ac[k] = __fmul2_rn(A, c2);
     }
 #pragma unroll 4
-    for (int j = 0; j < nvalid; ++j) red[j * 36 + lane] = w_out32_ut<KPT>(A1, A2, Ac, c * bp[j].h);
+    for (int j = 0; j < nvalid; ++j) red[j * 36 + lane] = w_out32_ut<KPT, SINGLE>(A1, A2, Ac, c * bp[j].h);
   } else if (VARIANT == kLayoutProduct) {
     float2 R[KPT], A[KPT];
 #pragma unroll
@@ -355,7 +356,7 @@ __device__ __forceinline__ float eval_batch32(const KState32 (&st)[KPT], const B
         Rc[k] = __fmul2_rn(R[k], c2);
         Ac[k] = __fmul2_rn(A[k], c2);
       }
-      red[j * 36 + lane] = w_out32<KPT>(st, Rc, Ac, p.h, p.c);
+      red[j * 36 + lane] = w_out32<KPT, SINGLE>(st, Rc, Ac, p.h, p.c);
     }
   } else {
 #pragma unroll 2
@@ -370,7 +371,7 @@ __device__ __forceinline__ float eval_batch32(const KState32 (&st)[KPT], const B
         Rc[k] = __fmul2_rn(R, c2);
         Ac[k] = __fmul2_rn(A, c2);
       }
-      red[j * 36 + lane] = w_out32<KPT>(st, Rc, Ac, p.h, p.c);
+      red[j * 36 + lane] = w_out32<KPT, SINGLE>(st, Rc, Ac, p.h, p.c);
     }
   }
   return transposed_total(red, nvalid, lane);
@@ -498,17 +499,21 @@ __device__ __forceinline__ void flush32(const KsumArgs& a, const WorkItem& w, co
                                         const int32_t* buf, int n, double* acc, BParF* bp, float* red) {
   constexpr int kG = (LAYOUT == kLayoutList) ? kLayoutList : kLayoutProduct;
   KState32 st[KPT];
+  int sgl = 1;  // every entry of this lane single (padding counts as single)
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
     const int i0 = 2 * k * 32 + lane, i1 = i0 + 32;
     Band32 x = i0 < n ? band32_at(a, g, buf[i0]) : band32_inert();
     Band32 y = i1 < n ? band32_at(a, g, buf[i1]) : band32_inert();
+    if (i0 < n) sgl &= (buf[i0] >> kSingleBit) & 1;
+    if (i1 < n) sgl &= (buf[i1] >> kSingleBit) & 1;
     if constexpr (SERIES) {  // (eta^2, 1/(2|s|), 1/s^2); padding entries have eta^2 = 0
       x = Band32{x.eta2, 0.5f / x.as, 1.0f / x.s2, 0.0f};
       y = Band32{y.eta2, 0.5f / y.as, 1.0f / y.s2, 0.0f};
     }
     st[k] = pack32(x, y);
   }
+  const bool single = __all_sync(kFull, sgl);  // warp-uniform: one ex2 per near band
   int64_t outs = 0;
   for (int b = w.b0; b < w.b1; ++b) {
     int di;
@@ -521,11 +526,15 @@ __device__ __forceinline__ void flush32(const KsumArgs& a, const WorkItem& w, co
       tot = eval_far32<KPT>(st, bp, nvalid, lane, red);
     } else {
       const float d2p = (kG == kLayoutProduct) ? a.d2f[g.delta_off + di] : 0.0f;
-      tot = eval_batch32<KPT, LAYOUT>(st, bp, nvalid, d2p, lane, red);
+      tot = single ? eval_batch32<KPT, LAYOUT, true>(st, bp, nvalid, d2p, lane, red)
+                   : eval_batch32<KPT, LAYOUT, false>(st, bp, nvalid, d2p, lane, red);
     }
     acc[(b - w.b0) * 32 + lane] += (double)tot;
   }
-  if (!FAR && a.near_evals && lane == 0) atomicAdd(a.near_evals, (unsigned long long)(n * outs));
+  if (!FAR && a.near_evals && lane == 0) {
+    atomicAdd(a.near_evals, (unsigned long long)(n * outs));
+    if (single) atomicAdd(a.near_evals + 1, (unsigned long long)(n * outs));
+  }
 }
 
 // Drops the first `done` entries of a warp's buffer of n entries.
@@ -603,14 +612,19 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
       for (int sl = 0; sl < 2; ++sl) {
         const bool fr = sl == 0 ? far0[k] : far1[k];
         const bool act = sl == 0 ? act0 : act1;
-        const int32_t e = kidx[k] | (pair << kPairBit) | (sl << kSlotBit);
+        const float eta2 = sl == 0 ? st[k].eta2.x : st[k].eta2.y;
+        const float s2 = sl == 0 ? st[k].s2.x : st[k].s2.y;
+        const float d0 = sl == 0 ? st[k].d0.x : st[k].d0.y;
+        // single: R + |d| >= sgl_r for every output, from R^2 >= s^2 + Delta_min^2 eta^2
+        // and |d| >= the distance of d0 from [hlo, hhi]
+        const float t = w.sgl_r - fmaxf(0.0f, fmaxf(w.far_hlo - d0, d0 - w.far_hhi));
+        const bool sg = t <= 0.0f || fmaf(w.sgl_d2min, eta2, s2) >= t * t;
+        const int32_t e = kidx[k] | (pair << kPairBit) | (sl << kSlotBit) | ((int32_t)sg << kSingleBit);
         const bool nr = !fr;  // near implies active and valid
         const unsigned m = __ballot_sync(kFull, nr);
         if (nr) nbuf[n_near + __popc(m & lt)] = e;
         n_near += __popc(m);
         if constexpr (kG == kLayoutList) {
-          const float eta2 = sl == 0 ? st[k].eta2.x : st[k].eta2.y;
-          const float s2 = sl == 0 ? st[k].s2.x : st[k].s2.y;
           const bool fe = fr && act && valid[k];
           const bool ser = fe && eta2 * w.far_d2max <= 0.04f * s2;  // x <= 0.04 for every output
           const bool cf = fe && !ser;

@@ -147,7 +147,7 @@ extern "C" ffe_status ffe_omega_noalloc(const ffe_model* m, int32_t N, double qx
     poff += (int64_t)n_chunks * (b1 - b0) * 32;
     for (int c = 0; c < n_chunks; ++c)
       g_na_items[n_items++] = WorkItem{0, sg, c, c * ck, std::min(n_ksets, (c + 1) * ck), b0, b1, 0.0f, 0.0f,
-                                       INFINITY, INFINITY, {0, 0}};
+                                       INFINITY, INFINITY, 0.0f, INFINITY};
   }
   const int64_t mchunk = 32768;
   const int m_chunks = (int)((nk + mchunk - 1) / mchunk);

@@ -145,8 +145,9 @@ def test_phase_scan_small(prec):
 @pytest.mark.parametrize("T, mixed", [(0.002, True), (0.6, False)])
 def test_far_k_points_take_the_short_form(T, mixed):
     """FP32: a band far from the Fermi surface for every output of a work item (its log
-    factors are 1 in FP32) is summed as W = c a; the others take the full term. At low T
-    most bands are far, at T = 0.6 none is; both match the oracle."""
+    factors are 1 in FP32) is summed as W = c a; the others take the full term, with one
+    exponential where c (R + |d|) >= 27 for every output. At low T most bands are far, at
+    T = 0.6 none is (and none has one exponential); both match the oracle."""
     N, U = 48, 4.0
     qx = np.array([0.0, 0.3])
     qy = np.zeros_like(qx)
@@ -162,10 +163,13 @@ def test_far_k_points_take_the_short_form(T, mixed):
         st = plan.stats()
         plan.destroy()
     frac = st["k_evals_near"] / (2 * st["k_evals"])  # full-term band evaluations, two bands per k-eval
+    single = st["k_evals_single"] / (2 * st["k_evals"])
     if mixed:
         assert 0.0 < frac < 0.6, frac
+        assert 0.0 < single <= frac, (single, frac)
     else:
         assert frac == 1.0, frac
+        assert single == 0.0, single
     assert np.array_equal(res["idx_star"], idx)
     assert per_site(res["omega_star"], star, N).max() <= TOL[ffe.FFE_FP32C]
     assert per_site(res["omega_lo"], om[..., 0], N).max() <= TOL[ffe.FFE_FP32C]
