@@ -581,8 +581,15 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
       far1[k] = !act1 || !valid[k] || far_band32(st[k].as.y, st[k].d0.y, w);
     }
     if constexpr (kG == kLayoutProduct) {
+      // far bands' a summed per batch; the other bands get eta^2 = 0, so a = 0
+      KState32 sf[KPT];
+#pragma unroll
+      for (int k = 0; k < KPT; ++k) {
+        sf[k] = st[k];
+        sf[k].eta2 = make_float2((far0[k] && act0 && valid[k]) ? st[k].eta2.x : 0.0f,
+                                 (far1[k] && act1 && valid[k]) ? st[k].eta2.y : 0.0f);
+      }
       int di = w.b0 / g.n_hblk, hb = w.b0 - di * g.n_hblk;  // batch b = di n_hblk + hb
-      float mine = 0.0f;  // the warp total of batch b0 + lane
       for (int b = w.b0; b < w.b1; ++b) {
         const float d2p = a.d2f[g.delta_off + di];
         if (++hb == g.n_hblk) {
@@ -593,18 +600,13 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
 #pragma unroll
         for (int k = 0; k < KPT; ++k) {
           float2 R, A;
-          ra32(st[k], d2p, R, A);
-          // active, valid, far bands only
-          A.x = (far0[k] && act0 && valid[k]) ? A.x : 0.0f;
-          A.y = (far1[k] && act1 && valid[k]) ? A.y : 0.0f;
+          ra32(sf[k], d2p, R, A);
           S = __fadd2_rn(S, A);
         }
-        float t = S.x + S.y;
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
-        mine = (lane == b - w.b0) ? t : mine;
+        red[(b - w.b0) * 36 + lane] = S.x + S.y;
       }
-      far_tot += (double)mine;  // one FP64 add per lane and k-set
+      // lane b - b0: the warp total of batch b; one FP64 add per lane and k-set
+      far_tot += (double)transposed_total(red, w.b1 - w.b0, lane);
     }
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
