@@ -165,55 +165,88 @@ __device__ __forceinline__ void band_pair(const ModelParams& m, Real cx, Real cy
 // ---- three-band model (App. B): eigenvalues of its hopping matrix -------
 // Its 3x3 hopping matrix has real T11, T22, T33, T12 and purely imaginary
 // T13 = i x, T23 = i y; conjugating with diag(1, 1, i) turns it into the real
-// symmetric matrix with off-diagonals T12, -x, -y and the same eigenvalues,
-// which cyclic Jacobi rotations (Jacobi 1846; the rotation of Rutishauser's
-// formulation) diagonalise in FP64.
-// One Jacobi rotation zeroing a_pq of a symmetric 3x3 matrix; r is the third index.
-__device__ __forceinline__ void jacobi_rotate(double& app, double& aqq, double& apq, double& arp, double& arq) {
-  if (apq == 0.0) return;
-  const double theta = (aqq - app) / (2.0 * apq);
-  double t;
-  if (fabs(theta) > 1e150)
-    t = 0.5 / theta;
+// symmetric matrix with off-diagonals T12, -x, -y and the same eigenvalues.
+// One Jacobi rotation (Jacobi 1846; the rotation of Rutishauser's
+// formulation) zeroing a_pq of a symmetric 3x3 matrix; r is the third index.
+template <typename R>
+__device__ __forceinline__ void jacobi_rotate(R& app, R& aqq, R& apq, R& arp, R& arq) {
+  if (apq == (R)0) return;
+  const R theta = (aqq - app) / ((R)2 * apq);
+  const R big = sizeof(R) == 4 ? (R)1e18f : (R)1e150;  // theta^2 would overflow
+  R t;
+  if (fabs(theta) > big)
+    t = (R)0.5 / theta;
   else
-    t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-  const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+    t = (theta >= (R)0 ? (R)1 : (R)-1) / (fabs(theta) + sqrt(theta * theta + (R)1));
+  const R c = (R)1 / sqrt(t * t + (R)1), s = t * c;
   app -= t * apq;
   aqq += t * apq;
-  apq = 0.0;
-  const double rp = c * arp - s * arq, rq = s * arp + c * arq;
+  apq = (R)0;
+  const R rp = c * arp - s * arq, rq = s * arp + c * arq;
   arp = rp;
   arq = rq;
 }
 
-// Eigenvalues, ascending, of the three-band matrix at momentum (cos, sin) of
-// each axis.
-__device__ __forceinline__ void bands3_at(const ModelParams& m, double cx, double sx, double cy, double sy,
-                                          double& e0, double& e1, double& e2) {
-  const double c2x = 2.0 * cx * cx - 1.0, c2y = 2.0 * cy * cy - 1.0;
-  double a00 = 2.0 * m.t2 * cx + 2.0 * m.t1 * cy + 4.0 * m.t3 * cx * cy + 2.0 * m.t11 * (c2x - c2y) +
-               4.0 * m.t12 * c2x * c2y;
-  double a11 = 2.0 * m.t1 * cx + 2.0 * m.t2 * cy + 4.0 * m.t3 * cx * cy - 2.0 * m.t11 * (c2x - c2y) +
-               4.0 * m.t12 * c2x * c2y;
-  double a22 = m.eps0 + 2.0 * m.t5 * (cx + cy) + 4.0 * m.t6 * cx * cy + 2.0 * m.t9 * (c2x + c2y) +
-               4.0 * m.t10 * (c2x * cy + cx * c2y);
-  double a01 = 4.0 * m.t4 * sx * sy;
-  double a02 = -(2.0 * m.t7 * sx + 4.0 * m.t8 * sx * cy);
-  double a12 = -(2.0 * m.t7 * sy + 4.0 * m.t8 * sy * cx);
-  // until the off-diagonal is 1e-14 of the diagonal (eigenvalue error below 1e-14 of the
-  // band width even at a degeneracy); quadratic convergence takes 3 to 4 sweeps
+// Cyclic Jacobi sweeps until the off-diagonal is `tol` of the diagonal
+// (quadratic convergence: 3 to 4 sweeps); eigenvalues ascending.
+template <typename R>
+__device__ __forceinline__ void jacobi3(R a00, R a11, R a22, R a01, R a02, R a12, R tol, R& e0, R& e1, R& e2) {
   for (int sweep = 0; sweep < 8; ++sweep) {
-    const double off = fabs(a01) + fabs(a02) + fabs(a12);
-    if (off <= 1e-14 * (fabs(a00) + fabs(a11) + fabs(a22) + 1e-300)) break;
-    jacobi_rotate(a00, a11, a01, a02, a12);  // (p, q) = (0, 1), r = 2
-    jacobi_rotate(a00, a22, a02, a01, a12);  // (0, 2), r = 1
-    jacobi_rotate(a11, a22, a12, a01, a02);  // (1, 2), r = 0
+    const R off = fabs(a01) + fabs(a02) + fabs(a12);
+    if (off <= tol * (fabs(a00) + fabs(a11) + fabs(a22) + (R)1e-30)) break;
+    jacobi_rotate<R>(a00, a11, a01, a02, a12);  // (p, q) = (0, 1), r = 2
+    jacobi_rotate<R>(a00, a22, a02, a01, a12);  // (0, 2), r = 1
+    jacobi_rotate<R>(a11, a22, a12, a01, a02);  // (1, 2), r = 0
   }
-  // sort the diagonal
-  double lo = fmin(a00, fmin(a11, a22)), hi = fmax(a00, fmax(a11, a22));
+  const R lo = fmin(a00, fmin(a11, a22)), hi = fmax(a00, fmax(a11, a22));
   e0 = lo;
   e2 = hi;
   e1 = a00 + a11 + a22 - lo - hi;
+}
+
+// Eigenvalues, ascending, of the three-band matrix at momentum (cos, sin) of
+// each axis, in FP64.  FP32 Jacobi gives estimates; two FP64 Newton steps on
+// the characteristic polynomial det(A - x) = ((c2 - x) x - c1) x + c0 from
+// the outer estimates give the outer eigenvalues and the trace the middle
+// one.  Where two estimates are closer than 1e-3 of the scale (the
+// polynomial's roots are ill-conditioned there) or a Newton step is not
+// small, FP64 Jacobi rotations to 1e-14 of the diagonal decide instead.
+__device__ __forceinline__ void bands3_at(const ModelParams& m, double cx, double sx, double cy, double sy,
+                                          double& e0, double& e1, double& e2) {
+  const double c2x = 2.0 * cx * cx - 1.0, c2y = 2.0 * cy * cy - 1.0;
+  const double a00 = 2.0 * m.t2 * cx + 2.0 * m.t1 * cy + 4.0 * m.t3 * cx * cy + 2.0 * m.t11 * (c2x - c2y) +
+                     4.0 * m.t12 * c2x * c2y;
+  const double a11 = 2.0 * m.t1 * cx + 2.0 * m.t2 * cy + 4.0 * m.t3 * cx * cy - 2.0 * m.t11 * (c2x - c2y) +
+                     4.0 * m.t12 * c2x * c2y;
+  const double a22 = m.eps0 + 2.0 * m.t5 * (cx + cy) + 4.0 * m.t6 * cx * cy + 2.0 * m.t9 * (c2x + c2y) +
+                     4.0 * m.t10 * (c2x * cy + cx * c2y);
+  const double a01 = 4.0 * m.t4 * sx * sy;
+  const double a02 = -(2.0 * m.t7 * sx + 4.0 * m.t8 * sx * cy);
+  const double a12 = -(2.0 * m.t7 * sy + 4.0 * m.t8 * sy * cx);
+  float f0, f1, f2;
+  jacobi3<float>((float)a00, (float)a11, (float)a22, (float)a01, (float)a02, (float)a12, 1e-6f, f0, f1, f2);
+  const double scale = fmax(fabs((double)f0), fabs((double)f2)) + 1e-30;
+  bool ok = fmin(f1 - f0, f2 - f1) >= 1e-3 * scale;
+  if (ok) {
+    const double c2 = a00 + a11 + a22;
+    const double c1 = a00 * a11 + a00 * a22 + a11 * a22 - a01 * a01 - a02 * a02 - a12 * a12;
+    const double c0 = a00 * (a11 * a22 - a12 * a12) - a01 * (a01 * a22 - a12 * a02) + a02 * (a01 * a12 - a11 * a02);
+    double x[2] = {(double)f0, (double)f2};
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        const double p = ((c2 - x[r]) * x[r] - c1) * x[r] + c0;
+        const double dp = (2.0 * c2 - 3.0 * x[r]) * x[r] - c1;
+        const double step = p / dp;
+        ok = ok && fabs(step) <= 1e-4 * scale;  // also false for NaN
+        x[r] -= step;
+      }
+    e0 = x[0];
+    e2 = x[1];
+    e1 = c2 - x[0] - x[1];
+  }
+  if (!ok) jacobi3<double>(a00, a11, a22, a01, a02, a12, 1e-14, e0, e1, e2);
 }
 
 // Per-k state: eta^2 and, per band, |s|, s^2 (floored at 1e-30 so that
