@@ -87,7 +87,7 @@ static bool finite(double x) { return std::isfinite(x); }
 namespace ffe {
 
 // Split every group's (batches x k-sets) into warp work items of roughly
-// `target` k-point evaluations, segments of <= kMaxBatchesPerItem batches.
+// `target` k-point evaluations, segments of <= max_batches(layout) batches.
 // FP32 path: a k-point is "far" for an item when, with h in [hlo, hhi] and
 // T <= Tmax over the item's outputs, min over bands of
 // |s| - max(|d0 - hlo|, |d0 - hhi|) >= tgap = 40 ln2 Tmax (+1e-5 against FP32
@@ -176,7 +176,7 @@ void build_items(ffe_plan* p) {
     const GroupDesc& g = p->groups[gi];
     const int64_t nk = (int64_t)g.N * g.N;
     const int n_ksets = (int)((nk + kset_pts - 1) / kset_pts);
-    const int sb = std::min(kMaxBatchesPerItem, std::max(1, g.n_batches));
+    const int sb = std::min(max_batches(g.layout), std::max(1, g.n_batches));
     for (int b0 = 0; b0 < g.n_batches; b0 += sb) {
       const int b1 = std::min(g.n_batches, b0 + sb);
       const int nb = b1 - b0;

@@ -27,7 +27,13 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kLayoutProduct = 0;  // outputs = Delta-list x (h,T)-list, shared R per Delta
 constexpr int kLayoutList = 1;     // outputs = explicit (Delta, h, T) triples
 constexpr int kLayoutProductUT = 2;  // kernel variant of PRODUCT: one T per 32-output batch
-constexpr int kMaxBatchesPerItem = 16;
+constexpr int kMaxBatchesPerItem = 16;  // batches (of 32 outputs) per work item, at most
+// LIST items take 8: their three entry buffers leave room for only 8 FP64
+// accumulator rows per warp at 16 warps per SM
+constexpr int kMaxBatchesList = 8;
+__host__ __device__ constexpr int max_batches(int group_layout) {
+  return group_layout == kLayoutList ? kMaxBatchesList : kMaxBatchesPerItem;
+}
 constexpr int kFlagRescored = 1;  // values of include/ffe.h FFE_FLAG_*
 constexpr int kFlagEdge = 2;
 constexpr int kFlagLower = 4;

@@ -678,8 +678,10 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  double* acc = reinterpret_cast<double*>(smem_raw) + (size_t)warp * (kMaxBatchesPerItem * 32);
-  unsigned char* after_acc = smem_raw + (size_t)nwarps * kMaxBatchesPerItem * 32 * sizeof(double);
+  constexpr int kGroupLayout = (LAYOUT == kLayoutList) ? kLayoutList : kLayoutProduct;
+  constexpr int kMB = max_batches(kGroupLayout);
+  double* acc = reinterpret_cast<double*>(smem_raw) + (size_t)warp * (kMB * 32);
+  unsigned char* after_acc = smem_raw + (size_t)nwarps * kMB * 32 * sizeof(double);
   BPar<Real>* bp = reinterpret_cast<BPar<Real>*>(after_acc) + warp * 32;
   // FP32 only: per-warp 32 x 36 transpose buffer of the output reduction and
   // the entry buffers (near; far for LIST), kbuf_entries(KPT) each
@@ -698,8 +700,7 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
     const WorkItem w = a.items[it];
     const GroupDesc g = a.groups[w.group];
     const int nb = w.b1 - w.b0;
-    constexpr int kGroupLayout = (LAYOUT == kLayoutList) ? kLayoutList : kLayoutProduct;
-    if (nb > kMaxBatchesPerItem || g.layout != kGroupLayout) {
+    if (nb > kMB || g.layout != kGroupLayout) {
       if (lane == 0) atomicOr(a.status, 1);
       continue;
     }
@@ -771,7 +772,8 @@ size_t ksum_smem_bytes(int prec, int layout, int kpt, int block_threads) {
   const size_t par = (prec == 1) ? sizeof(BParF) : sizeof(BParD);
   const int bufs = layout == kLayoutList ? 3 : 1;
   const size_t red = (prec == 1) ? 32 * 36 * sizeof(float) + (size_t)bufs * kbuf_entries(kpt) * sizeof(int32_t) : 0;
-  return (size_t)nw * (kMaxBatchesPerItem * 32 * sizeof(double) + 32 * par + red);
+  const int mb = max_batches(layout == kLayoutList ? kLayoutList : kLayoutProduct);
+  return (size_t)nw * (mb * 32 * sizeof(double) + 32 * par + red);
 }
 
 template <typename Real, int KPT, int LAYOUT>

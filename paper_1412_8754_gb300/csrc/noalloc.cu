@@ -44,7 +44,7 @@ constexpr size_t kOffC0D = align256(kOffTabD + 2 * kNAMaxN * sizeof(TabRowD));
 constexpr size_t kOffTabDF = align256(kOffC0D + 2 * kNAMaxN * sizeof(double));
 constexpr size_t kOffGroup = align256(kOffTabDF + 2 * kNAMaxN * sizeof(TabRowDF));
 constexpr size_t kOffSeg = align256(kOffGroup + sizeof(GroupDesc));
-constexpr int kNAMaxSegs = (kNAMaxOut / 32 + kMaxBatchesPerItem - 1) / kMaxBatchesPerItem;
+constexpr int kNAMaxSegs = (kNAMaxOut / 32 + kMaxBatchesList - 1) / kMaxBatchesList;
 constexpr size_t kOffItems = align256(kOffSeg + kNAMaxSegs * sizeof(Segment));
 constexpr size_t kOffMItems = align256(kOffItems + kNAMaxItems * sizeof(WorkItem));
 constexpr size_t kOffD2F = align256(kOffMItems + kNAMaxMItems * sizeof(MItem));
@@ -56,8 +56,8 @@ constexpr size_t kOffM = align256(kOffHList + kNAMaxOut * sizeof(double));
 constexpr size_t kOffMPart = align256(kOffM + kNAMaxOut * sizeof(double));
 constexpr size_t kOffMCnt = align256(kOffMPart + size_t(kNAMaxMItems) * 32 * sizeof(double));
 constexpr size_t kOffPart = align256(kOffMCnt + 64 * sizeof(int32_t));
-// partials: every k-chunk of every batch: <= kNAMaxItems items of <= kMaxBatchesPerItem batches
-constexpr size_t kOffV = align256(kOffPart + size_t(kNAMaxItems) * kMaxBatchesPerItem * 32 * sizeof(double));
+// partials: every k-chunk of every batch: <= kNAMaxItems items of <= kMaxBatchesList batches
+constexpr size_t kOffV = align256(kOffPart + size_t(kNAMaxItems) * kMaxBatchesList * 32 * sizeof(double));
 constexpr size_t kOffEB = align256(kOffV + kNAMaxOut * sizeof(double));
 constexpr size_t kOffCnt = align256(kOffEB + kNAMaxOut * sizeof(double));
 constexpr size_t kOffSegCnt = align256(kOffCnt + 8 * sizeof(int32_t));
@@ -130,9 +130,9 @@ extern "C" ffe_status ffe_omega_noalloc(const ffe_model* m, int32_t N, double qx
   const int64_t nk = (int64_t)N * N;
   const int kset_pts = 32 * kpt;
   const int n_ksets = (int)((nk + kset_pts - 1) / kset_pts);
-  // segments of <= kMaxBatchesPerItem batches, each split into the same k-chunks
-  const int n_segs = (g.n_batches + kMaxBatchesPerItem - 1) / kMaxBatchesPerItem;
-  const int seg_b = std::min(g.n_batches, kMaxBatchesPerItem);
+  // segments of <= kMaxBatchesList batches, each split into the same k-chunks
+  const int n_segs = (g.n_batches + kMaxBatchesList - 1) / kMaxBatchesList;
+  const int seg_b = std::min(g.n_batches, kMaxBatchesList);
   const double target = prec == FFE_FP32C ? 8388608.0 : 262144.0;
   int ck = (int)(target / ((double)seg_b * 32.0 * kset_pts));
   ck = std::max(ck, (n_ksets * n_segs + kNAMaxItems - 1) / kNAMaxItems);
@@ -142,7 +142,7 @@ extern "C" ffe_status ffe_omega_noalloc(const ffe_model* m, int32_t N, double qx
   int n_items = 0;
   int64_t poff = 0;
   for (int sg = 0; sg < n_segs; ++sg) {
-    const int b0 = sg * kMaxBatchesPerItem, b1 = std::min(g.n_batches, b0 + kMaxBatchesPerItem);
+    const int b0 = sg * kMaxBatchesList, b1 = std::min(g.n_batches, b0 + kMaxBatchesList);
     g_na_segs[sg] = Segment{0, b0, b1, n_chunks, poff};
     poff += (int64_t)n_chunks * (b1 - b0) * 32;
     for (int c = 0; c < n_chunks; ++c)
