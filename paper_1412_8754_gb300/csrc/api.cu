@@ -90,9 +90,10 @@ namespace ffe {
 // `target` k-point evaluations, segments of <= max_batches(layout) batches.
 // FP32 path: a k-point is "far" for an item when, with h in [hlo, hhi] and
 // T <= Tmax over the item's outputs, min over bands of
-// |s| - max(|d0 - hlo|, |d0 - hhi|) >= tgap = 40 ln2 Tmax (+1e-5 against FP32
-// rounding): then every output has c |R -+ d| >= 40, its four
-// (1 + 2^-c|R-+d|) factors are 1 in FP32, and its clamp term is c a.
+// |s| - max(|d0 - hlo|, |d0 - hhi|) >= tgap = 27 ln2 Tmax (+1e-5 against FP32
+// rounding): then every output has c |R -+ d| >= 27, each factor
+// (1 + 2^-c|R-+d|) leaves the FP32 product unchanged (P + P e with P e below
+// half an ulp of P: the same bits as the full term), and its clamp term is c a.
 // tgap = +inf for the FP64 path (no k-point is far).
 static void item_far_window(const ffe_plan* p, const GroupDesc& g, int b0, int b1, double golden_d2, WorkItem& w) {
   w.far_hlo = 0.0f;
@@ -151,7 +152,7 @@ static void item_far_window(const ffe_plan* p, const GroupDesc& g, int b0, int b
   // float bounds that contain the FP64 ones
   w.far_hlo = std::nextafter((float)hlo, -INFINITY);
   w.far_hhi = std::nextafter((float)hhi, INFINITY);
-  w.far_tgap = std::nextafter((float)(40.0 * 0.69314718055994530942 * tmax + 1e-5), INFINITY);
+  w.far_tgap = std::nextafter((float)(27.0 * 0.69314718055994530942 * tmax + 1e-5), INFINITY);
   w.sgl_r = std::nextafter((float)(27.0 * 0.69314718055994530942 * tmax + 1e-5), INFINITY);
 }
 

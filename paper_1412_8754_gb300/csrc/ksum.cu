@@ -227,7 +227,7 @@ __device__ __forceinline__ KState32 pack32(const Band32& x, const Band32& y) {
 }
 
 // Far band (see api.cu, item_far_window): for every output of the item the
-// band has c |R -+ d| >= 40, so its W is c a exactly in FP32.
+// band has c |R -+ d| >= 27, so its W is c a exactly in FP32.
 __device__ __forceinline__ bool far_band32(float as, float d0, const WorkItem& w) {
   return as - fmaxf(fabsf(d0 - w.far_hlo), fabsf(d0 - w.far_hhi)) >= w.far_tgap;
 }
