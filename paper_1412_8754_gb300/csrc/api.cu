@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -353,8 +354,9 @@ static ffe_status plan_alloc_requests(ffe_context* ctx, ffe_plan* p, Arena& aren
   p->e3_rows = e3_rows;
   ALLOC(d_e3d, e3_rows);
   ALLOC(d_e3f, e3_rows);
-  if (p->prec != FFE_FP32C || kst_rows * (int64_t)(sizeof(float4) + sizeof(float)) > kKstateTableMaxBytes)
-    kst_rows = 0;
+  int64_t kst_max = kKstateTableMaxBytes;  // FFE_KSTATE_TABLE_MAX_BYTES overrides (0: never a table)
+  if (const char* env = getenv("FFE_KSTATE_TABLE_MAX_BYTES")) kst_max = std::strtoll(env, nullptr, 10);
+  if (p->prec != FFE_FP32C || kst_rows * (int64_t)(sizeof(float4) + sizeof(float)) > kst_max) kst_rows = 0;
   p->kst_rows = kst_rows;
   ALLOC(d_kst4, kst_rows);
   ALLOC(d_kste, kst_rows);

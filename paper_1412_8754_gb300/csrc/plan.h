@@ -14,8 +14,9 @@ constexpr int kRing = 256;                          // timing event pairs per pl
 constexpr double kEbRel = 7.62939453125e-06;        // 2^-17: FP32 bound, relative to |sum_k v_k|
 constexpr double kEbAbs = 1.6527e-07;               // 2^-22 ln 2: log2 error per k-point, times T
 // The FP32 k-state table of a plan (20 bytes per group, band pair and lattice
-// point) is kept when it fits in this many bytes; larger plans build the
-// states inside the k-sum instead.
+// point) is kept when it fits in this many bytes (the environment variable
+// FFE_KSTATE_TABLE_MAX_BYTES, read when a plan is allocated, overrides it);
+// larger plans build the states inside the k-sum instead.
 constexpr int64_t kKstateTableMaxBytes = int64_t(32) << 30;
 
 enum { kPlanScanGrid = 1, kPlanMinGrid = 2, kPlanOmega = 3, kPlanScanGolden = 4, kPlanMinGolden = 5 };

@@ -142,6 +142,29 @@ def test_phase_scan_small(prec):
     assert np.array_equal(gbest, best)
 
 
+def test_states_built_in_the_ksum_match_the_table(monkeypatch):
+    """A plan too large for the FP32 k-state table builds the states inside the k-sum from the
+    trig tables, with the same FP32 arithmetic: a scan gives the same bits either way."""
+    N, U = 40, 4.0
+    qx = np.array([0.0, 0.2, 0.45])
+    args = (N, qx, np.zeros_like(qx), np.array([0.0, 0.05, 0.1]), np.array([0.004, 0.02]))
+    with ffe.Context(prec=ffe.FFE_FP32C, U=U) as ctx:
+        a = ctx.phase_scan(*args, n=33, lo=0.0, hi=0.2)
+    monkeypatch.setenv("FFE_KSTATE_TABLE_MAX_BYTES", "0")
+    with ffe.Context(prec=ffe.FFE_FP32C, U=U) as ctx:
+        b = ctx.phase_scan(*args, n=33, lo=0.0, hi=0.2)
+        plan = ctx.plan_phase_scan(*args, n=33, lo=0.0, hi=0.2)
+        without = plan.stats()["device_bytes"]
+        plan.destroy()
+    monkeypatch.delenv("FFE_KSTATE_TABLE_MAX_BYTES")
+    with ffe.Context(prec=ffe.FFE_FP32C, U=U) as ctx:
+        plan = ctx.plan_phase_scan(*args, n=33, lo=0.0, hi=0.2)
+        with_table = plan.stats()["device_bytes"]
+        plan.destroy()
+    assert_same_scan(a, b)
+    assert with_table - without >= len(qx) * N * N * 20 - 20  # the table (20 B per (q, k)) was left out
+
+
 @pytest.mark.parametrize("T, mixed", [(0.002, True), (0.6, False)])
 def test_far_k_points_take_the_short_form(T, mixed):
     """FP32: a band far from the Fermi surface for every output of a work item (its log
