@@ -174,17 +174,30 @@ __device__ __forceinline__ void band_pair(const ModelParams& m, Real cx, Real cy
 // symmetric matrix with off-diagonals T12, -x, -y and the same eigenvalues.
 // One Jacobi rotation (Jacobi 1846; the rotation of Rutishauser's
 // formulation) zeroing a_pq of a symmetric 3x3 matrix; r is the third index.
+// The FP32 form (estimates only) takes the approximate divide, reciprocal
+// square root and square root (x rsqrt(x)).
 template <typename R>
 __device__ __forceinline__ void jacobi_rotate(R& app, R& aqq, R& apq, R& arp, R& arq) {
   if (apq == (R)0) return;
-  const R theta = (aqq - app) / ((R)2 * apq);
-  const R big = sizeof(R) == 4 ? (R)1e18f : (R)1e150;  // theta^2 would overflow
-  R t;
-  if (fabs(theta) > big)
-    t = (R)0.5 / theta;
-  else
-    t = (theta >= (R)0 ? (R)1 : (R)-1) / (fabs(theta) + sqrt(theta * theta + (R)1));
-  const R c = (R)1 / sqrt(t * t + (R)1), s = t * c;
+  R t, c;
+  if constexpr (sizeof(R) == 4) {
+    const float theta = __fdividef(aqq - app, 2.0f * apq);
+    if (fabsf(theta) > 1e18f) {  // theta^2 would overflow
+      t = __fdividef(0.5f, theta);
+    } else {
+      const float q = theta * theta + 1.0f;
+      t = __fdividef(theta >= 0.0f ? 1.0f : -1.0f, fabsf(theta) + q * rsqrtf(q));
+    }
+    c = rsqrtf(t * t + 1.0f);
+  } else {
+    const R theta = (aqq - app) / ((R)2 * apq);
+    if (fabs(theta) > (R)1e150)  // theta^2 would overflow
+      t = (R)0.5 / theta;
+    else
+      t = (theta >= (R)0 ? (R)1 : (R)-1) / (fabs(theta) + sqrt(theta * theta + (R)1));
+    c = (R)1 / sqrt(t * t + (R)1);
+  }
+  const R s = t * c;
   app -= t * apq;
   aqq += t * apq;
   apq = (R)0;
@@ -214,9 +227,11 @@ __device__ __forceinline__ void jacobi3(R a00, R a11, R a22, R a01, R a02, R a12
 // each axis, in FP64.  FP32 Jacobi gives estimates; two FP64 Newton steps on
 // the characteristic polynomial det(A - x) = ((c2 - x) x - c1) x + c0 from
 // the outer estimates give the outer eigenvalues and the trace the middle
-// one.  Where two estimates are closer than 1e-3 of the scale (the
-// polynomial's roots are ill-conditioned there) or a Newton step is not
-// small, FP64 Jacobi rotations to 1e-14 of the diagonal decide instead.
+// one (each step divides by the derivative through an FP32 reciprocal: the
+// error still shrinks by a factor of ~1e-7 per step).  Where two estimates are
+// closer than 1e-4 of the scale (the polynomial's roots are ill-conditioned
+// there) or a Newton step is not small, FP64 Jacobi rotations to 1e-14 of the
+// diagonal decide instead.
 __device__ __forceinline__ void bands3_at(const ModelParams& m, double cx, double sx, double cy, double sy,
                                           double& e0, double& e1, double& e2) {
   const double c2x = 2.0 * cx * cx - 1.0, c2y = 2.0 * cy * cy - 1.0;
@@ -232,7 +247,7 @@ __device__ __forceinline__ void bands3_at(const ModelParams& m, double cx, doubl
   float f0, f1, f2;
   jacobi3<float>((float)a00, (float)a11, (float)a22, (float)a01, (float)a02, (float)a12, 1e-6f, f0, f1, f2);
   const double scale = fmax(fabs((double)f0), fabs((double)f2)) + 1e-30;
-  bool ok = fmin(f1 - f0, f2 - f1) >= 1e-3 * scale;
+  bool ok = fmin(f1 - f0, f2 - f1) >= 1e-4 * scale;
   if (ok) {
     const double c2 = a00 + a11 + a22;
     const double c1 = a00 * a11 + a00 * a22 + a11 * a22 - a01 * a01 - a02 * a02 - a12 * a12;
@@ -244,7 +259,7 @@ __device__ __forceinline__ void bands3_at(const ModelParams& m, double cx, doubl
       for (int it = 0; it < 2; ++it) {
         const double p = ((c2 - x[r]) * x[r] - c1) * x[r] + c0;
         const double dp = (2.0 * c2 - 3.0 * x[r]) * x[r] - c1;
-        const double step = p / dp;
+        const double step = p * (double)__frcp_rn((float)dp);
         ok = ok && fabs(step) <= 1e-4 * scale;  // also false for NaN
         x[r] -= step;
       }

@@ -46,33 +46,34 @@ cudaError_t tables_launch(const ModelParams&, const GroupDesc* groups, int n_gro
 
 // ---- three-band model (App. B): band tables (bands3_at, ffe_internal.cuh) --
 // Row (group g, momentum m, lattice point k): m = 0 is k + Q/2 (spin up),
-// m = 1 is -k + Q/2 (spin down; the sines' common sign does not change the
-// eigenvalues, so the k - Q/2 rows serve).
+// m = 1 is -k + Q/2 (spin down).  The second is the first at the lattice
+// point -k (mod N), so each thread diagonalises k + Q/2 once and writes it to
+// row (0, k) and row (1, -k).
 __global__ void bands3_kernel(const ModelParams m, const GroupDesc* __restrict__ groups,
                               const TabRowD* __restrict__ tabd, E3D* e3d, float4* e3f) {
   const GroupDesc g = groups[blockIdx.z];
   const int64_t nk = (int64_t)g.N * g.N;
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nk) return;
-  const int mom = blockIdx.y;
   const int iy = (int)(k / g.N);
   const int ix = (int)(k - (int64_t)iy * g.N);
   const TabRowD rx = tabd[g.tab_off + ix], ry = tabd[g.tab_off + g.N + iy];
   double e0, e1, e2;
-  if (mom == 0)
-    bands3_at(m, rx.cp, rx.sp, ry.cp, ry.sp, e0, e1, e2);
-  else
-    bands3_at(m, rx.cm, rx.sm, ry.cm, ry.sm, e0, e1, e2);
-  const int64_t row = g.e3_off + mom * nk + k;
-  e3d[row] = E3D{e0, e1, e2, 0.0};
-  e3f[row] = make_float4((float)e0, (float)e1, (float)e2, 0.0f);
+  bands3_at(m, rx.cp, rx.sp, ry.cp, ry.sp, e0, e1, e2);
+  const int mx = ix == 0 ? 0 : g.N - ix, my = iy == 0 ? 0 : g.N - iy;
+  const int64_t row0 = g.e3_off + k, row1 = g.e3_off + nk + (int64_t)my * g.N + mx;
+  e3d[row0] = E3D{e0, e1, e2, 0.0};
+  e3d[row1] = E3D{e0, e1, e2, 0.0};
+  const float4 f = make_float4((float)e0, (float)e1, (float)e2, 0.0f);
+  e3f[row0] = f;
+  e3f[row1] = f;
 }
 
 cudaError_t bands3_launch(const ModelParams& m, const GroupDesc* groups, int n_groups, int max_n,
                           const TabRowD* tabd, E3D* e3d, float4* e3f, cudaStream_t s) {
   if (n_groups <= 0 || m.nbands != 3) return cudaSuccess;
   const int64_t nk = (int64_t)max_n * max_n;
-  dim3 grid((unsigned)((nk + 255) / 256), 2, n_groups);
+  dim3 grid((unsigned)((nk + 255) / 256), 1, n_groups);
   bands3_kernel<<<grid, 256, 0, s>>>(m, groups, tabd, e3d, e3f);
   return cudaGetLastError();
 }
