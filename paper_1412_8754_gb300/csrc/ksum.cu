@@ -2,16 +2,20 @@
 //
 // Each warp repeatedly takes a work item (group, k-set range, output-batch
 // range) from a global atomic queue.  For every k-set of 32*KPT lattice points
-// it builds the per-k band state in registers from the trig tables (App. A
-// band energies at k+Q/2 and -k+Q/2: no band energies are stored in memory),
-// then for every batch of 32 outputs evaluates the k-point term v_k of each
-// output (see ffe_internal.cuh), sums it over the warp's k-points, and folds
-// the 32 per-lane sums into one value per output with a butterfly
-// reduce-scatter.  The warp keeps FP64 accumulators per output in shared
-// memory; at the end of the item it writes them as one partial per output and
-// the last warp to finish a segment (a fixed output range) adds the partials
-// of all its k-chunks in a fixed order (deterministic) and writes
-//   Omega = M + V + 2 N^2 Delta^2 / U
+// it loads the per-k band states (|s|, d0 per band, eta^2) from the FP32
+// k-state table that kstate_table_kernel writes once per execution (or, for
+// plans too large for the table, builds them from the trig tables: App. A
+// band energies at k+Q/2 and -k+Q/2).  FP32: each band is classified against
+// the item's window -- far bands (every log factor 1 in FP32) add c a, summed
+// per batch; near bands are compacted into a per-warp buffer and, 64*KPT at a
+// time, evaluated with the full term for every output of the item.  Per-lane
+// sums of a batch's 32 outputs are folded into one value per output through a
+// 32 x 36 transpose buffer in shared memory.  The warp keeps FP64
+// accumulators per output in shared memory; at the end of the item it writes
+// them as one partial per output and the last warp to finish a segment (a
+// fixed output range) adds the partials of all its k-chunks in a fixed order
+// (deterministic) and writes
+//   Omega = M + V + n_bands N^2 Delta^2 / U
 // together with an error bound for FP32 evaluation.  This replaces the
 // paper's per-block partial sums + second reduction kernel + host-side
 // remainder (Sec. 3, Alg. 2 and the three steps around it) by one launch.
@@ -684,7 +688,7 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
   unsigned char* after_acc = smem_raw + (size_t)nwarps * kMB * 32 * sizeof(double);
   BPar<Real>* bp = reinterpret_cast<BPar<Real>*>(after_acc) + warp * 32;
   // FP32 only: per-warp 32 x 36 transpose buffer of the output reduction and
-  // the entry buffers (near; far for LIST), kbuf_entries(KPT) each
+  // the entry buffers (near; LIST also far closed form and far series), kbuf_entries(KPT) each
   unsigned char* after_bp = after_acc + (size_t)nwarps * 32 * sizeof(BPar<Real>);
   float* red = reinterpret_cast<float*>(after_bp) + warp * 32 * 36;
   constexpr int kBufs = (LAYOUT == kLayoutList) ? 3 : 1;  // near (+ far closed form, far series for LIST)
