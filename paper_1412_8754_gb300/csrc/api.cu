@@ -95,7 +95,8 @@ namespace ffe {
 // rounding): then every output has c |R -+ d| >= 27, each factor
 // (1 + 2^-c|R-+d|) leaves the FP32 product unchanged (P + P e with P e below
 // half an ulp of P: the same bits as the full term), and its clamp term is c a.
-// tgap = +inf for the FP64 path (no k-point is far).
+// FP64 path: tgap = 750 Tmax, so that every exp(-|R -+ d|/T) of the band
+// underflows to 0 and its term is the clamp term -a alone, exactly.
 static void item_far_window(const ffe_plan* p, const GroupDesc& g, int b0, int b1, double golden_d2, WorkItem& w) {
   w.far_hlo = 0.0f;
   w.far_hhi = 0.0f;
@@ -103,8 +104,8 @@ static void item_far_window(const ffe_plan* p, const GroupDesc& g, int b0, int b
   w.far_d2max = INFINITY;
   w.sgl_d2min = 0.0f;
   w.sgl_r = INFINITY;
-  if (p->prec != FFE_FP32C) return;
-  if (p->golden_steps == 0) {  // the smallest Delta^2 of the item's outputs (golden: 0)
+  const bool f32 = p->prec == FFE_FP32C;
+  if (f32 && p->golden_steps == 0) {  // the smallest Delta^2 of the item's outputs (golden: 0)
     double d2 = INFINITY;
     for (int b = b0; b < b1; ++b) {
       if (g.layout == kLayoutProduct) {
@@ -119,7 +120,7 @@ static void item_far_window(const ffe_plan* p, const GroupDesc& g, int b0, int b
     }
     if (d2 < INFINITY) w.sgl_d2min = std::nextafter((float)d2, 0.0f);
   }
-  if (g.layout == kLayoutList) {  // the largest Delta^2 of the item's outputs
+  if (f32 && g.layout == kLayoutList) {  // the largest Delta^2 of the item's outputs
     double d2 = 0.0;
     if (p->golden_steps > 0) {  // golden brackets stay inside each line's [lo, hi]
       d2 = golden_d2;
@@ -153,6 +154,10 @@ static void item_far_window(const ffe_plan* p, const GroupDesc& g, int b0, int b
   // float bounds that contain the FP64 ones
   w.far_hlo = std::nextafter((float)hlo, -INFINITY);
   w.far_hhi = std::nextafter((float)hhi, INFINITY);
+  if (!f32) {
+    w.far_tgap = std::nextafter((float)(750.0 * tmax), INFINITY);
+    return;
+  }
   w.far_tgap = std::nextafter((float)(27.0 * 0.69314718055994530942 * tmax + 1e-5), INFINITY);
   w.sgl_r = std::nextafter((float)(27.0 * 0.69314718055994530942 * tmax + 1e-5), INFINITY);
 }

@@ -400,19 +400,32 @@ __device__ __forceinline__ float eval_far32(const KState32 (&st)[KPT], const BPa
   return transposed_total(red, nvalid, lane);
 }
 
+// fr[k][b]: band b of slot k is far for the whole warp (warp-uniform), so its
+// exponentials are exactly 0 and its term is -a (the same bits, without the
+// exp and log1p).
 template <int KPT>
 __device__ __forceinline__ double v_sum_f64(const KState<double> (&st)[KPT], const double (&R)[KPT][2],
-                                            const double (&A)[KPT][2], const BParD& p) {
+                                            const double (&A)[KPT][2], const BParD& p, const bool (&fr)[KPT][2]) {
   double s = 0.0;
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
-    double q0, f0, q1, f1;
-    band_term_f64(R[k][0], A[k][0], st[k].as[0], st[k].d0[0], p.h, p.inv_t, q0, f0);
-    band_term_f64(R[k][1], A[k][1], st[k].as[1], st[k].d0[1], p.h, p.inv_t, q1, f1);
-    const double Q = q0 + q1 + q0 * q1;  // (1+q0)(1+q1) - 1
-    s += (f0 + f1) - p.t * log1p(Q);
+    double q0 = 0.0, f0 = -A[k][0], q1 = 0.0, f1 = -A[k][1];
+    if (!fr[k][0]) band_term_f64(R[k][0], A[k][0], st[k].as[0], st[k].d0[0], p.h, p.inv_t, q0, f0);
+    if (!fr[k][1]) band_term_f64(R[k][1], A[k][1], st[k].as[1], st[k].d0[1], p.h, p.inv_t, q1, f1);
+    if (fr[k][0] && fr[k][1]) {
+      s += f0 + f1;
+    } else {
+      const double Q = q0 + q1 + q0 * q1;  // (1+q0)(1+q1) - 1
+      s += (f0 + f1) - p.t * log1p(Q);
+    }
   }
   return s;
+}
+
+// FP64 far band: for every output of the item |R -+ d| / T >= 750 (window as
+// in the FP32 path, threshold 750 T_max), so exp underflows to 0.
+__device__ __forceinline__ bool far_band64(double as, double d0, const WorkItem& w) {
+  return as - fmax(fabs(d0 - (double)w.far_hlo), fabs(d0 - (double)w.far_hhi)) >= (double)w.far_tgap;
 }
 
 template <typename Real, int KPT>
@@ -435,13 +448,13 @@ __device__ __forceinline__ void ra_all(const KState<Real> (&st)[KPT], Real d2, R
 // (butterfly reduce-scatter of the 32 per-lane sums).
 template <int KPT, int VARIANT>
 __device__ __forceinline__ double eval_batch64(const KState<double> (&st)[KPT], const BParD* bp, int nvalid,
-                                               double d2_product, int lane) {
+                                               double d2_product, int lane, const bool (&fr)[KPT][2]) {
   double part[32];
   if (VARIANT != kLayoutList) {
     double R[KPT][2], A[KPT][2];
     ra_all<double, KPT>(st, d2_product, R, A);
 #pragma unroll
-    for (int j = 0; j < 32; ++j) part[j] = (j < nvalid) ? v_sum_f64<KPT>(st, R, A, bp[j]) : 0.0;
+    for (int j = 0; j < 32; ++j) part[j] = (j < nvalid) ? v_sum_f64<KPT>(st, R, A, bp[j], fr) : 0.0;
   } else {
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
@@ -450,7 +463,7 @@ __device__ __forceinline__ double eval_batch64(const KState<double> (&st)[KPT], 
         const BParD p = bp[j];
         double R[KPT][2], A[KPT][2];
         ra_all<double, KPT>(st, p.d2, R, A);
-        s = v_sum_f64<KPT>(st, R, A, p);
+        s = v_sum_f64<KPT>(st, R, A, p, fr);
       }
       part[j] = s;
     }
@@ -717,6 +730,11 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
       if constexpr (!std::is_same<Real, float>::value) {
         KState<double> st[KPT];
         build_states<double, KPT>(a, g, ks, lane, pair, st);
+        bool fr[KPT][2];
+#pragma unroll
+        for (int k = 0; k < KPT; ++k)
+#pragma unroll
+          for (int b = 0; b < 2; ++b) fr[k][b] = __all_sync(kFull, far_band64(st[k].as[b], st[k].d0[b], w));
         for (int b = w.b0; b < w.b1; ++b) {
           int di;
           const int nvalid = stage_batch<double, kGroupLayout>(a, g, b, lane, bp, di);
@@ -725,7 +743,7 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
             const double dd = a.delta[g.delta_off + di];
             d2p = dd * dd;
           }
-          const double tot = eval_batch64<KPT, LAYOUT>(st, bp, nvalid, d2p, lane);
+          const double tot = eval_batch64<KPT, LAYOUT>(st, bp, nvalid, d2p, lane, fr);
           acc[(b - w.b0) * 32 + lane] += tot;
         }
       }
