@@ -390,10 +390,19 @@ ffe_status plan_alloc(ffe_context* ctx, ffe_plan* p) {
   Arena arena;
   for (int pass = 0; pass < 2; ++pass) {
     if (pass == 1) {  // one allocation for every buffer of the plan
+      const size_t need = std::max<size_t>(arena.off, 256);
       void* raw = nullptr;
-      cudaError_t e = cudaMalloc(&raw, std::max<size_t>(arena.off, 256));
-      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
-      p->allocs.push_back(raw);
+      if (ctx->spare && ctx->spare_bytes >= need && ctx->spare_bytes <= 2 * need + (size_t(64) << 20)) {
+        raw = ctx->spare;  // the context's kept block fits (and is not far larger)
+        p->arena_bytes = ctx->spare_bytes;
+        ctx->spare = nullptr;
+        ctx->spare_bytes = 0;
+      } else {
+        cudaError_t e = cudaMalloc(&raw, need);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+        p->arena_bytes = need;
+      }
+      p->arena = raw;
       arena.base = static_cast<unsigned char*>(raw);
       arena.off = 0;
     }
@@ -696,7 +705,19 @@ void plan_free(ffe_plan* p) {
   if (p->stream) cudaStreamSynchronize(p->stream);
   if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->graph) cudaGraphDestroy(p->graph);
-  for (void* a : p->allocs) cudaFree(a);
+  if (p->arena) {  // kept by the context for the next plan, or freed
+    ffe_context* c = p->ctx;
+    if (c && p->arena_bytes <= kSpareMaxBytes && p->arena_bytes > c->spare_bytes) {
+      // executions may still run on a caller's stream: wait for the device,
+      // as cudaFree would
+      cudaDeviceSynchronize();
+      if (c->spare) cudaFree(c->spare);
+      c->spare = p->arena;
+      c->spare_bytes = p->arena_bytes;
+    } else {
+      cudaFree(p->arena);
+    }
+  }
   if (p->ev_cap0) cudaEventDestroy(p->ev_cap0);
   if (p->ev_cap1) cudaEventDestroy(p->ev_cap1);
   for (int i = 0; i < kRing; ++i) {
@@ -986,6 +1007,7 @@ void ffe_destroy(ffe_context* ctx) {
   if (!ctx) return;
   for (ffe_plan* p : ctx->plans) plan_free(p);
   for (auto& kv : ctx->cache) plan_free(kv.second);
+  if (ctx->spare) cudaFree(ctx->spare);
   delete ctx;
 }
 

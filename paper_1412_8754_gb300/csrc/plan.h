@@ -18,6 +18,8 @@ constexpr double kEbAbs = 1.6527e-07;               // 2^-22 ln 2: log2 error pe
 // FFE_KSTATE_TABLE_MAX_BYTES, read when a plan is allocated, overrides it);
 // larger plans build the states inside the k-sum instead.
 constexpr int64_t kKstateTableMaxBytes = int64_t(32) << 30;
+// The largest freed plan block a context keeps for reuse.
+constexpr size_t kSpareMaxBytes = size_t(16) << 30;
 
 enum { kPlanScanGrid = 1, kPlanMinGrid = 2, kPlanOmega = 3, kPlanScanGolden = 4, kPlanMinGolden = 5 };
 
@@ -40,6 +42,11 @@ struct ffe_context {
   std::map<std::string, ffe_plan*> cache;     // plans reused by the host-buffer calls
   std::map<std::string, ffe::Tuning> tuned;   // autotuner results
   std::string tune_path;
+  // the device block of the last plan freed (at most kSpareMaxBytes), reused
+  // by the next plan that fits in it: short-lived plans (the surrogate-guided
+  // passes, the autotuner's trials) then skip cudaMalloc and cudaFree
+  void* spare = nullptr;
+  size_t spare_bytes = 0;
 };
 
 struct ffe_plan {
@@ -78,8 +85,9 @@ struct ffe_plan {
   int launches = 0;
   size_t bytes = 0;
   size_t h2d_bytes = 0, d2h_bytes = 0;
-  // device buffers
-  std::vector<void*> allocs;
+  // device buffers: one block (`arena`, arena_bytes) holds them all
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
   ffe::GroupDesc* d_groups = nullptr;
   ffe::WorkItem* d_items = nullptr;
   ffe::Segment* d_segs = nullptr;
