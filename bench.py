@@ -178,6 +178,43 @@ def run_extras(ffe, np, torch, stream, workloads):
     out["uneven_batch"] = {"jobs": 512, "k_evals_per_s": k / dt, "jobs_per_s": 512 / dt, "ms_per_step": 1e3 * dt,
                            "kernel_ms": kms, "autotuned": shape,
                            "workload": "512 jobs, N in {256,512,1024,2048}, 32..256 Delta, seed 1234"}
+
+    def timed(fn, reps=3):
+        fn()  # warm-up (plans, tables)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            r = fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps, r
+
+    # App. C pair susceptibility (FP64), two-band model
+    qs = np.linspace(0.0, 0.2 * math.pi, 32)
+    with ffe.Context(prec=ffe.FFE_FP64, U=2.0) as ctxc:
+        dtc, _ = timed(lambda: ctxc.pair_susceptibility(1024, qs, 0.0, 0.05, 0.002))
+    out["pair_susceptibility"] = {
+        "ms": 1e3 * dtc, "k_points_per_s": len(qs) * 1024 ** 2 / dtc,
+        "workload": "chi_ee'(q) of App. C, two-band model, N=1024, 32 q along x, h=0.05, T=0.002, FP64 "
+                    "(4 band pairs per k-point)"}
+    # full-Brillouin-zone Q scan: an 8 x 8 Q grid through its irreducible wedge
+    from paper_1412_8754_gb300 import qgrid
+    hs, Ts = np.linspace(0.0, 0.15, 32), np.array([0.002])
+    with ffe.Context(prec=ffe.FFE_FP32C, U=2.0) as ctxf:
+        dtf, rf = timed(lambda: qgrid.fbz_phase_scan(ctxf, 1024, 8, hs, Ts, n=64))
+    out["fbz_scan"] = {
+        "ms": 1e3 * dtf, "wedge_points": int(len(rf[3])), "grid_points": 64,
+        "labels": [int((rf[1] == i).sum()) for i in range(3)],
+        "workload": "Q over the 8 x 8 grid of the Brillouin zone (its 15-point wedge), N=1024, 32 h, T=0.002, "
+                    "64 Delta on [0, 0.2], FP32+comp"}
+    # per-band independent minimisation of the two-band model
+    pb = ffe.params(512, np.linspace(0.0, 0.2 * math.pi, 16).repeat(16), 0.0,
+                    np.tile(np.linspace(0.0, 0.15, 16), 16), 0.004, 0.0, 0.2, 64)
+    with ffe.Context(prec=ffe.FFE_FP32C, U=2.0) as ctxb:
+        dtb, _ = timed(lambda: ctxb.minimize_bands(pb))
+    out["per_band_minimize"] = {
+        "ms": 1e3 * dtb, "params_per_s": len(pb) / dtb,
+        "workload": "256 (q, h) points, each band minimised on its own: 64-point Delta grid, N=512, T=0.004, "
+                    "FP32+comp"}
     return out
 
 
