@@ -37,16 +37,9 @@ __device__ __forceinline__ double ln_sinhc(double y) {
   return ay + log1p(-exp(-2.0 * ay)) - 0.69314718055994530942 - log(ay);
 }
 
-__device__ __forceinline__ double pair_s(double a, double b, double T) {
-  const double x = 0.5 * a / T, z = 0.5 * b / T;
-  return exp(ln_sinhc(x + z) - ln_cosh(x) - ln_cosh(z)) / (4.0 * T);
-}
-
-// Band energies at momentum (kx, ky) of either model, ascending.
-__device__ __forceinline__ int bands_at(const ModelParams& m, double kx, double ky, double (&e)[3]) {
-  double sx, cx, sy, cy;
-  sincos(kx, &sx, &cx);
-  sincos(ky, &sy, &cy);
+// Band energies at a momentum given by (cos, sin) of each component, ascending.
+__device__ __forceinline__ int bands_at(const ModelParams& m, double cx, double sx, double cy, double sy,
+                                        double (&e)[3]) {
   if (m.nbands == 3) {
     bands3_at(m, cx, sx, cy, sy, e[0], e[1], e[2]);
     return 3;
@@ -59,28 +52,48 @@ __device__ __forceinline__ int bands_at(const ModelParams& m, double kx, double 
 constexpr int kChiChunk = 16384;  // k-points per block
 constexpr int kChiThreads = 256;
 
-__global__ void __launch_bounds__(kChiThreads) chi_kernel(const ModelParams m, int N, const double* __restrict__ qx,
-                                                          const double* __restrict__ qy, double h, double T,
+// (cos, sin) of both components of a pair momentum.
+struct __align__(16) QTrig {
+  double cx, sx, cy, sy;
+};
+
+// cs[i] = (cos, sin)(2 pi i / N), i < N; cq[q] = (cos qx, sin qx, cos qy, sin qy).
+// The momenta k and -k-q take their cosines and sines from these by the
+// angle-sum identities; ln cosh is formed once per band and momentum.
+__global__ void __launch_bounds__(kChiThreads) chi_kernel(const ModelParams m, int N, const double2* __restrict__ cs,
+                                                          const QTrig* __restrict__ cq, double h, double T,
                                                           int n_chunks, double* partials, int32_t* counters,
                                                           double* chi) {
   const int q = blockIdx.y, chunk = blockIdx.x;
   const int64_t nk = (int64_t)N * N;
   const int64_t k0 = (int64_t)chunk * kChiChunk, k1 = min(nk, k0 + kChiChunk);
   const int nb = m.nbands;
-  const double two_pi_n = 2.0 * 3.14159265358979323846 / (double)N;
+  const QTrig qq = cq[q];
+  const double half_inv_t = 0.5 / T;
   double acc[9];
 #pragma unroll
   for (int p = 0; p < 9; ++p) acc[p] = 0.0;
   for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     const int iy = (int)(k / N), ix = (int)(k - (int64_t)iy * N);
-    const double kx = two_pi_n * ix, ky = two_pi_n * iy;
+    const double2 tx = cs[ix], ty = cs[iy];
+    // k + q: cos(a + b) = ca cb - sa sb, sin(a + b) = sa cb + ca sb; -k-q: cos even, sin odd
+    const double cxq = tx.x * qq.cx - tx.y * qq.sx, sxq = tx.y * qq.cx + tx.x * qq.sx;
+    const double cyq = ty.x * qq.cy - ty.y * qq.sy, syq = ty.y * qq.cy + ty.x * qq.sy;
     double eu[3], ed[3];
-    bands_at(m, kx, ky, eu);
-    bands_at(m, -kx - qx[q], -ky - qy[q], ed);
-    const double eta = m.eta_amp * cos(kx + qx[q]) * cos(ky + qy[q]);
+    bands_at(m, tx.x, tx.y, ty.x, ty.y, eu);
+    bands_at(m, cxq, -sxq, cyq, -syq, ed);
+    const double eta = m.eta_amp * cxq * cyq;
     const double eta2 = eta * eta;
+    double xu[3], lu[3], zd[3], ld[3];
+    for (int e = 0; e < nb; ++e) {
+      xu[e] = (eu[e] - m.mu - h) * half_inv_t;
+      zd[e] = (ed[e] - m.mu + h) * half_inv_t;
+      lu[e] = ln_cosh(xu[e]);
+      ld[e] = ln_cosh(zd[e]);
+    }
+    const double w = eta2 / (4.0 * T);
     for (int e = 0; e < nb; ++e)
-      for (int f = 0; f < nb; ++f) acc[e * 3 + f] += eta2 * pair_s(eu[e] - m.mu - h, ed[f] - m.mu + h, T);
+      for (int f = 0; f < nb; ++f) acc[e * 3 + f] += w * exp(ln_sinhc(xu[e] + zd[f]) - lu[e] - ld[f]);
   }
   // block reduction of the 9 sums
   __shared__ double red[kChiThreads / 32][9];
@@ -130,24 +143,32 @@ extern "C" ffe_status ffe_pair_susceptibility(ffe_context* ctx, int32_t N, int32
   const int nb = ctx->mp.nbands;
   const int64_t nk = (int64_t)N * N;
   const int n_chunks = (int)((nk + kChiChunk - 1) / kChiChunk);
-  double *d_q = nullptr, *d_part = nullptr, *d_chi = nullptr;
+  std::vector<double2> cs(N);
+  std::vector<QTrig> cq(n_q);
+  const double two_pi_n = 2.0 * 3.14159265358979323846 / (double)N;
+  for (int i = 0; i < N; ++i) cs[i] = make_double2(std::cos(two_pi_n * i), std::sin(two_pi_n * i));
+  for (int i = 0; i < n_q; ++i) cq[i] = QTrig{std::cos(qx[i]), std::sin(qx[i]), std::cos(qy[i]), std::sin(qy[i])};
+  double2* d_cs = nullptr;
+  QTrig* d_cq = nullptr;
+  double *d_part = nullptr, *d_chi = nullptr;
   int32_t* d_cnt = nullptr;
-  cudaError_t e = cudaMalloc(&d_q, 2 * n_q * sizeof(double));
+  cudaError_t e = cudaMalloc(&d_cs, N * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc(&d_cq, n_q * sizeof(QTrig));
   if (e == cudaSuccess) e = cudaMalloc(&d_part, (size_t)n_q * n_chunks * 9 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&d_chi, (size_t)n_q * nb * nb * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&d_cnt, n_q * sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_q, qx, n_q * sizeof(double), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_q + n_q, qy, n_q * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_cs, cs.data(), N * sizeof(double2), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_cq, cq.data(), n_q * sizeof(QTrig), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, n_q * sizeof(int32_t), s);
   if (e == cudaSuccess) {
-    chi_kernel<<<dim3(n_chunks, n_q), kChiThreads, 0, s>>>(ctx->mp, N, d_q, d_q + n_q, h, T, n_chunks, d_part, d_cnt,
+    chi_kernel<<<dim3(n_chunks, n_q), kChiThreads, 0, s>>>(ctx->mp, N, d_cs, d_cq, h, T, n_chunks, d_part, d_cnt,
                                                             d_chi);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(chi, d_chi, (size_t)n_q * nb * nb * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  for (void* p : {(void*)d_q, (void*)d_part, (void*)d_chi, (void*)d_cnt})
+  for (void* p : {(void*)d_cs, (void*)d_cq, (void*)d_part, (void*)d_chi, (void*)d_cnt})
     if (p) cudaFree(p);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "pair susceptibility");
   return FFE_OK;
