@@ -440,6 +440,43 @@ def test_uneven_batch_full_size_sampled():
     assert np.all(np.abs(grid) > 0) and np.all(err >= 0)
 
 
+def test_fflo_scan_full_size_sampled():
+    """The benchmark's FFLO scan at full size (N = 1024, 64 q x 32 h x 256 Delta, one T, U = 2)
+    in the plan and launch configuration the benchmark times.  For two h values and every q the
+    oracle evaluates Omega at the GPU argmin, its neighbours and Delta = 0: values per site
+    within the FP32C tolerance, the argmin a local minimum of the oracle's Omega, and the label
+    and best q those the oracle's values give."""
+    cfg = workloads.fflo_scan()
+    U, N, T = 2.0, cfg["N"], float(cfg["T"][0])
+    grid = np.linspace(cfg["lo"], cfg["hi"], cfg["n"])
+    with ffe.Context(prec=ffe.FFE_FP32C, U=U) as ctx:
+        plan = ctx.plan_phase_scan(N, cfg["qx"], cfg["qy"], cfg["h"], cfg["T"], n=cfg["n"], lo=cfg["lo"],
+                                   hi=cfg["hi"])
+        plan.execute()
+        res, labels, best = plan.fetch()
+        plan.destroy()
+    m = oracle.make_model(U=U)
+    nq = len(cfg["qx"])
+    for ih in (3, 27):  # one point per (h, T): index ih of the h list
+        rows = []
+        for q in range(nq):
+            i = int(res["idx_star"][q, ih])
+            for ii in sorted({0, max(i - 1, 0), i, min(i + 1, cfg["n"] - 1)}):
+                rows.append((q, ii))
+        Q = np.array([r[0] for r in rows])
+        ref, _, _ = oracle.omega_batch(m, N, cfg["qx"][Q], 0.0, cfg["h"][ih], T, grid[[r[1] for r in rows]])
+        val = {r: ref[k] for k, r in enumerate(rows)}
+        star = np.array([val[(q, int(res["idx_star"][q, ih]))] for q in range(nq)])
+        zero = np.array([val[(q, 0)] for q in range(nq)])
+        assert per_site(res["omega_star"][:, ih], star, N).max() <= TOL[ffe.FFE_FP32C]
+        assert per_site(res["omega_lo"][:, ih], zero, N).max() <= TOL[ffe.FFE_FP32C]
+        for q in range(nq):
+            i = int(res["idx_star"][q, ih])
+            assert all(val[(q, i)] <= v + 1e-12 * abs(v) for (qq, _), v in val.items() if qq == q)
+        want, wq = search.phase_label(star, zero, cfg["qx"] == 0.0)
+        assert labels[ih] == want and best[ih] == wq
+
+
 def test_autotune_keeps_results():
     w = workloads.uneven_jobs(40, seed=8, sizes=(64, 128, 256))
     ps = ffe.params(w["N"], w["qx"], w["qy"], w["h"], w["T"], w["lo"], w["hi"], w["n"])
