@@ -477,6 +477,32 @@ def test_fflo_scan_full_size_sampled():
         assert labels[ih] == want and best[ih] == wq
 
 
+def test_golden_phase_diagram_full_size_sampled():
+    """The phase diagram's golden-section search at its full lattice (N = 2048, 24 reductions on
+    [0, 0.2]) on a few (q, h, T) lines: Omega at the GPU's Delta* and at Delta = 0 per site within
+    the FP32C tolerance, and Delta* no worse than the oracle at Delta* -+ 2e-3 (a minimum of the
+    oracle's Omega up to the FP32C tolerance)."""
+    pd = workloads.phase_diagram()
+    U, N = 2.0, pd["N"]
+    qx = pd["qx"][[0, 21, 42]]
+    h, T = pd["h"][[0, 40]], pd["T"][[0, 20]]
+    with ffe.Context(prec=ffe.FFE_FP32C, U=U) as ctx:
+        res, labels, best = ctx.phase_scan(N, qx, np.zeros_like(qx), h, T, search=ffe.FFE_SEARCH_GOLDEN,
+                                           n=pd["n"], lo=pd["lo"], hi=pd["hi"])
+    m = oracle.make_model(U=U)
+    pts = [(q, ih, it) for q in range(len(qx)) for ih in range(len(h)) for it in range(len(T))]
+    d = np.array([res["delta_star"][q, ih * len(T) + it] for q, ih, it in pts])
+    args = [(q, ih, it, x) for (q, ih, it), ds in zip(pts, d) for x in (ds, 0.0, max(ds - 2e-3, 0.0), ds + 2e-3)]
+    ref, _, _ = oracle.omega_batch(m, N, qx[[a[0] for a in args]], 0.0, h[[a[1] for a in args]],
+                                   T[[a[2] for a in args]], [a[3] for a in args])
+    ref = ref.reshape(len(pts), 4)
+    for k, (q, ih, it) in enumerate(pts):
+        pt = ih * len(T) + it
+        assert per_site(res["omega_star"][q, pt], ref[k, 0], N) <= TOL[ffe.FFE_FP32C]
+        assert per_site(res["omega_lo"][q, pt], ref[k, 1], N) <= TOL[ffe.FFE_FP32C]
+        assert (ref[k, 0] - ref[k, 2:].min()) / N ** 2 <= TOL[ffe.FFE_FP32C]
+
+
 def test_autotune_keeps_results():
     w = workloads.uneven_jobs(40, seed=8, sizes=(64, 128, 256))
     ps = ffe.params(w["N"], w["qx"], w["qy"], w["h"], w["T"], w["lo"], w["hi"], w["n"])
