@@ -265,6 +265,14 @@ FFE_API ffe_status ffe_plan_fetch_minimize(ffe_plan* plan, ffe_result* out, doub
 FFE_API ffe_status ffe_plan_autotune(ffe_plan* plan, void* stream, int32_t* kpt, int32_t* block,
                                      double* item_target);
 
+/* Environment variables read when a plan is built (none is needed):
+ *   FFE_KSUM_TUNING_FP32, FFE_KSUM_TUNING_FP64 = "kpt:block:item_target"
+ *     force the k-sum launch shape of FP32+comp / FP64 plans;
+ *   FFE_KSTATE_TABLE_MAX_BYTES = n
+ *     the largest FP32 k-state table (20 bytes per Q, band pair and lattice
+ *     point) a plan keeps (default 32 GiB; 0: none, the k-sum then builds
+ *     the states itself, with the same results). */
+
 /* ---- learned surrogate of Omega (no counterpart in the paper) ----------
  * A 4 -> 128 -> 128 -> 128 -> 1 MLP with SiLU activations over the raw
  * inputs (q, h, T, Delta), mapped to x = (raw - shift) * scale; it predicts
