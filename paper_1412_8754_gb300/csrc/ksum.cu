@@ -295,33 +295,30 @@ __device__ __forceinline__ float transposed_total(float* red, int nvalid, int la
   return tot;
 }
 
-// Far entries with x = Delta^2 eta^2 / s^2 <= 0.04 for every output of the
-// item: a = R - |s| = |s| (sqrt(1 + x) - 1) by the binomial series,
-// a = (D / 2|s|) (1 - x/4 + x^2/8 - 5x^3/64 + 7x^4/128 - 21x^5/512), truncated
-// where the next term is below 1.3e-10 relative -- no special-function unit.
-// Slot state per entry: eta^2 (eta2), 1/s^2 (s2), 1/(2|s|) (as).
-template <int KPT>
-__device__ __forceinline__ float eval_far32_series(const KState32 (&st)[KPT], const BParF* bp, int nvalid,
-                                                   int lane, float* red) {
-#pragma unroll 2
-  for (int j = 0; j < nvalid; ++j) {
-    const BParF p = bp[j];
-    const float2 d22 = make_float2(p.d2, p.d2);
-    float2 S = make_float2(0.0f, 0.0f);
+// LIST far bands with y = Delta_max^2 eta^2 / s^2 <= 0.04 (Delta_max^2 =
+// far_d2max bounds Delta^2 of every output of the item): by the binomial
+// series of a = R - |s| = |s| (sqrt(1 + x) - 1), x = Delta^2 eta^2 / s^2 =
+// t y with t = Delta^2 / Delta_max^2 <= 1,
+//   a = |s| sum_n alpha_n x^n = sum_n alpha_n t^n |s| y^n,
+//   alpha = 1/2, -1/8, 1/16, -5/128, 7/256, -21/1024 (n = 1..6; the next term is
+// below 1e-10 of the first), so the far sum of every output is the same six
+// moments M_n = sum_k |s_k| y_k^n, weighted by alpha_n t^n: the k-sum is
+// taken once per item, not once per output.
+constexpr int kMoments = 6;
+__device__ __forceinline__ void moments_add(float as, float y, float (&pm)[kMoments]) {
+  float t = as * y;
 #pragma unroll
-    for (int k = 0; k < KPT; ++k) {
-      const float2 D = __fmul2_rn(d22, st[k].eta2);
-      const float2 x = __fmul2_rn(D, st[k].s2);
-      float2 q = __ffma2_rn(x, make_float2(-21.0f / 512.0f, -21.0f / 512.0f), make_float2(7.0f / 128.0f, 7.0f / 128.0f));
-      q = __ffma2_rn(q, x, make_float2(-5.0f / 64.0f, -5.0f / 64.0f));
-      q = __ffma2_rn(q, x, make_float2(0.125f, 0.125f));
-      q = __ffma2_rn(q, x, make_float2(-0.25f, -0.25f));
-      q = __ffma2_rn(q, x, make_float2(1.0f, 1.0f));
-      S = __ffma2_rn(__fmul2_rn(D, st[k].as), q, S);
-    }
-    red[j * 36 + lane] = p.c * (S.x + S.y);
+  for (int n = 0; n < kMoments; ++n) {
+    pm[n] += t;
+    t *= y;
   }
-  return transposed_total(red, nvalid, lane);
+}
+__device__ __forceinline__ double moments_sum(const double (&M)[kMoments], double t) {
+  constexpr double alpha[kMoments] = {0.5, -0.125, 0.0625, -5.0 / 128.0, 7.0 / 256.0, -21.0 / 1024.0};
+  double r = alpha[kMoments - 1] * M[kMoments - 1];
+#pragma unroll
+  for (int n = kMoments - 2; n >= 0; --n) r = alpha[n] * M[n] + t * r;
+  return t * r;
 }
 
 // One batch of up to 32 outputs.  Output j's per-lane sum goes to row j of
@@ -511,7 +508,7 @@ __device__ void finalize_segment(const KsumArgs& a, const Segment& sg, const Gro
 
 // FP32 evaluation of n buffered (k-point, band) entries on every batch of the
 // item, two entries per float2 slot: the full term, or the far form W = c a.
-template <int KPT, int LAYOUT, bool FAR, bool SERIES = false>
+template <int KPT, int LAYOUT, bool FAR>
 __device__ __forceinline__ void flush32(const KsumArgs& a, const WorkItem& w, const GroupDesc& g, int lane,
                                         const int32_t* buf, int n, double* acc, BParF* bp, float* red) {
   constexpr int kG = (LAYOUT == kLayoutList) ? kLayoutList : kLayoutProduct;
@@ -520,14 +517,10 @@ __device__ __forceinline__ void flush32(const KsumArgs& a, const WorkItem& w, co
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
     const int i0 = 2 * k * 32 + lane, i1 = i0 + 32;
-    Band32 x = i0 < n ? band32_at(a, g, buf[i0]) : band32_inert();
-    Band32 y = i1 < n ? band32_at(a, g, buf[i1]) : band32_inert();
+    const Band32 x = i0 < n ? band32_at(a, g, buf[i0]) : band32_inert();
+    const Band32 y = i1 < n ? band32_at(a, g, buf[i1]) : band32_inert();
     if (i0 < n) sgl &= (buf[i0] >> kSingleBit) & 1;
     if (i1 < n) sgl &= (buf[i1] >> kSingleBit) & 1;
-    if constexpr (SERIES) {  // (eta^2, 1/(2|s|), 1/s^2); padding entries have eta^2 = 0
-      x = Band32{x.eta2, 0.5f / x.as, 1.0f / x.s2, 0.0f};
-      y = Band32{y.eta2, 0.5f / y.as, 1.0f / y.s2, 0.0f};
-    }
     st[k] = pack32(x, y);
   }
   const bool single = __all_sync(kFull, sgl);  // warp-uniform: one ex2 per near band
@@ -537,9 +530,7 @@ __device__ __forceinline__ void flush32(const KsumArgs& a, const WorkItem& w, co
     const int nvalid = stage_batch<float, kG>(a, g, b, lane, bp, di);
     outs += nvalid;
     float tot;
-    if constexpr (FAR && SERIES) {
-      tot = eval_far32_series<KPT>(st, bp, nvalid, lane, red);
-    } else if constexpr (FAR) {
+    if constexpr (FAR) {
       tot = eval_far32<KPT>(st, bp, nvalid, lane, red);
     } else {
       const float d2p = (kG == kLayoutProduct) ? a.d2f[g.delta_off + di] : 0.0f;
@@ -574,12 +565,15 @@ __device__ __forceinline__ void buffer_shift(int32_t* buf, int done, int n, int 
 template <int KPT, int LAYOUT>
 __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, const GroupDesc& g, int lane,
                                        double* acc, BParF* bp, float* red, int32_t* nbuf, int32_t* fbuf,
-                                       int32_t* xbuf) {
+                                       double* mom) {
   constexpr int kG = (LAYOUT == kLayoutList) ? kLayoutList : kLayoutProduct;
   constexpr int kFlush = 64 * KPT;
   const int64_t nk = (int64_t)g.N * g.N;
   const unsigned lt = (1u << lane) - 1u;
-  int n_near = 0, n_far = 0, n_ser = 0;  // LIST: far entries in closed form (fbuf) or series (xbuf)
+  int n_near = 0, n_far = 0;  // LIST: far entries in closed form (fbuf) or in the moments (mom)
+  if constexpr (kG == kLayoutList)
+#pragma unroll
+    for (int n = 0; n < kMoments; ++n) mom[n * 32 + lane] = 0.0;
   double far_tot = 0.0;  // PRODUCT: lane (b - b0) holds batch b's sum of a over far bands
   const int npairs = band_pairs(a.m.nbands);
   for (int ks = w.kset0; ks < w.kset1; ++ks)
@@ -588,6 +582,8 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
     build_states32<KPT>(a, g, ks, lane, pair, st);
     const bool act0 = slot_active(a.m.nbands, g.band_only, pair, 0);
     const bool act1 = slot_active(a.m.nbands, g.band_only, pair, 1);
+    float pm[kMoments] = {};  // LIST: this k-set's moments, this lane
+    bool any_ser = false;
     bool far0[KPT], far1[KPT], valid[KPT];
     int32_t kidx[KPT];
 #pragma unroll
@@ -645,15 +641,22 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
         n_near += __popc(m);
         if constexpr (kG == kLayoutList) {
           const bool fe = fr && act && valid[k];
-          const bool ser = fe && eta2 * w.far_d2max <= 0.04f * s2;  // x <= 0.04 for every output
+          const bool ser = fe && eta2 * w.far_d2max <= 0.04f * s2;  // y <= 0.04: into the moments
           const bool cf = fe && !ser;
-          const unsigned mf = __ballot_sync(kFull, cf), mx = __ballot_sync(kFull, ser);
+          const unsigned mf = __ballot_sync(kFull, cf);
           if (cf) fbuf[n_far + __popc(mf & lt)] = e;
-          if (ser) xbuf[n_ser + __popc(mx & lt)] = e;
           n_far += __popc(mf);
-          n_ser += __popc(mx);
+          if (ser) {
+            moments_add(sl == 0 ? st[k].as.x : st[k].as.y, __fdividef(eta2 * w.far_d2max, s2), pm);
+            any_ser = true;
+          }
         }
       }
+    }
+    if constexpr (kG == kLayoutList) {  // FP32 within a k-set, FP64 across k-sets
+      if (__any_sync(kFull, any_ser))
+#pragma unroll
+        for (int n = 0; n < kMoments; ++n) mom[n * 32 + lane] += (double)pm[n];
     }
     __syncwarp();
     if (n_near >= kFlush) {
@@ -667,17 +670,34 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
         buffer_shift(fbuf, kFlush, n_far, lane);
         n_far -= kFlush;
       }
-      if (n_ser >= kFlush) {
-        flush32<KPT, LAYOUT, true, true>(a, w, g, lane, xbuf, kFlush, acc, bp, red);
-        buffer_shift(xbuf, kFlush, n_ser, lane);
-        n_ser -= kFlush;
-      }
     }
   }
   if (n_near > 0) flush32<KPT, LAYOUT, false>(a, w, g, lane, nbuf, n_near, acc, bp, red);
   if constexpr (kG == kLayoutList) {
     if (n_far > 0) flush32<KPT, LAYOUT, true>(a, w, g, lane, fbuf, n_far, acc, bp, red);
-    if (n_ser > 0) flush32<KPT, LAYOUT, true, true>(a, w, g, lane, xbuf, n_ser, acc, bp, red);
+    // the moments' warp totals, then per output c sum_n alpha_n t^n M_n
+    double M[kMoments];
+    bool any = false;
+#pragma unroll
+    for (int n = 0; n < kMoments; ++n) {
+      double v = mom[n * 32 + lane];
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+      M[n] = v;
+      any = any || v != 0.0;
+    }
+    if (any) {
+      const double inv_d2max = 1.0 / (double)w.far_d2max;
+      for (int b = w.b0; b < w.b1; ++b) {
+        int di;
+        stage_batch<float, kG>(a, g, b, lane, bp, di);
+        const int o = b * 32 + lane;
+        if (o < g.n_out) {
+          const double d = a.delta[g.delta_off + o];
+          acc[(b - w.b0) * 32 + lane] += (double)bp[lane].c * moments_sum(M, d * d * inv_d2max);
+        }
+      }
+    }
   } else {
     for (int b = w.b0; b < w.b1; ++b) {
       int di;
@@ -704,11 +724,14 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
   // the entry buffers (near; LIST also far closed form and far series), kbuf_entries(KPT) each
   unsigned char* after_bp = after_acc + (size_t)nwarps * 32 * sizeof(BPar<Real>);
   float* red = reinterpret_cast<float*>(after_bp) + warp * 32 * 36;
-  constexpr int kBufs = (LAYOUT == kLayoutList) ? 3 : 1;  // near (+ far closed form, far series for LIST)
+  constexpr int kBufs = (LAYOUT == kLayoutList) ? 2 : 1;  // near (+ far closed form for LIST)
   int32_t* nbuf = reinterpret_cast<int32_t*>(after_bp + (size_t)nwarps * 32 * 36 * sizeof(float)) +
                   (size_t)warp * kBufs * kbuf_entries(KPT);
   int32_t* fbuf = nbuf + (kBufs > 1 ? 1 : 0) * kbuf_entries(KPT);
-  int32_t* xbuf = nbuf + (kBufs > 2 ? 2 : 0) * kbuf_entries(KPT);
+  // LIST: per-lane FP64 far-band moments, kMoments x 32 per warp
+  double* mom = reinterpret_cast<double*>(after_bp + (size_t)nwarps * 32 * 36 * sizeof(float) +
+                                          (size_t)nwarps * kBufs * kbuf_entries(KPT) * sizeof(int32_t)) +
+                (size_t)warp * kMoments * 32;
   for (;;) {
     int it = 0;
     if (lane == 0) it = atomicAdd(a.queue, 1);
@@ -723,7 +746,7 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
     }
     for (int b = 0; b < nb; ++b) acc[b * 32 + lane] = 0.0;
     if constexpr (std::is_same<Real, float>::value) {
-      item32<KPT, LAYOUT>(a, w, g, lane, acc, bp, red, nbuf, fbuf, xbuf);
+      item32<KPT, LAYOUT>(a, w, g, lane, acc, bp, red, nbuf, fbuf, mom);
     }
     for (int ks = w.kset0; ks < w.kset1; ++ks)
     for (int pair = 0; pair < band_pairs(a.m.nbands); ++pair) {
@@ -792,8 +815,10 @@ cudaError_t kstate_table_launch(const KsumArgs& a, int n_groups, int max_n, cuda
 size_t ksum_smem_bytes(int prec, int layout, int kpt, int block_threads) {
   const int nw = block_threads / 32;
   const size_t par = (prec == 1) ? sizeof(BParF) : sizeof(BParD);
-  const int bufs = layout == kLayoutList ? 3 : 1;
-  const size_t red = (prec == 1) ? 32 * 36 * sizeof(float) + (size_t)bufs * kbuf_entries(kpt) * sizeof(int32_t) : 0;
+  const int bufs = layout == kLayoutList ? 2 : 1;
+  const size_t mom = layout == kLayoutList ? (size_t)kMoments * 32 * sizeof(double) : 0;
+  const size_t red =
+      (prec == 1) ? 32 * 36 * sizeof(float) + (size_t)bufs * kbuf_entries(kpt) * sizeof(int32_t) + mom : 0;
   const int mb = max_batches(layout == kLayoutList ? kLayoutList : kLayoutProduct);
   return (size_t)nw * (mb * 32 * sizeof(double) + 32 * par + red);
 }
