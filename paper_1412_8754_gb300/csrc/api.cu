@@ -120,13 +120,18 @@ static void item_far_window(const ffe_plan* p, const GroupDesc& g, int b0, int b
     }
     if (d2 < INFINITY) w.sgl_d2min = std::nextafter((float)d2, 0.0f);
   }
-  if (f32 && g.layout == kLayoutList) {  // the largest Delta^2 of the item's outputs
+  if (f32) {  // the largest Delta^2 of the item's outputs
     double d2 = 0.0;
     if (p->golden_steps > 0) {  // golden brackets stay inside each line's [lo, hi]
       d2 = golden_d2;
-    } else {
+    } else if (g.layout == kLayoutList) {
       for (int64_t o = (int64_t)b0 * 32; o < std::min<int64_t>(g.n_out, (int64_t)b1 * 32); ++o) {
         const double d = p->delta[g.delta_off + o];
+        d2 = std::max(d2, d * d);
+      }
+    } else {
+      for (int b = b0; b < b1; ++b) {
+        const double d = p->delta[g.delta_off + b / g.n_hblk];
         d2 = std::max(d2, d * d);
       }
     }

@@ -594,15 +594,54 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
       far1[k] = !act1 || !valid[k] || far_band32(st[k].as.y, st[k].d0.y, w);
     }
     if constexpr (kG == kLayoutProduct) {
-      // far bands' a summed per batch; the other bands get eta^2 = 0, so a = 0
+      // Far bands in the series range (y = Delta_max^2 eta^2 / s^2 <= 0.04):
+      // the warp's six moments, then lane b - b0 evaluates batch b's
+      // sum_n alpha_n t^n M_n.  The other far bands' a is summed per batch
+      // (every other band gets eta^2 = 0 there, so a = 0).
       KState32 sf[KPT];
+      bool any_cf = false;
+      float2 pm2[kMoments];
+#pragma unroll
+      for (int n = 0; n < kMoments; ++n) pm2[n] = make_float2(0.0f, 0.0f);
+      const float2 dmx = make_float2(w.far_d2max, w.far_d2max);
 #pragma unroll
       for (int k = 0; k < KPT; ++k) {
+        const bool f0 = far0[k] && act0 && valid[k], f1 = far1[k] && act1 && valid[k];
+        const bool s0 = f0 && st[k].eta2.x * w.far_d2max <= 0.04f * st[k].s2.x;
+        const bool s1 = f1 && st[k].eta2.y * w.far_d2max <= 0.04f * st[k].s2.y;
+        const float2 y = __fmul2_rn(__fmul2_rn(st[k].eta2, dmx), make_float2(rcpa(st[k].s2.x), rcpa(st[k].s2.y)));
+        float2 tt = __fmul2_rn(make_float2(s0 ? st[k].as.x : 0.0f, s1 ? st[k].as.y : 0.0f), y);
+#pragma unroll
+        for (int n = 0; n < kMoments; ++n) {
+          pm2[n] = __fadd2_rn(pm2[n], tt);
+          tt = __fmul2_rn(tt, y);
+        }
         sf[k] = st[k];
-        sf[k].eta2 = make_float2((far0[k] && act0 && valid[k]) ? st[k].eta2.x : 0.0f,
-                                 (far1[k] && act1 && valid[k]) ? st[k].eta2.y : 0.0f);
+        sf[k].eta2 = make_float2(f0 && !s0 ? st[k].eta2.x : 0.0f, f1 && !s1 ? st[k].eta2.y : 0.0f);
+        any_cf = any_cf || (f0 && !s0) || (f1 && !s1);
+      }
+      {
+        float M[kMoments];
+        bool anym = false;
+#pragma unroll
+        for (int n = 0; n < kMoments; ++n) {
+          float v = pm2[n].x + pm2[n].y;
+#pragma unroll
+          for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+          M[n] = v;
+          anym = anym || v != 0.0f;
+        }
+        if (anym && lane < w.b1 - w.b0) {
+          const float t = a.d2f[g.delta_off + (w.b0 + lane) / g.n_hblk] / w.far_d2max;
+          constexpr float alpha[kMoments] = {0.5f, -0.125f, 0.0625f, -5.0f / 128.0f, 7.0f / 256.0f, -21.0f / 1024.0f};
+          float r = alpha[kMoments - 1] * M[kMoments - 1];
+#pragma unroll
+          for (int n = kMoments - 2; n >= 0; --n) r = fmaf(t, r, alpha[n] * M[n]);
+          far_tot += (double)(t * r);
+        }
       }
       int di = w.b0 / g.n_hblk, hb = w.b0 - di * g.n_hblk;  // batch b = di n_hblk + hb
+      if (__any_sync(kFull, any_cf)) {
       for (int b = w.b0; b < w.b1; ++b) {
         const float d2p = a.d2f[g.delta_off + di];
         if (++hb == g.n_hblk) {
@@ -620,6 +659,7 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
       }
       // lane b - b0: the warp total of batch b; one FP64 add per lane and k-set
       far_tot += (double)transposed_total(red, w.b1 - w.b0, lane);
+      }
     }
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
