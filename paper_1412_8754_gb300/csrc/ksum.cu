@@ -295,16 +295,18 @@ __device__ __forceinline__ float transposed_total(float* red, int nvalid, int la
   return tot;
 }
 
-// LIST far bands with y = Delta_max^2 eta^2 / s^2 <= 0.04 (Delta_max^2 =
+// Far bands with y = Delta_max^2 eta^2 / s^2 <= kSeriesY (Delta_max^2 =
 // far_d2max bounds Delta^2 of every output of the item): by the binomial
 // series of a = R - |s| = |s| (sqrt(1 + x) - 1), x = Delta^2 eta^2 / s^2 =
 // t y with t = Delta^2 / Delta_max^2 <= 1,
 //   a = |s| sum_n alpha_n x^n = sum_n alpha_n t^n |s| y^n,
-//   alpha = 1/2, -1/8, 1/16, -5/128, 7/256, -21/1024 (n = 1..6; the next term is
-// below 1e-10 of the first), so the far sum of every output is the same six
-// moments M_n = sum_k |s_k| y_k^n, weighted by alpha_n t^n: the k-sum is
-// taken once per item, not once per output.
+//   alpha = 1/2, -1/8, 1/16, -5/128, 7/256, -21/1024 (n = 1..6; the next term,
+// 33/2048 x^7, is below 3.3e-8 of the first for y <= 0.1), so the far sum of
+// every output is the same six moments M_n = sum_k |s_k| y_k^n, weighted by
+// alpha_n t^n: the k-sum is taken once per item (LIST) or k-set (shared
+// Delta), not once per output.
 constexpr int kMoments = 6;
+constexpr float kSeriesY = 0.1f;
 __device__ __forceinline__ void moments_add(float as, float y, float (&pm)[kMoments]) {
   float t = as * y;
 #pragma unroll
@@ -594,7 +596,7 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
       far1[k] = !act1 || !valid[k] || far_band32(st[k].as.y, st[k].d0.y, w);
     }
     if constexpr (kG == kLayoutProduct) {
-      // Far bands in the series range (y = Delta_max^2 eta^2 / s^2 <= 0.04):
+      // Far bands in the series range (y = Delta_max^2 eta^2 / s^2 <= kSeriesY):
       // the warp's six moments, then lane b - b0 evaluates batch b's
       // sum_n alpha_n t^n M_n.  The other far bands' a is summed per batch
       // (every other band gets eta^2 = 0 there, so a = 0).
@@ -607,8 +609,8 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
 #pragma unroll
       for (int k = 0; k < KPT; ++k) {
         const bool f0 = far0[k] && act0 && valid[k], f1 = far1[k] && act1 && valid[k];
-        const bool s0 = f0 && st[k].eta2.x * w.far_d2max <= 0.04f * st[k].s2.x;
-        const bool s1 = f1 && st[k].eta2.y * w.far_d2max <= 0.04f * st[k].s2.y;
+        const bool s0 = f0 && st[k].eta2.x * w.far_d2max <= kSeriesY * st[k].s2.x;
+        const bool s1 = f1 && st[k].eta2.y * w.far_d2max <= kSeriesY * st[k].s2.y;
         const float2 y = __fmul2_rn(__fmul2_rn(st[k].eta2, dmx), make_float2(rcpa(st[k].s2.x), rcpa(st[k].s2.y)));
         float2 tt = __fmul2_rn(make_float2(s0 ? st[k].as.x : 0.0f, s1 ? st[k].as.y : 0.0f), y);
 #pragma unroll
@@ -681,7 +683,7 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
         n_near += __popc(m);
         if constexpr (kG == kLayoutList) {
           const bool fe = fr && act && valid[k];
-          const bool ser = fe && eta2 * w.far_d2max <= 0.04f * s2;  // y <= 0.04: into the moments
+          const bool ser = fe && eta2 * w.far_d2max <= kSeriesY * s2;  // into the moments
           const bool cf = fe && !ser;
           const unsigned mf = __ballot_sync(kFull, cf);
           if (cf) fbuf[n_far + __popc(mf & lt)] = e;
