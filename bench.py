@@ -35,19 +35,21 @@ SFU_OTHER_PER_CLK = 16
 SM_MAX_MHZ = 2070.0
 
 
-def sfu_clk_per_band_eval(n_ht: int):
+def sfu_clk_per_band_eval(n_ht: int, outs_per_item: int):
     """SFU time (SM clocks) per band evaluation (one k-point, one band, one output) in the
-    shared-Delta scan layout, (near with two exponentials, near with one, far).  A far band
-    (its log factors 1 in FP32) needs only R and a: 1 rsqrt + 1 rcp per (k, Delta, band),
-    shared by the (up to 32) (h, T) outputs of one batch.  A near band is evaluated in full,
-    packed with another near band in a float2 slot: per output 2 ex2 -- 1 where c (R + |d|)
-    >= 27 makes the second factor exactly 1 -- and an eighth of one lg2 (one lg2 per output
-    over a lane's four slots), and its R and a a second time (once in the far pass, once in
-    the full-term pass)."""
+    shared-Delta scan layout: (near with two exponentials, near with one, far in the closed
+    form, far in the moments).  Every far band takes one rcp per k-set for y = Delta_max^2
+    eta^2 / s^2, shared by the item's outputs; one outside the series range (y > 0.1) also
+    needs R and a: 1 rsqrt + 1 rcp per (k, Delta, band), shared by the (up to 32) (h, T)
+    outputs of one batch.  A near band is evaluated in full, packed with another near band in
+    a float2 slot: per output 2 ex2 -- 1 where c (R + |d|) >= 27 makes the second factor
+    exactly 1 -- and an eighth of one lg2 (one lg2 per output over a lane's four slots), and
+    its R and a."""
     per_batch = min(32, n_ht)
     ra = 2.0 / (SFU_OTHER_PER_CLK * per_batch)
-    rest = 0.125 / SFU_OTHER_PER_CLK + 2.0 * ra
-    return 2.0 / SFU_EX2_PER_CLK + rest, 1.0 / SFU_EX2_PER_CLK + rest, ra
+    y = 1.0 / (SFU_OTHER_PER_CLK * outs_per_item)
+    rest = 0.125 / SFU_OTHER_PER_CLK + ra + y
+    return 2.0 / SFU_EX2_PER_CLK + rest, 1.0 / SFU_EX2_PER_CLK + rest, ra + y, y
 
 
 def dist_env():
@@ -463,14 +465,17 @@ def main():
 
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
-    c_near, c_single, c_far = sfu_clk_per_band_eval(n_pts)
-    band_evals = 2.0 * k_evals  # two bands per k-evaluation
     pst = plan.stats()
+    outs_item = min(16, cfg["n"]) * min(32, n_pts)  # outputs of one work item (16 batches of 32)
+    c_near, c_single, c_far, c_mom = sfu_clk_per_band_eval(n_pts, outs_item)
+    band_evals = 2.0 * k_evals  # two bands per k-evaluation
     b_near, b_single = pst["k_evals_near"], pst["k_evals_single"]  # full-term band evaluations
+    b_fc = pst["k_evals_far_closed"]  # far band evaluations in the closed form
     near_frac = b_near / band_evals if band_evals else 0.0
     single_frac = b_single / band_evals if band_evals else 0.0
-    clk_per_keval = 2.0 * ((near_frac - single_frac) * c_near + single_frac * c_single
-                           + (1.0 - near_frac) * c_far)
+    fc_frac = b_fc / band_evals if band_evals else 0.0
+    clk_per_keval = 2.0 * ((near_frac - single_frac) * c_near + single_frac * c_single + fc_frac * c_far
+                           + (1.0 - near_frac - fc_frac) * c_mom)
     peak = n_sm * SM_MAX_MHZ * 1e6 / clk_per_keval  # k-evals/s with the SFU saturated, at the maximum clock
     achieved = k_evals / (kern_ms / 1e3) if kern_ms > 0 else 0.0
 
@@ -489,10 +494,12 @@ def main():
                      "kernel": f"ksum_kernel<float,{info['kpt']},shared-Delta>", "kernel_ms": kern_ms,
                      "kernel_launches": kern_n,
                      "near_band_fraction": near_frac, "near_one_exp_fraction": single_frac,
+                     "far_closed_fraction": fc_frac,
                      "peak_basis": (f"{n_sm} SM x {SM_MAX_MHZ:.0f} MHz / {clk_per_keval:.4f} SFU clocks per "
                                     f"k-eval = 2 bands x ({near_frac - single_frac:.4f} x {c_near:.4f} (full "
                                     f"term, two ex2) + {single_frac:.4f} x {c_single:.4f} (full term, one ex2) "
-                                    f"+ {1 - near_frac:.4f} x {c_far:.4f} (far form)); ex2 "
+                                    f"+ {fc_frac:.4f} x {c_far:.4f} (far, R and a) + "
+                                    f"{1 - near_frac - fc_frac:.4f} x {c_mom:.5f} (far, moments)); ex2 "
                                     f"{SFU_EX2_PER_CLK}/clk, lg2 rsqrt rcp {SFU_OTHER_PER_CLK}/clk per SM; unit "
                                     f"counts checked by ffe_probe_peaks")},
         "fp64": fp64,

@@ -233,6 +233,12 @@ typedef struct {
                               item and that were evaluated with one exponential
                               (the other factor is exactly 1 in FP32); same
                               conventions                                     */
+  double k_evals_far_closed; /* FP32: far band evaluations that formed R and a
+                              (shared by an output batch's Delta, or per output
+                              in the LIST layout); the other far bands, with
+                              Delta_max^2 eta^2 / s^2 <= 0.1, enter six moments
+                              per k-set (shared Delta) or work item (LIST);
+                              same conventions                                */
 } ffe_plan_info;
 
 /* Static facts about a plan, the FP64 re-evaluation counts of the last

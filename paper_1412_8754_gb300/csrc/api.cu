@@ -336,7 +336,7 @@ static ffe_status plan_alloc_requests(ffe_context* ctx, ffe_plan* p, Arena& aren
   ALLOC(d_partials, p->n_partials);
   ALLOC(d_segcnt, p->segs.size());
   ALLOC(d_counters, 8);
-  ALLOC(d_near, 2);
+  ALLOC(d_near, 3);
   ALLOC(d_V, p->n_out);
   ALLOC(d_omega, p->n_out);
   ALLOC(d_eb, p->n_out);
@@ -508,7 +508,7 @@ ffe_status plan_enqueue(ffe_context* ctx, ffe_plan* p, cudaStream_t s, cudaEvent
                         unsigned ev_flags) {
   int launches = 0;
   FFE_CU(cudaMemsetAsync(p->d_counters, 0, 8 * sizeof(int32_t), s), "memset counters");
-  FFE_CU(cudaMemsetAsync(p->d_near, 0, 2 * sizeof(unsigned long long), s), "memset counters");
+  FFE_CU(cudaMemsetAsync(p->d_near, 0, 3 * sizeof(unsigned long long), s), "memset counters");
   FFE_CU(cudaMemsetAsync(p->d_rescored, 0, sizeof(int32_t) * std::max<int64_t>(1, p->n_out), s), "memset");
   FFE_CU(prep_params_launch(p->d_delta, (int64_t)p->delta.size(), p->d_d2f, p->d_ht, (int64_t)p->ht.size(),
                             p->d_htf, p->d_htd, s),
@@ -1059,11 +1059,13 @@ ffe_status ffe_plan_stats(const ffe_plan* p, ffe_plan_info* info) {
   info->device_bytes = (double)p->bytes;
   info->k_evals_near = -1.0;
   info->k_evals_single = -1.0;
+  info->k_evals_far_closed = -1.0;
   if (p->d_near && p->exec_count > 0) {
-    unsigned long long n[2] = {0, 0};
+    unsigned long long n[3] = {0, 0, 0};
     if (cudaMemcpy(n, p->d_near, sizeof n, cudaMemcpyDeviceToHost) != cudaSuccess) return FFE_ECUDA;
     info->k_evals_near = (double)n[0];
     info->k_evals_single = (double)n[1];
+    info->k_evals_far_closed = (double)n[2];
   }
   return FFE_OK;
 }

@@ -541,9 +541,13 @@ __device__ __forceinline__ void flush32(const KsumArgs& a, const WorkItem& w, co
     }
     acc[(b - w.b0) * 32 + lane] += (double)tot;
   }
-  if (!FAR && a.near_evals && lane == 0) {
-    atomicAdd(a.near_evals, (unsigned long long)(n * outs));
-    if (single) atomicAdd(a.near_evals + 1, (unsigned long long)(n * outs));
+  if (a.near_evals && lane == 0) {
+    if (FAR) {
+      atomicAdd(a.near_evals + 2, (unsigned long long)(n * outs));
+    } else {
+      atomicAdd(a.near_evals, (unsigned long long)(n * outs));
+      if (single) atomicAdd(a.near_evals + 1, (unsigned long long)(n * outs));
+    }
   }
 }
 
@@ -577,6 +581,7 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
 #pragma unroll
     for (int n = 0; n < kMoments; ++n) mom[n * 32 + lane] = 0.0;
   double far_tot = 0.0;  // PRODUCT: lane (b - b0) holds batch b's sum of a over far bands
+  int n_cf = 0;           // PRODUCT: this lane's far bands outside the series range (eta != 0)
   const int npairs = band_pairs(a.m.nbands);
   for (int ks = w.kset0; ks < w.kset1; ++ks)
   for (int pair = 0; pair < npairs; ++pair) {
@@ -644,6 +649,8 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
       }
       int di = w.b0 / g.n_hblk, hb = w.b0 - di * g.n_hblk;  // batch b = di n_hblk + hb
       if (__any_sync(kFull, any_cf)) {
+#pragma unroll
+      for (int k = 0; k < KPT; ++k) n_cf += (sf[k].eta2.x != 0.0f) + (sf[k].eta2.y != 0.0f);
       for (int b = w.b0; b < w.b1; ++b) {
         const float d2p = a.d2f[g.delta_off + di];
         if (++hb == g.n_hblk) {
@@ -741,6 +748,14 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
       }
     }
   } else {
+    int t = n_cf;  // closed-form far band evaluations: entries x outputs
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+    if (a.near_evals && lane == 0 && t > 0) {
+      int64_t outs = 0;
+      for (int b = w.b0; b < w.b1; ++b) outs += min(32, g.n_ht - (b % g.n_hblk) * 32);
+      atomicAdd(a.near_evals + 2, (unsigned long long)((int64_t)t * outs));
+    }
     for (int b = w.b0; b < w.b1; ++b) {
       int di;
       stage_batch<float, kG>(a, g, b, lane, bp, di);

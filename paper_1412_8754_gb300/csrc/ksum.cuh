@@ -36,7 +36,7 @@ struct KsumArgs {
   int32_t w_scaled;  // 1: partial sums hold W (FP32 path), V = -T ln2 W; 0: they hold V
   int32_t pad1;
   unsigned long long* near_evals;  // FP32 path: band evaluations with the full term, [1] those with one
-                                   // exponential (NULL: not counted)
+                                   // exponential, [2] far ones in the closed form (NULL: not counted)
   const float4* e3f;               // three-band model: band tables (GroupDesc::e3_off), FP32
   const E3D* e3d;                  // and FP64
   // FP32 k-state table (NULL: states are built from the trig tables): per

@@ -66,7 +66,7 @@ class ffe_plan_info(ctypes.Structure):
                 ("rescored_search", ctypes.c_int32), ("rescored_labels", ctypes.c_int32),
                 ("kpt", ctypes.c_int32), ("block", ctypes.c_int32), ("grid", ctypes.c_int32),
                 ("work_items", ctypes.c_int32), ("reserved", ctypes.c_int32), ("k_evals_near", ctypes.c_double),
-                ("k_evals_single", ctypes.c_double)]
+                ("k_evals_single", ctypes.c_double), ("k_evals_far_closed", ctypes.c_double)]
 
 
 _lock = threading.Lock()

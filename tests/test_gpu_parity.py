@@ -187,12 +187,14 @@ def test_far_k_points_take_the_short_form(T, mixed):
         plan.destroy()
     frac = st["k_evals_near"] / (2 * st["k_evals"])  # full-term band evaluations, two bands per k-eval
     single = st["k_evals_single"] / (2 * st["k_evals"])
+    closed = st["k_evals_far_closed"] / (2 * st["k_evals"])  # far bands that formed R and a
     if mixed:
         assert 0.0 < frac < 0.6, frac
         assert 0.0 < single <= frac, (single, frac)
+        assert 0.0 <= closed <= 1.0 - frac, (closed, frac)
     else:
         assert frac == 1.0, frac
-        assert single == 0.0, single
+        assert single == 0.0 and closed == 0.0, (single, closed)
     assert np.array_equal(res["idx_star"], idx)
     assert per_site(res["omega_star"], star, N).max() <= TOL[ffe.FFE_FP32C]
     assert per_site(res["omega_lo"], om[..., 0], N).max() <= TOL[ffe.FFE_FP32C]
