@@ -127,9 +127,9 @@ def cpu_baseline(cfg, seconds_target=15.0):
 
 # DRAM bytes (read + write) of one k-sum launch of the default workload, from
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum, one pass on the full-size
-# launch): 1.50 GB read (the FP32 k-state table, 1.34 GB, and the trig and job
-# tables) + 0.271 GB written (the FP64 k-chunk partial sums).
-DRAM_TRAFFIC_PER_LAUNCH = 1.771e9
+# launch): 1.49 GB read (the FP32 k-state table, 1.34 GB, and the trig and job
+# tables) + 0.270 GB written (the FP64 k-chunk partial sums).
+DRAM_TRAFFIC_PER_LAUNCH = 1.760e9
 
 
 def run_extras(ffe, np, torch, stream, workloads):
