@@ -319,7 +319,8 @@ FFE_API ffe_status ffe_surrogate_train(ffe_surrogate* s, const float* x, const f
 /* Phase scan guided by the surrogate, grid or golden-section search.  The
  * surrogate predicts every (q, h, T) line on a Delta grid (the search grid;
  * 256 points on [lo, hi] for golden); per (h, T) the exact k-sum verifies
- * q = 0 and the q_keep lines of lowest predicted minimum, each on a window
+ * q = 0 and the q_keep lines of lowest predicted minimum (and, with a
+ * margin, the q the surrogate cannot order against the best), each on a window
  * of `window` grid points around its predicted minimum, with Delta = 0 as
  * the reference (with the FP64 re-evaluation and label passes of
  * ffe_phase_scan).  Grid: the window's grid points.  Golden: the window is
@@ -342,7 +343,10 @@ typedef struct {
                            condensation energy below +margin (the basins may
                            swap within the surrogate's error, as at a
                            first-order transition) is searched over the
-                           whole range instead; 0: never               */
+                           whole range instead, and beyond q_keep every q
+                           predicted to condense by more than margin with a
+                           predicted minimum within margin of the best one
+                           is kept too; 0: neither                      */
 } ffe_guide;
 typedef struct {
   double k_evals;       /* exact k-point evaluations done                    */

@@ -3,7 +3,9 @@
 // A full scan (Alg. 1) searches every (q, h, T) line over the whole Delta
 // range.  Guided, the surrogate first predicts the condensation energy of
 // every line on a Delta grid (tensor-core inference); per (h, T) only q = 0
-// and the q_keep lines with the lowest predicted minimum are verified by the
+// and the q_keep lines with the lowest predicted minimum (and any other q
+// predicted to condense whose minimum is within the margin of the best) are
+// verified by the
 // exact k-sum, each on a window of `window` grid points around its predicted
 // minimum, with Delta = 0 as the reference (same kernels, same FP64
 // re-evaluation of near ties, same label passes as the full scan).  A grid
@@ -272,6 +274,7 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
   // 2. which lines to verify, and on which window
   const int w = guide->window;
   std::vector<char> kept(n_lines, 0);
+  const float ys = surrogate_y_scale(sur);
   std::vector<int> wstart(n_lines, 0);
   std::vector<int32_t> kept_rows;
   std::vector<int64_t> row_of(n_lines, -1);
@@ -287,6 +290,17 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
       });
       kept[(size_t)q0 * n_pts + pt] = 1;
       for (int k = 0; k < (int)order.size() && k < guide->q_keep; ++k) kept[(size_t)order[k] * n_pts + pt] = 1;
+      // beyond q_keep: every q predicted to condense by more than the margin
+      // whose predicted minimum is within the margin of the best one (the
+      // surrogate cannot order them)
+      if (guide->margin > 0.0 && !order.empty()) {
+        const double best = (double)ymin[(size_t)order[0] * n_pts + pt] * ys;
+        for (int k = guide->q_keep; k < (int)order.size(); ++k) {
+          const double yk = (double)ymin[(size_t)order[k] * n_pts + pt] * ys;
+          if (yk >= -guide->margin || yk > best + guide->margin) break;
+          kept[(size_t)order[k] * n_pts + pt] = 1;
+        }
+      }
     }
     for (int l = 0; l < n_lines; ++l)
       if (kept[l]) {
@@ -322,7 +336,7 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
   std::vector<LineSpec> spec(n_lines);
   std::vector<char> redo(n_lines, 0);  // searched over the whole range
   const double n2 = (double)sc->N * (double)sc->N;
-  const float ys = surrogate_y_scale(sur);
+  // (ys: the surrogate's y scale, |t1| per site per unit of y)
   for (int l = 0; l < n_lines; ++l) {
     if (!kept[l]) {
       spec[l].grid_idx = {0};
