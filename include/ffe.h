@@ -327,7 +327,8 @@ FFE_API ffe_status ffe_surrogate_train(ffe_surrogate* s, const float* x, const f
  * the initial bracket and takes as many fewer reductions as reach the full
  * search's final bracket width.  An (h, T) point with a line whose verified
  * minimum lies on an inner window edge (or that `margin` flags) is scanned
- * again with that line over the whole range.  Unverified (pruned) lines are
+ * again with all its verified lines over the whole range.  Unverified
+ * (pruned) lines are
  * not evaluated: they are reported with idx_star 0 (grid) or -1 (golden),
  * flags FFE_FLAG_LOWER | FFE_FLAG_PRUNED and the Delta = 0 value of the
  * q = 0 line at the same (h, T); a line whose minimum is its Delta = 0 point

@@ -11,8 +11,9 @@
 // re-evaluation of near ties, same label passes as the full scan).  A grid
 // scan evaluates the window's grid points; a golden-section scan brackets
 // the window and needs fewer reductions for the same final bracket width.
-// Where a verified minimum sits on an inner edge of its window, the (h, T)
-// point is scanned again with that line over the whole range.
+// Where a verified minimum sits on an inner edge of its window (or the
+// margin flags a line), the (h, T) point is scanned again with all its
+// verified lines over the whole range.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -376,13 +377,15 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
       pts1.push_back(pt);
     }
   const int n1 = (int)pts1.size();
-  auto sub_spec = [&](const std::vector<int>& pts, bool whole_for_redo) {
+  // whole: every verified line of the points over the whole range (the
+  // second pass; a window left there would get no edge check)
+  auto sub_spec = [&](const std::vector<int>& pts, bool whole) {
     std::vector<LineSpec> out((size_t)sc->n_q * pts.size());
     for (int q = 0; q < sc->n_q; ++q)
       for (size_t j = 0; j < pts.size(); ++j) {
         const size_t l = (size_t)q * n_pts + pts[j];
         LineSpec ls = spec[l];
-        if (whole_for_redo && redo[l]) {
+        if (whole && !ls.alias) {
           if (golden) {
             ls.wlo = sc->lo;
             ls.whi = sc->hi;
@@ -455,6 +458,8 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
     }
 
   // 5. the second pass: every point with a line to search over the whole range
+  // (an ambiguous line, or one whose minimum sat on an inner window edge) has
+  // all its verified lines searched over the whole range
   std::vector<int> pos_in2(n_pts, -1);
   for (int pt = 0; pt < n_pts; ++pt)
     if (point_has_redo(pt)) {

@@ -136,6 +136,29 @@ def test_guided_golden_with_whole_range_window_is_the_golden_scan(ctx):
     assert st["k_evals"] == st["k_evals_full"]
 
 
+def test_guided_golden_rescans_every_line_of_a_flagged_point(ctx):
+    """An untrained surrogate places the windows arbitrarily and a huge margin flags every line
+    predicted at Delta = lo; no q is pruned.  A flagged point is scanned again with all its
+    verified lines over the whole range (a line left on its window there would get no edge
+    check), the others fall back on their window edges: labels and best q are the golden
+    scan's."""
+    from paper_1412_8754_gb300 import surrogate as sg
+
+    N, U, steps = 32, 4.0, 12
+    qx = np.array([0.0, 0.2, 0.4])
+    h = np.array([0.0, 0.05, 0.1, 0.15])
+    T = np.array([0.004, 0.015])
+    with ffe.Context(prec=ffe.FFE_FP32C, U=U) as c:
+        ref, rlab, rbest = c.phase_scan(N, qx, np.zeros(3), h, T, search=ffe.FFE_SEARCH_GOLDEN, n=steps)
+        for seed in (5, 6, 7):
+            s = ffe.Surrogate(c, mlp.SHIFT, mlp.SCALE, Y_SCALE, sg.initial_params(seed))
+            res, lab, best, st = ffe.ffe_surrogate_scan(c.handle, s, N, qx, np.zeros(3), h, T, n=steps, window=16,
+                                                        q_keep=2, margin=1e3, search=ffe.FFE_SEARCH_GOLDEN)
+            s.close()
+            assert st["lines_pruned"] == 0
+            assert np.array_equal(lab, rlab) and np.array_equal(best, rbest), (seed, lab, rlab, best, rbest)
+
+
 def test_trained_surrogate_guides_the_scan():
     """A surrogate trained on the library's own free energies cuts the exact work of a
     grid scan while finding the full scan's minima and labels; an untrained one does not."""
