@@ -1,0 +1,90 @@
+"""The numerical facts the FP32 k-sum and the band tables rely on, checked on the CPU.
+
+Each test restates one claim made in the kernels' comments and checks it independently of them
+(numpy, IEEE float32 / float64): where a shortcut gives the same bits as the full formula, and
+where a truncated expansion stays inside its stated bound."""
+import numpy as np
+import pytest
+
+ALPHA = [0.5, -0.125, 0.0625, -5.0 / 128.0, 7.0 / 256.0, -21.0 / 1024.0]  # sqrt(1+x) - 1 = sum alpha_n x^n
+
+
+def f32_fma(a, b, c):
+    """float32 fused multiply-add: the exact a*b + c, rounded once to float32."""
+    return np.float32(np.float64(a) * np.float64(b) + np.float64(c))
+
+
+def test_moment_series_of_R_minus_abs_s():
+    """a = R - |s| = |s| sum_n alpha_n x^n, x = Delta^2 eta^2 / s^2, n <= 6, within 3.3e-8 of a
+    for x <= 0.1 (the range the far-band moments take), and the coefficients are the binomial
+    series of sqrt(1 + x) - 1."""
+    from math import comb
+    for n, a in enumerate(ALPHA, start=1):  # binomial(1/2, n) = (-1)^(n+1) C(2n, n) / (4^n (2n - 1))
+        assert a == pytest.approx((-1) ** (n + 1) * comb(2 * n, n) / (4 ** n * (2 * n - 1)), rel=1e-15)
+    x = np.linspace(0.0, 0.1, 10001)[1:]
+    exact = np.sqrt(1.0 + x) - 1.0
+    series = sum(a * x ** (n + 1) for n, a in enumerate(ALPHA))
+    assert np.max(np.abs(series - exact) / exact) <= 3.3e-8
+    # t = Delta^2 / Delta_max^2 <= 1 scales y = Delta_max^2 eta^2 / s^2: x = t y, moments |s| y^n
+    rng = np.random.default_rng(1)
+    s, y = rng.uniform(0.01, 3.0, 200), rng.uniform(0.0, 0.1, 200)  # the far bands of one item
+    moments = [np.sum(s * y ** (n + 1)) for n in range(6)]
+    for t in (0.0, 1e-3, 0.25, 0.7, 1.0):  # one output each
+        via_moments = sum(ALPHA[n] * t ** (n + 1) * moments[n] for n in range(6))
+        direct = np.sum(s * (np.sqrt(1.0 + t * y) - 1.0))
+        assert via_moments == pytest.approx(direct, rel=3.3e-8, abs=1e-300)
+
+
+@pytest.mark.parametrize("y", [26.0, 27.0, 40.0, 80.0])
+def test_a_factor_below_2_to_minus_26_leaves_the_fp32_product_unchanged(y):
+    """P + P e with e <= 2^-y, y >= 26, rounds to P in float32 for every P >= 1: the far form
+    (threshold 27) and the one-exponential near form give the same bits as the full term."""
+    rng = np.random.default_rng(int(y))
+    P = np.float32(rng.uniform(1.0, 2.0 ** 32, 20000))
+    P = np.concatenate([P, np.float32([1.0, 2.0, 4.0, np.nextafter(np.float32(2.0), np.float32(0.0))])])
+    e = np.float32(2.0 ** -y)
+    out = np.array([f32_fma(p, e, p) for p in P], dtype=np.float32)
+    assert np.array_equal(out, P)
+    # ... while 2^-22 would not (the bound is tight enough to matter)
+    big = np.float32(2.0 ** -22)
+    assert not np.array_equal(np.array([f32_fma(p, big, p) for p in P[:100]], dtype=np.float32), P[:100])
+
+
+def test_fp64_exponential_underflows_at_750():
+    """exp(-x) is exactly 0 in FP64 for x >= 746: the FP64 far bands (|R -+ d| / T >= 750)
+    skip their exponentials with the same bits."""
+    assert np.exp(np.float64(-746.0)) == 0.0 and np.exp(np.float64(-750.0)) == 0.0
+    assert np.exp(np.float64(-745.0)) > 0.0
+
+
+def test_newton_steps_refine_fp32_eigenvalues_to_fp64():
+    """Outer eigenvalues of a real symmetric 3x3 matrix from FP32 estimates and two Newton
+    steps on det(A - x) = ((c2 - x) x - c1) x + c0, dividing by the derivative through an FP32
+    reciprocal, the middle one from the trace: FP64 accuracy when the eigenvalues are at least
+    1e-4 of the scale apart (the band tables fall back to FP64 Jacobi below that): the error of
+    the cubic's roots grows like eps scale / gap, so ~1e-12 of the scale at the closest gaps
+    and FP64 rounding for typical ones."""
+    rng = np.random.default_rng(7)
+    errs = []
+    for _ in range(2000):
+        q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        lam = np.sort(rng.uniform(-3.0, 3.0, 3))
+        if np.min(np.diff(lam)) < 1e-4 * np.max(np.abs(lam)):
+            continue
+        A = q @ np.diag(lam) @ q.T
+        A = 0.5 * (A + A.T)
+        est = np.sort(np.linalg.eigvalsh(A.astype(np.float32)).astype(np.float64))  # ~1e-7 relative
+        c2 = np.trace(A)
+        c1 = A[0, 0] * A[1, 1] + A[0, 0] * A[2, 2] + A[1, 1] * A[2, 2] - A[0, 1] ** 2 - A[0, 2] ** 2 - A[1, 2] ** 2
+        c0 = np.linalg.det(A)
+        out = []
+        for x in (est[0], est[2]):
+            for _ in range(2):
+                p = ((c2 - x) * x - c1) * x + c0
+                dp = (2.0 * c2 - 3.0 * x) * x - c1
+                x -= p * np.float64(np.float32(1.0) / np.float32(dp))
+            out.append(x)
+        e = np.array([out[0], c2 - out[0] - out[1], out[1]])
+        ref = np.linalg.eigvalsh(A)
+        errs.append(np.max(np.abs(e - ref)) / np.max(np.abs(ref)))
+    assert max(errs) < 1e-11 and np.median(errs) < 1e-14, (max(errs), np.median(errs))
