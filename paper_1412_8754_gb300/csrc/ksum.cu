@@ -650,24 +650,24 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
       int di = w.b0 / g.n_hblk, hb = w.b0 - di * g.n_hblk;  // batch b = di n_hblk + hb
       if (__any_sync(kFull, any_cf)) {
 #pragma unroll
-      for (int k = 0; k < KPT; ++k) n_cf += (sf[k].eta2.x != 0.0f) + (sf[k].eta2.y != 0.0f);
-      for (int b = w.b0; b < w.b1; ++b) {
-        const float d2p = a.d2f[g.delta_off + di];
-        if (++hb == g.n_hblk) {
-          hb = 0;
-          ++di;
-        }
-        float2 S = make_float2(0.0f, 0.0f);
+        for (int k = 0; k < KPT; ++k) n_cf += (sf[k].eta2.x != 0.0f) + (sf[k].eta2.y != 0.0f);
+        for (int b = w.b0; b < w.b1; ++b) {
+          const float d2p = a.d2f[g.delta_off + di];
+          if (++hb == g.n_hblk) {
+            hb = 0;
+            ++di;
+          }
+          float2 S = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int k = 0; k < KPT; ++k) {
-          float2 R, A;
-          ra32(sf[k], d2p, R, A);
-          S = __fadd2_rn(S, A);
+          for (int k = 0; k < KPT; ++k) {
+            float2 R, A;
+            ra32(sf[k], d2p, R, A);
+            S = __fadd2_rn(S, A);
+          }
+          red[(b - w.b0) * 36 + lane] = S.x + S.y;
         }
-        red[(b - w.b0) * 36 + lane] = S.x + S.y;
-      }
-      // lane b - b0: the warp total of batch b; one FP64 add per lane and k-set
-      far_tot += (double)transposed_total(red, w.b1 - w.b0, lane);
+        // lane b - b0: the warp total of batch b; one FP64 add per lane and k-set
+        far_tot += (double)transposed_total(red, w.b1 - w.b0, lane);
       }
     }
 #pragma unroll
