@@ -105,7 +105,8 @@ struct WorkItem {
   // >= far_tgap is "far" for all of them (see ksum.cu); far_tgap = +inf:
   // no k-point is.
   float far_hlo, far_hhi, far_tgap;
-  // LIST items: Delta^2 <= far_d2max for every output (bounds the far series)
+  // Delta^2 <= far_d2max for every output of the item (the scale of the
+  // far-band moments, ksum.cu)
   float far_d2max;
   // Delta^2 >= sgl_d2min for every output; sgl_r = 27 ln2 Tmax (+ rounding
   // margin): a near band with R + |d| >= sgl_r for every output has

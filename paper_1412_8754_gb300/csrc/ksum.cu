@@ -778,7 +778,7 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
   unsigned char* after_acc = smem_raw + (size_t)nwarps * kMB * 32 * sizeof(double);
   BPar<Real>* bp = reinterpret_cast<BPar<Real>*>(after_acc) + warp * 32;
   // FP32 only: per-warp 32 x 36 transpose buffer of the output reduction and
-  // the entry buffers (near; LIST also far closed form and far series), kbuf_entries(KPT) each
+  // the entry buffers (near; LIST also far closed form), kbuf_entries(KPT) each
   unsigned char* after_bp = after_acc + (size_t)nwarps * 32 * sizeof(BPar<Real>);
   float* red = reinterpret_cast<float*>(after_bp) + warp * 32 * 36;
   constexpr int kBufs = (LAYOUT == kLayoutList) ? 2 : 1;  // near (+ far closed form for LIST)
