@@ -46,13 +46,14 @@ class Model(ctypes.Structure):
         ("mu", ctypes.c_double),
         ("eta_amp", ctypes.c_double),
         ("U", ctypes.c_double),
+        ("U_band", ctypes.c_double * 2),   # per-band coupling; 0 = U
     ]
 
 
-def make_model(U: float = 2.0, eta_amp: float = 1.0, **over) -> Model:
+def make_model(U: float = 2.0, eta_amp: float = 1.0, U_band=(0.0, 0.0), **over) -> Model:
     p = dict(RAGHU2)
     p.update(over)
-    return Model(p["t1"], p["t2"], p["t3"], p["t4"], p["mu"], eta_amp, U)
+    return Model(p["t1"], p["t2"], p["t3"], p["t4"], p["mu"], eta_amp, U, (ctypes.c_double * 2)(*U_band))
 
 
 def build(force: bool = False) -> str:
@@ -88,10 +89,11 @@ def lib():
             L.ffeo_omega_batch.restype = ctypes.c_int
             L.ffeo_band_grid.argtypes = [mp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
             L.ffeo_band_grid.restype = None
-            L.ffeo_omega_given.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp] + [ctypes.c_double] * 6 + [dp, dp]
+            L.ffeo_omega_given.argtypes = ([ctypes.c_int, ctypes.c_int, dp, dp] + [ctypes.c_double] * 2 + [dp]
+                                           + [ctypes.c_double] * 3 + [dp, dp])
             L.ffeo_omega_given.restype = None
-            L.ffeo_omega_given_batch.argtypes = ([ctypes.c_int, ctypes.c_int, dp, dp] + [ctypes.c_double] * 3
-                                                 + [ctypes.c_int64] + [dp] * 5 + [ctypes.c_int])
+            L.ffeo_omega_given_batch.argtypes = ([ctypes.c_int, ctypes.c_int, dp, dp] + [ctypes.c_double] * 2
+                                                 + [dp, ctypes.c_int64] + [dp] * 5 + [ctypes.c_int])
             L.ffeo_omega_given_batch.restype = ctypes.c_int
             L.ffeo_chi_given.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp] + [ctypes.c_double] * 3 + [dp]
             L.ffeo_chi_given.restype = None

@@ -45,7 +45,14 @@ typedef struct {
   double t1, t2, t3, t4, mu; /* hopping parameters and chemical potential */
   double eta_amp;            /* amplitude of the s+- form factor          */
   double U;                  /* pairing strength: term +Delta^2/U per k    */
+  double U_band[2];          /* per-band coupling V_eps of Sec. 2 (read as
+                                U_eps): > 0 replaces U in band eps's term  */
 } ffeo_model;
+
+/* The coupling of band b: its own U_eps where one is given, else U. */
+static double band_U(const ffeo_model* m, int b) {
+  return m->U_band[b] > 0.0 ? m->U_band[b] : m->U;
+}
 
 /* Neumaier (improved Kahan-Babuska) running sum. */
 typedef struct {
@@ -116,7 +123,7 @@ void ffeo_omega(const ffeo_model* m, int N, double qx, double qy, double h,
         double e_dn = e_mkq[b] - m->mu + h;
         double ep, em;
         ffeo_quasiparticle(e_up, e_dn, delta * eta, &ep, &em);
-        double term = ffeo_F(ep, T) + ffeo_F(em, T) + e_dn + delta * delta / m->U;
+        double term = ffeo_F(ep, T) + ffeo_F(em, T) + e_dn + delta * delta / band_U(m, b);
         nsum_add(&tot, term);
         nsum_add(&band[b], term);
       }
@@ -132,9 +139,10 @@ void ffeo_omega(const ffeo_model* m, int N, double qx, double qy, double h,
 /* Eq. freeene for a model of nb bands whose band energies are given:
  * e_up[(j*N + i)*nb + b] = E_b(k + Q/2), e_dn[...] = E_b(-k + Q/2) for
  * k = 2 pi (i, j)/N (the three-band model of App. B, whose 3x3 hopping matrix
- * the caller diagonalises).  omega_band (may be NULL) receives Omega_b. */
+ * the caller diagonalises); U[b] is band b's coupling.  omega_band (may be
+ * NULL) receives Omega_b. */
 void ffeo_omega_given(int nb, int N, const double* e_up, const double* e_dn,
-                      double eta_amp, double mu, double U, double h, double T,
+                      double eta_amp, double mu, const double* U, double h, double T,
                       double delta, double* omega, double* omega_band) {
   nsum tot = {0.0, 0.0};
   nsum band[8];
@@ -151,7 +159,7 @@ void ffeo_omega_given(int nb, int N, const double* e_up, const double* e_dn,
         double e_d = e_dn[base + b] - mu + h;
         double ep, em;
         ffeo_quasiparticle(e_u, e_d, delta * eta, &ep, &em);
-        double term = ffeo_F(ep, T) + ffeo_F(em, T) + e_d + delta * delta / U;
+        double term = ffeo_F(ep, T) + ffeo_F(em, T) + e_d + delta * delta / U[b];
         nsum_add(&tot, term);
         nsum_add(&band[b], term);
       }
@@ -165,7 +173,7 @@ void ffeo_omega_given(int nb, int N, const double* e_up, const double* e_dn,
 /* Many (h, T, Delta) points on one set of given band energies, OpenMP over
  * points; omega_band (may be NULL) is [n][nb].  Returns the threads used. */
 int ffeo_omega_given_batch(int nb, int N, const double* e_up, const double* e_dn,
-                           double eta_amp, double mu, double U, int64_t n,
+                           double eta_amp, double mu, const double* U, int64_t n,
                            const double* h, const double* T, const double* delta,
                            double* omega, double* omega_band, int nthreads) {
   int used = 1;

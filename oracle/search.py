@@ -75,11 +75,18 @@ def golden_section(f: Callable[[float], float], lo: float, hi: float, n_steps: i
     return best[0], best[1], seen
 
 
-def golden_section_batch(evaluate: Callable[[np.ndarray], np.ndarray], lo, hi, n_steps: int):
+def golden_section_batch(evaluate: Callable[[np.ndarray], np.ndarray], lo, hi, n_steps: int,
+                         trace: bool = False):
     """Lockstep golden-section search for many independent points.
 
     ``evaluate(deltas[n]) -> omegas[n]`` evaluates each point at its own Delta.
-    Returns (delta_star[n], omega_star[n], omega_lo[n])."""
+    Returns (delta_star[n], omega_star[n], omega_lo[n]).  With ``trace`` it also
+    returns a dict of the search's history: ``x`` and ``f`` [3 + n_steps, n], the
+    evaluated Delta and Omega in order (lo, x1, x2, then one per reduction);
+    ``a``, ``b`` and ``margin`` [n_steps, n], the bracket before each reduction
+    and |Omega(x1) - Omega(x2)| of the comparison that decides it.  Up to the
+    first comparison whose margin is below twice a per-value error bound, any
+    evaluation within that bound of these values takes the same decisions."""
     lo = np.asarray(lo, dtype=np.float64)
     hi = np.asarray(hi, dtype=np.float64)
     a, b = lo.copy(), hi.copy()
@@ -89,6 +96,7 @@ def golden_section_batch(evaluate: Callable[[np.ndarray], np.ndarray], lo, hi, n
     f1 = evaluate(x1.copy())
     f2 = evaluate(x2.copy())
     best_x, best_f = lo.copy(), f0.copy()
+    tr = dict(x=[lo.copy(), x1.copy(), x2.copy()], f=[f0, f1, f2], a=[], b=[], margin=[])
 
     def take(x, fx):
         better = (fx < best_f) | ((fx == best_f) & (x < best_x))
@@ -98,6 +106,9 @@ def golden_section_batch(evaluate: Callable[[np.ndarray], np.ndarray], lo, hi, n
     take(x1, f1)
     take(x2, f2)
     for _ in range(n_steps):
+        tr["a"].append(a)
+        tr["b"].append(b)
+        tr["margin"].append(np.abs(f1 - f2))
         left = f1 <= f2                      # keep [a, x2], else keep [x1, b]
         a, b = np.where(left, a, x1), np.where(left, x2, b)
         newx = np.where(left, a + (1.0 - PHI) * (b - a), a + PHI * (b - a))
@@ -105,7 +116,13 @@ def golden_section_batch(evaluate: Callable[[np.ndarray], np.ndarray], lo, hi, n
         x1, f1, x2, f2 = (np.where(left, newx, x2), np.where(left, fn, f2),
                           np.where(left, x1, newx), np.where(left, f1, fn))
         take(newx, fn)
-    return best_x, best_f, f0
+        tr["x"].append(newx)
+        tr["f"].append(fn)
+    if not trace:
+        return best_x, best_f, f0
+    shape = (0,) + lo.shape
+    tr = {k: (np.stack(v) if v else np.zeros(shape)) for k, v in tr.items()}
+    return best_x, best_f, f0, tr
 
 
 def phase_label(omega_star: Sequence[float], omega_zero: Sequence[float],

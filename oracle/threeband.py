@@ -66,8 +66,9 @@ def band_grids(N: int, qx: float, qy: float, p=DAGHOFER3):
 
 
 def omega_batch(N: int, qx: float, qy: float, h, T, delta, U: float, eta_amp: float = 1.0, p=DAGHOFER3,
-                bands: bool = False, nthreads: int = 0):
-    """Omega of the three-band model at many (h, T, Delta) of one (N, Q).
+                bands: bool = False, nthreads: int = 0, U_band=(0.0, 0.0, 0.0)):
+    """Omega of the three-band model at many (h, T, Delta) of one (N, Q); U_band[b] > 0 is band
+    b's own coupling (else U).
 
     Returns (omega[n], omega_band[n, 3] or None, threads_used)."""
     e_up, e_dn = band_grids(N, qx, qy, p)
@@ -78,7 +79,8 @@ def omega_batch(N: int, qx: float, qy: float, h, T, delta, U: float, eta_amp: fl
     om = np.zeros(n)
     ob = np.zeros((n, 3)) if bands else None
     L = lib()
-    used = L.ffeo_omega_given_batch(3, N, _dp(e_up), _dp(e_dn), eta_amp, p["mu"], U, n, _dp(h), _dp(T),
+    Ub = np.array([u if u > 0.0 else U for u in U_band], dtype=np.float64)
+    used = L.ffeo_omega_given_batch(3, N, _dp(e_up), _dp(e_dn), eta_amp, p["mu"], _dp(Ub), n, _dp(h), _dp(T),
                                     _dp(delta), _dp(om), _dp(ob) if bands else None, int(nthreads))
     return om, ob, used
 

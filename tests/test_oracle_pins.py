@@ -337,3 +337,38 @@ def test_weak_coupling_is_normal_state():
     i, d, _, om = search.minimize_grid(m, 64, 0, 0, 0, 0.005, 0.0, 0.2, 201)
     assert i == 0 and d == 0.0
     assert np.all(np.diff(om[:20]) > 0)
+
+
+def test_per_band_coupling_gap_equations():
+    """Each band with its own coupling U_eps (Sec. 2, V_eps per band): at Q = 0, h = 0 the minimum
+    of the band's own Omega_eps(Delta) solves that band's gap equation
+    1 = U_eps/(2 N^2) sum_k eta^2 tanh(R/2T) / R (Brent's method), and the two bands' minima differ.
+    The coupling enters only through Delta^2/U_eps: Omega_eps(U_a) - Omega_eps(U_b) = N^2 Delta^2 (1/U_a - 1/U_b)."""
+    from scipy.optimize import brentq
+
+    U0, Ub, T, N = 4.0, (7.0, 3.0), 0.005, 48
+    p = oracle.RAGHU2
+    m = oracle.make_model(U=U0, U_band=Ub)
+    ks = TWO_PI * np.arange(N) / N
+    KX, KY = np.meshgrid(ks, ks)
+    eta2 = (np.cos(KX) * np.cos(KY)).ravel() ** 2
+    ev = np.array([bands_eigvalsh(p, kx, ky) for kx, ky in zip(KX.ravel(), KY.ravel())])
+    roots = []
+    for b in range(2):
+        xi = ev[:, b] - p["mu"]
+
+        def gap_eq(d, xi=xi, U=Ub[b]):
+            R = np.sqrt(xi**2 + d * d * eta2)
+            return U / (2 * N * N) * np.sum(eta2 * np.tanh(R / (2 * T)) / R) - 1.0
+
+        root = brentq(gap_eq, 1e-3, 0.3, xtol=1e-14)
+        d_star, _, _ = search.golden_section(lambda d, b=b: oracle.omega(m, N, 0, 0, 0, T, d, bands=True)[1][b],
+                                             0.02, 0.3, 60)
+        assert abs(d_star - root) < 2e-6, (b, d_star, root)
+        roots.append(root)
+    assert abs(roots[0] - roots[1]) > 0.01
+    _, plain = oracle.omega(oracle.make_model(U=U0), N, 0.1, 0.0, 0.03, T, 0.07, bands=True)
+    _, per = oracle.omega(m, N, 0.1, 0.0, 0.03, T, 0.07, bands=True)
+    for b in range(2):
+        want = N * N * 0.07**2 * (1 / Ub[b] - 1 / U0)
+        assert abs((per[b] - plain[b]) - want) <= 1e-9 * abs(plain[b])

@@ -84,3 +84,28 @@ def test_phase_label_cases(ws, w0, qz, label, q):
 def test_phase_label_needs_q_zero():
     with pytest.raises(ValueError):
         search.phase_label([-1.0], [-1.0], [False])
+
+
+def test_golden_trace_of_a_parabola():
+    """On f = (x - c)^2 the traced history is the scalar search's: the same evaluated points in
+    order, brackets that shrink by phi and always contain c, and decision margins
+    |f(x1) - f(x2)| = |x1 - x2| |x1 + x2 - 2c| of the bracket's interior points."""
+    c, n = 0.0731, 12
+    xb, fb, f0, tr = search.golden_section_batch(lambda d: (d - c) ** 2, np.zeros(1), np.full(1, 0.2), n,
+                                                 trace=True)
+    x, fx, seen = search.golden_section(lambda d: (d - c) ** 2, 0.0, 0.2, n)
+    assert xb[0] == x and [s[0] for s in seen] == list(tr["x"][:, 0])
+    assert tr["x"].shape == (n + 3, 1) and tr["margin"].shape == (n, 1)
+    w = tr["b"][:, 0] - tr["a"][:, 0]
+    np.testing.assert_allclose(w[1:] / w[:-1], search.PHI, rtol=1e-9)
+    assert np.all((tr["a"][:, 0] <= c) & (c <= tr["b"][:, 0]))
+    for k in range(n):
+        a, b = tr["a"][k, 0], tr["b"][k, 0]
+        x1, x2 = a + (1 - search.PHI) * (b - a), a + search.PHI * (b - a)
+        assert math.isclose(tr["margin"][k, 0], abs(x1 - x2) * abs(x1 + x2 - 2 * c), rel_tol=1e-6, abs_tol=1e-18)
+
+
+def test_golden_trace_flags_a_flat_function():
+    """A constant function makes every decision a tie: margin 0."""
+    _, _, _, tr = search.golden_section_batch(lambda d: np.ones_like(d), np.zeros(3), np.full(3, 0.2), 8, trace=True)
+    assert np.all(tr["margin"] == 0.0)

@@ -95,8 +95,9 @@ def test_zero_temperature_limit_is_ground_state():
 
 
 def test_given_energies_path_matches_the_two_band_closed_form():
-    """The nb-band k-sum fed with the two-band energies reproduces the two-band oracle."""
-    m = oracle.make_model(U=2.0)
+    """The nb-band k-sum fed with the two-band energies reproduces the two-band oracle, each band
+    with its own coupling."""
+    m = oracle.make_model(U=2.0, U_band=(1.5, 3.0))
     N, qx, qy, h, T, d = 12, 0.35, 0.1, 0.05, 0.01, 0.12
     e_up = np.ascontiguousarray(oracle.band_grid(m, N, qx, qy))
     k = 2 * math.pi * np.arange(N) / N
@@ -107,7 +108,8 @@ def test_given_energies_path_matches_the_two_band_closed_form():
     out = np.zeros(1)
     ob = np.zeros(2)
     L = oracle.lib()
-    L.ffeo_omega_given(2, N, oracle._dp(e_up), oracle._dp(e_dn), 1.0, m.mu, m.U, h, T, d,
+    Ub = np.array([1.5, 3.0])
+    L.ffeo_omega_given(2, N, oracle._dp(e_up), oracle._dp(e_dn), 1.0, m.mu, oracle._dp(Ub), h, T, d,
                        oracle._dp(out), oracle._dp(ob))
     ref, rb = oracle.omega(m, N, qx, qy, h, T, d, bands=True)
     assert abs(out[0] - ref) <= 1e-12 * abs(ref)
