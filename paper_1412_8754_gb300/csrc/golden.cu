@@ -28,6 +28,13 @@ __device__ __forceinline__ void golden_take(GoldenState& s, double x, double f, 
   }
 }
 
+// Interior points a + w (b - a), rounded step by step (no fused multiply-add),
+// so that every line's bracket sequence is the one the textbook formula gives
+// in IEEE double: the same Delta values as any other plain evaluation of it.
+__device__ __forceinline__ double golden_point(double a, double b, double w) {
+  return __dadd_rn(a, __dmul_rn(w, __dsub_rn(b, a)));
+}
+
 __device__ __forceinline__ void set_delta(double* delta, float* d2f, int64_t e, double x) {
   delta[e] = x;
   d2f[e] = (float)(x * x);
@@ -63,8 +70,8 @@ __global__ void golden_kernel(int mode, const Line* __restrict__ lines, int n_li
       s.a = s.lo;
       s.b = s.hi;
       if (!(s.wide > 0.0)) s.wide = kWideRel * (s.hi - s.lo);
-      s.x1 = s.a + (1.0 - kPhi) * (s.b - s.a);
-      s.x2 = s.a + kPhi * (s.b - s.a);
+      s.x1 = golden_point(s.a, s.b, 1.0 - kPhi);
+      s.x2 = golden_point(s.a, s.b, kPhi);
       s.side = 0;
       set_delta(delta, d2f, e, s.x0);
       break;
@@ -116,7 +123,7 @@ __global__ void golden_kernel(int mode, const Line* __restrict__ lines, int n_li
         s.x2 = s.x1;
         s.f2 = s.f1;
         s.eb2 = s.eb1;
-        s.x1 = s.a + (1.0 - kPhi) * (s.b - s.a);
+        s.x1 = golden_point(s.a, s.b, 1.0 - kPhi);
         s.side = 0;
         set_delta(delta, d2f, e, s.x1);
       } else {  // keep [x1, b]
@@ -124,7 +131,7 @@ __global__ void golden_kernel(int mode, const Line* __restrict__ lines, int n_li
         s.x1 = s.x2;
         s.f1 = s.f2;
         s.eb1 = s.eb2;
-        s.x2 = s.a + kPhi * (s.b - s.a);
+        s.x2 = golden_point(s.a, s.b, kPhi);
         s.side = 1;
         set_delta(delta, d2f, e, s.x2);
       }

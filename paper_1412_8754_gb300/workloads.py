@@ -15,6 +15,11 @@ performance evaluation).  The workloads below keep that shape and scale it up:
   surrogate_set (q, h, T, Delta) samples for the surrogate (default_rng(1235))
   phase_diagram N=2048, 64 h in [0, 0.15] x 64 T in [0.001, 0.03], 64 q,
                 golden-section search with 24 reductions on [0, 0.2]
+  ff_scan       a scan that reaches the FF phase: the same hoppings with
+                mu = 3.8 (small hole pockets around (pi, pi), where
+                eta = cos kx cos ky is close to 1) and U = 5; 31 q in
+                [0, 0.3] along x, 11 h in [0.03, 0.05], T in {0.002, 0.003},
+                41 Delta in [0, 0.1]: BCS, FF and normal points
 """
 from __future__ import annotations
 
@@ -30,6 +35,14 @@ SMALL_BCS = dict(N=64, qx=[0.0], qy=[0.0], h=[0.0], T=[0.005], lo=0.0, hi=0.2, n
 def fflo_scan(N=1024, n_q=64, n_h=32, n_delta=256, T=0.002):
     return dict(N=N, qx=np.linspace(0.0, 0.2 * math.pi, n_q), qy=np.zeros(n_q),
                 h=np.linspace(0.0, 0.15, n_h), T=np.array([T]), lo=0.0, hi=0.2, n=n_delta)
+
+
+FF_MODEL = dict(mu=3.8, U=5.0)
+
+
+def ff_scan(N=64, n_q=31, n_h=11, n_delta=41, T=(0.002, 0.003)):
+    return dict(N=N, qx=np.linspace(0.0, 0.3, n_q), qy=np.zeros(n_q), h=np.linspace(0.03, 0.05, n_h),
+                T=np.array(T, dtype=float), lo=0.0, hi=0.1, n=n_delta)
 
 
 def threeband_scan(N=1024, n_q=16, n_h=16, n_delta=64, T=0.001):

@@ -335,32 +335,6 @@ def test_minimize_bands_golden_vs_oracle(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_golden_minimize_vs_oracle(prec):
-    N, U, steps = 32, 4.0, 24
-    rng = np.random.default_rng(17)
-    n = 40
-    qx = rng.uniform(0, 0.5, n)
-    qx[:4] = 0.0
-    h = rng.uniform(0, 0.12, n)
-    T = rng.uniform(0.002, 0.03, n)
-    m = oracle.make_model(U=U)
-    xb, fb, f0 = oracle_golden(m, N, qx, 0.0, h, T, 0.0, 0.2, steps)
-    with ffe.Context(prec=prec, U=U) as ctx:
-        res = ctx.minimize(ffe.params(N, qx, 0.0, h, T, 0.0, 0.2, steps), search=ffe.FFE_SEARCH_GOLDEN)
-    assert per_site(res["omega_lo"], f0, N).max() <= TOL[prec]
-    # the GPU's minimum is a point the oracle agrees with ...
-    at_gpu, _, _ = oracle.omega_batch(m, N, qx, 0.0, h, T, res["delta_star"])
-    assert per_site(res["omega_star"], at_gpu, N).max() <= TOL[prec]
-    # ... and as low as the oracle's own minimum within the comparison noise
-    slack = {ffe.FFE_FP64: 1e-11, ffe.FFE_FP32C: 1e-9}[prec]
-    assert np.all((at_gpu - fb) / N**2 <= slack)
-    bracket = 0.2 * search.PHI ** (steps + 1)
-    close = np.abs(res["delta_star"] - xb) <= 20 * bracket
-    assert close.mean() >= 0.9, np.abs(res["delta_star"] - xb)
-    assert np.array_equal(res["flags"] & ffe.FFE_FLAG_LOWER != 0, xb == 0.0)
-
-
-@pytest.mark.parametrize("prec", PRECS)
 def test_golden_phase_scan_vs_oracle(prec):
     """Golden phase scan: 5 q x (3 h x 2 T) at N=32, U=4; labels equal to the oracle's."""
     N, U, steps = 32, 4.0, 20
@@ -519,3 +493,34 @@ def test_autotune_keeps_results():
     assert shape["kpt"] in (2, 4, 8) and shape["block"] in (128, 256)
     assert np.array_equal(a["idx_star"], b["idx_star"])
     assert per_site(ga, gb, np.repeat(w["N"], w["n"])).max() <= 1e-8
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_per_band_coupling(prec):
+    """Each band with its own coupling U_eps (U_band = (9, 3)): Omega and Omega_eps at random points,
+    and the per-band grid minimisation at Q = 0 and small q, h against the oracle, index for index;
+    the two bands' minima differ."""
+    Ub = (9.0, 3.0)
+    w = workloads.random_points(60, seed=31)
+    m = oracle.make_model(U=4.0, U_band=Ub)
+    ref, ref_b, _ = oracle.omega_batch(m, w["N"], w["qx"], w["qy"], w["h"], w["T"], w["delta"], bands=True)
+    n, N = 41, 32
+    qx = np.array([0.0, 0.0, 0.1, 0.2])
+    h = np.array([0.0, 0.02, 0.01, 0.03])
+    T = np.array([0.003, 0.005, 0.004, 0.002])
+    grid = np.linspace(0.0, 0.3, n)
+    with ffe.Context(prec=prec, U=4.0, U_band=Ub) as ctx:
+        got, got_b = ctx.omega(ffe.points(w["N"], w["qx"], w["qy"], w["h"], w["T"], w["delta"]), bands=True)
+        res = ctx.minimize_bands(ffe.params(N, qx, 0.0, h, T, 0.0, 0.3, n))
+    assert per_site(got, ref, w["N"]).max() <= TOL[prec]
+    for b in range(2):
+        assert per_site(got_b[:, b], ref_b[:, b], w["N"]).max() <= TOL[prec]
+    differ = 0
+    for i in range(len(qx)):
+        _, ob, _ = oracle.omega_batch(m, N, qx[i], 0.0, h[i], T[i], grid, bands=True)
+        idx = [search.grid_argmin(ob[:, b]) for b in range(2)]
+        for b in range(2):
+            assert res[i, b]["idx_star"] == idx[b], (i, b, res[i, b]["idx_star"], idx[b])
+            assert per_site(res[i, b]["omega_star"], ob[idx[b], b], N) <= TOL[prec]
+        differ += idx[0] != idx[1] and min(idx) > 0
+    assert differ >= 2
