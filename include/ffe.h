@@ -72,7 +72,10 @@ typedef enum { FFE_MODEL_RAGHU2 = 0, FFE_MODEL_DAGHOFER3 = 1 } ffe_model_kind;
  *   t3=0.08375, t4=-0.03, t5=0.15, t6=0.15, t7=-0.12, t8=0.06, t9=0,
  *   t10=-0.024, t11=-0.01, t12=0.0275, eps0=0.75; n = 4 at mu=0.4748).  Its
  *   three bands are the eigenvalues of the 3x3 hopping matrix, ascending;
- *   every band pairs intra-band as in the two-band model. */
+ *   every band pairs intra-band as in the two-band model.
+ * Each band carries the pairing term + Delta^2/U_eps per k-point with its
+ * own coupling U_eps = U_band[eps] (U where that is 0); Sec. 2 writes one
+ * V_eps per band and minimises every band separately (ffe_minimize_bands). */
 typedef struct {
   int32_t kind;      /* ffe_model_kind                                         */
   int32_t prec;      /* ffe_precision used by every call on the context        */
@@ -81,6 +84,10 @@ typedef struct {
   double U;          /* pairing strength (> 0): + Delta^2/U per k and band     */
   double eta_amp;    /* s+- form factor eta(k) = eta_amp cos kx cos ky (Sec. 1) */
   double t5, t6, t7, t8, t9, t10, t11, t12, eps0;  /* FFE_MODEL_DAGHOFER3 only  */
+  double U_band[3];  /* per-band coupling U_eps (the V_eps of Sec. 2, one per
+                        band, bands ascending): > 0 replaces U in that band's
+                        + Delta^2/U_eps term; 0 = U.  Unused entries (the
+                        third of the two-band model) must be 0            */
 } ffe_model;
 
 /* One free-energy evaluation point. */
@@ -382,18 +389,23 @@ FFE_API ffe_status ffe_pair_susceptibility(ffe_context* ctx, int32_t N, int32_t 
  * (a cudaMalloc there fails or evicts), or a latency-critical loop in which
  * cudaMalloc/cudaFree would synchronise the device and stall other streams.
  * Computes Omega at n points (h[i], T[i], delta[i]) of one lattice N and one
- * pair momentum Q = (qx, qy) with the precision of m->prec, exactly as
- * ffe_omega does, but the caller passes DEVICE arrays h, T, delta (n doubles
- * each, T > 0, not checked) and omega (n doubles, written), and every
- * intermediate lives in one fixed 4 MiB __device__ array of the library that
- * each GPU loading the library holds until exit.  Limits of that array:
+ * pair momentum Q = (qx, qy) with the precision of m->prec, within the same
+ * per-site tolerance as ffe_omega (its own k-chunking, so not always the same
+ * bits).  The caller passes DEVICE arrays h, T, delta (n doubles each) and
+ * omega (n doubles, written); every intermediate, the job table included,
+ * is written by the call's kernels into one fixed 4 MiB __device__ array of
+ * the library that each GPU loading the library holds until exit: the call
+ * makes no host-to-device copy and allocates nothing.  Limits of that array:
  * N even in [2, 2048] and 1 <= n <= 512; beyond them the call returns
- * FFE_EINVAL before any device work.  The first call on a device looks up
- * the array's device address (once per device, with that device current);
- * make that first call before any stream capture.  The call allocates
- * nothing and returns once the work is queued on `stream`.  All calls share
- * the array, which keeps the last call's contents (counters are cleared at
- * the start of every call): calls that overlap on the GPU race and must be
+ * FFE_EINVAL before any device work.  The inputs are checked on the device:
+ * a point with T <= 0 or a non-finite h, T or delta gets omega = NaN (the
+ * other points are computed normally), and if a kernel of the call detects
+ * an internal inconsistency every omega of the call is NaN.  The first call
+ * on a device looks up the array's device address (once per device, with
+ * that device current); make that first call before any stream capture.  The
+ * call returns once the work is queued on `stream`.  All calls share the
+ * array, which keeps the last call's contents (counters are cleared at the
+ * start of every call): calls that overlap on the GPU race and must be
  * serialised by the caller. */
 FFE_API ffe_status ffe_omega_noalloc(const ffe_model* m, int32_t N, double qx, double qy,
                                      const double* h, const double* T, const double* delta,

@@ -966,6 +966,10 @@ ffe_status ffe_create(const ffe_model* m, ffe_context** out) {
     for (double x : {m->t5, m->t6, m->t7, m->t8, m->t9, m->t10, m->t11, m->t12, m->eps0})
       if (!std::isfinite(x)) return FFE_EINVAL;
   }
+  const int nb = m->kind == FFE_MODEL_DAGHOFER3 ? 3 : 2;
+  for (int b = 0; b < 3; ++b)
+    if (!std::isfinite(m->U_band[b]) || m->U_band[b] < 0.0 || (b >= nb && m->U_band[b] != 0.0))
+      return FFE_EINVAL;
   ffe_context* ctx = new (std::nothrow) ffe_context();
   if (!ctx) return FFE_ENOMEM;
   ctx->model = *m;
@@ -990,6 +994,10 @@ ffe_status ffe_create(const ffe_model* m, ffe_context** out) {
     mp.t11 = m->t11;
     mp.t12 = m->t12;
     mp.eps0 = m->eps0;
+  }
+  for (int b = 0; b < 3; ++b) {
+    mp.Ub[b] = m->U_band[b] > 0.0 ? m->U_band[b] : m->U;
+    if (b < mp.nbands && mp.Ub[b] != m->U) mp.per_band_u = 1;
   }
   ctx->mp = mp;
   cudaError_t e = cudaGetDevice(&ctx->device);

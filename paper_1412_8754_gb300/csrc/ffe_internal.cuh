@@ -46,7 +46,22 @@ struct ModelParams {
   int32_t kind;    // FFE_MODEL_RAGHU2 (0) or FFE_MODEL_DAGHOFER3 (1)
   int32_t nbands;  // 2 or 3
   double t5, t6, t7, t8, t9, t10, t11, t12, eps0;  // three-band model only
+  // per-band couplings (Sec. 2: V_eps per band); used when per_band_u != 0,
+  // else every band has U
+  double Ub[3];
+  int32_t per_band_u;
+  int32_t pad;
 };
+
+// The pairing term of Eq. freeene summed over the k-points and over the bands
+// of an output (all of them, or band band_only - 1): N^2 Delta^2 sum_b 1/U_b.
+__host__ __device__ __forceinline__ double pairing_term(const ModelParams& m, int band_only, double n2, double dl) {
+  if (!m.per_band_u) return (band_only ? 1.0 : (double)m.nbands) * n2 * dl * dl / m.U;
+  if (band_only) return n2 * dl * dl / m.Ub[band_only - 1];
+  double t = 0.0;
+  for (int b = 0; b < m.nbands; ++b) t += n2 * dl * dl / m.Ub[b];
+  return t;
+}
 
 // One group of outputs sharing (N, Q): the unit that shares per-k band work.
 struct GroupDesc {

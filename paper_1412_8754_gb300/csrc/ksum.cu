@@ -15,7 +15,7 @@
 // them as one partial per output and the last warp to finish a segment (a
 // fixed output range) adds the partials of all its k-chunks in a fixed order
 // (deterministic) and writes
-//   Omega = M + V + n_bands N^2 Delta^2 / U
+//   Omega = M + V + N^2 Delta^2 sum_bands 1/U_band
 // together with an error bound for FP32 evaluation.  This replaces the
 // paper's per-block partial sums + second reduction kernel + host-side
 // remainder (Sec. 3, Alg. 2 and the three steps around it) by one launch.
@@ -503,7 +503,7 @@ __device__ void finalize_segment(const KsumArgs& a, const Segment& sg, const Gro
     const double M = a.M[g.h_off + ht.h_idx];
     const int64_t out = g.out_off + o;
     a.V[out] = V;
-    a.omega[out] = M + V + (g.band_only ? 1.0 : (double)a.m.nbands) * n2 * dl * dl / a.m.U;
+    a.omega[out] = M + V + pairing_term(a.m, g.band_only, n2, dl);
     a.ebound[out] = a.eb_rel * fabs(V) + a.eb_abs * n2 * ht.T;
   }
 }

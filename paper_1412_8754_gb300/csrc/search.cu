@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256) rescore_kernel(const RescoreArgs a) {
       double V = 0.0;
       for (int i = 0; i < a.max_chunks; ++i) V += __ldcg(a.partials + (int64_t)r * a.max_chunks + i);
       const double n2 = (double)g.N * (double)g.N;
-      const double om = a.M[g.h_off + ht.h_idx] + V + (g.band_only ? 1.0 : (double)a.m.nbands) * n2 * d2 / a.m.U;
+      const double om = a.M[g.h_off + ht.h_idx] + V + pairing_term(a.m, g.band_only, n2, q.delta);
       if (q.kind == 0) {
         a.omega[q.dst] = om;
         a.ebound[q.dst] = 0.0;

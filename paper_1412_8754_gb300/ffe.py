@@ -49,7 +49,8 @@ class ffe_model(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("prec", ctypes.c_int32), ("t1", ctypes.c_double),
                 ("t2", ctypes.c_double), ("t3", ctypes.c_double), ("t4", ctypes.c_double),
                 ("mu", ctypes.c_double), ("U", ctypes.c_double), ("eta_amp", ctypes.c_double)] + [
-                    (f"t{i}", ctypes.c_double) for i in range(5, 13)] + [("eps0", ctypes.c_double)]
+                    (f"t{i}", ctypes.c_double) for i in range(5, 13)] + [("eps0", ctypes.c_double),
+                                                                         ("U_band", ctypes.c_double * 3)]
 
 
 class ffe_scan(ctypes.Structure):
@@ -246,13 +247,14 @@ def _check(ctx, st):
 
 
 # ------------------------------------------------------------ entry points
-def ffe_create(U=2.0, eta_amp=1.0, prec=FFE_FP32C, model="raghu2", **params):
+def ffe_create(U=2.0, eta_amp=1.0, prec=FFE_FP32C, model="raghu2", U_band=None, **params):
     """A context for `model` ("raghu2": App. A, "daghofer3": App. B) with its printed
-    parameters, any of which `params` overrides."""
+    parameters, any of which `params` overrides; U_band: per-band couplings (0 = U)."""
     kind, _, defaults = MODELS[model]
     p = dict(defaults)
     p.update(params)
-    m = ffe_model(kind=kind, prec=prec, U=U, eta_amp=eta_amp, **p)
+    ub = list(U_band or ()) + [0.0] * (3 - len(U_band or ()))
+    m = ffe_model(kind=kind, prec=prec, U=U, eta_amp=eta_amp, U_band=(ctypes.c_double * 3)(*ub), **p)
     h = _VP()
     st = lib().ffe_create(ctypes.byref(m), ctypes.byref(h))
     if st != FFE_OK:
@@ -418,9 +420,9 @@ class Plan:
 class Context:
     """Owning wrapper: ffe_create on construction, ffe_destroy on close()."""
 
-    def __init__(self, prec=FFE_FP32C, U=2.0, eta_amp=1.0, model="raghu2", **params):
+    def __init__(self, prec=FFE_FP32C, U=2.0, eta_amp=1.0, model="raghu2", U_band=None, **params):
         self.nbands = MODELS[model][1]
-        self.handle = ffe_create(prec=prec, U=U, eta_amp=eta_amp, model=model, **params)
+        self.handle = ffe_create(prec=prec, U=U, eta_amp=eta_amp, model=model, U_band=U_band, **params)
 
     def omega(self, points, stream=None, bands=False):
         return ffe_omega(self.handle, points, stream, self.nbands if bands else 0)
