@@ -119,6 +119,8 @@ typedef struct {
 #define FFE_FLAG_EDGE 2       /* argmin at the upper end of the Delta range    */
 #define FFE_FLAG_LOWER 4      /* argmin at Delta = lo                          */
 #define FFE_FLAG_PRUNED 8     /* guided scan: line not evaluated               */
+#define FFE_FLAG_INVALID 32   /* stream-ordered calls: the device reported an
+                                 internal inconsistency; values are NaN       */
 
 typedef struct {
   double delta_star;   /* minimising Delta                                     */
@@ -136,7 +138,9 @@ typedef struct {
 
 /* A phase-diagram scan: every q of the list against every (h, T) pair of the
  * product h-list x T-list (h-major: point p = ih * n_T + iT), all at one N.
- * The q list must contain Q = (0, 0) (it defines the normal/BCS reference). */
+ * Phase labels need Q = (0, 0) in the q list (it defines the normal/BCS
+ * reference); a scan without it gives the per-line minima only (labels and
+ * best_q must then be NULL; see ffe_label_candidates for split q lists). */
 typedef struct {
   int32_t N;
   int32_t n_q;
@@ -205,6 +209,77 @@ FFE_API ffe_status ffe_phase_scan(ffe_context* ctx, const ffe_scan* scan,
                           ffe_result* per_point, int8_t* labels,
                           int32_t* best_q, void* stream);
 
+/* ---- stream-ordered forms: device arrays, no host synchronisation ------
+ * For callers whose inputs and outputs live in device memory (torch tensors
+ * passed by data_ptr(), with torch.cuda.current_stream() as `stream`).  Each
+ * call queues its work on `stream` and returns without waiting for the
+ * device; results are in the caller's DEVICE arrays once `stream` reaches
+ * them (synchronise or record an event as usual).  Descriptions that decide
+ * the shape of the work (lattice sizes, grid lengths, pair momenta, the
+ * ffe_param / ffe_scan structs and their lists) stay HOST memory.  Errors
+ * the device finds cannot be returned: a point with T <= 0 or a non-finite
+ * input gets NaN, and a kernel-side inconsistency sets FFE_FLAG_INVALID with
+ * NaN values (ffe_minimize_async, ffe_phase_scan_async) or NaN in every
+ * output (ffe_omega_async).  The first call of a shape builds and caches a
+ * plan on the context (device allocation and an upload that waits); later
+ * calls of the same shape stage their values in page-locked memory and only
+ * queue copies and kernels.  Calls on one context share its cached plans and
+ * scratch: calls on different streams must be ordered by the caller (one
+ * context per stream otherwise).  The caller's arrays must stay valid until
+ * the stream has passed the call. */
+
+/* Omega (Eq. freeene) at n points (h[i], T[i], delta[i]) of one lattice N and
+ * pair momentum Q: h, T, delta are DEVICE arrays of n doubles; omega (n
+ * doubles) and omega_band (NULL or [n][nb], nb = 2 or 3 bands ascending) are
+ * DEVICE outputs.  Every point is its own (h, T) entry (a distinct h costs one
+ * normal-state sum; for grids of parameters prefer ffe_minimize_async).  The
+ * job table is written on the device; the context's scratch grows to the
+ * largest call (growing waits for the device).  n in [1, 2^24]. */
+FFE_API ffe_status ffe_omega_async(ffe_context* ctx, int32_t N, double qx, double qy, const double* h,
+                                   const double* T, const double* delta, int64_t n, double* omega,
+                                   double* omega_band, void* stream);
+
+/* ffe_minimize with the results left on the device: out[n] (DEVICE) as in
+ * ffe_minimize; omega_grid (GRID only; NULL or DEVICE, sum_i ps[i].n doubles)
+ * the Omega grids.  ps is host memory. */
+FFE_API ffe_status ffe_minimize_async(ffe_context* ctx, int32_t search, const ffe_param* ps, int64_t n,
+                                      ffe_result* out, double* omega_grid, void* stream);
+
+/* ffe_phase_scan with the results left on the device: per_point, labels and
+ * best_q (each NULL or DEVICE, sizes as in ffe_phase_scan).  *scan and its
+ * lists are host memory. */
+FFE_API ffe_status ffe_phase_scan_async(ffe_context* ctx, const ffe_scan* scan, ffe_result* per_point,
+                                        int8_t* labels, int32_t* best_q, void* stream);
+
+/* ---- phase labels over q lists split across ranks (Alg. 1, outer argmin) --
+ * Host functions (no device work).  A scan's q list may be split across
+ * ranks (one process per GPU); each rank scans its own q (a scan without
+ * Q = (0, 0) gives no labels) and reduces its lines per (h, T) point to one
+ * candidate, then the ranks' candidates are merged.  omega_n[n_pts] is the
+ * normal state Omega(q = 0, Delta = 0) of each point (the omega_lo of the
+ * q = 0 lines, from the rank that scans q = 0); tau = 1e-12 |omega_n| as in
+ * ffe_phase_scan.  A rank's values are those of its own scan: FP32+comp
+ * values within their error bound of a competitor's on another rank are not
+ * re-evaluated in FP64, as the single-process labels are. */
+
+/* Per point, the lowest omega_star among the rank's lines (per_point
+ * [n_q][n_pts], laid out as ffe_phase_scan's) that condense (omega_star <
+ * omega_lo - tau), ties to the lowest global q index; q_global[n_q] maps the
+ * rank's q to the global list.  best_val[n_pts] (+inf where none) and
+ * best_q[n_pts] (the global index, -1 where none). */
+FFE_API ffe_status ffe_label_candidates(const ffe_result* per_point, int32_t n_q, int32_t n_pts,
+                                        const int32_t* q_global, const double* omega_n, double* best_val,
+                                        int32_t* best_q);
+
+/* Labels from the stacked candidates of `world` ranks (best_val, best_q:
+ * [world][n_pts]): the lowest candidate (ties to the lowest global q) wins
+ * when it lies below omega_n - tau, BCS if its q is zero_q (the global index
+ * of Q = (0, 0)), else FFLO; NORMAL otherwise.  labels[n_pts], best_q_out
+ * [n_pts] (-1 for normal), as from ffe_phase_scan. */
+FFE_API ffe_status ffe_merge_candidates(int32_t world, int32_t n_pts, const double* best_val,
+                                        const int32_t* best_q, const double* omega_n, int32_t zero_q,
+                                        int8_t* labels, int32_t* best_q_out);
+
 /* ---- device-resident plans (for repeated execution) --------------------
  * A plan holds the packed job table, device buffers and a captured CUDA
  * graph of one scan.  ffe_plan_execute replays the graph on `stream` without
@@ -216,6 +291,12 @@ FFE_API ffe_status ffe_plan_phase_scan(ffe_context* ctx, const ffe_scan* scan,
 FFE_API ffe_status ffe_plan_execute(ffe_plan* plan, void* stream);
 FFE_API ffe_status ffe_plan_fetch(ffe_plan* plan, ffe_result* per_point,
                           int8_t* labels, int32_t* best_q, void* stream);
+/* The whole Omega(Delta) grid of every line of a grid phase-scan plan after
+ * its last execution: omega_grid[n_q][n_h*n_T][n] (lines as in per_point,
+ * grid index fastest); err_grid (NULL or the same size) the FP32 error bound
+ * of each value (0 where evaluated or re-evaluated in FP64).  Synchronises
+ * `stream`. */
+FFE_API ffe_status ffe_plan_fetch_grid(ffe_plan* plan, double* omega_grid, double* err_grid, void* stream);
 typedef struct {
   double k_evals;          /* k-point evaluations (one k-point, one Delta, one
                               (q,h,T), both bands) of the main k-sum per execution */
@@ -324,24 +405,25 @@ FFE_API ffe_status ffe_surrogate_train(ffe_surrogate* s, const float* x, const f
                                        float* loss_per_epoch, void* stream);
 
 /* Phase scan guided by the surrogate, grid or golden-section search.  The
- * surrogate predicts every (q, h, T) line on a Delta grid (the search grid;
- * 256 points on [lo, hi] for golden); per (h, T) the exact k-sum verifies
- * q = 0 and the q_keep lines of lowest predicted minimum (and, with a
- * margin, the q the surrogate cannot order against the best), each on a window
- * of `window` grid points around its predicted minimum, with Delta = 0 as
- * the reference (with the FP64 re-evaluation and label passes of
- * ffe_phase_scan).  Grid: the window's grid points.  Golden: the window is
- * the initial bracket and takes as many fewer reductions as reach the full
- * search's final bracket width.  An (h, T) point with a line whose verified
- * minimum lies on an inner window edge (or that `margin` flags) is scanned
- * again with all its verified lines over the whole range.  Unverified
- * (pruned) lines are
- * not evaluated: they are reported with idx_star 0 (grid) or -1 (golden),
- * flags FFE_FLAG_LOWER | FFE_FLAG_PRUNED and the Delta = 0 value of the
- * q = 0 line at the same (h, T); a line whose minimum is its Delta = 0 point
- * never decides a label, so pruning changes a label only where the exact
- * minimum of a pruned q would have beaten the kept ones.  Outputs as in
- * ffe_phase_scan. */
+ * surrogate predicts every (q, h, T) line's condensation energy on a Delta
+ * grid (the search grid; 256 points on [lo, hi] for golden) and the exact
+ * k-sum evaluates every line's normal state Omega(q, Delta = lo); per (h, T)
+ * the exact k-sum verifies q = 0 and the q_keep lines of lowest predicted
+ * minimum (exact normal state + predicted condensation energy: on a finite
+ * lattice the normal states of different q differ, and the labels compare
+ * Omega across q), with a margin also every q within the margin of the
+ * lowest, each on a window of `window` grid points around its predicted
+ * minimum, with Delta = 0 as the reference (with the FP64 re-evaluation and
+ * label passes of ffe_phase_scan).  Grid: the window's grid points.  Golden:
+ * the window is the initial bracket and takes as many fewer reductions as
+ * reach the full search's final bracket width.  An (h, T) point with a line
+ * whose verified minimum lies on an inner window edge (or that `margin`
+ * flags) is scanned again with all its verified lines over the whole range.
+ * Unverified (pruned) lines report their exact Delta = lo value, idx_star 0
+ * (grid) or -1 (golden) and flags FFE_FLAG_LOWER | FFE_FLAG_PRUNED; a line
+ * whose minimum is its Delta = 0 point never decides a label, so pruning
+ * changes a label only where the exact minimum of a pruned q would have
+ * beaten the kept ones.  Outputs as in ffe_phase_scan. */
 typedef struct {
   int32_t window;       /* grid points per verified line, 2..n               */
   int32_t q_keep;       /* q values kept per (h, T) besides q = 0            */
@@ -352,12 +434,12 @@ typedef struct {
                            swap within the surrogate's error, as at a
                            first-order transition) is searched over the
                            whole range instead, and beyond q_keep every q
-                           predicted to condense by more than margin with a
-                           predicted minimum within margin of the best one
-                           is kept too; 0: neither                      */
+                           whose predicted minimum is within margin of the
+                           lowest one is kept too; 0: neither             */
 } ffe_guide;
 typedef struct {
-  double k_evals;       /* exact k-point evaluations done                    */
+  double k_evals;       /* exact k-point evaluations done (the normal state
+                           of every line included)                           */
   double k_evals_full;  /* those of the unguided grid scan                   */
   int64_t lines_kept, lines_pruned;
   int64_t fallbacks;    /* kept lines searched over the whole range          */

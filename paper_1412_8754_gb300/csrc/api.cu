@@ -417,22 +417,74 @@ ffe_status plan_alloc(ffe_context* ctx, ffe_plan* p) {
 }
 
 
-// The per-call inputs: Delta values, (h, T) entries, distinct h lists and Q.
-ffe_status plan_upload_params(ffe_context* ctx, ffe_plan* p, cudaStream_t s) {
-  ffe_status st;
+// The per-call inputs -- Delta values, (h, T) entries, distinct h lists, Q,
+// golden-section ranges -- as a list of host-to-device copies.
+static ffe_status plan_param_copies(ffe_context* ctx, ffe_plan* p, std::vector<HostCopy>& out) {
   int64_t e3_rows, kst_rows;
   table_offsets(ctx, p, e3_rows, kst_rows);  // refilled groups: offsets again
   if (e3_rows > p->e3_rows || (p->kst_rows > 0 && kst_rows > p->kst_rows))
     return set_err(ctx, "plan groups outgrew their table buffers"), FFE_EINTERNAL;
-  if ((st = upload(ctx, p->d_delta, p->delta, s)) != FFE_OK) return st;
-  if ((st = upload(ctx, p->d_ht, p->ht, s)) != FFE_OK) return st;
-  if ((st = upload(ctx, p->d_hlist, p->hlist, s)) != FFE_OK) return st;
-  if ((st = upload(ctx, p->d_groups, p->groups, s)) != FFE_OK) return st;
-  if ((st = upload(ctx, p->d_qzero, p->q_is_zero, s)) != FFE_OK) return st;
-  if ((st = upload(ctx, p->d_golden, p->golden0, s)) != FFE_OK) return st;
+  auto add = [&](void* dst, const void* src, size_t bytes) {
+    if (bytes) out.push_back(HostCopy{dst, src, bytes});
+  };
+  add(p->d_delta, p->delta.data(), p->delta.size() * sizeof(double));
+  add(p->d_ht, p->ht.data(), p->ht.size() * sizeof(HT));
+  add(p->d_hlist, p->hlist.data(), p->hlist.size() * sizeof(double));
+  add(p->d_groups, p->groups.data(), p->groups.size() * sizeof(GroupDesc));
+  add(p->d_qzero, p->q_is_zero.data(), p->q_is_zero.size() * sizeof(int32_t));
+  add(p->d_golden, p->golden0.data(), p->golden0.size() * sizeof(GoldenState));
   p->h2d_bytes = p->delta.size() * sizeof(double) + p->ht.size() * sizeof(HT) +
                  p->hlist.size() * sizeof(double) + p->groups.size() * sizeof(GroupDesc) +
                  p->golden0.size() * sizeof(GoldenState);
+  return FFE_OK;
+}
+
+ffe_status plan_upload_params(ffe_context* ctx, ffe_plan* p, cudaStream_t s) {
+  std::vector<HostCopy> copies;
+  ffe_status st = plan_param_copies(ctx, p, copies);
+  if (st != FFE_OK) return st;
+  for (const HostCopy& c : copies)
+    FFE_CU(cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, s), "upload");
+  return FFE_OK;
+}
+
+// A plan refilled with new values of the same shape (a cached plan): the work
+// items' far windows depend on the values (h range, T_max, Delta range), so
+// they are rebuilt and uploaded with the parameters.  pinned: stage the copies
+// in the plan's page-locked buffer so that the call does not wait for the
+// device (the buffer is reused once the previous refill's copies are done).
+ffe_status plan_refill(ffe_context* ctx, ffe_plan* p, cudaStream_t s, bool pinned) {
+  const size_t n_items = p->items.size();
+  build_items(p);
+  if (p->items.size() != n_items) return set_err(ctx, "plan refill changed its work items"), FFE_EINTERNAL;
+  std::vector<HostCopy> copies;
+  copies.push_back(HostCopy{p->d_items, p->items.data(), p->items.size() * sizeof(WorkItem)});
+  ffe_status st = plan_param_copies(ctx, p, copies);
+  if (st != FFE_OK) return st;
+  if (!pinned) {
+    for (const HostCopy& c : copies)
+      FFE_CU(cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, s), "upload");
+    return FFE_OK;
+  }
+  size_t need = 0;
+  for (const HostCopy& c : copies) need += (c.bytes + 255) & ~size_t(255);
+  if (p->staged_ev) FFE_CU(cudaEventSynchronize(p->staged_ev), "staging wait");
+  else FFE_CU(cudaEventCreateWithFlags(&p->staged_ev, cudaEventDisableTiming), "event");
+  if (need > p->staging_bytes) {
+    if (p->staging) cudaFreeHost(p->staging);
+    p->staging = nullptr;
+    p->staging_bytes = 0;
+    FFE_CU(cudaHostAlloc(&p->staging, need, cudaHostAllocDefault), "cudaHostAlloc");
+    p->staging_bytes = need;
+  }
+  unsigned char* buf = static_cast<unsigned char*>(p->staging);
+  size_t off = 0;
+  for (const HostCopy& c : copies) {
+    std::memcpy(buf + off, c.src, c.bytes);
+    FFE_CU(cudaMemcpyAsync(c.dst, buf + off, c.bytes, cudaMemcpyHostToDevice, s), "upload");
+    off += (c.bytes + 255) & ~size_t(255);
+  }
+  FFE_CU(cudaEventRecord(p->staged_ev, s), "event");
   return FFE_OK;
 }
 
@@ -723,6 +775,8 @@ void plan_free(ffe_plan* p) {
       cudaFree(p->arena);
     }
   }
+  if (p->staging) cudaFreeHost(p->staging);
+  if (p->staged_ev) cudaEventDestroy(p->staged_ev);
   if (p->ev_cap0) cudaEventDestroy(p->ev_cap0);
   if (p->ev_cap1) cudaEventDestroy(p->ev_cap1);
   for (int i = 0; i < kRing; ++i) {
@@ -738,7 +792,7 @@ void plan_free(ffe_plan* p) {
 // ---------------------------------------------------------- plan builders
 namespace ffe {
 
-static ffe_status check_scan(ffe_context* ctx, const ffe_scan* sc) {
+ffe_status check_scan(ffe_context* ctx, const ffe_scan* sc) {
   if (!sc) return set_err(ctx, "scan is NULL"), FFE_EINVAL;
   if (!valid_N(sc->N)) return set_err(ctx, "N=%d must be even in [2, 8192]", sc->N), FFE_EINVAL;
   if (sc->n_q < 1 || sc->n_h < 1 || sc->n_T < 1 || !sc->qx || !sc->qy || !sc->h || !sc->T)
@@ -751,12 +805,8 @@ static ffe_status check_scan(ffe_context* ctx, const ffe_scan* sc) {
     return set_err(ctx, "golden reductions n=%d out of [1, 200]", sc->n), FFE_EINVAL;
   if (!finite(sc->lo) || !finite(sc->hi) || sc->lo > sc->hi || sc->lo != 0.0)
     return set_err(ctx, "Delta range must be finite with lo = 0 <= hi"), FFE_EINVAL;
-  bool has_zero = false;
-  for (int i = 0; i < sc->n_q; ++i) {
+  for (int i = 0; i < sc->n_q; ++i)
     if (!finite(sc->qx[i]) || !finite(sc->qy[i])) return set_err(ctx, "q not finite"), FFE_EINVAL;
-    if (sc->qx[i] == 0.0 && sc->qy[i] == 0.0) has_zero = true;
-  }
-  if (!has_zero) return set_err(ctx, "the q list must contain Q = (0, 0)"), FFE_EINVAL;
   for (int i = 0; i < sc->n_h; ++i)
     if (!finite(sc->h[i])) return set_err(ctx, "h not finite"), FFE_EINVAL;
   for (int i = 0; i < sc->n_T; ++i)
@@ -764,6 +814,19 @@ static ffe_status check_scan(ffe_context* ctx, const ffe_scan* sc) {
   const int64_t outs = (int64_t)sc->n_q * sc->n_h * sc->n_T * (int64_t)std::max(1, sc->n);
   if (outs > ((int64_t)1 << 31)) return set_err(ctx, "scan too large"), FFE_EINVAL;
   return FFE_OK;
+}
+
+// Labels need the normal state of Q = (0, 0) in the q list.
+static bool scan_has_q0(const ffe_scan* sc) {
+  for (int i = 0; i < sc->n_q; ++i)
+    if (sc->qx[i] == 0.0 && sc->qy[i] == 0.0) return true;
+  return false;
+}
+
+static bool plan_has_q0(const ffe_plan* p) {
+  for (int32_t z : p->q_is_zero)
+    if (z) return true;
+  return false;
 }
 
 // Grid scan: one PRODUCT group per q (outputs = Delta grid x (h,T) points).
@@ -1021,6 +1084,7 @@ void ffe_destroy(ffe_context* ctx) {
   for (ffe_plan* p : ctx->plans) plan_free(p);
   for (auto& kv : ctx->cache) plan_free(kv.second);
   if (ctx->spare) cudaFree(ctx->spare);
+  if (ctx->direct) cudaFree(ctx->direct);
   delete ctx;
 }
 
@@ -1050,7 +1114,29 @@ ffe_status ffe_plan_execute(ffe_plan* p, void* stream) {
 
 ffe_status ffe_plan_fetch(ffe_plan* p, ffe_result* per_point, int8_t* labels, int32_t* best_q, void* stream) {
   if (!p) return FFE_EINVAL;
+  if ((labels || best_q) && !plan_has_q0(p))
+    return set_err(p->ctx, "labels need Q = (0, 0) in the q list"), FFE_EINVAL;
   return fetch_scan(p->ctx, p, per_point, labels, best_q, (cudaStream_t)stream);
+}
+
+ffe_status ffe_plan_fetch_grid(ffe_plan* p, double* omega_grid, double* err_grid, void* stream) {
+  if (!p || !omega_grid) return FFE_EINVAL;
+  ffe_context* ctx = p->ctx;
+  if (p->kind != kPlanScanGrid) return set_err(ctx, "ffe_plan_fetch_grid: not a grid phase-scan plan"), FFE_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  ffe_status st = plan_check_status(ctx, p, s);
+  if (st != FFE_OK) return st;
+  std::vector<double> om(p->n_out), eb(err_grid ? p->n_out : 0);
+  FFE_CU(cudaMemcpyAsync(om.data(), p->d_omega, p->n_out * sizeof(double), cudaMemcpyDeviceToHost, s), "fetch");
+  if (err_grid) FFE_CU(cudaMemcpyAsync(eb.data(), p->d_eb, p->n_out * sizeof(double), cudaMemcpyDeviceToHost, s), "fetch");
+  FFE_CU(cudaStreamSynchronize(s), "sync");
+  int64_t k = 0;
+  for (const Line& L : p->lines)  // lines in the order of ffe_plan_fetch's per_point
+    for (int i = 0; i < L.count; ++i, ++k) {
+      omega_grid[k] = om[L.out0 + (int64_t)i * L.stride];
+      if (err_grid) err_grid[k] = eb[L.out0 + (int64_t)i * L.stride];
+    }
+  return FFE_OK;
 }
 
 ffe_status ffe_plan_stats(const ffe_plan* p, ffe_plan_info* info) {
@@ -1104,11 +1190,60 @@ void ffe_plan_destroy(ffe_plan* p) {
   plan_free(p);
 }
 
+ffe_status ffe_phase_scan_async(ffe_context* ctx, const ffe_scan* scan, ffe_result* per_point, int8_t* labels,
+                                int32_t* best_q, void* stream) {
+  if (!ctx) return FFE_EINVAL;
+  ffe_status st = check_scan(ctx, scan);
+  if (st != FFE_OK) return st;
+  if ((labels || best_q) && !scan_has_q0(scan))
+    return set_err(ctx, "labels need Q = (0, 0) in the q list"), FFE_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  char key[160];
+  snprintf(key, sizeof key, "ascan:%d:%d:%d:%d:%d:%d:%d", ctx->model.prec, scan->search, scan->N, scan->n_q,
+           scan->n_h, scan->n_T, scan->n);
+  const int kind = scan->search == FFE_SEARCH_GRID ? kPlanScanGrid : kPlanScanGolden;
+  ffe_plan* p = nullptr;
+  auto it = ctx->cache.find(key);
+  if (it != ctx->cache.end()) {
+    p = it->second;
+    fill_scan(p, scan);
+    const bool ut = ctx->model.prec == FFE_FP32C && kind == kPlanScanGrid && batches_share_T(p);
+    if (ut != (p->variant == kLayoutProductUT)) {  // the kernel variant no longer fits: rebuild
+      plan_free(p);
+      ctx->cache.erase(it);
+      p = nullptr;
+    } else if ((st = plan_refill(ctx, p, s, true)) != FFE_OK) {
+      return st;
+    }
+  }
+  if (!p) {
+    p = plan_new(ctx, kind);
+    fill_scan(p, scan);
+    st = plan_configure(ctx, p);
+    if (st == FFE_OK) st = plan_finish(ctx, p, true);
+    if (st != FFE_OK) {
+      plan_free(p);
+      return st;
+    }
+    ctx->cache[key] = p;
+  }
+  if ((st = plan_run(ctx, p, s)) != FFE_OK) return st;
+  cudaError_t e = cudaSuccess;
+  if (per_point) e = results_launch(p->d_lres, (int64_t)p->lines.size(), p->d_counters, p->cap, per_point, s);
+  if (e == cudaSuccess && labels)
+    e = cudaMemcpyAsync(labels, p->d_labels, p->n_pts * sizeof(int8_t), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && best_q)
+    e = cudaMemcpyAsync(best_q, p->d_bestq, p->n_pts * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+  return e == cudaSuccess ? FFE_OK : cuda_fail(ctx, e, "ffe_phase_scan_async");
+}
+
 ffe_status ffe_phase_scan(ffe_context* ctx, const ffe_scan* scan, ffe_result* per_point, int8_t* labels,
                           int32_t* best_q, void* stream) {
   if (!ctx) return FFE_EINVAL;
   ffe_status st = check_scan(ctx, scan);
   if (st != FFE_OK) return st;
+  if ((labels || best_q) && !scan_has_q0(scan))
+    return set_err(ctx, "labels need Q = (0, 0) in the q list"), FFE_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   char key[160];
   snprintf(key, sizeof key, "scan:%d:%d:%d:%d:%d:%d:%d", ctx->model.prec, scan->search, scan->N, scan->n_q,
@@ -1124,7 +1259,7 @@ ffe_status ffe_phase_scan(ffe_context* ctx, const ffe_scan* scan, ffe_result* pe
       plan_free(p);
       ctx->cache.erase(it);
       p = nullptr;
-    } else if ((st = plan_upload_params(ctx, p, s)) != FFE_OK) {
+    } else if ((st = plan_refill(ctx, p, s, false)) != FFE_OK) {
       return st;
     }
   }

@@ -47,6 +47,10 @@ struct ffe_context {
   // passes, the autotuner's trials) then skip cudaMalloc and cudaFree
   void* spare = nullptr;
   size_t spare_bytes = 0;
+  // scratch of the stream-ordered point evaluation (ffe_omega_async), grown
+  // to the largest call
+  void* direct = nullptr;
+  size_t direct_bytes = 0;
 };
 
 struct ffe_plan {
@@ -141,9 +145,20 @@ struct ffe_plan {
   int64_t exec_count = 0;
   int64_t timed_upto = 0;
   int32_t last_rescored[2] = {0, 0};  // FP64 requests of the last fetched execution
+  // page-locked staging of a refill's uploads (stream-ordered calls) and the
+  // event after its copies
+  void* staging = nullptr;
+  size_t staging_bytes = 0;
+  cudaEvent_t staged_ev = nullptr;
 };
 
 namespace ffe {
+
+struct HostCopy {
+  void* dst;
+  const void* src;
+  size_t bytes;
+};
 
 void set_err(ffe_context* c, const char* fmt, ...);
 ffe_status cuda_fail(ffe_context* c, cudaError_t e, const char* what);
@@ -154,6 +169,9 @@ void plan_free(ffe_plan* p);
 ffe_status plan_configure(ffe_context* ctx, ffe_plan* p);
 ffe_status plan_finish(ffe_context* ctx, ffe_plan* p, bool use_graph);
 ffe_status plan_upload_params(ffe_context* ctx, ffe_plan* p, cudaStream_t s);
+ffe_status plan_refill(ffe_context* ctx, ffe_plan* p, cudaStream_t s, bool pinned);
+void fill_scan(ffe_plan* p, const ffe_scan* sc);
+ffe_status check_scan(ffe_context* ctx, const ffe_scan* sc);
 ffe_status plan_run(ffe_context* ctx, ffe_plan* p, cudaStream_t s);
 ffe_status plan_check_status(ffe_context* ctx, ffe_plan* p, cudaStream_t s);
 double plan_k_evals(const ffe_plan* p);

@@ -362,6 +362,61 @@ ffe_status ffe_minimize(ffe_context* ctx, int32_t search, const ffe_param* ps, i
   return st;
 }
 
+ffe_status ffe_minimize_async(ffe_context* ctx, int32_t search, const ffe_param* ps, int64_t n, ffe_result* out,
+                              double* omega_grid, void* stream) {
+  if (!ctx) return FFE_EINVAL;
+  if (!out) return set_err(ctx, "ffe_minimize_async: out is NULL"), FFE_EINVAL;
+  ffe_status st = check_params(ctx, search, ps, n);
+  if (st != FFE_OK) return st;
+  if (search == FFE_SEARCH_GOLDEN && omega_grid)
+    return set_err(ctx, "omega_grid applies to grid searches only"), FFE_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  // plans are cached by shape: the lattices, grid lengths and pair momenta
+  // (which decide the groups and work items), not the (h, T, Delta) values
+  uint64_t hash = 1469598103934665603ull;
+  auto mix = [&](const void* v, size_t bytes) {
+    const unsigned char* c = static_cast<const unsigned char*>(v);
+    for (size_t i = 0; i < bytes; ++i) hash = (hash ^ c[i]) * 1099511628211ull;
+  };
+  for (int64_t i = 0; i < n; ++i) {
+    mix(&ps[i].N, sizeof ps[i].N);
+    mix(&ps[i].n, sizeof ps[i].n);
+    mix(&ps[i].qx, sizeof ps[i].qx);
+    mix(&ps[i].qy, sizeof ps[i].qy);
+  }
+  char key[160];
+  snprintf(key, sizeof key, "amin:%d:%d:%lld:%016llx", ctx->model.prec, search, (long long)n,
+           (unsigned long long)hash);
+  ffe_plan* p = nullptr;
+  auto it = ctx->cache.find(key);
+  if (it != ctx->cache.end()) {
+    p = it->second;
+    p->groups.clear();
+    p->delta.clear();
+    p->ht.clear();
+    p->hlist.clear();
+    p->lines.clear();
+    p->golden0.clear();
+    if (search == FFE_SEARCH_GRID)
+      fill_min_grid(p, ps, n);
+    else
+      fill_min_golden(p, ps, n);
+    if ((st = plan_refill(ctx, p, s, true)) != FFE_OK) return st;
+  } else {
+    st = build_min_plan(ctx, search, ps, n, true, &p);
+    if (st != FFE_OK) {
+      plan_free(p);
+      return st;
+    }
+    ctx->cache[key] = p;
+  }
+  if ((st = plan_run(ctx, p, s)) != FFE_OK) return st;
+  cudaError_t e = results_launch(p->d_lres, (int64_t)p->lines.size(), p->d_counters, p->cap, out, s);
+  if (e == cudaSuccess && omega_grid)
+    e = cudaMemcpyAsync(omega_grid, p->d_omega, p->n_out * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  return e == cudaSuccess ? FFE_OK : cuda_fail(ctx, e, "ffe_minimize_async");
+}
+
 ffe_status ffe_plan_minimize(ffe_context* ctx, int32_t search, const ffe_param* ps, int64_t n, void* stream,
                              ffe_plan** out) {
   if (!ctx || !out) return FFE_EINVAL;

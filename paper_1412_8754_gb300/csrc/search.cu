@@ -18,6 +18,7 @@
 #include <cfloat>
 #include <climits>
 
+#include "../../include/ffe.h"
 #include "ffe_internal.cuh"
 #include "ksum.cuh"
 
@@ -316,6 +317,34 @@ cudaError_t labels_launch(LineResult* res, int n_q, int n_pts, const int32_t* q_
   if (n_pts <= 0) return cudaSuccess;
   labels_kernel<<<(n_pts + 127) / 128, 128, 0, s>>>(res, n_q, n_pts, q_is_zero, lines, delta, mode, req,
                                                      n_req, cap, labels, best_q);
+  return cudaGetLastError();
+}
+
+// Line results in the C ABI's layout, written on the device for the
+// stream-ordered entry points.  counters: the plan's counter block ([3], [4]
+// the FP64 requests of the search and of the labels, [7] the status word); a
+// request count above cap or a non-zero status marks every line
+// FFE_FLAG_INVALID with NaN values.
+__global__ void results_kernel(const LineResult* __restrict__ lr, int64_t n, const int32_t* __restrict__ counters,
+                               int32_t cap, ffe_result* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool bad = counters[7] != 0 || counters[3] > cap || counters[4] > cap;
+  const LineResult r = lr[i];
+  ffe_result o;
+  o.delta_star = bad ? NAN : r.delta_star;
+  o.omega_star = bad ? NAN : r.omega_star;
+  o.omega_lo = bad ? NAN : r.omega_lo;
+  o.err_bound = bad ? NAN : r.eb_star;
+  o.idx_star = r.idx_star;
+  o.flags = bad ? (r.flags | FFE_FLAG_INVALID) : r.flags;
+  out[i] = o;
+}
+
+cudaError_t results_launch(const LineResult* lr, int64_t n, const int32_t* counters, int32_t cap, void* out,
+                           cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  results_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(lr, n, counters, cap, static_cast<ffe_result*>(out));
   return cudaGetLastError();
 }
 

@@ -28,7 +28,7 @@ DAGHOFER3_PARAMS = dict(t1=-0.08, t2=0.1825, t3=0.08375, t4=-0.03, t5=0.15, t6=0
                         t9=0.0, t10=-0.024, t11=-0.01, t12=0.0275, eps0=0.75, mu=0.4748)
 MODELS = {"raghu2": (FFE_MODEL_RAGHU2, 2, RAGHU2_PARAMS), "daghofer3": (FFE_MODEL_DAGHOFER3, 3, DAGHOFER3_PARAMS)}
 FFE_SEARCH_GRID, FFE_SEARCH_GOLDEN = 0, 1
-FFE_FLAG_RESCORED, FFE_FLAG_EDGE, FFE_FLAG_LOWER, FFE_FLAG_PRUNED = 1, 2, 4, 8
+FFE_FLAG_RESCORED, FFE_FLAG_EDGE, FFE_FLAG_LOWER, FFE_FLAG_PRUNED, FFE_FLAG_INVALID = 1, 2, 4, 8, 32
 FFE_PHASE_NORMAL, FFE_PHASE_BCS, FFE_PHASE_FFLO = 0, 1, 2
 
 POINT_DTYPE = np.dtype([("N", "<i4"), ("reserved", "<i4"), ("qx", "<f8"), ("qy", "<f8"),
@@ -90,6 +90,7 @@ _SIGNATURES = [
     ("ffe_plan_execute", ctypes.c_int, [_VP, _VP]),
     ("ffe_plan_fetch", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     ("ffe_plan_stats", ctypes.c_int, [_VP, ctypes.POINTER(ffe_plan_info)]),
+    ("ffe_plan_fetch_grid", ctypes.c_int, [_VP, _VP, _VP, _VP]),
     ("ffe_plan_kernel_ms", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     ("ffe_plan_destroy", None, [_VP]),
     ("ffe_plan_minimize", ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.POINTER(_VP)]),
@@ -108,6 +109,13 @@ _SIGNATURES = [
     ("ffe_surrogate_scan", ctypes.c_int, [_VP, _VP, ctypes.POINTER(ffe_scan), _VP, _VP, _VP, _VP, _VP, _VP]),
     ("ffe_omega_noalloc", ctypes.c_int, [ctypes.POINTER(ffe_model), ctypes.c_int32, ctypes.c_double,
                                          ctypes.c_double, _VP, _VP, _VP, ctypes.c_int32, _VP, _VP]),
+    ("ffe_omega_async", ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _VP, _VP, _VP,
+                                       ctypes.c_int64, _VP, _VP, _VP]),
+    ("ffe_minimize_async", ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, _VP, _VP]),
+    ("ffe_phase_scan_async", ctypes.c_int, [_VP, ctypes.POINTER(ffe_scan), _VP, _VP, _VP, _VP]),
+    ("ffe_label_candidates", ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP, _VP]),
+    ("ffe_merge_candidates", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_int32, _VP,
+                                            _VP]),
 ]
 
 
@@ -304,6 +312,48 @@ def ffe_minimize(ctx, params: np.ndarray, search=FFE_SEARCH_GRID, want_grid=Fals
     return (res, grid, err) if want_grid else res
 
 
+def _dptr(t):
+    """Device address of a tensor-like argument (anything with data_ptr()), or None."""
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def ffe_omega_async(ctx, N, qx, qy, h, T, delta, omega, omega_band=None, stream=None):
+    """Stream-ordered Omega at the points of one (N, Q): h, T, delta, omega (and omega_band,
+    [n, nb]) are device tensors of float64; returns without waiting for the device."""
+    _check(ctx, lib().ffe_omega_async(ctx, int(N), float(qx), float(qy), _dptr(h), _dptr(T), _dptr(delta),
+                                      int(h.numel()), _dptr(omega), _dptr(omega_band), _stream(stream)))
+
+
+def ffe_minimize_async(ctx, params: np.ndarray, out, search=FFE_SEARCH_GRID, omega_grid=None, stream=None):
+    """Stream-ordered minimisation: params host (PARAM_DTYPE), out a device buffer of
+    len(params) * RESULT_DTYPE.itemsize bytes (see result_buffer), omega_grid a device tensor."""
+    ps = np.ascontiguousarray(params, dtype=PARAM_DTYPE)
+    _check(ctx, lib().ffe_minimize_async(ctx, search, _ptr(ps), len(ps), _dptr(out), _dptr(omega_grid),
+                                         _stream(stream)))
+
+
+def ffe_phase_scan_async(ctx, N, qx, qy, h, T, per_point=None, labels=None, best_q=None, search=FFE_SEARCH_GRID,
+                         n=256, lo=0.0, hi=0.2, stream=None):
+    """Stream-ordered phase scan: per_point (result buffer), labels (int8) and best_q (int32)
+    are device tensors or None."""
+    sc, keep = make_scan(N, qx, qy, h, T, search, n, lo, hi)
+    _check(ctx, lib().ffe_phase_scan_async(ctx, ctypes.byref(sc), _dptr(per_point), _dptr(labels), _dptr(best_q),
+                                           _stream(stream)))
+    del keep
+
+
+def result_buffer(n, device="cuda"):
+    """A device buffer for n ffe_result records (torch uint8); view it on the host with
+    as_results(buffer)."""
+    import torch
+
+    return torch.empty(int(n) * RESULT_DTYPE.itemsize, dtype=torch.uint8, device=device)
+
+
+def as_results(buf) -> np.ndarray:
+    return buf.cpu().numpy().view(RESULT_DTYPE)
+
+
 def make_scan(N, qx, qy, h, T, search=FFE_SEARCH_GRID, n=256, lo=0.0, hi=0.2):
     """Returns (ffe_scan, keepalive arrays)."""
     arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (qx, qy, h, T)]
@@ -314,13 +364,15 @@ def make_scan(N, qx, qy, h, T, search=FFE_SEARCH_GRID, n=256, lo=0.0, hi=0.2):
     return sc, arrs
 
 
-def ffe_phase_scan(ctx, N, qx, qy, h, T, search=FFE_SEARCH_GRID, n=256, lo=0.0, hi=0.2, stream=None):
-    """Returns (per_point[n_q, n_h*n_T], labels[n_h*n_T], best_q[n_h*n_T])."""
+def ffe_phase_scan(ctx, N, qx, qy, h, T, search=FFE_SEARCH_GRID, n=256, lo=0.0, hi=0.2, stream=None,
+                   labels=True):
+    """Returns (per_point[n_q, n_h*n_T], labels[n_h*n_T], best_q[n_h*n_T]); labels=False (a q
+    list without Q = 0): the labels and best q are None."""
     sc, keep = make_scan(N, qx, qy, h, T, search, n, lo, hi)
     npts = sc.n_h * sc.n_T
     res = np.zeros((sc.n_q, npts), dtype=RESULT_DTYPE)
-    labels = np.zeros(npts, dtype=np.int8)
-    best = np.zeros(npts, dtype=np.int32)
+    labels = np.zeros(npts, dtype=np.int8) if labels else None
+    best = np.zeros(npts, dtype=np.int32) if labels is not None else None
     _check(ctx, lib().ffe_phase_scan(ctx, ctypes.byref(sc), _ptr(res), _ptr(labels), _ptr(best),
                                      _stream(stream)))
     del keep
@@ -339,12 +391,20 @@ def ffe_plan_execute(plan, stream=None):
     _check(plan.ctx, lib().ffe_plan_execute(plan.handle, _stream(stream)))
 
 
-def ffe_plan_fetch(plan, stream=None):
+def ffe_plan_fetch(plan, stream=None, labels=True):
     res = np.zeros((plan.n_q, plan.n_pts), dtype=RESULT_DTYPE)
-    labels = np.zeros(plan.n_pts, dtype=np.int8)
-    best = np.zeros(plan.n_pts, dtype=np.int32)
+    labels = np.zeros(plan.n_pts, dtype=np.int8) if labels else None
+    best = np.zeros(plan.n_pts, dtype=np.int32) if labels is not None else None
     _check(plan.ctx, lib().ffe_plan_fetch(plan.handle, _ptr(res), _ptr(labels), _ptr(best), _stream(stream)))
     return res, labels, best
+
+
+def ffe_plan_fetch_grid(plan, n, stream=None, want_err=False):
+    """Omega(Delta) grids [n_q, n_pts, n] of a grid phase-scan plan (and their error bounds)."""
+    om = np.zeros((plan.n_q, plan.n_pts, n))
+    eb = np.zeros_like(om) if want_err else None
+    _check(plan.ctx, lib().ffe_plan_fetch_grid(plan.handle, _ptr(om), _ptr(eb), _stream(stream)))
+    return (om, eb) if want_err else om
 
 
 def ffe_plan_stats(plan) -> dict:
@@ -398,8 +458,8 @@ class Plan:
     def execute(self, stream=None):
         ffe_plan_execute(self, stream)
 
-    def fetch(self, stream=None):
-        return ffe_plan_fetch(self, stream)
+    def fetch(self, stream=None, labels=True):
+        return ffe_plan_fetch(self, stream, labels)
 
     def fetch_minimize(self, want_grid=False, stream=None):
         return ffe_plan_fetch_minimize(self, want_grid, stream)
@@ -409,6 +469,9 @@ class Plan:
 
     def stats(self):
         return ffe_plan_stats(self)
+
+    def fetch_grid(self, n, stream=None, want_err=False):
+        return ffe_plan_fetch_grid(self, n, stream, want_err)
 
     def kernel_ms(self):
         return ffe_plan_kernel_ms(self)
