@@ -2,11 +2,12 @@
 //
 // A full scan (Alg. 1) searches every (q, h, T) line over the whole Delta
 // range.  Guided, the surrogate first predicts the condensation energy of
-// every line on a Delta grid (tensor-core inference); per (h, T) only q = 0
-// and the q_keep lines with the lowest predicted minimum (and any other q
-// predicted to condense whose minimum is within the margin of the best) are
-// verified by the
-// exact k-sum, each on a window of `window` grid points around its predicted
+// every line on a Delta grid (tensor-core inference), and the exact k-sum
+// evaluates every line's normal state (Delta = 0, one k-sum per line); per
+// (h, T) only q = 0 and the q_keep lines with the lowest predicted minimum
+// (exact normal state + predicted condensation energy; with a margin also
+// every q within the margin of the lowest) are verified by the exact k-sum,
+// each on a window of `window` grid points around its predicted
 // minimum, with Delta = 0 as the reference (same kernels, same FP64
 // re-evaluation of near ties, same label passes as the full scan).  A grid
 // scan evaluates the window's grid points; a golden-section scan brackets
@@ -272,33 +273,56 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
   if (e == cudaSuccess && st == FFE_OK) e = cudaMemcpyAsync(ymin.data(), d_ymin, n_lines * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && st == FFE_OK) e = cudaStreamSynchronize(s);
 
-  // 2. which lines to verify, and on which window
+  // 2. the exact normal state Omega(q, Delta = lo) of every line.  The
+  // surrogate predicts condensation energies, each relative to its own line's
+  // normal state, while the labels compare Omega across q, and on a finite
+  // lattice the normal states of different q differ; the pruning orders the
+  // q by exact normal state + predicted condensation energy.
+  double k_evals = 0.0;
+  std::vector<double> anchor(n_lines, 0.0), anchor_eb(n_lines, 0.0);
+  if (e == cudaSuccess && st == FFE_OK) {
+    std::vector<int> all_pts(n_pts);
+    std::iota(all_pts.begin(), all_pts.end(), 0);
+    std::vector<LineSpec> spec0(n_lines);
+    for (LineSpec& ls : spec0) ls.grid_idx = {0};
+    PassResult r0;
+    st = run_explicit(ctx, sc, q0, all_pts, 0, grid, spec0, s, r0, &k_evals);
+    if (st == FFE_OK)
+      for (int l = 0; l < n_lines; ++l) {
+        anchor[l] = r0.res[l].omega_lo;
+        anchor_eb[l] = r0.res[l].err_bound;
+      }
+  }
+
+  // 3. which lines to verify, and on which window
   const int w = guide->window;
   std::vector<char> kept(n_lines, 0);
   const float ys = surrogate_y_scale(sur);
+  const double n2 = (double)sc->N * (double)sc->N;
   std::vector<int> wstart(n_lines, 0);
   std::vector<int32_t> kept_rows;
   std::vector<int64_t> row_of(n_lines, -1);
   std::vector<float> ypred;  // prediction rows of the kept lines
   if (e == cudaSuccess && st == FFE_OK) {
     std::vector<int> order;
+    // predicted minimum per site: exact normal state + predicted condensation
+    auto pred_min = [&](int q, int pt) {
+      const size_t l = (size_t)q * n_pts + pt;
+      return anchor[l] / n2 + (double)ymin[l] * ys;
+    };
     for (int pt = 0; pt < n_pts; ++pt) {
       order.clear();
       for (int q = 0; q < sc->n_q; ++q)
         if (q != q0) order.push_back(q);
-      std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        return ymin[(size_t)a * n_pts + pt] < ymin[(size_t)b * n_pts + pt];
-      });
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pred_min(a, pt) < pred_min(b, pt); });
       kept[(size_t)q0 * n_pts + pt] = 1;
       for (int k = 0; k < (int)order.size() && k < guide->q_keep; ++k) kept[(size_t)order[k] * n_pts + pt] = 1;
-      // beyond q_keep: every q predicted to condense by more than the margin
-      // whose predicted minimum is within the margin of the best one (the
-      // surrogate cannot order them)
+      // beyond q_keep: every q whose predicted minimum is within the margin of
+      // the lowest one (q = 0 included): the surrogate cannot order them
       if (guide->margin > 0.0 && !order.empty()) {
-        const double best = (double)ymin[(size_t)order[0] * n_pts + pt] * ys;
+        const double best = std::min(pred_min(order[0], pt), pred_min(q0, pt));
         for (int k = guide->q_keep; k < (int)order.size(); ++k) {
-          const double yk = (double)ymin[(size_t)order[k] * n_pts + pt] * ys;
-          if (yk >= -guide->margin || yk > best + guide->margin) break;
+          if (pred_min(order[k], pt) > best + guide->margin) break;
           kept[(size_t)order[k] * n_pts + pt] = 1;
         }
       }
@@ -336,7 +360,6 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
   }
   std::vector<LineSpec> spec(n_lines);
   std::vector<char> redo(n_lines, 0);  // searched over the whole range
-  const double n2 = (double)sc->N * (double)sc->N;
   // (ys: the surrogate's y scale, |t1| per site per unit of y)
   for (int l = 0; l < n_lines; ++l) {
     if (!kept[l]) {
@@ -399,8 +422,7 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
     return out;
   };
 
-  // 3. exact verification of the windows
-  double k_evals = 0.0;
+  // 4. exact verification of the windows
   PassResult r1;
   std::vector<LineSpec> spec1;
   if (n1 > 0) {
@@ -409,7 +431,7 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
     if (st != FFE_OK) return st;
   }
 
-  // 4. surrogate error at the verified points; lines whose minimum sits on an inner window edge
+  // 5. surrogate error at the verified points; lines whose minimum sits on an inner window edge
   double se = 0.0;
   int64_t n_se = 0, fallbacks = 0, n_kept = 0;
   std::vector<int64_t> off((size_t)sc->n_q * n1 + 1, 0);
@@ -457,7 +479,7 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
       }
     }
 
-  // 5. the second pass: every point with a line to search over the whole range
+  // 6. the second pass: every point with a line to search over the whole range
   // (an ambiguous line, or one whose minimum sat on an inner window edge) has
   // all its verified lines searched over the whole range
   std::vector<int> pos_in2(n_pts, -1);
@@ -475,7 +497,7 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
     if (st != FFE_OK) return st;
   }
 
-  // 6. results: per line from the pass that scanned its point last; grid indices
+  // 7. results: per line from the pass that scanned its point last; grid indices
   for (int l = 0; l < n_lines; ++l) {
     const int q = l / n_pts, pt = l % n_pts;
     const bool second = pos_in2[pt] >= 0;
@@ -485,12 +507,11 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
     const LineSpec& ls = second ? spec2[m] : spec1[m];
     const PassResult& pr = second ? r2 : r1;
     ffe_result r = pr.res[m];
-    if (!kept[l]) {  // the q = 0 line's reference value
-      const ffe_result& rn = pr.res[(size_t)q0 * nsub + j];
+    if (!kept[l]) {  // the line's own exact value at Delta = lo
       r.delta_star = sc->lo;
-      r.omega_star = rn.omega_lo;
-      r.omega_lo = rn.omega_lo;
-      r.err_bound = 0.0;
+      r.omega_star = anchor[l];
+      r.omega_lo = anchor[l];
+      r.err_bound = anchor_eb[l];
       r.idx_star = golden ? -1 : 0;
       r.flags = FFE_FLAG_LOWER | FFE_FLAG_PRUNED;
     } else if (golden) {
