@@ -99,30 +99,47 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(cfg, seconds_target=15.0):
-    """The FP64 oracle as it stands, on the host cores, on a bounded sample of
-    the workload: the 256-point Delta grid of one (q, h) pair at N = 1024,
-    parallel over Delta with OpenMP."""
+def cpu_baseline(cfg, lines, diagram_lines=None, tol=2e-7):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of the workload:
+    the whole 256-point Delta grid of a few (q, h) lines at N = 1024, parallel over Delta with
+    OpenMP (timed).  The same oracle values give the per-result error of the GPU scan on those
+    lines (every grid value per site, and the argmin index), and, for the phase diagram, the
+    oracle at the GPU's Delta* and at Delta = 0 of a few golden-section lines."""
     import numpy as np
 
     import oracle
+    from oracle import search
 
     m = oracle.make_model(U=cfg["U"])
     N = cfg["N"]
     grid = np.linspace(cfg["lo"], cfg["hi"], cfg["n"])
-    # time a few points to size the sample
+    oracle.omega_batch(m, N, lines[0]["qx"], 0.0, lines[0]["h"], cfg["T"][0], grid[:threads_hint()])  # warm-up
     t0 = time.perf_counter()
-    _, _, threads = oracle.omega_batch(m, N, cfg["qx"][5], 0.0, cfg["h"][3], cfg["T"][0], grid[:threads_hint()])
+    refs = []
+    for ln in lines:
+        ref, _, threads = oracle.omega_batch(m, N, ln["qx"], 0.0, ln["h"], cfg["T"][0], grid)
+        refs.append(ref)
     dt = time.perf_counter() - t0
-    per_pt = dt / threads_hint()
-    n_pts = int(max(threads, min(len(grid), seconds_target / max(per_pt, 1e-9))))
-    sample = grid[:n_pts]
-    t0 = time.perf_counter()
-    _, _, threads = oracle.omega_batch(m, N, cfg["qx"][5], 0.0, cfg["h"][3], cfg["T"][0], sample)
-    dt = time.perf_counter() - t0
-    kev = float(N * N) * len(sample)
-    return {"value": kev / dt, "unit": "k-evals/s", "cores": threads, "kind": "oracle",
-            "sample": f"{len(sample)} Delta values of one (q, h) at N={N} (FP64, OpenMP over Delta), {dt:.1f} s"}
+    kev = float(N * N) * len(grid) * len(lines)
+    err = max(float(np.max(np.abs(ln["omega"] - r)) / N**2) for ln, r in zip(lines, refs))
+    same = all(int(ln["idx_star"]) == search.grid_argmin(r) for ln, r in zip(lines, refs))
+    out = {"value": kev / dt, "unit": "k-evals/s", "cores": threads, "kind": "oracle",
+           "sample": (f"the {len(grid)}-point Delta grids of {len(lines)} (q, h) lines at N={N} (FP64, OpenMP "
+                      f"over Delta), {dt:.1f} s"),
+           "per_result_error": {"fflo_scan": {
+               "lines": [f"q={ln['qx']:.4f}, h={ln['h']:.4f}" for ln in lines], "values": len(lines) * len(grid),
+               "max_err_per_site_vs_oracle": err, "tolerance_per_site": tol, "argmin_identical": same}}}
+    if diagram_lines:
+        d = diagram_lines
+        Nd = d["N"]
+        md = oracle.make_model(U=cfg["U"])
+        at, _, _ = oracle.omega_batch(md, Nd, d["qx"], 0.0, d["h"], d["T"], d["delta_star"])
+        at0, _, _ = oracle.omega_batch(md, Nd, d["qx"], 0.0, d["h"], d["T"], 0.0)
+        e = np.concatenate([np.abs(at - d["omega_star"]), np.abs(at0 - d["omega_lo"])]) / Nd**2
+        out["per_result_error"]["phase_diagram"] = {
+            "lines": int(len(d["qx"])), "values": int(e.size), "max_err_per_site_vs_oracle": float(e.max()),
+            "tolerance_per_site": tol, "at": "the GPU's golden-section Delta* and Delta = 0"}
+    return out
 
 
 # DRAM bytes (read + write) of one k-sum launch of the default workload, from
@@ -130,6 +147,11 @@ def cpu_baseline(cfg, seconds_target=15.0):
 # launch): 1.49 GB read (the FP32 k-state table, 1.34 GB, and the trig and job
 # tables) + 0.270 GB written (the FP64 k-chunk partial sums).
 DRAM_TRAFFIC_PER_LAUNCH = 1.760e9
+# From the committed one-kernel ncu capture of the same kernel on 8 of the 64 q
+# (profiles/ksum_fflo_scan_N1024_q8.md): issue slots busy and the SFU (XU)
+# pipe's share of its peak.
+NCU_HEADLINE = {"issue_active_pct": 58.5, "sfu_pct_of_peak": 32.9,
+                "source": "profiles/ksum_fflo_scan_N1024_q8.md"}
 
 
 def run_extras(ffe, np, torch, stream, workloads):
@@ -249,14 +271,14 @@ def run_surrogate(ffe, np, torch, workloads, cfg, ref, full_s, fp64_rate, epochs
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
         rms_train = sg.rms_error(sur, x, y)
-        pd_out = run_phase_diagram(ffe, np, torch, workloads, ctx, sur, 3.0 * rms_train, fp64_rate,
-                                   cfg["U"]) if diagram else None
+        pd_check, pd_out = run_phase_diagram(ffe, np, torch, workloads, ctx, sur, 3.0 * rms_train, fp64_rate,
+                                             cfg["U"]) if diagram else (None, None)
         sur.close()
     dt = statistics.median(times)
     kept = (res["flags"] & ffe.FFE_FLAG_PRUNED) == 0
     full64_s = st["k_evals_full"] / fp64_rate if fp64_rate else None
     n_pts = len(labels)
-    return pd_out, {
+    return pd_check, pd_out, {
         "workload": (f"train: {len(x)} samples (q,h,T,Delta) at N=512 from the FP32+comp k-sum, {epochs} epochs, "
                      f"batch 4096; guide: fflo_scan N={cfg['N']}, window 16 + Delta=0, q=0 and 3 q kept per h"),
         "datagen_s": t_data, "train_s": t_train, "train_loss_first_last": [float(losses[0]), float(losses[-1])],
@@ -302,7 +324,18 @@ def run_phase_diagram(ffe, np, torch, workloads, ctx, sur, margin, fp64_rate, U)
         t64 = time.perf_counter() - t0
     sub = (np.arange(2)[:, None] * len(pd["T"]) + np.arange(4)[None, :]).ravel()
     k64 = float(pd["N"]) ** 2 * len(pd["qx"]) * len(sub) * (3 + pd["n"])
-    return {
+    # a few golden-section lines for the oracle check of the CPU leg: (q, point) pairs spread over
+    # the diagram, BCS points included where there are any
+    rng = np.random.default_rng(7)
+    picks = [(int(q), int(p)) for q, p in zip(rng.integers(0, len(pd["qx"]), 6), rng.integers(0, n_pts, 6))]
+    picks += [(int(fbest[p]), int(p)) for p in np.flatnonzero(fbest >= 0)[:2]]
+    check = {"N": pd["N"], "qx": np.array([pd["qx"][q] for q, _ in picks]),
+             "h": np.array([pd["h"][p // len(pd["T"])] for _, p in picks]),
+             "T": np.array([pd["T"][p % len(pd["T"])] for _, p in picks]),
+             "delta_star": np.array([full["delta_star"][q, p] for q, p in picks]),
+             "omega_star": np.array([full["omega_star"][q, p] for q, p in picks]),
+             "omega_lo": np.array([full["omega_lo"][q, p] for q, p in picks])}
+    return check, {
         "workload": (f"N={pd['N']}, {len(pd['qx'])} q x {len(pd['h'])} h x {len(pd['T'])} T, golden "
                      f"{pd['n']} reductions on [0, 0.2], U={U}"),
         "fp32c_full": {"seconds": t_full, "points_per_s": len(pd["qx"]) * n_pts / t_full,
@@ -364,9 +397,10 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1412_8754_gb300 import ffe, shard
 
-    # shard the q list across ranks (q = 0 stays on every rank: it is the label reference)
+    # shard the q list across ranks, round robin (q = 0, the label reference, on rank 0 only)
     q_all = cfg["qx"]
     mine = shard.shard_q(len(q_all), rank, ws)
+    has_q0 = 0 in mine
     qx = q_all[mine]
     qy = np.zeros_like(qx)
     n_pts = len(cfg["h"]) * len(cfg["T"])
@@ -384,7 +418,7 @@ def main():
 
     for _ in range(args.warmup):
         plan.execute(stream)
-    plan.fetch(stream)
+    plan.fetch(stream, labels=has_q0)
     plan.kernel_ms()  # discard warm-up kernel timings
     clocks = Clocks(local)
     barrier()
@@ -402,9 +436,10 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in evs]
     t_total = sum(step_ms) / 1e3
     kern_ms, kern_n = plan.kernel_ms()
-    res, labels, best = plan.fetch(stream)
+    res, labels, best = plan.fetch(stream, labels=has_q0)
     if ws > 1:  # labels over the union of the ranks' q lists (outer argmin of Alg. 1)
-        bv, bq, omega_n = shard.local_candidates(res["omega_star"], res["omega_lo"], mine, qx == 0.0)
+        omega_n = shard.broadcast_normal_state(res["omega_lo"][0] if has_q0 else np.zeros(n_pts), src=0)
+        bv, bq = shard.local_candidates(res, mine, omega_n)
         labels, best = shard.gather_labels(bv, bq, omega_n)
         t = torch.tensor([t_total], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -421,18 +456,23 @@ def main():
     value = k_job * args.steps / t_total
     points_per_s = points_job * args.steps / t_total
 
-    # end to end through the host-buffer C ABI (inputs copied in, results copied out, every step)
+    # end to end through the host-buffer C ABI (inputs copied in, results copied out, every step;
+    # on several ranks each times its own part, the job's time is the slowest rank's)
     e2e_times = []
     for i in range(max(2, min(args.steps, 5))):
-        torch.cuda.synchronize()
+        barrier()
         t0 = time.perf_counter()
         full = ctx.phase_scan(cfg["N"], qx, qy, cfg["h"], cfg["T"], n=cfg["n"], lo=cfg["lo"], hi=cfg["hi"],
-                              stream=stream)
+                              stream=stream, labels=has_q0)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
     e2e_t = statistics.median(e2e_times[1:])
-    h2d = len(mine) * (cfg["n"] * 8 + n_pts * 24 + len(cfg["h"]) * 8 + 128)
-    d2h = len(mine) * n_pts * 40 + n_pts * 5
+    h2d = len(q_all) * (cfg["n"] * 8 + n_pts * 24 + len(cfg["h"]) * 8 + 128)
+    d2h = len(q_all) * n_pts * 40 + n_pts * 5
+    if ws > 1:
+        t = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_t = float(t.item())
 
     # FP64 plain kernel on a sample of the q list (it is ~60x slower)
     fp64 = None
@@ -453,13 +493,20 @@ def main():
         p64.destroy()
         ctx64.close()
 
-    extras = {}
+    # the Omega grids of two lines of the timed plan, for the oracle check of the CPU leg
+    check_lines = []
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        og = plan.fetch_grid(cfg["n"], stream)
+        for q, ih in ((5, 3), (0, 11)):
+            check_lines.append({"qx": float(qx[q]), "h": float(cfg["h"][ih]), "omega": og[q, ih],
+                                "idx_star": int(res["idx_star"][q, ih])})
+    extras, pd_check = {}, None
     if rank == 0 and not args.no_extras:
         extras = run_extras(ffe, np, torch, stream, workloads)
         if ws == 1:
-            pd_out, extras["surrogate"] = run_surrogate(ffe, np, torch, workloads, cfg, full, e2e_t,
-                                                        fp64["k_evals_per_s"] if fp64 else None,
-                                                        diagram=not args.no_diagram)
+            pd_check, pd_out, extras["surrogate"] = run_surrogate(ffe, np, torch, workloads, cfg, full, e2e_t,
+                                                                  fp64["k_evals_per_s"] if fp64 else None,
+                                                                  diagram=not args.no_diagram)
             if pd_out:
                 extras["phase_diagram"] = pd_out
 
@@ -478,16 +525,22 @@ def main():
                            + (1.0 - near_frac - fc_frac) * c_mom)
     peak = n_sm * SM_MAX_MHZ * 1e6 / clk_per_keval  # k-evals/s with the SFU saturated, at the maximum clock
     achieved = k_evals / (kern_ms / 1e3) if kern_ms > 0 else 0.0
+    # the algorithmic bound: every k-eval with its 10 transcendentals (2 sqrt + 4 exp + 4 log, both
+    # bands) at the SFU rates ffe_probe_peaks measures, or the FP32 pipe at ~50 operations
+    pk = ffe.ffe_probe_peaks()
+    sfu_bound = 1.0 / (4.0 / pk["ex2"] + 4.0 / pk["lg2"] + 2.0 / pk["rsqrt"])
+    fp32_bound = pk["fma32"] / 50.0
+    alg_peak = min(sfu_bound, fp32_bound)
 
     out = {
         "metric": METRIC, "value": value, "unit": "k-evals/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": arm_config(cfg, ws),
         "points_per_s": points_per_s,
-        "e2e": {"value": k_job / e2e_t if ws == 1 else None, "unit": "k-evals/s",
+        "e2e": {"value": k_job / e2e_t, "unit": "k-evals/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "points_per_s": (len(mine) * n_pts) / e2e_t},
+                "points_per_s": points_job / e2e_t},
         "gpu_launches": launches * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "k-evals/s (SFU-bound)",
                      "frac": achieved / peak if peak else None, "traffic": DRAM_TRAFFIC_PER_LAUNCH,
@@ -501,7 +554,17 @@ def main():
                                     f"+ {fc_frac:.4f} x {c_far:.4f} (far, R and a) + "
                                     f"{1 - near_frac - fc_frac:.4f} x {c_mom:.5f} (far, moments)); ex2 "
                                     f"{SFU_EX2_PER_CLK}/clk, lg2 rsqrt rcp {SFU_OTHER_PER_CLK}/clk per SM; unit "
-                                    f"counts checked by ffe_probe_peaks")},
+                                    f"counts checked by ffe_probe_peaks"),
+                     "frac_algorithmic": achieved / alg_peak,
+                     "peak_algorithmic": alg_peak,
+                     "peak_algorithmic_basis": (
+                         f"every k-eval with its 10 transcendentals (2 sqrt + 4 exp + 4 log) at the measured "
+                         f"SFU rates (ex2 {pk['ex2']:.3g}/s, lg2 {pk['lg2']:.3g}/s, rsqrt {pk['rsqrt']:.3g}/s: "
+                         f"{sfu_bound:.3g} k-evals/s), or the FP32 pipe at 50 operations ({fp32_bound:.3g}); "
+                         f"work-reduced: far bands skip the transcendentals (their log factors are exactly 1 in "
+                         f"FP32), so the kernel exceeds this bound"),
+                     "ncu": NCU_HEADLINE},
+        "fp64_reevals_per_step": {"search": pst["rescored_search"], "labels": pst["rescored_labels"]},
         "fp64": fp64,
         **extras,
         "clocks": clk,
@@ -509,7 +572,7 @@ def main():
                    "fflo": int((labels == 2).sum())},
     }
     if rank == 0 and ws == 1 and not args.no_cpu:
-        out["cpu_baseline"] = cpu_baseline(cfg)
+        out["cpu_baseline"] = cpu_baseline(cfg, check_lines, pd_check)
     if rank == 0:
         print(json.dumps(out), flush=True)
     plan.destroy()
@@ -551,7 +614,7 @@ def run_reference(args, cfg, ws, rank):
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "k-evals/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": arm_config(cfg, ws),
         "cpu_baseline": {"value": v, "unit": "k-evals/s", "cores": used, "kind": "oracle", "sample": desc},
         "e2e": {"value": v, "unit": "k-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
