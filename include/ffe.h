@@ -390,6 +390,14 @@ FFE_API void ffe_surrogate_destroy(ffe_surrogate* s);
 /* Replace the weights (resets the Adam moments). */
 FFE_API ffe_status ffe_surrogate_set_params(ffe_surrogate* s, const float* params);
 FFE_API ffe_status ffe_surrogate_get_params(ffe_surrogate* s, float* params);
+/* Checkpoint of the whole training state -- weights, Adam moments and step,
+ * input/output maps -- as host bytes: buf NULL returns the size in *bytes;
+ * otherwise *bytes is the buffer's size on entry and the bytes written on
+ * return.  Training resumed from a loaded checkpoint continues exactly as the
+ * saved one would have (the same bits).  load rejects a buffer that is not a
+ * checkpoint of this network (FFE_EINVAL). */
+FFE_API ffe_status ffe_surrogate_save(ffe_surrogate* s, void* buf, size_t* bytes);
+FFE_API ffe_status ffe_surrogate_load(ffe_surrogate* s, const void* buf, size_t bytes);
 /* y[n] = prediction at x[n][4] = (q, h, T, Delta). */
 FFE_API ffe_status ffe_surrogate_predict(ffe_surrogate* s, const float* x, int64_t n, float* y,
                                          void* stream);
@@ -411,8 +419,11 @@ FFE_API ffe_status ffe_surrogate_train(ffe_surrogate* s, const float* x, const f
  * the exact k-sum verifies q = 0 and the q_keep lines of lowest predicted
  * minimum (exact normal state + predicted condensation energy: on a finite
  * lattice the normal states of different q differ, and the labels compare
- * Omega across q), with a margin also every q within the margin of the
- * lowest, each on a window of `window` grid points around its predicted
+ * Omega across q), with a margin also every q predicted to condense by more
+ * than the margin whose predicted minimum is within the margin of the
+ * lowest and every q whose exact normal state lies more than the margin
+ * below that of q = 0 (any condensation would make it the winner), each on a
+ * window of `window` grid points around its predicted
  * minimum, with Delta = 0 as the reference (with the FP64 re-evaluation and
  * label passes of ffe_phase_scan).  Grid: the window's grid points.  Golden:
  * the window is the initial bracket and takes as many fewer reductions as
@@ -434,8 +445,11 @@ typedef struct {
                            swap within the surrogate's error, as at a
                            first-order transition) is searched over the
                            whole range instead, and beyond q_keep every q
-                           whose predicted minimum is within margin of the
-                           lowest one is kept too; 0: neither             */
+                           predicted to condense by more than margin whose
+                           predicted minimum is within margin of the lowest
+                           one, and every q whose exact normal state lies
+                           more than margin below that of q = 0, is kept
+                           too; 0: none of these                          */
 } ffe_guide;
 typedef struct {
   double k_evals;       /* exact k-point evaluations done (the normal state

@@ -6,7 +6,9 @@
 // evaluates every line's normal state (Delta = 0, one k-sum per line); per
 // (h, T) only q = 0 and the q_keep lines with the lowest predicted minimum
 // (exact normal state + predicted condensation energy; with a margin also
-// every q within the margin of the lowest) are verified by the exact k-sum,
+// every q predicted to condense by more than the margin within the margin of
+// the lowest, and every q whose exact normal state lies more than the margin
+// below that of q = 0) are verified by the exact k-sum,
 // each on a window of `window` grid points around its predicted
 // minimum, with Delta = 0 as the reference (same kernels, same FP64
 // re-evaluation of near ties, same label passes as the full scan).  A grid
@@ -317,13 +319,19 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
       std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pred_min(a, pt) < pred_min(b, pt); });
       kept[(size_t)q0 * n_pts + pt] = 1;
       for (int k = 0; k < (int)order.size() && k < guide->q_keep; ++k) kept[(size_t)order[k] * n_pts + pt] = 1;
-      // beyond q_keep: every q whose predicted minimum is within the margin of
-      // the lowest one (q = 0 included): the surrogate cannot order them
+      // beyond q_keep: every q predicted to condense by more than the margin
+      // whose predicted minimum is within the margin of the lowest one (q = 0
+      // included): the surrogate cannot order them; and every q whose exact
+      // normal state lies more than the margin below that of q = 0: any
+      // condensation, even one below the surrogate's resolution, makes it the
+      // winner (on a finite lattice the normal states of different q differ)
       if (guide->margin > 0.0 && !order.empty()) {
         const double best = std::min(pred_min(order[0], pt), pred_min(q0, pt));
+        const double normal0 = anchor[(size_t)q0 * n_pts + pt] / n2;
         for (int k = guide->q_keep; k < (int)order.size(); ++k) {
-          if (pred_min(order[k], pt) > best + guide->margin) break;
-          kept[(size_t)order[k] * n_pts + pt] = 1;
+          const size_t l = (size_t)order[k] * n_pts + pt;
+          const bool condenses = (double)ymin[l] * ys < -guide->margin && pred_min(order[k], pt) <= best + guide->margin;
+          if (condenses || anchor[l] / n2 < normal0 - guide->margin) kept[l] = 1;
         }
       }
     }

@@ -4,10 +4,19 @@
 // only proposes where the exact k-sum should look.)
 //
 // Precision: the two 128 x 128 layers multiply BF16 activations by BF16
-// weights on the tensor cores (mma.sync m16n8k16, FP32 accumulation); the
-// 4-wide input layer, the 1-wide output layer, SiLU, its derivative and the
-// loss are FP32.  Master weights and Adam moments are FP32.  Every reduction
-// over samples is a fixed-order sum of per-block partials (deterministic).
+// weights on the 5th-generation tensor cores (tcgen05.mma, kind::f16, FP32
+// accumulators in tensor memory); the 4-wide input layer, the 1-wide output
+// layer, SiLU, its derivative and the loss are FP32.  Master weights and Adam
+// moments are FP32.  Every reduction over samples is a fixed-order sum of
+// per-block partials (deterministic).
+//
+// One CTA of 128 threads owns 128 samples (the MMA's M): thread r owns sample
+// r, which is TMEM lane r of the accumulator (warp w reads lanes 32w..32w+31).
+// Each 128 x 128 product is eight K = 16 MMAs issued by one thread from two
+// shared-memory tiles (the activations and the weights) and committed to an
+// mbarrier; the weights' tiles arrive by one bulk asynchronous copy (TMA)
+// each.  Tiles are in the canonical K-major layout without swizzle: 8 x 16-byte
+// core matrices, 128 B apart along K and 2048 B apart along M/N.
 //
 // Flat parameter layout (33 793 floats): W1[4][128], b1[128], W2[128][128],
 // b2[128], W3[128][128], b3[128], W4[128], b4[1]; W[i][o] maps input i to
@@ -27,19 +36,23 @@
 namespace ffe {
 
 constexpr int kW = 128;       // layer width
-constexpr int kRows = 64;     // samples per block
-constexpr int kLdA = 136;     // padded row stride (bf16) of [rows][128] tiles
-constexpr int kLdT = 72;      // padded row stride (bf16) of transposed [128][64] tiles
+constexpr int kRows = 128;    // samples per block (the MMA's M)
+constexpr int kTile = kW * kW;  // bf16 elements of one 128 x 128 tile
+constexpr int kTileBytes = kTile * 2;
 constexpr int kOffW1 = 0, kOffB1 = 512, kOffW2 = 640, kOffB2 = 17024, kOffW3 = 17152, kOffB3 = 33536,
               kOffW4 = 33664, kOffB4 = 33792, kNParams = 33793;
+constexpr int kPartStride = 33796;  // floats per block of gradient partials (16-byte rows)
+// BF16 weight tiles (global, each in the MMA layout): the B operands of the
+// forward products (n = out, k = in) and of the data-gradient products
+// (n = in, k = out)
+enum { kT2f = 0, kT3f = 1, kT2b = 2, kT3b = 3 };
+constexpr unsigned kWaitLimit = 1u << 26;  // polls of an mbarrier before giving up
 
 struct MlpDev {
   const float* master;          // FP32 parameters (layout above)
-  const __nv_bfloat16* w2t;     // W2 transposed [out][in]
-  const __nv_bfloat16* w3t;     // W3 transposed [out][in]
-  const __nv_bfloat16* w2n;     // W2 [in][out]
-  const __nv_bfloat16* w3n;     // W3 [in][out]
+  const __nv_bfloat16* tiles;   // the four weight tiles
   float shift[4], scale[4];
+  int32_t* status;              // set to 1 when a wait gave up
 };
 
 __device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + __expf(-z)); }
@@ -49,270 +62,372 @@ __device__ __forceinline__ float silu_primef_(float z) {
   return s * (1.0f + z * (1.0f - s));
 }
 
-__device__ __forceinline__ uint32_t ld32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+// Byte offset of element (r, k) of a 128 x 128 BF16 tile in the K-major
+// no-swizzle layout: core matrix (r / 8, k / 8), 16-byte rows inside it.
+__host__ __device__ __forceinline__ uint32_t tile_off(int r, int k) {
+  return (uint32_t)((((r >> 3) << 4) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1);
+}
 
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+// ---- tcgen05 / mbarrier helpers (inline PTX) ---------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start address, leading (K) byte offset 128,
+// stride (M/N) byte offset 2048, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t tile_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(2048 >> 4) << 32) |
+         (1ull << 46);
+}
+
+// Instruction descriptor: D FP32, A and B BF16, both K-major, N = 128, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+// Bounded wait on a phase of an mbarrier; false when it gave up (status set).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int32_t* status) {
+  uint32_t done = 0;
+  for (unsigned it = 0; it < kWaitLimit; ++it) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity));
+    if (done) return true;
+  }
+  atomicOr(status, 1);
+  return false;
+}
+
+// One 32 KB weight tile from global memory by the bulk copy engine, completing
+// on bar (whose expected transaction bytes the caller has set).
+__device__ __forceinline__ void tile_load_async(void* dst, const void* src, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(kTileBytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes));
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot) {  // one warp
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_addr(slot)));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_free(uint32_t tmem) {  // the same warp
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+}
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;"); }
+// Generic-proxy writes of shared memory made visible to the tensor cores.
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// D[128 x 128] (TMEM) = A[128 x 128] * B[128 x 128]^T from two K-major tiles;
+// one thread issues, the commit arrives on bar when the products are done.
+__device__ __forceinline__ void mma_tile(uint32_t tmem, const void* a, const void* b, uint64_t* bar) {
+  const uint32_t a0 = smem_addr(a), b0 = smem_addr(b);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const uint64_t ad = tile_desc(a0 + k * 256), bd = tile_desc(b0 + k * 256);  // K = 16: two core matrices
+    const uint32_t acc = k > 0 ? 1u : 0u;
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+  }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar)));
+}
+
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_row32(uint32_t tmem, int c0, float (&v)[32]) {
+  const uint32_t ta = tmem + ((uint32_t)((threadIdx.x >> 5) * 32) << 16) + (uint32_t)c0;
+  uint32_t r[32];
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(ta));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// Block-level C[M x 128] = A[M x K] * B[K x 128] with 4 warps; A stored [m][k]
-// (stride lda), B stored transposed Bt[n][k] (stride ldb); M = 64 * MT.
-// Warp w owns rows [16 MT w, 16 MT (w+1)).  acc[mt][nt][.] follows the
-// m16n8 accumulator layout: rows g, g+8 of the tile, columns 2t, 2t+1.
-template <int MT>
-__device__ __forceinline__ void gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* Bt, int ldb, int K,
-                                          float (&acc)[MT][16][4]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
+// Eight values of row r, columns c0..c0+7 (c0 % 8 == 0), into a tile: one 16-byte store.
+__device__ __forceinline__ void tile_store8(unsigned char* tile, int r, int c0, const float* v) {
+  __align__(16) __nv_bfloat162 p[4];
 #pragma unroll
-  for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 16; ++nt)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.0f;
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    uint32_t a[MT][4];
-#pragma unroll
-    for (int mt = 0; mt < MT; ++mt) {
-      const int r = (warp * MT + mt) * 16 + g;
-      a[mt][0] = ld32(A + r * lda + k0 + 2 * t);
-      a[mt][1] = ld32(A + (r + 8) * lda + k0 + 2 * t);
-      a[mt][2] = ld32(A + r * lda + k0 + 2 * t + 8);
-      a[mt][3] = ld32(A + (r + 8) * lda + k0 + 2 * t + 8);
-    }
-#pragma unroll
-    for (int nt = 0; nt < 16; ++nt) {
-      const int n = nt * 8 + g;
-      const uint32_t b0 = ld32(Bt + n * ldb + k0 + 2 * t);
-      const uint32_t b1 = ld32(Bt + n * ldb + k0 + 2 * t + 8);
-#pragma unroll
-      for (int mt = 0; mt < MT; ++mt) mma_bf16(acc[mt][nt], a[mt], b0, b1);
-    }
-  }
+  for (int j = 0; j < 4; ++j) p[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+  *reinterpret_cast<uint4*>(tile + tile_off(r, c0)) = *reinterpret_cast<const uint4*>(p);
 }
 
-// Copy a [128][128] BF16 matrix from global into a padded shared tile.
-__device__ __forceinline__ void load_w(__nv_bfloat16* dst, const __nv_bfloat16* src) {
-  for (int i = threadIdx.x; i < kW * kW / 2; i += blockDim.x) {
-    const int r = (2 * i) / kW, c = (2 * i) % kW;
-    *reinterpret_cast<uint32_t*>(dst + r * kLdA + c) = reinterpret_cast<const uint32_t*>(src)[i];
-  }
+// The MMA of one layer and the wait for it, with the fences that order it
+// after the threads' tile writes and TMEM reads.  Returns false if the wait
+// gave up.
+__device__ __forceinline__ bool layer_mma(uint32_t tmem, const void* a, const void* b, uint64_t* bar,
+                                          uint32_t parity, int32_t* status) {
+  proxy_fence();
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  if (threadIdx.x == 0) mma_tile(tmem, a, b, bar);
+  const bool ok = mbar_wait(bar, parity, status);
+  tc_after_sync();
+  return ok;
 }
 
-// Forward pass of up to 64 samples per block.  With Z/H non-NULL it also
-// keeps the pre-activations z1..z3 (FP32) and activations h1, h2 (BF16) for
-// the backward pass.
+// Shared-memory plan of the kernels: up to three tiles, then the barriers, the
+// TMEM address and small FP32 parameters.
+constexpr size_t kSmemTiles3 = 3 * (size_t)kTileBytes;
+constexpr size_t kSmemExtra = 64 + 4 * 1088;
+constexpr size_t kSmemFwd = kSmemTiles3 + kSmemExtra;
+constexpr size_t kSmemBwdData = kSmemTiles3 + kSmemExtra;
+constexpr size_t kSmemBwdW = 2 * (size_t)kTileBytes + kSmemExtra;
+
+struct Bars {
+  uint64_t w, mma;
+  uint32_t tmem;
+  int32_t ok;
+};
+
+// Forward pass of up to 128 samples per block.  With Z/H non-NULL it also
+// keeps the pre-activations z1..z3 (FP32) and activations h1, h2 (BF16), each
+// as [layer][feature][ld] (ld >= the rows of every block, a multiple of 128)
+// for the backward pass; rows of the block at or beyond n are computed from
+// x = 0 and kept too (the backward pass gives them zero weight).
 __global__ void __launch_bounds__(128) mlp_fwd_kernel(const MlpDev P, const float* __restrict__ xraw, int64_t n,
-                                                      float* y, float* Z, __nv_bfloat16* H) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  float* X = reinterpret_cast<float*>(sm);                                   // [64][4]
-  __nv_bfloat16* Ha = reinterpret_cast<__nv_bfloat16*>(sm + 64 * 4 * 4);     // [64][136]
-  __nv_bfloat16* Hb = Ha + kRows * kLdA;                                      // [64][136]
-  __nv_bfloat16* Ws = Hb + kRows * kLdA;                                      // [128][136]
-  const int64_t row0 = (int64_t)blockIdx.x * kRows;
+                                                      float* y, float* Z, __nv_bfloat16* H, int64_t ld) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char* T2 = sm;
+  unsigned char* T3 = sm + kTileBytes;
+  unsigned char* Ht = sm + 2 * kTileBytes;
+  Bars* bars = reinterpret_cast<Bars*>(sm + kSmemTiles3);
+  float* prm = reinterpret_cast<float*>(sm + kSmemTiles3 + 64);  // W1 (512), b1, b2, b3, W4 (128 each), b4
   const int tid = threadIdx.x;
-  for (int i = tid; i < kRows * 4; i += blockDim.x) {
-    const int r = i / 4, f = i % 4;
-    const int64_t row = row0 + r;
-    X[i] = row < n ? (xraw[row * 4 + f] - P.shift[f]) * P.scale[f] : 0.0f;
+  if (tid == 0) {
+    mbar_init(&bars->w, 1);
+    mbar_init(&bars->mma, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    expect_tx(&bars->w, 2 * kTileBytes);
+    tile_load_async(T2, P.tiles + kT2f * kTile, &bars->w);
+    tile_load_async(T3, P.tiles + kT3f * kTile, &bars->w);
   }
+  if (tid < 32) tmem_alloc(&bars->tmem);
+  for (int i = tid; i < 512; i += 128) prm[i] = P.master[kOffW1 + i];
+  prm[512 + tid] = P.master[kOffB1 + tid];
+  prm[640 + tid] = P.master[kOffB2 + tid];
+  prm[768 + tid] = P.master[kOffB3 + tid];
+  prm[896 + tid] = P.master[kOffW4 + tid];
+  if (tid == 0) prm[1024] = P.master[kOffB4];
+  tc_before_sync();
   __syncthreads();
-  {  // layer 1 in FP32: thread = output column
-    const int c = tid;
-    const float w0 = P.master[kOffW1 + 0 * kW + c], w1 = P.master[kOffW1 + 1 * kW + c];
-    const float w2 = P.master[kOffW1 + 2 * kW + c], w3 = P.master[kOffW1 + 3 * kW + c];
-    const float b = P.master[kOffB1 + c];
-    for (int r = 0; r < kRows; ++r) {
-      const float z = fmaf(X[r * 4 + 0], w0, fmaf(X[r * 4 + 1], w1, fmaf(X[r * 4 + 2], w2, fmaf(X[r * 4 + 3], w3, b))));
-      const __nv_bfloat16 hb = __float2bfloat16(siluf_(z));
-      Ha[r * kLdA + c] = hb;
-      const int64_t row = row0 + r;
-      if (Z && row < n) {
-        Z[(0 * n + row) * kW + c] = z;
-        H[(0 * n + row) * kW + c] = hb;
+  tc_after_sync();
+  const uint32_t tmem = bars->tmem;
+  const int64_t row = (int64_t)blockIdx.x * kRows + tid;
+  const bool live = row < n;
+  float x[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) x[f] = live ? (xraw[row * 4 + f] - P.shift[f]) * P.scale[f] : 0.0f;
+  // layer 1 in FP32 (thread = sample)
+  for (int c0 = 0; c0 < kW; c0 += 8) {
+    float h[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = c0 + j;
+      const float z = fmaf(x[0], prm[c], fmaf(x[1], prm[128 + c], fmaf(x[2], prm[256 + c],
+                                                                         fmaf(x[3], prm[384 + c], prm[512 + c]))));
+      h[j] = siluf_(z);
+      if (Z) {
+        Z[(0 * kW + c) * ld + row] = z;
+        H[(0 * kW + c) * ld + row] = __float2bfloat16(h[j]);
       }
     }
+    tile_store8(Ht, tid, c0, h);
   }
-  load_w(Ws, P.w2t);
-  __syncthreads();
-  const int lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
-  {  // layer 2: tensor cores
-    float acc[1][16][4];
-    gemm_bf16<1>(Ha, kLdA, Ws, kLdA, kW, acc);
+  if (tid == 0) bars->ok = mbar_wait(&bars->w, 0, P.status) ? 1 : 0;  // the weight tiles are in
+  bool ok = layer_mma(tmem, Ht, T2, &bars->mma, 0, P.status) && bars->ok;
+  // layer 2 epilogue: bias, SiLU, next layer's A tile
+  for (int c0 = 0; c0 < kW; c0 += 32) {
+    float v[32];
+    tmem_row32(tmem, c0, v);
 #pragma unroll
-    for (int nt = 0; nt < 16; ++nt)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int r = warp * 16 + g + (i >= 2 ? 8 : 0), c = nt * 8 + 2 * t + (i & 1);
-        const float z = acc[0][nt][i] + P.master[kOffB2 + c];
-        const __nv_bfloat16 hb = __float2bfloat16(siluf_(z));
-        Hb[r * kLdA + c] = hb;
-        const int64_t row = row0 + r;
-        if (Z && row < n) {
-          Z[(1 * n + row) * kW + c] = z;
-          H[(1 * n + row) * kW + c] = hb;
-        }
+    for (int j = 0; j < 32; ++j) {
+      const int c = c0 + j;
+      const float z = v[j] + prm[640 + c];
+      v[j] = siluf_(z);
+      if (Z) {
+        Z[(1 * kW + c) * ld + row] = z;
+        H[(1 * kW + c) * ld + row] = __float2bfloat16(v[j]);
       }
+    }
+#pragma unroll
+    for (int j = 0; j < 32; j += 8) tile_store8(Ht, tid, c0 + j, v + j);
   }
-  __syncthreads();
-  load_w(Ws, P.w3t);
-  __syncthreads();
-  {  // layer 3 and the output layer
-    float acc[1][16][4];
-    gemm_bf16<1>(Hb, kLdA, Ws, kLdA, kW, acc);
-    float s0 = 0.0f, s1 = 0.0f;  // rows g and g + 8 of this warp's tile
+  ok = layer_mma(tmem, Ht, T3, &bars->mma, 1, P.status) && ok;
+  // layer 3 epilogue and the output layer
+  float acc = 0.0f;
+  for (int c0 = 0; c0 < kW; c0 += 32) {
+    float v[32];
+    tmem_row32(tmem, c0, v);
 #pragma unroll
-    for (int nt = 0; nt < 16; ++nt)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int r = warp * 16 + g + (i >= 2 ? 8 : 0), c = nt * 8 + 2 * t + (i & 1);
-        const float z = acc[0][nt][i] + P.master[kOffB3 + c];
-        const int64_t row = row0 + r;
-        if (Z && row < n) Z[(2 * n + row) * kW + c] = z;
-        const float hw = siluf_(z) * P.master[kOffW4 + c];
-        if (i < 2)
-          s0 += hw;
-        else
-          s1 += hw;
-      }
-    s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-    s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
-    s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
-    s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
-    if (t == 0) {
-      const int64_t ra = row0 + warp * 16 + g, rb = ra + 8;
-      const float b4 = P.master[kOffB4];
-      if (ra < n) y[ra] = s0 + b4;
-      if (rb < n) y[rb] = s1 + b4;
+    for (int j = 0; j < 32; ++j) {
+      const int c = c0 + j;
+      const float z = v[j] + prm[768 + c];
+      if (Z) Z[(2 * kW + c) * ld + row] = z;
+      acc = fmaf(siluf_(z), prm[896 + c], acc);
     }
   }
+  if (live) y[row] = ok ? acc + prm[1024] : NAN;
+  tc_before_sync();
+  __syncthreads();
+  if (tid < 32) tmem_free(tmem);
 }
 
-// Backward pass through the layers (data gradients), 64 samples per block:
+// Backward pass through the layers (data gradients), 128 samples per block:
 // dz3 = dy W4 s'(z3), dz2 = (dz3 W3^T) s'(z2), dz1 = (dz2 W2^T) s'(z1).
 // dy = 2 (y - t) / B for the mean squared error over a batch of B samples.
+// dZ is written for every row of the block (zero at and beyond n).
 __global__ void __launch_bounds__(128) mlp_bwd_data_kernel(const MlpDev P, const float* __restrict__ y,
                                                            const float* __restrict__ tgt, float inv_yscale, int64_t n,
                                                            float two_over_b, const float* __restrict__ Z, float* dZ,
-                                                           float* dy_out, double* loss_part) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  float* dy = reinterpret_cast<float*>(sm);                                  // [64]
-  __nv_bfloat16* Da = reinterpret_cast<__nv_bfloat16*>(sm + 64 * 4);        // [64][136]
-  __nv_bfloat16* Ws = Da + kRows * kLdA;                                     // [128][136]
-  const int64_t row0 = (int64_t)blockIdx.x * kRows;
+                                                           float* dy_out, double* loss_part, int64_t ld) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char* T3 = sm;                    // B of dz2 = dz3 W3^T: (n = in, k = out)
+  unsigned char* T2 = sm + kTileBytes;       // B of dz1 = dz2 W2^T
+  unsigned char* Dt = sm + 2 * kTileBytes;   // the data gradient of the current layer, A
+  Bars* bars = reinterpret_cast<Bars*>(sm + kSmemTiles3);
+  float* red = reinterpret_cast<float*>(sm + kSmemTiles3 + 64);  // [128] squared residuals
   const int tid = threadIdx.x;
-  if (tid < kRows) {
-    const int64_t row = row0 + tid;
-    float r = 0.0f;
-    if (row < n) r = y[row] - tgt[row] * inv_yscale;
-    dy[tid] = two_over_b * r;
-    if (row < n) dy_out[row] = two_over_b * r;
-    // per-block sum of squared residuals (fixed order: thread 0 adds below)
-    reinterpret_cast<float*>(Ws)[tid] = r * r;
-  }
-  __syncthreads();
   if (tid == 0) {
+    mbar_init(&bars->w, 1);
+    mbar_init(&bars->mma, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    expect_tx(&bars->w, 2 * kTileBytes);
+    tile_load_async(T3, P.tiles + kT3b * kTile, &bars->w);
+    tile_load_async(T2, P.tiles + kT2b * kTile, &bars->w);
+  }
+  if (tid < 32) tmem_alloc(&bars->tmem);
+  const int64_t row = (int64_t)blockIdx.x * kRows + tid;
+  const bool live = row < n;
+  const float r = live ? y[row] - tgt[row] * inv_yscale : 0.0f;
+  const float dy = two_over_b * r;
+  if (live) dy_out[row] = dy;
+  red[tid] = r * r;
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  if (tid == 0) {  // per-block sum of squared residuals, fixed order
     double s = 0.0;
-    for (int i = 0; i < kRows; ++i) s += reinterpret_cast<float*>(Ws)[i];
+    for (int i = 0; i < kRows; ++i) s += red[i];
     loss_part[blockIdx.x] = s;
   }
-  __syncthreads();
-  {  // dz3 = dy W4 s'(z3)
-    const int c = tid;
-    const float w4 = P.master[kOffW4 + c];
-    for (int r = 0; r < kRows; ++r) {
-      const int64_t row = row0 + r;
-      float d = 0.0f;
-      if (row < n) {
-        d = dy[r] * w4 * silu_primef_(Z[(2 * n + row) * kW + c]);
-        dZ[(2 * n + row) * kW + c] = d;
+  const uint32_t tmem = bars->tmem;
+  for (int c0 = 0; c0 < kW; c0 += 8) {  // dz3 = dy W4 s'(z3)
+    float d[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = c0 + j;
+      d[j] = live ? dy * P.master[kOffW4 + c] * silu_primef_(Z[(2 * kW + c) * ld + row]) : 0.0f;
+      dZ[(2 * kW + c) * ld + row] = d[j];
+    }
+    tile_store8(Dt, tid, c0, d);
+  }
+  if (tid == 0) bars->ok = mbar_wait(&bars->w, 0, P.status) ? 1 : 0;
+  bool ok = true;
+  for (int layer = 1; layer >= 0; --layer) {
+    ok = layer_mma(tmem, Dt, layer == 1 ? T3 : T2, &bars->mma, layer == 1 ? 0 : 1, P.status) && bars->ok && ok;
+    for (int c0 = 0; c0 < kW; c0 += 32) {
+      float v[32];
+      tmem_row32(tmem, c0, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int c = c0 + j;
+        v[j] = live ? (ok ? v[j] : NAN) * silu_primef_(Z[(layer * kW + c) * ld + row]) : 0.0f;
+        dZ[(layer * kW + c) * ld + row] = v[j];
       }
-      Da[r * kLdA + c] = __float2bfloat16(d);
+      if (layer == 1) {
+#pragma unroll
+        for (int j = 0; j < 32; j += 8) tile_store8(Dt, tid, c0 + j, v + j);
+      }
     }
   }
-  load_w(Ws, P.w3n);  // B[k = out][n = in] = W3[in][out]: the natural layout is Bt
+  tc_before_sync();
   __syncthreads();
-  const int lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
-  for (int layer = 1; layer >= 0; --layer) {
-    float acc[1][16][4];
-    gemm_bf16<1>(Da, kLdA, Ws, kLdA, kW, acc);
-    __syncthreads();
-#pragma unroll
-    for (int nt = 0; nt < 16; ++nt)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int r = warp * 16 + g + (i >= 2 ? 8 : 0), c = nt * 8 + 2 * t + (i & 1);
-        const int64_t row = row0 + r;
-        float d = 0.0f;
-        if (row < n) {
-          d = acc[0][nt][i] * silu_primef_(Z[(layer * n + row) * kW + c]);
-          dZ[(layer * n + row) * kW + c] = d;
-        }
-        Da[r * kLdA + c] = __float2bfloat16(d);
-      }
-    if (layer == 1) load_w(Ws, P.w2n);
-    __syncthreads();
-  }
+  if (tid < 32) tmem_free(tmem);
 }
 
-// Weight gradients of the two 128 x 128 layers for 64 samples:
-// dW2 = h1^T dz2 (blockIdx.y = 0), dW3 = h2^T dz3 (blockIdx.y = 1).
-__global__ void __launch_bounds__(128) mlp_bwd_weight_kernel(const __nv_bfloat16* __restrict__ H,
-                                                             const float* __restrict__ dZ, int64_t n, float* part) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  __nv_bfloat16* At = reinterpret_cast<__nv_bfloat16*>(sm);  // [128][72]: h^T
-  __nv_bfloat16* Bt = At + kW * kLdT;                         // [128][72]: dz^T
-  const int L = blockIdx.y;
+// Weight gradients of the two 128 x 128 layers for 128 samples:
+// dW2 = h1^T dz2 (blockIdx.y = 0), dW3 = h2^T dz3 (blockIdx.y = 1), as
+// D[i][o] = sum_s A[i][s] B[o][s] with A = h^T, B = dz^T (both K-major in s).
+__global__ void __launch_bounds__(128) mlp_bwd_weight_kernel(const MlpDev P, const __nv_bfloat16* __restrict__ H,
+                                                             const float* __restrict__ dZ, float* part, int64_t ld) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char* At = sm;
+  unsigned char* Bt = sm + kTileBytes;
+  Bars* bars = reinterpret_cast<Bars*>(sm + 2 * kTileBytes);
+  const int L = blockIdx.y, tid = threadIdx.x;
   const int64_t row0 = (int64_t)blockIdx.x * kRows;
-  for (int i = threadIdx.x; i < kRows * kW; i += blockDim.x) {
-    const int r = i / kW, c = i % kW;
-    const int64_t row = row0 + r;
-    const bool ok = row < n;
-    At[c * kLdT + r] = ok ? H[((int64_t)L * n + row) * kW + c] : __float2bfloat16(0.0f);
-    Bt[c * kLdT + r] = __float2bfloat16(ok ? dZ[((int64_t)(L + 1) * n + row) * kW + c] : 0.0f);
+  if (tid == 0) {
+    mbar_init(&bars->mma, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
   }
+  if (tid < 32) tmem_alloc(&bars->tmem);
+  // rows i of A (features) and o of B: 8 consecutive samples per 16-byte store
+  for (int e = tid; e < kW * (kRows / 8); e += 128) {
+    const int f = e / (kRows / 8), s0 = (e % (kRows / 8)) * 8;
+    *reinterpret_cast<uint4*>(At + tile_off(f, s0)) =
+        *reinterpret_cast<const uint4*>(H + ((int64_t)L * kW + f) * ld + row0 + s0);
+    const float4 a = *reinterpret_cast<const float4*>(dZ + ((int64_t)(L + 1) * kW + f) * ld + row0 + s0);
+    const float4 b = *reinterpret_cast<const float4*>(dZ + ((int64_t)(L + 1) * kW + f) * ld + row0 + s0 + 4);
+    const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    tile_store8(Bt, f, s0, v);
+  }
+  tc_before_sync();
   __syncthreads();
-  float acc[2][16][4];
-  gemm_bf16<2>(At, kLdT, Bt, kLdT, kRows, acc);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-  float* dst = part + (int64_t)blockIdx.x * kNParams + (L == 0 ? kOffW2 : kOffW3);
+  tc_after_sync();
+  const uint32_t tmem = bars->tmem;
+  const bool ok = layer_mma(tmem, At, Bt, &bars->mma, 0, P.status);
+  float* dst = part + (int64_t)blockIdx.x * kPartStride + (L == 0 ? kOffW2 : kOffW3) + (int64_t)tid * kW;
+  for (int c0 = 0; c0 < kW; c0 += 32) {
+    float v[32];
+    tmem_row32(tmem, c0, v);
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 16; ++nt)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int m = (warp * 2 + mt) * 16 + g + (i >= 2 ? 8 : 0), c = nt * 8 + 2 * t + (i & 1);
-        dst[m * kW + c] = acc[mt][nt][i];
-      }
+    for (int j = 0; j < 32; j += 4)
+      *reinterpret_cast<float4*>(dst + c0 + j) =
+          ok ? make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]) : make_float4(NAN, NAN, NAN, NAN);
+  }
+  tc_before_sync();
+  __syncthreads();
+  if (tid < 32) tmem_free(tmem);
 }
 
-// The thin parts of the gradient for 64 samples: dW1 = x^T dz1, biases,
+// The thin parts of the gradient for 128 samples: dW1 = x^T dz1, biases,
 // dW4 = h3^T dy, db4 = sum dy (thread = column).
 __global__ void __launch_bounds__(128) mlp_bwd_small_kernel(const MlpDev P, const float* __restrict__ xraw,
                                                             const float* __restrict__ Z, const float* __restrict__ dZ,
-                                                            const float* __restrict__ dyv, int64_t n, float* part) {
+                                                            const float* __restrict__ dyv, int64_t n, float* part,
+                                                            int64_t ld) {
   const int c = threadIdx.x;
   const int64_t row0 = (int64_t)blockIdx.x * kRows;
   float gw1[4] = {0, 0, 0, 0}, gb1 = 0, gb2 = 0, gb3 = 0, gw4 = 0, gb4 = 0;
   for (int r = 0; r < kRows; ++r) {
     const int64_t row = row0 + r;
     if (row >= n) break;
-    const float d1 = dZ[(0 * n + row) * kW + c];
+    const float d1 = dZ[(0 * kW + c) * ld + row];
 #pragma unroll
     for (int f = 0; f < 4; ++f) gw1[f] += (xraw[row * 4 + f] - P.shift[f]) * P.scale[f] * d1;
     gb1 += d1;
-    gb2 += dZ[(1 * n + row) * kW + c];
-    gb3 += dZ[(2 * n + row) * kW + c];
+    gb2 += dZ[(1 * kW + c) * ld + row];
+    gb3 += dZ[(2 * kW + c) * ld + row];
     const float dy = dyv[row];
-    gw4 += siluf_(Z[(2 * n + row) * kW + c]) * dy;
+    gw4 += siluf_(Z[(2 * kW + c) * ld + row]) * dy;
     gb4 += dy;
   }
-  float* dst = part + (int64_t)blockIdx.x * kNParams;
+  float* dst = part + (int64_t)blockIdx.x * kPartStride;
 #pragma unroll
   for (int f = 0; f < 4; ++f) dst[kOffW1 + f * kW + c] = gw1[f];
   dst[kOffB1 + c] = gb1;
@@ -322,16 +437,22 @@ __global__ void __launch_bounds__(128) mlp_bwd_small_kernel(const MlpDev P, cons
   if (c == 0) dst[kOffB4] = gb4;
 }
 
+// The weight tiles of W2 / W3 element (in, out) in the MMA layout.
+__device__ __forceinline__ void put_weight(__nv_bfloat16* tiles, int layer3, int in, int out, float w) {
+  const __nv_bfloat16 b = __float2bfloat16(w);
+  tiles[(layer3 ? kT3f : kT2f) * kTile + tile_off(out, in) / 2] = b;  // forward: n = out, k = in
+  tiles[(layer3 ? kT3b : kT2b) * kTile + tile_off(in, out) / 2] = b;  // backward: n = in, k = out
+}
+
 // Sum the per-block partials (fixed order); optionally write the gradient;
-// optionally take an Adam step and refresh the BF16 copies.
+// optionally take an Adam step and refresh the BF16 tiles.
 __global__ void mlp_reduce_kernel(const float* __restrict__ part, int n_blocks, float* grad, float* master, float* m,
                                   float* v, float lr, float beta1, float beta2, float eps, float bc1, float bc2,
-                                  int do_step, __nv_bfloat16* w2t, __nv_bfloat16* w3t, __nv_bfloat16* w2n,
-                                  __nv_bfloat16* w3n) {
+                                  int do_step, __nv_bfloat16* tiles) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kNParams) return;
   float gsum = 0.0f;
-  for (int b = 0; b < n_blocks; ++b) gsum += part[(int64_t)b * kNParams + i];
+  for (int b = 0; b < n_blocks; ++b) gsum += part[(int64_t)b * kPartStride + i];
   if (grad) grad[i] = gsum;
   if (!do_step) return;
   const float mi = beta1 * m[i] + (1.0f - beta1) * gsum;
@@ -341,31 +462,29 @@ __global__ void mlp_reduce_kernel(const float* __restrict__ part, int n_blocks, 
   const float w = master[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
   master[i] = w;
   if (i >= kOffW2 && i < kOffW2 + kW * kW) {
-    const int j = i - kOffW2, in = j / kW, out = j % kW;
-    w2n[in * kW + out] = __float2bfloat16(w);
-    w2t[out * kW + in] = __float2bfloat16(w);
+    const int j = i - kOffW2;
+    put_weight(tiles, 0, j / kW, j % kW, w);
   } else if (i >= kOffW3 && i < kOffW3 + kW * kW) {
-    const int j = i - kOffW3, in = j / kW, out = j % kW;
-    w3n[in * kW + out] = __float2bfloat16(w);
-    w3t[out * kW + in] = __float2bfloat16(w);
+    const int j = i - kOffW3;
+    put_weight(tiles, 1, j / kW, j % kW, w);
   }
 }
 
-// BF16 copies of W2 and W3 from the master weights.
-__global__ void mlp_copies_kernel(const float* master, __nv_bfloat16* w2t, __nv_bfloat16* w3t, __nv_bfloat16* w2n,
-                                  __nv_bfloat16* w3n) {
+// BF16 tiles of W2 and W3 from the master weights.
+__global__ void mlp_copies_kernel(const float* master, __nv_bfloat16* tiles) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= kW * kW) return;
-  const int in = j / kW, out = j % kW;
-  w2n[j] = __float2bfloat16(master[kOffW2 + j]);
-  w3n[j] = __float2bfloat16(master[kOffW3 + j]);
-  w2t[out * kW + in] = w2n[j];
-  w3t[out * kW + in] = w3n[j];
+  put_weight(tiles, 0, j / kW, j % kW, master[kOffW2 + j]);
+  put_weight(tiles, 1, j / kW, j % kW, master[kOffW3 + j]);
 }
 
-constexpr size_t kSmemFwd = 64 * 4 * 4 + 2 * kRows * kLdA * 2 + kW * kLdA * 2;
-constexpr size_t kSmemBwdData = 64 * 4 + kRows * kLdA * 2 + kW * kLdA * 2;
-constexpr size_t kSmemBwdW = 2 * kW * kLdT * 2;
+// Adds a step's loss partials (fixed order) to the epoch's total.
+__global__ void mlp_loss_kernel(const double* __restrict__ loss_part, int n_blocks, double* total) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = 0; b < n_blocks; ++b) s += loss_part[b];
+  *total += s;
+}
 
 }  // namespace ffe
 
@@ -378,10 +497,13 @@ struct ffe_surrogate {
   float* master = nullptr;
   float* m = nullptr;
   float* v = nullptr;
-  __nv_bfloat16* wcopies = nullptr;  // w2t, w3t, w2n, w3n
+  __nv_bfloat16* tiles = nullptr;  // the BF16 weight tiles in the MMA layout (kT2f, kT3f, kT2b, kT3b)
+  int32_t* status = nullptr;       // device word: a kernel's wait gave up
+  double* epoch_loss = nullptr;    // device: per-epoch loss totals of a training call
+  int32_t epoch_cap = 0;
   int64_t adam_t = 0;
-  // training scratch, sized for `cap` samples
-  int64_t cap = 0;
+  // training scratch, sized for `cap` samples; per-sample arrays [layer][feature][ld]
+  int64_t cap = 0, ld = 0;
   float *x = nullptr, *t = nullptr, *y = nullptr, *Z = nullptr, *dZ = nullptr, *dy = nullptr, *part = nullptr;
   double* loss_part = nullptr;
   __nv_bfloat16* H = nullptr;
@@ -394,10 +516,8 @@ namespace {
 MlpDev make_dev(const ffe_surrogate* s) {
   MlpDev P;
   P.master = s->master;
-  P.w2t = s->wcopies;
-  P.w3t = s->wcopies + kW * kW;
-  P.w2n = s->wcopies + 2 * kW * kW;
-  P.w3n = s->wcopies + 3 * kW * kW;
+  P.tiles = s->tiles;
+  P.status = s->status;
   for (int f = 0; f < 4; ++f) {
     P.shift[f] = s->meta.shift[f];
     P.scale[f] = s->meta.scale[f];
@@ -421,20 +541,23 @@ void free_scratch(ffe_surrogate* s) {
   s->loss_part = nullptr;
   s->H = nullptr;
   s->cap = 0;
+  s->ld = 0;
 }
 
 ffe_status ensure_scratch(ffe_surrogate* s, int64_t n) {
   if (n <= s->cap) return FFE_OK;
   free_scratch(s);
   const int64_t nb = (n + kRows - 1) / kRows;
+  const int64_t ld = nb * kRows;  // rows of the per-sample arrays: every block's, padded
   SUR_CU(cudaMalloc(&s->x, n * 4 * sizeof(float)), "cudaMalloc");
   SUR_CU(cudaMalloc(&s->t, n * sizeof(float)), "cudaMalloc");
   SUR_CU(cudaMalloc(&s->y, n * sizeof(float)), "cudaMalloc");
   SUR_CU(cudaMalloc(&s->dy, n * sizeof(float)), "cudaMalloc");
-  SUR_CU(cudaMalloc(&s->Z, 3 * n * kW * sizeof(float)), "cudaMalloc");
-  SUR_CU(cudaMalloc(&s->dZ, 3 * n * kW * sizeof(float)), "cudaMalloc");
-  SUR_CU(cudaMalloc(&s->H, 2 * n * kW * sizeof(__nv_bfloat16)), "cudaMalloc");
-  SUR_CU(cudaMalloc(&s->part, nb * kNParams * sizeof(float)), "cudaMalloc");
+  SUR_CU(cudaMalloc(&s->Z, 3 * ld * kW * sizeof(float)), "cudaMalloc");
+  SUR_CU(cudaMalloc(&s->dZ, 3 * ld * kW * sizeof(float)), "cudaMalloc");
+  SUR_CU(cudaMalloc(&s->H, 2 * ld * kW * sizeof(__nv_bfloat16)), "cudaMalloc");
+  s->ld = ld;
+  SUR_CU(cudaMalloc(&s->part, nb * kPartStride * sizeof(float)), "cudaMalloc");
   SUR_CU(cudaMalloc(&s->loss_part, nb * sizeof(double)), "cudaMalloc");
   s->cap = n;
   return FFE_OK;
@@ -454,15 +577,28 @@ ffe_status set_attrs(ffe_surrogate* s) {
 ffe_status fwd_bwd(ffe_surrogate* s, const float* x, const float* t, int64_t n, cudaStream_t st) {
   const MlpDev P = make_dev(s);
   const int nb = (int)((n + kRows - 1) / kRows);
-  mlp_fwd_kernel<<<nb, 128, kSmemFwd, st>>>(P, x, n, s->y, s->Z, s->H);
+  if ((int64_t)nb * kRows > s->ld) return set_err(s->ctx, "surrogate scratch too small"), FFE_EINTERNAL;
+  mlp_fwd_kernel<<<nb, 128, kSmemFwd, st>>>(P, x, n, s->y, s->Z, s->H, s->ld);
   SUR_CU(cudaGetLastError(), "mlp_fwd");
   mlp_bwd_data_kernel<<<nb, 128, kSmemBwdData, st>>>(P, s->y, t, 1.0f / s->meta.y_scale, n, 2.0f / (float)n, s->Z,
-                                                      s->dZ, s->dy, s->loss_part);
+                                                      s->dZ, s->dy, s->loss_part, s->ld);
   SUR_CU(cudaGetLastError(), "mlp_bwd_data");
-  mlp_bwd_weight_kernel<<<dim3(nb, 2), 128, kSmemBwdW, st>>>(s->H, s->dZ, n, s->part);
+  mlp_bwd_weight_kernel<<<dim3(nb, 2), 128, kSmemBwdW, st>>>(P, s->H, s->dZ, s->part, s->ld);
   SUR_CU(cudaGetLastError(), "mlp_bwd_weight");
-  mlp_bwd_small_kernel<<<nb, 128, 0, st>>>(P, x, s->Z, s->dZ, s->dy, n, s->part);
+  mlp_bwd_small_kernel<<<nb, 128, 0, st>>>(P, x, s->Z, s->dZ, s->dy, n, s->part, s->ld);
   SUR_CU(cudaGetLastError(), "mlp_bwd_small");
+  return FFE_OK;
+}
+
+// Waits for the surrogate's stream and reports a kernel whose wait gave up.
+ffe_status check_status(ffe_surrogate* s) {
+  int32_t st = 0;
+  SUR_CU(cudaMemcpyAsync(&st, s->status, sizeof st, cudaMemcpyDeviceToHost, s->stream), "status");
+  SUR_CU(cudaStreamSynchronize(s->stream), "sync");
+  if (st != 0) {
+    set_err(s->ctx, "surrogate kernel: a tensor-core wait gave up");
+    return FFE_ETIMEOUT;
+  }
   return FFE_OK;
 }
 
@@ -482,7 +618,9 @@ ffe_status ffe_surrogate_create(ffe_context* ctx, const ffe_surrogate_meta* meta
   cudaError_t e = cudaMalloc(&s->master, kNParams * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&s->m, kNParams * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&s->v, kNParams * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&s->wcopies, 4 * kW * kW * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc(&s->tiles, 4 * (size_t)kTileBytes);
+  if (e == cudaSuccess) e = cudaMalloc(&s->status, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(s->status, 0, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&s->grad, kNParams * sizeof(float));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
@@ -504,7 +642,8 @@ void ffe_surrogate_destroy(ffe_surrogate* s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
   free_scratch(s);
-  for (void* p : {(void*)s->master, (void*)s->m, (void*)s->v, (void*)s->wcopies, (void*)s->grad})
+  for (void* p : {(void*)s->master, (void*)s->m, (void*)s->v, (void*)s->tiles, (void*)s->grad, (void*)s->status,
+                  (void*)s->epoch_loss})
     if (p) cudaFree(p);
   if (s->stream) cudaStreamDestroy(s->stream);
   delete s;
@@ -521,8 +660,7 @@ ffe_status ffe_surrogate_set_params(ffe_surrogate* s, const float* params) {
   SUR_CU(cudaMemset(s->m, 0, kNParams * sizeof(float)), "memset");
   SUR_CU(cudaMemset(s->v, 0, kNParams * sizeof(float)), "memset");
   s->adam_t = 0;
-  mlp_copies_kernel<<<(kW * kW + 255) / 256, 256, 0, s->stream>>>(s->master, s->wcopies, s->wcopies + kW * kW,
-                                                                   s->wcopies + 2 * kW * kW, s->wcopies + 3 * kW * kW);
+  mlp_copies_kernel<<<(kW * kW + 255) / 256, 256, 0, s->stream>>>(s->master, s->tiles);
   SUR_CU(cudaGetLastError(), "copies");
   SUR_CU(cudaStreamSynchronize(s->stream), "sync");
   return FFE_OK;
@@ -535,6 +673,65 @@ ffe_status ffe_surrogate_get_params(ffe_surrogate* s, float* params) {
   return FFE_OK;
 }
 
+// Checkpoint layout (host bytes, little-endian as the machine writes it):
+// header {magic "FFESUR01", parameter count, Adam step, meta}, then the FP32
+// master weights, Adam first and second moments (kNParams floats each).
+struct SurCheckpointHeader {
+  char magic[8];
+  int64_t n_params;
+  int64_t adam_t;
+  ffe_surrogate_meta meta;
+};
+constexpr char kSurMagic[8] = {'F', 'F', 'E', 'S', 'U', 'R', '0', '1'};
+
+ffe_status ffe_surrogate_save(ffe_surrogate* s, void* buf, size_t* bytes) {
+  if (!s || !bytes) return FFE_EINVAL;
+  const size_t need = sizeof(SurCheckpointHeader) + 3 * (size_t)kNParams * sizeof(float);
+  if (!buf) {
+    *bytes = need;
+    return FFE_OK;
+  }
+  if (*bytes < need) return set_err(s->ctx, "surrogate checkpoint: buffer of %zu bytes, %zu needed", *bytes, need),
+                            FFE_EINVAL;
+  SUR_CU(cudaStreamSynchronize(s->stream), "sync");
+  SurCheckpointHeader h;
+  std::memset(&h, 0, sizeof h);
+  std::memcpy(h.magic, kSurMagic, 8);
+  h.n_params = kNParams;
+  h.adam_t = s->adam_t;
+  h.meta = s->meta;
+  unsigned char* b = static_cast<unsigned char*>(buf);
+  std::memcpy(b, &h, sizeof h);
+  float* f = reinterpret_cast<float*>(b + sizeof h);
+  SUR_CU(cudaMemcpy(f, s->master, kNParams * sizeof(float), cudaMemcpyDeviceToHost), "save");
+  SUR_CU(cudaMemcpy(f + kNParams, s->m, kNParams * sizeof(float), cudaMemcpyDeviceToHost), "save");
+  SUR_CU(cudaMemcpy(f + 2 * kNParams, s->v, kNParams * sizeof(float), cudaMemcpyDeviceToHost), "save");
+  *bytes = need;
+  return FFE_OK;
+}
+
+ffe_status ffe_surrogate_load(ffe_surrogate* s, const void* buf, size_t bytes) {
+  if (!s || !buf) return FFE_EINVAL;
+  const size_t need = sizeof(SurCheckpointHeader) + 3 * (size_t)kNParams * sizeof(float);
+  SurCheckpointHeader h;
+  if (bytes < sizeof h) return set_err(s->ctx, "surrogate checkpoint: truncated"), FFE_EINVAL;
+  std::memcpy(&h, buf, sizeof h);
+  if (std::memcmp(h.magic, kSurMagic, 8) != 0 || h.n_params != kNParams || bytes < need || h.adam_t < 0 ||
+      !(h.meta.y_scale > 0.0f))
+    return set_err(s->ctx, "surrogate checkpoint: not a checkpoint of this network"), FFE_EINVAL;
+  const float* f = reinterpret_cast<const float*>(static_cast<const unsigned char*>(buf) + sizeof h);
+  SUR_CU(cudaStreamSynchronize(s->stream), "sync");
+  SUR_CU(cudaMemcpy(s->master, f, kNParams * sizeof(float), cudaMemcpyHostToDevice), "load");
+  SUR_CU(cudaMemcpy(s->m, f + kNParams, kNParams * sizeof(float), cudaMemcpyHostToDevice), "load");
+  SUR_CU(cudaMemcpy(s->v, f + 2 * kNParams, kNParams * sizeof(float), cudaMemcpyHostToDevice), "load");
+  s->adam_t = h.adam_t;
+  s->meta = h.meta;
+  mlp_copies_kernel<<<(kW * kW + 255) / 256, 256, 0, s->stream>>>(s->master, s->tiles);
+  SUR_CU(cudaGetLastError(), "copies");
+  SUR_CU(cudaStreamSynchronize(s->stream), "sync");
+  return FFE_OK;
+}
+
 ffe_status ffe_surrogate_predict(ffe_surrogate* s, const float* xraw, int64_t n, float* y, void* stream) {
   if (!s || !xraw || !y || n < 1) return FFE_EINVAL;
   (void)stream;
@@ -543,11 +740,11 @@ ffe_status ffe_surrogate_predict(ffe_surrogate* s, const float* xraw, int64_t n,
   cudaStream_t cs = s->stream;
   SUR_CU(cudaMemcpyAsync(s->x, xraw, n * 4 * sizeof(float), cudaMemcpyHostToDevice, cs), "upload");
   const int nb = (int)((n + kRows - 1) / kRows);
-  mlp_fwd_kernel<<<nb, 128, kSmemFwd, cs>>>(make_dev(s), s->x, n, s->y, nullptr, nullptr);
+  mlp_fwd_kernel<<<nb, 128, kSmemFwd, cs>>>(make_dev(s), s->x, n, s->y, nullptr, nullptr, 0);
   SUR_CU(cudaGetLastError(), "mlp_fwd");
   std::vector<float> yn(n);
   SUR_CU(cudaMemcpyAsync(yn.data(), s->y, n * sizeof(float), cudaMemcpyDeviceToHost, cs), "download");
-  SUR_CU(cudaStreamSynchronize(cs), "sync");
+  if ((st = check_status(s)) != FFE_OK) return st;
   for (int64_t i = 0; i < n; ++i) y[i] = yn[i] * s->meta.y_scale;
   return FFE_OK;
 }
@@ -564,12 +761,12 @@ ffe_status ffe_surrogate_grad(ffe_surrogate* s, const float* xraw, const float* 
   if ((st = fwd_bwd(s, s->x, s->t, n, cs)) != FFE_OK) return st;
   const int nb = (int)((n + kRows - 1) / kRows);
   mlp_reduce_kernel<<<(kNParams + 255) / 256, 256, 0, cs>>>(s->part, nb, s->grad, nullptr, nullptr, nullptr, 0, 0, 0,
-                                                             0, 1, 1, 0, nullptr, nullptr, nullptr, nullptr);
+                                                             0, 1, 1, 0, nullptr);
   SUR_CU(cudaGetLastError(), "reduce");
   std::vector<double> lp(nb);
   SUR_CU(cudaMemcpyAsync(grad, s->grad, kNParams * sizeof(float), cudaMemcpyDeviceToHost, cs), "download");
   SUR_CU(cudaMemcpyAsync(lp.data(), s->loss_part, nb * sizeof(double), cudaMemcpyDeviceToHost, cs), "download");
-  SUR_CU(cudaStreamSynchronize(cs), "sync");
+  if ((st = check_status(s)) != FFE_OK) return st;
   if (loss) {
     double tot = 0.0;
     for (double v : lp) tot += v;
@@ -580,39 +777,47 @@ ffe_status ffe_surrogate_grad(ffe_surrogate* s, const float* xraw, const float* 
 
 ffe_status ffe_surrogate_train(ffe_surrogate* s, const float* xraw, const float* traw, int64_t n, int32_t epochs,
                                int32_t batch, float lr, float* loss_per_epoch, void* stream) {
-  if (!s || !xraw || !traw || n < 1 || epochs < 1 || batch < kRows || batch % kRows != 0 || !(lr > 0.0f))
+  if (!s || !xraw || !traw || n < 1 || epochs < 1 || batch < 64 || batch % 64 != 0 || !(lr > 0.0f))
     return s ? (set_err(s->ctx, "train: bad arguments (batch a multiple of 64)"), FFE_EINVAL) : FFE_EINVAL;
   (void)stream;
   ffe_status st = ensure_scratch(s, std::max<int64_t>(n, batch));
   if (st != FFE_OK) return st;
   cudaStream_t cs = s->stream;
+  if (epochs > s->epoch_cap) {
+    if (s->epoch_loss) cudaFree(s->epoch_loss);
+    s->epoch_loss = nullptr;
+    s->epoch_cap = 0;
+    SUR_CU(cudaMalloc(&s->epoch_loss, epochs * sizeof(double)), "cudaMalloc");
+    s->epoch_cap = epochs;
+  }
+  SUR_CU(cudaMemsetAsync(s->epoch_loss, 0, epochs * sizeof(double), cs), "memset");
   SUR_CU(cudaMemcpyAsync(s->x, xraw, n * 4 * sizeof(float), cudaMemcpyHostToDevice, cs), "upload");
   SUR_CU(cudaMemcpyAsync(s->t, traw, n * sizeof(float), cudaMemcpyHostToDevice, cs), "upload");
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   const int64_t steps = n / batch;  // the tail that does not fill a batch is left out of the epoch
   if (steps < 1) return set_err(s->ctx, "train: fewer samples than one batch"), FFE_EINVAL;
-  std::vector<double> lp((batch + kRows - 1) / kRows);
+  const int nb = (batch + kRows - 1) / kRows;
   for (int ep = 0; ep < epochs; ++ep) {
-    double ep_loss = 0.0;
     for (int64_t k = 0; k < steps; ++k) {
       const int64_t off = k * batch;
       if ((st = fwd_bwd(s, s->x + off * 4, s->t + off, batch, cs)) != FFE_OK) return st;
       ++s->adam_t;
       const float bc1 = 1.0f - powf(b1, (float)s->adam_t), bc2 = 1.0f - powf(b2, (float)s->adam_t);
       mlp_reduce_kernel<<<(kNParams + 255) / 256, 256, 0, cs>>>(
-          s->part, batch / kRows, nullptr, s->master, s->m, s->v, lr, b1, b2, eps, bc1, bc2, 1, s->wcopies,
-          s->wcopies + kW * kW, s->wcopies + 2 * kW * kW, s->wcopies + 3 * kW * kW);
+          s->part, nb, nullptr, s->master, s->m, s->v, lr, b1, b2, eps, bc1, bc2, 1, s->tiles);
       SUR_CU(cudaGetLastError(), "adam");
       if (loss_per_epoch) {
-        SUR_CU(cudaMemcpyAsync(lp.data(), s->loss_part, lp.size() * sizeof(double), cudaMemcpyDeviceToHost, cs),
-               "download");
-        SUR_CU(cudaStreamSynchronize(cs), "sync");
-        for (double v : lp) ep_loss += v;
+        mlp_loss_kernel<<<1, 32, 0, cs>>>(s->loss_part, nb, s->epoch_loss + ep);
+        SUR_CU(cudaGetLastError(), "loss");
       }
     }
-    if (loss_per_epoch) loss_per_epoch[ep] = (float)(ep_loss / (double)(steps * batch));
   }
-  SUR_CU(cudaStreamSynchronize(cs), "sync");
+  std::vector<double> el(epochs);
+  if (loss_per_epoch)
+    SUR_CU(cudaMemcpyAsync(el.data(), s->epoch_loss, epochs * sizeof(double), cudaMemcpyDeviceToHost, cs), "download");
+  if ((st = check_status(s)) != FFE_OK) return st;
+  if (loss_per_epoch)
+    for (int ep = 0; ep < epochs; ++ep) loss_per_epoch[ep] = (float)(el[ep] / (double)(steps * batch));
   return FFE_OK;
 }
 
@@ -623,7 +828,7 @@ namespace ffe {
 ffe_status surrogate_infer_device(ffe_surrogate* s, const float* x, int64_t n, float* y, cudaStream_t st) {
   if (n < 1) return FFE_OK;
   const int nb = (int)((n + kRows - 1) / kRows);
-  mlp_fwd_kernel<<<nb, 128, kSmemFwd, st>>>(make_dev(s), x, n, y, nullptr, nullptr);
+  mlp_fwd_kernel<<<nb, 128, kSmemFwd, st>>>(make_dev(s), x, n, y, nullptr, nullptr, 0);
   SUR_CU(cudaGetLastError(), "mlp_fwd");
   return FFE_OK;
 }

@@ -103,6 +103,8 @@ _SIGNATURES = [
     ("ffe_surrogate_set_params", ctypes.c_int, [_VP, _VP]),
     ("ffe_surrogate_get_params", ctypes.c_int, [_VP, _VP]),
     ("ffe_surrogate_predict", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP]),
+    ("ffe_surrogate_save", ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_size_t)]),
+    ("ffe_surrogate_load", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     ("ffe_surrogate_grad", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.POINTER(ctypes.c_double), _VP]),
     ("ffe_surrogate_train", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_float, _VP, _VP]),
@@ -170,6 +172,18 @@ class Surrogate:
         p = np.zeros(N_SURROGATE_PARAMS, dtype=np.float32)
         _check(self.ctx.handle, lib().ffe_surrogate_get_params(self.handle, _ptr(p)))
         return p
+
+    def save(self) -> bytes:
+        """Checkpoint (weights, Adam moments and step, input/output maps) as bytes."""
+        n = ctypes.c_size_t(0)
+        _check(self.ctx.handle, lib().ffe_surrogate_save(self.handle, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(self.ctx.handle, lib().ffe_surrogate_save(self.handle, buf, ctypes.byref(n)))
+        return buf.raw[: n.value]
+
+    def load(self, data: bytes):
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        _check(self.ctx.handle, lib().ffe_surrogate_load(self.handle, buf, len(data)))
 
     def predict(self, x):
         x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 4)

@@ -157,10 +157,13 @@ def ff_surrogate(ctx, N, seed):
 
 def test_ff_guided_scan_labels_are_exact(ff_oracle):
     """The FF scan guided by a surrogate trained on the FF model (grid: 8-point windows; golden:
-    16-point windows; 5 q kept besides q = 0, margin 3 x the training RMS error): the labels and
-    best q of every point are the oracle's, FF points included, and the exact work is cut.  (The
-    surrogate's RMS error is below the FF condensation energies here, ~1.4e-5 per site at the
-    highest FF field; a network that cannot tell them from zero may prune the FF line.)"""
+    16-point windows; 5 q kept besides q = 0, margin 3 x the training RMS error).  On this small
+    lattice the FF winners are lines whose own condensation is tiny (1e-9 .. 4e-6 per site, below
+    the surrogate's resolution) but whose exact normal state lies 1.4e-5 .. 1.65e-5 per site below
+    that of q = 0; the guided scan verifies such lines because of their exact normal state, so the
+    labels and best q of every point, FF points included, are the oracle's.  (The normal states of
+    most q lie below that of q = 0 by more than the margin here, so most lines are verified: the
+    work saved is modest on this lattice, unlike on the large ones where the normal states agree.)"""
     c = workloads.ff_scan()
     N = c["N"]
     om, idx, star, labels, best = ff_oracle
@@ -178,12 +181,12 @@ def test_ff_guided_scan_labels_are_exact(ff_oracle):
     assert rms < 5e-6
     assert np.array_equal(glab, labels), (glab, labels)
     assert np.array_equal(gbest, best), (gbest, best)
-    assert st["k_evals"] < st["k_evals_full"], st
+    assert st["k_evals"] < st["k_evals_full"] and st["lines_pruned"] > 0, st
     kept = (res["flags"] & ffe.FFE_FLAG_PRUNED) == 0
     assert np.array_equal(res["idx_star"][kept & (res["idx_star"] > 0)], idx[kept & (res["idx_star"] > 0)])
-    assert np.array_equal(ggl, flab_g) and np.array_equal(ggb, fbest_g), (ggl, flab_g)
+    assert np.array_equal(ggl, flab_g) and np.array_equal(ggb, fbest_g), (ggl, flab_g, ggb, fbest_g)
     assert (ggl == search.FFLO).sum() >= 3
-    assert gst["k_evals"] < gst["k_evals_full"], gst
+    assert gst["k_evals"] < gst["k_evals_full"] and gst["lines_pruned"] > 0, gst
 
 
 def test_fflo_scan_u4_full_size_whole_lines():

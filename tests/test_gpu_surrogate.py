@@ -228,3 +228,26 @@ def test_trained_surrogate_guides_the_scan():
 
 def trained_scale(y):
     return float(max(np.std(y), 1e-6))
+
+
+def test_checkpoint_resumes_training_bit_for_bit(ctx):
+    """Save after two epochs, train two more; load the checkpoint into a fresh surrogate (other
+    weights, other maps) and train the same two epochs: the same losses and weights, bit for bit."""
+    rng = np.random.default_rng(9)
+    xr = raw_inputs(4096, rng)
+    f = mlp.features(xr)
+    t = (np.sin(3 * f[:, 0]) * f[:, 3] ** 2 - 0.5 * f[:, 1] * f[:, 3]) * Y_SCALE
+    s = make(ctx, mlp.init_params(21))
+    s.train(xr, t, epochs=2, batch=512, lr=2e-3)
+    ckpt = s.save()
+    la = s.train(xr, t, epochs=2, batch=512, lr=2e-3)
+    wa = s.get_params()
+    s.close()
+    r = ffe.Surrogate(ctx, np.zeros(4), np.ones(4), 1.0, mlp.init_params(22).astype(np.float32))
+    r.load(ckpt)
+    lb = r.train(xr, t, epochs=2, batch=512, lr=2e-3)
+    wb = r.get_params()
+    with pytest.raises(ffe.FFEError):
+        r.load(ckpt[:100])
+    r.close()
+    assert np.array_equal(la, lb) and np.array_equal(wa, wb)
