@@ -278,7 +278,15 @@ def run_surrogate(ffe, np, torch, workloads, cfg, ref, full_s, fp64_rate, epochs
     kept = (res["flags"] & ffe.FFE_FLAG_PRUNED) == 0
     full64_s = st["k_evals_full"] / fp64_rate if fp64_rate else None
     n_pts = len(labels)
+    # the MLP's arithmetic: per sample and epoch a forward (2 x (4x128 + 2x128^2 + 128) flops) and a
+    # backward of twice that, against the measured BF16 dense peak
+    train_flops = 3.0 * 2.0 * (4 * 128 + 2 * 128 * 128 + 128) * len(x) * epochs
+    peak_bf16 = measured_peak("bf16_tflops", 1900.0) * 1e12
     return pd_check, pd_out, {
+        "train_tflops": train_flops / t_train / 1e12,
+        "train_frac_of_bf16_peak": train_flops / t_train / peak_bf16,
+        "train_note": ("tcgen05.mma (BF16 x BF16 -> FP32 in TMEM), 128 samples per CTA; batches of 4096 keep "
+                       "32 CTAs busy, so the run is latency-bound, not tensor-bound"),
         "workload": (f"train: {len(x)} samples (q,h,T,Delta) at N=512 from the FP32+comp k-sum, {epochs} epochs, "
                      f"batch 4096; guide: fflo_scan N={cfg['N']}, window 16 + Delta=0, q=0 and 3 q kept per h"),
         "datagen_s": t_data, "train_s": t_train, "train_loss_first_last": [float(losses[0]), float(losses[-1])],
@@ -354,6 +362,15 @@ def run_phase_diagram(ffe, np, torch, workloads, ctx, sur, margin, fp64_rate, U)
                          "best_q_agreement_vs_fp32c": float(np.mean(best64 == fbest[sub])),
                          "full_seconds_extrapolated": k_full / (k64 / t64)},
     }
+
+
+def measured_peak(key, fallback):
+    """A peak from the driver's measurement file next to this script, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key])
+    except (OSError, KeyError, ValueError):
+        return fallback
 
 
 def threads_hint():

@@ -406,26 +406,44 @@ __global__ void __launch_bounds__(128) mlp_bwd_weight_kernel(const MlpDev P, con
 }
 
 // The thin parts of the gradient for 128 samples: dW1 = x^T dz1, biases,
-// dW4 = h3^T dy, db4 = sum dy (thread = column).
+// dW4 = h3^T dy, db4 = sum dy (thread = column; each column's 128 rows are
+// contiguous in the feature-major arrays and read four at a time; rows at or
+// beyond n have zero data gradients).
 __global__ void __launch_bounds__(128) mlp_bwd_small_kernel(const MlpDev P, const float* __restrict__ xraw,
                                                             const float* __restrict__ Z, const float* __restrict__ dZ,
                                                             const float* __restrict__ dyv, int64_t n, float* part,
                                                             int64_t ld) {
+  __shared__ float xs[kRows][4];
+  __shared__ float dys[kRows];
   const int c = threadIdx.x;
   const int64_t row0 = (int64_t)blockIdx.x * kRows;
-  float gw1[4] = {0, 0, 0, 0}, gb1 = 0, gb2 = 0, gb3 = 0, gw4 = 0, gb4 = 0;
-  for (int r = 0; r < kRows; ++r) {
-    const int64_t row = row0 + r;
-    if (row >= n) break;
-    const float d1 = dZ[(0 * kW + c) * ld + row];
+  {
+    const int64_t row = row0 + c;
+    const bool live = row < n;
 #pragma unroll
-    for (int f = 0; f < 4; ++f) gw1[f] += (xraw[row * 4 + f] - P.shift[f]) * P.scale[f] * d1;
-    gb1 += d1;
-    gb2 += dZ[(1 * kW + c) * ld + row];
-    gb3 += dZ[(2 * kW + c) * ld + row];
-    const float dy = dyv[row];
-    gw4 += siluf_(Z[(2 * kW + c) * ld + row]) * dy;
-    gb4 += dy;
+    for (int f = 0; f < 4; ++f) xs[c][f] = live ? (xraw[row * 4 + f] - P.shift[f]) * P.scale[f] : 0.0f;
+    dys[c] = live ? dyv[row] : 0.0f;
+  }
+  __syncthreads();
+  const float4* d1 = reinterpret_cast<const float4*>(dZ + (0 * kW + c) * ld + row0);
+  const float4* d2 = reinterpret_cast<const float4*>(dZ + (1 * kW + c) * ld + row0);
+  const float4* d3 = reinterpret_cast<const float4*>(dZ + (2 * kW + c) * ld + row0);
+  const float4* z3 = reinterpret_cast<const float4*>(Z + (2 * kW + c) * ld + row0);
+  float gw1[4] = {0, 0, 0, 0}, gb1 = 0, gb2 = 0, gb3 = 0, gw4 = 0, gb4 = 0;
+  for (int r4 = 0; r4 < kRows / 4; ++r4) {
+    const float4 a = d1[r4], b = d2[r4], e = d3[r4], z = z3[r4];
+    const float av[4] = {a.x, a.y, a.z, a.w}, zv[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = 4 * r4 + i;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) gw1[f] += xs[r][f] * av[i];
+      gw4 += siluf_(zv[i]) * dys[r];
+      gb4 += dys[r];
+    }
+    gb1 += (a.x + a.y) + (a.z + a.w);
+    gb2 += (b.x + b.y) + (b.z + b.w);
+    gb3 += (e.x + e.y) + (e.z + e.w);
   }
   float* dst = part + (int64_t)blockIdx.x * kPartStride;
 #pragma unroll
@@ -544,22 +562,27 @@ void free_scratch(ffe_surrogate* s) {
   s->ld = 0;
 }
 
-ffe_status ensure_scratch(ffe_surrogate* s, int64_t n) {
-  if (n <= s->cap) return FFE_OK;
-  free_scratch(s);
-  const int64_t nb = (n + kRows - 1) / kRows;
+// Scratch for n samples of input, target and output, and for the activations
+// and gradient partials of n_act samples at once (0: inference only).
+ffe_status ensure_scratch(ffe_surrogate* s, int64_t n, int64_t n_act) {
+  const int64_t nb = (n_act + kRows - 1) / kRows;
   const int64_t ld = nb * kRows;  // rows of the per-sample arrays: every block's, padded
-  SUR_CU(cudaMalloc(&s->x, n * 4 * sizeof(float)), "cudaMalloc");
-  SUR_CU(cudaMalloc(&s->t, n * sizeof(float)), "cudaMalloc");
-  SUR_CU(cudaMalloc(&s->y, n * sizeof(float)), "cudaMalloc");
-  SUR_CU(cudaMalloc(&s->dy, n * sizeof(float)), "cudaMalloc");
-  SUR_CU(cudaMalloc(&s->Z, 3 * ld * kW * sizeof(float)), "cudaMalloc");
-  SUR_CU(cudaMalloc(&s->dZ, 3 * ld * kW * sizeof(float)), "cudaMalloc");
-  SUR_CU(cudaMalloc(&s->H, 2 * ld * kW * sizeof(__nv_bfloat16)), "cudaMalloc");
-  s->ld = ld;
-  SUR_CU(cudaMalloc(&s->part, nb * kPartStride * sizeof(float)), "cudaMalloc");
-  SUR_CU(cudaMalloc(&s->loss_part, nb * sizeof(double)), "cudaMalloc");
-  s->cap = n;
+  if (n <= s->cap && ld <= s->ld) return FFE_OK;
+  const int64_t cap = std::max(n, s->cap), ldn = std::max(ld, s->ld);
+  free_scratch(s);
+  SUR_CU(cudaMalloc(&s->x, cap * 4 * sizeof(float)), "cudaMalloc");
+  SUR_CU(cudaMalloc(&s->t, cap * sizeof(float)), "cudaMalloc");
+  SUR_CU(cudaMalloc(&s->y, cap * sizeof(float)), "cudaMalloc");
+  SUR_CU(cudaMalloc(&s->dy, cap * sizeof(float)), "cudaMalloc");
+  s->cap = cap;
+  if (ldn > 0) {
+    SUR_CU(cudaMalloc(&s->Z, 3 * ldn * kW * sizeof(float)), "cudaMalloc");
+    SUR_CU(cudaMalloc(&s->dZ, 3 * ldn * kW * sizeof(float)), "cudaMalloc");
+    SUR_CU(cudaMalloc(&s->H, 2 * ldn * kW * sizeof(__nv_bfloat16)), "cudaMalloc");
+    SUR_CU(cudaMalloc(&s->part, (ldn / kRows) * kPartStride * sizeof(float)), "cudaMalloc");
+    SUR_CU(cudaMalloc(&s->loss_part, (ldn / kRows) * sizeof(double)), "cudaMalloc");
+  }
+  s->ld = ldn;
   return FFE_OK;
 }
 
@@ -735,7 +758,7 @@ ffe_status ffe_surrogate_load(ffe_surrogate* s, const void* buf, size_t bytes) {
 ffe_status ffe_surrogate_predict(ffe_surrogate* s, const float* xraw, int64_t n, float* y, void* stream) {
   if (!s || !xraw || !y || n < 1) return FFE_EINVAL;
   (void)stream;
-  ffe_status st = ensure_scratch(s, n);
+  ffe_status st = ensure_scratch(s, n, 0);
   if (st != FFE_OK) return st;
   cudaStream_t cs = s->stream;
   SUR_CU(cudaMemcpyAsync(s->x, xraw, n * 4 * sizeof(float), cudaMemcpyHostToDevice, cs), "upload");
@@ -753,7 +776,7 @@ ffe_status ffe_surrogate_grad(ffe_surrogate* s, const float* xraw, const float* 
                               double* loss, void* stream) {
   if (!s || !xraw || !traw || !grad || n < 1) return FFE_EINVAL;
   (void)stream;
-  ffe_status st = ensure_scratch(s, n);
+  ffe_status st = ensure_scratch(s, n, n);
   if (st != FFE_OK) return st;
   cudaStream_t cs = s->stream;
   SUR_CU(cudaMemcpyAsync(s->x, xraw, n * 4 * sizeof(float), cudaMemcpyHostToDevice, cs), "upload");
@@ -780,7 +803,7 @@ ffe_status ffe_surrogate_train(ffe_surrogate* s, const float* xraw, const float*
   if (!s || !xraw || !traw || n < 1 || epochs < 1 || batch < 64 || batch % 64 != 0 || !(lr > 0.0f))
     return s ? (set_err(s->ctx, "train: bad arguments (batch a multiple of 64)"), FFE_EINVAL) : FFE_EINVAL;
   (void)stream;
-  ffe_status st = ensure_scratch(s, std::max<int64_t>(n, batch));
+  ffe_status st = ensure_scratch(s, std::max<int64_t>(n, batch), batch);
   if (st != FFE_OK) return st;
   cudaStream_t cs = s->stream;
   if (epochs > s->epoch_cap) {

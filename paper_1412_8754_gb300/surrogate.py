@@ -41,14 +41,23 @@ def training_data(ctx: ffe.Context, N: int, sset: dict):
     return x.astype(np.float32), y.ravel().astype(np.float32)
 
 
-def fit(ctx: ffe.Context, x, y, epochs=30, batch=4096, lr=2e-3, seed=0, y_scale=None):
-    """A surrogate trained on (x, y) with Adam; returns (Surrogate, losses)."""
+def fit(ctx: ffe.Context, x, y, epochs=30, batch=4096, lr=2e-3, seed=0, y_scale=None, decay=True):
+    """A surrogate trained on (x, y) with Adam; returns (Surrogate, losses).  decay: the learning
+    rate follows a half cosine from lr down to lr/50 over the epochs (one training call per
+    epoch), so that the final weights settle instead of ending wherever constant-rate steps leave
+    them."""
     rng = np.random.default_rng(seed)
     perm = rng.permutation(len(x))
     ys = float(y_scale) if y_scale else float(max(np.std(y), 1e-6))
     s = ffe.Surrogate(ctx, workloads.SURROGATE_SHIFT, workloads.SURROGATE_SCALE, ys, initial_params(seed))
-    losses = s.train(x[perm], y[perm], epochs=epochs, batch=batch, lr=lr)
-    return s, losses
+    xp, yp = np.ascontiguousarray(x[perm]), np.ascontiguousarray(y[perm])
+    if not decay:
+        return s, s.train(xp, yp, epochs=epochs, batch=batch, lr=lr)
+    losses = []
+    for e in range(epochs):
+        lr_e = lr * (0.02 + 0.98 * 0.5 * (1.0 + np.cos(np.pi * e / max(1, epochs - 1))))
+        losses.append(float(s.train(xp, yp, epochs=1, batch=batch, lr=float(lr_e))[0]))
+    return s, np.array(losses, dtype=np.float32)
 
 
 def rms_error(s: "ffe.Surrogate", x, y, n=65536, seed=0) -> float:
