@@ -380,10 +380,24 @@ __device__ __forceinline__ float eval_batch32(const KState32 (&st)[KPT], const B
   return transposed_total(red, nvalid, lane);
 }
 
-// Far k-points of a LIST batch: W = c (a_0 + a_1) per output and k-point.
+// Far k-points of a LIST batch: W = c (a_0 + a_1) per output and k-point;
+// with one Delta for the whole batch (uniform), a once per k-point.
 template <int KPT>
 __device__ __forceinline__ float eval_far32(const KState32 (&st)[KPT], const BParF* bp, int nvalid, int lane,
-                                            float* red) {
+                                            float* red, bool uniform) {
+  if (uniform) {
+    float2 S = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      float2 R, A;
+      ra32(st[k], bp[0].d2, R, A);
+      S = __fadd2_rn(S, A);
+    }
+    const float s = S.x + S.y;
+#pragma unroll 4
+    for (int j = 0; j < nvalid; ++j) red[j * 36 + lane] = bp[j].c * s;
+    return transposed_total(red, nvalid, lane);
+  }
 #pragma unroll 2
   for (int j = 0; j < nvalid; ++j) {
     const BParF p = bp[j];
@@ -532,10 +546,27 @@ __device__ __forceinline__ void flush32(const KsumArgs& a, const WorkItem& w, co
     const int nvalid = stage_batch<float, kG>(a, g, b, lane, bp, di);
     outs += nvalid;
     float tot;
+    // LIST: a batch whose outputs share Delta (a golden-section search whose lines took the same
+    // decisions, a reference at Delta = 0) forms R and a once per slot, and with one T too takes
+    // the shared-T form of the scans
+    bool uni_d = false, uni_c = false;
+    if constexpr (kG == kLayoutList) {
+      const BParF p0 = bp[0], pl = bp[lane];
+      uni_d = __all_sync(kFull, lane >= nvalid || pl.d2 == p0.d2);
+      uni_c = __all_sync(kFull, lane >= nvalid || pl.c == p0.c);
+    }
     if constexpr (FAR) {
-      tot = eval_far32<KPT>(st, bp, nvalid, lane, red);
+      tot = eval_far32<KPT>(st, bp, nvalid, lane, red, uni_d);
+    } else if constexpr (kG == kLayoutList) {
+      const float d2u = bp[0].d2;
+      if (uni_d && uni_c)
+        tot = single ? eval_batch32<KPT, kLayoutProductUT, true>(st, bp, nvalid, d2u, lane, red)
+                     : eval_batch32<KPT, kLayoutProductUT, false>(st, bp, nvalid, d2u, lane, red);
+      else
+        tot = single ? eval_batch32<KPT, LAYOUT, true>(st, bp, nvalid, 0.0f, lane, red)
+                     : eval_batch32<KPT, LAYOUT, false>(st, bp, nvalid, 0.0f, lane, red);
     } else {
-      const float d2p = (kG == kLayoutProduct) ? a.d2f[g.delta_off + di] : 0.0f;
+      const float d2p = a.d2f[g.delta_off + di];
       tot = single ? eval_batch32<KPT, LAYOUT, true>(st, bp, nvalid, d2p, lane, red)
                    : eval_batch32<KPT, LAYOUT, false>(st, bp, nvalid, d2p, lane, red);
     }
