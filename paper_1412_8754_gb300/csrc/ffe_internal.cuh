@@ -415,14 +415,19 @@ __device__ __forceinline__ void ra_f64(double D, double s2, double as, double& R
 
 // FP64 band term for one (h,T): q = p - 1 = e1 + e2 + e1 e2 (kept as p - 1
 // for log1p) and first = min(0, max(|d|-|s|, 0) - a).
+// An exponential exp(-y) with y >= kExpZero underflows to 0 in IEEE double
+// (the smallest subnormal is e^-744.4): it is taken as 0 without evaluating it.
+constexpr double kExpZero = 750.0;
 __device__ __forceinline__ void band_term_f64(double R, double a, double as, double d0, double h,
                                               double inv_t, double& q, double& first) {
   double d = d0 - h;
   double ad = fabs(d);
   double x1 = fabs(R - ad);
   double x2 = R + ad;
-  double e1 = exp(-x1 * inv_t);
-  double e2 = exp(-x2 * inv_t);
+  const double y1 = x1 * inv_t, y2 = x2 * inv_t;
+  double e1 = 0.0, e2 = 0.0;
+  if (y1 < kExpZero) e1 = exp(-y1);
+  if (y2 < kExpZero) e2 = exp(-y2);
   q = e1 + e2 + e1 * e2;
   double g = fmax(ad - as, 0.0);
   first = fmin(g - a, 0.0);

@@ -131,6 +131,7 @@ __device__ __forceinline__ double v_term_f64(const KState<double>& st, double d2
     band_term_f64(R, A, st.as[b], st.d0[b], h, inv_t, q[b], f[b]);
   }
   const double Q = q[0] + q[1] + q[0] * q[1];
+  if (Q == 0.0) return f[0] + f[1];  // log1p(0) = 0: the same value
   return (f[0] + f[1]) - t * log1p(Q);
 }
 
