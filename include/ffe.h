@@ -414,12 +414,15 @@ FFE_API ffe_status ffe_surrogate_train(ffe_surrogate* s, const float* x, const f
 
 /* Phase scan guided by the surrogate, grid or golden-section search.  The
  * surrogate predicts every (q, h, T) line's condensation energy on a Delta
- * grid (the search grid; 256 points on [lo, hi] for golden) and the exact
- * k-sum evaluates every line's normal state Omega(q, Delta = lo); per (h, T)
- * the exact k-sum verifies q = 0 and the q_keep lines of lowest predicted
- * minimum (exact normal state + predicted condensation energy: on a finite
- * lattice the normal states of different q differ, and the labels compare
- * Omega across q), with a margin also every q predicted to condense by more
+ * grid (the search grid; 256 points on [lo, hi] for golden); with a margin,
+ * the exact k-sum evaluates the normal states Omega(q, Delta = lo) of every q
+ * at a sample of at most 64 (h, T) points, and at every point when they
+ * differ from those of q = 0 by more than a tenth of the margin somewhere
+ * in the sample (on a finite lattice the normal states of different q
+ * differ, and the labels compare Omega across q).  Per (h, T) the exact k-sum
+ * verifies q = 0 and the q_keep lines of lowest predicted minimum (the
+ * normal state relative to q = 0's where evaluated, plus the predicted
+ * condensation energy), with a margin also every q predicted to condense by more
  * than the margin whose predicted minimum is within the margin of the
  * lowest and every q whose exact normal state lies more than the margin
  * below that of q = 0 (any condensation would make it the winner), each on a
@@ -430,8 +433,9 @@ FFE_API ffe_status ffe_surrogate_train(ffe_surrogate* s, const float* x, const f
  * reach the full search's final bracket width.  An (h, T) point with a line
  * whose verified minimum lies on an inner window edge (or that `margin`
  * flags) is scanned again with all its verified lines over the whole range.
- * Unverified (pruned) lines report their exact Delta = lo value, idx_star 0
- * (grid) or -1 (golden) and flags FFE_FLAG_LOWER | FFE_FLAG_PRUNED; a line
+ * Unverified (pruned) lines are reported with idx_star 0 (grid) or -1
+ * (golden), flags FFE_FLAG_LOWER | FFE_FLAG_PRUNED and the Delta = lo value
+ * of the q = 0 line at the same (h, T); a line
  * whose minimum is its Delta = 0 point never decides a label, so pruning
  * changes a label only where the exact minimum of a pruned q would have
  * beaten the kept ones.  Outputs as in ffe_phase_scan. */
@@ -452,8 +456,8 @@ typedef struct {
                            too; 0: none of these                          */
 } ffe_guide;
 typedef struct {
-  double k_evals;       /* exact k-point evaluations done (the normal state
-                           of every line included)                           */
+  double k_evals;       /* exact k-point evaluations done (the normal states
+                           included)                                         */
   double k_evals_full;  /* those of the unguided grid scan                   */
   int64_t lines_kept, lines_pruned;
   int64_t fallbacks;    /* kept lines searched over the whole range          */

@@ -3,7 +3,9 @@
 // A full scan (Alg. 1) searches every (q, h, T) line over the whole Delta
 // range.  Guided, the surrogate first predicts the condensation energy of
 // every line on a Delta grid (tensor-core inference), and the exact k-sum
-// evaluates every line's normal state (Delta = 0, one k-sum per line); per
+// evaluates the lines' normal states (Delta = 0: at a sample of points, and
+// at every point where the sample shows the normal states of different q
+// to differ by more than a tenth of the margin); per
 // (h, T) only q = 0 and the q_keep lines with the lowest predicted minimum
 // (exact normal state + predicted condensation energy; with a margin also
 // every q predicted to condense by more than the margin within the margin of
@@ -275,32 +277,59 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
   if (e == cudaSuccess && st == FFE_OK) e = cudaMemcpyAsync(ymin.data(), d_ymin, n_lines * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && st == FFE_OK) e = cudaStreamSynchronize(s);
 
-  // 2. the exact normal state Omega(q, Delta = lo) of every line.  The
+  // 2. the exact normal state Omega(q, Delta = lo) of the lines.  The
   // surrogate predicts condensation energies, each relative to its own line's
   // normal state, while the labels compare Omega across q, and on a finite
   // lattice the normal states of different q differ; the pruning orders the
-  // q by exact normal state + predicted condensation energy.
+  // q by exact normal state + predicted condensation energy.  With a margin,
+  // the normal states of every q are first evaluated at a sample of at most
+  // 64 (h, T) points spread over the scan; where they differ from those of
+  // q = 0 by more than a tenth of the margin somewhere in the sample, every
+  // line's normal state is evaluated, otherwise (large lattices, where they
+  // agree) the predictions alone order the q.  Without a margin the
+  // predictions alone order them.
   double k_evals = 0.0;
-  std::vector<double> anchor(n_lines, 0.0), anchor_eb(n_lines, 0.0);
-  if (e == cudaSuccess && st == FFE_OK) {
-    std::vector<int> all_pts(n_pts);
-    std::iota(all_pts.begin(), all_pts.end(), 0);
-    std::vector<LineSpec> spec0(n_lines);
+  std::vector<double> anchor(n_lines, 0.0);  // per site, relative to q = 0 at the same (h, T)
+  const double n2 = (double)sc->N * (double)sc->N;
+  bool anchored = false;
+  auto normal_states = [&](const std::vector<int>& pts, std::vector<double>& rel) -> ffe_status {
+    std::vector<LineSpec> spec0((size_t)sc->n_q * pts.size());
     for (LineSpec& ls : spec0) ls.grid_idx = {0};
     PassResult r0;
-    st = run_explicit(ctx, sc, q0, all_pts, 0, grid, spec0, s, r0, &k_evals);
-    if (st == FFE_OK)
-      for (int l = 0; l < n_lines; ++l) {
-        anchor[l] = r0.res[l].omega_lo;
-        anchor_eb[l] = r0.res[l].err_bound;
+    ffe_status st0 = run_explicit(ctx, sc, q0, pts, 0, grid, spec0, s, r0, &k_evals);
+    if (st0 != FFE_OK) return st0;
+    rel.assign(spec0.size(), 0.0);
+    for (int q = 0; q < sc->n_q; ++q)
+      for (size_t j = 0; j < pts.size(); ++j)
+        rel[(size_t)q * pts.size() + j] =
+            (r0.res[(size_t)q * pts.size() + j].omega_lo - r0.res[(size_t)q0 * pts.size() + j].omega_lo) / n2;
+    return FFE_OK;
+  };
+  if (e == cudaSuccess && st == FFE_OK && guide->margin > 0.0 && sc->n_q > 1) {
+    std::vector<int> sample;
+    const int stride = std::max(1, (n_pts + 63) / 64);
+    for (int pt = 0; pt < n_pts; pt += stride) sample.push_back(pt);
+    std::vector<double> rel;
+    st = normal_states(sample, rel);
+    double spread = 0.0;
+    for (double v : rel) spread = std::max(spread, std::fabs(v));
+    if (st == FFE_OK && spread > 0.1 * guide->margin) {
+      std::vector<int> all_pts(n_pts);
+      std::iota(all_pts.begin(), all_pts.end(), 0);
+      if ((int)sample.size() == n_pts) {
+        anchor = rel;
+      } else {
+        st = normal_states(all_pts, rel);
+        if (st == FFE_OK) anchor = rel;
       }
+      anchored = st == FFE_OK;
+    }
   }
 
   // 3. which lines to verify, and on which window
   const int w = guide->window;
   std::vector<char> kept(n_lines, 0);
   const float ys = surrogate_y_scale(sur);
-  const double n2 = (double)sc->N * (double)sc->N;
   std::vector<int> wstart(n_lines, 0);
   std::vector<int32_t> kept_rows;
   std::vector<int64_t> row_of(n_lines, -1);
@@ -310,7 +339,7 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
     // predicted minimum per site: exact normal state + predicted condensation
     auto pred_min = [&](int q, int pt) {
       const size_t l = (size_t)q * n_pts + pt;
-      return anchor[l] / n2 + (double)ymin[l] * ys;
+      return anchor[l] + (double)ymin[l] * ys;
     };
     for (int pt = 0; pt < n_pts; ++pt) {
       order.clear();
@@ -327,11 +356,10 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
       // winner (on a finite lattice the normal states of different q differ)
       if (guide->margin > 0.0 && !order.empty()) {
         const double best = std::min(pred_min(order[0], pt), pred_min(q0, pt));
-        const double normal0 = anchor[(size_t)q0 * n_pts + pt] / n2;
         for (int k = guide->q_keep; k < (int)order.size(); ++k) {
           const size_t l = (size_t)order[k] * n_pts + pt;
           const bool condenses = (double)ymin[l] * ys < -guide->margin && pred_min(order[k], pt) <= best + guide->margin;
-          if (condenses || anchor[l] / n2 < normal0 - guide->margin) kept[l] = 1;
+          if (condenses || (anchored && anchor[l] < -guide->margin)) kept[l] = 1;
         }
       }
     }
@@ -515,11 +543,12 @@ extern "C" ffe_status ffe_surrogate_scan(ffe_context* ctx, ffe_surrogate* sur, c
     const LineSpec& ls = second ? spec2[m] : spec1[m];
     const PassResult& pr = second ? r2 : r1;
     ffe_result r = pr.res[m];
-    if (!kept[l]) {  // the line's own exact value at Delta = lo
+    if (!kept[l]) {  // the q = 0 line's reference value
+      const ffe_result& rn = pr.res[(size_t)q0 * nsub + j];
       r.delta_star = sc->lo;
-      r.omega_star = anchor[l];
-      r.omega_lo = anchor[l];
-      r.err_bound = anchor_eb[l];
+      r.omega_star = rn.omega_lo;
+      r.omega_lo = rn.omega_lo;
+      r.err_bound = 0.0;
       r.idx_star = golden ? -1 : 0;
       r.flags = FFE_FLAG_LOWER | FFE_FLAG_PRUNED;
     } else if (golden) {
