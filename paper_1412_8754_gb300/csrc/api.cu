@@ -95,8 +95,9 @@ namespace ffe {
 // rounding): then every output has c |R -+ d| >= 27, each factor
 // (1 + 2^-c|R-+d|) leaves the FP32 product unchanged (P + P e with P e below
 // half an ulp of P: the same bits as the full term), and its clamp term is c a.
-// FP64 path: tgap = 750 Tmax, so that every exp(-|R -+ d|/T) of the band
-// underflows to 0 and its term is the clamp term -a alone, exactly.
+// FP64 path: tgap = kExpNegligible Tmax, so that every exp(-|R -+ d|/T) of
+// the band has an argument of at least kExpNegligible, is taken as 0 (as in
+// band_term_f64) and the band's term is the clamp term -a alone.
 static void item_far_window(const ffe_plan* p, const GroupDesc& g, int b0, int b1, double golden_d2, WorkItem& w) {
   w.far_hlo = 0.0f;
   w.far_hhi = 0.0f;
@@ -160,7 +161,7 @@ static void item_far_window(const ffe_plan* p, const GroupDesc& g, int b0, int b
   w.far_hlo = std::nextafter((float)hlo, -INFINITY);
   w.far_hhi = std::nextafter((float)hhi, INFINITY);
   if (!f32) {
-    w.far_tgap = std::nextafter((float)(750.0 * tmax), INFINITY);
+    w.far_tgap = std::nextafter((float)(kExpNegligible * tmax), INFINITY);
     return;
   }
   w.far_tgap = std::nextafter((float)(27.0 * 0.69314718055994530942 * tmax + 1e-5), INFINITY);
@@ -670,7 +671,10 @@ ffe_status plan_configure(ffe_context* ctx, ffe_plan* p) {
   if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy");
   if (bps < 1) bps = 1;
   p->grid = ctx->n_sm * bps;
-  p->rescore_grid = ctx->n_sm * 4;
+  int rbps = 0;
+  e = rescore_occupancy(&rbps);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy");
+  p->rescore_grid = ctx->n_sm * std::max(1, rbps);
   build_items(p);
   build_mitems(p);
   p->k_evals = plan_k_evals(p);

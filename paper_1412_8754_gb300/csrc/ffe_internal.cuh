@@ -415,9 +415,12 @@ __device__ __forceinline__ void ra_f64(double D, double s2, double as, double& R
 
 // FP64 band term for one (h,T): q = p - 1 = e1 + e2 + e1 e2 (kept as p - 1
 // for log1p) and first = min(0, max(|d|-|s|, 0) - a).
-// An exponential exp(-y) with y >= kExpZero underflows to 0 in IEEE double
-// (the smallest subnormal is e^-744.4): it is taken as 0 without evaluating it.
-constexpr double kExpZero = 750.0;
+// An exponential exp(-y) with y >= kExpNegligible = 64 is taken as 0 without
+// evaluating it: e^-64 < 1.7e-28, so the band's -T ln(1 + q) term, which is
+// then dropped, is below 3 e^-64 T < 5.1e-28 T, and the free energy per site
+// changes by less than 1.6e-27 T (three bands) -- eleven orders of magnitude
+// below the rounding of an FP64 sum of terms of size 1e-6 or more.
+constexpr double kExpNegligible = 64.0;
 __device__ __forceinline__ void band_term_f64(double R, double a, double as, double d0, double h,
                                               double inv_t, double& q, double& first) {
   double d = d0 - h;
@@ -426,8 +429,8 @@ __device__ __forceinline__ void band_term_f64(double R, double a, double as, dou
   double x2 = R + ad;
   const double y1 = x1 * inv_t, y2 = x2 * inv_t;
   double e1 = 0.0, e2 = 0.0;
-  if (y1 < kExpZero) e1 = exp(-y1);
-  if (y2 < kExpZero) e2 = exp(-y2);
+  if (y1 < kExpNegligible) e1 = exp(-y1);
+  if (y2 < kExpNegligible) e2 = exp(-y2);
   q = e1 + e2 + e1 * e2;
   double g = fmax(ad - as, 0.0);
   first = fmin(g - a, 0.0);

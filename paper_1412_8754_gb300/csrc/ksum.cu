@@ -413,75 +413,170 @@ __device__ __forceinline__ float eval_far32(const KState32 (&st)[KPT], const BPa
   return transposed_total(red, nvalid, lane);
 }
 
-// fr[k][b]: band b of slot k is far for the whole warp (warp-uniform), so its
-// exponentials are exactly 0 and its term is -a (the same bits, without the
-// exp and log1p).
-template <int KPT>
-__device__ __forceinline__ double v_sum_f64(const KState<double> (&st)[KPT], const double (&R)[KPT][2],
-                                            const double (&A)[KPT][2], const BParD& p, const bool (&fr)[KPT][2]) {
-  double s = 0.0;
-#pragma unroll
-  for (int k = 0; k < KPT; ++k) {
-    double q0 = 0.0, f0 = -A[k][0], q1 = 0.0, f1 = -A[k][1];
-    if (!fr[k][0]) band_term_f64(R[k][0], A[k][0], st[k].as[0], st[k].d0[0], p.h, p.inv_t, q0, f0);
-    if (!fr[k][1]) band_term_f64(R[k][1], A[k][1], st[k].as[1], st[k].d0[1], p.h, p.inv_t, q1, f1);
-    if (fr[k][0] && fr[k][1]) {
-      s += f0 + f1;
-    } else {
-      const double Q = q0 + q1 + q0 * q1;  // (1+q0)(1+q1) - 1
-      s += (f0 + f1) - p.t * log1p(Q);
-    }
-  }
-  return s;
-}
-
-// FP64 far band: for every output of the item |R -+ d| / T >= 750 (window as
-// in the FP32 path, threshold 750 T_max), so exp underflows to 0.
+// FP64 far band: for every output of the item |R -+ d| / T >= kExpNegligible
+// (window as in the FP32 path, threshold kExpNegligible T_max), so both
+// exponentials are taken as 0 (band_term_f64) and the band's term is -a.
 __device__ __forceinline__ bool far_band64(double as, double d0, const WorkItem& w) {
   return as - fmax(fabs(d0 - (double)w.far_hlo), fabs(d0 - (double)w.far_hhi)) >= (double)w.far_tgap;
 }
 
-template <typename Real, int KPT>
-__device__ __forceinline__ void ra_all(const KState<Real> (&st)[KPT], Real d2, Real (&R)[KPT][2],
-                                       Real (&A)[KPT][2]) {
-#pragma unroll
-  for (int k = 0; k < KPT; ++k) {
-    const Real D = d2 * st[k].eta2;
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      if constexpr (std::is_same<Real, float>::value)
-        ra_f32(D, st[k].s2[b], st[k].as[b], R[k][b], A[k][b]);
-      else
-        ra_f64(D, st[k].s2[b], st[k].as[b], R[k][b], A[k][b]);
+// FP64 near-band entries per warp buffer: a flush takes 32 (one per lane), a
+// k-set adds at most 64 KPT, the remainder after flushing is below 32.
+__host__ __device__ constexpr int kbuf64_entries(int kpt) { return 32 + 64 * kpt; }
+
+// Lane l: the sum of row l (32 doubles, in order) of the warp's FP64 transpose
+// buffer (row stride 33), 0 for l >= nrows.
+__device__ __forceinline__ double row_total64(const double* red, int nrows, int lane) {
+  __syncwarp();
+  double t = 0.0;
+  if (lane < nrows)
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) t += red[lane * 33 + i];
+  __syncwarp();
+  return t;
+}
+
+// FP64 evaluation of up to 32 buffered near (k-point, band) entries, one per
+// lane, on every output of the item: v = min(max(|d| - |s|, 0) - a, 0)
+// - T ln(1 + q) per band, q = e1 + e2 + e1 e2 (log1p once per band; the
+// k-point's two bands add their logarithms).
+template <int LAYOUT>
+__device__ __forceinline__ void flush64(const KsumArgs& a, const WorkItem& w, const GroupDesc& g, int lane,
+                                        const int32_t* buf, int n, double* acc, BParD* bp, double* red) {
+  constexpr int kG = (LAYOUT == kLayoutList) ? kLayoutList : kLayoutProduct;
+  const bool live = lane < n;
+  double as = 1e15, s2 = 1e30, d0 = 0.0, eta2 = 0.0;
+  if (live) {
+    const int32_t e = buf[lane];
+    KState<double> st;
+    state_at<double>(a, g, e & kKidxMask, (e >> kPairBit) & 1, st);
+    const int sl = (e >> kSlotBit) & 1;
+    as = st.as[sl];
+    s2 = st.s2[sl];
+    d0 = st.d0[sl];
+    eta2 = st.eta2;
+  }
+  for (int b = w.b0; b < w.b1; ++b) {
+    int di;
+    const int nvalid = stage_batch<double, kG>(a, g, b, lane, bp, di);
+    double R = 0.0, A = 0.0;
+    if (kG == kLayoutProduct) {
+      const double dd = a.delta[g.delta_off + di];
+      ra_f64(dd * dd * eta2, s2, as, R, A);
     }
+    for (int j = 0; j < nvalid; ++j) {
+      const BParD p = bp[j];
+      if (kG == kLayoutList) ra_f64(p.d2 * eta2, s2, as, R, A);
+      double v = 0.0;
+      if (live) {
+        double q, f;
+        band_term_f64(R, A, as, d0, p.h, p.inv_t, q, f);
+        v = q == 0.0 ? f : f - p.t * log1p(q);
+      }
+      red[j * 33 + lane] = v;
+    }
+    const double t = row_total64(red, nvalid, lane);
+    if (lane < nvalid) acc[(b - w.b0) * 32 + lane] += t;
   }
 }
 
-// FP64 path, one batch: returns, in lane l, the warp's sum of v for output l
-// (butterfly reduce-scatter of the 32 per-lane sums).
-template <int KPT, int VARIANT>
-__device__ __forceinline__ double eval_batch64(const KState<double> (&st)[KPT], const BParD* bp, int nvalid,
-                                               double d2_product, int lane, const bool (&fr)[KPT][2]) {
-  double part[32];
-  if (VARIANT != kLayoutList) {
-    double R[KPT][2], A[KPT][2];
-    ra_all<double, KPT>(st, d2_product, R, A);
+// One work item in FP64.  Every band of every k-point is classified per lane:
+// far (its term is -a exactly, far_band64) or near.  Far bands form a once per
+// (k-point, Delta) -- per batch with a shared Delta (PRODUCT), per output
+// (LIST) -- and their warp sums go through the transpose buffer; near bands
+// are compacted (ballot + prefix count) into the warp's buffer and evaluated
+// in full, 32 at a time, on every output.  Only near bands pay the
+// exponentials and the logarithm.
+template <int KPT, int LAYOUT>
+__device__ __forceinline__ void item64(const KsumArgs& a, const WorkItem& w, const GroupDesc& g, int lane,
+                                       double* acc, BParD* bp, double* red, int32_t* nbuf) {
+  constexpr int kG = (LAYOUT == kLayoutList) ? kLayoutList : kLayoutProduct;
+  const int64_t nk = (int64_t)g.N * g.N;
+  const unsigned lt = (1u << lane) - 1u;
+  const int nb = w.b1 - w.b0;
+  int n_near = 0;
+  double far_acc = 0.0;  // PRODUCT: lane b - b0 holds batch b's sum of a over far bands
+  for (int ks = w.kset0; ks < w.kset1; ++ks)
+  for (int pair = 0; pair < band_pairs(a.m.nbands); ++pair) {
+    KState<double> st[KPT];
+    build_states<double, KPT>(a, g, ks, lane, pair, st);
+    const bool act0 = slot_active(a.m.nbands, g.band_only, pair, 0);
+    const bool act1 = slot_active(a.m.nbands, g.band_only, pair, 1);
+    bool far[KPT][2], near[KPT][2];
+    int32_t kidx[KPT];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) part[j] = (j < nvalid) ? v_sum_f64<KPT>(st, R, A, bp[j], fr) : 0.0;
-  } else {
+    for (int k = 0; k < KPT; ++k) {
+      kidx[k] = ks * (32 * KPT) + k * 32 + lane;
+      const bool valid = kidx[k] < nk;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      double s = 0.0;
-      if (j < nvalid) {
-        const BParD p = bp[j];
-        double R[KPT][2], A[KPT][2];
-        ra_all<double, KPT>(st, p.d2, R, A);
-        s = v_sum_f64<KPT>(st, R, A, p, fr);
+      for (int sl = 0; sl < 2; ++sl) {
+        const bool use = valid && (sl == 0 ? act0 : act1);
+        far[k][sl] = use && far_band64(st[k].as[sl], st[k].d0[sl], w);
+        near[k][sl] = use && !far[k][sl];
       }
-      part[j] = s;
+    }
+    if (__any_sync(kFull, far[0][0] || far[0][1] || (KPT > 1 && (far[KPT - 1][0] || far[KPT - 1][1])))) {
+      if (kG == kLayoutProduct) {
+        for (int b = w.b0; b < w.b1; ++b) {
+          const double dd = a.delta[g.delta_off + b / g.n_hblk];
+          double S = 0.0;
+#pragma unroll
+          for (int k = 0; k < KPT; ++k)
+#pragma unroll
+            for (int sl = 0; sl < 2; ++sl)
+              if (far[k][sl]) {
+                double R, A;
+                ra_f64(dd * dd * st[k].eta2, st[k].s2[sl], st[k].as[sl], R, A);
+                S += A;
+              }
+          red[(b - w.b0) * 33 + lane] = S;
+        }
+        far_acc += row_total64(red, nb, lane);
+      } else {
+        for (int b = w.b0; b < w.b1; ++b) {
+          int di;
+          const int nvalid = stage_batch<double, kG>(a, g, b, lane, bp, di);
+          for (int j = 0; j < nvalid; ++j) {
+            const double d2 = bp[j].d2;
+            double S = 0.0;
+#pragma unroll
+            for (int k = 0; k < KPT; ++k)
+#pragma unroll
+              for (int sl = 0; sl < 2; ++sl)
+                if (far[k][sl]) {
+                  double R, A;
+                  ra_f64(d2 * st[k].eta2, st[k].s2[sl], st[k].as[sl], R, A);
+                  S += A;
+                }
+            red[j * 33 + lane] = S;
+          }
+          const double t = row_total64(red, nvalid, lane);
+          if (lane < nvalid) acc[(b - w.b0) * 32 + lane] -= t;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < KPT; ++k)
+#pragma unroll
+      for (int sl = 0; sl < 2; ++sl) {
+        const unsigned m = __ballot_sync(kFull, near[k][sl]);
+        if (near[k][sl]) nbuf[n_near + __popc(m & lt)] = kidx[k] | (pair << kPairBit) | (sl << kSlotBit);
+        n_near += __popc(m);
+      }
+    __syncwarp();
+    int done = 0;
+    for (; n_near - done >= 32; done += 32) flush64<LAYOUT>(a, w, g, lane, nbuf + done, 32, acc, bp, red);
+    if (done > 0) {
+      __syncwarp();
+      if (lane < n_near - done) nbuf[lane] = nbuf[done + lane];  // fewer than 32 left
+      __syncwarp();
+      n_near -= done;
     }
   }
-  return reduce_scatter32<double>(part, lane);
+  if (n_near > 0) flush64<LAYOUT>(a, w, g, lane, nbuf, n_near, acc, bp, red);
+  if (kG == kLayoutProduct)
+    for (int b = w.b0; b < w.b1; ++b) acc[(b - w.b0) * 32 + lane] -= __shfl_sync(kFull, far_acc, b - w.b0);
+  __syncwarp();
 }
 
 // Output index (within the group) of lane `lane` in batch b, or -1.
@@ -820,6 +915,11 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
   double* mom = reinterpret_cast<double*>(after_bp + (size_t)nwarps * 32 * 36 * sizeof(float) +
                                           (size_t)nwarps * kBufs * kbuf_entries(KPT) * sizeof(int32_t)) +
                 (size_t)warp * kMoments * 32;
+  // FP64 only: per-warp 32 x 33 transpose buffer and near-entry buffer
+  double* red64 = reinterpret_cast<double*>(after_bp) + (size_t)warp * 32 * 33;
+  if constexpr (!std::is_same<Real, float>::value)
+    nbuf = reinterpret_cast<int32_t*>(after_bp + (size_t)nwarps * 32 * 33 * sizeof(double)) +
+           (size_t)warp * kbuf64_entries(KPT);
   for (;;) {
     int it = 0;
     if (lane == 0) it = atomicAdd(a.queue, 1);
@@ -833,32 +933,10 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
       continue;
     }
     for (int b = 0; b < nb; ++b) acc[b * 32 + lane] = 0.0;
-    if constexpr (std::is_same<Real, float>::value) {
+    if constexpr (std::is_same<Real, float>::value)
       item32<KPT, LAYOUT>(a, w, g, lane, acc, bp, red, nbuf, fbuf, mom);
-    }
-    for (int ks = w.kset0; ks < w.kset1; ++ks)
-    for (int pair = 0; pair < band_pairs(a.m.nbands); ++pair) {
-      if constexpr (!std::is_same<Real, float>::value) {
-        KState<double> st[KPT];
-        build_states<double, KPT>(a, g, ks, lane, pair, st);
-        bool fr[KPT][2];
-#pragma unroll
-        for (int k = 0; k < KPT; ++k)
-#pragma unroll
-          for (int b = 0; b < 2; ++b) fr[k][b] = __all_sync(kFull, far_band64(st[k].as[b], st[k].d0[b], w));
-        for (int b = w.b0; b < w.b1; ++b) {
-          int di;
-          const int nvalid = stage_batch<double, kGroupLayout>(a, g, b, lane, bp, di);
-          double d2p = 0.0;
-          if (kGroupLayout == kLayoutProduct) {
-            const double dd = a.delta[g.delta_off + di];
-            d2p = dd * dd;
-          }
-          const double tot = eval_batch64<KPT, LAYOUT>(st, bp, nvalid, d2p, lane, fr);
-          acc[(b - w.b0) * 32 + lane] += tot;
-        }
-      }
-    }
+    else
+      item64<KPT, LAYOUT>(a, w, g, lane, acc, bp, red64, nbuf);
     const Segment sg = a.segs[w.seg];
     double* dst = a.partials + sg.partial_off + (int64_t)w.chunk * nb * 32;
     for (int b = 0; b < nb; ++b) dst[b * 32 + lane] = acc[b * 32 + lane];
@@ -905,8 +983,8 @@ size_t ksum_smem_bytes(int prec, int layout, int kpt, int block_threads) {
   const size_t par = (prec == 1) ? sizeof(BParF) : sizeof(BParD);
   const int bufs = layout == kLayoutList ? 2 : 1;
   const size_t mom = layout == kLayoutList ? (size_t)kMoments * 32 * sizeof(double) : 0;
-  const size_t red =
-      (prec == 1) ? 32 * 36 * sizeof(float) + (size_t)bufs * kbuf_entries(kpt) * sizeof(int32_t) + mom : 0;
+  const size_t red = (prec == 1) ? 32 * 36 * sizeof(float) + (size_t)bufs * kbuf_entries(kpt) * sizeof(int32_t) + mom
+                                 : 32 * 33 * sizeof(double) + (size_t)kbuf64_entries(kpt) * sizeof(int32_t);
   const int mb = max_batches(layout == kLayoutList ? kLayoutList : kLayoutProduct);
   return (size_t)nw * (mb * 32 * sizeof(double) + 32 * par + red);
 }

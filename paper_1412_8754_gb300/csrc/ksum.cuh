@@ -158,6 +158,7 @@ cudaError_t argmin_launch(const Line* lines, int n_lines, const double* omega, c
                           const double* delta, const int32_t* rescored, int mode, Rescore* req,
                           int32_t* n_req, int32_t cap, LineResult* res, cudaStream_t s);
 cudaError_t rescore_launch(const RescoreArgs& a, int grid, cudaStream_t s);
+cudaError_t rescore_occupancy(int* blocks_per_sm);  // resident rescore blocks (256 threads) per SM
 // LineResult -> ffe_result (include/ffe.h) of n lines on the device.
 cudaError_t results_launch(const LineResult* lr, int64_t n, const int32_t* counters, int32_t cap, void* out,
                            cudaStream_t s);

@@ -119,26 +119,32 @@ cudaError_t argmin_launch(const Line* lines, int n_lines, const double* omega, c
   return cudaGetLastError();
 }
 
-// FP64 k-point term v_k (both bands) at one (Delta, h, T).
-__device__ __forceinline__ double v_term_f64(const KState<double>& st, double d2, double h, double inv_t,
-                                             double t) {
-  const double D = d2 * st.eta2;
-  double q[2], f[2];
-#pragma unroll
-  for (int b = 0; b < 2; ++b) {
-    double R, A;
-    ra_f64(D, st.s2[b], st.as[b], R, A);
-    band_term_f64(R, A, st.as[b], st.d0[b], h, inv_t, q[b], f[b]);
-  }
-  const double Q = q[0] + q[1] + q[0] * q[1];
-  if (Q == 0.0) return f[0] + f[1];  // log1p(0) = 0: the same value
-  return (f[0] + f[1]) - t * log1p(Q);
+// Near-band entries per warp in the FP64 re-evaluation: a flush takes the top
+// 32, a step of 32 k-points adds at most 32 x (two band pairs x two slots).
+constexpr int kRescoreBuf = 32 + 32 * 4;
+
+// -T ln(1 + q), q = e1 + e2 + e1 e2, of one near band (y1 = |R - |d|| / T < kExpNegligible,
+// y2 = (R + |d|) / T), with band_term_f64's cut-off for e2.
+__device__ __forceinline__ double near_log_term(double2 y, double t) {
+  const double e1 = exp(-y.x);
+  const double e2 = y.y < kExpNegligible ? exp(-y.y) : 0.0;
+  return -t * log1p(e1 + e2 + e1 * e2);
 }
 
+// The FP64 k-sum of one request, k-chunk by k-chunk.  Each warp takes 32
+// consecutive k-points per step; every active band adds its clamp term
+// min(max(|d| - |s|, 0) - a, 0) at once, and only a band with
+// |R - |d|| / T < kExpNegligible (near) has exponentials that are not 0: such
+// bands are compacted (ballot + prefix count) into the warp's buffer and their
+// -T ln(1 + q) evaluated 32 at a time, so the exponentials and the logarithm
+// run on full warps.  The two bands of a k-point add their logarithms.
 __global__ void __launch_bounds__(256) rescore_kernel(const RescoreArgs a) {
   __shared__ double red[8];
   __shared__ int sh_w, sh_last;
+  __shared__ double2 near_buf[8][kRescoreBuf];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  double2* nb = near_buf[warp];
   const int nreq = min(*a.n_req, a.cap);
   const int total = nreq * a.max_chunks;
   for (;;) {
@@ -156,22 +162,47 @@ __global__ void __launch_bounds__(256) rescore_kernel(const RescoreArgs a) {
     const int64_t k1 = min(nk, k0 + a.chunk_k);
     const double d2 = q.delta * q.delta, inv_t = 1.0 / ht.T;
     double s = 0.0;
-    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-      const int iy = (int)(k / g.N);
-      const int ix = (int)(k - (int64_t)iy * g.N);
+    int n_near = 0;
+    for (int64_t kb = k0 + warp * 32; kb < k1; kb += blockDim.x) {
+      const int64_t k = kb + lane;
+      const bool valid = k < k1;
+      const int iy = valid ? (int)(k / g.N) : 0;
+      const int ix = valid ? (int)(k - (int64_t)iy * g.N) : 0;
       for (int pair = 0; pair < band_pairs(a.m.nbands); ++pair) {
         KState<double> st;
-        if (a.m.nbands == 3) {
+        if (!valid) {
+          kstate_invalid<double>(st);
+        } else if (a.m.nbands == 3) {
           const double eta = a.m.eta_amp * a.c0d[g.tab_off + ix] * a.c0d[g.tab_off + g.N + iy];
           kstate_from_table3<double, E3D>(a.m, eta, a.e3d[g.e3_off + k], a.e3d[g.e3_off + nk + k], pair, st);
         } else {
           kstate_make<double, TabRowD>(a.m, a.tabd[g.tab_off + ix], a.tabd[g.tab_off + g.N + iy],
                                        a.c0d[g.tab_off + ix], a.c0d[g.tab_off + g.N + iy], st);
         }
-        kstate_mask<double>(st, a.m.nbands, g.band_only, pair);
-        s += v_term_f64(st, d2, ht.h, inv_t, ht.T);
+        const double D = d2 * st.eta2;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          const bool use = valid && slot_active(a.m.nbands, g.band_only, pair, b);
+          double R, A;
+          ra_f64(D, st.s2[b], st.as[b], R, A);
+          const double ad = fabs(st.d0[b] - ht.h);
+          const double y1 = fabs(R - ad) * inv_t;
+          if (use) s += fmin(fmax(ad - st.as[b], 0.0) - A, 0.0);
+          const bool near = use && y1 < kExpNegligible;
+          const unsigned m = __ballot_sync(kFull, near);
+          if (near) nb[n_near + __popc(m & lt)] = make_double2(y1, (R + ad) * inv_t);
+          n_near += __popc(m);
+        }
       }
+      __syncwarp();
+      while (n_near >= 32) {  // the top 32 entries, one per lane
+        n_near -= 32;
+        s += near_log_term(nb[n_near + lane], ht.T);
+      }
+      __syncwarp();
     }
+    if (lane < n_near) s += near_log_term(nb[lane], ht.T);
+    __syncwarp();
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
     if (lane == 0) red[warp] = s;
@@ -225,6 +256,10 @@ __global__ void __launch_bounds__(256) rescore_kernel(const RescoreArgs a) {
     }
     __syncthreads();
   }
+}
+
+cudaError_t rescore_occupancy(int* blocks_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, rescore_kernel, 256, 0);
 }
 
 cudaError_t rescore_launch(const RescoreArgs& a, int grid, cudaStream_t s) {
