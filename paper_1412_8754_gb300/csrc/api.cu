@@ -121,7 +121,7 @@ static void item_far_window(const ffe_plan* p, const GroupDesc& g, int b0, int b
     }
     if (d2 < INFINITY) w.sgl_d2min = std::nextafter((float)d2, 0.0f);
   }
-  if (f32) {  // the largest Delta^2 of the item's outputs
+  {  // the largest Delta^2 of the item's outputs (far series, blocked bands)
     double d2 = 0.0;
     if (p->golden_steps > 0) {  // golden brackets stay inside each line's [lo, hi]
       d2 = golden_d2;

@@ -45,7 +45,7 @@ __global__ void direct_pack_kernel(DirectShape sh, DirectLayout L, const double*
 
 // One warp per segment: the far window of its outputs, as the host planner
 // sets it for a LIST group (FP32: h range, 27 ln2 T_max, Delta^2 range; FP64:
-// h range and kExpNegligible T_max), rounded outward to float.
+// h range, kExpNegligible T_max and the largest Delta^2), rounded outward to float.
 __global__ void direct_window_kernel(DirectShape sh, DirectLayout L, unsigned char* base) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x & 31;
   if (warp >= sh.n_segs) return;
@@ -77,7 +77,7 @@ __global__ void direct_window_kernel(DirectShape sh, DirectLayout L, unsigned ch
   w[1] = nextafterf(__double2float_rn(hhi), INFINITY);
   w[2] = f32 ? nextafterf(__double2float_rn(27.0 * ln2 * tmax + 1e-5), INFINITY)
              : nextafterf(__double2float_rn(kExpNegligible * tmax), INFINITY);
-  w[3] = f32 ? nextafterf(__double2float_rn(d2hi), INFINITY) : INFINITY;
+  w[3] = nextafterf(__double2float_rn(d2hi), INFINITY);
   w[4] = f32 ? nextafterf(__double2float_rn(d2lo), 0.0f) : 0.0f;
   w[5] = f32 ? w[2] : INFINITY;
 }

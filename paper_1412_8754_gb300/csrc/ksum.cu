@@ -236,6 +236,20 @@ __device__ __forceinline__ bool far_band32(float as, float d0, const WorkItem& w
   return as - fmaxf(fabsf(d0 - w.far_hlo), fabsf(d0 - w.far_hhi)) >= w.far_tgap;
 }
 
+// Blocked band: for every output of the item |d| - R >= far_tgap, with
+// |d| = |d0 - h| >= its distance from [far_hlo, far_hhi] and
+// R^2 <= s^2 + far_d2max eta^2.  Then c |R -+ d| >= 27 for both signs, so both
+// factors (1 + 2^-c|R -+ d|) leave the FP32 product unchanged, and
+// min(c (R - d), c (R + d), c a) = c (R - |d|) < 0 clamps to 0: the band adds
+// nothing to W, the same bits as its full term.  (The pair state is
+// "blocked": one member below and one above the chemical potential by more
+// than the window.)  The squares are compared with a relative margin of
+// 2^-20 for their FP32 rounding.
+__device__ __forceinline__ bool blocked_band32(float d0, float eta2, float s2, const WorkItem& w) {
+  const float m = fmaxf(0.0f, fmaxf(w.far_hlo - d0, d0 - w.far_hhi)) - w.far_tgap;
+  return m > 0.0f && m * m >= fmaf(w.far_d2max, eta2, s2) * (1.0f + 0x1p-20f);
+}
+
 // R and a = Delta^2 eta^2 / (R + |s|) of both halves at Delta^2 = d2.
 __device__ __forceinline__ void ra32(const KState32& st, float d2, float2& R, float2& A) {
   const float2 D2 = __fmul2_rn(make_float2(d2, d2), st.eta2);
@@ -420,6 +434,15 @@ __device__ __forceinline__ bool far_band64(double as, double d0, const WorkItem&
   return as - fmax(fabs(d0 - (double)w.far_hlo), fabs(d0 - (double)w.far_hhi)) >= (double)w.far_tgap;
 }
 
+// FP64 blocked band: |d| - R >= kExpNegligible T_max for every output of the
+// item (as blocked_band32), so both exponentials are taken as 0 and the clamp
+// term min(max(|d| - |s|, 0) - a, 0) = min(|d| - R, 0) is 0: the band's term
+// is exactly 0.
+__device__ __forceinline__ bool blocked_band64(double d0, double eta2, double s2, const WorkItem& w) {
+  const double m = fmax(0.0, fmax((double)w.far_hlo - d0, d0 - (double)w.far_hhi)) - (double)w.far_tgap;
+  return m > 0.0 && m * m >= fma((double)w.far_d2max, eta2, s2) * (1.0 + 0x1p-40);
+}
+
 // FP64 near-band entries per warp buffer: a flush takes 32 (one per lane), a
 // k-set adds at most 64 KPT, the remainder after flushing is below 32.
 __host__ __device__ constexpr int kbuf64_entries(int kpt) { return 32 + 64 * kpt; }
@@ -481,7 +504,8 @@ __device__ __forceinline__ void flush64(const KsumArgs& a, const WorkItem& w, co
 }
 
 // One work item in FP64.  Every band of every k-point is classified per lane:
-// far (its term is -a exactly, far_band64) or near.  Far bands form a once per
+// far (its term is -a exactly, far_band64), blocked (its term is 0,
+// blocked_band64) or near.  Far bands form a once per
 // (k-point, Delta) -- per batch with a shared Delta (PRODUCT), per output
 // (LIST) -- and their warp sums go through the transpose buffer; near bands
 // are compacted (ballot + prefix count) into the warp's buffer and evaluated
@@ -512,7 +536,7 @@ __device__ __forceinline__ void item64(const KsumArgs& a, const WorkItem& w, con
       for (int sl = 0; sl < 2; ++sl) {
         const bool use = valid && (sl == 0 ? act0 : act1);
         far[k][sl] = use && far_band64(st[k].as[sl], st[k].d0[sl], w);
-        near[k][sl] = use && !far[k][sl];
+        near[k][sl] = use && !far[k][sl] && !blocked_band64(st[k].d0[sl], st[k].eta2, st[k].s2[sl], w);
       }
     }
     if (__any_sync(kFull, far[0][0] || far[0][1] || (KPT > 1 && (far[KPT - 1][0] || far[KPT - 1][1])))) {
@@ -686,7 +710,7 @@ __device__ __forceinline__ void buffer_shift(int32_t* buf, int done, int n, int 
 
 // One work item in FP32.  Every band of every k-point of a k-set is "far"
 // (far_band32: for all outputs of the item its log terms are 1 in FP32 and
-// W = c a) or "near".  Far bands cost, per batch, their R and a: with a
+// W = c a), "blocked" (blocked_band32: W = 0, skipped) or "near".  Far bands cost, per batch, their R and a: with a
 // shared Delta (PRODUCT layouts) their a is summed over the warp once per
 // batch and applied as c (sum) to every output at the end; with a Delta per
 // output (LIST) they are buffered and evaluated per output in the far form.
@@ -810,7 +834,7 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
         const float t = w.sgl_r - fmaxf(0.0f, fmaxf(w.far_hlo - d0, d0 - w.far_hhi));
         const bool sg = t <= 0.0f || fmaf(w.sgl_d2min, eta2, s2) >= t * t;
         const int32_t e = kidx[k] | (pair << kPairBit) | (sl << kSlotBit) | ((int32_t)sg << kSingleBit);
-        const bool nr = !fr;  // near implies active and valid
+        const bool nr = !fr && !blocked_band32(d0, eta2, s2, w);  // near implies active and valid
         const unsigned m = __ballot_sync(kFull, nr);
         if (nr) nbuf[n_near + __popc(m & lt)] = e;
         n_near += __popc(m);
