@@ -106,55 +106,40 @@ static void item_far_window(const ffe_plan* p, const GroupDesc& g, int b0, int b
   w.sgl_d2min = 0.0f;
   w.sgl_r = INFINITY;
   const bool f32 = p->prec == FFE_FP32C;
+  // the item's Delta entries [d0, d1) and (h, T) entries [e0, e1): PRODUCT
+  // items are consecutive batches of one h-block (tile_pos), LIST items their
+  // outputs
+  int64_t d0, d1, e0, e1;
+  if (g.layout == kLayoutProduct) {
+    const int hb = tile_hb(g), db = tile_db(g), nd = tile_n_dblk(g);
+    const int hblk = b0 / nd, dblk0 = b0 - hblk * nd;
+    d0 = (int64_t)dblk0 * db;
+    d1 = std::min<int64_t>(g.n_delta, (int64_t)(dblk0 + (b1 - b0)) * db);
+    e0 = (int64_t)hblk * hb;
+    e1 = std::min<int64_t>(g.n_ht, e0 + hb);
+  } else {
+    d0 = e0 = (int64_t)b0 * 32;
+    d1 = e1 = std::min<int64_t>(g.n_out, (int64_t)b1 * 32);
+  }
   if (f32 && p->golden_steps == 0) {  // the smallest Delta^2 of the item's outputs (golden: 0)
     double d2 = INFINITY;
-    for (int b = b0; b < b1; ++b) {
-      if (g.layout == kLayoutProduct) {
-        const double d = p->delta[g.delta_off + b / g.n_hblk];
-        d2 = std::min(d2, d * d);
-      } else {
-        for (int64_t o = (int64_t)b * 32; o < std::min<int64_t>(g.n_out, (int64_t)b * 32 + 32); ++o) {
-          const double d = p->delta[g.delta_off + o];
-          d2 = std::min(d2, d * d);
-        }
-      }
-    }
+    for (int64_t i = d0; i < d1; ++i) d2 = std::min(d2, p->delta[g.delta_off + i] * p->delta[g.delta_off + i]);
     if (d2 < INFINITY) w.sgl_d2min = std::nextafter((float)d2, 0.0f);
   }
   {  // the largest Delta^2 of the item's outputs (far series, blocked bands)
     double d2 = 0.0;
-    if (p->golden_steps > 0) {  // golden brackets stay inside each line's [lo, hi]
+    if (p->golden_steps > 0)  // golden brackets stay inside each line's [lo, hi]
       d2 = golden_d2;
-    } else if (g.layout == kLayoutList) {
-      for (int64_t o = (int64_t)b0 * 32; o < std::min<int64_t>(g.n_out, (int64_t)b1 * 32); ++o) {
-        const double d = p->delta[g.delta_off + o];
-        d2 = std::max(d2, d * d);
-      }
-    } else {
-      for (int b = b0; b < b1; ++b) {
-        const double d = p->delta[g.delta_off + b / g.n_hblk];
-        d2 = std::max(d2, d * d);
-      }
-    }
+    else
+      for (int64_t i = d0; i < d1; ++i) d2 = std::max(d2, p->delta[g.delta_off + i] * p->delta[g.delta_off + i]);
     w.far_d2max = std::nextafter((float)d2, INFINITY);
   }
   double hlo = INFINITY, hhi = -INFINITY, tmax = 0.0;
-  for (int b = b0; b < b1; ++b) {
-    int64_t e0, e1;
-    if (g.layout == kLayoutProduct) {
-      const int j0 = (b % g.n_hblk) * 32;
-      e0 = j0;
-      e1 = std::min<int64_t>(g.n_ht, j0 + 32);
-    } else {
-      e0 = (int64_t)b * 32;
-      e1 = std::min<int64_t>(g.n_out, e0 + 32);
-    }
-    for (int64_t e = e0; e < e1; ++e) {
-      const HT& x = p->ht[g.ht_off + e];
-      hlo = std::min(hlo, x.h);
-      hhi = std::max(hhi, x.h);
-      tmax = std::max(tmax, x.T);
-    }
+  for (int64_t e = e0; e < e1; ++e) {
+    const HT& x = p->ht[g.ht_off + e];
+    hlo = std::min(hlo, x.h);
+    hhi = std::max(hhi, x.h);
+    tmax = std::max(tmax, x.T);
   }
   if (!(hlo <= hhi)) return;
   // float bounds that contain the FP64 ones
@@ -189,9 +174,13 @@ void build_items(ffe_plan* p) {
     const GroupDesc& g = p->groups[gi];
     const int64_t nk = (int64_t)g.N * g.N;
     const int n_ksets = (int)((nk + kset_pts - 1) / kset_pts);
-    const int sb = std::min(max_batches(g.layout), std::max(1, g.n_batches));
-    for (int b0 = 0; b0 < g.n_batches; b0 += sb) {
-      const int b1 = std::min(g.n_batches, b0 + sb);
+    // segments: LIST, <= kMaxBatchesList batches; PRODUCT, consecutive batches of one h-block
+    // spanning at most 64 Delta values (the k-sum keeps two far sums per lane)
+    const bool prod = g.layout == kLayoutProduct;
+    const int sb = prod ? std::min(kMaxBatchesPerItem, 64 / tile_db(g)) : max_batches(g.layout);
+    const int run = prod ? tile_n_dblk(g) : std::max(1, g.n_batches);  // batches per h-block
+    for (int b0 = 0; b0 < g.n_batches;) {
+      const int b1 = std::min(b0 - b0 % run + run, b0 + sb);
       const int nb = b1 - b0;
       const double outs = (double)nb * 32.0;
       int ck = (int)std::max(1.0, std::floor(target / (outs * kset_pts)));
@@ -226,6 +215,7 @@ void build_items(ffe_plan* p) {
         w.sgl_r = proto.sgl_r;
         p->items.push_back(w);
       }
+      b0 = b1;
     }
   }
   p->n_partials = poff;
@@ -268,17 +258,39 @@ void build_mitems(ffe_plan* p) {
   p->n_mcounters = counter;
 }
 
-// True when every 32-entry (h,T) batch of every PRODUCT group has one T.
+// The tile width of a PRODUCT group under the shared-T kernel: 8 (h,T)
+// entries x 4 Delta rows per batch -- a work item then spans the h range of 8
+// entries, so fewer bands are near for some output of it -- or, for a short
+// (h,T) list, the smallest power of two that holds it.
+static int tile_width(const GroupDesc& g) {
+  int hb = 8;
+  while (hb > 1 && hb / 2 >= g.n_ht) hb /= 2;
+  return hb;
+}
+
+// True when every tile's (h,T) entries of every PRODUCT group share one T.
 bool batches_share_T(const ffe_plan* p) {
   for (const GroupDesc& g : p->groups) {
     if (g.layout != kLayoutProduct) return false;
-    for (int j0 = 0; j0 < g.n_ht; j0 += 32) {
-      const int j1 = std::min(g.n_ht, j0 + 32);
+    const int hb = tile_width(g);
+    for (int j0 = 0; j0 < g.n_ht; j0 += hb) {
+      const int j1 = std::min(g.n_ht, j0 + hb);
       for (int j = j0 + 1; j < j1; ++j)
         if (p->ht[g.ht_off + j].T != p->ht[g.ht_off + j0].T) return false;
     }
   }
   return true;
+}
+
+// PRODUCT batch shapes: tiles (tile_width entries x 32 / tile_width Delta rows)
+// for the shared-T kernel, else 32 entries of one Delta.
+void apply_tiles(ffe_plan* p, bool shared_t) {
+  for (GroupDesc& g : p->groups) {
+    if (g.layout != kLayoutProduct) continue;
+    g.hb = shared_t ? tile_width(g) : 32;
+    g.n_hblk = (g.n_ht + g.hb - 1) / g.hb;
+    g.n_batches = g.n_hblk * tile_n_dblk(g);
+  }
 }
 
 double plan_k_evals(const ffe_plan* p) {
@@ -456,6 +468,7 @@ ffe_status plan_upload_params(ffe_context* ctx, ffe_plan* p, cudaStream_t s) {
 // device (the buffer is reused once the previous refill's copies are done).
 ffe_status plan_refill(ffe_context* ctx, ffe_plan* p, cudaStream_t s, bool pinned) {
   const size_t n_items = p->items.size();
+  apply_tiles(p, p->variant == kLayoutProductUT);
   build_items(p);
   if (p->items.size() != n_items) return set_err(ctx, "plan refill changed its work items"), FFE_EINTERNAL;
   std::vector<HostCopy> copies;
@@ -660,6 +673,7 @@ ffe_status plan_enqueue(ffe_context* ctx, ffe_plan* p, cudaStream_t s, cudaEvent
 ffe_status plan_configure(ffe_context* ctx, ffe_plan* p) {
   p->variant = p->layout;
   if (p->prec == FFE_FP32C && p->layout == kLayoutProduct && batches_share_T(p)) p->variant = kLayoutProductUT;
+  apply_tiles(p, p->variant == kLayoutProductUT);
   // launch shape: persistent grid of resident blocks
   const Tuning t = tuning_for(ctx, p);
   p->kpt = t.kpt;
@@ -855,6 +869,7 @@ static void fill_scan_grid(ffe_plan* p, const ffe_scan* sc) {
     g.layout = kLayoutProduct;
     g.n_delta = sc->n;
     g.n_ht = n_pts;
+    g.hb = 32;  // apply_tiles sets the batch shape of the kernel variant
     g.n_hblk = (n_pts + 31) / 32;
     g.n_batches = g.n_delta * g.n_hblk;
     g.n_h = sc->n_h;

@@ -34,9 +34,12 @@ static std::string tuning_key(const ffe_context* ctx, const ffe_plan* p) {
   return k;
 }
 
-static Tuning default_tuning(int prec) {
+// Defaults measured on GB300: FP32 shared-T tiles 2 k-points per thread
+// (34.7 ms against 46.1 ms with 4 on the N = 1024 FFLO scan), the other FP32
+// layouts 4 (LIST: 683 ms against 736 ms with 2 on a golden diagram), FP64 1.
+static Tuning default_tuning(int prec, int variant) {
   Tuning t;
-  t.kpt = prec == FFE_FP32C ? 4 : 1;
+  t.kpt = prec == FFE_FP32C ? (variant == kLayoutProductUT ? 2 : 4) : 1;
   t.block = 256;
   t.item_target = prec == FFE_FP32C ? 8388608.0 : 262144.0;
   return t;
@@ -55,7 +58,7 @@ Tuning tuning_for(ffe_context* ctx, const ffe_plan* p) {
   }
   auto it = ctx->tuned.find(tuning_key(ctx, p));
   if (it != ctx->tuned.end()) return it->second;
-  return default_tuning(p->prec);
+  return default_tuning(p->prec, p->variant);
 }
 
 void tuning_load(ffe_context* ctx) {

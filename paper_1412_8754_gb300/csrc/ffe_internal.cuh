@@ -69,8 +69,8 @@ struct GroupDesc {
   int32_t layout;     // kLayoutProduct / kLayoutList
   int32_t n_delta;    // PRODUCT: Delta values; LIST: outputs
   int32_t n_ht;       // PRODUCT: (h,T) pairs; LIST: outputs
-  int32_t n_hblk;     // PRODUCT: ceil(n_ht/32); LIST: 1
-  int32_t n_batches;  // PRODUCT: n_delta*n_hblk; LIST: ceil(n_out/32)
+  int32_t n_hblk;     // PRODUCT: ceil(n_ht/hb); LIST: 1
+  int32_t n_batches;  // PRODUCT: n_hblk*ceil(n_delta/(32/hb)); LIST: ceil(n_out/32)
   int32_t n_h;        // distinct h values of the group (for the M sum)
   int32_t n_out;      // outputs of the group
   int64_t out_off;    // first output in the global output arrays
@@ -80,11 +80,38 @@ struct GroupDesc {
   int64_t h_off;      // first entry of the distinct-h list and of the M sums
   double qx, qy;
   int32_t band_only;  // 0: every band; b + 1: band b only (bands in ascending order of energy)
-  int32_t pad;
+  int32_t hb;         // PRODUCT: (h,T) entries per batch (a power of two <= 32; 0 means 32)
   int64_t e3_off;     // three-band model: first entry of the group's band tables
                       // (k + Q/2 at e3_off + k, -k + Q/2 at e3_off + N^2 + k)
   int64_t kst_off;    // FP32 k-state table: entry of (pair, k) at kst_off + pair N^2 + k
 };
+
+// PRODUCT batches are tiles of hb (h,T) entries x db = 32/hb Delta values:
+// lane l holds Delta dblk db + l / hb and entry hblk hb + l % hb.  Batches run
+// h-block-major, b = hblk n_dblk + dblk, so a work item (consecutive batches
+// of one h-block) spans the h range of hb entries only.  hb = 32 is the plain
+// layout: one Delta and 32 entries per batch.
+__host__ __device__ inline int tile_hb(const GroupDesc& g) { return g.hb > 0 ? g.hb : 32; }
+__host__ __device__ inline int tile_db(const GroupDesc& g) { return 32 / tile_hb(g); }
+__host__ __device__ inline int tile_n_dblk(const GroupDesc& g) {
+  const int db = tile_db(g);
+  return (g.n_delta + db - 1) / db;
+}
+// Delta index and (h,T) entry of lane `lane` in PRODUCT batch b (in range or not).
+__host__ __device__ inline void tile_pos(const GroupDesc& g, int b, int lane, int& di, int& hi) {
+  const int hb = tile_hb(g), nd = tile_n_dblk(g);
+  const int hblk = b / nd, dblk = b - hblk * nd;
+  di = dblk * (32 / hb) + lane / hb;
+  hi = hblk * hb + (lane & (hb - 1));
+}
+// Outputs of PRODUCT batch b that exist: (Delta rows) x (entries).
+__host__ __device__ inline int tile_outputs(const GroupDesc& g, int b) {
+  const int hb = tile_hb(g), db = 32 / hb, nd = tile_n_dblk(g);
+  const int hblk = b / nd, dblk = b - hblk * nd;
+  const int rows = g.n_delta - dblk * db < db ? g.n_delta - dblk * db : db;
+  const int cols = g.n_ht - hblk * hb < hb ? g.n_ht - hblk * hb : hb;
+  return rows * cols;
+}
 
 // Bands are evaluated two at a time, as the two halves of packed operations:
 // the two-band model in one pair, the three-band model in two, (0, 1) and

@@ -105,37 +105,47 @@ __device__ __forceinline__ void build_states(const KsumArgs& a, const GroupDesc&
 }
 
 // Stage the parameters of batch b (32 outputs) into this warp's shared slot.
-// Returns the number of valid outputs in the batch.
+// Returns the number of rows to evaluate: LIST, the valid outputs (a prefix);
+// PRODUCT, up to the last valid lane (a lane inside that range whose entry
+// lies past n_ht is staged with c = 0 and its row is ignored).  delta_i:
+// PRODUCT, the Delta of lane 0 (the batch's Delta when hb = 32).
 template <typename Real, int LAYOUT>
 __device__ __forceinline__ int stage_batch(const KsumArgs& a, const GroupDesc& g, int b, int lane,
                                            BPar<Real>* bp, int& delta_i) {
   int nvalid;
+  bool valid;
   int64_t ht_e, d_e;
   if (LAYOUT == kLayoutProduct) {
-    delta_i = b / g.n_hblk;
-    const int j0 = (b - delta_i * g.n_hblk) * 32;
-    nvalid = min(32, g.n_ht - j0);
-    ht_e = g.ht_off + j0 + lane;
-    d_e = g.delta_off + delta_i;
+    const int hb = tile_hb(g);
+    int di, hi, di0, hi0;
+    tile_pos(g, b, lane, di, hi);
+    tile_pos(g, b, 0, di0, hi0);
+    delta_i = di0;
+    const int rows = min(32 / hb, g.n_delta - di0), cols = min(hb, g.n_ht - hi0);
+    nvalid = (rows - 1) * hb + cols;
+    valid = di < g.n_delta && hi < g.n_ht;
+    ht_e = g.ht_off + hi;
+    d_e = g.delta_off + di;
   } else {
     delta_i = -1;
     const int o0 = b * 32;
     nvalid = min(32, g.n_out - o0);
+    valid = lane < nvalid;
     ht_e = g.ht_off + o0 + lane;
     d_e = g.delta_off + o0 + lane;
   }
   __syncwarp();
   BPar<Real> p;
-  if (lane < nvalid) {
+  if (valid) {
     if constexpr (std::is_same<Real, float>::value) {
       const HTf q = a.htf[ht_e];
-      p.d2 = (LAYOUT == kLayoutList) ? a.d2f[d_e] : 0.0f;
+      p.d2 = a.d2f[d_e];
       p.h = q.h;
       p.c = q.c;
       p.tl = q.tl;
     } else {
       const HTd q = a.htd[ht_e];
-      const double dd = (LAYOUT == kLayoutList) ? a.delta[d_e] : 0.0;
+      const double dd = a.delta[d_e];
       p.d2 = dd * dd;
       p.h = q.h;
       p.inv_t = q.inv_t;
@@ -340,25 +350,30 @@ __device__ __forceinline__ double moments_sum(const double (&M)[kMoments], doubl
 // One batch of up to 32 outputs.  Output j's per-lane sum goes to row j of
 // the warp's transpose buffer `red` (row stride 36 floats); lane l then adds
 // row l.  The output loop stays rolled (small code); returns in lane l the
-// warp total of output l (0 for l >= nvalid).
+// warp total of output l (0 for l >= nvalid).  Shared-T batches (ProductUT)
+// are tiles of rows of hb outputs sharing a Delta: R and a once per row.
 template <int KPT, int VARIANT, bool SINGLE>
 __device__ __forceinline__ float eval_batch32(const KState32 (&st)[KPT], const BParF* bp, int nvalid,
-                                              float d2_product, int lane, float* red) {
+                                              float d2_product, int lane, float* red, int hb = 32) {
   if (VARIANT == kLayoutProductUT) {
     const float c = bp[0].c;
     const float2 c2 = make_float2(c, c), nc2 = make_float2(-c, -c);
-    float2 A1[KPT], A2[KPT], Ac[KPT];
+    for (int j0 = 0; j0 < nvalid; j0 += hb) {
+      const float d2 = bp[j0].d2;
+      float2 A1[KPT], A2[KPT], Ac[KPT];
 #pragma unroll
-    for (int k = 0; k < KPT; ++k) {
-      float2 R, A;
-      ra32(st[k], d2_product, R, A);
-      const float2 Rc = __fmul2_rn(R, c2);
-      A1[k] = __ffma2_rn(st[k].d0, nc2, Rc);
-      A2[k] = __ffma2_rn(st[k].d0, c2, Rc);
-      Ac[k] = __fmul2_rn(A, c2);
-    }
+      for (int k = 0; k < KPT; ++k) {
+        float2 R, A;
+        ra32(st[k], d2, R, A);
+        const float2 Rc = __fmul2_rn(R, c2);
+        A1[k] = __ffma2_rn(st[k].d0, nc2, Rc);
+        A2[k] = __ffma2_rn(st[k].d0, c2, Rc);
+        Ac[k] = __fmul2_rn(A, c2);
+      }
+      const int j1 = min(nvalid, j0 + hb);
 #pragma unroll 4
-    for (int j = 0; j < nvalid; ++j) red[j * 36 + lane] = w_out32_ut<KPT, SINGLE>(A1, A2, Ac, c * bp[j].h);
+      for (int j = j0; j < j1; ++j) red[j * 36 + lane] = w_out32_ut<KPT, SINGLE>(A1, A2, Ac, c * bp[j].h);
+    }
   } else if (VARIANT == kLayoutProduct) {
     float2 R[KPT], A[KPT];
 #pragma unroll
@@ -542,7 +557,9 @@ __device__ __forceinline__ void item64(const KsumArgs& a, const WorkItem& w, con
     if (__any_sync(kFull, far[0][0] || far[0][1] || (KPT > 1 && (far[KPT - 1][0] || far[KPT - 1][1])))) {
       if (kG == kLayoutProduct) {
         for (int b = w.b0; b < w.b1; ++b) {
-          const double dd = a.delta[g.delta_off + b / g.n_hblk];
+          int di0, hi0;  // hb = 32 in FP64 plans: one Delta per batch
+          tile_pos(g, b, 0, di0, hi0);
+          const double dd = a.delta[g.delta_off + di0];
           double S = 0.0;
 #pragma unroll
           for (int k = 0; k < KPT; ++k)
@@ -607,9 +624,8 @@ __device__ __forceinline__ void item64(const KsumArgs& a, const WorkItem& w, con
 __device__ __forceinline__ int batch_output(const GroupDesc& g, int b, int lane, int& delta_i,
                                             int& ht_i) {
   if (g.layout == kLayoutProduct) {
-    delta_i = b / g.n_hblk;
-    ht_i = (b - delta_i * g.n_hblk) * 32 + lane;
-    if (ht_i >= g.n_ht) return -1;
+    tile_pos(g, b, lane, delta_i, ht_i);
+    if (ht_i >= g.n_ht || delta_i >= g.n_delta) return -1;
     return delta_i * g.n_ht + ht_i;
   }
   const int o = b * 32 + lane;
@@ -660,10 +676,11 @@ __device__ __forceinline__ void flush32(const KsumArgs& a, const WorkItem& w, co
   }
   const bool single = __all_sync(kFull, sgl);  // warp-uniform: one ex2 per near band
   int64_t outs = 0;
+  const int hb = tile_hb(g);
   for (int b = w.b0; b < w.b1; ++b) {
     int di;
     const int nvalid = stage_batch<float, kG>(a, g, b, lane, bp, di);
-    outs += nvalid;
+    outs += kG == kLayoutList ? nvalid : tile_outputs(g, b);
     float tot;
     // LIST: a batch whose outputs share Delta (a golden-section search whose lines took the same
     // decisions, a reference at Delta = 0) forms R and a once per slot, and with one T too takes
@@ -685,9 +702,9 @@ __device__ __forceinline__ void flush32(const KsumArgs& a, const WorkItem& w, co
         tot = single ? eval_batch32<KPT, LAYOUT, true>(st, bp, nvalid, 0.0f, lane, red)
                      : eval_batch32<KPT, LAYOUT, false>(st, bp, nvalid, 0.0f, lane, red);
     } else {
-      const float d2p = a.d2f[g.delta_off + di];
-      tot = single ? eval_batch32<KPT, LAYOUT, true>(st, bp, nvalid, d2p, lane, red)
-                   : eval_batch32<KPT, LAYOUT, false>(st, bp, nvalid, d2p, lane, red);
+      const float d2p = a.d2f[g.delta_off + di];  // hb = 32 (plain PRODUCT): the batch's Delta
+      tot = single ? eval_batch32<KPT, LAYOUT, true>(st, bp, nvalid, d2p, lane, red, hb)
+                   : eval_batch32<KPT, LAYOUT, false>(st, bp, nvalid, d2p, lane, red, hb);
     }
     acc[(b - w.b0) * 32 + lane] += (double)tot;
   }
@@ -698,6 +715,47 @@ __device__ __forceinline__ void flush32(const KsumArgs& a, const WorkItem& w, co
       atomicAdd(a.near_evals, (unsigned long long)(n * outs));
       if (single) atomicAdd(a.near_evals + 1, (unsigned long long)(n * outs));
     }
+  }
+}
+
+// PRODUCT far bands outside the series range (closed form): n buffered
+// entries, two per float2 slot.  For each of the item's Delta values r (the
+// Delta rows dbase + r, r < nd_item <= 64) the warp's sum of a over the
+// entries is added, through the transpose buffer, to fsum[r] (the warp's
+// FP64 far sums in shared memory); each output later adds c times its
+// Delta's sum.
+template <int KPT>
+__device__ __forceinline__ void flush_far_product(const KsumArgs& a, const WorkItem& w, const GroupDesc& g, int lane,
+                                                  const int32_t* buf, int n, float* red, int dbase, int nd_item,
+                                                  double* fsum) {
+  KState32 st[KPT];
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) {
+    const int i0 = 2 * k * 32 + lane, i1 = i0 + 32;
+    st[k] = pack32(i0 < n ? band32_at(a, g, buf[i0]) : band32_inert(),
+                   i1 < n ? band32_at(a, g, buf[i1]) : band32_inert());
+  }
+  for (int r0 = 0; r0 < nd_item; r0 += 32) {
+    const int r1 = min(nd_item, r0 + 32);
+#pragma unroll 2
+    for (int r = r0; r < r1; ++r) {
+      const float d2 = a.d2f[g.delta_off + dbase + r];
+      float2 S = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int k = 0; k < KPT; ++k) {
+        float2 R, A;
+        ra32(st[k], d2, R, A);
+        S = __fadd2_rn(S, A);
+      }
+      red[(r - r0) * 36 + lane] = S.x + S.y;
+    }
+    const float tot = transposed_total(red, r1 - r0, lane);  // lane r - r0: Delta r
+    if (lane < r1 - r0) fsum[r0 + lane] += (double)tot;
+  }
+  if (a.near_evals && lane == 0) {
+    int64_t outs = 0;
+    for (int b = w.b0; b < w.b1; ++b) outs += tile_outputs(g, b);
+    atomicAdd(a.near_evals + 2, (unsigned long long)((int64_t)n * outs));
   }
 }
 
@@ -730,8 +788,18 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
   if constexpr (kG == kLayoutList)
 #pragma unroll
     for (int n = 0; n < kMoments; ++n) mom[n * 32 + lane] = 0.0;
-  double far_tot = 0.0;  // PRODUCT: lane (b - b0) holds batch b's sum of a over far bands
-  int n_cf = 0;           // PRODUCT: this lane's far bands outside the series range (eta != 0)
+  // PRODUCT: the item's Delta values are dbase + r, r < nd_item <= 64 (one
+  // h-block, consecutive Delta rows); fsum[r] (shared memory, 64 per warp)
+  // holds the FP64 far sum of Delta r
+  double* fsum = mom;
+  int dbase = 0, nd_item = 0;
+  if constexpr (kG == kLayoutProduct) {
+    const int db = tile_db(g);
+    dbase = (w.b0 % tile_n_dblk(g)) * db;
+    nd_item = min(g.n_delta - dbase, (w.b1 - w.b0) * db);
+    fsum[lane] = 0.0;
+    fsum[lane + 32] = 0.0;
+  }
   const int npairs = band_pairs(a.m.nbands);
   for (int ks = w.kset0; ks < w.kset1; ++ks)
   for (int pair = 0; pair < npairs; ++pair) {
@@ -752,11 +820,9 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
     }
     if constexpr (kG == kLayoutProduct) {
       // Far bands in the series range (y = Delta_max^2 eta^2 / s^2 <= kSeriesY):
-      // the warp's six moments, then lane b - b0 evaluates batch b's
-      // sum_n alpha_n t^n M_n.  The other far bands' a is summed per batch
-      // (every other band gets eta^2 = 0 there, so a = 0).
-      KState32 sf[KPT];
-      bool any_cf = false;
+      // the warp's six moments, then lane r evaluates the item's Delta r
+      // (and r + 32): sum_n alpha_n t^n M_n.  The other far bands go to the
+      // closed-form buffer.
       float2 pm2[kMoments];
 #pragma unroll
       for (int n = 0; n < kMoments; ++n) pm2[n] = make_float2(0.0f, 0.0f);
@@ -773,9 +839,6 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
           pm2[n] = __fadd2_rn(pm2[n], tt);
           tt = __fmul2_rn(tt, y);
         }
-        sf[k] = st[k];
-        sf[k].eta2 = make_float2(f0 && !s0 ? st[k].eta2.x : 0.0f, f1 && !s1 ? st[k].eta2.y : 0.0f);
-        any_cf = any_cf || (f0 && !s0) || (f1 && !s1);
       }
       {
         float M[kMoments];
@@ -788,36 +851,16 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
           M[n] = v;
           anym = anym || v != 0.0f;
         }
-        if (anym && lane < w.b1 - w.b0) {
-          const float t = a.d2f[g.delta_off + (w.b0 + lane) / g.n_hblk] / w.far_d2max;
+        if (anym) {  // lane r: the item's Delta r (and r + 32)
           constexpr float alpha[kMoments] = {0.5f, -0.125f, 0.0625f, -5.0f / 128.0f, 7.0f / 256.0f, -21.0f / 1024.0f};
-          float r = alpha[kMoments - 1] * M[kMoments - 1];
+          for (int r = lane; r < nd_item; r += 32) {
+            const float t = a.d2f[g.delta_off + dbase + r] / w.far_d2max;
+            float v = alpha[kMoments - 1] * M[kMoments - 1];
 #pragma unroll
-          for (int n = kMoments - 2; n >= 0; --n) r = fmaf(t, r, alpha[n] * M[n]);
-          far_tot += (double)(t * r);
-        }
-      }
-      int di = w.b0 / g.n_hblk, hb = w.b0 - di * g.n_hblk;  // batch b = di n_hblk + hb
-      if (__any_sync(kFull, any_cf)) {
-#pragma unroll
-        for (int k = 0; k < KPT; ++k) n_cf += (sf[k].eta2.x != 0.0f) + (sf[k].eta2.y != 0.0f);
-        for (int b = w.b0; b < w.b1; ++b) {
-          const float d2p = a.d2f[g.delta_off + di];
-          if (++hb == g.n_hblk) {
-            hb = 0;
-            ++di;
+            for (int n = kMoments - 2; n >= 0; --n) v = fmaf(t, v, alpha[n] * M[n]);
+            fsum[r] += (double)(t * v);
           }
-          float2 S = make_float2(0.0f, 0.0f);
-#pragma unroll
-          for (int k = 0; k < KPT; ++k) {
-            float2 R, A;
-            ra32(sf[k], d2p, R, A);
-            S = __fadd2_rn(S, A);
-          }
-          red[(b - w.b0) * 36 + lane] = S.x + S.y;
         }
-        // lane b - b0: the warp total of batch b; one FP64 add per lane and k-set
-        far_tot += (double)transposed_total(red, w.b1 - w.b0, lane);
       }
     }
 #pragma unroll
@@ -838,13 +881,13 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
         const unsigned m = __ballot_sync(kFull, nr);
         if (nr) nbuf[n_near + __popc(m & lt)] = e;
         n_near += __popc(m);
+        const bool fe = fr && act && valid[k];
+        const bool ser = fe && eta2 * w.far_d2max <= kSeriesY * s2;  // into the moments
+        const bool cf = fe && !ser;
+        const unsigned mf = __ballot_sync(kFull, cf);
+        if (cf) fbuf[n_far + __popc(mf & lt)] = e;
+        n_far += __popc(mf);
         if constexpr (kG == kLayoutList) {
-          const bool fe = fr && act && valid[k];
-          const bool ser = fe && eta2 * w.far_d2max <= kSeriesY * s2;  // into the moments
-          const bool cf = fe && !ser;
-          const unsigned mf = __ballot_sync(kFull, cf);
-          if (cf) fbuf[n_far + __popc(mf & lt)] = e;
-          n_far += __popc(mf);
           if (ser) {
             moments_add(sl == 0 ? st[k].as.x : st[k].as.y, __fdividef(eta2 * w.far_d2max, s2), pm);
             any_ser = true;
@@ -863,15 +906,19 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
       buffer_shift(nbuf, kFlush, n_near, lane);
       n_near -= kFlush;
     }
-    if constexpr (kG == kLayoutList) {
-      if (n_far >= kFlush) {
+    if (n_far >= kFlush) {
+      if constexpr (kG == kLayoutList)
         flush32<KPT, LAYOUT, true>(a, w, g, lane, fbuf, kFlush, acc, bp, red);
-        buffer_shift(fbuf, kFlush, n_far, lane);
-        n_far -= kFlush;
-      }
+      else
+        flush_far_product<KPT>(a, w, g, lane, fbuf, kFlush, red, dbase, nd_item, fsum);
+      buffer_shift(fbuf, kFlush, n_far, lane);
+      n_far -= kFlush;
     }
   }
   if (n_near > 0) flush32<KPT, LAYOUT, false>(a, w, g, lane, nbuf, n_near, acc, bp, red);
+  if constexpr (kG == kLayoutProduct) {
+    if (n_far > 0) flush_far_product<KPT>(a, w, g, lane, fbuf, n_far, red, dbase, nd_item, fsum);
+  }
   if constexpr (kG == kLayoutList) {
     if (n_far > 0) flush32<KPT, LAYOUT, true>(a, w, g, lane, fbuf, n_far, acc, bp, red);
     // the moments' warp totals, then per output c sum_n alpha_n t^n M_n
@@ -898,26 +945,20 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
       }
     }
   } else {
-    int t = n_cf;  // closed-form far band evaluations: entries x outputs
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
-    if (a.near_evals && lane == 0 && t > 0) {
-      int64_t outs = 0;
-      for (int b = w.b0; b < w.b1; ++b) outs += min(32, g.n_ht - (b % g.n_hblk) * 32);
-      atomicAdd(a.near_evals + 2, (unsigned long long)((int64_t)t * outs));
-    }
+    const int hb = tile_hb(g), db = 32 / hb;
+    __syncwarp();
     for (int b = w.b0; b < w.b1; ++b) {
       int di;
       stage_batch<float, kG>(a, g, b, lane, bp, di);
-      const double F = __shfl_sync(kFull, far_tot, b - w.b0);
-      acc[(b - w.b0) * 32 + lane] += (double)bp[lane].c * F;  // c = 0 on lanes without an output
+      const int r = min(63, (b - w.b0) * db + lane / hb);  // the item's Delta index of this lane's output
+      acc[(b - w.b0) * 32 + lane] += (double)bp[lane].c * fsum[r];  // c = 0 without an output
     }
   }
   __syncwarp();
 }
 
 template <typename Real, int KPT, int LAYOUT>
-__global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
+__global__ void __launch_bounds__(256, (sizeof(Real) == 4 && KPT <= 4) ? 2 : 1) ksum_kernel(const KsumArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -928,17 +969,19 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
   unsigned char* after_acc = smem_raw + (size_t)nwarps * kMB * 32 * sizeof(double);
   BPar<Real>* bp = reinterpret_cast<BPar<Real>*>(after_acc) + warp * 32;
   // FP32 only: per-warp 32 x 36 transpose buffer of the output reduction and
-  // the entry buffers (near; LIST also far closed form), kbuf_entries(KPT) each
+  // the entry buffers (near, far closed form), kbuf_entries(KPT) each
   unsigned char* after_bp = after_acc + (size_t)nwarps * 32 * sizeof(BPar<Real>);
   float* red = reinterpret_cast<float*>(after_bp) + warp * 32 * 36;
-  constexpr int kBufs = (LAYOUT == kLayoutList) ? 2 : 1;  // near (+ far closed form for LIST)
+  constexpr int kBufs = 2;  // near, far closed form
   int32_t* nbuf = reinterpret_cast<int32_t*>(after_bp + (size_t)nwarps * 32 * 36 * sizeof(float)) +
                   (size_t)warp * kBufs * kbuf_entries(KPT);
   int32_t* fbuf = nbuf + (kBufs > 1 ? 1 : 0) * kbuf_entries(KPT);
-  // LIST: per-lane FP64 far-band moments, kMoments x 32 per warp
+  // LIST: per-lane FP64 far-band moments, kMoments x 32 per warp; PRODUCT:
+  // the FP64 far sums of the item's (at most 64) Delta values
+  constexpr int kMomStride = (LAYOUT == kLayoutList) ? kMoments * 32 : 64;
   double* mom = reinterpret_cast<double*>(after_bp + (size_t)nwarps * 32 * 36 * sizeof(float) +
                                           (size_t)nwarps * kBufs * kbuf_entries(KPT) * sizeof(int32_t)) +
-                (size_t)warp * kMoments * 32;
+                (size_t)warp * kMomStride;
   // FP64 only: per-warp 32 x 33 transpose buffer and near-entry buffer
   double* red64 = reinterpret_cast<double*>(after_bp) + (size_t)warp * 32 * 33;
   if constexpr (!std::is_same<Real, float>::value)
@@ -952,7 +995,9 @@ __global__ void __launch_bounds__(256) ksum_kernel(const KsumArgs a) {
     const WorkItem w = a.items[it];
     const GroupDesc g = a.groups[w.group];
     const int nb = w.b1 - w.b0;
-    if (nb > kMB || g.layout != kGroupLayout) {
+    const bool bad_tile = kGroupLayout == kLayoutProduct &&
+                          (w.b0 / tile_n_dblk(g) != (w.b1 - 1) / tile_n_dblk(g) || nb * tile_db(g) > 64);
+    if (nb > kMB || g.layout != kGroupLayout || bad_tile) {
       if (lane == 0) atomicOr(a.status, 1);
       continue;
     }
@@ -1005,8 +1050,8 @@ cudaError_t kstate_table_launch(const KsumArgs& a, int n_groups, int max_n, cuda
 size_t ksum_smem_bytes(int prec, int layout, int kpt, int block_threads) {
   const int nw = block_threads / 32;
   const size_t par = (prec == 1) ? sizeof(BParF) : sizeof(BParD);
-  const int bufs = layout == kLayoutList ? 2 : 1;
-  const size_t mom = layout == kLayoutList ? (size_t)kMoments * 32 * sizeof(double) : 0;
+  const int bufs = 2;
+  const size_t mom = (layout == kLayoutList ? (size_t)kMoments * 32 : 64) * sizeof(double);
   const size_t red = (prec == 1) ? 32 * 36 * sizeof(float) + (size_t)bufs * kbuf_entries(kpt) * sizeof(int32_t) + mom
                                  : 32 * 33 * sizeof(double) + (size_t)kbuf64_entries(kpt) * sizeof(int32_t);
   const int mb = max_batches(layout == kLayoutList ? kLayoutList : kLayoutProduct);

@@ -178,6 +178,7 @@ double plan_k_evals(const ffe_plan* p);
 void build_items(ffe_plan* p);
 void build_mitems(ffe_plan* p);
 bool batches_share_T(const ffe_plan* p);
+void apply_tiles(ffe_plan* p, bool shared_t);
 ffe_status fetch_scan(ffe_context* ctx, ffe_plan* p, ffe_result* per_point, int8_t* labels, int32_t* best_q,
                       cudaStream_t s);
 // MLP inference on device arrays (mlp.cu): y[n] (network units) at raw x[n][4].
