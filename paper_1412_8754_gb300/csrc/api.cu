@@ -89,8 +89,8 @@ namespace ffe {
 
 // Split every group's (batches x k-sets) into warp work items of roughly
 // `target` k-point evaluations, segments of <= max_batches(layout) batches.
-// FP32 path: a k-point is "far" for an item when, with h in [hlo, hhi] and
-// T <= Tmax over the item's outputs, min over bands of
+// FP32 path: a band is "far" for an item when, with h in [hlo, hhi] and
+// T <= Tmax over the item's outputs,
 // |s| - max(|d0 - hlo|, |d0 - hhi|) >= tgap = 27 ln2 Tmax (+1e-5 against FP32
 // rounding): then every output has c |R -+ d| >= 27, each factor
 // (1 + 2^-c|R-+d|) leaves the FP32 product unchanged (P + P e with P e below
@@ -175,9 +175,11 @@ void build_items(ffe_plan* p) {
     const int64_t nk = (int64_t)g.N * g.N;
     const int n_ksets = (int)((nk + kset_pts - 1) / kset_pts);
     // segments: LIST, <= kMaxBatchesList batches; PRODUCT, consecutive batches of one h-block
-    // spanning at most 64 Delta values (the k-sum keeps two far sums per lane)
+    // spanning at most kMaxTileDeltas Delta values (FP32: the warp's far sums per Delta)
     const bool prod = g.layout == kLayoutProduct;
-    const int sb = prod ? std::min(kMaxBatchesPerItem, 64 / tile_db(g)) : max_batches(g.layout);
+    const bool f32 = p->prec == FFE_FP32C;
+    const int sb = prod ? std::min(max_batches(g.layout, f32), (f32 ? kMaxTileDeltas : 32) / tile_db(g))
+                        : max_batches(g.layout, f32);
     const int run = prod ? tile_n_dblk(g) : std::max(1, g.n_batches);  // batches per h-block
     for (int b0 = 0; b0 < g.n_batches;) {
       const int b1 = std::min(b0 - b0 % run + run, b0 + sb);

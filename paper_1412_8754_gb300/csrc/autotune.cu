@@ -34,12 +34,13 @@ static std::string tuning_key(const ffe_context* ctx, const ffe_plan* p) {
   return k;
 }
 
-// Defaults measured on GB300: FP32 shared-T tiles 2 k-points per thread
-// (34.7 ms against 46.1 ms with 4 on the N = 1024 FFLO scan), the other FP32
-// layouts 4 (LIST: 683 ms against 736 ms with 2 on a golden diagram), FP64 1.
+// Defaults measured on GB300: FP32 PRODUCT 2 k-points per thread (34.7 ms
+// against 46.1 ms with 4 on the N = 1024 FFLO scan; 4 would also leave room
+// for only one block per SM), LIST 4 (683 ms against 736 ms with 2 on a golden
+// diagram), FP64 1.
 static Tuning default_tuning(int prec, int variant) {
   Tuning t;
-  t.kpt = prec == FFE_FP32C ? (variant == kLayoutProductUT ? 2 : 4) : 1;
+  t.kpt = prec == FFE_FP32C ? (variant == kLayoutList ? 4 : 2) : 1;
   t.block = 256;
   t.item_target = prec == FFE_FP32C ? 8388608.0 : 262144.0;
   return t;

@@ -26,13 +26,18 @@ constexpr int kWarp = 32;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kLayoutProduct = 0;  // outputs = Delta-list x (h,T)-list, shared R per Delta
 constexpr int kLayoutList = 1;     // outputs = explicit (Delta, h, T) triples
-constexpr int kLayoutProductUT = 2;  // kernel variant of PRODUCT: one T per 32-output batch
-constexpr int kMaxBatchesPerItem = 16;  // batches (of 32 outputs) per work item, at most
-// LIST items take 8: their three entry buffers leave room for only 8 FP64
-// accumulator rows per warp at 16 warps per SM
+constexpr int kLayoutProductUT = 2;  // kernel variant of PRODUCT: one T per tile of a batch
+// Batches (of 32 outputs) per work item, at most: the FP64 accumulator rows a
+// warp keeps in shared memory at 16 warps per SM.  FP32 PRODUCT items take 24
+// (the per-k-point classification is shared by 768 outputs) and at most
+// kMaxTileDeltas Delta rows (the warp's FP64 far sums); FP64 PRODUCT items 16;
+// LIST items 8 (their entry buffers and moments take the rest).
+constexpr int kMaxBatchesPerItem = 16;
+constexpr int kMaxBatchesTile = 24;
+constexpr int kMaxTileDeltas = 96;
 constexpr int kMaxBatchesList = 8;
-__host__ __device__ constexpr int max_batches(int group_layout) {
-  return group_layout == kLayoutList ? kMaxBatchesList : kMaxBatchesPerItem;
+__host__ __device__ constexpr int max_batches(int group_layout, bool fp32) {
+  return group_layout == kLayoutList ? kMaxBatchesList : (fp32 ? kMaxBatchesTile : kMaxBatchesPerItem);
 }
 constexpr int kFlagRescored = 1;  // values of include/ffe.h FFE_FLAG_*
 constexpr int kFlagEdge = 2;

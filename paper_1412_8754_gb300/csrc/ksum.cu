@@ -31,8 +31,8 @@ namespace ffe {
 __host__ __device__ constexpr int kbuf_entries(int kpt) { return 128 * kpt; }
 
 // Batch parameters staged in shared memory, one entry per output of a batch.
-struct BParF {  // FP32: Delta^2 (LIST only), h, c = 1/(T ln 2), T ln 2
-  float d2, h, c, tl;
+struct BParF {  // FP32: Delta^2, h, c = 1/(T ln 2), c h
+  float d2, h, c, ch;
 };
 struct BParD {  // FP64: Delta^2 (LIST only), h, 1/T, T
   double d2, h, inv_t, t;
@@ -142,7 +142,7 @@ __device__ __forceinline__ int stage_batch(const KsumArgs& a, const GroupDesc& g
       p.d2 = a.d2f[d_e];
       p.h = q.h;
       p.c = q.c;
-      p.tl = q.tl;
+      p.ch = q.c * q.h;
     } else {
       const HTd q = a.htd[ht_e];
       const double dd = a.delta[d_e];
@@ -156,7 +156,7 @@ __device__ __forceinline__ int stage_batch(const KsumArgs& a, const GroupDesc& g
     p.h = 0;
     if constexpr (std::is_same<Real, float>::value) {
       p.c = 0;
-      p.tl = 0;
+      p.ch = 0;
     } else {
       p.inv_t = 0;
       p.t = 0;
@@ -206,9 +206,8 @@ __device__ __forceinline__ void build_states32(const KsumArgs& a, const GroupDes
 }
 
 // A buffered (k-point, band) entry: lattice index | band pair << kPairBit |
-// band slot << kSlotBit | single << kSingleBit (lattice index < 8192^2 = 2^26;
-// single: c (R + |d|) >= 27 for every output of the item).
-constexpr int kPairBit = 27, kSlotBit = 28, kSingleBit = 29;
+// band slot << kSlotBit (lattice index < 8192^2 = 2^26).
+constexpr int kPairBit = 27, kSlotBit = 28;
 constexpr int32_t kKidxMask = (1 << 26) - 1;
 
 // One band of one entry: eta^2, |s|, s^2, d0; an inert band past the end.
@@ -230,6 +229,16 @@ __device__ __forceinline__ Band32 band32_at(const KsumArgs& a, const GroupDesc& 
 }
 
 __device__ __forceinline__ Band32 band32_inert() { return Band32{0.0f, 1e15f, 1e30f, 0.0f}; }
+
+// Single band: c (R + |d|) >= 27 for every output of the item (R + |d| >=
+// sgl_r, from R^2 >= s^2 + Delta_min^2 eta^2 and |d| >= the distance of d0
+// from [hlo, hhi]), so its second factor (1 + 2^-c(R + |d|)) is 1 in FP32 and
+// one exponential, of min(|y1|, |y2|) = c |R - |d||, gives its term.  The
+// inert band counts as single.
+__device__ __forceinline__ bool single_band32(const Band32& b, const WorkItem& w) {
+  const float t = w.sgl_r - fmaxf(0.0f, fmaxf(w.far_hlo - b.d0, b.d0 - w.far_hhi));
+  return t <= 0.0f || fmaf(w.sgl_d2min, b.eta2, b.s2) >= t * t;
+}
 
 __device__ __forceinline__ KState32 pack32(const Band32& x, const Band32& y) {
   KState32 t;
@@ -331,6 +340,14 @@ __device__ __forceinline__ float transposed_total(float* red, int nvalid, int la
 // Delta), not once per output.
 constexpr int kMoments = 6;
 constexpr float kSeriesY = 0.1f;
+// Kahan's compensated summation: s + x with the rounding error carried in c
+// (the sum is s - c); additions only, so nothing is fused or reordered.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
 __device__ __forceinline__ void moments_add(float as, float y, float (&pm)[kMoments]) {
   float t = as * y;
 #pragma unroll
@@ -371,8 +388,9 @@ __device__ __forceinline__ float eval_batch32(const KState32 (&st)[KPT], const B
         Ac[k] = __fmul2_rn(A, c2);
       }
       const int j1 = min(nvalid, j0 + hb);
-#pragma unroll 4
-      for (int j = j0; j < j1; ++j) red[j * 36 + lane] = w_out32_ut<KPT, SINGLE>(A1, A2, Ac, c * bp[j].h);
+      // four outputs in flight at 2 k-points per thread; two at 4 (registers)
+#pragma unroll(KPT <= 2 ? 4 : 2)
+      for (int j = j0; j < j1; ++j) red[j * 36 + lane] = w_out32_ut<KPT, SINGLE>(A1, A2, Ac, bp[j].ch);
     }
   } else if (VARIANT == kLayoutProduct) {
     float2 R[KPT], A[KPT];
@@ -664,14 +682,13 @@ __device__ __forceinline__ void flush32(const KsumArgs& a, const WorkItem& w, co
                                         const int32_t* buf, int n, double* acc, BParF* bp, float* red) {
   constexpr int kG = (LAYOUT == kLayoutList) ? kLayoutList : kLayoutProduct;
   KState32 st[KPT];
-  int sgl = 1;  // every entry of this lane single (padding counts as single)
+  bool sgl = true;  // every entry of this lane single (padding counts as single)
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
     const int i0 = 2 * k * 32 + lane, i1 = i0 + 32;
     const Band32 x = i0 < n ? band32_at(a, g, buf[i0]) : band32_inert();
     const Band32 y = i1 < n ? band32_at(a, g, buf[i1]) : band32_inert();
-    if (i0 < n) sgl &= (buf[i0] >> kSingleBit) & 1;
-    if (i1 < n) sgl &= (buf[i1] >> kSingleBit) & 1;
+    if (!FAR) sgl = sgl && single_band32(x, w) && single_band32(y, w);
     st[k] = pack32(x, y);
   }
   const bool single = __all_sync(kFull, sgl);  // warp-uniform: one ex2 per near band
@@ -720,9 +737,9 @@ __device__ __forceinline__ void flush32(const KsumArgs& a, const WorkItem& w, co
 
 // PRODUCT far bands outside the series range (closed form): n buffered
 // entries, two per float2 slot.  For each of the item's Delta values r (the
-// Delta rows dbase + r, r < nd_item <= 64) the warp's sum of a over the
-// entries is added, through the transpose buffer, to fsum[r] (the warp's
-// FP64 far sums in shared memory); each output later adds c times its
+// Delta rows dbase + r, r < nd_item <= kMaxTileDeltas) the warp's sum of a
+// over the entries is added, through the transpose buffer, to fsum[r] (the
+// warp's FP64 far sums in shared memory); each output later adds c times its
 // Delta's sum.
 template <int KPT>
 __device__ __forceinline__ void flush_far_product(const KsumArgs& a, const WorkItem& w, const GroupDesc& g, int lane,
@@ -788,18 +805,20 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
   if constexpr (kG == kLayoutList)
 #pragma unroll
     for (int n = 0; n < kMoments; ++n) mom[n * 32 + lane] = 0.0;
-  // PRODUCT: the item's Delta values are dbase + r, r < nd_item <= 64 (one
-  // h-block, consecutive Delta rows); fsum[r] (shared memory, 64 per warp)
-  // holds the FP64 far sum of Delta r
+  // PRODUCT: the item's Delta values are dbase + r, r < nd_item <=
+  // kMaxTileDeltas (one h-block, consecutive Delta rows); fsum[r] (shared
+  // memory, per warp) holds the FP64 far sum of Delta r
   double* fsum = mom;
   int dbase = 0, nd_item = 0;
   if constexpr (kG == kLayoutProduct) {
     const int db = tile_db(g);
     dbase = (w.b0 % tile_n_dblk(g)) * db;
     nd_item = min(g.n_delta - dbase, (w.b1 - w.b0) * db);
-    fsum[lane] = 0.0;
-    fsum[lane + 32] = 0.0;
+    for (int r = lane; r < kMaxTileDeltas; r += 32) fsum[r] = 0.0;
   }
+  float msum[kMoments], mcomp[kMoments];  // PRODUCT: this lane's moments (sum, compensation)
+#pragma unroll
+  for (int n = 0; n < kMoments; ++n) msum[n] = mcomp[n] = 0.0f;
   const int npairs = band_pairs(a.m.nbands);
   for (int ks = w.kset0; ks < w.kset1; ++ks)
   for (int pair = 0; pair < npairs; ++pair) {
@@ -820,9 +839,9 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
     }
     if constexpr (kG == kLayoutProduct) {
       // Far bands in the series range (y = Delta_max^2 eta^2 / s^2 <= kSeriesY):
-      // the warp's six moments, then lane r evaluates the item's Delta r
-      // (and r + 32): sum_n alpha_n t^n M_n.  The other far bands go to the
-      // closed-form buffer.
+      // this lane's six moments, summed over the item's k-sets with Kahan's
+      // compensation and over the warp at the end of the item.  The other far
+      // bands go to the closed-form buffer.
       float2 pm2[kMoments];
 #pragma unroll
       for (int n = 0; n < kMoments; ++n) pm2[n] = make_float2(0.0f, 0.0f);
@@ -840,28 +859,8 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
           tt = __fmul2_rn(tt, y);
         }
       }
-      {
-        float M[kMoments];
-        bool anym = false;
 #pragma unroll
-        for (int n = 0; n < kMoments; ++n) {
-          float v = pm2[n].x + pm2[n].y;
-#pragma unroll
-          for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-          M[n] = v;
-          anym = anym || v != 0.0f;
-        }
-        if (anym) {  // lane r: the item's Delta r (and r + 32)
-          constexpr float alpha[kMoments] = {0.5f, -0.125f, 0.0625f, -5.0f / 128.0f, 7.0f / 256.0f, -21.0f / 1024.0f};
-          for (int r = lane; r < nd_item; r += 32) {
-            const float t = a.d2f[g.delta_off + dbase + r] / w.far_d2max;
-            float v = alpha[kMoments - 1] * M[kMoments - 1];
-#pragma unroll
-            for (int n = kMoments - 2; n >= 0; --n) v = fmaf(t, v, alpha[n] * M[n]);
-            fsum[r] += (double)(t * v);
-          }
-        }
-      }
+      for (int n = 0; n < kMoments; ++n) kahan_add(msum[n], mcomp[n], pm2[n].x + pm2[n].y);
     }
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
@@ -872,11 +871,7 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
         const float eta2 = sl == 0 ? st[k].eta2.x : st[k].eta2.y;
         const float s2 = sl == 0 ? st[k].s2.x : st[k].s2.y;
         const float d0 = sl == 0 ? st[k].d0.x : st[k].d0.y;
-        // single: R + |d| >= sgl_r for every output, from R^2 >= s^2 + Delta_min^2 eta^2
-        // and |d| >= the distance of d0 from [hlo, hhi]
-        const float t = w.sgl_r - fmaxf(0.0f, fmaxf(w.far_hlo - d0, d0 - w.far_hhi));
-        const bool sg = t <= 0.0f || fmaf(w.sgl_d2min, eta2, s2) >= t * t;
-        const int32_t e = kidx[k] | (pair << kPairBit) | (sl << kSlotBit) | ((int32_t)sg << kSingleBit);
+        const int32_t e = kidx[k] | (pair << kPairBit) | (sl << kSlotBit);
         const bool nr = !fr && !blocked_band32(d0, eta2, s2, w);  // near implies active and valid
         const unsigned m = __ballot_sync(kFull, nr);
         if (nr) nbuf[n_near + __popc(m & lt)] = e;
@@ -945,12 +940,29 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
       }
     }
   } else {
+    // the moments' warp totals (FP64), then per Delta r of the item
+    // fsum[r] += sum_n alpha_n t^n M_n, t = Delta_r^2 / Delta_max^2
+    double M[kMoments];
+    bool any = false;
+#pragma unroll
+    for (int n = 0; n < kMoments; ++n) {
+      double v = (double)msum[n] - (double)mcomp[n];
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+      M[n] = v;
+      any = any || v != 0.0;
+    }
+    if (any) {
+      const double inv_d2max = 1.0 / (double)w.far_d2max;
+      for (int r = lane; r < nd_item; r += 32)
+        fsum[r] += moments_sum(M, (double)a.d2f[g.delta_off + dbase + r] * inv_d2max);
+    }
     const int hb = tile_hb(g), db = 32 / hb;
     __syncwarp();
     for (int b = w.b0; b < w.b1; ++b) {
       int di;
       stage_batch<float, kG>(a, g, b, lane, bp, di);
-      const int r = min(63, (b - w.b0) * db + lane / hb);  // the item's Delta index of this lane's output
+      const int r = min(kMaxTileDeltas - 1, (b - w.b0) * db + lane / hb);  // this output's Delta in the item
       acc[(b - w.b0) * 32 + lane] += (double)bp[lane].c * fsum[r];  // c = 0 without an output
     }
   }
@@ -958,13 +970,13 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
 }
 
 template <typename Real, int KPT, int LAYOUT>
-__global__ void __launch_bounds__(256, (sizeof(Real) == 4 && KPT <= 4) ? 2 : 1) ksum_kernel(const KsumArgs a) {
+__global__ void __launch_bounds__(256, (sizeof(Real) == 4 ? KPT <= 4 : KPT == 1) ? 2 : 1) ksum_kernel(const KsumArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   constexpr int kGroupLayout = (LAYOUT == kLayoutList) ? kLayoutList : kLayoutProduct;
-  constexpr int kMB = max_batches(kGroupLayout);
+  constexpr int kMB = max_batches(kGroupLayout, std::is_same<Real, float>::value);
   double* acc = reinterpret_cast<double*>(smem_raw) + (size_t)warp * (kMB * 32);
   unsigned char* after_acc = smem_raw + (size_t)nwarps * kMB * 32 * sizeof(double);
   BPar<Real>* bp = reinterpret_cast<BPar<Real>*>(after_acc) + warp * 32;
@@ -978,7 +990,7 @@ __global__ void __launch_bounds__(256, (sizeof(Real) == 4 && KPT <= 4) ? 2 : 1) 
   int32_t* fbuf = nbuf + (kBufs > 1 ? 1 : 0) * kbuf_entries(KPT);
   // LIST: per-lane FP64 far-band moments, kMoments x 32 per warp; PRODUCT:
   // the FP64 far sums of the item's (at most 64) Delta values
-  constexpr int kMomStride = (LAYOUT == kLayoutList) ? kMoments * 32 : 64;
+  constexpr int kMomStride = (LAYOUT == kLayoutList) ? kMoments * 32 : kMaxTileDeltas;
   double* mom = reinterpret_cast<double*>(after_bp + (size_t)nwarps * 32 * 36 * sizeof(float) +
                                           (size_t)nwarps * kBufs * kbuf_entries(KPT) * sizeof(int32_t)) +
                 (size_t)warp * kMomStride;
@@ -996,7 +1008,8 @@ __global__ void __launch_bounds__(256, (sizeof(Real) == 4 && KPT <= 4) ? 2 : 1) 
     const GroupDesc g = a.groups[w.group];
     const int nb = w.b1 - w.b0;
     const bool bad_tile = kGroupLayout == kLayoutProduct &&
-                          (w.b0 / tile_n_dblk(g) != (w.b1 - 1) / tile_n_dblk(g) || nb * tile_db(g) > 64);
+                          (w.b0 / tile_n_dblk(g) != (w.b1 - 1) / tile_n_dblk(g) ||
+                           nb * tile_db(g) > (std::is_same<Real, float>::value ? kMaxTileDeltas : 32));
     if (nb > kMB || g.layout != kGroupLayout || bad_tile) {
       if (lane == 0) atomicOr(a.status, 1);
       continue;
@@ -1051,10 +1064,10 @@ size_t ksum_smem_bytes(int prec, int layout, int kpt, int block_threads) {
   const int nw = block_threads / 32;
   const size_t par = (prec == 1) ? sizeof(BParF) : sizeof(BParD);
   const int bufs = 2;
-  const size_t mom = (layout == kLayoutList ? (size_t)kMoments * 32 : 64) * sizeof(double);
+  const size_t mom = (layout == kLayoutList ? (size_t)kMoments * 32 : kMaxTileDeltas) * sizeof(double);
   const size_t red = (prec == 1) ? 32 * 36 * sizeof(float) + (size_t)bufs * kbuf_entries(kpt) * sizeof(int32_t) + mom
                                  : 32 * 33 * sizeof(double) + (size_t)kbuf64_entries(kpt) * sizeof(int32_t);
-  const int mb = max_batches(layout == kLayoutList ? kLayoutList : kLayoutProduct);
+  const int mb = max_batches(layout == kLayoutList ? kLayoutList : kLayoutProduct, prec == 1);
   return (size_t)nw * (mb * 32 * sizeof(double) + 32 * par + red);
 }
 
