@@ -181,13 +181,15 @@ void build_items(ffe_plan* p) {
     const int sb = prod ? std::min(max_batches(g.layout, f32), (f32 ? kMaxTileDeltas : 32) / tile_db(g))
                         : max_batches(g.layout, f32);
     const int run = prod ? tile_n_dblk(g) : std::max(1, g.n_batches);  // batches per h-block
+    // one k-chunk length for all segments of the group (sized for the widest), so that
+    // chunk c of every segment reads the same k-states
+    int ck = (int)std::max(1.0, std::floor(target / ((double)std::min(sb, g.n_batches) * 32.0 * kset_pts)));
+    ck = std::min(ck, n_ksets);
+    const int n_chunks = (n_ksets + ck - 1) / ck;
+    const size_t first_item = p->items.size();
     for (int b0 = 0; b0 < g.n_batches;) {
       const int b1 = std::min(b0 - b0 % run + run, b0 + sb);
       const int nb = b1 - b0;
-      const double outs = (double)nb * 32.0;
-      int ck = (int)std::max(1.0, std::floor(target / (outs * kset_pts)));
-      ck = std::min(ck, n_ksets);
-      const int n_chunks = (n_ksets + ck - 1) / ck;
       Segment sg;
       sg.group = gi;
       sg.b0 = b0;
@@ -219,14 +221,17 @@ void build_items(ffe_plan* p) {
       }
       b0 = b1;
     }
+    // chunk-major within the group: the segments of one k-chunk run side by side and share
+    // the chunk's k-states in L2
+    std::stable_sort(p->items.begin() + first_item, p->items.end(),
+                     [](const WorkItem& a, const WorkItem& b) { return a.chunk < b.chunk; });
   }
   p->n_partials = poff;
-  // longest first: the queue hands out big items early, small ones fill the tail
-  std::stable_sort(p->items.begin(), p->items.end(), [&](const WorkItem& a, const WorkItem& b) {
-    const double ca = (double)(a.kset1 - a.kset0) * (a.b1 - a.b0);
-    const double cb = (double)(b.kset1 - b.kset0) * (b.b1 - b.b0);
-    return ca > cb;
-  });
+  // longest first: the queue hands out big items early, small ones fill the tail; items
+  // of one size keep their group and chunk order
+  auto cost = [](const WorkItem& w) { return (double)(w.kset1 - w.kset0) * (w.b1 - w.b0); };
+  std::stable_sort(p->items.begin(), p->items.end(),
+                   [&](const WorkItem& a, const WorkItem& b) { return cost(a) > cost(b); });
 }
 
 void build_mitems(ffe_plan* p) {
