@@ -675,11 +675,111 @@ __device__ void finalize_segment(const KsumArgs& a, const Segment& sg, const Gro
   }
 }
 
+// Shared-T items (kLayoutProductUT): the item's batch parameters, staged once per
+// item in the warp's batch-parameter slot as floats -- c = 1/(T ln 2) (one T for
+// the item: its batches are tiles of one h-block), c h of the h-block's hb <= 8
+// entries (0 past n_ht) and Delta^2 of its nd_item <= kMaxTileDeltas Delta rows.
+constexpr int kUtMaxHb = 8, kUtCh = 1, kUtD2 = 1 + kUtMaxHb;
+static_assert(kUtD2 + kMaxTileDeltas <= 32 * (int)(sizeof(BParF) / sizeof(float)),
+              "shared-T item parameters exceed the batch-parameter slot");
+
+__device__ __forceinline__ void stage_item_ut(const KsumArgs& a, const GroupDesc& g, const WorkItem& w, int lane,
+                                              int dbase, int nd_item, float* ip) {
+  const int hb = tile_hb(g);
+  const int e0 = (w.b0 / tile_n_dblk(g)) * hb;  // first (h,T) entry of the item's h-block
+  const int cols = min(hb, g.n_ht - e0);
+  __syncwarp();
+  if (lane < hb) {
+    float c = 0.0f, ch = 0.0f;
+    if (lane < cols) {
+      const HTf q = a.htf[g.ht_off + e0 + lane];
+      c = q.c;
+      ch = q.c * q.h;
+    }
+    ip[kUtCh + lane] = ch;
+    if (lane == 0) ip[0] = c;
+  }
+  for (int r = lane; r < nd_item; r += 32) ip[kUtD2 + r] = a.d2f[g.delta_off + dbase + r];
+  __syncwarp();
+}
+
+// W of one output summed over this lane's KPT slots when every band of the warp
+// is single (single_band32): the one factor that differs from 1 is
+// 1 + 2^-|x| with x = min(y1, y2) = c (R - |d|) (R >= 0 gives
+// min(|y1|, |y2|) = |x|), and the clamp term is max(min(x, c a), 0).  From
+// Rc = c R, D0c = c d0 and Ac = c a per slot: x = Rc - |D0c - c h|.
+template <int KPT>
+__device__ __forceinline__ float w_out32_x(const float2 (&Rc)[KPT], const float2 (&D0c)[KPT],
+                                           const float2 (&Ac)[KPT], float ch) {
+  const float2 nch2 = make_float2(-ch, -ch);
+  float2 cp2 = make_float2(0.0f, 0.0f), P2 = make_float2(1.0f, 1.0f);
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) {
+    const float2 t = __fadd2_rn(D0c[k], nch2);  // c d
+    const float x0 = Rc[k].x - fabsf(t.x), x1 = Rc[k].y - fabsf(t.y);
+    P2 = __ffma2_rn(P2, make_float2(ex2a(-fabsf(x0)), ex2a(-fabsf(x1))), P2);
+    cp2 = __fadd2_rn(cp2, make_float2(fmaxf(fminf(x0, Ac[k].x), 0.0f), fmaxf(fminf(x1, Ac[k].y), 0.0f)));
+  }
+  return (cp2.x + cp2.y) + lg2a(P2.x * P2.y);
+}
+
+// Near entries of a shared-T item on each of its batches: per Delta row R and a
+// once per slot, then the hb outputs of the row (single bands: from c R, c d0
+// and c a; otherwise from A1 = c (R - d0), A2 = c (R + d0) and c a); the
+// batch's per-lane sums go through the transpose buffer into acc.
+template <int KPT, bool SINGLE>
+__device__ __forceinline__ void flush_batches_ut(const KState32 (&st)[KPT], const WorkItem& w, const GroupDesc& g,
+                                                 int lane, const float* ip, int nd_item, double* acc, float* red) {
+  const int hb = tile_hb(g), db = 32 / hb;
+  const int cols = min(hb, g.n_ht - (w.b0 / tile_n_dblk(g)) * hb);
+  const float c = ip[0];
+  const float2 c2 = make_float2(c, c), nc2 = make_float2(-c, -c);
+  float2 D0c[KPT];
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) D0c[k] = __fmul2_rn(st[k].d0, c2);
+  for (int b = w.b0; b < w.b1; ++b) {
+    const int rb = (b - w.b0) * db;  // the batch's first Delta row in the item
+    const int rows = min(db, nd_item - rb);
+    const int nvalid = (rows - 1) * hb + cols;
+    for (int r = 0; r < rows; ++r) {
+      const float d2 = ip[kUtD2 + rb + r];
+      const int j0 = r * hb, j1 = min(nvalid, j0 + hb);
+      if constexpr (SINGLE) {
+        float2 Rc[KPT], Ac[KPT];
+#pragma unroll
+        for (int k = 0; k < KPT; ++k) {
+          float2 R, A;
+          ra32(st[k], d2, R, A);
+          Rc[k] = __fmul2_rn(R, c2);
+          Ac[k] = __fmul2_rn(A, c2);
+        }
+#pragma unroll(KPT <= 2 ? 4 : 2)
+        for (int j = j0; j < j1; ++j) red[j * 36 + lane] = w_out32_x<KPT>(Rc, D0c, Ac, ip[kUtCh + j - j0]);
+      } else {
+        float2 A1[KPT], A2[KPT], Ac[KPT];
+#pragma unroll
+        for (int k = 0; k < KPT; ++k) {
+          float2 R, A;
+          ra32(st[k], d2, R, A);
+          const float2 Rc = __fmul2_rn(R, c2);
+          A1[k] = __ffma2_rn(st[k].d0, nc2, Rc);
+          A2[k] = __ffma2_rn(st[k].d0, c2, Rc);
+          Ac[k] = __fmul2_rn(A, c2);
+        }
+#pragma unroll(KPT <= 2 ? 4 : 2)
+        for (int j = j0; j < j1; ++j) red[j * 36 + lane] = w_out32_ut<KPT, false>(A1, A2, Ac, ip[kUtCh + j - j0]);
+      }
+    }
+    acc[(b - w.b0) * 32 + lane] += (double)transposed_total(red, nvalid, lane);
+  }
+}
+
 // FP32 evaluation of n buffered (k-point, band) entries on every batch of the
 // item, two entries per float2 slot: the full term, or the far form W = c a.
 template <int KPT, int LAYOUT, bool FAR>
 __device__ __forceinline__ void flush32(const KsumArgs& a, const WorkItem& w, const GroupDesc& g, int lane,
-                                        const int32_t* buf, int n, double* acc, BParF* bp, float* red) {
+                                        const int32_t* buf, int n, double* acc, BParF* bp, float* red,
+                                        int nd_item = 0) {
   constexpr int kG = (LAYOUT == kLayoutList) ? kLayoutList : kLayoutProduct;
   KState32 st[KPT];
   bool sgl = true;  // every entry of this lane single (padding counts as single)
@@ -693,6 +793,19 @@ __device__ __forceinline__ void flush32(const KsumArgs& a, const WorkItem& w, co
   }
   const bool single = __all_sync(kFull, sgl);  // warp-uniform: one ex2 per near band
   int64_t outs = 0;
+  if constexpr (LAYOUT == kLayoutProductUT && !FAR) {  // parameters staged per item (stage_item_ut)
+    const float* ip = reinterpret_cast<const float*>(bp);
+    if (single)
+      flush_batches_ut<KPT, true>(st, w, g, lane, ip, nd_item, acc, red);
+    else
+      flush_batches_ut<KPT, false>(st, w, g, lane, ip, nd_item, acc, red);
+    if (a.near_evals && lane == 0) {
+      for (int b = w.b0; b < w.b1; ++b) outs += tile_outputs(g, b);
+      atomicAdd(a.near_evals, (unsigned long long)(n * outs));
+      if (single) atomicAdd(a.near_evals + 1, (unsigned long long)(n * outs));
+    }
+    return;
+  }
   const int hb = tile_hb(g);
   for (int b = w.b0; b < w.b1; ++b) {
     int di;
@@ -815,6 +928,7 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
     dbase = (w.b0 % tile_n_dblk(g)) * db;
     nd_item = min(g.n_delta - dbase, (w.b1 - w.b0) * db);
     for (int r = lane; r < kMaxTileDeltas; r += 32) fsum[r] = 0.0;
+    if constexpr (LAYOUT == kLayoutProductUT) stage_item_ut(a, g, w, lane, dbase, nd_item, reinterpret_cast<float*>(bp));
   }
   float msum[kMoments], mcomp[kMoments];  // PRODUCT: this lane's moments (sum, compensation)
 #pragma unroll
@@ -862,6 +976,11 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
 #pragma unroll
       for (int n = 0; n < kMoments; ++n) kahan_add(msum[n], mcomp[n], pm2[n].x + pm2[n].y);
     }
+    // near bands and far bands in the closed form are appended to their buffers; most k-sets
+    // hold neither (they cluster where the lattice row crosses a Fermi line), and the warp
+    // then skips the ballots
+    bool nr[KPT][2], cf[KPT][2];
+    bool any_buf = false;
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
 #pragma unroll
@@ -871,22 +990,31 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
         const float eta2 = sl == 0 ? st[k].eta2.x : st[k].eta2.y;
         const float s2 = sl == 0 ? st[k].s2.x : st[k].s2.y;
         const float d0 = sl == 0 ? st[k].d0.x : st[k].d0.y;
-        const int32_t e = kidx[k] | (pair << kPairBit) | (sl << kSlotBit);
-        const bool nr = !fr && !blocked_band32(d0, eta2, s2, w);  // near implies active and valid
-        const unsigned m = __ballot_sync(kFull, nr);
-        if (nr) nbuf[n_near + __popc(m & lt)] = e;
-        n_near += __popc(m);
+        nr[k][sl] = !fr && !blocked_band32(d0, eta2, s2, w);  // near implies active and valid
         const bool fe = fr && act && valid[k];
         const bool ser = fe && eta2 * w.far_d2max <= kSeriesY * s2;  // into the moments
-        const bool cf = fe && !ser;
-        const unsigned mf = __ballot_sync(kFull, cf);
-        if (cf) fbuf[n_far + __popc(mf & lt)] = e;
-        n_far += __popc(mf);
+        cf[k][sl] = fe && !ser;
+        any_buf = any_buf || nr[k][sl] || cf[k][sl];
         if constexpr (kG == kLayoutList) {
           if (ser) {
             moments_add(sl == 0 ? st[k].as.x : st[k].as.y, __fdividef(eta2 * w.far_d2max, s2), pm);
             any_ser = true;
           }
+        }
+      }
+    }
+    if (__any_sync(kFull, any_buf)) {
+#pragma unroll
+      for (int k = 0; k < KPT; ++k) {
+#pragma unroll
+        for (int sl = 0; sl < 2; ++sl) {
+          const int32_t e = kidx[k] | (pair << kPairBit) | (sl << kSlotBit);
+          const unsigned m = __ballot_sync(kFull, nr[k][sl]);
+          if (nr[k][sl]) nbuf[n_near + __popc(m & lt)] = e;
+          n_near += __popc(m);
+          const unsigned mf = __ballot_sync(kFull, cf[k][sl]);
+          if (cf[k][sl]) fbuf[n_far + __popc(mf & lt)] = e;
+          n_far += __popc(mf);
         }
       }
     }
@@ -897,7 +1025,7 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
     }
     __syncwarp();
     if (n_near >= kFlush) {
-      flush32<KPT, LAYOUT, false>(a, w, g, lane, nbuf, kFlush, acc, bp, red);
+      flush32<KPT, LAYOUT, false>(a, w, g, lane, nbuf, kFlush, acc, bp, red, nd_item);
       buffer_shift(nbuf, kFlush, n_near, lane);
       n_near -= kFlush;
     }
@@ -910,7 +1038,7 @@ __device__ __forceinline__ void item32(const KsumArgs& a, const WorkItem& w, con
       n_far -= kFlush;
     }
   }
-  if (n_near > 0) flush32<KPT, LAYOUT, false>(a, w, g, lane, nbuf, n_near, acc, bp, red);
+  if (n_near > 0) flush32<KPT, LAYOUT, false>(a, w, g, lane, nbuf, n_near, acc, bp, red, nd_item);
   if constexpr (kG == kLayoutProduct) {
     if (n_far > 0) flush_far_product<KPT>(a, w, g, lane, fbuf, n_far, red, dbase, nd_item, fsum);
   }
@@ -1009,7 +1137,8 @@ __global__ void __launch_bounds__(256, (sizeof(Real) == 4 ? KPT <= 4 : KPT == 1)
     const int nb = w.b1 - w.b0;
     const bool bad_tile = kGroupLayout == kLayoutProduct &&
                           (w.b0 / tile_n_dblk(g) != (w.b1 - 1) / tile_n_dblk(g) ||
-                           nb * tile_db(g) > (std::is_same<Real, float>::value ? kMaxTileDeltas : 32));
+                           nb * tile_db(g) > (std::is_same<Real, float>::value ? kMaxTileDeltas : 32) ||
+                           (LAYOUT == kLayoutProductUT && tile_hb(g) > kUtMaxHb));
     if (nb > kMB || g.layout != kGroupLayout || bad_tile) {
       if (lane == 0) atomicOr(a.status, 1);
       continue;
