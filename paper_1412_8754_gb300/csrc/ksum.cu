@@ -753,7 +753,7 @@ __device__ __forceinline__ void flush_batches_ut(const KState32 (&st)[KPT], cons
           Rc[k] = __fmul2_rn(R, c2);
           Ac[k] = __fmul2_rn(A, c2);
         }
-#pragma unroll(KPT <= 2 ? 4 : 2)
+#pragma unroll 2
         for (int j = j0; j < j1; ++j) red[j * 36 + lane] = w_out32_x<KPT>(Rc, D0c, Ac, ip[kUtCh + j - j0]);
       } else {
         float2 A1[KPT], A2[KPT], Ac[KPT];
