@@ -35,18 +35,17 @@ SFU_OTHER_PER_CLK = 16
 SM_MAX_MHZ = 2070.0
 
 
-def sfu_clk_per_band_eval(n_ht: int, outs_per_item: int):
+def sfu_clk_per_band_eval(per_row: int, outs_per_item: int):
     """SFU time (SM clocks) per band evaluation (one k-point, one band, one output) in the
-    shared-Delta scan layout: (near with two exponentials, near with one, far in the closed
+    shared-T scan layout: (near with two exponentials, near with one, far in the closed
     form, far in the moments).  Every far band takes one rcp per k-set for y = Delta_max^2
     eta^2 / s^2, shared by the item's outputs; one outside the series range (y > 0.1) also
-    needs R and a: 1 rsqrt + 1 rcp per (k, Delta, band), shared by the (up to 32) (h, T)
-    outputs of one batch.  A near band is evaluated in full, packed with another near band in
-    a float2 slot: per output 2 ex2 -- 1 where c (R + |d|) >= 27 makes the second factor
-    exactly 1 -- and an eighth of one lg2 (one lg2 per output over a lane's four slots), and
-    its R and a."""
-    per_batch = min(32, n_ht)
-    ra = 2.0 / (SFU_OTHER_PER_CLK * per_batch)
+    needs R and a: 1 rsqrt + 1 rcp per (k, Delta, band), shared by the per_row (h, T)
+    outputs of one Delta row of a tile.  A near band is evaluated in full, packed with another
+    near band in a float2 slot: per output 2 ex2 -- 1 where c (R + |d|) >= 27 makes the second
+    factor exactly 1 -- and an eighth of one lg2 (one lg2 per output over a lane's four
+    slots), and its R and a."""
+    ra = 2.0 / (SFU_OTHER_PER_CLK * per_row)
     y = 1.0 / (SFU_OTHER_PER_CLK * outs_per_item)
     rest = 0.125 / SFU_OTHER_PER_CLK + ra + y
     return 2.0 / SFU_EX2_PER_CLK + rest, 1.0 / SFU_EX2_PER_CLK + rest, ra + y, y
@@ -530,8 +529,11 @@ def main():
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
     pst = plan.stats()
-    outs_item = min(16, cfg["n"]) * min(32, n_pts)  # outputs of one work item (16 batches of 32)
-    c_near, c_single, c_far, c_mom = sfu_clk_per_band_eval(n_pts, outs_item)
+    # a work item of the shared-T layout: tiles of 8 (h, T) entries x 4 Delta rows, 24 tiles
+    # (96 Delta rows); R and a per (k-point, band, Delta row) serve the row's 8 outputs
+    per_row = min(8, n_pts)
+    outs_item = min(96, cfg["n"]) * per_row
+    c_near, c_single, c_far, c_mom = sfu_clk_per_band_eval(per_row, outs_item)
     band_evals = 2.0 * k_evals  # two bands per k-evaluation
     b_near, b_single = pst["k_evals_near"], pst["k_evals_single"]  # full-term band evaluations
     b_fc = pst["k_evals_far_closed"]  # far band evaluations in the closed form

@@ -447,12 +447,13 @@ __device__ __forceinline__ void ra_f64(double D, double s2, double as, double& R
 
 // FP64 band term for one (h,T): q = p - 1 = e1 + e2 + e1 e2 (kept as p - 1
 // for log1p) and first = min(0, max(|d|-|s|, 0) - a).
-// An exponential exp(-y) with y >= kExpNegligible = 64 is taken as 0 without
-// evaluating it: e^-64 < 1.7e-28, so the band's -T ln(1 + q) term, which is
-// then dropped, is below 3 e^-64 T < 5.1e-28 T, and the free energy per site
-// changes by less than 1.6e-27 T (three bands) -- eleven orders of magnitude
-// below the rounding of an FP64 sum of terms of size 1e-6 or more.
-constexpr double kExpNegligible = 64.0;
+// An exponential exp(-y) with y >= kExpNegligible = 40 is taken as 0 without
+// evaluating it: e^-40 < 4.3e-18, so the band's -T ln(1 + q) term, which is
+// then dropped, is below 3 e^-40 T < 1.3e-17 T, and the free energy per site
+// changes by less than 3.9e-17 T (three bands) -- for T <= 1 below a fifth of
+// one FP64 ulp of a per-site value of 1, and far below the rounding of the
+// k-sum itself (its N^2 terms are added in FP64).
+constexpr double kExpNegligible = 40.0;
 __device__ __forceinline__ void band_term_f64(double R, double a, double as, double d0, double h,
                                               double inv_t, double& q, double& first) {
   double d = d0 - h;

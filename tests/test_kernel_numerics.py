@@ -50,22 +50,24 @@ def test_a_factor_below_2_to_minus_26_leaves_the_fp32_product_unchanged(y):
     assert not np.array_equal(np.array([f32_fma(p, big, p) for p in P[:100]], dtype=np.float32), P[:100])
 
 
-def test_fp64_negligible_exponentials_leave_band_terms_unchanged():
-    """FP64 band terms take exp(-y) as 0 for y >= 64 (the k-sum's far bands need no exponential):
-    the dropped -T ln(1 + q) is below 3 e^-64 T < 5.1e-28 T, so every band term f - T ln(1 + q)
-    whose clamp term has |f| >= 1e-11 keeps its bits (T <= 1), and the rest move by < 5.1e-28 T."""
-    rng = np.random.default_rng(64)
+def test_fp64_negligible_exponentials_move_omega_below_fp64_rounding():
+    """FP64 band terms take exp(-y) as 0 for y >= 40 (the k-sum's far bands need no exponential):
+    the dropped -T ln(1 + q) is below 3 e^-40 T < 1.3e-17 T per band, so Omega per site (a mean of
+    N^2 k-point terms) moves by less than 3.9e-17 T with three bands: for T <= 1 below a fifth of
+    one FP64 ulp of a per-site value of 1."""
+    rng = np.random.default_rng(40)
     T = rng.uniform(1e-4, 1.0, 20000)
-    y1 = rng.uniform(64.0, 80.0, 20000)
+    y1 = rng.uniform(40.0, 80.0, 20000)
     y2 = y1 + rng.uniform(0.0, 40.0, 20000)
     e1, e2 = np.exp(-y1), np.exp(-y2)
     q = e1 + e2 + e1 * e2
-    assert np.all(T * np.log1p(q) < 5.1e-28 * T)
-    f = -np.exp(rng.uniform(np.log(1e-11), np.log(1e3), 20000))
-    assert np.array_equal(f - T * np.log1p(q), f)
-    # at y = 40 the same terms would move (the cut-off is not loose)
-    q40 = 3.0 * np.exp(-40.0)
-    assert not np.array_equal(f[:2000] - T[:2000] * np.log1p(q40), f[:2000])
+    assert np.all(T * np.log1p(q) < 1.3e-17 * T)
+    assert 3.0 * 1.3e-17 < 0.2 * np.spacing(1.0)
+    # a per-site mean of such terms moves by at most the largest of them
+    terms = -T * np.log1p(q)
+    assert abs(terms.mean()) < 1.3e-17
+    # at y = 36 the dropped part of three bands would exceed half an ulp of 1 (the cut-off is not loose)
+    assert 3.0 * np.exp(-36.0) > 0.5 * np.spacing(1.0)
 
 
 def test_newton_steps_refine_fp32_eigenvalues_to_fp64():
