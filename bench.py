@@ -142,14 +142,14 @@ def cpu_baseline(cfg, lines, diagram_lines=None, tol=2e-7):
 
 
 # DRAM bytes (read + write) of one k-sum launch of the default workload, from
-# ncu (dram__bytes_read.sum + dram__bytes_write.sum, one pass on the full-size
-# launch): 1.49 GB read (the FP32 k-state table, 1.34 GB, and the trig and job
-# tables) + 0.270 GB written (the FP64 k-chunk partial sums).
-DRAM_TRAFFIC_PER_LAUNCH = 1.760e9
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum, one launch of the full-size
+# plan): 3.12 GB read (mostly the FP32 k-state table, 1.34 GB, about 2.3 times)
+# + 0.42 GB written (the FP64 k-chunk partial sums).
+DRAM_TRAFFIC_PER_LAUNCH = 3.542e9
 # From the committed one-kernel ncu capture of the same kernel on 8 of the 64 q
 # (profiles/ksum_fflo_scan_N1024_q8.md): issue slots busy and the SFU (XU)
 # pipe's share of its peak.
-NCU_HEADLINE = {"issue_active_pct": 58.5, "sfu_pct_of_peak": 32.9,
+NCU_HEADLINE = {"issue_active_pct": 61.2, "sfu_pct_of_peak": 31.9,
                 "source": "profiles/ksum_fflo_scan_N1024_q8.md"}
 
 
