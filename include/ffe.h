@@ -398,6 +398,15 @@ FFE_API ffe_status ffe_surrogate_get_params(ffe_surrogate* s, float* params);
  * checkpoint of this network (FFE_EINVAL). */
 FFE_API ffe_status ffe_surrogate_save(ffe_surrogate* s, void* buf, size_t* bytes);
 FFE_API ffe_status ffe_surrogate_load(ffe_surrogate* s, const void* buf, size_t bytes);
+/* Training targets of the surrogate (data generation, no counterpart in the
+ * paper): omega holds n_lines lines of n_per_line free energies of one lattice
+ * size N, each line's first value at its reference Delta = 0; y receives the
+ * condensation energy per site (omega[l][j] - omega[l][0]) / N^2 of every value,
+ * rounded to FP32 from the FP64 difference and quotient.  Host arrays (caller
+ * owned, n_lines * n_per_line each); computed by a kernel.  FFE_EINVAL for
+ * NULL arrays, n_lines < 1, n_per_line < 1 or N < 1. */
+FFE_API ffe_status ffe_surrogate_targets(ffe_context* ctx, const double* omega, int64_t n_lines,
+                                         int32_t n_per_line, int32_t N, float* y);
 /* y[n] = prediction at x[n][4] = (q, h, T, Delta). */
 FFE_API ffe_status ffe_surrogate_predict(ffe_surrogate* s, const float* x, int64_t n, float* y,
                                          void* stream);

@@ -496,6 +496,16 @@ __global__ void mlp_copies_kernel(const float* master, __nv_bfloat16* tiles) {
   put_weight(tiles, 1, j / kW, j % kW, master[kOffW3 + j]);
 }
 
+// Training targets: y = (omega - omega of the line's first value) / N^2, one thread per value.
+__global__ void targets_kernel(const double* __restrict__ omega, int64_t n_values, int32_t n_per_line,
+                               double n2, float* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_values;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ref = i - i % n_per_line;
+    y[i] = (float)((omega[i] - omega[ref]) / n2);
+  }
+}
+
 // Adds a step's loss partials (fixed order) to the epoch's total.
 __global__ void mlp_loss_kernel(const double* __restrict__ loss_part, int n_blocks, double* total) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -752,6 +762,30 @@ ffe_status ffe_surrogate_load(ffe_surrogate* s, const void* buf, size_t bytes) {
   mlp_copies_kernel<<<(kW * kW + 255) / 256, 256, 0, s->stream>>>(s->master, s->tiles);
   SUR_CU(cudaGetLastError(), "copies");
   SUR_CU(cudaStreamSynchronize(s->stream), "sync");
+  return FFE_OK;
+}
+
+ffe_status ffe_surrogate_targets(ffe_context* ctx, const double* omega, int64_t n_lines, int32_t n_per_line,
+                                 int32_t N, float* y) {
+  if (!ctx || !omega || !y || n_lines < 1 || n_per_line < 1 || N < 1) return FFE_EINVAL;
+  const int64_t n = n_lines * (int64_t)n_per_line;
+  double* d_om = nullptr;
+  float* d_y = nullptr;
+  cudaError_t e = cudaMalloc(&d_om, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_y, n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(d_om, omega, n * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 65535);
+    targets_kernel<<<blocks, 256>>>(d_om, n, n_per_line, (double)N * (double)N, d_y);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(y, d_y, n * sizeof(float), cudaMemcpyDeviceToHost);
+  cudaFree(d_om);
+  cudaFree(d_y);
+  if (e != cudaSuccess) {
+    set_err(ctx, "surrogate targets: %s", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? FFE_ENOMEM : FFE_ECUDA;
+  }
   return FFE_OK;
 }
 

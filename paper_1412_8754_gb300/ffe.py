@@ -102,6 +102,7 @@ _SIGNATURES = [
     ("ffe_surrogate_destroy", None, [_VP]),
     ("ffe_surrogate_set_params", ctypes.c_int, [_VP, _VP]),
     ("ffe_surrogate_get_params", ctypes.c_int, [_VP, _VP]),
+    ("ffe_surrogate_targets", ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _VP]),
     ("ffe_surrogate_predict", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP]),
     ("ffe_surrogate_save", ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_size_t)]),
     ("ffe_surrogate_load", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
@@ -269,6 +270,16 @@ def _check(ctx, st):
 
 
 # ------------------------------------------------------------ entry points
+def ffe_surrogate_targets(ctx, omega, N):
+    """Condensation energies per site (omega[l, j] - omega[l, 0]) / N^2 in FP32 of the lines
+    (rows) of omega, computed by the library."""
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    lines = om.reshape(-1, om.shape[-1])
+    y = np.zeros(lines.shape, dtype=np.float32)
+    _check(ctx, lib().ffe_surrogate_targets(ctx, _ptr(lines), lines.shape[0], lines.shape[1], int(N), _ptr(y)))
+    return y.reshape(om.shape)
+
+
 def ffe_create(U=2.0, eta_amp=1.0, prec=FFE_FP32C, model="raghu2", U_band=None, **params):
     """A context for `model` ("raghu2": App. A, "daghofer3": App. B) with its printed
     parameters, any of which `params` overrides; U_band: per-band couplings (0 = U)."""

@@ -36,9 +36,9 @@ def training_data(ctx: ffe.Context, N: int, sset: dict):
     HH = np.broadcast_to(h[:, :, None], (G, H, D))
     TT = np.broadcast_to(T[:, :, None], (G, H, D))
     om = ctx.omega(ffe.points(N, Q.ravel(), 0.0, HH.ravel(), TT.ravel(), d.ravel())).reshape(G, H, D)
-    y = (om - om[..., :1]) / float(N) ** 2
+    y = ffe.ffe_surrogate_targets(ctx.handle, om, N)
     x = np.stack([Q.ravel(), HH.ravel(), TT.ravel(), d.ravel()], axis=1)
-    return x.astype(np.float32), y.ravel().astype(np.float32)
+    return x.astype(np.float32), y.ravel()
 
 
 def fit(ctx: ffe.Context, x, y, epochs=30, batch=4096, lr=2e-3, seed=0, y_scale=None, decay=True):

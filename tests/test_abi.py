@@ -1,8 +1,10 @@
 """The C-ABI library loads without a GPU and exports every symbol of include/ffe.h."""
+import ctypes
 import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_1412_8754_gb300 import ffe
@@ -68,3 +70,12 @@ def test_null_context_is_rejected(built):
     L = ffe.lib()
     assert L.ffe_omega(None, None, 0, None, None, None) == ffe.FFE_EINVAL
     L.ffe_destroy(None)  # NULL-safe
+
+
+def test_invalid_arguments_are_rejected_before_any_device_work(built):
+    L = ffe.lib()
+    om = np.zeros(4)
+    y = np.zeros(4, dtype=np.float32)
+    # no context, empty lines, bad N: FFE_EINVAL (1) without touching a GPU
+    assert L.ffe_surrogate_targets(None, om.ctypes.data_as(ctypes.c_void_p), 1, 4, 8,
+                                   y.ctypes.data_as(ctypes.c_void_p)) == 1

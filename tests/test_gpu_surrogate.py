@@ -250,3 +250,16 @@ def test_checkpoint_resumes_training_bit_for_bit(ctx):
         r.load(ckpt[:100])
     r.close()
     assert np.array_equal(la, lb) and np.array_equal(wa, wb)
+
+
+@pytest.mark.parametrize("N", [512, 24])
+def test_training_targets_are_the_condensation_energies(ctx, N):
+    """ffe_surrogate_targets: (omega[l, j] - omega[l, 0]) / N^2 per line, rounded once to FP32 from
+    the FP64 difference and quotient (IEEE: the same bits as numpy's), on a ragged line count."""
+    rng = np.random.default_rng(N)
+    om = -1.7 * N * N + rng.normal(0.0, 1e-3 * N * N, (37, 5, 16))
+    got = ffe.ffe_surrogate_targets(ctx.handle, om, N)
+    want = ((om - om[..., :1]) / float(N) ** 2).astype(np.float32)
+    assert got.dtype == np.float32 and got.shape == om.shape
+    assert np.array_equal(got, want)
+    assert np.all(got[..., 0] == 0.0)
