@@ -282,6 +282,10 @@ __device__ __forceinline__ void ra32(const KState32& st, float d2, float2& R, fl
 // one lg2 of the product of all (1 + e) factors (each half of P2 at most
 // 4^KPT, the product at most 16^KPT <= 2^32).  Rc = R c, Ac = a c per slot;
 // y1 = c (R - d), y2 = c (R + d) with d = d0 - h.
+// SINGLE: only the factor of x = min(y1, y2) = c R - c |d| differs from 1; x is
+// formed directly by one fused multiply-add per band (the same rounding as the
+// smaller of y1 and y2, so the same bits as the two-sided form) and enters as
+// 2^-|x| and max(min(x, c a), 0).
 template <int KPT, bool SINGLE>
 __device__ __forceinline__ float w_out32(const KState32 (&st)[KPT], const float2 (&Rc)[KPT],
                                          const float2 (&Ac)[KPT], float h, float c) {
@@ -290,7 +294,13 @@ __device__ __forceinline__ float w_out32(const KState32 (&st)[KPT], const float2
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
     const float2 d = __fadd2_rn(st[k].d0, nh2);
-    w_term32<SINGLE>(__ffma2_rn(d, nc2, Rc[k]), __ffma2_rn(d, c2, Rc[k]), Ac[k], P2, cp2);
+    if constexpr (SINGLE) {
+      const float x0 = fmaf(-c, fabsf(d.x), Rc[k].x), x1 = fmaf(-c, fabsf(d.y), Rc[k].y);
+      P2 = __ffma2_rn(P2, make_float2(ex2a(-fabsf(x0)), ex2a(-fabsf(x1))), P2);
+      cp2 = __fadd2_rn(cp2, make_float2(fmaxf(fminf(x0, Ac[k].x), 0.0f), fmaxf(fminf(x1, Ac[k].y), 0.0f)));
+    } else {
+      w_term32<false>(__ffma2_rn(d, nc2, Rc[k]), __ffma2_rn(d, c2, Rc[k]), Ac[k], P2, cp2);
+    }
   }
   return (cp2.x + cp2.y) + lg2a(P2.x * P2.y);
 }
