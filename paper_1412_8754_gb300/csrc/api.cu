@@ -372,6 +372,9 @@ static ffe_status plan_alloc_requests(ffe_context* ctx, ffe_plan* p, Arena& aren
   p->rescore_chunks = (int)((nk_max + p->rescore_chunk - 1) / p->rescore_chunk);
   ALLOC(d_rpart, (int64_t)p->cap * p->rescore_chunks);
   ALLOC(d_rcnt, p->cap);
+  ALLOC(d_rorder, p->cap);
+  ALLOC(d_rruns, p->cap);
+  ALLOC(d_rgcount, 4 * (p->groups.size() + 1));
   ALLOC(d_lres, p->lines.size());
   ALLOC(d_labels, std::max<size_t>(1, p->n_pts));
   ALLOC(d_bestq, std::max<size_t>(1, p->n_pts));
@@ -568,7 +571,10 @@ static RescoreArgs make_rescore_args(ffe_plan* p, int queue_slot, int count_slot
   r.rescored = p->d_rescored;
   r.golden = p->d_golden;
   r.cap = p->cap;
-  r.pad = 0;
+  r.n_groups = (int32_t)p->groups.size();
+  r.order = p->d_rorder;
+  r.runs = p->d_rruns;
+  r.gcount = p->d_rgcount;
   return r;
 }
 
@@ -633,7 +639,7 @@ ffe_status plan_enqueue(ffe_context* ctx, ffe_plan* p, cudaStream_t s, cudaEvent
       FFE_CU(cudaMemsetAsync(p->d_counters + 5, 0, 2 * sizeof(int32_t), s), "memset");
       if ((st = golden(kGoldenMark)) != FFE_OK) return st;
       FFE_CU(rescore_launch(make_rescore_args(p, 6, 5), p->rescore_grid, s), "rescore golden");
-      ++launches;
+      launches += 2;
       if ((st = golden(kGoldenDecide)) != FFE_OK) return st;
       if ((st = ksum()) != FFE_OK) return st;
       if ((st = golden(kGoldenRecord)) != FFE_OK) return st;
@@ -642,7 +648,7 @@ ffe_status plan_enqueue(ffe_context* ctx, ffe_plan* p, cudaStream_t s, cudaEvent
     FFE_CU(cudaMemsetAsync(p->d_counters + 5, 0, 2 * sizeof(int32_t), s), "memset");
     if ((st = golden(kGoldenMarkFinal)) != FFE_OK) return st;
     FFE_CU(rescore_launch(make_rescore_args(p, 6, 5), p->rescore_grid, s), "rescore golden");
-    ++launches;
+    launches += 2;
     if ((st = golden(kGoldenFinish)) != FFE_OK) return st;
   } else {
     if (ev0) FFE_CU(cudaEventRecordWithFlags(ev0, s, ev_flags), "event");
@@ -659,7 +665,7 @@ ffe_status plan_enqueue(ffe_context* ctx, ffe_plan* p, cudaStream_t s, cudaEvent
     FFE_CU(argmin_launch(p->d_lines, n_lines, p->d_omega, p->d_eb, p->d_delta, p->d_rescored, 1, p->d_req,
                          p->d_counters + 3, p->cap, p->d_lres, s),
            "argmin B");
-    launches += 3;
+    launches += 4;  // argmin A, request grouping, rescore, argmin B
     }
     if (p->n_q > 0) {
       // the request slots are reused once pass A's requests are done (stream order)
@@ -670,7 +676,7 @@ ffe_status plan_enqueue(ffe_context* ctx, ffe_plan* p, cudaStream_t s, cudaEvent
       FFE_CU(labels_launch(p->d_lres, p->n_q, p->n_pts, p->d_qzero, p->d_lines, p->d_delta, 1, p->d_req,
                            p->d_counters + 4, p->cap, p->d_labels, p->d_bestq, s),
              "labels 1");
-      launches += 3;
+      launches += 4;  // labels 0, request grouping, rescore, labels 1
     }
   }
   p->launches = launches;

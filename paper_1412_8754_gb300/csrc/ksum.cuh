@@ -144,9 +144,19 @@ struct RescoreArgs {
   int32_t* rescored;    // per output flag (kind 0)
   GoldenState* golden;  // kinds 3 (x1) and 4 (x2)
   int32_t cap;
-  int32_t pad;
+  int32_t n_groups;     // groups of the plan (the requests' group ids are below it)
   const E3D* e3d;       // three-band model: FP64 band tables (GroupDesc::e3_off)
+  // grouping of the requests (rescore_sort_kernel): request indices ordered
+  // by group [cap], runs of at most kRescoreRun of them within one group
+  // (first, count) [cap], and per group its request count, request offset,
+  // run offset and a fill counter [4 (n_groups + 1)]; the run count in total
+  // is gcount[n_groups]
+  int32_t* order;
+  int2* runs;
+  int32_t* gcount;
 };
+// Requests of one group evaluated together (one pass over its band energies).
+constexpr int kRescoreRun = 6;
 
 enum { kGoldenInit = 0, kGoldenLo, kGoldenX1, kGoldenX2, kGoldenMark, kGoldenDecide, kGoldenRecord,
        kGoldenMarkFinal, kGoldenFinish };
@@ -158,7 +168,7 @@ cudaError_t argmin_launch(const Line* lines, int n_lines, const double* omega, c
                           const double* delta, const int32_t* rescored, int mode, Rescore* req,
                           int32_t* n_req, int32_t cap, LineResult* res, cudaStream_t s);
 cudaError_t rescore_launch(const RescoreArgs& a, int grid, cudaStream_t s);
-cudaError_t rescore_occupancy(int* blocks_per_sm);  // resident rescore blocks (256 threads) per SM
+cudaError_t rescore_occupancy(int* blocks_per_sm);  // resident rescore blocks (128 threads) per SM
 // LineResult -> ffe_result (include/ffe.h) of n lines on the device.
 cudaError_t results_launch(const LineResult* lr, int64_t n, const int32_t* counters, int32_t cap, void* out,
                            cudaStream_t s);

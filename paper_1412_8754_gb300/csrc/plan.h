@@ -129,6 +129,9 @@ struct ffe_plan {
   ffe::Rescore* d_req = nullptr;
   double* d_rpart = nullptr;
   int32_t* d_rcnt = nullptr;
+  int32_t* d_rorder = nullptr;  // requests sorted by (group, dst) [cap]
+  int2* d_rruns = nullptr;      // runs of requests of one group [cap]
+  int32_t* d_rgcount = nullptr; // per-group request counts, offsets, run offsets, fill [4 (n_groups + 1)]
   ffe::LineResult* d_lres = nullptr;
   int8_t* d_labels = nullptr;
   int32_t* d_bestq = nullptr;

@@ -119,9 +119,11 @@ cudaError_t argmin_launch(const Line* lines, int n_lines, const double* omega, c
   return cudaGetLastError();
 }
 
-// Near-band entries per warp in the FP64 re-evaluation: a flush takes the top
-// 32, a step of 32 k-points adds at most 32 x (two band pairs x two slots).
-constexpr int kRescoreBuf = 32 + 32 * 4;
+// Near-band entries per warp and request in the FP64 re-evaluation: a flush
+// takes the top 32, a step of 32 k-points adds at most 32 x (two slots) per
+// band pair; the three-band model (two pairs) takes two request slots.
+constexpr int kRescoreBufSlot = 32 + 32 * 2;
+__host__ __device__ constexpr int rescore_run_max(int nbands) { return nbands == 3 ? kRescoreRun / 2 : kRescoreRun; }
 
 // -T ln(1 + q), q = e1 + e2 + e1 e2, of one near band (y1 = |R - |d|| / T < kExpNegligible,
 // y2 = (R + |d|) / T), with band_term_f64's cut-off for e2.
@@ -131,38 +133,115 @@ __device__ __forceinline__ double near_log_term(double2 y, double t) {
   return -t * log1p(e1 + e2 + e1 * e2);
 }
 
-// The FP64 k-sum of one request, k-chunk by k-chunk.  Each warp takes 32
-// consecutive k-points per step; every active band adds its clamp term
-// min(max(|d| - |s|, 0) - a, 0) at once, and only a band with
-// |R - |d|| / T < kExpNegligible (near) has exponentials that are not 0: such
-// bands are compacted (ballot + prefix count) into the warp's buffer and their
-// -T ln(1 + q) evaluated 32 at a time, so the exponentials and the logarithm
-// run on full warps.  The two bands of a k-point add their logarithms.
-__global__ void __launch_bounds__(256) rescore_kernel(const RescoreArgs a) {
-  __shared__ double red[8];
+// Groups the queued requests by group: counts, offsets and a scatter of the
+// request indices, then runs of at most rescore_run_max of one group.  Which
+// requests share a run does not change any request's sums (each keeps its own
+// accumulators and near-band buffer in rescore_kernel).  One block.
+__global__ void __launch_bounds__(1024) rescore_sort_kernel(const RescoreArgs a) {
+  __shared__ int32_t part[1024];
+  __shared__ int32_t rpart[1024];
+  const int nreq = min(*a.n_req, a.cap);
+  const int ng = a.n_groups;
+  const int R = rescore_run_max(a.m.nbands);
+  int32_t* cnt = a.gcount;                // [ng + 1]; cnt[ng] = runs in total
+  int32_t* off = a.gcount + (ng + 1);     // [ng + 1] request offset per group
+  int32_t* roff = a.gcount + 2 * (ng + 1);  // [ng + 1] run offset per group
+  int32_t* fill = a.gcount + 3 * (ng + 1);  // [ng + 1]
+  const int t = threadIdx.x, nt = blockDim.x;
+  for (int g = t; g <= ng; g += nt) {
+    cnt[g] = 0;
+    fill[g] = 0;
+  }
+  __syncthreads();
+  for (int r = t; r < nreq; r += nt) {
+    const int g = a.req[r].group;
+    if (g >= 0 && g < ng) atomicAdd(cnt + g, 1);
+  }
+  __syncthreads();
+  // exclusive scans of the request and run counts: contiguous ranges per thread
+  const int per = (ng + nt - 1) / nt, g0 = min(ng, t * per), g1 = min(ng, g0 + per);
+  int sum = 0, rsum = 0;
+  for (int g = g0; g < g1; ++g) {
+    sum += cnt[g];
+    rsum += (cnt[g] + R - 1) / R;
+  }
+  part[t] = sum;
+  rpart[t] = rsum;
+  __syncthreads();
+  if (t == 0) {
+    int acc = 0, racc = 0;
+    for (int i = 0; i < nt; ++i) {
+      const int v = part[i], rv = rpart[i];
+      part[i] = acc;
+      rpart[i] = racc;
+      acc += v;
+      racc += rv;
+    }
+    cnt[ng] = racc;
+  }
+  __syncthreads();
+  int acc = part[t], racc = rpart[t];
+  for (int g = g0; g < g1; ++g) {
+    off[g] = acc;
+    roff[g] = racc;
+    acc += cnt[g];
+    racc += (cnt[g] + R - 1) / R;
+  }
+  __syncthreads();
+  for (int r = t; r < nreq; r += nt) {
+    const int g = a.req[r].group;
+    if (g >= 0 && g < ng) a.order[off[g] + atomicAdd(fill + g, 1)] = r;
+  }
+  for (int g = t; g < ng; g += nt)
+    for (int i = 0; i * R < cnt[g]; ++i) a.runs[roff[g] + i] = make_int2(off[g] + i * R, min(R, cnt[g] - i * R));
+}
+
+// The FP64 k-sums of a run of requests of one group, k-chunk by k-chunk: the
+// band energies of each k-point are formed once and serve every request of
+// the run.  Per request each warp takes 32 consecutive k-points per step;
+// every active band adds its clamp term min(max(|d| - |s|, 0) - a, 0) at
+// once, and only a band with |R - |d|| / T < kExpNegligible (near) has
+// exponentials that are not 0: such bands are compacted (ballot + prefix
+// count) into the request's warp buffer and their -T ln(1 + q) evaluated 32 at
+// a time, so the exponentials and the logarithm run on full warps.  Each
+// request keeps its own per-thread sums and buffers, so its result has the
+// same bits whichever requests share its run.
+constexpr int kRescoreThreads = 128;
+
+__global__ void __launch_bounds__(kRescoreThreads) rescore_kernel(const RescoreArgs a) {
+  __shared__ double red[kRescoreThreads / 32];
   __shared__ int sh_w, sh_last;
-  __shared__ double2 near_buf[8][kRescoreBuf];
+  __shared__ Rescore sh_req[kRescoreRun];
+  __shared__ int32_t sh_ri[kRescoreRun];
+  __shared__ double acc[kRescoreRun][kRescoreThreads];
+  __shared__ double2 near_buf[kRescoreThreads / 32][kRescoreRun * kRescoreBufSlot];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  double2* nb = near_buf[warp];
-  const int nreq = min(*a.n_req, a.cap);
-  const int total = nreq * a.max_chunks;
+  const int slot = a.m.nbands == 3 ? 2 * kRescoreBufSlot : kRescoreBufSlot;
+  const int n_runs = a.gcount[a.n_groups];
+  const int total = n_runs * a.max_chunks;
   for (;;) {
     if (threadIdx.x == 0) sh_w = atomicAdd(a.queue, 1);
     __syncthreads();
     const int w = sh_w;
-    __syncthreads();
     if (w >= total) break;
-    const int r = w / a.max_chunks, c = w - r * a.max_chunks;
-    const Rescore q = a.req[r];
-    const GroupDesc g = a.groups[q.group];
-    const HT ht = a.ht[q.ht];
+    const int ru = w / a.max_chunks, c = w - ru * a.max_chunks;
+    const int2 run = a.runs[ru];
+    const int m = run.y;
+    if (threadIdx.x < m) {
+      const int ri = a.order[run.x + threadIdx.x];
+      sh_ri[threadIdx.x] = ri;
+      sh_req[threadIdx.x] = a.req[ri];
+    }
+    for (int j = 0; j < m; ++j) acc[j][threadIdx.x] = 0.0;
+    __syncthreads();
+    const GroupDesc g = a.groups[sh_req[0].group];
     const int64_t nk = (int64_t)g.N * g.N;
     const int64_t k0 = (int64_t)c * a.chunk_k;
     const int64_t k1 = min(nk, k0 + a.chunk_k);
-    const double d2 = q.delta * q.delta, inv_t = 1.0 / ht.T;
-    double s = 0.0;
-    int n_near = 0;
+    int n_near[kRescoreRun];
+#pragma unroll
+    for (int j = 0; j < kRescoreRun; ++j) n_near[j] = 0;
     for (int64_t kb = k0 + warp * 32; kb < k1; kb += blockDim.x) {
       const int64_t k = kb + lane;
       const bool valid = k < k1;
@@ -179,91 +258,117 @@ __global__ void __launch_bounds__(256) rescore_kernel(const RescoreArgs a) {
           kstate_make<double, TabRowD>(a.m, a.tabd[g.tab_off + ix], a.tabd[g.tab_off + g.N + iy],
                                        a.c0d[g.tab_off + ix], a.c0d[g.tab_off + g.N + iy], st);
         }
-        const double D = d2 * st.eta2;
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-          const bool use = valid && slot_active(a.m.nbands, g.band_only, pair, b);
-          double R, A;
-          ra_f64(D, st.s2[b], st.as[b], R, A);
-          const double ad = fabs(st.d0[b] - ht.h);
-          const double y1 = fabs(R - ad) * inv_t;
-          if (use) s += fmin(fmax(ad - st.as[b], 0.0) - A, 0.0);
-          const bool near = use && y1 < kExpNegligible;
-          const unsigned m = __ballot_sync(kFull, near);
-          if (near) nb[n_near + __popc(m & lt)] = make_double2(y1, (R + ad) * inv_t);
-          n_near += __popc(m);
+        for (int j = 0; j < kRescoreRun; ++j) {
+          if (j >= m) break;
+          const Rescore q = sh_req[j];
+          const HT ht = a.ht[q.ht];
+          const double inv_t = 1.0 / ht.T;
+          const double D = (q.delta * q.delta) * st.eta2;
+          double2* nb = near_buf[warp] + j * slot;
+          double sj = 0.0;
+#pragma unroll
+          for (int b = 0; b < 2; ++b) {
+            const bool use = valid && slot_active(a.m.nbands, g.band_only, pair, b);
+            double R, A;
+            ra_f64(D, st.s2[b], st.as[b], R, A);
+            const double ad = fabs(st.d0[b] - ht.h);
+            const double y1 = fabs(R - ad) * inv_t;
+            if (use) sj += fmin(fmax(ad - st.as[b], 0.0) - A, 0.0);
+            const bool near = use && y1 < kExpNegligible;
+            const unsigned msk = __ballot_sync(kFull, near);
+            if (near) nb[n_near[j] + __popc(msk & lt)] = make_double2(y1, (R + ad) * inv_t);
+            n_near[j] += __popc(msk);
+          }
+          acc[j][threadIdx.x] += sj;
         }
       }
       __syncwarp();
-      while (n_near >= 32) {  // the top 32 entries, one per lane
-        n_near -= 32;
-        s += near_log_term(nb[n_near + lane], ht.T);
+#pragma unroll
+      for (int j = 0; j < kRescoreRun; ++j) {
+        if (j >= m) break;
+        const double T = a.ht[sh_req[j].ht].T;
+        const double2* nb = near_buf[warp] + j * slot;
+        while (n_near[j] >= 32) {  // the top 32 entries, one per lane
+          n_near[j] -= 32;
+          acc[j][threadIdx.x] += near_log_term(nb[n_near[j] + lane], T);
+        }
       }
       __syncwarp();
     }
-    if (lane < n_near) s += near_log_term(nb[lane], ht.T);
-    __syncwarp();
+    for (int j = 0; j < m; ++j) {
+      const double T = a.ht[sh_req[j].ht].T;
+      double s = acc[j][threadIdx.x];
+      if (lane < n_near[j]) s += near_log_term(near_buf[warp][j * slot + lane], T);
+      __syncwarp();
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-    if (lane == 0) red[warp] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double b = 0.0;
-      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) b += red[i];
-      a.partials[(int64_t)r * a.max_chunks + c] = b;
-      __threadfence();
-      sh_last = (atomicAdd(a.counters + r, 1) == a.max_chunks - 1);
-    }
-    __syncthreads();
-    if (sh_last && threadIdx.x == 0) {
-      __threadfence();
-      double V = 0.0;
-      for (int i = 0; i < a.max_chunks; ++i) V += __ldcg(a.partials + (int64_t)r * a.max_chunks + i);
-      const double n2 = (double)g.N * (double)g.N;
-      const double om = a.M[g.h_off + ht.h_idx] + V + pairing_term(a.m, g.band_only, n2, q.delta);
-      if (q.kind == 0) {
-        a.omega[q.dst] = om;
-        a.ebound[q.dst] = 0.0;
-        a.rescored[q.dst] = 1;
-      } else if (q.kind == 3) {
-        a.golden[q.dst].f1 = om;
-        a.golden[q.dst].eb1 = 0.0;
-      } else if (q.kind == 4) {
-        a.golden[q.dst].f2 = om;
-        a.golden[q.dst].eb2 = 0.0;
-      } else if (q.kind == 5) {
-        a.golden[q.dst].fb = om;
-        a.golden[q.dst].ebb = 0.0;
-      } else if (q.kind == 6) {
-        a.golden[q.dst].flo = om;
-        a.golden[q.dst].eblo = 0.0;
-      } else {
-        // kinds 1 (minimum) and 2 (Delta = lo) name the same value when the
-        // minimum is the Delta = lo point: keep both copies identical
-        LineResult& L = a.lines[q.dst];
-        const bool same = (L.flags & kFlagLower) != 0;
-        if (q.kind == 1 || same) {
-          L.omega_star = om;
-          L.eb_star = 0.0;
-          L.flags |= kFlagRescored;
-        }
-        if (q.kind == 2 || same) {
-          L.omega_lo = om;
-          L.eb_lo = 0.0;
-        }
+      for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+      if (lane == 0) red[warp] = s;
+      __syncthreads();
+      const int r = sh_ri[j];
+      const Rescore q = sh_req[j];
+      if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) b += red[i];
+        a.partials[(int64_t)r * a.max_chunks + c] = b;
+        __threadfence();
+        sh_last = (atomicAdd(a.counters + r, 1) == a.max_chunks - 1);
       }
-      a.counters[r] = 0;
+      __syncthreads();
+      if (sh_last && threadIdx.x == 0) {
+        __threadfence();
+        const HT ht = a.ht[q.ht];
+        double V = 0.0;
+        for (int i = 0; i < a.max_chunks; ++i) V += __ldcg(a.partials + (int64_t)r * a.max_chunks + i);
+        const double n2 = (double)g.N * (double)g.N;
+        const double om = a.M[g.h_off + ht.h_idx] + V + pairing_term(a.m, g.band_only, n2, q.delta);
+        if (q.kind == 0) {
+          a.omega[q.dst] = om;
+          a.ebound[q.dst] = 0.0;
+          a.rescored[q.dst] = 1;
+        } else if (q.kind == 3) {
+          a.golden[q.dst].f1 = om;
+          a.golden[q.dst].eb1 = 0.0;
+        } else if (q.kind == 4) {
+          a.golden[q.dst].f2 = om;
+          a.golden[q.dst].eb2 = 0.0;
+        } else if (q.kind == 5) {
+          a.golden[q.dst].fb = om;
+          a.golden[q.dst].ebb = 0.0;
+        } else if (q.kind == 6) {
+          a.golden[q.dst].flo = om;
+          a.golden[q.dst].eblo = 0.0;
+        } else {
+          // kinds 1 (minimum) and 2 (Delta = lo) name the same value when the
+          // minimum is the Delta = lo point: keep both copies identical
+          LineResult& L = a.lines[q.dst];
+          const bool same = (L.flags & kFlagLower) != 0;
+          if (q.kind == 1 || same) {
+            L.omega_star = om;
+            L.eb_star = 0.0;
+            L.flags |= kFlagRescored;
+          }
+          if (q.kind == 2 || same) {
+            L.omega_lo = om;
+            L.eb_lo = 0.0;
+          }
+        }
+        a.counters[r] = 0;
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
 cudaError_t rescore_occupancy(int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, rescore_kernel, 256, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, rescore_kernel, kRescoreThreads, 0);
 }
 
 cudaError_t rescore_launch(const RescoreArgs& a, int grid, cudaStream_t s) {
-  rescore_kernel<<<grid, 256, 0, s>>>(a);
+  rescore_sort_kernel<<<1, 1024, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  rescore_kernel<<<grid, kRescoreThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
