@@ -59,19 +59,37 @@ def dist_env():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi sampling of SM clock and throttle reasons; only the samples taken inside the
+    timed region (host wall clock, marked by begin()/end()) are summarised."""
 
     def __init__(self, index: int):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        self.t0 = self.t1 = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.5)  # let the sampler start before the timed region
         except OSError:
             self.p = None
+
+    def begin(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def _when(stamp: str):
+        import datetime
+
+        try:
+            return datetime.datetime.strptime(stamp, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
 
     def stop(self):
         if self.p is None:
@@ -85,17 +103,21 @@ class Clocks:
         rows = []
         for line in open(self.f.name):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9:
+            if len(parts) >= 10:
                 rows.append(parts)
         os.unlink(self.f.name)
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        inside = rows
+        if self.t0 is not None and self.t1 is not None:
+            inside = [r for r in rows if (w := self._when(r[0])) is not None and self.t0 - 0.05 <= w <= self.t1 + 0.05]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples in the timed region"],
+                    "samples": 0, "samples_total": len(rows)}
+        sm = [float(r[2]) for r in inside if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in inside if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[6 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(inside), "interval_ms": 100}
 
 
 def cpu_baseline(cfg, lines, diagram_lines=None, tol=2e-7):
@@ -381,7 +403,7 @@ def threads_hint():
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ffe", choices=["ffe", "reference"])
     ap.add_argument("--N", type=int, default=1024)
@@ -438,6 +460,7 @@ def main():
     plan.kernel_ms()  # discard warm-up kernel timings
     clocks = Clocks(local)
     barrier()
+    clocks.begin()
     evs = []
     for _ in range(args.steps):
         flush.fill_(1.0)  # L2 flush between timed steps (outside the event pair)
@@ -448,6 +471,7 @@ def main():
         e1.record(stream)
         evs.append((e0, e1))
     barrier()
+    clocks.end()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     t_total = sum(step_ms) / 1e3

@@ -420,6 +420,13 @@ FFE_API ffe_status ffe_surrogate_grad(ffe_surrogate* s, const float* x, const fl
 FFE_API ffe_status ffe_surrogate_train(ffe_surrogate* s, const float* x, const float* t, int64_t n,
                                        int32_t epochs, int32_t batch, float lr,
                                        float* loss_per_epoch, void* stream);
+/* The same with one learning rate per epoch (lr_per_epoch[epochs], host,
+ * each > 0): the samples are uploaded once for the whole schedule.  A call
+ * with epochs E and rates r gives the same bits as E calls of
+ * ffe_surrogate_train with one epoch and rate r[e] each. */
+FFE_API ffe_status ffe_surrogate_train_schedule(ffe_surrogate* s, const float* x, const float* t, int64_t n,
+                                                int32_t epochs, int32_t batch, const float* lr_per_epoch,
+                                                float* loss_per_epoch, void* stream);
 
 /* Phase scan guided by the surrogate, grid or golden-section search.  The
  * surrogate predicts every (q, h, T) line's condensation energy on a Delta

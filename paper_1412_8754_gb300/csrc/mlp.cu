@@ -42,6 +42,9 @@ constexpr int kTileBytes = kTile * 2;
 constexpr int kOffW1 = 0, kOffB1 = 512, kOffW2 = 640, kOffB2 = 17024, kOffW3 = 17152, kOffB3 = 33536,
               kOffW4 = 33664, kOffB4 = 33792, kNParams = 33793;
 constexpr int kPartStride = 33796;  // floats per block of gradient partials (16-byte rows)
+// Threads of the forward and data-gradient kernels: kSplit per sample, each
+// owning kW / kSplit consecutive columns of its sample's row.
+constexpr int kSplit = 4, kThreads = kSplit * kRows, kCols = kW / kSplit;
 // BF16 weight tiles (global, each in the MMA layout): the B operands of the
 // forward products (n = out, k = in) and of the data-gradient products
 // (n = in, k = out)
@@ -140,9 +143,10 @@ __device__ __forceinline__ void mma_tile(uint32_t tmem, const void* a, const voi
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar)));
 }
 
-// 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane (warp w
+// reads lanes 32 (w mod 4) .. 32 (w mod 4) + 31).
 __device__ __forceinline__ void tmem_row32(uint32_t tmem, int c0, float (&v)[32]) {
-  const uint32_t ta = tmem + ((uint32_t)((threadIdx.x >> 5) * 32) << 16) + (uint32_t)c0;
+  const uint32_t ta = tmem + ((uint32_t)(((threadIdx.x >> 5) & 3) * 32) << 16) + (uint32_t)c0;
   uint32_t r[32];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
@@ -183,7 +187,7 @@ __device__ __forceinline__ bool layer_mma(uint32_t tmem, const void* a, const vo
 // Shared-memory plan of the kernels: up to three tiles, then the barriers, the
 // TMEM address and small FP32 parameters.
 constexpr size_t kSmemTiles3 = 3 * (size_t)kTileBytes;
-constexpr size_t kSmemExtra = 64 + 4 * 1088;
+constexpr size_t kSmemExtra = 64 + 4 * 1088 + 4 * kSplit * kRows;
 constexpr size_t kSmemFwd = kSmemTiles3 + kSmemExtra;
 constexpr size_t kSmemBwdData = kSmemTiles3 + kSmemExtra;
 constexpr size_t kSmemBwdW = 2 * (size_t)kTileBytes + kSmemExtra;
@@ -194,20 +198,24 @@ struct Bars {
   int32_t ok;
 };
 
-// Forward pass of up to 128 samples per block.  With Z/H non-NULL it also
-// keeps the pre-activations z1..z3 (FP32) and activations h1, h2 (BF16), each
-// as [layer][feature][ld] (ld >= the rows of every block, a multiple of 128)
-// for the backward pass; rows of the block at or beyond n are computed from
-// x = 0 and kept too (the backward pass gives them zero weight).
-__global__ void __launch_bounds__(128) mlp_fwd_kernel(const MlpDev P, const float* __restrict__ xraw, int64_t n,
-                                                      float* y, float* Z, __nv_bfloat16* H, int64_t ld) {
+// Forward pass of up to 128 samples per block, kSplit threads per sample
+// (thread t: sample t mod 128, columns kCols (t / 128) onwards).  With Z/H
+// non-NULL it also keeps the pre-activations z1..z3 (FP32) and activations
+// h1, h2 (BF16), each as [layer][feature][ld] (ld >= the rows of every block,
+// a multiple of 128) for the backward pass; rows of the block at or beyond n
+// are computed from x = 0 and kept too (the backward pass gives them zero
+// weight).
+__global__ void __launch_bounds__(kThreads, 2) mlp_fwd_kernel(const MlpDev P, const float* __restrict__ xraw,
+                                                              int64_t n, float* __restrict__ y, float* __restrict__ Z,
+                                                              __nv_bfloat16* __restrict__ H, int64_t ld) {
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* T2 = sm;
   unsigned char* T3 = sm + kTileBytes;
   unsigned char* Ht = sm + 2 * kTileBytes;
   Bars* bars = reinterpret_cast<Bars*>(sm + kSmemTiles3);
   float* prm = reinterpret_cast<float*>(sm + kSmemTiles3 + 64);  // W1 (512), b1, b2, b3, W4 (128 each), b4
-  const int tid = threadIdx.x;
+  float* outp = prm + 1088;                                        // [kSplit][128] output-layer partials
+  const int tid = threadIdx.x, rl = tid & (kRows - 1), cb = (tid / kRows) * kCols;
   if (tid == 0) {
     mbar_init(&bars->w, 1);
     mbar_init(&bars->mma, 1);
@@ -217,23 +225,25 @@ __global__ void __launch_bounds__(128) mlp_fwd_kernel(const MlpDev P, const floa
     tile_load_async(T3, P.tiles + kT3f * kTile, &bars->w);
   }
   if (tid < 32) tmem_alloc(&bars->tmem);
-  for (int i = tid; i < 512; i += 128) prm[i] = P.master[kOffW1 + i];
-  prm[512 + tid] = P.master[kOffB1 + tid];
-  prm[640 + tid] = P.master[kOffB2 + tid];
-  prm[768 + tid] = P.master[kOffB3 + tid];
-  prm[896 + tid] = P.master[kOffW4 + tid];
+  for (int i = tid; i < 512; i += kThreads) prm[i] = P.master[kOffW1 + i];
+  for (int i = tid; i < kW; i += kThreads) {
+    prm[512 + i] = P.master[kOffB1 + i];
+    prm[640 + i] = P.master[kOffB2 + i];
+    prm[768 + i] = P.master[kOffB3 + i];
+    prm[896 + i] = P.master[kOffW4 + i];
+  }
   if (tid == 0) prm[1024] = P.master[kOffB4];
   tc_before_sync();
   __syncthreads();
   tc_after_sync();
   const uint32_t tmem = bars->tmem;
-  const int64_t row = (int64_t)blockIdx.x * kRows + tid;
+  const int64_t row = (int64_t)blockIdx.x * kRows + rl;
   const bool live = row < n;
   float x[4];
 #pragma unroll
   for (int f = 0; f < 4; ++f) x[f] = live ? (xraw[row * 4 + f] - P.shift[f]) * P.scale[f] : 0.0f;
-  // layer 1 in FP32 (thread = sample)
-  for (int c0 = 0; c0 < kW; c0 += 8) {
+  // layer 1 in FP32
+  for (int c0 = cb; c0 < cb + kCols; c0 += 8) {
     float h[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -246,17 +256,16 @@ __global__ void __launch_bounds__(128) mlp_fwd_kernel(const MlpDev P, const floa
         H[(0 * kW + c) * ld + row] = __float2bfloat16(h[j]);
       }
     }
-    tile_store8(Ht, tid, c0, h);
+    tile_store8(Ht, rl, c0, h);
   }
   if (tid == 0) bars->ok = mbar_wait(&bars->w, 0, P.status) ? 1 : 0;  // the weight tiles are in
   bool ok = layer_mma(tmem, Ht, T2, &bars->mma, 0, P.status) && bars->ok;
-  // layer 2 epilogue: bias, SiLU, next layer's A tile
-  for (int c0 = 0; c0 < kW; c0 += 32) {
-    float v[32];
-    tmem_row32(tmem, c0, v);
+  {  // layer 2 epilogue: bias, SiLU, next layer's A tile
+    float v[kCols];
+    tmem_row32(tmem, cb, v);
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const int c = c0 + j;
+    for (int j = 0; j < kCols; ++j) {
+      const int c = cb + j;
       const float z = v[j] + prm[640 + c];
       v[j] = siluf_(z);
       if (Z) {
@@ -265,43 +274,52 @@ __global__ void __launch_bounds__(128) mlp_fwd_kernel(const MlpDev P, const floa
       }
     }
 #pragma unroll
-    for (int j = 0; j < 32; j += 8) tile_store8(Ht, tid, c0 + j, v + j);
+    for (int j = 0; j < kCols; j += 8) tile_store8(Ht, rl, cb + j, v + j);
   }
   ok = layer_mma(tmem, Ht, T3, &bars->mma, 1, P.status) && ok;
-  // layer 3 epilogue and the output layer
-  float acc = 0.0f;
-  for (int c0 = 0; c0 < kW; c0 += 32) {
-    float v[32];
-    tmem_row32(tmem, c0, v);
+  {  // layer 3 epilogue and this thread's share of the output layer
+    float v[kCols];
+    tmem_row32(tmem, cb, v);
+    float acc = 0.0f;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const int c = c0 + j;
+    for (int j = 0; j < kCols; ++j) {
+      const int c = cb + j;
       const float z = v[j] + prm[768 + c];
       if (Z) Z[(2 * kW + c) * ld + row] = z;
       acc = fmaf(siluf_(z), prm[896 + c], acc);
     }
+    outp[tid] = acc;
   }
-  if (live) y[row] = ok ? acc + prm[1024] : NAN;
   tc_before_sync();
   __syncthreads();
+  if (tid < kRows && live) {  // the shares of sample tid in a fixed order
+    float acc = outp[tid];
+#pragma unroll
+    for (int p = 1; p < kSplit; ++p) acc += outp[p * kRows + tid];
+    y[row] = ok ? acc + prm[1024] : NAN;
+  }
   if (tid < 32) tmem_free(tmem);
 }
 
-// Backward pass through the layers (data gradients), 128 samples per block:
+// Backward pass through the layers (data gradients), 128 samples per block,
+// kSplit threads per sample as in the forward pass:
 // dz3 = dy W4 s'(z3), dz2 = (dz3 W3^T) s'(z2), dz1 = (dz2 W2^T) s'(z1).
 // dy = 2 (y - t) / B for the mean squared error over a batch of B samples.
 // dZ is written for every row of the block (zero at and beyond n).
-__global__ void __launch_bounds__(128) mlp_bwd_data_kernel(const MlpDev P, const float* __restrict__ y,
-                                                           const float* __restrict__ tgt, float inv_yscale, int64_t n,
-                                                           float two_over_b, const float* __restrict__ Z, float* dZ,
-                                                           float* dy_out, double* loss_part, int64_t ld) {
+__global__ void __launch_bounds__(kThreads, 1) mlp_bwd_data_kernel(const MlpDev P, const float* __restrict__ y,
+                                                                   const float* __restrict__ tgt, float inv_yscale,
+                                                                   int64_t n, float two_over_b,
+                                                                   const float* __restrict__ Z, float* __restrict__ dZ,
+                                                                   float* __restrict__ dy_out,
+                                                                   double* __restrict__ loss_part, int64_t ld) {
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* T3 = sm;                    // B of dz2 = dz3 W3^T: (n = in, k = out)
   unsigned char* T2 = sm + kTileBytes;       // B of dz1 = dz2 W2^T
   unsigned char* Dt = sm + 2 * kTileBytes;   // the data gradient of the current layer, A
   Bars* bars = reinterpret_cast<Bars*>(sm + kSmemTiles3);
   float* red = reinterpret_cast<float*>(sm + kSmemTiles3 + 64);  // [128] squared residuals
-  const int tid = threadIdx.x;
+  float* w4 = red + kRows;                                        // [128] W4
+  const int tid = threadIdx.x, rl = tid & (kRows - 1), cb = (tid / kRows) * kCols;
   if (tid == 0) {
     mbar_init(&bars->w, 1);
     mbar_init(&bars->mma, 1);
@@ -311,12 +329,19 @@ __global__ void __launch_bounds__(128) mlp_bwd_data_kernel(const MlpDev P, const
     tile_load_async(T2, P.tiles + kT2b * kTile, &bars->w);
   }
   if (tid < 32) tmem_alloc(&bars->tmem);
-  const int64_t row = (int64_t)blockIdx.x * kRows + tid;
+  for (int i = tid; i < kW; i += kThreads) w4[i] = P.master[kOffW4 + i];
+  const int64_t row = (int64_t)blockIdx.x * kRows + rl;
   const bool live = row < n;
   const float r = live ? y[row] - tgt[row] * inv_yscale : 0.0f;
   const float dy = two_over_b * r;
-  if (live) dy_out[row] = dy;
-  red[tid] = r * r;
+  if (tid < kRows) {
+    if (live) dy_out[row] = dy;
+    red[tid] = r * r;
+  }
+  // this thread's columns of the saved pre-activations, loaded before any store
+  float z[kCols];
+#pragma unroll
+  for (int j = 0; j < kCols; ++j) z[j] = live ? Z[(2 * kW + cb + j) * ld + row] : 0.0f;
   tc_before_sync();
   __syncthreads();
   tc_after_sync();
@@ -326,33 +351,31 @@ __global__ void __launch_bounds__(128) mlp_bwd_data_kernel(const MlpDev P, const
     loss_part[blockIdx.x] = s;
   }
   const uint32_t tmem = bars->tmem;
-  for (int c0 = 0; c0 < kW; c0 += 8) {  // dz3 = dy W4 s'(z3)
-    float d[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int c = c0 + j;
-      d[j] = live ? dy * P.master[kOffW4 + c] * silu_primef_(Z[(2 * kW + c) * ld + row]) : 0.0f;
-      dZ[(2 * kW + c) * ld + row] = d[j];
-    }
-    tile_store8(Dt, tid, c0, d);
+  for (int j = 0; j < kCols; ++j) {  // dz3 = dy W4 s'(z3)
+    z[j] = live ? dy * w4[cb + j] * silu_primef_(z[j]) : 0.0f;
+    dZ[(2 * kW + cb + j) * ld + row] = z[j];
   }
+#pragma unroll
+  for (int j = 0; j < kCols; j += 8) tile_store8(Dt, rl, cb + j, z + j);
   if (tid == 0) bars->ok = mbar_wait(&bars->w, 0, P.status) ? 1 : 0;
   bool ok = true;
   for (int layer = 1; layer >= 0; --layer) {
+#pragma unroll
+    for (int j = 0; j < kCols; ++j) z[j] = live ? Z[(layer * kW + cb + j) * ld + row] : 0.0f;
     ok = layer_mma(tmem, Dt, layer == 1 ? T3 : T2, &bars->mma, layer == 1 ? 0 : 1, P.status) && bars->ok && ok;
-    for (int c0 = 0; c0 < kW; c0 += 32) {
-      float v[32];
-      tmem_row32(tmem, c0, v);
+    float v[kCols];
+    tmem_row32(tmem, cb, v);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int c = c0 + j;
-        v[j] = live ? (ok ? v[j] : NAN) * silu_primef_(Z[(layer * kW + c) * ld + row]) : 0.0f;
-        dZ[(layer * kW + c) * ld + row] = v[j];
-      }
-      if (layer == 1) {
+    for (int j = 0; j < kCols; ++j) {
+      v[j] = live ? (ok ? v[j] : NAN) * silu_primef_(z[j]) : 0.0f;
+      dZ[(layer * kW + cb + j) * ld + row] = v[j];
+    }
+    if (layer == 1) {
+      // every thread's reads of the layer's TMEM result and of the A tile are
+      // done before the tile is overwritten (the MMA that read it has completed)
 #pragma unroll
-        for (int j = 0; j < 32; j += 8) tile_store8(Dt, tid, c0 + j, v + j);
-      }
+      for (int j = 0; j < kCols; j += 8) tile_store8(Dt, rl, cb + j, v + j);
     }
   }
   tc_before_sync();
@@ -360,16 +383,94 @@ __global__ void __launch_bounds__(128) mlp_bwd_data_kernel(const MlpDev P, const
   if (tid < 32) tmem_free(tmem);
 }
 
-// Weight gradients of the two 128 x 128 layers for 128 samples:
-// dW2 = h1^T dz2 (blockIdx.y = 0), dW3 = h2^T dz3 (blockIdx.y = 1), as
-// D[i][o] = sum_s A[i][s] B[o][s] with A = h^T, B = dz^T (both K-major in s).
-__global__ void __launch_bounds__(128) mlp_bwd_weight_kernel(const MlpDev P, const __nv_bfloat16* __restrict__ H,
-                                                             const float* __restrict__ dZ, float* part, int64_t ld) {
+// The thin parts of the gradient for 128 samples: dW1 = x^T dz1, biases,
+// dW4 = h3^T dy, db4 = sum dy.  Thread t sums column t mod 128 over the 32
+// rows 32 (t / 128) .. 32 (t / 128) + 31 (each column's rows are contiguous in
+// the feature-major arrays and read four at a time; rows at or beyond n have
+// zero data gradients); the kSplit row-segment sums are then added in a fixed
+// order.  sh: 5248 floats of shared memory.
+__device__ __forceinline__ void bwd_small_block(const MlpDev& P, const float* __restrict__ xraw,
+                                                const float* __restrict__ Z, const float* __restrict__ dZ,
+                                                const float* __restrict__ dyv, int64_t n, float* __restrict__ part,
+                                                int64_t ld, float* sh) {
+  constexpr int kSeg = kRows / kSplit, kNv = 9;  // rows per thread, sums per column
+  float(*xs)[4] = reinterpret_cast<float(*)[4]>(sh);
+  float* dys = sh + 4 * kRows;
+  float* psum = dys + kRows;  // [kNv][kSplit][128]
+  const int tid = threadIdx.x, c = tid & (kRows - 1), seg = tid / kRows;
+  const int64_t row0 = (int64_t)blockIdx.x * kRows;
+  if (tid < kRows) {
+    const int64_t row = row0 + tid;
+    const bool live = row < n;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) xs[tid][f] = live ? (xraw[row * 4 + f] - P.shift[f]) * P.scale[f] : 0.0f;
+    dys[tid] = live ? dyv[row] : 0.0f;
+  }
+  __syncthreads();
+  const int64_t rs = row0 + seg * kSeg;
+  const float4* d1 = reinterpret_cast<const float4*>(dZ + (0 * kW + c) * ld + rs);
+  const float4* d2 = reinterpret_cast<const float4*>(dZ + (1 * kW + c) * ld + rs);
+  const float4* d3 = reinterpret_cast<const float4*>(dZ + (2 * kW + c) * ld + rs);
+  const float4* z3 = reinterpret_cast<const float4*>(Z + (2 * kW + c) * ld + rs);
+  float g[kNv] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // dW1 (4), db1, db2, db3, dW4, db4
+#pragma unroll 2
+  for (int r4 = 0; r4 < kSeg / 4; ++r4) {
+    const float4 a = d1[r4], b = d2[r4], e = d3[r4], z = z3[r4];
+    const float av[4] = {a.x, a.y, a.z, a.w}, zv[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = seg * kSeg + 4 * r4 + i;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) g[f] += xs[r][f] * av[i];
+      g[7] += siluf_(zv[i]) * dys[r];
+      g[8] += dys[r];
+    }
+    g[4] += (a.x + a.y) + (a.z + a.w);
+    g[5] += (b.x + b.y) + (b.z + b.w);
+    g[6] += (e.x + e.y) + (e.z + e.w);
+  }
+#pragma unroll
+  for (int k = 0; k < kNv; ++k) psum[(k * kSplit + seg) * kRows + c] = g[k];
+  __syncthreads();
+  if (tid >= kRows) return;
+#pragma unroll
+  for (int k = 0; k < kNv; ++k) {
+    float t = psum[(k * kSplit) * kRows + c];
+#pragma unroll
+    for (int q = 1; q < kSplit; ++q) t += psum[(k * kSplit + q) * kRows + c];
+    g[k] = t;
+  }
+  float* dst = part + (int64_t)blockIdx.x * kPartStride;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) dst[kOffW1 + f * kW + c] = g[f];
+  dst[kOffB1 + c] = g[4];
+  dst[kOffB2 + c] = g[5];
+  dst[kOffB3 + c] = g[6];
+  dst[kOffW4 + c] = g[7];
+  if (c == 0) dst[kOffB4] = g[8];
+}
+
+// Weight gradients for 128 samples: dW2 = h1^T dz2 (blockIdx.y = 0),
+// dW3 = h2^T dz3 (blockIdx.y = 1), as D[i][o] = sum_s A[i][s] B[o][s] with
+// A = h^T, B = dz^T (both K-major in s) on the tensor cores, thread t reading
+// out columns kCols (t / 128) onwards of row t mod 128; the thin parts
+// (blockIdx.y = 2) on the FP32 pipe.
+__global__ void __launch_bounds__(kThreads, 1) mlp_bwd_weight_kernel(const MlpDev P,
+                                                                     const __nv_bfloat16* __restrict__ H,
+                                                                     const float* __restrict__ dZ,
+                                                                     float* __restrict__ part, int64_t ld,
+                                                                     const float* __restrict__ xraw,
+                                                                     const float* __restrict__ Z,
+                                                                     const float* __restrict__ dyv, int64_t n) {
   extern __shared__ __align__(1024) unsigned char sm[];
+  if (blockIdx.y == 2) {
+    bwd_small_block(P, xraw, Z, dZ, dyv, n, part, ld, reinterpret_cast<float*>(sm));
+    return;
+  }
   unsigned char* At = sm;
   unsigned char* Bt = sm + kTileBytes;
   Bars* bars = reinterpret_cast<Bars*>(sm + 2 * kTileBytes);
-  const int L = blockIdx.y, tid = threadIdx.x;
+  const int L = blockIdx.y, tid = threadIdx.x, rl = tid & (kRows - 1), cb = (tid / kRows) * kCols;
   const int64_t row0 = (int64_t)blockIdx.x * kRows;
   if (tid == 0) {
     mbar_init(&bars->mma, 1);
@@ -377,7 +478,7 @@ __global__ void __launch_bounds__(128) mlp_bwd_weight_kernel(const MlpDev P, con
   }
   if (tid < 32) tmem_alloc(&bars->tmem);
   // rows i of A (features) and o of B: 8 consecutive samples per 16-byte store
-  for (int e = tid; e < kW * (kRows / 8); e += 128) {
+  for (int e = tid; e < kW * (kRows / 8); e += kThreads) {
     const int f = e / (kRows / 8), s0 = (e % (kRows / 8)) * 8;
     *reinterpret_cast<uint4*>(At + tile_off(f, s0)) =
         *reinterpret_cast<const uint4*>(H + ((int64_t)L * kW + f) * ld + row0 + s0);
@@ -391,68 +492,18 @@ __global__ void __launch_bounds__(128) mlp_bwd_weight_kernel(const MlpDev P, con
   tc_after_sync();
   const uint32_t tmem = bars->tmem;
   const bool ok = layer_mma(tmem, At, Bt, &bars->mma, 0, P.status);
-  float* dst = part + (int64_t)blockIdx.x * kPartStride + (L == 0 ? kOffW2 : kOffW3) + (int64_t)tid * kW;
-  for (int c0 = 0; c0 < kW; c0 += 32) {
-    float v[32];
-    tmem_row32(tmem, c0, v);
+  float* dst = part + (int64_t)blockIdx.x * kPartStride + (L == 0 ? kOffW2 : kOffW3) + (int64_t)rl * kW + cb;
+  {
+    float v[kCols];
+    tmem_row32(tmem, cb, v);
 #pragma unroll
-    for (int j = 0; j < 32; j += 4)
-      *reinterpret_cast<float4*>(dst + c0 + j) =
+    for (int j = 0; j < kCols; j += 4)
+      *reinterpret_cast<float4*>(dst + j) =
           ok ? make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]) : make_float4(NAN, NAN, NAN, NAN);
   }
   tc_before_sync();
   __syncthreads();
   if (tid < 32) tmem_free(tmem);
-}
-
-// The thin parts of the gradient for 128 samples: dW1 = x^T dz1, biases,
-// dW4 = h3^T dy, db4 = sum dy (thread = column; each column's 128 rows are
-// contiguous in the feature-major arrays and read four at a time; rows at or
-// beyond n have zero data gradients).
-__global__ void __launch_bounds__(128) mlp_bwd_small_kernel(const MlpDev P, const float* __restrict__ xraw,
-                                                            const float* __restrict__ Z, const float* __restrict__ dZ,
-                                                            const float* __restrict__ dyv, int64_t n, float* part,
-                                                            int64_t ld) {
-  __shared__ float xs[kRows][4];
-  __shared__ float dys[kRows];
-  const int c = threadIdx.x;
-  const int64_t row0 = (int64_t)blockIdx.x * kRows;
-  {
-    const int64_t row = row0 + c;
-    const bool live = row < n;
-#pragma unroll
-    for (int f = 0; f < 4; ++f) xs[c][f] = live ? (xraw[row * 4 + f] - P.shift[f]) * P.scale[f] : 0.0f;
-    dys[c] = live ? dyv[row] : 0.0f;
-  }
-  __syncthreads();
-  const float4* d1 = reinterpret_cast<const float4*>(dZ + (0 * kW + c) * ld + row0);
-  const float4* d2 = reinterpret_cast<const float4*>(dZ + (1 * kW + c) * ld + row0);
-  const float4* d3 = reinterpret_cast<const float4*>(dZ + (2 * kW + c) * ld + row0);
-  const float4* z3 = reinterpret_cast<const float4*>(Z + (2 * kW + c) * ld + row0);
-  float gw1[4] = {0, 0, 0, 0}, gb1 = 0, gb2 = 0, gb3 = 0, gw4 = 0, gb4 = 0;
-  for (int r4 = 0; r4 < kRows / 4; ++r4) {
-    const float4 a = d1[r4], b = d2[r4], e = d3[r4], z = z3[r4];
-    const float av[4] = {a.x, a.y, a.z, a.w}, zv[4] = {z.x, z.y, z.z, z.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = 4 * r4 + i;
-#pragma unroll
-      for (int f = 0; f < 4; ++f) gw1[f] += xs[r][f] * av[i];
-      gw4 += siluf_(zv[i]) * dys[r];
-      gb4 += dys[r];
-    }
-    gb1 += (a.x + a.y) + (a.z + a.w);
-    gb2 += (b.x + b.y) + (b.z + b.w);
-    gb3 += (e.x + e.y) + (e.z + e.w);
-  }
-  float* dst = part + (int64_t)blockIdx.x * kPartStride;
-#pragma unroll
-  for (int f = 0; f < 4; ++f) dst[kOffW1 + f * kW + c] = gw1[f];
-  dst[kOffB1 + c] = gb1;
-  dst[kOffB2 + c] = gb2;
-  dst[kOffB3 + c] = gb3;
-  dst[kOffW4 + c] = gw4;
-  if (c == 0) dst[kOffB4] = gb4;
 }
 
 // The weight tiles of W2 / W3 element (in, out) in the MMA layout.
@@ -463,10 +514,21 @@ __device__ __forceinline__ void put_weight(__nv_bfloat16* tiles, int layer3, int
 }
 
 // Sum the per-block partials (fixed order); optionally write the gradient;
-// optionally take an Adam step and refresh the BF16 tiles.
+// optionally take an Adam step and refresh the BF16 tiles.  With loss_total
+// non-NULL the grid has one more block, whose first thread adds the step's
+// loss partials (fixed order) to *loss_total.
 __global__ void mlp_reduce_kernel(const float* __restrict__ part, int n_blocks, float* grad, float* master, float* m,
                                   float* v, float lr, float beta1, float beta2, float eps, float bc1, float bc2,
-                                  int do_step, __nv_bfloat16* tiles) {
+                                  int do_step, __nv_bfloat16* tiles, const double* __restrict__ loss_part,
+                                  double* loss_total) {
+  if (loss_total && blockIdx.x == gridDim.x - 1) {
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int b = 0; b < n_blocks; ++b) s += loss_part[b];
+      *loss_total += s;
+    }
+    return;
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kNParams) return;
   float gsum = 0.0f;
@@ -504,14 +566,6 @@ __global__ void targets_kernel(const double* __restrict__ omega, int64_t n_value
     const int64_t ref = i - i % n_per_line;
     y[i] = (float)((omega[i] - omega[ref]) / n2);
   }
-}
-
-// Adds a step's loss partials (fixed order) to the epoch's total.
-__global__ void mlp_loss_kernel(const double* __restrict__ loss_part, int n_blocks, double* total) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double s = 0.0;
-  for (int b = 0; b < n_blocks; ++b) s += loss_part[b];
-  *total += s;
 }
 
 }  // namespace ffe
@@ -611,15 +665,13 @@ ffe_status fwd_bwd(ffe_surrogate* s, const float* x, const float* t, int64_t n, 
   const MlpDev P = make_dev(s);
   const int nb = (int)((n + kRows - 1) / kRows);
   if ((int64_t)nb * kRows > s->ld) return set_err(s->ctx, "surrogate scratch too small"), FFE_EINTERNAL;
-  mlp_fwd_kernel<<<nb, 128, kSmemFwd, st>>>(P, x, n, s->y, s->Z, s->H, s->ld);
+  mlp_fwd_kernel<<<nb, kThreads, kSmemFwd, st>>>(P, x, n, s->y, s->Z, s->H, s->ld);
   SUR_CU(cudaGetLastError(), "mlp_fwd");
-  mlp_bwd_data_kernel<<<nb, 128, kSmemBwdData, st>>>(P, s->y, t, 1.0f / s->meta.y_scale, n, 2.0f / (float)n, s->Z,
+  mlp_bwd_data_kernel<<<nb, kThreads, kSmemBwdData, st>>>(P, s->y, t, 1.0f / s->meta.y_scale, n, 2.0f / (float)n, s->Z,
                                                       s->dZ, s->dy, s->loss_part, s->ld);
   SUR_CU(cudaGetLastError(), "mlp_bwd_data");
-  mlp_bwd_weight_kernel<<<dim3(nb, 2), 128, kSmemBwdW, st>>>(P, s->H, s->dZ, s->part, s->ld);
+  mlp_bwd_weight_kernel<<<dim3(nb, 3), kThreads, kSmemBwdW, st>>>(P, s->H, s->dZ, s->part, s->ld, x, s->Z, s->dy, n);
   SUR_CU(cudaGetLastError(), "mlp_bwd_weight");
-  mlp_bwd_small_kernel<<<nb, 128, 0, st>>>(P, x, s->Z, s->dZ, s->dy, n, s->part, s->ld);
-  SUR_CU(cudaGetLastError(), "mlp_bwd_small");
   return FFE_OK;
 }
 
@@ -797,7 +849,7 @@ ffe_status ffe_surrogate_predict(ffe_surrogate* s, const float* xraw, int64_t n,
   cudaStream_t cs = s->stream;
   SUR_CU(cudaMemcpyAsync(s->x, xraw, n * 4 * sizeof(float), cudaMemcpyHostToDevice, cs), "upload");
   const int nb = (int)((n + kRows - 1) / kRows);
-  mlp_fwd_kernel<<<nb, 128, kSmemFwd, cs>>>(make_dev(s), s->x, n, s->y, nullptr, nullptr, 0);
+  mlp_fwd_kernel<<<nb, kThreads, kSmemFwd, cs>>>(make_dev(s), s->x, n, s->y, nullptr, nullptr, 0);
   SUR_CU(cudaGetLastError(), "mlp_fwd");
   std::vector<float> yn(n);
   SUR_CU(cudaMemcpyAsync(yn.data(), s->y, n * sizeof(float), cudaMemcpyDeviceToHost, cs), "download");
@@ -818,7 +870,7 @@ ffe_status ffe_surrogate_grad(ffe_surrogate* s, const float* xraw, const float* 
   if ((st = fwd_bwd(s, s->x, s->t, n, cs)) != FFE_OK) return st;
   const int nb = (int)((n + kRows - 1) / kRows);
   mlp_reduce_kernel<<<(kNParams + 255) / 256, 256, 0, cs>>>(s->part, nb, s->grad, nullptr, nullptr, nullptr, 0, 0, 0,
-                                                             0, 1, 1, 0, nullptr);
+                                                             0, 1, 1, 0, nullptr, nullptr, nullptr);
   SUR_CU(cudaGetLastError(), "reduce");
   std::vector<double> lp(nb);
   SUR_CU(cudaMemcpyAsync(grad, s->grad, kNParams * sizeof(float), cudaMemcpyDeviceToHost, cs), "download");
@@ -832,10 +884,13 @@ ffe_status ffe_surrogate_grad(ffe_surrogate* s, const float* xraw, const float* 
   return FFE_OK;
 }
 
-ffe_status ffe_surrogate_train(ffe_surrogate* s, const float* xraw, const float* traw, int64_t n, int32_t epochs,
-                               int32_t batch, float lr, float* loss_per_epoch, void* stream) {
-  if (!s || !xraw || !traw || n < 1 || epochs < 1 || batch < 64 || batch % 64 != 0 || !(lr > 0.0f))
+ffe_status ffe_surrogate_train_schedule(ffe_surrogate* s, const float* xraw, const float* traw, int64_t n,
+                                        int32_t epochs, int32_t batch, const float* lr_per_epoch,
+                                        float* loss_per_epoch, void* stream) {
+  if (!s || !xraw || !traw || !lr_per_epoch || n < 1 || epochs < 1 || batch < 64 || batch % 64 != 0)
     return s ? (set_err(s->ctx, "train: bad arguments (batch a multiple of 64)"), FFE_EINVAL) : FFE_EINVAL;
+  for (int ep = 0; ep < epochs; ++ep)
+    if (!(lr_per_epoch[ep] > 0.0f)) return set_err(s->ctx, "train: learning rates must be > 0"), FFE_EINVAL;
   (void)stream;
   ffe_status st = ensure_scratch(s, std::max<int64_t>(n, batch), batch);
   if (st != FFE_OK) return st;
@@ -855,18 +910,17 @@ ffe_status ffe_surrogate_train(ffe_surrogate* s, const float* xraw, const float*
   if (steps < 1) return set_err(s->ctx, "train: fewer samples than one batch"), FFE_EINVAL;
   const int nb = (batch + kRows - 1) / kRows;
   for (int ep = 0; ep < epochs; ++ep) {
+    const float lr = lr_per_epoch[ep];
     for (int64_t k = 0; k < steps; ++k) {
       const int64_t off = k * batch;
       if ((st = fwd_bwd(s, s->x + off * 4, s->t + off, batch, cs)) != FFE_OK) return st;
       ++s->adam_t;
       const float bc1 = 1.0f - powf(b1, (float)s->adam_t), bc2 = 1.0f - powf(b2, (float)s->adam_t);
-      mlp_reduce_kernel<<<(kNParams + 255) / 256, 256, 0, cs>>>(
-          s->part, nb, nullptr, s->master, s->m, s->v, lr, b1, b2, eps, bc1, bc2, 1, s->tiles);
+      double* loss_total = loss_per_epoch ? s->epoch_loss + ep : nullptr;
+      mlp_reduce_kernel<<<(kNParams + 255) / 256 + (loss_total ? 1 : 0), 256, 0, cs>>>(
+          s->part, nb, nullptr, s->master, s->m, s->v, lr, b1, b2, eps, bc1, bc2, 1, s->tiles, s->loss_part,
+          loss_total);
       SUR_CU(cudaGetLastError(), "adam");
-      if (loss_per_epoch) {
-        mlp_loss_kernel<<<1, 32, 0, cs>>>(s->loss_part, nb, s->epoch_loss + ep);
-        SUR_CU(cudaGetLastError(), "loss");
-      }
     }
   }
   std::vector<double> el(epochs);
@@ -878,6 +932,14 @@ ffe_status ffe_surrogate_train(ffe_surrogate* s, const float* xraw, const float*
   return FFE_OK;
 }
 
+ffe_status ffe_surrogate_train(ffe_surrogate* s, const float* xraw, const float* traw, int64_t n, int32_t epochs,
+                               int32_t batch, float lr, float* loss_per_epoch, void* stream) {
+  if (!s || epochs < 1 || !(lr > 0.0f))
+    return s ? (set_err(s->ctx, "train: bad arguments"), FFE_EINVAL) : FFE_EINVAL;
+  std::vector<float> lrs(epochs, lr);
+  return ffe_surrogate_train_schedule(s, xraw, traw, n, epochs, batch, lrs.data(), loss_per_epoch, stream);
+}
+
 }  // extern "C"
 
 namespace ffe {
@@ -885,7 +947,7 @@ namespace ffe {
 ffe_status surrogate_infer_device(ffe_surrogate* s, const float* x, int64_t n, float* y, cudaStream_t st) {
   if (n < 1) return FFE_OK;
   const int nb = (int)((n + kRows - 1) / kRows);
-  mlp_fwd_kernel<<<nb, 128, kSmemFwd, st>>>(make_dev(s), x, n, y, nullptr, nullptr, 0);
+  mlp_fwd_kernel<<<nb, kThreads, kSmemFwd, st>>>(make_dev(s), x, n, y, nullptr, nullptr, 0);
   SUR_CU(cudaGetLastError(), "mlp_fwd");
   return FFE_OK;
 }

@@ -109,6 +109,8 @@ _SIGNATURES = [
     ("ffe_surrogate_grad", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.POINTER(ctypes.c_double), _VP]),
     ("ffe_surrogate_train", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_float, _VP, _VP]),
+    ("ffe_surrogate_train_schedule", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                                    _VP, _VP, _VP]),
     ("ffe_surrogate_scan", ctypes.c_int, [_VP, _VP, ctypes.POINTER(ffe_scan), _VP, _VP, _VP, _VP, _VP, _VP]),
     ("ffe_omega_noalloc", ctypes.c_int, [ctypes.POINTER(ffe_model), ctypes.c_int32, ctypes.c_double,
                                          ctypes.c_double, _VP, _VP, _VP, ctypes.c_int32, _VP, _VP]),
@@ -207,6 +209,16 @@ class Surrogate:
         losses = np.zeros(epochs, dtype=np.float32)
         _check(self.ctx.handle, lib().ffe_surrogate_train(self.handle, _ptr(x), _ptr(t), len(x), epochs, batch,
                                                           float(lr), _ptr(losses), None))
+        return losses
+
+    def train_schedule(self, x, t, lr_per_epoch, batch):
+        """Training with one learning rate per epoch; the samples are uploaded once."""
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 4)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        lrs = np.ascontiguousarray(lr_per_epoch, dtype=np.float32)
+        losses = np.zeros(len(lrs), dtype=np.float32)
+        _check(self.ctx.handle, lib().ffe_surrogate_train_schedule(self.handle, _ptr(x), _ptr(t), len(x), len(lrs),
+                                                                   batch, _ptr(lrs), _ptr(losses), None))
         return losses
 
     def close(self):

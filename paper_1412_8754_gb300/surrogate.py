@@ -43,8 +43,8 @@ def training_data(ctx: ffe.Context, N: int, sset: dict):
 
 def fit(ctx: ffe.Context, x, y, epochs=30, batch=4096, lr=2e-3, seed=0, y_scale=None, decay=True):
     """A surrogate trained on (x, y) with Adam; returns (Surrogate, losses).  decay: the learning
-    rate follows a half cosine from lr down to lr/50 over the epochs (one training call per
-    epoch), so that the final weights settle instead of ending wherever constant-rate steps leave
+    rate follows a half cosine from lr down to lr/50 over the epochs (one training call with a
+    rate per epoch), so that the final weights settle instead of ending wherever constant-rate steps leave
     them."""
     rng = np.random.default_rng(seed)
     perm = rng.permutation(len(x))
@@ -53,11 +53,9 @@ def fit(ctx: ffe.Context, x, y, epochs=30, batch=4096, lr=2e-3, seed=0, y_scale=
     xp, yp = np.ascontiguousarray(x[perm]), np.ascontiguousarray(y[perm])
     if not decay:
         return s, s.train(xp, yp, epochs=epochs, batch=batch, lr=lr)
-    losses = []
-    for e in range(epochs):
-        lr_e = lr * (0.02 + 0.98 * 0.5 * (1.0 + np.cos(np.pi * e / max(1, epochs - 1))))
-        losses.append(float(s.train(xp, yp, epochs=1, batch=batch, lr=float(lr_e))[0]))
-    return s, np.array(losses, dtype=np.float32)
+    e = np.arange(epochs)
+    lrs = (lr * (0.02 + 0.98 * 0.5 * (1.0 + np.cos(np.pi * e / max(1, epochs - 1))))).astype(np.float32)
+    return s, s.train_schedule(xp, yp, lrs, batch=batch)
 
 
 def rms_error(s: "ffe.Surrogate", x, y, n=65536, seed=0) -> float:

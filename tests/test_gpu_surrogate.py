@@ -263,3 +263,25 @@ def test_training_targets_are_the_condensation_energies(ctx, N):
     assert got.dtype == np.float32 and got.shape == om.shape
     assert np.array_equal(got, want)
     assert np.all(got[..., 0] == 0.0)
+
+
+def test_learning_rate_schedule_equals_one_call_per_epoch(ctx):
+    """ffe_surrogate_train_schedule with rates r[0..2] gives the same losses and weights, bit for
+    bit, as three one-epoch ffe_surrogate_train calls at r[e] (the Adam step count carries over)."""
+    rng = np.random.default_rng(31)
+    xr = raw_inputs(3000, rng)
+    f = mlp.features(xr)
+    t = (np.cos(2 * f[:, 0]) * f[:, 3] ** 2 + 0.3 * f[:, 2] * f[:, 3]) * Y_SCALE
+    lrs = np.array([3e-3, 1.5e-3, 2e-4], dtype=np.float32)
+    a = make(ctx, mlp.init_params(41))
+    la = np.array([a.train(xr, t, epochs=1, batch=256, lr=float(r))[0] for r in lrs], dtype=np.float32)
+    wa = a.get_params()
+    a.close()
+    b = make(ctx, mlp.init_params(41))
+    lb = b.train_schedule(xr, t, lrs, batch=256)
+    wb = b.get_params()
+    with pytest.raises(ffe.FFEError):
+        b.train_schedule(xr, t, np.array([1e-3, 0.0], dtype=np.float32), batch=256)
+    b.close()
+    assert np.array_equal(la, lb) and np.array_equal(wa, wb)
+    assert lb[-1] < lb[0]
