@@ -44,7 +44,7 @@ constexpr int kOffW1 = 0, kOffB1 = 512, kOffW2 = 640, kOffB2 = 17024, kOffW3 = 1
 constexpr int kPartStride = 33796;  // floats per block of gradient partials (16-byte rows)
 // Threads of the forward and data-gradient kernels: kSplit per sample, each
 // owning kW / kSplit consecutive columns of its sample's row.
-constexpr int kSplit = 4, kThreads = kSplit * kRows, kCols = kW / kSplit;
+constexpr int kSplit = 8, kThreads = kSplit * kRows, kCols = kW / kSplit;
 // BF16 weight tiles (global, each in the MMA layout): the B operands of the
 // forward products (n = out, k = in) and of the data-gradient products
 // (n = in, k = out)
@@ -143,22 +143,32 @@ __device__ __forceinline__ void mma_tile(uint32_t tmem, const void* a, const voi
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar)));
 }
 
-// 32 consecutive FP32 accumulator columns of this thread's TMEM lane (warp w
-// reads lanes 32 (w mod 4) .. 32 (w mod 4) + 31).
-__device__ __forceinline__ void tmem_row32(uint32_t tmem, int c0, float (&v)[32]) {
+// NC (16 or 32) consecutive FP32 accumulator columns of this thread's TMEM
+// lane (warp w reads lanes 32 (w mod 4) .. 32 (w mod 4) + 31).
+template <int NC>
+__device__ __forceinline__ void tmem_row(uint32_t tmem, int c0, float (&v)[NC]) {
+  static_assert(NC == 16 || NC == 32, "16 or 32 columns");
   const uint32_t ta = tmem + ((uint32_t)(((threadIdx.x >> 5) & 3) * 32) << 16) + (uint32_t)c0;
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
-      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(ta));
+  uint32_t r[NC];
+  if constexpr (NC == 32) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+        "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(ta));
+  } else {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(ta));
+  }
   asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+  for (int j = 0; j < NC; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 // Eight values of row r, columns c0..c0+7 (c0 % 8 == 0), into a tile: one 16-byte store.
@@ -205,7 +215,7 @@ struct Bars {
 // a multiple of 128) for the backward pass; rows of the block at or beyond n
 // are computed from x = 0 and kept too (the backward pass gives them zero
 // weight).
-__global__ void __launch_bounds__(kThreads, 2) mlp_fwd_kernel(const MlpDev P, const float* __restrict__ xraw,
+__global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(const MlpDev P, const float* __restrict__ xraw,
                                                               int64_t n, float* __restrict__ y, float* __restrict__ Z,
                                                               __nv_bfloat16* __restrict__ H, int64_t ld) {
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -262,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 2) mlp_fwd_kernel(const MlpDev P, co
   bool ok = layer_mma(tmem, Ht, T2, &bars->mma, 0, P.status) && bars->ok;
   {  // layer 2 epilogue: bias, SiLU, next layer's A tile
     float v[kCols];
-    tmem_row32(tmem, cb, v);
+    tmem_row<kCols>(tmem, cb, v);
 #pragma unroll
     for (int j = 0; j < kCols; ++j) {
       const int c = cb + j;
@@ -279,7 +289,7 @@ __global__ void __launch_bounds__(kThreads, 2) mlp_fwd_kernel(const MlpDev P, co
   ok = layer_mma(tmem, Ht, T3, &bars->mma, 1, P.status) && ok;
   {  // layer 3 epilogue and this thread's share of the output layer
     float v[kCols];
-    tmem_row32(tmem, cb, v);
+    tmem_row<kCols>(tmem, cb, v);
     float acc = 0.0f;
 #pragma unroll
     for (int j = 0; j < kCols; ++j) {
@@ -345,10 +355,11 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_data_kernel(const MlpDev 
   tc_before_sync();
   __syncthreads();
   tc_after_sync();
-  if (tid == 0) {  // per-block sum of squared residuals, fixed order
-    double s = 0.0;
-    for (int i = 0; i < kRows; ++i) s += red[i];
-    loss_part[blockIdx.x] = s;
+  if (tid < 32) {  // per-block sum of squared residuals: four per lane, then a fixed butterfly
+    double s = ((double)red[tid] + (double)red[tid + 32]) + ((double)red[tid + 64] + (double)red[tid + 96]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (tid == 0) loss_part[blockIdx.x] = s;
   }
   const uint32_t tmem = bars->tmem;
 #pragma unroll
@@ -365,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_data_kernel(const MlpDev 
     for (int j = 0; j < kCols; ++j) z[j] = live ? Z[(layer * kW + cb + j) * ld + row] : 0.0f;
     ok = layer_mma(tmem, Dt, layer == 1 ? T3 : T2, &bars->mma, layer == 1 ? 0 : 1, P.status) && bars->ok && ok;
     float v[kCols];
-    tmem_row32(tmem, cb, v);
+    tmem_row<kCols>(tmem, cb, v);
 #pragma unroll
     for (int j = 0; j < kCols; ++j) {
       v[j] = live ? (ok ? v[j] : NAN) * silu_primef_(z[j]) : 0.0f;
@@ -388,7 +399,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_data_kernel(const MlpDev 
 // rows 32 (t / 128) .. 32 (t / 128) + 31 (each column's rows are contiguous in
 // the feature-major arrays and read four at a time; rows at or beyond n have
 // zero data gradients); the kSplit row-segment sums are then added in a fixed
-// order.  sh: 5248 floats of shared memory.
+// order.  sh: (5 + 9 kSplit) 128 floats of shared memory.
 __device__ __forceinline__ void bwd_small_block(const MlpDev& P, const float* __restrict__ xraw,
                                                 const float* __restrict__ Z, const float* __restrict__ dZ,
                                                 const float* __restrict__ dyv, int64_t n, float* __restrict__ part,
@@ -413,7 +424,7 @@ __device__ __forceinline__ void bwd_small_block(const MlpDev& P, const float* __
   const float4* d3 = reinterpret_cast<const float4*>(dZ + (2 * kW + c) * ld + rs);
   const float4* z3 = reinterpret_cast<const float4*>(Z + (2 * kW + c) * ld + rs);
   float g[kNv] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // dW1 (4), db1, db2, db3, dW4, db4
-#pragma unroll 2
+#pragma unroll 1
   for (int r4 = 0; r4 < kSeg / 4; ++r4) {
     const float4 a = d1[r4], b = d2[r4], e = d3[r4], z = z3[r4];
     const float av[4] = {a.x, a.y, a.z, a.w}, zv[4] = {z.x, z.y, z.z, z.w};
@@ -495,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_weight_kernel(const MlpDe
   float* dst = part + (int64_t)blockIdx.x * kPartStride + (L == 0 ? kOffW2 : kOffW3) + (int64_t)rl * kW + cb;
   {
     float v[kCols];
-    tmem_row32(tmem, cb, v);
+    tmem_row<kCols>(tmem, cb, v);
 #pragma unroll
     for (int j = 0; j < kCols; j += 4)
       *reinterpret_cast<float4*>(dst + j) =
