@@ -502,8 +502,62 @@ __device__ __forceinline__ double row_total64(const double* red, int nrows, int 
   return t;
 }
 
+// Split exponentials.  With P = R - d0 + h and M = R + d0 - h (P + M = 2R >= 0)
+// the two arguments of band_term_f64 are {|R - |d||, R + |d|} = {|P|, |M|},
+// and for a batch whose outputs share T,
+//   e^{-|P|/T} = e^{-alpha} e^{-eta}  (P >= 0),  e^{alpha} e^{eta}  (P < 0),
+//   e^{-|M|/T} = e^{-beta} e^{eta}    (M >= 0),  e^{beta} e^{-eta}  (M < 0),
+// alpha = (R - d0)/T, beta = (R + d0)/T per entry, eta = h/T per output: four
+// exponentials per entry and two per output for the whole batch instead of two
+// per (entry, output).  With |eta| <= 600 every factor taken is finite: a
+// factor e^{-alpha} is used only where alpha >= -eta >= -600 (the arguments
+// are capped at 700, so an unused one never overflows), and one that
+// underflows belongs to an argument |P|/T or |M|/T beyond kExpNegligible,
+// which is 0 anyway.  Rounding: each factor and the product are within a few
+// ulp; the arguments' own rounding (the cancellation in R - d0, scaled by 1/T)
+// is of the same size as in the direct form.
+__device__ __forceinline__ bool split_exp_batch(const BParD* bp, int nvalid, int lane) {
+  const BParD p0 = bp[0];
+  const bool ok = lane >= nvalid || (bp[lane].t == p0.t && fabs(bp[lane].h * p0.inv_t) <= 600.0);
+  return __all_sync(kFull, ok);
+}
+
+// |x| >= kExpNegligible (40) from the high word of x: the order of the bit
+// patterns of non-negative doubles is their numeric order.
+__device__ __forceinline__ bool beyond_exp40(double x) {
+  return (__double2hiint(x) & 0x7fffffff) >= 0x40440000;  // high word of 40.0
+}
+
+// flush64's band terms of one shared-T batch by split exponentials; each lane's
+// entry (as, d0; R, A at the batch's Delta) on every output j into red[j][lane].
+__device__ __forceinline__ void flush64_split(const BParD* bp, int nvalid, int lane, bool live, double R, double A,
+                                              double as, double d0, double* red) {
+  const double it = bp[0].inv_t, t = bp[0].t;
+  const double eta_l = lane < nvalid ? bp[lane].h * it : 0.0;
+  const double xp_l = exp(eta_l), xm_l = exp(-eta_l);  // this lane's output: e^{eta}, e^{-eta}
+  const double al = (R - d0) * it, be = (R + d0) * it;
+  const double eam = exp(fmin(-al, 700.0)), eap = exp(fmin(al, 700.0));
+  const double ebm = exp(fmin(-be, 700.0)), ebp = exp(fmin(be, 700.0));
+  for (int j = 0; j < nvalid; ++j) {
+    const double xp = __shfl_sync(kFull, xp_l, j), xm = __shfl_sync(kFull, xm_l, j);
+    const double h = bp[j].h;
+    const double eta = h * it;  // the same bits as output j's lane computed
+    const double ps = al + eta, ms = be - eta;
+    double e1 = __double2hiint(ps) >= 0 ? eam * xm : eap * xp;
+    double e2 = __double2hiint(ms) >= 0 ? ebm * xp : ebp * xm;
+    if (beyond_exp40(ps)) e1 = 0.0;
+    if (beyond_exp40(ms)) e2 = 0.0;
+    const double q = e1 + e2 + e1 * e2;
+    const double f = fmin(fmax(fabs(d0 - h) - as, 0.0) - A, 0.0);
+    double v = 0.0;
+    if (live) v = q == 0.0 ? f : f - t * log1p(q);
+    red[j * 33 + lane] = v;
+  }
+}
+
 // FP64 evaluation of up to 32 buffered near (k-point, band) entries, one per
-// lane, on every output of the item: v = min(max(|d| - |s|, 0) - a, 0)
+// lane, on every output of the item (PRODUCT batches that share T: by split
+// exponentials, flush64_split): v = min(max(|d| - |s|, 0) - a, 0)
 // - T ln(1 + q) per band, q = e1 + e2 + e1 e2 (log1p once per band; the
 // k-point's two bands add their logarithms).
 template <int LAYOUT>
@@ -529,6 +583,12 @@ __device__ __forceinline__ void flush64(const KsumArgs& a, const WorkItem& w, co
     if (kG == kLayoutProduct) {
       const double dd = a.delta[g.delta_off + di];
       ra_f64(dd * dd * eta2, s2, as, R, A);
+      if (split_exp_batch(bp, nvalid, lane)) {
+        flush64_split(bp, nvalid, lane, live, R, A, as, d0, red);
+        const double t = row_total64(red, nvalid, lane);
+        if (lane < nvalid) acc[(b - w.b0) * 32 + lane] += t;
+        continue;
+      }
     }
     for (int j = 0; j < nvalid; ++j) {
       const BParD p = bp[j];
