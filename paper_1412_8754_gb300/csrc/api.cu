@@ -153,13 +153,51 @@ static void item_far_window(const ffe_plan* p, const GroupDesc& g, int b0, int b
   w.sgl_r = std::nextafter((float)(27.0 * 0.69314718055994530942 * tmax + 1e-5), INFINITY);
 }
 
+// Golden plans: the largest Delta^2 any bracket can reach (brackets stay in
+// [lo, hi]; x0 may lie outside); 0 for grid plans.
+static double golden_reach(const ffe_plan* p) {
+  double d2 = 0.0;
+  for (const GoldenState& gs : p->golden0) d2 = std::max({d2, gs.lo * gs.lo, gs.hi * gs.hi, gs.x0 * gs.x0});
+  return d2;
+}
+
+// What the structure of the work items depends on: the launch shape and, per
+// group, its lattice, layout, output counts and tiles -- not the parameter
+// values, which enter only through each segment's windows.
+static std::vector<int64_t> item_signature(const ffe_plan* p) {
+  std::vector<int64_t> s = {p->prec, p->kpt, p->grid, p->block, (int64_t)std::llround(p->item_target),
+                            (int64_t)p->groups.size()};
+  for (const GroupDesc& g : p->groups)
+    s.insert(s.end(), {g.N, g.layout, g.n_delta, g.n_ht, g.n_hblk, g.n_batches, g.hb, g.n_out});
+  return s;
+}
+
+// The far and single-band windows of every segment from the plan's current
+// parameter values, written into the segment's items (their structure stays):
+// the same windows build_items gives.
+static void refresh_item_windows(ffe_plan* p) {
+  const double golden_d2 = golden_reach(p);
+  std::vector<WorkItem> win(p->segs.size());
+  for (size_t i = 0; i < p->segs.size(); ++i) {
+    const Segment& sg = p->segs[i];
+    item_far_window(p, p->groups[sg.group], sg.b0, sg.b1, golden_d2, win[i]);
+  }
+  for (WorkItem& w : p->items) {
+    const WorkItem& x = win[w.seg];
+    w.far_hlo = x.far_hlo;
+    w.far_hhi = x.far_hhi;
+    w.far_tgap = x.far_tgap;
+    w.far_d2max = x.far_d2max;
+    w.sgl_d2min = x.sgl_d2min;
+    w.sgl_r = x.sgl_r;
+  }
+}
+
 void build_items(ffe_plan* p) {
   p->items.clear();
   p->segs.clear();
   const int kset_pts = 32 * p->kpt;
-  double golden_d2 = 0.0;  // golden plans: the largest Delta^2 any bracket can reach
-  for (const GoldenState& gs : p->golden0)  // brackets stay in [lo, hi]; x0 may lie outside
-    golden_d2 = std::max({golden_d2, gs.lo * gs.lo, gs.hi * gs.hi, gs.x0 * gs.x0});
+  const double golden_d2 = golden_reach(p);
   // A small plan gets smaller items, so that the persistent grid's warps all
   // find work: at least about four items per resident warp.
   double work = 0.0;
@@ -232,6 +270,7 @@ void build_items(ffe_plan* p) {
   auto cost = [](const WorkItem& w) { return (double)(w.kset1 - w.kset0) * (w.b1 - w.b0); };
   std::stable_sort(p->items.begin(), p->items.end(),
                    [&](const WorkItem& a, const WorkItem& b) { return cost(a) > cost(b); });
+  p->item_sig = item_signature(p);
 }
 
 void build_mitems(ffe_plan* p) {
@@ -479,7 +518,10 @@ ffe_status plan_upload_params(ffe_context* ctx, ffe_plan* p, cudaStream_t s) {
 ffe_status plan_refill(ffe_context* ctx, ffe_plan* p, cudaStream_t s, bool pinned) {
   const size_t n_items = p->items.size();
   apply_tiles(p, p->variant == kLayoutProductUT);
-  build_items(p);
+  if (!p->item_sig.empty() && item_signature(p) == p->item_sig)
+    refresh_item_windows(p);  // same shapes: only the windows follow the new values
+  else
+    build_items(p);
   if (p->items.size() != n_items) return set_err(ctx, "plan refill changed its work items"), FFE_EINTERNAL;
   std::vector<HostCopy> copies;
   copies.push_back(HostCopy{p->d_items, p->items.data(), p->items.size() * sizeof(WorkItem)});

@@ -62,6 +62,7 @@ struct ffe_plan {
   std::vector<ffe::GroupDesc> groups;
   std::vector<ffe::WorkItem> items;
   std::vector<ffe::Segment> segs;
+  std::vector<int64_t> item_sig;  // the shapes items/segs were built for (item_signature)
   std::vector<ffe::MItem> mitems;
   std::vector<ffe::Line> lines;
   std::vector<double> delta;

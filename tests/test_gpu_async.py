@@ -146,3 +146,27 @@ def test_cached_scan_plan_refilled_with_new_temperatures():
     for name in ("delta_star", "omega_star", "omega_lo", "idx_star"):
         assert np.array_equal(again[0][name], ref[0][name]), name
     assert np.array_equal(again[1], ref[1]) and np.array_equal(again[2], ref[2])
+
+
+@pytest.mark.parametrize("kind", [ffe.FFE_SEARCH_GRID, ffe.FFE_SEARCH_GOLDEN])
+def test_refilled_plan_with_new_values_equals_a_fresh_plan(kind):
+    """A cached scan plan refilled with other q, h, T values and another Delta range (same
+    shapes: the work items keep their structure and only their windows are recomputed) gives
+    the same bits as a plan built for those values from scratch; many h blocks, so many
+    segments with different windows."""
+    N, U = 64, 4.0
+    n = 48 if kind == ffe.FFE_SEARCH_GRID else 12
+    first = dict(qx=np.linspace(0.0, 0.5, 5), h=np.linspace(0.0, 0.12, 40), T=np.array([0.002, 0.01]), lo=0.0,
+                 hi=0.2)
+    second = dict(qx=np.linspace(0.0, 0.3, 5), h=np.linspace(0.02, 0.2, 40), T=np.array([0.004, 0.03]), lo=0.0,
+                  hi=0.3)
+    with ffe.Context(prec=ffe.FFE_FP32C, U=U) as ctx:
+        for v in (first, second):
+            again = ctx.phase_scan(N, v["qx"], np.zeros(5), v["h"], v["T"], search=kind, n=n, lo=v["lo"],
+                                   hi=v["hi"])
+    with ffe.Context(prec=ffe.FFE_FP32C, U=U) as fresh:
+        v = second
+        ref = fresh.phase_scan(N, v["qx"], np.zeros(5), v["h"], v["T"], search=kind, n=n, lo=v["lo"], hi=v["hi"])
+    for name in ("delta_star", "omega_star", "omega_lo", "idx_star", "flags"):
+        assert np.array_equal(again[0][name], ref[0][name]), name
+    assert np.array_equal(again[1], ref[1]) and np.array_equal(again[2], ref[2])
