@@ -203,28 +203,35 @@ struct MVal<true> {
   }
 };
 
-// The four band values u_lo, u_hi (k+Q/2) and d_lo, d_hi (-k+Q/2), minus mu.
+// The band values u_lo, u_hi at k+Q/2, minus mu, in v[0], v[1], and copies of
+// them in v[2], v[3] for the sum against -h: M sums min(d, -h) over every k,
+// with d = E(-k+Q/2) - mu = u(-k), and k -> -k is a bijection of the lattice
+// (the bands are 2 pi-periodic), so that sum equals the sum of min(u, -h).
 __device__ __forceinline__ void band_values(const ModelParams& m, const ModelDF&, const TabRowD& rx,
                                             const TabRowD& ry, const TabRowDF&, const TabRowDF&, double (&v)[4]) {
   band_pair<double>(m, rx.cp, ry.cp, rx.sp, ry.sp, v[0], v[1]);
-  band_pair<double>(m, rx.cm, ry.cm, rx.sm, ry.sm, v[2], v[3]);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) v[i] -= m.mu;
+  v[0] -= m.mu;
+  v[1] -= m.mu;
+  v[2] = v[0];
+  v[3] = v[1];
 }
 __device__ __forceinline__ void band_values(const ModelParams&, const ModelDF& md, const TabRowD&, const TabRowD&,
                                             const TabRowDF& rx, const TabRowDF& ry, DF (&v)[4]) {
   auto f = [](float2 a) { return DF{a.x, a.y}; };
   band_pair_df(md, f(rx.cp), f(ry.cp), f(rx.sp), f(ry.sp), v[0], v[1]);
-  band_pair_df(md, f(rx.cm), f(ry.cm), f(rx.sm), f(ry.sm), v[2], v[3]);
   const DF nmu = df_neg(md.mu);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) v[i] = df_add(v[i], nmu);
+  v[0] = df_add(v[0], nmu);
+  v[1] = df_add(v[1], nmu);
+  v[2] = v[0];
+  v[3] = v[1];
 }
 
 // M(h) for up to 32 h values per item, over the item's k range.
 //
 // With u = E(k+Q/2) - mu and d = E(-k+Q/2) - mu the summand is
-// min(u, h) + min(d, -h), so each band value contributes either itself or
+// min(u, h) + min(d, -h); summed over the lattice, the d of point k is the u
+// of point -k, so every d is taken as a copy of u (band_values: one band
+// evaluation per k-point), and each value contributes either itself or
 // +-h.  Lane j of a warp owns h_j.  A value below every h of the item (u) or
 // below every -h (d) adds itself to every h: it goes to a per-lane total S.
 // A value above all of them adds +h_j (u) or -h_j (d) to every h: it goes to
@@ -290,14 +297,14 @@ __global__ void __launch_bounds__(256) normal_kernel(const ModelParams m,
     for (int i = 0; i < NV; ++i) v[i] = V::zero();
     unsigned rare = 0;
     if (k < k1) {
-      if constexpr (NB3) {
-        const E3D eu = e3d[g.e3_off + k], ed = e3d[g.e3_off + (int64_t)g.N * g.N + k];
+      if constexpr (NB3) {  // the -k+Q/2 values by the same relabelling (band_values)
+        const E3D eu = e3d[g.e3_off + k];
         v[0] = eu.x - m.mu;
         v[1] = eu.y - m.mu;
         v[2] = eu.z - m.mu;
-        v[3] = ed.x - m.mu;
-        v[4] = ed.y - m.mu;
-        v[5] = ed.z - m.mu;
+        v[3] = v[0];
+        v[4] = v[1];
+        v[5] = v[2];
       } else {
         const int iy = k / g.N;
         const int ix = k - iy * g.N;
