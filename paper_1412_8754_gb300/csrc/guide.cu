@@ -131,11 +131,25 @@ void fill_explicit(ffe_plan* p, const ffe_scan* sc, int q0, const std::vector<in
         p->hlist.push_back(sc->h[ih]);
       }
     g.n_h = n_hq;
+    // Golden: the group's outputs (one per line) ordered by T, then bracket, so
+    // that a batch of 32 outputs shares T and, while its lines take the same
+    // decisions, Delta -- the shared-T evaluation of the k-sum; the lines keep
+    // their order (each points at its own output).
+    std::vector<int> order;
+    for (int j = 0; j < n_sub; ++j)
+      if (!spec[(size_t)q * n_sub + j].alias) order.push_back(j);
+    if (golden)
+      std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const LineSpec &a = spec[(size_t)q * n_sub + x], &b = spec[(size_t)q * n_sub + y];
+        const int tx = pts[x] % sc->n_T, ty = pts[y] % sc->n_T;
+        if (tx != ty) return tx < ty;
+        if (a.wlo != b.wlo) return a.wlo < b.wlo;
+        return a.whi < b.whi;
+      });
     int n_out = 0;
-    for (int j = 0; j < n_sub; ++j) {
+    for (const int j : order) {
       const size_t l = (size_t)q * n_sub + j;
       const LineSpec& ls = spec[l];
-      if (ls.alias) continue;
       const int ih = pts[j] / sc->n_T, it = pts[j] % sc->n_T;
       Line& L = p->lines[l];
       L.out0 = out + n_out;
