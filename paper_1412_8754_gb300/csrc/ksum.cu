@@ -486,9 +486,15 @@ __device__ __forceinline__ bool blocked_band64(double d0, double eta2, double s2
   return m > 0.0 && m * m >= fma((double)w.far_d2max, eta2, s2) * (1.0 + 0x1p-40);
 }
 
-// FP64 near-band entries per warp buffer: a flush takes 32 (one per lane), a
-// k-set adds at most 64 KPT, the remainder after flushing is below 32.
-__host__ __device__ constexpr int kbuf64_entries(int kpt) { return 32 + 64 * kpt; }
+// FP64 near-band entries per warp buffer: a flush takes 64 (two per lane), a
+// k-set adds at most 64 KPT, the remainder after flushing is below 64.
+__host__ __device__ constexpr int kbuf64_entries(int kpt) { return 64 + 64 * kpt; }
+
+// One buffered near (k-point, band) entry of a lane in FP64: |s|, s^2, d0,
+// eta^2 (an empty slot: a band far above every window, which adds nothing).
+struct Ent64 {
+  double as = 1e15, s2 = 1e30, d0 = 0.0, eta2 = 0.0;
+};
 
 // Lane l: the sum of row l (32 doubles, in order) of the warp's FP64 transpose
 // buffer (row stride 33), 0 for l >= nrows.
@@ -528,63 +534,83 @@ __device__ __forceinline__ bool beyond_exp40(double x) {
   return (__double2hiint(x) & 0x7fffffff) >= 0x40440000;  // high word of 40.0
 }
 
-// flush64's band terms of one shared-T batch by split exponentials; each lane's
-// entry (as, d0; R, A at the batch's Delta) on every output j into red[j][lane].
-__device__ __forceinline__ void flush64_split(const BParD* bp, int nvalid, int lane, bool live, double R, double A,
-                                              double as, double d0, double* red) {
+// flush64's band terms of one shared-T batch by split exponentials: the lane's
+// two entries (R, A at the batch's Delta) on every output j, their two log
+// factors under one log1p (log1p(q0) + log1p(q1) = log1p(q0 + q1 + q0 q1)),
+// into red[j][lane].
+__device__ __forceinline__ void flush64_split(const BParD* bp, int nvalid, int lane, const bool (&live)[2],
+                                              const double (&R)[2], const double (&A)[2], const Ent64 (&en)[2],
+                                              double* red) {
   const double it = bp[0].inv_t, t = bp[0].t;
   const double eta_l = lane < nvalid ? bp[lane].h * it : 0.0;
   const double xp_l = exp(eta_l), xm_l = exp(-eta_l);  // this lane's output: e^{eta}, e^{-eta}
-  const double al = (R - d0) * it, be = (R + d0) * it;
-  const double eam = exp(fmin(-al, 700.0)), eap = exp(fmin(al, 700.0));
-  const double ebm = exp(fmin(-be, 700.0)), ebp = exp(fmin(be, 700.0));
+  double al[2], be[2], eam[2], eap[2], ebm[2], ebp[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    al[u] = (R[u] - en[u].d0) * it;
+    be[u] = (R[u] + en[u].d0) * it;
+    eam[u] = exp(fmin(-al[u], 700.0));
+    eap[u] = exp(fmin(al[u], 700.0));
+    ebm[u] = exp(fmin(-be[u], 700.0));
+    ebp[u] = exp(fmin(be[u], 700.0));
+  }
   for (int j = 0; j < nvalid; ++j) {
     const double xp = __shfl_sync(kFull, xp_l, j), xm = __shfl_sync(kFull, xm_l, j);
     const double h = bp[j].h;
     const double eta = h * it;  // the same bits as output j's lane computed
-    const double ps = al + eta, ms = be - eta;
-    double e1 = __double2hiint(ps) >= 0 ? eam * xm : eap * xp;
-    double e2 = __double2hiint(ms) >= 0 ? ebm * xp : ebp * xm;
-    if (beyond_exp40(ps)) e1 = 0.0;
-    if (beyond_exp40(ms)) e2 = 0.0;
-    const double q = e1 + e2 + e1 * e2;
-    const double f = fmin(fmax(fabs(d0 - h) - as, 0.0) - A, 0.0);
-    double v = 0.0;
-    if (live) v = q == 0.0 ? f : f - t * log1p(q);
-    red[j * 33 + lane] = v;
+    double f = 0.0, q = 0.0;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (!live[u]) continue;
+      const double ps = al[u] + eta, ms = be[u] - eta;
+      double e1 = __double2hiint(ps) >= 0 ? eam[u] * xm : eap[u] * xp;
+      double e2 = __double2hiint(ms) >= 0 ? ebm[u] * xp : ebp[u] * xm;
+      if (beyond_exp40(ps)) e1 = 0.0;
+      if (beyond_exp40(ms)) e2 = 0.0;
+      const double qu = e1 + e2 + e1 * e2;
+      q = q + qu + q * qu;
+      f += fmin(fmax(fabs(en[u].d0 - h) - en[u].as, 0.0) - A[u], 0.0);
+    }
+    red[j * 33 + lane] = q == 0.0 ? f : f - t * log1p(q);
   }
 }
 
-// FP64 evaluation of up to 32 buffered near (k-point, band) entries, one per
-// lane, on every output of the item (PRODUCT batches that share T: by split
-// exponentials, flush64_split): v = min(max(|d| - |s|, 0) - a, 0)
-// - T ln(1 + q) per band, q = e1 + e2 + e1 e2 (log1p once per band; the
-// k-point's two bands add their logarithms).
+// FP64 evaluation of up to 64 buffered near (k-point, band) entries, entries
+// lane and lane + 32 of each lane, on every output of the item (PRODUCT
+// batches that share T: by split exponentials, flush64_split):
+// v = min(max(|d| - |s|, 0) - a, 0) - T ln(1 + q) per band, q = e1 + e2 + e1 e2;
+// the lane's two entries add their logarithms under one log1p.
 template <int LAYOUT>
 __device__ __forceinline__ void flush64(const KsumArgs& a, const WorkItem& w, const GroupDesc& g, int lane,
                                         const int32_t* buf, int n, double* acc, BParD* bp, double* red) {
   constexpr int kG = (LAYOUT == kLayoutList) ? kLayoutList : kLayoutProduct;
-  const bool live = lane < n;
-  double as = 1e15, s2 = 1e30, d0 = 0.0, eta2 = 0.0;
-  if (live) {
-    const int32_t e = buf[lane];
-    KState<double> st;
-    state_at<double>(a, g, e & kKidxMask, (e >> kPairBit) & 1, st);
-    const int sl = (e >> kSlotBit) & 1;
-    as = st.as[sl];
-    s2 = st.s2[sl];
-    d0 = st.d0[sl];
-    eta2 = st.eta2;
+  bool live[2];
+  Ent64 en[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int i = lane + 32 * u;
+    live[u] = i < n;
+    if (live[u]) {
+      const int32_t e = buf[i];
+      KState<double> st;
+      state_at<double>(a, g, e & kKidxMask, (e >> kPairBit) & 1, st);
+      const int sl = (e >> kSlotBit) & 1;
+      en[u].as = st.as[sl];
+      en[u].s2 = st.s2[sl];
+      en[u].d0 = st.d0[sl];
+      en[u].eta2 = st.eta2;
+    }
   }
   for (int b = w.b0; b < w.b1; ++b) {
     int di;
     const int nvalid = stage_batch<double, kG>(a, g, b, lane, bp, di);
-    double R = 0.0, A = 0.0;
+    double R[2] = {0.0, 0.0}, A[2] = {0.0, 0.0};
     if (kG == kLayoutProduct) {
       const double dd = a.delta[g.delta_off + di];
-      ra_f64(dd * dd * eta2, s2, as, R, A);
+#pragma unroll
+      for (int u = 0; u < 2; ++u) ra_f64(dd * dd * en[u].eta2, en[u].s2, en[u].as, R[u], A[u]);
       if (split_exp_batch(bp, nvalid, lane)) {
-        flush64_split(bp, nvalid, lane, live, R, A, as, d0, red);
+        flush64_split(bp, nvalid, lane, live, R, A, en, red);
         const double t = row_total64(red, nvalid, lane);
         if (lane < nvalid) acc[(b - w.b0) * 32 + lane] += t;
         continue;
@@ -592,14 +618,17 @@ __device__ __forceinline__ void flush64(const KsumArgs& a, const WorkItem& w, co
     }
     for (int j = 0; j < nvalid; ++j) {
       const BParD p = bp[j];
-      if (kG == kLayoutList) ra_f64(p.d2 * eta2, s2, as, R, A);
-      double v = 0.0;
-      if (live) {
-        double q, f;
-        band_term_f64(R, A, as, d0, p.h, p.inv_t, q, f);
-        v = q == 0.0 ? f : f - p.t * log1p(q);
+      double f = 0.0, q = 0.0;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (!live[u]) continue;
+        if (kG == kLayoutList) ra_f64(p.d2 * en[u].eta2, en[u].s2, en[u].as, R[u], A[u]);
+        double qu, fu;
+        band_term_f64(R[u], A[u], en[u].as, en[u].d0, p.h, p.inv_t, qu, fu);
+        q = q + qu + q * qu;
+        f += fu;
       }
-      red[j * 33 + lane] = v;
+      red[j * 33 + lane] = q == 0.0 ? f : f - p.t * log1p(q);
     }
     const double t = row_total64(red, nvalid, lane);
     if (lane < nvalid) acc[(b - w.b0) * 32 + lane] += t;
@@ -694,10 +723,11 @@ __device__ __forceinline__ void item64(const KsumArgs& a, const WorkItem& w, con
       }
     __syncwarp();
     int done = 0;
-    for (; n_near - done >= 32; done += 32) flush64<LAYOUT>(a, w, g, lane, nbuf + done, 32, acc, bp, red);
+    for (; n_near - done >= 64; done += 64) flush64<LAYOUT>(a, w, g, lane, nbuf + done, 64, acc, bp, red);
     if (done > 0) {
       __syncwarp();
-      if (lane < n_near - done) nbuf[lane] = nbuf[done + lane];  // fewer than 32 left
+      // fewer than 64 left, moved from [done, ...) to [0, ...): done >= 64, so the ranges do not overlap
+      for (int i = lane; i < n_near - done; i += 32) nbuf[i] = nbuf[done + i];
       __syncwarp();
       n_near -= done;
     }
