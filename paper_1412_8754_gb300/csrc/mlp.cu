@@ -10,8 +10,10 @@
 // moments are FP32.  Every reduction over samples is a fixed-order sum of
 // per-block partials (deterministic).
 //
-// One CTA of 128 threads owns 128 samples (the MMA's M): thread r owns sample
-// r, which is TMEM lane r of the accumulator (warp w reads lanes 32w..32w+31).
+// One CTA owns 128 samples (the MMA's M) with kSplit threads per sample:
+// thread t works on sample t mod 128, which is TMEM lane t mod 128 of the
+// accumulator (warp w reads lanes 32 (w mod 4) .. 32 (w mod 4) + 31), and on
+// kCols consecutive columns of it, so every SIMT epilogue is kCols deep.
 // Each 128 x 128 product is eight K = 16 MMAs issued by one thread from two
 // shared-memory tiles (the activations and the weights) and committed to an
 // mbarrier; the weights' tiles arrive by one bulk asynchronous copy (TMA)
