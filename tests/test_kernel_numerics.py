@@ -101,3 +101,78 @@ def test_newton_steps_refine_fp32_eigenvalues_to_fp64():
         ref = np.linalg.eigvalsh(A)
         errs.append(np.max(np.abs(e - ref)) / np.max(np.abs(ref)))
     assert max(errs) < 1e-11 and np.median(errs) < 1e-14, (max(errs), np.median(errs))
+
+
+def _bands_app_a(kx, ky, t1=-1.0, t2=1.3, t3=-0.85, t4=-0.85):
+    """App. A: the two eigenvalues of the 2 x 2 hopping matrix at (kx, ky), written out here."""
+    cx, cy = np.cos(kx), np.cos(ky)
+    t11 = -2.0 * (t1 * cx + t2 * cy) - 4.0 * t3 * cx * cy
+    t22 = -2.0 * (t2 * cx + t1 * cy) - 4.0 * t3 * cx * cy
+    t12 = -4.0 * t4 * np.sin(kx) * np.sin(ky)
+    mean, root = 0.5 * (t11 + t22), np.sqrt((0.5 * (t11 - t22)) ** 2 + t12 ** 2)
+    return mean - root, mean + root
+
+
+@pytest.mark.parametrize("q", [(0.0, 0.0), (0.31, 0.0), (0.2, -0.13), (np.pi / 8, np.pi / 16)])
+def test_minus_k_band_values_are_the_plus_k_values_relabelled(q):
+    """The normal-state sums take the spin-down band values E(-k + Q/2) of the lattice as the
+    spin-up values E(k + Q/2) relabelled k -> -k: on the N x N lattice (k = 2 pi (i, j) / N) the
+    two multisets agree, so every lattice sum of a function of them agrees, here
+    sum_k min(E - mu, -h), to FP64 rounding."""
+    N, mu = 48, 1.54
+    i = 2.0 * np.pi * np.arange(N) / N
+    kx, ky = np.meshgrid(i, i, indexing="ij")
+    up = np.concatenate([e.ravel() for e in _bands_app_a(kx + q[0] / 2, ky + q[1] / 2)]) - mu
+    dn = np.concatenate([e.ravel() for e in _bands_app_a(-kx + q[0] / 2, -ky + q[1] / 2)]) - mu
+    assert np.allclose(np.sort(up), np.sort(dn), rtol=0, atol=1e-13)
+    for h in (0.0, 0.05, 0.15):
+        a, b = np.sum(np.minimum(dn, -h)), np.sum(np.minimum(up, -h))
+        assert abs(a - b) <= 1e-12 * abs(a)
+
+
+def test_split_exponentials_equal_the_direct_exponentials():
+    """FP64 near bands of a batch with one T: with P = R - d0 + h, M = R + d0 - h, the arguments
+    {|R - |d||, R + |d|} / T (d = d0 - h) are {|P|, |M|} / T, and e^{-|P|/T} is e^{-alpha} e^{-eta}
+    (P >= 0) or e^{alpha} e^{eta} (P < 0) with alpha = (R - d0)/T, eta = h/T (M likewise with
+    beta = (R + d0)/T, -eta); arguments capped at 700 and |eta| <= 600 keep every factor taken
+    finite; agreement with the direct exponentials within the arguments' own rounding."""
+    rng = np.random.default_rng(64)
+    n = 200000
+    T = rng.uniform(1e-3, 0.05, n)
+    h = rng.uniform(-0.2, 0.2, n)
+    d0 = rng.uniform(-3.0, 3.0, n)
+    R = np.abs(d0 - h) + rng.uniform(-40.0, 40.0, n) * T  # near: |R - |d|| / T < 40
+    R = np.maximum(R, 0.0)
+    d = d0 - h
+    y = np.stack([np.abs(R - np.abs(d)), R + np.abs(d)]) / T
+    direct = np.where(y < 40.0, np.exp(-np.minimum(y, 700.0)), 0.0)
+    it = 1.0 / T
+    al, be, eta = (R - d0) * it, (R + d0) * it, h * it
+    assert np.all(np.abs(eta) <= 600.0)
+    eam, eap = np.exp(np.minimum(-al, 700.0)), np.exp(np.minimum(al, 700.0))
+    ebm, ebp = np.exp(np.minimum(-be, 700.0)), np.exp(np.minimum(be, 700.0))
+    xp, xm = np.exp(eta), np.exp(-eta)
+    ps, ms = al + eta, be - eta
+    with np.errstate(over="ignore"):  # np.where forms both products; the unselected one may overflow
+        e1 = np.where(ps >= 0.0, eam * xm, eap * xp)
+        e2 = np.where(ms >= 0.0, ebm * xp, ebp * xm)
+    e1 = np.where(np.abs(ps) >= 40.0, 0.0, e1)
+    e2 = np.where(np.abs(ms) >= 40.0, 0.0, e2)
+    assert np.all(np.isfinite(e1)) and np.all(np.isfinite(e2))
+    split = np.sort(np.stack([e1, e2]), axis=0)
+    want = np.sort(direct, axis=0)
+    both = np.all(np.abs(np.sort(np.stack([np.abs(ps), np.abs(ms)]), axis=0) - np.sort(y, axis=0)) < 1e-9, axis=0)
+    both &= np.all(np.abs(np.sort(y, axis=0) - 40.0) > 1e-6, axis=0)  # away from the cut-off
+    scale = (np.abs(al) + np.abs(eta) + np.abs(be) + 1.0) * 2.3e-16
+    assert np.all(np.abs(split - want)[:, both] <= 8.0 * scale[both] * np.maximum(want[:, both], 1e-300) + 1e-300)
+
+
+def test_two_log_factors_under_one_log1p():
+    """log1p(q0) + log1p(q1) = log1p(q0 + q1 + q0 q1) (the FP64 flush puts a lane's two near
+    entries under one logarithm), to a few FP64 ulp, for q from 1e-18 (a factor e^-40) to 3."""
+    rng = np.random.default_rng(3)
+    q0 = np.concatenate([10.0 ** rng.uniform(-18, np.log10(3.0), 50000), [0.0, 3.0]])
+    q1 = np.concatenate([10.0 ** rng.uniform(-18, np.log10(3.0), 50000), [5e-18, 0.0]])
+    lhs = np.log1p(q0) + np.log1p(q1)
+    rhs = np.log1p(q0 + q1 + q0 * q1)
+    assert np.all(np.abs(lhs - rhs) <= 4.0 * np.spacing(np.maximum(lhs, 1e-300)) + 1e-300)
