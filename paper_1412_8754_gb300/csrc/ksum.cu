@@ -530,8 +530,9 @@ __device__ __forceinline__ bool split_exp_batch(const BParD* bp, int nvalid, int
 
 // |x| >= kExpNegligible (40) from the high word of x: the order of the bit
 // patterns of non-negative doubles is their numeric order.
+static_assert(kExpNegligible == 40.0, "beyond_exp40 compares against the high word of 40.0");
 __device__ __forceinline__ bool beyond_exp40(double x) {
-  return (__double2hiint(x) & 0x7fffffff) >= 0x40440000;  // high word of 40.0
+  return (__double2hiint(x) & 0x7fffffff) >= 0x40440000;  // high word of 40.0 (low word 0)
 }
 
 // flush64's band terms of one shared-T batch by split exponentials: the lane's
