@@ -263,7 +263,7 @@ def run_extras(ffe, np, torch, stream, workloads):
     return out
 
 
-def run_surrogate(ffe, np, torch, workloads, cfg, ref, full_s, fp64_rate, epochs=20, diagram=True):
+def run_surrogate(ffe, np, torch, workloads, cfg, ref, full_s, fp64_rate, epochs=40, diagram=True):
     """The learned surrogate: ~2M samples at N=512, training, the guided scan of
     the headline workload against its full FP32 scan, and the N=2048 phase
     diagram (golden-section) in its full FP32, guided and sampled FP64 forms."""
