@@ -100,24 +100,29 @@ class Clocks:
         except subprocess.TimeoutExpired:
             self.p.kill()
         self.f.flush()
-        rows = []
-        for line in open(self.f.name):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 10:
-                rows.append(parts)
+        lines = open(self.f.name).read().splitlines()
         os.unlink(self.f.name)
-        inside = rows
-        if self.t0 is not None and self.t1 is not None:
-            inside = [r for r in rows if (w := self._when(r[0])) is not None and self.t0 - 0.05 <= w <= self.t1 + 0.05]
-        if not inside:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples in the timed region"],
-                    "samples": 0, "samples_total": len(rows)}
-        sm = [float(r[2]) for r in inside if r[2].replace(".", "").isdigit()]
-        mx = [float(r[3]) for r in inside if r[3].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in inside for i in range(4) if r[6 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(inside), "interval_ms": 100}
+        return summarize_clocks(lines, self.t0, self.t1)
+
+
+def summarize_clocks(lines, t0=None, t1=None):
+    """Median SM clock, maximum clock and throttle reasons of the nvidia-smi CSV rows
+    (timestamp, index, clocks.sm, clocks.max.sm, power, active, hw_slowdown, hw_thermal_slowdown,
+    sw_thermal_slowdown, sw_power_cap) taken inside [t0, t1] (host wall clock, 50 ms slack)."""
+    rows = [[x.strip() for x in line.split(",")] for line in lines]
+    rows = [r for r in rows if len(r) >= 10]
+    inside = rows
+    if t0 is not None and t1 is not None:
+        inside = [r for r in rows if (w := Clocks._when(r[0])) is not None and t0 - 0.05 <= w <= t1 + 0.05]
+    if not inside:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples in the timed region"],
+                "samples": 0, "samples_total": len(rows)}
+    sm = [float(r[2]) for r in inside if r[2].replace(".", "").isdigit()]
+    mx = [float(r[3]) for r in inside if r[3].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in inside for i in range(4) if r[6 + i].lower() == "active"})
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(inside), "interval_ms": 100}
 
 
 def cpu_baseline(cfg, lines, diagram_lines=None, tol=2e-7):
