@@ -415,7 +415,8 @@ FFE_API ffe_status ffe_surrogate_predict(ffe_surrogate* s, const float* x, int64
 FFE_API ffe_status ffe_surrogate_grad(ffe_surrogate* s, const float* x, const float* t, int64_t n,
                                       float* grad, double* loss, void* stream);
 /* Adam training over `epochs` passes of the samples in their given order
- * (batch a multiple of 64; the tail that does not fill a batch is skipped).
+ * (epochs in [1, 1000000], batch a multiple of 64; the tail that does not
+ * fill a batch is skipped).
  * loss_per_epoch (NULL or [epochs]) receives the mean batch loss. */
 FFE_API ffe_status ffe_surrogate_train(ffe_surrogate* s, const float* x, const float* t, int64_t n,
                                        int32_t epochs, int32_t batch, float lr,

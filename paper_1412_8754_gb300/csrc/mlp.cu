@@ -52,6 +52,7 @@ constexpr int kSplit = 8, kThreads = kSplit * kRows, kCols = kW / kSplit;
 // (n = in, k = out)
 enum { kT2f = 0, kT3f = 1, kT2b = 2, kT3b = 3 };
 constexpr unsigned kWaitLimit = 1u << 26;  // polls of an mbarrier before giving up
+constexpr int kMaxEpochs = 1000000;         // epochs of one training call
 
 struct MlpDev {
   const float* master;          // FP32 parameters (layout above)
@@ -900,8 +901,11 @@ ffe_status ffe_surrogate_grad(ffe_surrogate* s, const float* xraw, const float* 
 ffe_status ffe_surrogate_train_schedule(ffe_surrogate* s, const float* xraw, const float* traw, int64_t n,
                                         int32_t epochs, int32_t batch, const float* lr_per_epoch,
                                         float* loss_per_epoch, void* stream) {
-  if (!s || !xraw || !traw || !lr_per_epoch || n < 1 || epochs < 1 || batch < 64 || batch % 64 != 0)
-    return s ? (set_err(s->ctx, "train: bad arguments (batch a multiple of 64)"), FFE_EINVAL) : FFE_EINVAL;
+  if (!s || !xraw || !traw || !lr_per_epoch || n < 1 || epochs < 1 || epochs > kMaxEpochs || batch < 64 ||
+      batch % 64 != 0)
+    return s ? (set_err(s->ctx, "train: bad arguments (epochs in [1, %d], batch a multiple of 64)", kMaxEpochs),
+                FFE_EINVAL)
+             : FFE_EINVAL;
   for (int ep = 0; ep < epochs; ++ep)
     if (!(lr_per_epoch[ep] > 0.0f)) return set_err(s->ctx, "train: learning rates must be > 0"), FFE_EINVAL;
   (void)stream;
@@ -947,8 +951,9 @@ ffe_status ffe_surrogate_train_schedule(ffe_surrogate* s, const float* xraw, con
 
 ffe_status ffe_surrogate_train(ffe_surrogate* s, const float* xraw, const float* traw, int64_t n, int32_t epochs,
                                int32_t batch, float lr, float* loss_per_epoch, void* stream) {
-  if (!s || epochs < 1 || !(lr > 0.0f))
-    return s ? (set_err(s->ctx, "train: bad arguments"), FFE_EINVAL) : FFE_EINVAL;
+  if (!s || epochs < 1 || epochs > kMaxEpochs || !(lr > 0.0f))
+    return s ? (set_err(s->ctx, "train: bad arguments (epochs in [1, %d], lr > 0)", kMaxEpochs), FFE_EINVAL)
+             : FFE_EINVAL;
   std::vector<float> lrs(epochs, lr);
   return ffe_surrogate_train_schedule(s, xraw, traw, n, epochs, batch, lrs.data(), loss_per_epoch, stream);
 }
