@@ -391,7 +391,8 @@ def run_phase_diagram(ffe, np, torch, workloads, ctx, sur, margin, fp64_rate, U)
 
 
 def measured_peak(key, fallback):
-    """A peak from the driver's measurement file next to this script, else the fallback."""
+    """A peak from the measured-peaks file next to this script (HBM copy bandwidth, BF16 GEMM rate),
+    else the fallback."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return float(json.load(f)[key])
